@@ -1,0 +1,316 @@
+"""Throughput of the IB-FE-IPCS time step on GB300.
+
+A step is one full IPCS time step (tentative-velocity BiCGStab, BCE-IB force
+solve and correction, pressure-increment PCG, velocity-correction PCG) of the
+64x64x256 immersed cylinder with one refinement level in a 2-cell band around
+the wall and domain reduction (32k wall points, pulsatile inflow, nu = 0.02,
+dt = 0.002), mixed precision (FP32 Krylov iterations inside FP64 defect
+correction).  Metric: active leaf cells x steps / second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                    [--precision mixed|fp64] [--workload NAME]
+
+Under torchrun each rank runs an independent replica on its own GPU (the path
+has no exchange step between problems): value = all ranks' cell-steps / the
+slowest rank's time.  --impl reference times the CPU oracle instead (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IPCS cell-steps/s at 1e-6 vs plain FP64 GPU path; %HBM peak; serve p50/p99"
+UNIT = "cell-steps/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload(name):
+    import workloads as W
+    if name == "cylinder_64x64x256_L1":
+        return W.cylinder_refined_64x64x256()
+    if name == "cylinder_16x16x64":
+        return W.cylinder_uniform_16x16x64()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def sample_case(name):
+    """Bounded sample of the workload for the CPU oracle: the same cross-section,
+    grid, bands and point density over 8 coarse cells of the tube's length."""
+    import workloads as W
+    if name == "cylinder_64x64x256_L1":
+        c = W.cylinder_refined_64x64x256()
+        length = 4.0 * 16 / 256
+        M = max(64, int(round(32000 * 16 / 256)))
+        return W.cylinder_case(n=(64, 64, 16), length=length, M=M, seed=2, max_level=1, refine_band=2,
+                               reduce_band=2, nu=c["nu"], dt=c["dt"], a0=1.0, b=(0.5,),
+                               name="cylinder_64x64x16_L1_slab"), "64x64x16 coarse-cell slab of the same tube (16 of 256 cells in z), 2 steps"
+    return workload(name), "full workload, 2 steps"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# algorithmic bytes per stored node copy and launch, by profiling class
+# (FP32 values in the mixed path's inner solves, FP64 otherwise; meta = 2 B)
+def class_bytes(cls, vb):
+    return {
+        0: 2 * vb + 2,                 # Poisson apply: read p, meta; write q
+        1: 7 * vb + 2,                 # Poisson CG update: x rw, r rw, p, q, D^-1 read; z write; meta
+        2: 3 * vb,                     # p = z + beta p: z read, p rw
+        3: 6 * vb + 2,                 # mass apply, 3 components
+        4: 3 * 6 * vb + vb + 2,        # mass CG update, 3 components + D^-1
+        5: 3 * 3 * vb,                 # mass direction update
+        6: 15 * vb + 6 * vb + 2,       # momentum apply: 15 coefficients, 3 in, 3 out
+    }.get(cls)
+
+
+CLASS_NAMES = {0: "k_apply<Poisson> (stencil q = K p, fused p.q)", 1: "k_cg_update<Poisson>",
+               2: "k_cg_p<Poisson>", 3: "k_apply<mass>", 4: "k_cg_update<mass>", 5: "k_cg_p<mass>",
+               6: "k_apply<momentum 15-point>"}
+
+
+def run_native(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2007_02082_gb300 import IBGrid, load_library
+
+    torch.cuda.set_device(local_rank)
+    load_library(build_if_missing=True)
+    case = workload(args.workload)
+    g = IBGrid(case, precision=args.precision, device=local_rank, profile=True)
+    info0 = g.ib_grid_info()
+    cells = info0["n_leaf_cells"]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        g.ipcs_step(1)
+    torch.cuda.synchronize()
+    i1 = g.ib_grid_info()
+    clocks = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()                     # evict the working set from L2 between steps
+        g.ipcs_step(1)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    i2 = g.ib_grid_info()
+    launches = i2["kernel_launches"] - i1["kernel_launches"]
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = cells * args.steps * world / (ms / 1e3)
+
+    # dominant profiled kernel class over the timed region
+    dms = [i2["prof_ms"][k] - i1["prof_ms"][k] for k in range(12)]
+    dn = [i2["prof_launches"][k] - i1["prof_launches"][k] for k in range(12)]
+    dom = max((k for k in CLASS_NAMES if dn[k] > 0), key=lambda k: dms[k])
+    vb = 4 if args.precision == "mixed" else 8
+    per_launch_bytes = class_bytes(dom, vb) * info0["n_valid_slots"]
+    avg_ms = dms[dom] / dn[dom]
+    achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
+    peak, peak_src = peaks()
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            key = f"{args.workload}:{args.precision}:{dom}"
+            traffic = tj.get(key)
+        except Exception:
+            traffic = None
+
+    # end to end through the public API with host buffers: per step, set the
+    # state from pinned host memory, step, read the state back
+    N = info0["n_nodes"]
+    hu = torch.empty((N, 3), dtype=torch.float64, pin_memory=True).numpy()
+    hp = torch.empty((N,), dtype=torch.float64, pin_memory=True).numpy()
+    hu[:] = g.ib_fields_get("U")
+    hp[:] = g.ib_fields_get("P")
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.ib_fields_set("U", hu)
+        g.ib_fields_set("P", hp)
+        g.ipcs_step(1)
+        hu[:] = g.ib_fields_get("U")
+        hp[:] = g.ib_fields_get("P")
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te
+    if dist:
+        tt = torch.tensor([te], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+    e2e = {"value": cells * e2e_steps * world / te, "unit": UNIT,
+           "h2d_bytes_per_step": int(hu.nbytes + hp.nbytes), "d2h_bytes_per_step": int(hu.nbytes + hp.nbytes)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-inner/f64-outer" if args.precision == "mixed" else "f64",
+        "data": "synthetic (seeded analytic geometry)",
+        "config": {"workload": case["name"], "grid": list(case["n"]), "max_level": case["max_level"],
+                   "leaf_cells": cells, "nodes": info0["n_nodes"], "points": info0["n_points"],
+                   "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": CLASS_NAMES[dom], "peak_source": peak_src,
+                     "avg_launch_us": avg_ms * 1e3, "bytes_per_launch": per_launch_bytes},
+        "clocks": ck,
+        "e2e": e2e,
+        "iters_last_step": {k: i2[k] for k in ("iters_mom", "iters_ib", "iters_p", "iters_corr", "outer_mom",
+                                              "outer_p", "outer_corr")},
+    }
+    g.close()
+    return out
+
+
+def run_oracle_sample(name, steps=2):
+    """Time the CPU oracle (as it stands) on a bounded sample of the workload."""
+    from oracle import ibfe
+    case, desc = sample_case(name)
+    o = ibfe.Oracle(case)
+    cells = int(len(o.mesh.leaf_corner))
+    t = time.perf_counter()
+    o.run(steps)
+    t = time.perf_counter() - t
+    return {"value": cells * steps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{desc}: {cells} leaf cells, {t:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="cylinder_64x64x256_L1")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = run_oracle_sample(args.workload)
+        v = cb["value"]
+        out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded analytic geometry)",
+               "config": {"workload": args.workload, "precision": "f64 oracle"},
+               "cpu_baseline": dict(cb, value=v),
+               "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    out = run_native(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = run_oracle_sample(args.workload)
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * ib.h - C ABI of the GB300 IB-FE-IPCS library.
+ *
+ * One object, ib_grid, holds one immersed-boundary flow problem resident on one
+ * GPU: the locally refined, domain-reduced Cartesian grid of P1 Kuhn tetrahedra,
+ * the Lagrangian boundary points, the fields and every Krylov workspace.  The
+ * calls follow the paper's statement of the problem: a box domain discretised
+ * by a box mesh whose vertices form a uniform Cartesian grid (Sec. 3.1), refined
+ * near the immersed boundary (Sec. 3.2) and reduced to the vessel and a band
+ * around it (Sec. 4.3); Lagrangian points X_i with area elements dS_i and
+ * prescribed velocities U_B (Sec. 2.3, Eq. 3, Sec. 2.5); inflow/outflow ports
+ * (Sec. 3.1); kinematic viscosity nu, density rho and time step dt.
+ *
+ * Conventions
+ *   - All functions are extern "C", never throw, and return an ib_status.
+ *     ib_last_error() gives a one-line text for the last failure on a handle.
+ *   - Host arrays are row-major, C order, float64 unless stated.  Coarse-cell
+ *     arrays are [n[2]][n[1]][n[0]] (x fastest).
+ *   - Node fields are returned in the canonical node order: every distinct
+ *     vertex of an active leaf cell (hanging nodes included), sorted by its
+ *     finest-level integer coordinates (z, then y, then x).
+ *   - Device memory comes from desc->dev_alloc / dev_free when given (for
+ *     example a caching allocator), else from cudaMalloc / cudaFree.  The
+ *     library owns everything it allocates and frees it in ib_grid_destroy.
+ *   - Work is enqueued on desc->stream (a cudaStream_t, NULL = legacy default
+ *     stream).  A handle is not thread-safe: one host thread and one stream per
+ *     handle.  Calls that return fields synchronise that stream.
+ *   - Errors: IB_EINVAL for bad arguments or inputs the method cannot accept,
+ *     IB_ESTATE when ib_set_boundary has not succeeded yet, IB_ENOMEM when an
+ *     allocation fails, IB_ENOCONV / IB_EBREAKDOWN when a Krylov solve of a
+ *     step fails (the state before that step is kept: steps are committed only
+ *     when every solve converged), IB_ECUDA for a CUDA runtime error.
+ */
+#ifndef IB_H
+#define IB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ib_grid ib_grid; /* opaque */
+
+typedef enum {
+  IB_OK = 0,
+  IB_EINVAL = 1,
+  IB_ENOMEM = 2,
+  IB_ESTATE = 3,
+  IB_ENOCONV = 4,
+  IB_EBREAKDOWN = 5,
+  IB_ECUDA = 6,
+  IB_ETIMEOUT = 7
+} ib_status;
+
+enum { IB_INLET_VELOCITY = 0, IB_OUTLET_ZERO_P = 1 };
+enum { IB_PARABOLIC = 0 };
+enum { IB_FP64 = 0, IB_MIXED = 1 };
+
+#define IB_MAX_PORTS 8
+#define IB_MAX_HARMONICS 8
+#define IB_MAX_LEVEL 3
+
+/*
+ * A port is a disc on a face of the box (Sec. 3.1: inlet and outlet circles).
+ *   axis, side   face normal axis (0,1,2) and side (0 = low face, 1 = high face)
+ *   center       disc centre (its coordinate along `axis` is ignored)
+ *   radius       disc radius R; a face node is a port node when
+ *                dx*dx + dy*dy <= R*R, evaluated in FP64 without FMA
+ *   kind         IB_INLET_VELOCITY: parabolic velocity u_max(t)(1 - r^2/R^2)
+ *                along the inward normal; IB_OUTLET_ZERO_P: Phi = 0, no velocity
+ *                condition (do-nothing outlet)
+ *   waveform     u_max(t) = a0 + sum_{k=1..n_harm} a[k-1] cos(2 pi k t / period)
+ *                                             + b[k-1] sin(2 pi k t / period)
+ */
+typedef struct {
+  int32_t axis, side;
+  double center[3];
+  double radius;
+  int32_t kind;
+  int32_t profile;
+  int32_t n_harm;
+  double a0, a[IB_MAX_HARMONICS], b[IB_MAX_HARMONICS], period;
+} ib_port;
+
+/*
+ * Grid and solver description.
+ *   origin, extent, n   box [origin, origin + extent] cut into n[0] x n[1] x n[2]
+ *                       coarse cells; every cell is split into the 6 Kuhn
+ *                       tetrahedra around its (0,0,0)-(1,1,1) diagonal
+ *   max_level           refinement levels near the wall (0 = uniform); a coarse
+ *                       cell at level l is cut into 2^l x 2^l x 2^l leaf cells
+ *   refine_band         cells within this Chebyshev distance (coarse cells) of a
+ *                       cell holding a Lagrangian point get max_level; each
+ *                       further band of this width one level less; 2:1 balanced
+ *   reduce_band         domain reduction: a coarse cell is active when it is
+ *                       inside the vessel or within this distance of a point
+ *                       cell; < 0 keeps the whole box
+ *   nu, rho, dt         kinematic viscosity, density, time step
+ *   precision           IB_FP64: every solve in FP64.  IB_MIXED: FP32 operators
+ *                       and preconditioners inside FP64 defect correction; FP64
+ *                       residuals, inner products and IB force solve
+ *   rtol_*              relative residual tolerances of the momentum, Poisson,
+ *                       velocity-correction and force solves (0 = defaults)
+ *   max_iter            iteration cap per Krylov solve (0 = default)
+ *   profile             1: record CUDA events around the solvers' kernel
+ *                       launches (ib_info.prof_ms / prof_launches)
+ *   stream              cudaStream_t on which all work is enqueued
+ *   dev_alloc/dev_free  optional device allocator (ctx = alloc_ctx)
+ */
+typedef struct {
+  double origin[3], extent[3];
+  int32_t n[3];
+  int32_t max_level, refine_band, reduce_band;
+  double nu, rho, dt;
+  int32_t precision;
+  double rtol_mom, rtol_p, rtol_corr, rtol_ib;
+  int32_t max_iter;
+  int32_t profile;          /* 1: time solver kernel launches with CUDA events */
+  int32_t n_ports;
+  ib_port ports[IB_MAX_PORTS];
+  void* stream;
+  void* (*dev_alloc)(size_t bytes, void* ctx);
+  void (*dev_free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+} ib_grid_desc;
+
+/* Counts, spacing ratio and the last step's solver statistics. */
+typedef struct {
+  int64_t n_nodes;          /* canonical nodes (hanging included) */
+  int64_t n_dof;            /* non-hanging nodes */
+  int64_t n_hanging;
+  int64_t n_leaf_cells;     /* active leaf cells, all levels */
+  int64_t n_leaf_cells_level[IB_MAX_LEVEL + 1];
+  int64_t n_active_coarse;
+  int64_t n_bricks;         /* 8x8x8-node storage bricks, all levels */
+  int64_t n_slots;          /* n_bricks * 512 */
+  int64_t n_interface;      /* nodes stored on two levels */
+  int64_t n_points;         /* Lagrangian points M */
+  int64_t af_nnz;           /* nonzeros of A_F */
+  double a_ratio[3];        /* sqrt(mean dS) / h_finest per axis (Sec. 2.5) */
+  int64_t step;             /* committed steps */
+  double time;
+  int32_t iters_mom[3], iters_ib, iters_p, iters_corr[3];
+  int32_t outer_mom, outer_p, outer_corr;
+  double res_mom, res_ib, res_p, res_corr;   /* final relative residuals */
+  int64_t device_bytes;     /* device memory held by the handle */
+  int64_t n_valid_slots;    /* stored node copies, all levels (hanging included) */
+  /* with desc.profile: accumulated device time and launch count per kernel
+     class since ib_set_boundary; class = base + {0 operator apply, 1 vector
+     update, 2 direction update}, base 0 Poisson, 3 mass, 6 momentum */
+  double prof_ms[12];
+  int64_t prof_launches[12];
+  int64_t kernel_launches;  /* kernels launched by this process's library so far */
+} ib_info;
+
+/* Field identifiers for ib_fields_get / ib_fields_set. */
+enum {
+  IB_FIELD_U = 0,           /* velocity, double [n_nodes][3]          (get/set) */
+  IB_FIELD_P = 1,           /* pressure, double [n_nodes]             (get/set) */
+  IB_FIELD_PHI = 2,         /* last pressure increment, double [n_nodes] (get) */
+  IB_FIELD_U_TENT = 3,      /* last tentative velocity u~, [n_nodes][3]  (get) */
+  IB_FIELD_U_IB = 4,        /* last IB-corrected velocity, [n_nodes][3]  (get) */
+  IB_FIELD_F_LAG = 5,       /* last Lagrangian force F, double [M][3]    (get) */
+  IB_FIELD_B_F = 6,         /* last right-hand side B_F, double [M][3]   (get) */
+  IB_FIELD_NODE_Q = 7,      /* finest integer coordinates, int32 [n_nodes][3] */
+  IB_FIELD_NODE_FLAGS = 8,  /* uint8 [n_nodes]: 1 hanging, 2 velocity Dirichlet,
+                               4 outlet (Phi = 0), 8 inlet, 16 boundary */
+  IB_FIELD_ACTIVE = 9,      /* uint8 coarse active mask [n2][n1][n0] */
+  IB_FIELD_LEVEL = 10,      /* uint8 coarse level map [n2][n1][n0] */
+  IB_FIELD_IB_ORIGIN = 11,  /* int32 [M][3] support origin on the finest grid */
+  IB_FIELD_IB_WEIGHTS = 12, /* double [M][64] delta weights (0 where missing) */
+  IB_FIELD_IB_FREE = 13     /* uint8 [M][64]: 1 existing free node, 2 existing
+                               non-free node, 0 missing */
+};
+
+/*
+ * ib_grid_create: validate the description and allocate an empty handle.
+ * The grid itself is built by ib_set_boundary (it depends on the points).
+ * Errors: IB_EINVAL (n <= 0, extent <= 0, max_level outside [0, IB_MAX_LEVEL],
+ * bands < 1 where used, nu/dt/rho <= 0, ports not on a box face, more than
+ * IB_MAX_PORTS ports, no outlet port), IB_ENOMEM.
+ */
+ib_status ib_grid_create(const ib_grid_desc* desc, ib_grid** out);
+
+/*
+ * ib_set_boundary: give the immersed boundary and build everything that depends
+ * on it (Sec. 2.3, Eq. 17-22; Sec. 3.2; Sec. 4.3):
+ *   M        number of Lagrangian points (>= 0)
+ *   X        host double [M][3], point coordinates inside the box
+ *   dS       host double [M], area elements (> 0)
+ *   UB       host double [M][3] prescribed velocities, or NULL for a rigid wall
+ *   inside   host uint8 [n2][n1][n0], 1 for coarse cells inside the vessel, or
+ *            NULL (only allowed when reduce_band < 0)
+ * Builds the level map, active cells, node numbering, hanging-node constraints,
+ * boundary and port masks, delta weights (Eq. 17-18), the force matrix A_F
+ * (Eq. 22) and its solver workspace, then resets u = p = 0 and t = 0.
+ * All host inputs are copied.  Errors: IB_EINVAL (a point outside the box, an
+ * IB support that touches a hanging node or a coarser level, a non-finite
+ * input, no pressure-Dirichlet node), IB_ENOMEM, IB_ECUDA.
+ */
+ib_status ib_set_boundary(ib_grid* g, int64_t M, const double* X, const double* dS,
+                          const double* UB, const uint8_t* inside);
+
+/*
+ * ipcs_step: advance nsteps time steps of the combined algorithm (Sec. 2.4):
+ * tentative velocity (Eq. 9), IB force solve and correction (Eq. 14, 19-21),
+ * pressure-increment Poisson solve (Eq. 12), velocity correction and pressure
+ * update.  nsteps = 0 is a no-op.  Synchronises the stream after every step to
+ * read its status; on IB_ENOCONV / IB_EBREAKDOWN the state of the last
+ * committed step is kept.
+ */
+ib_status ipcs_step(ib_grid* g, int32_t nsteps);
+
+/*
+ * ib_fields_get / ib_fields_set: copy a field out of / into the handle (see the
+ * IB_FIELD_* list for types and shapes).  `bytes` must equal the field size.
+ * dst/src are device pointers when *_on_device != 0, host pointers otherwise.
+ * Setting U or P writes every stored copy and then re-imposes the hanging-node
+ * constraint (a hanging node takes the mean of its parents).
+ */
+ib_status ib_fields_get(ib_grid* g, int32_t field, void* dst, size_t bytes, int32_t dst_on_device);
+ib_status ib_fields_set(ib_grid* g, int32_t field, const void* src, size_t bytes, int32_t src_on_device);
+
+/* ib_grid_info: counts and the last step's statistics. */
+ib_status ib_grid_info(const ib_grid* g, ib_info* out);
+
+/* ib_last_error: text of the last error on g (never NULL; "" if none). */
+const char* ib_last_error(const ib_grid* g);
+
+/* ib_grid_destroy: free every resource of g (NULL is a no-op). */
+void ib_grid_destroy(ib_grid* g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IB_H */

@@ -1,0 +1,131 @@
+// Device-side view of the composite grid and shared helpers.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ibg {
+
+// Every kernel launch of the library goes through launch_kernel, which counts
+// it (ib_info.kernel_launches).
+extern std::atomic<long long> g_launches;
+
+template <typename... KArgs, typename... Args>
+inline void launch_kernel(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          Args&&... args) {
+  k<<<grid, block, smem, st>>>(static_cast<KArgs>(args)...);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+#define IBG_LAUNCH(k, grid, block, smem, st, ...) \
+  ::ibg::launch_kernel(k, dim3(grid), dim3(block), size_t(smem), st, __VA_ARGS__)
+
+constexpr int DBS = 8;          // brick edge (nodes)
+constexpr int DBV = 512;        // nodes per brick = threads per brick CTA
+constexpr int TILE = 10;        // brick plus a one-node halo
+constexpr int TILE3 = 1000;
+
+// per-slot metadata bits (mirror of setup.hpp)
+constexpr uint16_t D_VALID = 1u << 8, D_HANG = 1u << 9, D_DUP = 1u << 10,
+                   D_VDIR = 1u << 11, D_PDIR = 1u << 12;
+
+struct DevGrid {
+  int32_t nbricks;
+  int64_t nslots;
+  const int32_t* __restrict__ blev;   // [nbricks]
+  const int32_t* __restrict__ bnbr;   // [nbricks][27]
+  const uint16_t* __restrict__ meta;  // [nslots]
+  double h[4][3];                     // cell spacing per level
+  // nodes stored on two levels: coarse owner, fine copy, hanging children
+  int32_t n_if;
+  const int32_t* __restrict__ if_c;
+  const int32_t* __restrict__ if_f;
+  const int32_t* __restrict__ if_off;
+  const int32_t* __restrict__ if_kid;
+  // hanging nodes and their parents (fine-level slots)
+  int32_t n_hang;
+  const int32_t* __restrict__ hg;
+  const int32_t* __restrict__ hp1;
+  const int32_t* __restrict__ hp2;
+};
+
+// Krylov scalars of one right-hand side (one velocity component or Phi).
+struct KState {
+  double rz, rz_new, pq, alpha, beta, rr, bb, tol2;
+  double rho, omega, rv, ts, tt;
+  int32_t iter, max_iter, done, status;   // status: 0 ok, 4 no convergence, 5 breakdown
+};
+
+__device__ __forceinline__ int tile_index(int lx, int ly, int lz) {   // l in [-1, 8]
+  return ((lz + 1) * TILE + (ly + 1)) * TILE + (lx + 1);
+}
+
+// Load x (ncomp components, component stride cs) of this brick plus a one-node
+// halo into tile[c*1000 + ...]; missing neighbours read as zero.
+template <typename T>
+__device__ __forceinline__ void load_tile(T* tile, const T* __restrict__ x, int64_t cs, int ncomp,
+                                          const int32_t* __restrict__ nb27) {
+  for (int t = threadIdx.x; t < TILE3; t += blockDim.x) {
+    int hx = t % TILE, hy = (t / TILE) % TILE, hz = t / (TILE * TILE);
+    int lx = hx - 1, ly = hy - 1, lz = hz - 1;
+    int ox = lx < 0 ? -1 : (lx > 7 ? 1 : 0);
+    int oy = ly < 0 ? -1 : (ly > 7 ? 1 : 0);
+    int oz = lz < 0 ? -1 : (lz > 7 ? 1 : 0);
+    int nb = nb27[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+    int64_t s = (int64_t)nb * DBV + (((lz & 7) * DBS + (ly & 7)) * DBS + (lx & 7));
+    for (int c = 0; c < ncomp; ++c) tile[c * TILE3 + t] = nb >= 0 ? x[c * cs + s] : T(0);
+  }
+}
+
+// Block-wide sum of NV doubles (blockDim.x a multiple of 32, <= 1024).
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [32*NV] */) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  __syncthreads();
+  if (lane == 0)
+    for (int k = 0; k < NV; ++k) sh[k * 32 + w] = v[k];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      v[k] = lane < nw ? sh[k * 32 + lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+  }
+}
+
+// Deterministic grid reduction: every block writes its NV partials, the last
+// block to arrive sums all partials in block order and returns true (only in
+// that block; totals in tot[] are valid in thread 0).  The counter is reset.
+template <int NV>
+__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* __restrict__ partials,
+                                              unsigned* __restrict__ counter, double (&tot)[NV]) {
+  __shared__ double sh[32 * NV];
+  __shared__ bool last;
+  block_sum<NV>(v, sh);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NV; ++k) partials[(int64_t)blockIdx.x * NV + k] = v[k];
+    __threadfence();
+    unsigned prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double acc[NV];
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  // fixed order: thread t sums blocks t, t+blockDim, ... ; then a fixed tree
+  for (int64_t b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + b * NV + k);
+  block_sum<NV>(acc, sh);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NV; ++k) tot[k] = acc[k];
+    *counter = 0u;
+  }
+  return true;
+}
+
+}  // namespace ibg

@@ -1,0 +1,986 @@
+// Matrix-free P1 operators on the brick-stored composite grid, and the Krylov
+// solvers of the IPCS step (Sec. 2.2, Eq. 9 and Eq. 12; velocity correction).
+//
+// Every operator is applied per level on the level's own node lattice: one CTA
+// per 8x8x8-node brick stages the brick plus a one-node halo in shared memory
+// and every thread produces one node's row.  The constrained (hanging-node)
+// operator P^T (sum_l A_l) P is completed by fe_sync (sum of the two stored
+// copies of an interface node plus half of each hanging child) and fe_expand
+// (hanging value = mean of parents).  Inner products run in FP64 with a fixed
+// reduction order (block partials, then one block sums them in block order), so
+// results are bitwise reproducible.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fe.hpp"
+
+namespace ibg {
+
+std::atomic<long long> g_launches{0};
+
+// ---------------------------------------------------------------- tables
+__constant__ int8_t c_sten[15][3];
+__constant__ int16_t c_toff[15];               // tile offset of each stencil slot
+__constant__ int8_t c_slot_of_rel[27];
+__constant__ uint8_t c_massw[256][15];         // sum over tets of (1 + delta_nb), units V/120
+__constant__ int8_t c_stiffw[256][7][3];       // sum over tets of g_n,a g_b,a, units (V/6)/h_a^2
+__constant__ int8_t c_kperm[6][3];
+
+static const int8_t h_sten[15][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                                     {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {0, 1, 1},
+                                     {0, -1, -1}, {1, 0, 1}, {-1, 0, -1}, {1, 1, 1},  {-1, -1, -1}};
+static const int8_t h_kperm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+cudaError_t fe_init_tables() {
+  int8_t slot_of_rel[27];
+  std::memset(slot_of_rel, -1, sizeof(slot_of_rel));
+  int16_t toff[15];
+  for (int k = 0; k < 15; ++k) {
+    slot_of_rel[(h_sten[k][2] + 1) * 9 + (h_sten[k][1] + 1) * 3 + (h_sten[k][0] + 1)] = int8_t(k);
+    toff[k] = int16_t((h_sten[k][2] * TILE + h_sten[k][1]) * TILE + h_sten[k][0]);
+  }
+  // Per incident-cell mask: which Kuhn tetrahedra contain the node, and how
+  // they couple it to its neighbours.  Tet (a1,a2,a3) of a cell has vertices
+  // v0 = 0, v1 = e_a1, v2 = e_a1 + e_a2, v3 = (1,1,1) and barycentric gradients
+  // -e_a1/h, e_a1/h - e_a2/h, e_a2/h - e_a3/h, e_a3/h (integers g below).
+  static uint8_t massw[256][15];
+  static int8_t stiffw[256][7][3];
+  std::memset(massw, 0, sizeof(massw));
+  std::memset(stiffw, 0, sizeof(stiffw));
+  for (int mask = 0; mask < 256; ++mask) {
+    int stf[15][3] = {};
+    for (int c = 0; c < 8; ++c) {
+      if (!(mask >> c & 1)) continue;
+      int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+      int qb = (1 - dx) | ((1 - dy) << 1) | ((1 - dz) << 2);
+      for (int p = 0; p < 6; ++p) {
+        int a1 = h_kperm[p][0], a2 = h_kperm[p][1], a3 = h_kperm[p][2];
+        int vb[4] = {0, 1 << a1, (1 << a1) | (1 << a2), 7};
+        int gr[4][3] = {};
+        gr[0][a1] = -1;
+        gr[1][a1] = 1; gr[1][a2] = -1;
+        gr[2][a2] = 1; gr[2][a3] = -1;
+        gr[3][a3] = 1;
+        int kn = -1;
+        for (int k = 0; k < 4; ++k)
+          if (vb[k] == qb) kn = k;
+        if (kn < 0) continue;
+        for (int k = 0; k < 4; ++k) {
+          int rx = dx - 1 + (vb[k] & 1), ry = dy - 1 + ((vb[k] >> 1) & 1), rz = dz - 1 + ((vb[k] >> 2) & 1);
+          int sl = slot_of_rel[(rz + 1) * 9 + (ry + 1) * 3 + (rx + 1)];
+          if (sl < 0) return cudaErrorInvalidValue;
+          massw[mask][sl] += uint8_t(k == kn ? 2 : 1);
+          for (int a = 0; a < 3; ++a) stf[sl][a] += gr[kn][a] * gr[k][a];
+        }
+      }
+    }
+    for (int sl = 7; sl < 15; ++sl)
+      for (int a = 0; a < 3; ++a)
+        if (stf[sl][a] != 0) return cudaErrorInvalidValue;   // stiffness is 7-point
+    for (int sl = 0; sl < 7; ++sl)
+      for (int a = 0; a < 3; ++a) stiffw[mask][sl][a] = int8_t(stf[sl][a]);
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_sten, h_sten, sizeof(h_sten))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_toff, toff, sizeof(toff))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_slot_of_rel, slot_of_rel, sizeof(slot_of_rel))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_massw, massw, sizeof(massw))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_stiffw, stiffw, sizeof(stiffw))) != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_kperm, h_kperm, sizeof(h_kperm));
+}
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ bool is_dof(uint16_t m, uint16_t dmask) {
+  return (m & D_VALID) && !(m & (D_HANG | D_DUP | dmask));
+}
+
+// row coefficients of the mask-tabulated operators
+template <typename T, int OP>
+__device__ __forceinline__ T table_coef(int mask, int k, const double (&f)[3], double vm) {
+  if (OP == OP_POISSON)
+    return T(double(c_stiffw[mask][k][0]) * f[0] + double(c_stiffw[mask][k][1]) * f[1] +
+             double(c_stiffw[mask][k][2]) * f[2]);
+  return T(double(c_massw[mask][k]) * vm);
+}
+
+enum Post : int { POST_NONE = 0, POST_CG_ALPHA = 1 };
+
+// y = A x on every stored node of a brick; optional fused pre-sync x.y per
+// component, whose total gives p.Ap of the constrained operator and alpha.
+template <typename T, int OP, int NC>
+__global__ void __launch_bounds__(512) k_apply(DevGrid g, const T* __restrict__ x, T* __restrict__ y,
+                                               const T* __restrict__ coef, uint16_t dmask, int post,
+                                               KState* __restrict__ ks, double* __restrict__ partials,
+                                               unsigned* __restrict__ counter) {
+  __shared__ T tile[NC * TILE3];
+  const int b = blockIdx.x;
+  load_tile<T>(tile, x, g.nslots, NC, g.bnbr + 27 * b);
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+  const int64_t s = (int64_t)b * DBV + t;
+  const uint16_t m = g.meta[s];
+  const int ti = tile_index(lx, ly, lz);
+  T out[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) out[c] = T(0);
+  if (m & D_VALID) {
+    const int mask = m & 0xFF;
+    const int lev = g.blev[b];
+    const double hx = g.h[lev][0], hy = g.h[lev][1], hz = g.h[lev][2];
+    const double V = hx * hy * hz;
+    if (OP == OP_POISSON) {
+      const double f[3] = {V / (6.0 * hx * hx), V / (6.0 * hy * hy), V / (6.0 * hz * hz)};
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        T ck = table_coef<T, OP_POISSON>(mask, k, f, 0.0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[c] += ck * tile[c * TILE3 + ti + c_toff[k]];
+      }
+    } else if (OP == OP_MASS) {
+      const double f[3] = {0, 0, 0};
+      const double vm = V / 120.0;
+#pragma unroll
+      for (int k = 0; k < 15; ++k) {
+        T ck = table_coef<T, OP_MASS>(mask, k, f, vm);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[c] += ck * tile[c * TILE3 + ti + c_toff[k]];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 15; ++k) {
+        T ck = coef[(int64_t)k * g.nslots + s];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[c] += ck * tile[c * TILE3 + ti + c_toff[k]];
+      }
+    }
+  }
+  if (m & dmask) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) out[c] = T(0);
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) y[c * g.nslots + s] = out[c];
+  if (post == POST_CG_ALPHA) {
+    double v[NC], tot[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) v[c] = double(tile[c * TILE3 + ti]) * double(out[c]);
+    if (grid_sum_last<NC>(v, partials, counter, tot) && threadIdx.x == 0) {
+      for (int c = 0; c < NC; ++c) {
+        KState& k = ks[c];
+        if (k.done) continue;
+        k.pq = tot[c];
+        if (!(tot[c] > 0.0) || !isfinite(tot[c])) { k.done = 1; k.status = 5; k.alpha = 0.0; continue; }
+        k.alpha = k.rz / tot[c];
+      }
+    }
+  }
+}
+
+template <typename T, int NC>
+__global__ void k_sync(DevGrid g, T* __restrict__ y, uint16_t dmask) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.n_if) return;
+  const int32_t sc = g.if_c[e], sf = g.if_f[e];
+  const bool zero = (g.meta[sc] & dmask) != 0;
+  for (int c = 0; c < NC; ++c) {
+    T* yc = y + c * g.nslots;
+    T tot = yc[sc] + yc[sf];
+    for (int k = g.if_off[e]; k < g.if_off[e + 1]; ++k) tot += T(0.5) * yc[g.if_kid[k]];
+    if (zero) tot = T(0);
+    yc[sc] = tot;
+    yc[sf] = tot;
+  }
+}
+
+template <typename T, int NC>
+__global__ void k_expand(DevGrid g, T* __restrict__ x, T* __restrict__ x2) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= g.n_hang) return;
+  const int32_t s = g.hg[h], p1 = g.hp1[h], p2 = g.hp2[h];
+  for (int c = 0; c < NC; ++c) {
+    T* xc = x + c * g.nslots;
+    xc[s] = T(0.5) * (xc[p1] + xc[p2]);
+    if (x2) {
+      T* x2c = x2 + c * g.nslots;
+      x2c[s] = T(0.5) * (x2c[p1] + x2c[p2]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- CG
+// start: r = b - y (DOFs only), z = D^-1 r, p = z; rz, rr, bb
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict__ b, const T* __restrict__ y,
+                                                  T* __restrict__ r, T* __restrict__ z, T* __restrict__ p,
+                                                  const T* __restrict__ dinv, uint16_t dmask, KState* ks,
+                                                  double* partials, unsigned* counter) {
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = is_dof(m, dmask);
+  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));   // DOF or its duplicate copy
+  double v[3 * NC];
+  for (int c = 0; c < NC; ++c) {
+    const int64_t i = c * g.nslots + s;
+    T rv = keep ? T(b[i] - y[i]) : T(0);
+    T zv = rv * dinv[s];
+    r[i] = rv;
+    z[i] = zv;
+    p[i] = zv;
+    v[3 * c] = dof ? double(rv) * double(zv) : 0.0;
+    v[3 * c + 1] = dof ? double(rv) * double(rv) : 0.0;
+    v[3 * c + 2] = dof ? double(b[i]) * double(b[i]) : 0.0;
+  }
+  double tot[3 * NC];
+  if (grid_sum_last<3 * NC>(v, partials, counter, tot) && threadIdx.x == 0) {
+    for (int c = 0; c < NC; ++c) {
+      KState& k = ks[c];
+      k.rz = tot[3 * c];
+      k.rr = tot[3 * c + 1];
+      k.bb = tot[3 * c + 2];
+      k.iter = 0;
+      k.status = 0;
+      k.alpha = 0.0;
+      k.beta = 0.0;
+      k.done = (k.rr <= k.tol2 * k.bb) ? 1 : 0;
+      if (!isfinite(k.rr)) { k.done = 1; k.status = 5; }
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q, z = D^-1 r; rz_new, rr; beta
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_cg_update(DevGrid g, T* __restrict__ x, T* __restrict__ r,
+                                                   T* __restrict__ z, const T* __restrict__ p,
+                                                   const T* __restrict__ q, const T* __restrict__ dinv,
+                                                   uint16_t dmask, KState* ks, double* partials,
+                                                   unsigned* counter) {
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = is_dof(m, dmask);
+  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
+  double v[2 * NC];
+  for (int c = 0; c < NC; ++c) {
+    v[2 * c] = v[2 * c + 1] = 0.0;
+    if (ks[c].done) continue;
+    const T a = T(ks[c].alpha);
+    const int64_t i = c * g.nslots + s;
+    if (m & D_VALID) x[i] += a * p[i];
+    T rv = keep ? T(r[i] - a * q[i]) : T(0);
+    T zv = rv * dinv[s];
+    r[i] = rv;
+    z[i] = zv;
+    if (dof) {
+      v[2 * c] = double(rv) * double(zv);
+      v[2 * c + 1] = double(rv) * double(rv);
+    }
+  }
+  double tot[2 * NC];
+  if (grid_sum_last<2 * NC>(v, partials, counter, tot) && threadIdx.x == 0) {
+    for (int c = 0; c < NC; ++c) {
+      KState& k = ks[c];
+      if (k.done) continue;
+      k.iter++;
+      k.rr = tot[2 * c + 1];
+      const double rzn = tot[2 * c];
+      if (!isfinite(k.rr) || !isfinite(rzn)) { k.done = 1; k.status = 5; continue; }
+      if (k.rr <= k.tol2 * k.bb) { k.done = 1; continue; }
+      if (k.iter >= k.max_iter) { k.done = 1; k.status = 4; continue; }
+      k.beta = rzn / k.rz;
+      k.rz = rzn;
+    }
+  }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_cg_p(DevGrid g, const T* __restrict__ z, T* __restrict__ p,
+                                              const KState* ks) {
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  for (int c = 0; c < NC; ++c) {
+    if (ks[c].done) continue;
+    const int64_t i = c * g.nslots + s;
+    p[i] = z[i] + T(ks[c].beta) * p[i];
+  }
+}
+
+// ---------------------------------------------------------------- BiCGStab
+// start: r = b - y on DOF slots (and copies), rh = r, p = v = 0; rho = (rh, r)
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restrict__ b, const T* __restrict__ y,
+                                                   T* __restrict__ r, T* __restrict__ rh, T* __restrict__ p,
+                                                   T* __restrict__ v, uint16_t dmask, KState* ks,
+                                                   double* partials, unsigned* counter) {
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = is_dof(m, dmask);
+  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
+  double w[2 * NC];
+  for (int c = 0; c < NC; ++c) {
+    const int64_t i = c * g.nslots + s;
+    T rv = keep ? T(b[i] - y[i]) : T(0);
+    r[i] = rv;
+    rh[i] = rv;
+    p[i] = T(0);
+    v[i] = T(0);
+    w[2 * c] = dof ? double(rv) * double(rv) : 0.0;
+    w[2 * c + 1] = dof ? double(b[i]) * double(b[i]) : 0.0;
+  }
+  double tot[2 * NC];
+  if (grid_sum_last<2 * NC>(w, partials, counter, tot) && threadIdx.x == 0) {
+    for (int c = 0; c < NC; ++c) {
+      KState& k = ks[c];
+      k.rr = tot[2 * c];
+      k.bb = tot[2 * c + 1];
+      k.rho = k.rr;
+      k.alpha = 1.0;
+      k.omega = 1.0;
+      k.beta = 0.0;
+      k.iter = 0;
+      k.status = 0;
+      k.done = (k.rr <= k.tol2 * k.bb) ? 1 : 0;
+      if (!isfinite(k.rr)) { k.done = 1; k.status = 5; }
+    }
+  }
+}
+
+// p = r + beta (p - omega v); ph = D^-1 p
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_bcg_p(DevGrid g, const T* __restrict__ r, T* __restrict__ p,
+                                               const T* __restrict__ v, T* __restrict__ ph,
+                                               const T* __restrict__ dinv, uint16_t dmask, const KState* ks) {
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
+  for (int c = 0; c < NC; ++c) {
+    if (ks[c].done) continue;
+    const int64_t i = c * g.nslots + s;
+    T pv = keep ? T(r[i] + T(ks[c].beta) * (p[i] - T(ks[c].omega) * v[i])) : T(0);
+    p[i] = pv;
+    ph[i] = pv * dinv[s];
+  }
+}
+
+// dot kernels with a post step: mode 0 -> alpha = rho / (rh, v); mode 1 -> omega = (t,s)/(t,t)
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_bcg_dot(DevGrid g, const T* __restrict__ a1, const T* __restrict__ b1,
+                                                 const T* __restrict__ a2, uint16_t dmask, int mode, KState* ks,
+                                                 double* partials, unsigned* counter) {
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = is_dof(m, dmask);
+  double w[2 * NC];
+  for (int c = 0; c < NC; ++c) {
+    const int64_t i = c * g.nslots + s;
+    w[2 * c] = dof ? double(a1[i]) * double(b1[i]) : 0.0;
+    w[2 * c + 1] = (dof && mode == 1) ? double(a2[i]) * double(a2[i]) : 0.0;
+  }
+  double tot[2 * NC];
+  if (grid_sum_last<2 * NC>(w, partials, counter, tot) && threadIdx.x == 0) {
+    for (int c = 0; c < NC; ++c) {
+      KState& k = ks[c];
+      if (k.done) continue;
+      if (mode == 0) {
+        k.rv = tot[2 * c];
+        if (k.rv == 0.0 || !isfinite(k.rv)) { k.done = 1; k.status = 5; k.alpha = 0.0; continue; }
+        k.alpha = k.rho / k.rv;
+      } else {
+        k.ts = tot[2 * c];
+        k.tt = tot[2 * c + 1];
+        k.omega = (k.tt > 0.0) ? k.ts / k.tt : 0.0;
+      }
+    }
+  }
+}
+
+// s = r - alpha v; sh = D^-1 s   (s stored in r's place is avoided: separate buffer)
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_bcg_s(DevGrid g, const T* __restrict__ r, const T* __restrict__ v,
+                                               T* __restrict__ sv, T* __restrict__ sh, const T* __restrict__ dinv,
+                                               uint16_t dmask, const KState* ks) {
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
+  for (int c = 0; c < NC; ++c) {
+    if (ks[c].done) continue;
+    const int64_t i = c * g.nslots + s;
+    T val = keep ? T(r[i] - T(ks[c].alpha) * v[i]) : T(0);
+    sv[i] = val;
+    sh[i] = val * dinv[s];
+  }
+}
+
+// x += alpha ph + omega sh; r = s - omega t; rr, rho_new = (rh, r); beta
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_bcg_xr(DevGrid g, T* __restrict__ x, T* __restrict__ r,
+                                                const T* __restrict__ rh, const T* __restrict__ ph,
+                                                const T* __restrict__ sh, const T* __restrict__ sv,
+                                                const T* __restrict__ tv, uint16_t dmask, KState* ks,
+                                                double* partials, unsigned* counter) {
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = is_dof(m, dmask);
+  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
+  double w[2 * NC];
+  for (int c = 0; c < NC; ++c) {
+    w[2 * c] = w[2 * c + 1] = 0.0;
+    if (ks[c].done) continue;
+    const int64_t i = c * g.nslots + s;
+    const T al = T(ks[c].alpha), om = T(ks[c].omega);
+    if (m & D_VALID) x[i] += al * ph[i] + om * sh[i];
+    T rv = keep ? T(sv[i] - om * tv[i]) : T(0);
+    r[i] = rv;
+    if (dof) {
+      w[2 * c] = double(rv) * double(rv);
+      w[2 * c + 1] = double(rh[i]) * double(rv);
+    }
+  }
+  double tot[2 * NC];
+  if (grid_sum_last<2 * NC>(w, partials, counter, tot) && threadIdx.x == 0) {
+    for (int c = 0; c < NC; ++c) {
+      KState& k = ks[c];
+      if (k.done) continue;
+      k.iter++;
+      k.rr = tot[2 * c];
+      const double rhon = tot[2 * c + 1];
+      if (!isfinite(k.rr)) { k.done = 1; k.status = 5; continue; }
+      if (k.rr <= k.tol2 * k.bb) { k.done = 1; continue; }
+      if (k.iter >= k.max_iter) { k.done = 1; k.status = 4; continue; }
+      if (k.omega == 0.0 || rhon == 0.0 || !isfinite(rhon)) { k.done = 1; k.status = 5; continue; }
+      k.beta = (rhon / k.rho) * (k.alpha / k.omega);
+      k.rho = rhon;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- residual (FP64 outer loop)
+template <int NC>
+__global__ void __launch_bounds__(512) k_residual(DevGrid g, const double* __restrict__ b,
+                                                  const double* __restrict__ y, double* __restrict__ r,
+                                                  uint16_t dmask, double* partials, unsigned* counter,
+                                                  double* out) {
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = is_dof(m, dmask);
+  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
+  double w[2 * NC];
+  for (int c = 0; c < NC; ++c) {
+    const int64_t i = c * g.nslots + s;
+    double rv = keep ? b[i] - y[i] : 0.0;
+    r[i] = rv;
+    w[2 * c] = dof ? rv * rv : 0.0;
+    w[2 * c + 1] = dof ? b[i] * b[i] : 0.0;
+  }
+  double tot[2 * NC];
+  if (grid_sum_last<2 * NC>(w, partials, counter, tot) && threadIdx.x == 0)
+    for (int k = 0; k < 2 * NC; ++k) out[k] = tot[k];
+}
+
+// ---------------------------------------------------------------- Jacobi
+template <typename T, int OP>
+__global__ void __launch_bounds__(512) k_diag(DevGrid g, const T* __restrict__ coef, T* __restrict__ diag) {
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  T d = T(0);
+  if (m & D_VALID) {
+    const int lev = g.blev[blockIdx.x];
+    const double hx = g.h[lev][0], hy = g.h[lev][1], hz = g.h[lev][2], V = hx * hy * hz;
+    if (OP == OP_POISSON) {
+      const double f[3] = {V / (6.0 * hx * hx), V / (6.0 * hy * hy), V / (6.0 * hz * hz)};
+      d = table_coef<T, OP_POISSON>(m & 0xFF, 0, f, 0.0);
+    } else if (OP == OP_MASS) {
+      const double f[3] = {0, 0, 0};
+      d = table_coef<T, OP_MASS>(m & 0xFF, 0, f, V / 120.0);
+    } else {
+      d = coef[s];
+    }
+  }
+  diag[s] = d;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_dinv(DevGrid g, const T* __restrict__ diag, T* __restrict__ dinv,
+                                              uint16_t dmask) {
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
+  dinv[s] = (keep && diag[s] != T(0)) ? T(1) / diag[s] : T(0);
+}
+
+// ---------------------------------------------------------------- tet-loop kernels (FP64)
+// For every Kuhn tetrahedron T of an active incident leaf cell that contains
+// the node: f(T, kn, rel[4], grad[4][3], V) with kn the node's vertex index,
+// rel the tile offsets of the 4 vertices and grad the barycentric gradients.
+template <typename F>
+__device__ __forceinline__ void for_each_tet(int mask, const double h[3], F&& f) {
+  for (int c = 0; c < 8; ++c) {
+    if (!(mask >> c & 1)) continue;
+    const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+    const int qb = (1 - dx) | ((1 - dy) << 1) | ((1 - dz) << 2);
+    for (int p = 0; p < 6; ++p) {
+      const int a1 = c_kperm[p][0], a2 = c_kperm[p][1], a3 = c_kperm[p][2];
+      const int vb[4] = {0, 1 << a1, (1 << a1) | (1 << a2), 7};
+      int kn = -1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (vb[k] == qb) kn = k;
+      if (kn < 0) continue;
+      int rel[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int rx = dx - 1 + (vb[k] & 1), ry = dy - 1 + ((vb[k] >> 1) & 1), rz = dz - 1 + ((vb[k] >> 2) & 1);
+        rel[k] = (rz * TILE + ry) * TILE + rx;
+      }
+      double gr[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      gr[0][a1] = -1.0 / h[a1];
+      gr[1][a1] = 1.0 / h[a1];
+      gr[1][a2] = -1.0 / h[a2];
+      gr[2][a2] = 1.0 / h[a2];
+      gr[2][a3] = -1.0 / h[a3];
+      gr[3][a3] = 1.0 / h[a3];
+      f(kn, rel, gr, vb, dx, dy, dz);
+    }
+  }
+}
+
+// out_c = (M u_c) - dt (G_c p)
+__global__ void __launch_bounds__(512) k_rhs_mass_grad(DevGrid g, const double* __restrict__ u,
+                                                       const double* __restrict__ p, double dt,
+                                                       double* __restrict__ out) {
+  __shared__ double tile[4 * TILE3];
+  const int b = blockIdx.x;
+  load_tile<double>(tile, u, g.nslots, 3, g.bnbr + 27 * b);
+  load_tile<double>(tile + 3 * TILE3, p, g.nslots, 1, g.bnbr + 27 * b);
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int64_t s = (int64_t)b * DBV + t;
+  const uint16_t m = g.meta[s];
+  double o[3] = {0, 0, 0};
+  if (m & D_VALID) {
+    const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
+    const int lev = g.blev[b];
+    const double h[3] = {g.h[lev][0], g.h[lev][1], g.h[lev][2]};
+    const double V = h[0] * h[1] * h[2];
+    for_each_tet(m & 0xFF, h, [&](int kn, const int (&rel)[4], const double (&gr)[4][3], const int*, int, int, int) {
+      double gp[3] = {0, 0, 0};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double pk = tile[3 * TILE3 + ti + rel[k]];
+        const double w = (k == kn ? 2.0 : 1.0) * (V / 120.0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          o[a] += w * tile[a * TILE3 + ti + rel[k]];
+          gp[a] += pk * gr[k][a];
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) o[a] -= dt * (V / 24.0) * gp[a];
+    });
+  }
+  for (int a = 0; a < 3; ++a) out[a * g.nslots + s] = o[a];
+}
+
+// out = scale * (div u, q)
+__global__ void __launch_bounds__(512) k_rhs_div(DevGrid g, const double* __restrict__ u, double scale,
+                                                 double* __restrict__ out) {
+  __shared__ double tile[3 * TILE3];
+  const int b = blockIdx.x;
+  load_tile<double>(tile, u, g.nslots, 3, g.bnbr + 27 * b);
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int64_t s = (int64_t)b * DBV + t;
+  const uint16_t m = g.meta[s];
+  double o = 0.0;
+  if (m & D_VALID) {
+    const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
+    const int lev = g.blev[b];
+    const double h[3] = {g.h[lev][0], g.h[lev][1], g.h[lev][2]};
+    const double V = h[0] * h[1] * h[2];
+    for_each_tet(m & 0xFF, h, [&](int, const int (&rel)[4], const double (&gr)[4][3], const int*, int, int, int) {
+      double dv = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dv += tile[a * TILE3 + ti + rel[k]] * gr[k][a];
+      o += (V / 24.0) * dv;
+    });
+  }
+  out[s] = scale * o;
+}
+
+// coef[k] = M + dt C(u) + dt nu K row entries (Eq. 9 operator), k over the 15 slots
+__global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __restrict__ u, double dt, double nu,
+                                                  double* __restrict__ coef, float* __restrict__ coef32) {
+  __shared__ double tile[3 * TILE3];
+  const int b = blockIdx.x;
+  load_tile<double>(tile, u, g.nslots, 3, g.bnbr + 27 * b);
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int64_t s = (int64_t)b * DBV + t;
+  const uint16_t m = g.meta[s];
+  double cf[15];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) cf[k] = 0.0;
+  if (m & D_VALID) {
+    const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
+    const int lev = g.blev[b];
+    const double h[3] = {g.h[lev][0], g.h[lev][1], g.h[lev][2]};
+    const double V = h[0] * h[1] * h[2];
+    for_each_tet(m & 0xFF, h, [&](int kn, const int (&rel)[4], const double (&gr)[4][3], const int* vb, int dx, int dy,
+                                  int dz) {
+      double S[3] = {0, 0, 0};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) S[a] += tile[a * TILE3 + ti + rel[k]];
+      double w[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) w[a] = (V / 120.0) * (S[a] + tile[a * TILE3 + ti]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int rx = dx - 1 + (vb[k] & 1), ry = dy - 1 + ((vb[k] >> 1) & 1), rz = dz - 1 + ((vb[k] >> 2) & 1);
+        const int sl = c_slot_of_rel[(rz + 1) * 9 + (ry + 1) * 3 + (rx + 1)];
+        const double mass = (k == kn ? 2.0 : 1.0) * (V / 120.0);
+        const double conv = w[0] * gr[k][0] + w[1] * gr[k][1] + w[2] * gr[k][2];
+        const double visc = (V / 6.0) * (gr[kn][0] * gr[k][0] + gr[kn][1] * gr[k][1] + gr[kn][2] * gr[k][2]);
+        cf[sl] += mass + dt * conv + dt * nu * visc;
+      }
+    });
+  }
+#pragma unroll
+  for (int k = 0; k < 15; ++k) {
+    coef[(int64_t)k * g.nslots + s] = cf[k];
+    if (coef32) coef32[(int64_t)k * g.nslots + s] = float(cf[k]);
+  }
+}
+
+// ---------------------------------------------------------------- elementwise
+__global__ void k_cast_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = float(a[i]);
+}
+__global__ void k_add_f2d(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] += double(a[i]);
+}
+__global__ void k_add_d(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] += a[i];
+}
+__global__ void k_copy_d(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+template <typename T>
+__global__ void k_zero(int64_t n, T* __restrict__ a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = T(0);
+}
+
+template <typename T>
+__global__ void k_gather_canon(int64_t N, const int32_t* __restrict__ cs, int nc, int64_t nslots,
+                               const T* __restrict__ x, T* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < nc; ++c) out[i * nc + c] = x[c * nslots + cs[i]];
+}
+__global__ void k_scatter_canon(int64_t N, const int32_t* __restrict__ cs, int nc, int64_t nslots,
+                                const double* __restrict__ in, double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < nc; ++c) x[c * nslots + cs[i]] = in[i * nc + c];
+}
+__global__ void k_copy_to_fine(DevGrid g, int nc, double* __restrict__ x) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.n_if) return;
+  for (int c = 0; c < nc; ++c) x[c * g.nslots + g.if_f[e]] = x[c * g.nslots + g.if_c[e]];
+}
+
+__global__ void k_set_inlet(int64_t n, const int32_t* __restrict__ slot, const int32_t* __restrict__ port,
+                            const double* __restrict__ shape, const PortDev* __restrict__ ports,
+                            const double* __restrict__ tp, int64_t nslots, double* __restrict__ u) {
+  const double t = *tp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const PortDev& P = ports[port[i]];
+    const double w = 2.0 * 3.14159265358979323846 / P.period;
+    double um = P.a0;
+    for (int k = 0; k < P.nh; ++k) um += P.a[k] * cos((k + 1) * w * t) + P.b[k] * sin((k + 1) * w * t);
+    u[P.axis * nslots + slot[i]] = um * shape[i];
+  }
+}
+__global__ void k_time(double* tc, double* tn, double dt, int commit) {
+  if (commit) *tc = *tn;
+  else *tn = *tc + dt;
+}
+
+// ---------------------------------------------------------------- profiling
+void Prof::begin(int c, cudaStream_t st) {
+  if (!on) return;
+  if (2 * (used + 1) > int(ev.size())) {
+    for (int k = 0; k < 64; ++k) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev.push_back(e);
+    }
+  }
+  cls.push_back(c);
+  cudaEventRecord(ev[2 * used], st);
+}
+void Prof::end(cudaStream_t st) {
+  if (!on) return;
+  cudaEventRecord(ev[2 * used + 1], st);
+  used++;
+}
+void Prof::collect() {
+  for (int i = 0; i < used; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) {
+      ms[cls[i]] += t;
+      n[cls[i]] += 1;
+    }
+  }
+  used = 0;
+  cls.clear();
+}
+void Prof::release() {
+  for (auto e : ev) cudaEventDestroy(e);
+  ev.clear();
+  cls.clear();
+  used = 0;
+}
+
+// ---------------------------------------------------------------- host wrappers
+static inline int nblk(int64_t n, int bs = 256) {
+  int64_t b = (n + bs - 1) / bs;
+  return int(std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 16));
+}
+
+template <typename T, int NC>
+static void launch_apply(const DevGrid& g, int op, const T* x, T* y, const T* coef, uint16_t dmask, int post,
+                         KState* ks, RedBuf rb, cudaStream_t st) {
+  if (op == OP_POISSON)
+    IBG_LAUNCH((k_apply<T, OP_POISSON, NC>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks, rb.partials, rb.counter);
+  else if (op == OP_MASS)
+    IBG_LAUNCH((k_apply<T, OP_MASS, NC>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks, rb.partials, rb.counter);
+  else
+    IBG_LAUNCH((k_apply<T, OP_COEF, NC>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks, rb.partials, rb.counter);
+}
+
+template <typename T>
+void fe_sync(const DevGrid& g, int nc, T* y, uint16_t dmask, cudaStream_t st) {
+  if (g.n_if == 0) return;
+  int bl = (g.n_if + 255) / 256;
+  if (nc == 1) IBG_LAUNCH((k_sync<T, 1>), bl, 256, 0, st, g, y, dmask);
+  else IBG_LAUNCH((k_sync<T, 3>), bl, 256, 0, st, g, y, dmask);
+}
+
+template <typename T>
+static void expand2(const DevGrid& g, int nc, T* x, T* x2, cudaStream_t st) {
+  if (g.n_hang == 0) return;
+  int bl = (g.n_hang + 255) / 256;
+  if (nc == 1) IBG_LAUNCH((k_expand<T, 1>), bl, 256, 0, st, g, x, x2);
+  else IBG_LAUNCH((k_expand<T, 3>), bl, 256, 0, st, g, x, x2);
+}
+
+template <typename T>
+void fe_expand(const DevGrid& g, int nc, T* x, cudaStream_t st) {
+  expand2<T>(g, nc, x, (T*)nullptr, st);
+}
+
+template <typename T>
+void fe_apply(const DevGrid& g, const OpDesc<T>& A, int nc, const T* x, T* y, cudaStream_t st) {
+  RedBuf none;
+  if (nc == 1) launch_apply<T, 1>(g, A.op, x, y, A.coef, A.dmask, POST_NONE, nullptr, none, st);
+  else launch_apply<T, 3>(g, A.op, x, y, A.coef, A.dmask, POST_NONE, nullptr, none, st);
+  fe_sync<T>(g, nc, y, A.dmask, st);
+}
+
+template <typename T>
+void fe_jacobi(const DevGrid& g, int op, const T* coef, uint16_t dmask, T* diag, T* dinv, cudaStream_t st) {
+  if (op == OP_POISSON) IBG_LAUNCH((k_diag<T, OP_POISSON>), g.nbricks, DBV, 0, st, g, coef, diag);
+  else if (op == OP_MASS) IBG_LAUNCH((k_diag<T, OP_MASS>), g.nbricks, DBV, 0, st, g, coef, diag);
+  else IBG_LAUNCH((k_diag<T, OP_COEF>), g.nbricks, DBV, 0, st, g, coef, diag);
+  fe_sync<T>(g, 1, diag, 0, st);
+  IBG_LAUNCH((k_dinv<T>), g.nbricks, DBV, 0, st, g, diag, dinv, dmask);
+}
+
+static SolveStats read_stats(const KState* ks, KState* ks_host, int nc, cudaStream_t st, bool* all_done) {
+  cudaMemcpyAsync(ks_host, ks, nc * sizeof(KState), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  SolveStats S;
+  *all_done = true;
+  for (int c = 0; c < nc; ++c) {
+    S.iters[c] = ks_host[c].iter;
+    if (!ks_host[c].done) *all_done = false;
+    if (ks_host[c].status) S.status = ks_host[c].status;
+    double rel = ks_host[c].bb > 0 ? std::sqrt(std::max(ks_host[c].rr, 0.0) / ks_host[c].bb) : 0.0;
+    S.relres = std::max(S.relres, rel);
+  }
+  return S;
+}
+
+static void init_states(KState* ks, KState* ks_host, int nc, double rtol, int max_iter, cudaStream_t st) {
+  for (int c = 0; c < nc; ++c) {
+    std::memset(&ks_host[c], 0, sizeof(KState));
+    ks_host[c].tol2 = rtol * rtol;
+    ks_host[c].max_iter = max_iter;
+  }
+  cudaMemcpyAsync(ks, ks_host, nc * sizeof(KState), cudaMemcpyHostToDevice, st);
+}
+
+template <typename T, int NC>
+static SolveStats cg_impl(const DevGrid& g, const OpDesc<T>& A, const T* b, T* x, T* work, KState* ks,
+                          KState* ks_host, RedBuf rb, double rtol, int max_iter, cudaStream_t st) {
+  const int64_t L = NC * g.nslots;
+  T *r = work, *z = work + L, *p = work + 2 * L, *q = work + 3 * L;
+  init_states(ks, ks_host, NC, rtol, max_iter, st);
+  launch_apply<T, NC>(g, A.op, x, q, A.coef, A.dmask, POST_NONE, nullptr, rb, st);
+  fe_sync<T>(g, NC, q, A.dmask, st);
+  IBG_LAUNCH((k_cg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, q, r, z, p, A.dinv, A.dmask, ks, rb.partials, rb.counter);
+  expand2<T>(g, NC, z, p, st);
+  int it = 0, chunk = 4;
+  bool done = false;
+  SolveStats S = read_stats(ks, ks_host, NC, st, &done);
+  while (!done) {
+    Prof* pf = A.prof;
+    for (int k = 0; k < chunk; ++k) {
+      if (pf) pf->begin(A.pbase + 0, st);
+      launch_apply<T, NC>(g, A.op, p, q, A.coef, A.dmask, POST_CG_ALPHA, ks, rb, st);
+      if (pf) pf->end(st);
+      fe_sync<T>(g, NC, q, A.dmask, st);
+      if (pf) pf->begin(A.pbase + 1, st);
+      IBG_LAUNCH((k_cg_update<T, NC>), g.nbricks, DBV, 0, st, g, x, r, z, p, q, A.dinv, A.dmask, ks, rb.partials, rb.counter);
+      if (pf) pf->end(st);
+      expand2<T>(g, NC, z, (T*)nullptr, st);
+      if (pf) pf->begin(A.pbase + 2, st);
+      IBG_LAUNCH((k_cg_p<T, NC>), g.nbricks, DBV, 0, st, g, z, p, ks);
+      if (pf) pf->end(st);
+    }
+    it += chunk;
+    chunk = std::min(chunk * 2, 32);
+    S = read_stats(ks, ks_host, NC, st, &done);
+    if (it > max_iter + 64) break;
+  }
+  return S;
+}
+
+template <typename T>
+SolveStats fe_cg(const DevGrid& g, const OpDesc<T>& A, int nc, const T* b, T* x, T* work, KState* ks,
+                 KState* ks_host, RedBuf rb, double rtol, int max_iter, cudaStream_t st) {
+  if (nc == 1) return cg_impl<T, 1>(g, A, b, x, work, ks, ks_host, rb, rtol, max_iter, st);
+  return cg_impl<T, 3>(g, A, b, x, work, ks, ks_host, rb, rtol, max_iter, st);
+}
+
+template <typename T, int NC>
+static SolveStats bcg_impl(const DevGrid& g, const OpDesc<T>& A, const T* b, T* x, T* work, KState* ks,
+                           KState* ks_host, RedBuf rb, double rtol, int max_iter, cudaStream_t st) {
+  const int64_t L = NC * g.nslots;
+  T *r = work, *rh = work + L, *p = work + 2 * L, *v = work + 3 * L, *sv = work + 4 * L, *tv = work + 5 * L,
+    *ph = work + 6 * L, *sh = work + 7 * L;
+  init_states(ks, ks_host, NC, rtol, max_iter, st);
+  launch_apply<T, NC>(g, A.op, x, tv, A.coef, A.dmask, POST_NONE, nullptr, rb, st);
+  fe_sync<T>(g, NC, tv, A.dmask, st);
+  IBG_LAUNCH((k_bcg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, tv, r, rh, p, v, A.dmask, ks, rb.partials, rb.counter);
+  int it = 0, chunk = 2;
+  bool done = false;
+  SolveStats S = read_stats(ks, ks_host, NC, st, &done);
+  while (!done) {
+    for (int k = 0; k < chunk; ++k) {
+      IBG_LAUNCH((k_bcg_p<T, NC>), g.nbricks, DBV, 0, st, g, r, p, v, ph, A.dinv, A.dmask, ks);
+      expand2<T>(g, NC, ph, (T*)nullptr, st);
+      if (A.prof) A.prof->begin(A.pbase + 0, st);
+      launch_apply<T, NC>(g, A.op, ph, v, A.coef, A.dmask, POST_NONE, nullptr, rb, st);
+      if (A.prof) A.prof->end(st);
+      fe_sync<T>(g, NC, v, A.dmask, st);
+      IBG_LAUNCH((k_bcg_dot<T, NC>), g.nbricks, DBV, 0, st, g, rh, v, v, A.dmask, 0, ks, rb.partials, rb.counter);
+      IBG_LAUNCH((k_bcg_s<T, NC>), g.nbricks, DBV, 0, st, g, r, v, sv, sh, A.dinv, A.dmask, ks);
+      expand2<T>(g, NC, sh, (T*)nullptr, st);
+      launch_apply<T, NC>(g, A.op, sh, tv, A.coef, A.dmask, POST_NONE, nullptr, rb, st);
+      fe_sync<T>(g, NC, tv, A.dmask, st);
+      IBG_LAUNCH((k_bcg_dot<T, NC>), g.nbricks, DBV, 0, st, g, tv, sv, tv, A.dmask, 1, ks, rb.partials, rb.counter);
+      IBG_LAUNCH((k_bcg_xr<T, NC>), g.nbricks, DBV, 0, st, g, x, r, rh, ph, sh, sv, tv, A.dmask, ks, rb.partials, rb.counter);
+    }
+    it += chunk;
+    chunk = std::min(chunk * 2, 16);
+    S = read_stats(ks, ks_host, NC, st, &done);
+    if (it > max_iter + 32) break;
+  }
+  return S;
+}
+
+template <typename T>
+SolveStats fe_bicgstab(const DevGrid& g, const OpDesc<T>& A, int nc, const T* b, T* x, T* work, KState* ks,
+                       KState* ks_host, RedBuf rb, double rtol, int max_iter, cudaStream_t st) {
+  if (nc == 1) return bcg_impl<T, 1>(g, A, b, x, work, ks, ks_host, rb, rtol, max_iter, st);
+  return bcg_impl<T, 3>(g, A, b, x, work, ks, ks_host, rb, rtol, max_iter, st);
+}
+
+void fe_residual64(const DevGrid& g, const OpDesc<double>& A, int nc, const double* b, const double* x, double* y,
+                   double* r, RedBuf rb, double* host_rr_bb, cudaStream_t st) {
+  fe_apply<double>(g, A, nc, x, y, st);
+  double* out = rb.partials + int64_t(g.nbricks) * 16;   // after the block partials
+  if (nc == 1) IBG_LAUNCH((k_residual<1>), g.nbricks, DBV, 0, st, g, b, y, r, A.dmask, rb.partials, rb.counter, out);
+  else IBG_LAUNCH((k_residual<3>), g.nbricks, DBV, 0, st, g, b, y, r, A.dmask, rb.partials, rb.counter, out);
+  cudaMemcpyAsync(host_rr_bb, out, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+}
+
+void fe_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t st) { IBG_LAUNCH(k_cast_d2f, nblk(n), 256, 0, st, n, a, b); }
+void fe_add_f2d(int64_t n, const float* a, double* b, cudaStream_t st) { IBG_LAUNCH(k_add_f2d, nblk(n), 256, 0, st, n, a, b); }
+void fe_copy_d(int64_t n, const double* a, double* b, cudaStream_t st) { IBG_LAUNCH(k_copy_d, nblk(n), 256, 0, st, n, a, b); }
+void fe_add_d(int64_t n, const double* a, double* b, cudaStream_t st) { IBG_LAUNCH(k_add_d, nblk(n), 256, 0, st, n, a, b); }
+template <typename T>
+void fe_zero(int64_t n, T* a, cudaStream_t st) { IBG_LAUNCH((k_zero<T>), nblk(n), 256, 0, st, n, a); }
+
+void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double dt, double* out, cudaStream_t st) {
+  IBG_LAUNCH(k_rhs_mass_grad, g.nbricks, DBV, 0, st, g, u, p, dt, out);
+}
+void fe_rhs_div(const DevGrid& g, const double* u, double scale, double* out, cudaStream_t st) {
+  IBG_LAUNCH(k_rhs_div, g.nbricks, DBV, 0, st, g, u, scale, out);
+}
+void fe_momentum_coef(const DevGrid& g, const double* u, double dt, double nu, double* coef64, float* coef32,
+                      cudaStream_t st) {
+  IBG_LAUNCH(k_mom_coef, g.nbricks, DBV, 0, st, g, u, dt, nu, coef64, coef32);
+}
+
+template <typename T>
+void fe_gather_canon(int64_t N, const int32_t* cs, int nc, int64_t nslots, const T* x, T* out, cudaStream_t st) {
+  IBG_LAUNCH((k_gather_canon<T>), nblk(N), 256, 0, st, N, cs, nc, nslots, x, out);
+}
+void fe_scatter_canon(const DevGrid& g, int64_t N, const int32_t* cs, int nc, const double* in, double* x,
+                      cudaStream_t st) {
+  IBG_LAUNCH(k_scatter_canon, nblk(N), 256, 0, st, N, cs, nc, g.nslots, in, x);
+  if (g.n_if) IBG_LAUNCH(k_copy_to_fine, (g.n_if + 255) / 256, 256, 0, st, g, nc, x);
+  fe_expand<double>(g, nc, x, st);
+}
+
+void fe_set_inlet(int64_t n, const int32_t* slot, const int32_t* port, const double* shape, const PortDev* ports,
+                  const double* t, int64_t nslots, double* u, cudaStream_t st) {
+  if (n == 0) return;
+  IBG_LAUNCH(k_set_inlet, nblk(n), 256, 0, st, n, slot, port, shape, ports, t, nslots, u);
+}
+void fe_time_advance(double* tc, double* tn, double dt, int commit, cudaStream_t st) {
+  IBG_LAUNCH(k_time, 1, 1, 0, st, tc, tn, dt, commit);
+}
+
+// explicit instantiations
+template void fe_apply<double>(const DevGrid&, const OpDesc<double>&, int, const double*, double*, cudaStream_t);
+template void fe_apply<float>(const DevGrid&, const OpDesc<float>&, int, const float*, float*, cudaStream_t);
+template void fe_jacobi<double>(const DevGrid&, int, const double*, uint16_t, double*, double*, cudaStream_t);
+template void fe_jacobi<float>(const DevGrid&, int, const float*, uint16_t, float*, float*, cudaStream_t);
+template SolveStats fe_cg<double>(const DevGrid&, const OpDesc<double>&, int, const double*, double*, double*,
+                                  KState*, KState*, RedBuf, double, int, cudaStream_t);
+template SolveStats fe_cg<float>(const DevGrid&, const OpDesc<float>&, int, const float*, float*, float*, KState*,
+                                 KState*, RedBuf, double, int, cudaStream_t);
+template SolveStats fe_bicgstab<double>(const DevGrid&, const OpDesc<double>&, int, const double*, double*, double*,
+                                        KState*, KState*, RedBuf, double, int, cudaStream_t);
+template SolveStats fe_bicgstab<float>(const DevGrid&, const OpDesc<float>&, int, const float*, float*, float*,
+                                       KState*, KState*, RedBuf, double, int, cudaStream_t);
+template void fe_zero<double>(int64_t, double*, cudaStream_t);
+template void fe_zero<float>(int64_t, float*, cudaStream_t);
+template void fe_expand<double>(const DevGrid&, int, double*, cudaStream_t);
+template void fe_expand<float>(const DevGrid&, int, float*, cudaStream_t);
+template void fe_sync<double>(const DevGrid&, int, double*, uint16_t, cudaStream_t);
+template void fe_sync<float>(const DevGrid&, int, float*, uint16_t, cudaStream_t);
+template void fe_gather_canon<double>(int64_t, const int32_t*, int, int64_t, const double*, double*, cudaStream_t);
+
+}  // namespace ibg

@@ -1,0 +1,288 @@
+// BCE-IB kernels (Sec. 2.3): the 4-point delta kernel of Eq. 18, interpolation
+// B_F = U_B - h^3 D^T u~ (Eq. 23), the force matrix of Eq. 22 and its PCG solve,
+// and spreading f = sum_i F_i D_ij dS_i (Eq. 19) fused with u = u~ + dt f/rho
+// (Eq. 14).  With area elements on the columns (dS_k in A_F[i,k]) A_F = S diag(dS)
+// with S symmetric; the solver works with G = dS * F, so F = G / dS.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ib.hpp"
+
+namespace ibg {
+
+// Eq. 18
+__device__ __forceinline__ double delta4(double r) {
+  r = fabs(r);
+  if (r <= 1.0) return (3.0 - 2.0 * r + sqrt(1.0 + 4.0 * r - 4.0 * r * r)) * 0.125;
+  if (r <= 2.0) return (5.0 - 2.0 * r - sqrt(-7.0 + 12.0 * r - 4.0 * r * r)) * 0.125;
+  return 0.0;
+}
+
+__global__ void k_ib_weights(int64_t M, const double* __restrict__ X, const int32_t* __restrict__ org,
+                             const int32_t* __restrict__ slot, double o0, double o1, double o2, double h0,
+                             double h1, double h2, double* __restrict__ W) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= M * 64) return;
+  const int64_t i = e >> 6;
+  const int a = int(e & 63);
+  if (slot[e] < 0) { W[e] = 0.0; return; }
+  const double x = o0 + double(org[3 * i] + (a & 3)) * h0;
+  const double y = o1 + double(org[3 * i + 1] + ((a >> 2) & 3)) * h1;
+  const double z = o2 + double(org[3 * i + 2] + (a >> 4)) * h2;
+  W[e] = delta4((x - X[3 * i]) / h0) * delta4((y - X[3 * i + 1]) / h1) * delta4((z - X[3 * i + 2]) / h2);
+}
+
+// one warp per row: S[i,k] = scale * sum over free common support nodes of w_ia w_kb
+__global__ void k_af_values(int64_t M, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const int32_t* __restrict__ org, const uint64_t* __restrict__ fb,
+                            const double* __restrict__ W, double scale, double* __restrict__ val,
+                            double* __restrict__ dinv) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= M) return;
+  for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+    const int k = col[e];
+    const int dx = org[3 * k] - org[3 * i], dy = org[3 * k + 1] - org[3 * i + 1], dz = org[3 * k + 2] - org[3 * i + 2];
+    double acc = 0.0;
+    for (int a = 0; a < 64; ++a) {
+      if (!(fb[i] >> a & 1)) continue;
+      const int bx = (a & 3) - dx, by = ((a >> 2) & 3) - dy, bz = (a >> 4) - dz;
+      if (bx < 0 || by < 0 || bz < 0 || bx > 3 || by > 3 || bz > 3) continue;
+      const int bb = (bz * 4 + by) * 4 + bx;
+      acc += W[i * 64 + a] * W[(int64_t)k * 64 + bb];
+    }
+    val[e] = scale * acc;
+    if (k == i) dinv[i] = acc > 0.0 ? 1.0 / (scale * acc) : 0.0;
+  }
+}
+
+// one warp per point: B_F = U_B - sum_a w_ia u(slot_ia), fixed lane order
+__global__ void k_ib_gather(int64_t M, const int32_t* __restrict__ slot, const double* __restrict__ W,
+                            const double* __restrict__ u, int64_t nslots, const double* __restrict__ UB,
+                            double* __restrict__ BF) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= M) return;
+  double acc[3] = {0, 0, 0};
+  for (int a = lane; a < 64; a += 32) {
+    const int32_t s = slot[i * 64 + a];
+    if (s < 0) continue;
+    const double w = W[i * 64 + a];
+    for (int c = 0; c < 3; ++c) acc[c] += w * u[c * nslots + s];
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+  if (lane == 0)
+    for (int c = 0; c < 3; ++c) BF[3 * i + c] = UB[3 * i + c] - acc[c];
+}
+
+// ---------------------------------------------------------------- PCG on S (3 rhs, [M][3])
+constexpr int IBB = 256;   // threads per block; 8 rows per block in the SpMV
+
+__device__ __forceinline__ void spmv_row(int64_t i, int lane, const int32_t* __restrict__ rowptr,
+                                         const int32_t* __restrict__ col, const double* __restrict__ val,
+                                         const double* __restrict__ x, double (&acc)[3]) {
+  acc[0] = acc[1] = acc[2] = 0.0;
+  for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+    const double v = val[e];
+    const int k = col[e];
+    for (int c = 0; c < 3; ++c) acc[c] += v * x[3 * k + c];
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+}
+
+// q = S p; p.q -> alpha (mode 1) | y = S x (mode 0)
+__global__ void __launch_bounds__(IBB) k_af_apply(int64_t M, const int32_t* __restrict__ rowptr,
+                                                  const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                  const double* __restrict__ p, double* __restrict__ q, int mode,
+                                                  KState* ks, double* partials, unsigned* counter) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  double acc[3] = {0, 0, 0};
+  if (i < M) spmv_row(i, lane, rowptr, col, val, p, acc);
+  double v[3] = {0, 0, 0};
+  if (i < M && lane == 0)
+    for (int c = 0; c < 3; ++c) {
+      q[3 * i + c] = acc[c];
+      v[c] = p[3 * i + c] * acc[c];
+    }
+  if (mode == 0) return;
+  double tot[3];
+  if (grid_sum_last<3>(v, partials, counter, tot) && threadIdx.x == 0) {
+    for (int c = 0; c < 3; ++c) {
+      KState& k = ks[c];
+      if (k.done) continue;
+      k.pq = tot[c];
+      if (!(tot[c] > 0.0) || !isfinite(tot[c])) { k.done = 1; k.status = 5; k.alpha = 0.0; continue; }
+      k.alpha = k.rz / tot[c];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(IBB) k_af_start(int64_t M, const double* __restrict__ b, const double* __restrict__ y,
+                                                  double* __restrict__ r, double* __restrict__ z,
+                                                  double* __restrict__ p, const double* __restrict__ dinv, KState* ks,
+                                                  double* partials, unsigned* counter) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (i < M)
+    for (int c = 0; c < 3; ++c) {
+      const double rv = b[3 * i + c] - y[3 * i + c];
+      const double zv = rv * dinv[i];
+      r[3 * i + c] = rv;
+      z[3 * i + c] = zv;
+      p[3 * i + c] = zv;
+      v[3 * c] = rv * zv;
+      v[3 * c + 1] = rv * rv;
+      v[3 * c + 2] = b[3 * i + c] * b[3 * i + c];
+    }
+  double tot[9];
+  if (grid_sum_last<9>(v, partials, counter, tot) && threadIdx.x == 0) {
+    for (int c = 0; c < 3; ++c) {
+      KState& k = ks[c];
+      k.rz = tot[3 * c];
+      k.rr = tot[3 * c + 1];
+      k.bb = tot[3 * c + 2];
+      k.iter = 0;
+      k.status = 0;
+      k.done = (k.rr <= k.tol2 * k.bb) ? 1 : 0;
+      if (!isfinite(k.rr)) { k.done = 1; k.status = 5; }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(IBB) k_af_update(int64_t M, double* __restrict__ x, double* __restrict__ r,
+                                                   double* __restrict__ z, const double* __restrict__ p,
+                                                   const double* __restrict__ q, const double* __restrict__ dinv,
+                                                   KState* ks, double* partials, unsigned* counter) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  if (i < M)
+    for (int c = 0; c < 3; ++c) {
+      if (ks[c].done) continue;
+      const double a = ks[c].alpha;
+      x[3 * i + c] += a * p[3 * i + c];
+      const double rv = r[3 * i + c] - a * q[3 * i + c];
+      const double zv = rv * dinv[i];
+      r[3 * i + c] = rv;
+      z[3 * i + c] = zv;
+      v[2 * c] = rv * zv;
+      v[2 * c + 1] = rv * rv;
+    }
+  double tot[6];
+  if (grid_sum_last<6>(v, partials, counter, tot) && threadIdx.x == 0) {
+    for (int c = 0; c < 3; ++c) {
+      KState& k = ks[c];
+      if (k.done) continue;
+      k.iter++;
+      k.rr = tot[2 * c + 1];
+      const double rzn = tot[2 * c];
+      if (!isfinite(k.rr)) { k.done = 1; k.status = 5; continue; }
+      if (k.rr <= k.tol2 * k.bb) { k.done = 1; continue; }
+      if (k.iter >= k.max_iter) { k.done = 1; k.status = 4; continue; }
+      k.beta = rzn / k.rz;
+      k.rz = rzn;
+    }
+  }
+}
+
+__global__ void k_af_p(int64_t M, const double* __restrict__ z, double* __restrict__ p, const KState* ks) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  for (int c = 0; c < 3; ++c)
+    if (!ks[c].done) p[3 * i + c] = z[3 * i + c] + ks[c].beta * p[3 * i + c];
+}
+
+// one thread per free support node: u += coef * sum_e W[ent] G[point(ent)]
+__global__ void k_ib_spread(int64_t n, const int32_t* __restrict__ sp_slot, const int32_t* __restrict__ sp_off,
+                            const int32_t* __restrict__ sp_ent, const double* __restrict__ W,
+                            const double* __restrict__ G, double coef, double* __restrict__ u, int64_t nslots) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double acc[3] = {0, 0, 0};
+  for (int e = sp_off[j]; e < sp_off[j + 1]; ++e) {
+    const int32_t ent = sp_ent[e];
+    const double w = W[ent];
+    const int64_t i = ent >> 6;
+    for (int c = 0; c < 3; ++c) acc[c] += w * G[3 * i + c];
+  }
+  const int32_t s = sp_slot[j];
+  for (int c = 0; c < 3; ++c) u[c * nslots + s] += coef * acc[c];
+}
+
+// ---------------------------------------------------------------- host wrappers
+void ib_weights(const IBDev& ib, const double origin[3], const double hf[3], cudaStream_t st) {
+  if (ib.M == 0) return;
+  const int64_t n = ib.M * 64;
+  IBG_LAUNCH(k_ib_weights, int((n + 255) / 256), 256, 0, st, ib.M, ib.X, ib.org, ib.slot, origin[0], origin[1], origin[2],
+                                                     hf[0], hf[1], hf[2], ib.W);
+}
+
+void ib_assemble(const IBDev& ib, double scale, cudaStream_t st) {
+  if (ib.M == 0) return;
+  const int64_t th = ib.M * 32;
+  IBG_LAUNCH(k_af_values, int((th + 255) / 256), 256, 0, st, ib.M, ib.rowptr, ib.col, ib.org, ib.freeb, ib.W, scale, ib.val,
+                                                     ib.dinv);
+}
+
+void ib_gather(const IBDev& ib, const double* u, int64_t nslots, const double* UB, double* BF, cudaStream_t st) {
+  if (ib.M == 0) return;
+  const int64_t th = ib.M * 32;
+  IBG_LAUNCH(k_ib_gather, int((th + 255) / 256), 256, 0, st, ib.M, ib.slot, ib.W, u, nslots, UB, BF);
+}
+
+SolveStats ib_solve(const IBDev& ib, const double* BF, double* G, double* work, KState* ks, KState* ks_host,
+                    RedBuf rb, double rtol, int max_iter, cudaStream_t st) {
+  SolveStats S;
+  if (ib.M == 0) return S;
+  const int64_t L = 3 * ib.M;
+  double *r = work, *z = work + L, *p = work + 2 * L, *q = work + 3 * L;
+  for (int c = 0; c < 3; ++c) {
+    std::memset(&ks_host[c], 0, sizeof(KState));
+    ks_host[c].tol2 = rtol * rtol;
+    ks_host[c].max_iter = max_iter;
+  }
+  cudaMemcpyAsync(ks, ks_host, 3 * sizeof(KState), cudaMemcpyHostToDevice, st);
+  const int gw = int((ib.M * 32 + IBB - 1) / IBB);   // warp-per-row grids
+  const int gt = int((ib.M + IBB - 1) / IBB);        // thread-per-row grids
+  IBG_LAUNCH(k_af_apply, gw, IBB, 0, st, ib.M, ib.rowptr, ib.col, ib.val, G, q, 0, ks, rb.partials, rb.counter);
+  IBG_LAUNCH(k_af_start, gt, IBB, 0, st, ib.M, BF, q, r, z, p, ib.dinv, ks, rb.partials, rb.counter);
+  int it = 0, chunk = 8;
+  bool done = false;
+  auto poll = [&]() {
+    cudaMemcpyAsync(ks_host, ks, 3 * sizeof(KState), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    done = true;
+    S = SolveStats();
+    for (int c = 0; c < 3; ++c) {
+      S.iters[c] = ks_host[c].iter;
+      if (!ks_host[c].done) done = false;
+      if (ks_host[c].status) S.status = ks_host[c].status;
+      double rel = ks_host[c].bb > 0 ? std::sqrt(std::max(ks_host[c].rr, 0.0) / ks_host[c].bb) : 0.0;
+      S.relres = std::max(S.relres, rel);
+    }
+  };
+  poll();
+  while (!done) {
+    for (int k = 0; k < chunk; ++k) {
+      IBG_LAUNCH(k_af_apply, gw, IBB, 0, st, ib.M, ib.rowptr, ib.col, ib.val, p, q, 1, ks, rb.partials, rb.counter);
+      IBG_LAUNCH(k_af_update, gt, IBB, 0, st, ib.M, G, r, z, p, q, ib.dinv, ks, rb.partials, rb.counter);
+      IBG_LAUNCH(k_af_p, gt, IBB, 0, st, ib.M, z, p, ks);
+    }
+    it += chunk;
+    chunk = std::min(chunk * 2, 64);
+    poll();
+    if (it > max_iter + 128) break;
+  }
+  return S;
+}
+
+void ib_spread(const IBDev& ib, const double* G, double coef, double* u, int64_t nslots, cudaStream_t st) {
+  if (ib.n_sp == 0) return;
+  IBG_LAUNCH(k_ib_spread, int((ib.n_sp + 255) / 256), 256, 0, st, ib.n_sp, ib.sp_slot, ib.sp_off, ib.sp_ent, ib.W, G, coef,
+                                                          u, nslots);
+}
+
+}  // namespace ibg

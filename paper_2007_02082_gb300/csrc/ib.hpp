@@ -1,0 +1,41 @@
+// Host-side interface of the BCE-IB kernels (ib.cu), Sec. 2.3.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "fe.hpp"
+
+namespace ibg {
+
+struct IBDev {
+  int64_t M;
+  const double* X;         // [M][3]
+  const int32_t* org;      // [M][3] support origin, finest grid
+  const int32_t* slot;     // [M][64] slot of support node a (-1 missing)
+  const uint64_t* freeb;   // [M] bit a: support node a free
+  double* W;               // [M][64] delta weights (0 where missing)
+  const int32_t* rowptr;   // A_F pattern
+  const int32_t* col;
+  double* val;             // S = (dt / (rho h^3)) W_f W_f^T values
+  double* dinv;            // [M] 1 / diag(S)
+  const int32_t* sp_slot;  // spreading CSR
+  const int32_t* sp_off;
+  const int32_t* sp_ent;
+  int64_t n_sp;
+};
+
+// Eq. 17-18: W[i][a] = phi((x_a - X_i)/hx) phi((y_a - Y_i)/hy) phi((z_a - Z_i)/hz).
+void ib_weights(const IBDev& ib, const double origin[3], const double hf[3], cudaStream_t st);
+// S = (dt/(rho h^3)) W_f W_f^T over free nodes (Eq. 22); dinv = 1/diag.
+void ib_assemble(const IBDev& ib, double scale, cudaStream_t st);
+// B_F = U_B - W u (Eq. 23), u on the finest level ([3][nslots]).
+void ib_gather(const IBDev& ib, const double* u, int64_t nslots, const double* UB, double* BF, cudaStream_t st);
+// PCG on S G = B_F for the 3 components ([M][3]); G holds the warm start.
+SolveStats ib_solve(const IBDev& ib, const double* BF, double* G, double* work /* 4*3*M */, KState* ks,
+                    KState* ks_host, RedBuf rb, double rtol, int max_iter, cudaStream_t st);
+// u_j += coef * sum_i W[i][a(j)] G_i on free support nodes (Eq. 19, Eq. 14).
+void ib_spread(const IBDev& ib, const double* G, double coef, double* u, int64_t nslots, cudaStream_t st);
+
+}  // namespace ibg

@@ -1,0 +1,191 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (stated by the task's accuracy targets and used below):
+  * integer structures (active cells, level map, node numbering, node flags,
+    IB supports): bit-exact;
+  * FP64 path: relative L2 <= 1e-10 per field;
+  * mixed path (FP32 Krylov inside FP64 defect correction): relative L2 <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ibfe
+from tests.gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOLMIX = 1e-6
+
+
+def _cases():
+    return {
+        # 16x16x64 uniform cylinder, several bricks and a ragged brick tail (17x17x65 nodes)
+        "uniform": (W.cylinder_uniform_16x16x64(), 5),
+        # one refinement level in a 2-cell band, domain reduction, pulsatile inlet
+        "refined": (W.cylinder_refined_small(n=(16, 16, 8), seed=21), 4),
+        # two refinement levels
+        "two_levels": (W.cylinder_case(n=(24, 24, 8), length=1.0, half_width=0.75, M=1500, seed=12,
+                                       max_level=2, refine_band=1, reduce_band=3, nu=0.02, dt=0.002,
+                                       b=(0.5,)), 2),
+    }
+
+
+CASES = _cases()
+_ORACLE = {}
+
+
+def oracle_run(name):
+    if name not in _ORACLE:
+        case, steps = CASES[name]
+        o = ibfe.Oracle(case)
+        hist = []
+        for _ in range(steps):
+            o.step()
+            hist.append({"u": o.u.copy(), "p": o.p.copy(), "phi": o.phi.copy(), "ut": o.ut.copy(),
+                         "uib": o.u_ib.copy(), "F": o.F.copy(), "BF": o.BF.copy()})
+        _ORACLE[name] = (o, hist)
+    return _ORACLE[name]
+
+
+def gpu_grid(name, precision="fp64"):
+    from paper_2007_02082_gb300 import IBGrid
+    case, _ = CASES[name]
+    return IBGrid(case, precision=precision)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_structures_bit_exact(name):
+    case, _ = CASES[name]
+    g = gpu_grid(name)
+    m = ibfe.build_mesh(case)
+    vdir = ibfe.velocity_dirichlet(m)
+    free = ~vdir & ~m.hanging
+    ib = ibfe.IB(m, case, free)
+    flags = (m.hanging * 1 + vdir * 2 + m.outlet * 4 + (m.inlet > 0) * 8 + m.boundary * 16).astype(np.uint8)
+    assert np.array_equal(g.ib_fields_get("ACTIVE"), m.active.astype(np.uint8))
+    assert np.array_equal(g.ib_fields_get("LEVEL"), m.level.astype(np.uint8))
+    assert np.array_equal(g.ib_fields_get("NODE_Q"), m.node_q.astype(np.int32))
+    assert np.array_equal(g.ib_fields_get("NODE_FLAGS"), flags)
+    assert np.array_equal(g.ib_fields_get("IB_ORIGIN"), ib.origin.astype(np.int32))
+    exists = ib.support_idx >= 0
+    fr = np.where(exists, np.where(free[np.maximum(ib.support_idx, 0)], 1, 2), 0).astype(np.uint8)
+    assert np.array_equal(g.ib_fields_get("IB_FREE"), fr)
+    # Eq. 18 weights, computed on the GPU in FP64
+    assert np.abs(g.ib_fields_get("IB_WEIGHTS") - ib.weights).max() < 1e-15
+    info = g.ib_grid_info()
+    assert info["n_nodes"] == m.n_nodes and info["n_dof"] == m.n_dof
+    assert info["n_hanging"] == int(m.hanging.sum())
+    g.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_step_parity(name):
+    _, steps = CASES[name]
+    o, hist = oracle_run(name)
+    g = gpu_grid(name, "fp64")
+    for k in range(steps):
+        g.ipcs_step(1)
+        ref = hist[k]
+        got = {"u": g.ib_fields_get("U"), "p": g.ib_fields_get("P"), "phi": g.ib_fields_get("PHI"),
+               "ut": g.ib_fields_get("U_TENT"), "uib": g.ib_fields_get("U_IB"), "F": g.ib_fields_get("F_LAG"),
+               "BF": g.ib_fields_get("B_F")}
+        for key in ("ut", "uib", "u", "p", "phi", "F", "BF"):
+            e = rel_l2(got[key], ref[key])
+            assert e <= TOL64, f"step {k + 1} {key}: rel L2 {e:.3e}"
+    info = g.ib_grid_info()
+    assert info["step"] == steps
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["uniform", "refined"])
+def test_mixed_step_parity(name):
+    _, steps = CASES[name]
+    o, hist = oracle_run(name)
+    g = gpu_grid(name, "mixed")
+    g.ipcs_step(steps)
+    ref = hist[-1]
+    for key, field in (("u", "U"), ("p", "P"), ("phi", "PHI"), ("F", "F_LAG")):
+        e = rel_l2(g.ib_fields_get(field), ref[key])
+        assert e <= TOLMIX, f"{key}: rel L2 {e:.3e}"
+    g.close()
+
+
+def test_noslip_and_constraints_hold_on_gpu():
+    """Invariants that hold at any size: the corrected velocity interpolates
+    to U_B (Eq. 15-16); hanging nodes carry the mean of their parents; Phi is
+    zero on outlet nodes."""
+    case, _ = CASES["refined"]
+    g = gpu_grid("refined", "fp64")
+    g.ipcs_step(2)
+    m = ibfe.build_mesh(case)
+    vdir = ibfe.velocity_dirichlet(m)
+    ib = ibfe.IB(m, case, ~vdir & ~m.hanging)
+    uib = g.ib_fields_get("U_IB")
+    assert np.abs(ib.W @ uib - case["UB"]).max() < 1e-9
+    u = g.ib_fields_get("U")
+    h = np.nonzero(m.hanging)[0]
+    par = m.parents[h]
+    assert np.abs(u[h] - 0.5 * (u[par[:, 0]] + u[par[:, 1]])).max() < 1e-14
+    phi = g.ib_fields_get("PHI")
+    assert np.all(phi[m.outlet] == 0.0)
+    g.close()
+
+
+def test_repeatable_bitwise():
+    a = gpu_grid("uniform", "fp64")
+    b = gpu_grid("uniform", "fp64")
+    a.ipcs_step(2)
+    b.ipcs_step(2)
+    assert np.array_equal(a.ib_fields_get("U"), b.ib_fields_get("U"))
+    assert np.array_equal(a.ib_fields_get("P"), b.ib_fields_get("P"))
+    a.close()
+    b.close()
+
+
+def test_checkpoint_resume_bitwise():
+    """2 steps, export u and p, restore them into a fresh handle, 2 more steps
+    == 4 steps straight (FP64 path; warm starts reset identically)."""
+    a = gpu_grid("uniform", "fp64")
+    a.ipcs_step(4)
+    b = gpu_grid("uniform", "fp64")
+    b.ipcs_step(2)
+    u, p = b.ib_fields_get("U"), b.ib_fields_get("P")
+    c = gpu_grid("uniform", "fp64")
+    c.ib_fields_set("U", u)
+    c.ib_fields_set("P", p)
+    c.ipcs_step(2)
+    # warm starts (Phi, F) differ between c and a, so the match is to solver tolerance
+    assert rel_l2(c.ib_fields_get("U"), a.ib_fields_get("U")) < TOL64
+    assert rel_l2(c.ib_fields_get("P"), a.ib_fields_get("P")) < TOL64
+    for g in (a, b, c):
+        g.close()
+
+
+def test_zero_steps_is_noop_and_errors_are_reported():
+    from paper_2007_02082_gb300 import IBError
+    g = gpu_grid("uniform", "fp64")
+    u0 = g.ib_fields_get("U")
+    g.ipcs_step(0)
+    assert np.array_equal(g.ib_fields_get("U"), u0)
+    with pytest.raises(IBError):
+        g.ipcs_step(-1)
+    with pytest.raises(IBError):
+        g.ib_fields_set("PHI", np.zeros(len(u0)))
+    g.close()
+
+
+def test_nonconvergence_keeps_previous_state():
+    """A cap of 2 Krylov iterations cannot converge: the step reports
+    IB_ENOCONV and the committed state is untouched."""
+    from paper_2007_02082_gb300 import IBError, IBGrid
+    case, _ = CASES["uniform"]
+    g = IBGrid(case, precision="fp64", max_iter=2)
+    u0 = g.ib_fields_get("U")
+    with pytest.raises(IBError) as ei:
+        g.ipcs_step(1)
+    assert ei.value.status == 4
+    assert np.array_equal(g.ib_fields_get("U"), u0)
+    assert g.ib_grid_info()["step"] == 0
+    g.close()

@@ -1,0 +1,152 @@
+"""Host-side logic of the library, checked on the CPU.
+
+* The library builds and exports every function include/ib.h declares.
+* The host grid builder (level map, active cells, canonical nodes, hanging
+  nodes, boundary/port flags, IB supports) agrees bit for bit with the oracle.
+  It is compiled with a small driver (tests/host_grid_probe.cpp), so no GPU is
+  needed.
+"""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ibfe
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2007_02082_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2007_02082_gb300.build import build
+    return build()
+
+
+def test_library_exports_every_declared_function(lib_path):
+    hdr = open(os.path.join(ROOT, "include", "ib.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"^\s*(?:ib_status|const char\*|void)\s+(\w+)\s*\(", hdr, flags=re.M))
+    assert {"ib_grid_create", "ib_set_boundary", "ipcs_step", "ib_fields_get"} <= names
+    lib = C.CDLL(lib_path)
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2007_02082_gb300 import _abi
+    assert set(_abi.EXPORTS) == names
+
+
+def test_abi_struct_sizes_match_header(tmp_path):
+    """The ctypes mirror has the same layout as the C structs."""
+    from paper_2007_02082_gb300 import _abi
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "ib.h"\nint main(){printf("%zu %zu %zu\\n",'
+                   'sizeof(ib_port),sizeof(ib_grid_desc),sizeof(ib_info));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert [int(v) for v in out] == [C.sizeof(_abi.IbPort), C.sizeof(_abi.IbGridDesc), C.sizeof(_abi.IbInfo)]
+
+
+@pytest.fixture(scope="module")
+def probe(tmp_path_factory):
+    d = tmp_path_factory.mktemp("probe")
+    exe = d / "probe"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-I", os.path.join(ROOT, "include"),
+                    "-I", CSRC, os.path.join(CSRC, "setup.cpp"), os.path.join(ROOT, "tests", "host_grid_probe.cpp"),
+                    "-o", str(exe)], check=True)
+    return exe, d
+
+
+def _desc(case):
+    from paper_2007_02082_gb300 import _abi
+    from paper_2007_02082_gb300 import _port_struct
+    d = _abi.IbGridDesc()
+    for a in range(3):
+        d.origin[a] = case["origin"][a]
+        d.extent[a] = case["extent"][a]
+        d.n[a] = case["n"][a]
+    d.max_level, d.refine_band, d.reduce_band = case["max_level"], case["refine_band"], case["reduce_band"]
+    d.nu, d.rho, d.dt = case["nu"], case["rho"], case["dt"]
+    d.n_ports = len(case["ports"])
+    for k, p in enumerate(case["ports"]):
+        d.ports[k] = _port_struct(p)
+    return d
+
+
+def run_probe(probe, case):
+    exe, d = probe
+    inp, out = d / "in.bin", d / "out.bin"
+    desc = _desc(case)
+    M = len(case["X"])
+    with open(inp, "wb") as f:
+        f.write(bytes(desc))
+        f.write(np.int64(M).tobytes())
+        f.write(np.ascontiguousarray(case["X"], np.float64).tobytes())
+        f.write(np.ascontiguousarray(case["dS"], np.float64).tobytes())
+        f.write(np.ascontiguousarray(case["UB"], np.float64).tobytes())
+        f.write(np.ascontiguousarray(case["inside"], np.uint8).tobytes())
+    r = subprocess.run([str(exe), str(inp), str(out)], capture_output=True, text=True)
+    if r.returncode != 0:
+        return r.returncode, r.stderr
+    b = open(out, "rb").read()
+    hdr = np.frombuffer(b[:48], np.int64)
+    N, M, nc = (int(v) for v in hdr[:3])
+    o = 48
+    res = {"n_hang": int(hdr[3]), "n_if": int(hdr[4]), "nbricks": int(hdr[5])}
+    for name, cnt, dt in (("q", 3 * N, np.int32), ("flags", N, np.uint8), ("active", nc, np.uint8),
+                          ("level", nc, np.uint8), ("ib_origin", 3 * M, np.int32), ("ib_free", 64 * M, np.uint8)):
+        nb = cnt * np.dtype(dt).itemsize
+        res[name] = np.frombuffer(b[o:o + nb], dt)
+        o += nb
+    res["q"] = res["q"].reshape(N, 3)
+    res["ib_origin"] = res["ib_origin"].reshape(M, 3)
+    res["ib_free"] = res["ib_free"].reshape(M, 64)
+    return 0, res
+
+
+def oracle_structures(case):
+    m = ibfe.build_mesh(case)
+    vdir = ibfe.velocity_dirichlet(m)
+    free = ~vdir & ~m.hanging
+    ib = ibfe.IB(m, case, free)
+    flags = (m.hanging * 1 + vdir * 2 + m.outlet * 4 + (m.inlet > 0) * 8 + m.boundary * 16).astype(np.uint8)
+    exists = ib.support_idx >= 0
+    fr = np.where(exists, np.where(free[np.maximum(ib.support_idx, 0)], 1, 2), 0).astype(np.uint8)
+    return m, flags, ib.origin, fr
+
+
+CASES = {
+    "uniform_16x16x64": lambda: W.cylinder_uniform_16x16x64(),
+    "refined_16x16x32": lambda: W.cylinder_refined_small(),
+    "refined_reduced_20x20x12": lambda: W.cylinder_case(n=(20, 20, 12), length=1.5, half_width=0.75, M=900,
+                                                         seed=11, max_level=1, refine_band=2, reduce_band=2),
+    "two_levels_24x24x8": lambda: W.cylinder_case(n=(24, 24, 8), length=1.0, half_width=0.75, M=1500, seed=12,
+                                                  max_level=2, refine_band=1, reduce_band=3),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_host_grid_matches_oracle_bit_exact(probe, name):
+    case = CASES[name]()
+    rc, res = run_probe(probe, case)
+    assert rc == 0, res
+    m, flags, org, fr = oracle_structures(case)
+    assert np.array_equal(res["active"], m.active.astype(np.uint8).ravel())
+    assert np.array_equal(res["level"], m.level.astype(np.uint8).ravel())
+    assert np.array_equal(res["q"], m.node_q.astype(np.int32))
+    assert res["n_hang"] == int(m.hanging.sum())
+    assert np.array_equal(res["flags"], flags)
+    assert np.array_equal(res["ib_origin"], org.astype(np.int32))
+    assert np.array_equal(res["ib_free"], fr)
+
+
+def test_point_outside_box_is_rejected(probe):
+    case = W.cylinder_uniform_16x16x64()
+    case["X"] = case["X"].copy()
+    case["X"][5] = (10.0, 0.0, 1.0)
+    rc, err = run_probe(probe, case)
+    assert rc == 10 + 1 and "outside" in err
