@@ -288,22 +288,25 @@ SolveStats solve(ib_grid* g, int op, bool bicg, int nc, uint16_t dmask, const do
   SolveStats tot;
   const int max_outer = 30;
   int outer = 0;
+  double ref[3] = {0.0, 0.0, 0.0};   // max(||b||^2, ||r0||^2) per component
   for (; outer < max_outer; ++outer) {
     fe_residual64(dg, A64, nc, b, x, g->y64, g->r64, g->rb, g->host_rrbb, g->st);
     double rel = 0.0;
     for (int c = 0; c < nc; ++c) {
       double rr = g->host_rrbb[2 * c], bb = g->host_rrbb[2 * c + 1];
-      rel = std::max(rel, bb > 0 ? std::sqrt(rr / bb) : (rr > 0 ? INFINITY : 0.0));
+      if (outer == 0) ref[c] = std::max(bb, rr);
+      rel = std::max(rel, ref[c] > 0 ? std::sqrt(rr / ref[c]) : 0.0);
     }
     tot.relres = rel;
     if (!std::isfinite(rel)) { tot.status = 5; break; }
     if (rel <= rtol) break;
     fe_cast_d2f(n, g->r64, g->r32, g->st);
     fe_zero<float>(n, g->e32, g->st);
-    SolveStats in = bicg ? fe_bicgstab<float>(dg, A32, nc, g->r32, g->e32, g->w32, g->ks, g->ks_host, g->rb,
-                                              std::max(g->d.precision == IB_MIXED ? 1e-4 : rtol, rtol), max_iter, g->st)
-                         : fe_cg<float>(dg, A32, nc, g->r32, g->e32, g->w32, g->ks, g->ks_host, g->rb,
-                                        std::max(1e-4, rtol), max_iter, g->st);
+    const double rin = std::max(tolerances(g).inner, rtol);
+    SolveStats in = bicg ? fe_bicgstab<float>(dg, A32, nc, g->r32, g->e32, g->w32, g->ks, g->ks_host, g->rb, rin,
+                                              max_iter, g->st)
+                         : fe_cg<float>(dg, A32, nc, g->r32, g->e32, g->w32, g->ks, g->ks_host, g->rb, rin, max_iter,
+                                        g->st);
     for (int c = 0; c < 3; ++c) tot.iters[c] += in.iters[c];
     if (in.status == 5) { tot.status = 5; break; }
     fe_add_f2d(n, g->e32, x, g->st);

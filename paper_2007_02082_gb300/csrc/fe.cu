@@ -239,7 +239,9 @@ __global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict
       KState& k = ks[c];
       k.rz = tot[3 * c];
       k.rr = tot[3 * c + 1];
-      k.bb = tot[3 * c + 2];
+      // reference norm: max(||b||, ||r0||) covers a zero right-hand side with
+      // nonzero Dirichlet lifting as well as warm starts
+      k.bb = fmax(tot[3 * c + 2], k.rr);
       k.iter = 0;
       k.status = 0;
       k.alpha = 0.0;
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restric
     for (int c = 0; c < NC; ++c) {
       KState& k = ks[c];
       k.rr = tot[2 * c];
-      k.bb = tot[2 * c + 1];
+      k.bb = fmax(tot[2 * c + 1], k.rr);
       k.rho = k.rr;
       k.alpha = 1.0;
       k.omega = 1.0;

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(IBB) k_af_start(int64_t M, const double* __res
       KState& k = ks[c];
       k.rz = tot[3 * c];
       k.rr = tot[3 * c + 1];
-      k.bb = tot[3 * c + 2];
+      k.bb = fmax(tot[3 * c + 2], k.rr);
       k.iter = 0;
       k.status = 0;
       k.done = (k.rr <= k.tol2 * k.bb) ? 1 : 0;
