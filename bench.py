@@ -149,7 +149,7 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     load_library(build_if_missing=True)
     case = workload(args.workload)
-    g = IBGrid(case, precision=args.precision, device=local_rank, profile=True)
+    g = IBGrid(case, precision=args.precision, device=local_rank)
     info0 = g.ib_grid_info()
     cells = info0["n_leaf_cells"]
     stream = torch.cuda.current_stream()
@@ -174,7 +174,11 @@ def run_native(args, rank, world, local_rank):
     t0.record(stream)
     for _ in range(args.steps):
         flush.zero_()                     # evict the working set from L2 between steps
+        if args.nvtx:
+            torch.cuda.nvtx.range_push("ipcs_step")
         g.ipcs_step(1)
+        if args.nvtx:
+            torch.cuda.nvtx.range_pop()
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
@@ -189,10 +193,24 @@ def run_native(args, rank, world, local_rank):
         ms = float(tt.item())
     value = cells * args.steps * world / (ms / 1e3)
 
-    # dominant profiled kernel class over the timed region
-    dms = [i2["prof_ms"][k] - i1["prof_ms"][k] for k in range(12)]
-    dn = [i2["prof_launches"][k] - i1["prof_launches"][k] for k in range(12)]
+    # Kernels inside the step graph cannot be bracketed by events, so the same
+    # step is replayed eagerly on a second handle (same stream, same kernels,
+    # same order) with CUDA events around every solver kernel launch.
+    gp = IBGrid(case, precision=args.precision, device=local_rank, profile=True)
+    for _ in range(max(1, args.warmup)):
+        gp.ipcs_step(1)
+    j1 = gp.ib_grid_info()
+    prof_steps = max(1, min(args.steps, 3))
+    for _ in range(prof_steps):
+        flush.zero_()
+        gp.ipcs_step(1)
+    torch.cuda.synchronize()
+    j2 = gp.ib_grid_info()
+    gp.close()
+    dms = [j2["prof_ms"][k] - j1["prof_ms"][k] for k in range(12)]
+    dn = [j2["prof_launches"][k] - j1["prof_launches"][k] for k in range(12)]
     dom = max((k for k in CLASS_NAMES if dn[k] > 0), key=lambda k: dms[k])
+    prof_share = {CLASS_NAMES[k]: round(dms[k] / max(sum(dms), 1e-30), 4) for k in CLASS_NAMES if dn[k] > 0}
     vb = 4 if args.precision == "mixed" else 8
     per_launch_bytes = class_bytes(dom, vb) * info0["n_valid_slots"]
     avg_ms = dms[dom] / dn[dom]
@@ -245,7 +263,9 @@ def run_native(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": CLASS_NAMES[dom], "peak_source": peak_src,
-                     "avg_launch_us": avg_ms * 1e3, "bytes_per_launch": per_launch_bytes},
+                     "avg_launch_us": avg_ms * 1e3, "bytes_per_launch": per_launch_bytes,
+                     "timing": "CUDA events around each launch, eager replay of the same step",
+                     "solver_kernel_time_share": prof_share},
         "clocks": ck,
         "e2e": e2e,
         "iters_last_step": {k: i2[k] for k in ("iters_mom", "iters_ib", "iters_p", "iters_corr", "outer_mom",
@@ -277,6 +297,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="cylinder_64x64x256_L1")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nvtx", action="store_true", help="wrap each timed step in an NVTX range 'ipcs_step'")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

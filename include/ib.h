@@ -41,7 +41,8 @@
 extern "C" {
 #endif
 
-typedef struct ib_grid ib_grid; /* opaque */
+typedef struct ib_grid ib_grid;   /* opaque: one problem */
+typedef struct ib_batch ib_batch; /* opaque: several deferred problems stepped together */
 
 typedef enum {
   IB_OK = 0,
@@ -104,8 +105,14 @@ typedef struct {
  *   rtol_*              relative residual tolerances of the momentum, Poisson,
  *                       velocity-correction and force solves (0 = defaults)
  *   max_iter            iteration cap per Krylov solve (0 = default)
- *   profile             1: record CUDA events around the solvers' kernel
- *                       launches (ib_info.prof_ms / prof_launches)
+ *   profile             1: run each step eagerly (host-polled loops instead of
+ *                       the captured step graph) and record CUDA events
+ *                       around the solvers' kernel launches
+ *                       (ib_info.prof_ms / prof_launches); results are
+ *                       bitwise those of the graph path
+ *   deferred            1: ib_set_boundary builds the grid and a device state
+ *                       snapshot only; the problem is advanced by ib_batch_step
+ *                       together with other deferred problems
  *   stream              cudaStream_t on which all work is enqueued
  *   dev_alloc/dev_free  optional device allocator (ctx = alloc_ctx)
  */
@@ -118,6 +125,8 @@ typedef struct {
   double rtol_mom, rtol_p, rtol_corr, rtol_ib;
   int32_t max_iter;
   int32_t profile;          /* 1: time solver kernel launches with CUDA events */
+  int32_t deferred;         /* 1: keep only the grid and a state snapshot; the
+                               problem is stepped inside an ib_batch */
   int32_t n_ports;
   ib_port ports[IB_MAX_PORTS];
   void* stream;
@@ -229,8 +238,37 @@ ib_status ib_grid_info(const ib_grid* g, ib_info* out);
 /* ib_last_error: text of the last error on g (never NULL; "" if none). */
 const char* ib_last_error(const ib_grid* g);
 
-/* ib_grid_destroy: free every resource of g (NULL is a no-op). */
+/* ib_grid_destroy: free every resource of g (NULL is a no-op; a handle that a
+ * batch still holds is left alone: destroy the batch first). */
 void ib_grid_destroy(ib_grid* g);
+
+/*
+ * Batches (continuous batching of several problems on one GPU).
+ *
+ * ib_batch_create: lay out the grids, fields and solver state of n deferred
+ *   handles side by side on the device and load each one's state snapshot
+ *   (zero for a new problem).  One step of the batch is one captured graph in
+ *   which every kernel runs over the concatenated bricks of all members and
+ *   every Krylov reduction is segmented per member, so each member's result is
+ *   bitwise the same alone and in any mix.  Members must share the precision;
+ *   each keeps its own grid, nu, dt, rho, ports and tolerances of member 0.
+ *   Errors: IB_EINVAL (a member not deferred, not ready, repeated, or already
+ *   in a batch), IB_ENOMEM, IB_ECUDA.
+ * ib_batch_step: nsteps steps of every member; status[i] (if not NULL, n
+ *   entries) receives each member's status of the last step.  A member whose
+ *   solves failed keeps its previous state; the call returns the worst status.
+ * ib_batch_fields_get / ib_batch_info: as ib_fields_get / ib_grid_info for
+ *   member i (ib_fields_get and ib_grid_info on a member handle forward here).
+ * ib_batch_destroy: store every member's state back into its snapshot and
+ *   release the batch (members can then join another batch).
+ */
+ib_status ib_batch_create(ib_grid* const* members, int32_t n, ib_batch** out);
+ib_status ib_batch_step(ib_batch* b, int32_t nsteps, int32_t* status);
+ib_status ib_batch_fields_get(ib_batch* b, int32_t member, int32_t field, void* dst, size_t bytes,
+                              int32_t dst_on_device);
+ib_status ib_batch_info(const ib_batch* b, int32_t member, ib_info* out);
+const char* ib_batch_last_error(const ib_batch* b);
+void ib_batch_destroy(ib_batch* b);
 
 #ifdef __cplusplus
 }

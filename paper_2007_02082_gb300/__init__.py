@@ -91,7 +91,7 @@ class IBGrid:
     """One resident IB-FE-IPCS problem (an ib_grid handle)."""
 
     def __init__(self, case, precision="fp64", stream=None, torch_alloc=True, rtol=None, max_iter=0,
-                 device=0, profile=False):
+                 device=0, profile=False, deferred=False):
         self.lib = load_library()
         self.case = case
         self._alloc = None
@@ -125,6 +125,7 @@ class IBGrid:
         d.rtol_ib = rt.get("ib", 0.0)
         d.max_iter = max_iter
         d.profile = 1 if profile else 0
+        d.deferred = 1 if deferred else 0
         d.n_ports = len(case["ports"])
         for k, port in enumerate(case["ports"]):
             d.ports[k] = _port_struct(port)
@@ -205,4 +206,49 @@ class IBGrid:
             pass
 
 
-__all__ = ["IBGrid", "IBError", "load_library", "FIELD"]
+class IBBatch:
+    """Several deferred IBGrid problems stepped together (ib_batch_*)."""
+
+    def __init__(self, members):
+        self.lib = load_library()
+        self.members = list(members)
+        n = len(self.members)
+        arr = (C.c_void_p * n)(*[m.h.value for m in self.members])
+        h = C.c_void_p()
+        s = self.lib.ib_batch_create(arr, n, C.byref(h))
+        if s != 0:
+            msg = self.members[0].lib.ib_last_error(self.members[0].h).decode() if n else ""
+            raise IBError("ib_batch_create", s, msg)
+        self.h = h
+
+    def step(self, nsteps=1):
+        """Advance every member; returns the per-member status of the last step."""
+        st = np.zeros(len(self.members), dtype=np.int32)
+        s = self.lib.ib_batch_step(self.h, int(nsteps), st.ctypes.data)
+        if s not in (0, 4, 5):
+            raise IBError("ib_batch_step", s, self.lib.ib_batch_last_error(self.h).decode())
+        return st
+
+    def info(self, i):
+        info = _abi.IbInfo()
+        s = self.lib.ib_batch_info(self.h, int(i), C.byref(info))
+        if s != 0:
+            raise IBError("ib_batch_info", s, "")
+        return info.as_dict()
+
+    def fields_get(self, i, field):
+        return self.members[i].ib_fields_get(field)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ib_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["IBGrid", "IBBatch", "IBError", "load_library", "FIELD"]

@@ -17,7 +17,8 @@ FIELD = {
 }
 
 EXPORTS = ("ib_grid_create", "ib_set_boundary", "ipcs_step", "ib_fields_get", "ib_fields_set",
-           "ib_grid_info", "ib_last_error", "ib_grid_destroy")
+           "ib_grid_info", "ib_last_error", "ib_grid_destroy", "ib_batch_create", "ib_batch_step",
+           "ib_batch_fields_get", "ib_batch_info", "ib_batch_last_error", "ib_batch_destroy")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -38,7 +39,7 @@ class IbGridDesc(C.Structure):
         ("max_level", C.c_int32), ("refine_band", C.c_int32), ("reduce_band", C.c_int32),
         ("nu", C.c_double), ("rho", C.c_double), ("dt", C.c_double), ("precision", C.c_int32),
         ("rtol_mom", C.c_double), ("rtol_p", C.c_double), ("rtol_corr", C.c_double), ("rtol_ib", C.c_double),
-        ("max_iter", C.c_int32), ("profile", C.c_int32), ("n_ports", C.c_int32), ("ports", IbPort * IB_MAX_PORTS),
+        ("max_iter", C.c_int32), ("profile", C.c_int32), ("deferred", C.c_int32), ("n_ports", C.c_int32), ("ports", IbPort * IB_MAX_PORTS),
         ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]
 
@@ -83,6 +84,18 @@ def bind(lib: C.CDLL) -> C.CDLL:
     lib.ib_last_error.restype = C.c_char_p
     lib.ib_grid_destroy.argtypes = [C.c_void_p]
     lib.ib_grid_destroy.restype = None
+    lib.ib_batch_create.argtypes = [P(C.c_void_p), C.c_int32, P(C.c_void_p)]
+    lib.ib_batch_create.restype = C.c_int
+    lib.ib_batch_step.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+    lib.ib_batch_step.restype = C.c_int
+    lib.ib_batch_fields_get.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.c_int32]
+    lib.ib_batch_fields_get.restype = C.c_int
+    lib.ib_batch_info.argtypes = [C.c_void_p, C.c_int32, P(IbInfo)]
+    lib.ib_batch_info.restype = C.c_int
+    lib.ib_batch_last_error.argtypes = [C.c_void_p]
+    lib.ib_batch_last_error.restype = C.c_char_p
+    lib.ib_batch_destroy.argtypes = [C.c_void_p]
+    lib.ib_batch_destroy.restype = None
     return lib
 
 

@@ -1,4 +1,4 @@
-// C ABI (include/ib.h): handle lifetime, device buffers and the IPCS step driver.
+// C ABI (include/ib.h): handles, batches, device buffers and the IPCS step driver.
 //
 // One step (combined algorithm of Sec. 2.4):
 //   1. tentative velocity: (M + dt C(u^n) + dt nu K) u~ = M u^n - dt G p^n   (Eq. 9)
@@ -8,10 +8,24 @@
 //   5. (grad Phi, grad q) = -(1/dt)(div u, q), Phi = 0 on outlet nodes (Eq. 12); PCG.
 //   6. (u^{n+1}, v) = (u, v) - dt (grad Phi, v) with the velocity conditions;
 //      p^{n+1} = p^n + Phi; PCG on the consistent mass matrix.
-// The step is committed (buffers swapped, time advanced) only when every solve
-// converged.  With precision IB_MIXED each solve runs FP32 Krylov iterations
-// (FP32 operator and Jacobi preconditioner) inside an FP64 defect-correction
-// loop whose residual b - A x is formed in FP64.
+// With precision IB_MIXED each solve runs FP32 Krylov iterations (FP32 operator
+// and Jacobi preconditioner) inside an FP64 defect-correction loop whose
+// residual b - A x is formed in FP64.
+//
+// Engine.  The device state of one or several problem instances laid out side
+// by side: bricks, slots and Lagrangian rows of instance i follow those of
+// instance i - 1, so every kernel runs once over all instances and every
+// reduction is segmented per instance (each instance's scalars depend only on
+// its own data).  A standalone handle owns an engine of one instance; a batch
+// is an engine over several deferred handles.
+//
+// Execution: the whole step is captured once into a CUDA graph (two graphs, one
+// per ping-pong parity of the u/p buffers) in which every Krylov loop and the
+// FP64 outer loop are conditional WHILE nodes decided on the device; a step is
+// one graph launch and one host synchronisation (to read the solve records).
+// With desc.profile the same launches run eagerly, loops polled from the host,
+// and every solver kernel is timed with CUDA events.  A step is committed per
+// instance: an instance whose solves failed keeps its previous state.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -21,47 +35,119 @@
 #include "fe.hpp"
 #include "ib.h"
 #include "ib.hpp"
+#include "krylov.hpp"
 #include "setup.hpp"
 
 using namespace ibg;
+
+namespace ibg {
+unsigned long long fe_kcount();
+unsigned long long krylov_kcount();
+unsigned long long ib_kcount();
+}
+
+namespace {
+
+struct Tols {
+  double mom, p, corr, ib, inner;
+  int max_iter;
+};
+
+Tols tolerances(const ib_grid_desc& d) {
+  const bool mixed = d.precision == IB_MIXED;
+  Tols t;
+  t.mom = d.rtol_mom > 0 ? d.rtol_mom : (mixed ? 1e-10 : 1e-13);
+  t.p = d.rtol_p > 0 ? d.rtol_p : (mixed ? 1e-10 : 1e-13);
+  t.corr = d.rtol_corr > 0 ? d.rtol_corr : (mixed ? 1e-10 : 1e-13);
+  t.ib = d.rtol_ib > 0 ? d.rtol_ib : 1e-13;
+  t.inner = 1e-4;
+  t.max_iter = d.max_iter > 0 ? d.max_iter : 20000;
+  return t;
+}
+
+struct Engine {
+  std::vector<const HostGrid*> H;
+  std::vector<ib_grid_desc> D;
+  int ninst = 0;
+  bool mixed = false;
+  Tols tol{};
+  cudaStream_t st = nullptr;
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*freef)(void*, void*) = nullptr;
+  void* actx = nullptr;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  std::string err;
+  // layout
+  std::vector<int64_t> brick0, slot0, ns_i, row0, canon0;
+  int64_t nbricks = 0, ns = 0, Mtot = 0, n_inlet = 0, n_valid = 0;
+  DevGrid g{};
+  IBDev ib{};
+  int32_t* canon = nullptr;        // concatenated canonical -> global slot
+  int32_t *in_slot = nullptr, *in_port = nullptr;
+  double* in_shape = nullptr;
+  PortDev* ports = nullptr;
+  double *tc = nullptr, *tn = nullptr, *pdt = nullptr;
+  int32_t* ok = nullptr;
+  // fields [3][ns] / [ns]
+  double *ubuf[2] = {nullptr, nullptr}, *pbuf[2] = {nullptr, nullptr};
+  double *u = nullptr, *un = nullptr, *p = nullptr, *pn = nullptr, *phi = nullptr, *ut = nullptr, *uib = nullptr;
+  double *rhs3 = nullptr, *y64 = nullptr, *r64 = nullptr, *w64 = nullptr;
+  double *coef64 = nullptr, *diag64 = nullptr, *dK64 = nullptr, *dM64 = nullptr, *dA64 = nullptr;
+  float *coef32 = nullptr, *diag32 = nullptr, *dK32 = nullptr, *dM32 = nullptr, *dA32 = nullptr;
+  float *r32 = nullptr, *e32 = nullptr, *w32 = nullptr;
+  double *X = nullptr, *dS = nullptr, *UB = nullptr, *BF = nullptr, *Gf = nullptr, *ibw = nullptr;
+  // solver state
+  KState* ks = nullptr;
+  KState* ks_host = nullptr;
+  OState* os = nullptr;
+  OState* os_host = nullptr;
+  SolveRec* recs = nullptr;
+  SolveRec* recs_host = nullptr;
+  int32_t* ok_host = nullptr;
+  RedBuf rb{};
+  Prof prof;
+  bool use_graph = true;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  cudaStream_t cap_st = nullptr;
+  CaptureCtx cc;
+  // per-instance host counters
+  std::vector<int64_t> step;
+  std::vector<double> time;
+  std::vector<ib_info> last;
+  std::vector<int> status;
+};
+
+}  // namespace
+
+// device snapshot of a deferred handle's state in its own slot layout
+struct Snapshot {
+  double* u = nullptr;    // [3][ns]
+  double* p = nullptr;    // [ns]
+  double* phi = nullptr;  // [ns]
+  double* G = nullptr;    // [M][3]
+  int32_t* canon = nullptr;
+  int64_t step = 0;
+  double time = 0.0;
+  bool valid = false;
+};
 
 struct ib_grid {
   ib_grid_desc d{};
   std::string err;
   bool ready = false;
-  cudaStream_t st = nullptr;
   HostGrid H;
-  DevGrid g{};
-  IBDev ib{};
-  std::vector<void*> allocs;
-  int64_t dev_bytes = 0;
-  // topology
-  int32_t* canon = nullptr;
-  int32_t *in_slot = nullptr, *in_port = nullptr;
-  double* in_shape = nullptr;
-  PortDev* ports = nullptr;
-  double *tc = nullptr, *tn = nullptr;
-  // fields, [3][nslots] for vectors
-  double *u = nullptr, *un = nullptr, *p = nullptr, *pn = nullptr, *phi = nullptr, *ut = nullptr, *uib = nullptr;
-  // FP64 work
-  double *rhs3 = nullptr, *y64 = nullptr, *r64 = nullptr, *w64 = nullptr;
-  double *coef64 = nullptr, *diag64 = nullptr, *dK64 = nullptr, *dM64 = nullptr, *dA64 = nullptr;
-  // FP32 work (mixed)
-  float *coef32 = nullptr, *diag32 = nullptr, *dK32 = nullptr, *dM32 = nullptr, *dA32 = nullptr;
-  float *r32 = nullptr, *e32 = nullptr, *w32 = nullptr;
-  // IB
-  double *X = nullptr, *dS = nullptr, *UB = nullptr, *BF = nullptr, *Gf = nullptr, *ibw = nullptr;
-  // solver state
-  KState* ks = nullptr;
-  KState ks_host[3];
-  RedBuf rb{};
-  double* host_rrbb = nullptr;
-  Prof prof;
-  int64_t n_valid = 0;
-  // committed state
-  int64_t step = 0;
-  double time = 0.0;
-  ib_info last{};
+  Engine* eng = nullptr;        // standalone handle
+  Snapshot snap;                // deferred handle
+  std::vector<void*> snap_allocs;
+  int64_t snap_bytes = 0;
+  ib_batch* batch = nullptr;    // batch currently holding a deferred handle
+  int batch_index = -1;
+};
+
+struct ib_batch {
+  std::vector<ib_grid*> members;
+  Engine E;
 };
 
 namespace {
@@ -70,49 +156,10 @@ namespace {
   do {                                                                             \
     cudaError_t e_ = (x);                                                          \
     if (e_ != cudaSuccess) {                                                       \
-      g->err = std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #x;         \
+      E.err = std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #x;          \
       return IB_ECUDA;                                                             \
     }                                                                              \
   } while (0)
-
-template <typename T>
-ib_status dalloc(ib_grid* g, T** p, int64_t n) {
-  size_t bytes = size_t(std::max<int64_t>(n, 1)) * sizeof(T);
-  void* ptr = nullptr;
-  if (g->d.dev_alloc) {
-    ptr = g->d.dev_alloc(bytes, g->d.alloc_ctx);
-    if (!ptr) { g->err = "device allocator returned NULL"; return IB_ENOMEM; }
-  } else {
-    cudaError_t e = cudaMalloc(&ptr, bytes);
-    if (e != cudaSuccess) { g->err = std::string("cudaMalloc: ") + cudaGetErrorString(e); return IB_ENOMEM; }
-  }
-  g->allocs.push_back(ptr);
-  g->dev_bytes += int64_t(bytes);
-  *p = static_cast<T*>(ptr);
-  return IB_OK;
-}
-
-template <typename T>
-ib_status upload(ib_grid* g, T** p, const std::vector<T>& v) {
-  ib_status s = dalloc(g, p, int64_t(v.size()));
-  if (s != IB_OK) return s;
-  if (!v.empty()) CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, g->st));
-  return IB_OK;
-}
-
-void free_all(ib_grid* g) {
-  if (g->st) cudaStreamSynchronize(g->st);
-  for (void* p : g->allocs) {
-    if (g->d.dev_free) g->d.dev_free(p, g->d.alloc_ctx);
-    else cudaFree(p);
-  }
-  g->allocs.clear();
-  g->dev_bytes = 0;
-  g->prof.release();
-  for (int k = 0; k < Prof::K; ++k) { g->prof.ms[k] = 0.0; g->prof.n[k] = 0; }
-  if (g->host_rrbb) { cudaFreeHost(g->host_rrbb); g->host_rrbb = nullptr; }
-  g->ready = false;
-}
 
 #define TRY(x)                         \
   do {                                 \
@@ -120,284 +167,514 @@ void free_all(ib_grid* g) {
     if (s_ != IB_OK) return s_;        \
   } while (0)
 
-ib_status allocate_and_upload(ib_grid* g) {
-  HostGrid& H = g->H;
-  const int64_t ns = H.nbricks * BV;
-  DevGrid& dg = g->g;
-  dg = DevGrid();
-  dg.nbricks = int32_t(H.nbricks);
-  dg.nslots = ns;
-  for (int l = 0; l <= H.L; ++l)
-    for (int a = 0; a < 3; ++a) dg.h[l][a] = H.levels[l].h[a];
-  int32_t *blev, *bnbr, *ifc, *iff, *ifo, *ifk, *hg, *hp1, *hp2;
-  uint16_t* meta;
-  TRY(upload(g, &blev, H.brick_level));
-  TRY(upload(g, &bnbr, H.brick_nbr));
-  TRY(upload(g, &meta, H.meta));
-  std::vector<int32_t> ifo_v = H.if_child_off;
-  if (ifo_v.empty()) ifo_v.push_back(0);
-  TRY(upload(g, &ifc, H.if_coarse));
-  TRY(upload(g, &iff, H.if_fine));
-  TRY(upload(g, &ifo, ifo_v));
-  TRY(upload(g, &ifk, H.if_child));
-  TRY(upload(g, &hg, H.hang_slot));
-  TRY(upload(g, &hp1, H.hang_p1));
-  TRY(upload(g, &hp2, H.hang_p2));
-  dg.blev = blev; dg.bnbr = bnbr; dg.meta = meta;
-  dg.n_if = int32_t(H.if_coarse.size());
-  dg.if_c = ifc; dg.if_f = iff; dg.if_off = ifo; dg.if_kid = ifk;
-  dg.n_hang = int32_t(H.hang_slot.size());
-  dg.hg = hg; dg.hp1 = hp1; dg.hp2 = hp2;
-  TRY(upload(g, &g->canon, H.canon_slot));
-  TRY(upload(g, &g->in_slot, H.inlet_slot));
-  TRY(upload(g, &g->in_port, H.inlet_port));
-  TRY(upload(g, &g->in_shape, H.inlet_shape));
-  std::vector<PortDev> pd(std::max(1, int(g->d.n_ports)));
-  for (int p = 0; p < g->d.n_ports; ++p) {
-    const ib_port& P = g->d.ports[p];
-    pd[p] = PortDev();
-    pd[p].axis = P.axis;
-    pd[p].nh = std::min(P.n_harm, 8);
-    pd[p].a0 = P.a0;
-    pd[p].period = P.period > 0 ? P.period : 1.0;
-    for (int k = 0; k < 8; ++k) { pd[p].a[k] = P.a[k]; pd[p].b[k] = P.b[k]; }
-  }
-  TRY(upload(g, &g->ports, pd));
-  TRY(dalloc(g, &g->tc, 1));
-  TRY(dalloc(g, &g->tn, 1));
-  // fields and FP64 work
-  const bool mixed = g->d.precision == IB_MIXED;
-  TRY(dalloc(g, &g->u, 3 * ns));
-  TRY(dalloc(g, &g->un, 3 * ns));
-  TRY(dalloc(g, &g->ut, 3 * ns));
-  TRY(dalloc(g, &g->uib, 3 * ns));
-  TRY(dalloc(g, &g->p, ns));
-  TRY(dalloc(g, &g->pn, ns));
-  TRY(dalloc(g, &g->phi, ns));
-  TRY(dalloc(g, &g->rhs3, 3 * ns));
-  TRY(dalloc(g, &g->y64, 3 * ns));
-  TRY(dalloc(g, &g->r64, 3 * ns));
-  TRY(dalloc(g, &g->w64, mixed ? 3 * ns : 8 * 3 * ns));
-  TRY(dalloc(g, &g->coef64, 15 * ns));
-  TRY(dalloc(g, &g->diag64, ns));
-  TRY(dalloc(g, &g->dK64, ns));
-  TRY(dalloc(g, &g->dM64, ns));
-  TRY(dalloc(g, &g->dA64, ns));
-  if (mixed) {
-    TRY(dalloc(g, &g->coef32, 15 * ns));
-    TRY(dalloc(g, &g->diag32, ns));
-    TRY(dalloc(g, &g->dK32, ns));
-    TRY(dalloc(g, &g->dM32, ns));
-    TRY(dalloc(g, &g->dA32, ns));
-    TRY(dalloc(g, &g->r32, 3 * ns));
-    TRY(dalloc(g, &g->e32, 3 * ns));
-    TRY(dalloc(g, &g->w32, 8 * 3 * ns));
-  }
-  // IB
-  const int64_t M = H.M;
-  IBDev& ib = g->ib;
-  ib = IBDev();
-  ib.M = M;
-  int32_t *org, *slot, *rp, *col, *sps, *spo, *spe;
-  uint64_t* fb;
-  TRY(upload(g, &g->X, H.X));
-  TRY(upload(g, &g->dS, H.dS));
-  TRY(upload(g, &g->UB, H.UB));
-  TRY(upload(g, &org, H.ib_origin));
-  TRY(upload(g, &slot, H.ib_slot));
-  TRY(upload(g, &fb, H.ib_free));
-  std::vector<int32_t> rpv = H.af_rowptr;
-  if (rpv.empty()) rpv.push_back(0);
-  TRY(upload(g, &rp, rpv));
-  TRY(upload(g, &col, H.af_col));
-  std::vector<int32_t> spov = H.sp_off;
-  if (spov.empty()) spov.push_back(0);
-  TRY(upload(g, &sps, H.sp_slot));
-  TRY(upload(g, &spo, spov));
-  TRY(upload(g, &spe, H.sp_ent));
-  ib.X = g->X; ib.org = org; ib.slot = slot; ib.freeb = fb; ib.rowptr = rp; ib.col = col;
-  ib.sp_slot = sps; ib.sp_off = spo; ib.sp_ent = spe; ib.n_sp = int64_t(H.sp_slot.size());
-  TRY(dalloc(g, &ib.W, 64 * M));
-  TRY(dalloc(g, &ib.val, int64_t(H.af_col.size())));
-  TRY(dalloc(g, &ib.dinv, M));
-  TRY(dalloc(g, &g->BF, 3 * M));
-  TRY(dalloc(g, &g->Gf, 3 * M));
-  TRY(dalloc(g, &g->ibw, 4 * 3 * M));
-  // reductions
-  int64_t maxblk = std::max<int64_t>(H.nbricks, (M * 32 + 255) / 256 + 1);
-  TRY(dalloc(g, &g->rb.partials, maxblk * 16 + 64));
-  TRY(dalloc(g, &g->rb.counter, 1));
-  TRY(dalloc(g, &g->ks, 3));
-  CK(cudaMemsetAsync(g->rb.counter, 0, sizeof(unsigned), g->st));
-  CK(cudaMallocHost(&g->host_rrbb, 16 * sizeof(double)));
+void* raw_alloc(void* (*al)(size_t, void*), void* ctx, size_t bytes) {
+  void* ptr = nullptr;
+  if (al) return al(bytes, ctx);
+  if (cudaMalloc(&ptr, bytes) != cudaSuccess) return nullptr;
+  return ptr;
+}
+void raw_free(void (*fr)(void*, void*), void* ctx, void* p) {
+  if (fr) fr(p, ctx);
+  else cudaFree(p);
+}
+
+template <typename T>
+ib_status dalloc(Engine& E, T** p, int64_t n, bool zero = false) {
+  size_t bytes = size_t(std::max<int64_t>(n, 1)) * sizeof(T);
+  void* ptr = raw_alloc(E.alloc, E.actx, bytes);
+  if (!ptr) { E.err = "device allocation failed"; return IB_ENOMEM; }
+  E.allocs.push_back(ptr);
+  E.bytes += int64_t(bytes);
+  *p = static_cast<T*>(ptr);
+  if (zero) CK(cudaMemsetAsync(ptr, 0, bytes, E.st));
   return IB_OK;
 }
 
-ib_status reset_state(ib_grid* g) {
-  const int64_t ns = g->g.nslots;
-  CK(cudaMemsetAsync(g->u, 0, 3 * ns * sizeof(double), g->st));
-  CK(cudaMemsetAsync(g->un, 0, 3 * ns * sizeof(double), g->st));
-  CK(cudaMemsetAsync(g->ut, 0, 3 * ns * sizeof(double), g->st));
-  CK(cudaMemsetAsync(g->uib, 0, 3 * ns * sizeof(double), g->st));
-  CK(cudaMemsetAsync(g->p, 0, ns * sizeof(double), g->st));
-  CK(cudaMemsetAsync(g->pn, 0, ns * sizeof(double), g->st));
-  CK(cudaMemsetAsync(g->phi, 0, ns * sizeof(double), g->st));
-  CK(cudaMemsetAsync(g->tc, 0, sizeof(double), g->st));
-  CK(cudaMemsetAsync(g->tn, 0, sizeof(double), g->st));
-  if (g->H.M) {
-    CK(cudaMemsetAsync(g->Gf, 0, 3 * g->H.M * sizeof(double), g->st));
-    CK(cudaMemsetAsync(g->BF, 0, 3 * g->H.M * sizeof(double), g->st));
-  }
-  g->step = 0;
-  g->time = 0.0;
+template <typename T>
+ib_status upload(Engine& E, T** p, const std::vector<T>& v) {
+  TRY(dalloc(E, p, int64_t(v.size())));
+  if (!v.empty()) CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, E.st));
   return IB_OK;
 }
 
-struct Tols {
-  double mom, p, corr, ib, inner;
-  int max_iter;
-};
-
-Tols tolerances(const ib_grid* g) {
-  const bool mixed = g->d.precision == IB_MIXED;
-  Tols t;
-  t.mom = g->d.rtol_mom > 0 ? g->d.rtol_mom : (mixed ? 1e-10 : 1e-13);
-  t.p = g->d.rtol_p > 0 ? g->d.rtol_p : (mixed ? 1e-10 : 1e-13);
-  t.corr = g->d.rtol_corr > 0 ? g->d.rtol_corr : (mixed ? 1e-10 : 1e-13);
-  t.ib = g->d.rtol_ib > 0 ? g->d.rtol_ib : 1e-13;
-  t.inner = 1e-4;
-  t.max_iter = g->d.max_iter > 0 ? g->d.max_iter : 20000;
-  return t;
+void engine_free(Engine& E) {
+  if (E.st) cudaStreamSynchronize(E.st);
+  for (int k = 0; k < 2; ++k)
+    if (E.gexec[k]) { cudaGraphExecDestroy(E.gexec[k]); E.gexec[k] = nullptr; }
+  for (void* p : E.allocs) raw_free(E.freef, E.actx, p);
+  E.allocs.clear();
+  E.bytes = 0;
+  E.prof.release();
+  for (cudaStream_t s : E.cc.side) cudaStreamDestroy(s);
+  E.cc.side.clear();
+  if (E.cap_st) { cudaStreamDestroy(E.cap_st); E.cap_st = nullptr; }
+  if (E.ks_host) { cudaFreeHost(E.ks_host); E.ks_host = nullptr; }
+  if (E.os_host) { cudaFreeHost(E.os_host); E.os_host = nullptr; }
+  if (E.recs_host) { cudaFreeHost(E.recs_host); E.recs_host = nullptr; }
+  if (E.ok_host) { cudaFreeHost(E.ok_host); E.ok_host = nullptr; }
 }
 
-// One linear solve, FP64 or FP32-inside-FP64 defect correction.
-SolveStats solve(ib_grid* g, int op, bool bicg, int nc, uint16_t dmask, const double* coef64, const double* dinv64,
-                 const float* coef32, const float* dinv32, const double* b, double* x, double rtol, int max_iter,
-                 int* outer_out) {
-  const DevGrid& dg = g->g;
-  const int pbase = op == OP_POISSON ? 0 : op == OP_MASS ? 3 : 6;
-  Prof* pf = g->prof.on ? &g->prof : nullptr;
-  OpDesc<double> A64{op, coef64, dmask, dinv64, pf, pbase};
-  if (g->d.precision != IB_MIXED) {
-    *outer_out = 1;
-    return bicg ? fe_bicgstab<double>(dg, A64, nc, b, x, g->w64, g->ks, g->ks_host, g->rb, rtol, max_iter, g->st)
-                : fe_cg<double>(dg, A64, nc, b, x, g->w64, g->ks, g->ks_host, g->rb, rtol, max_iter, g->st);
+// Concatenate the members' host grids, upload, and build the constant
+// preconditioners and the IB force matrices.
+ib_status engine_build(Engine& E) {
+  const int n = E.ninst;
+  E.mixed = E.D[0].precision == IB_MIXED;
+  E.tol = tolerances(E.D[0]);
+  E.brick0.assign(n + 1, 0);
+  E.slot0.assign(n + 1, 0);
+  E.ns_i.assign(n, 0);
+  E.row0.assign(n + 1, 0);
+  E.canon0.assign(n + 1, 0);
+  int64_t nif = 0, nkid = 0, nport = 0;
+  for (int i = 0; i < n; ++i) {
+    const HostGrid& H = *E.H[i];
+    E.brick0[i + 1] = E.brick0[i] + H.nbricks;
+    E.slot0[i + 1] = E.brick0[i + 1] * BV;
+    E.ns_i[i] = H.nbricks * BV;
+    E.row0[i + 1] = E.row0[i] + ((H.M + 255) / 256) * 256;
+    E.canon0[i + 1] = E.canon0[i] + int64_t(H.canon_slot.size());
   }
-  OpDesc<float> A32{op, coef32, dmask, dinv32, pf, pbase};
-  const int64_t n = int64_t(nc) * dg.nslots;
-  SolveStats tot;
-  const int max_outer = 30;
-  int outer = 0;
-  double ref[3] = {0.0, 0.0, 0.0};   // max(||b||^2, ||r0||^2) per component
-  for (; outer < max_outer; ++outer) {
-    fe_residual64(dg, A64, nc, b, x, g->y64, g->r64, g->rb, g->host_rrbb, g->st);
-    double rel = 0.0;
-    for (int c = 0; c < nc; ++c) {
-      double rr = g->host_rrbb[2 * c], bb = g->host_rrbb[2 * c + 1];
-      if (outer == 0) ref[c] = std::max(bb, rr);
-      rel = std::max(rel, ref[c] > 0 ? std::sqrt(rr / ref[c]) : 0.0);
+  E.nbricks = E.brick0[n];
+  E.ns = E.slot0[n];
+  E.Mtot = E.row0[n];
+  const int64_t ns = E.ns, Mt = E.Mtot;
+  if (E.ns > (int64_t(1) << 31) - 1) { E.err = "too many node slots for 32-bit indices"; return IB_EINVAL; }
+
+  // ---- concatenated topology
+  std::vector<int32_t> blev, binst, bseg(n + 1), bnbr, ifc, iff, ifo(1, 0), ifk, ifos, hg, hp1, hp2, canon, ins, inp;
+  std::vector<uint16_t> meta;
+  std::vector<double> hl(size_t(n) * 12, 0.0), pdt(n), pnu(n), insh;
+  std::vector<PortDev> ports;
+  for (int i = 0; i < n; ++i) {
+    const HostGrid& H = *E.H[i];
+    const ib_grid_desc& d = E.D[i];
+    const int32_t B0 = int32_t(E.brick0[i]);
+    const int64_t S0 = E.slot0[i];
+    bseg[i] = B0;
+    for (int32_t b = 0; b < H.nbricks; ++b) {
+      blev.push_back(H.brick_level[b]);
+      binst.push_back(i);
+      for (int k = 0; k < 27; ++k) {
+        int32_t v = H.brick_nbr[27 * int64_t(b) + k];
+        bnbr.push_back(v >= 0 ? v + B0 : -1);
+      }
     }
-    tot.relres = rel;
-    if (!std::isfinite(rel)) { tot.status = 5; break; }
-    if (rel <= rtol) break;
-    fe_cast_d2f(n, g->r64, g->r32, g->st);
-    fe_zero<float>(n, g->e32, g->st);
-    const double rin = std::max(tolerances(g).inner, rtol);
-    SolveStats in = bicg ? fe_bicgstab<float>(dg, A32, nc, g->r32, g->e32, g->w32, g->ks, g->ks_host, g->rb, rin,
-                                              max_iter, g->st)
-                         : fe_cg<float>(dg, A32, nc, g->r32, g->e32, g->w32, g->ks, g->ks_host, g->rb, rin, max_iter,
-                                        g->st);
-    for (int c = 0; c < 3; ++c) tot.iters[c] += in.iters[c];
-    if (in.status == 5) { tot.status = 5; break; }
-    fe_add_f2d(n, g->e32, x, g->st);
+    meta.insert(meta.end(), H.meta.begin(), H.meta.end());
+    for (int l = 0; l <= H.L; ++l)
+      for (int a = 0; a < 3; ++a) hl[(i * 4 + l) * 3 + a] = H.levels[l].h[a];
+    pdt[i] = d.dt;
+    pnu[i] = d.nu;
+    const int32_t E0 = int32_t(nif);
+    for (size_t e = 0; e < H.if_coarse.size(); ++e) {
+      ifc.push_back(int32_t(H.if_coarse[e] + S0));
+      iff.push_back(int32_t(H.if_fine[e] + S0));
+      ifo.push_back(int32_t(nkid + H.if_child_off[e + 1]));
+    }
+    for (int32_t k : H.if_child) ifk.push_back(int32_t(k + S0));
+    for (int32_t v : H.if_of_slot) ifos.push_back(v >= 0 ? v + E0 : -1);
+    nif += int64_t(H.if_coarse.size());
+    nkid += int64_t(H.if_child.size());
+    for (size_t h = 0; h < H.hang_slot.size(); ++h) {
+      hg.push_back(int32_t(H.hang_slot[h] + S0));
+      hp1.push_back(int32_t(H.hang_p1[h] + S0));
+      hp2.push_back(int32_t(H.hang_p2[h] + S0));
+    }
+    for (int32_t s : H.canon_slot) canon.push_back(int32_t(s + S0));
+    for (size_t k = 0; k < H.inlet_slot.size(); ++k) {
+      ins.push_back(int32_t(H.inlet_slot[k] + S0));
+      inp.push_back(int32_t(H.inlet_port[k] + nport));
+      insh.push_back(H.inlet_shape[k]);
+    }
+    for (int q = 0; q < d.n_ports; ++q) {
+      const ib_port& P = d.ports[q];
+      PortDev pd{};
+      pd.axis = P.axis;
+      pd.nh = std::min(P.n_harm, 8);
+      pd.inst = i;
+      pd.a0 = P.a0;
+      pd.period = P.period > 0 ? P.period : 1.0;
+      for (int k = 0; k < 8; ++k) { pd.a[k] = P.a[k]; pd.b[k] = P.b[k]; }
+      ports.push_back(pd);
+    }
+    nport += d.n_ports;
   }
-  if (outer >= max_outer) tot.status = 4;
-  *outer_out = outer;
-  return tot;
+  bseg[n] = int32_t(E.nbricks);
+  E.n_inlet = int64_t(ins.size());
+  E.n_valid = 0;
+  for (uint16_t m : meta)
+    if (m & M_VALID) E.n_valid++;
+
+  DevGrid& g = E.g;
+  g = DevGrid();
+  g.nbricks = int32_t(E.nbricks);
+  g.nslots = ns;
+  g.ninst = n;
+  int32_t *d_blev, *d_binst, *d_bseg, *d_bnbr, *d_ifc, *d_iff, *d_ifo, *d_ifk, *d_ifos, *d_hg, *d_hp1, *d_hp2;
+  uint16_t* d_meta;
+  double *d_hl, *d_pnu;
+  TRY(upload(E, &d_blev, blev));
+  TRY(upload(E, &d_binst, binst));
+  TRY(upload(E, &d_bseg, bseg));
+  TRY(upload(E, &d_bnbr, bnbr));
+  TRY(upload(E, &d_meta, meta));
+  TRY(upload(E, &d_hl, hl));
+  TRY(upload(E, &E.pdt, pdt));
+  TRY(upload(E, &d_pnu, pnu));
+  TRY(upload(E, &d_ifc, ifc));
+  TRY(upload(E, &d_iff, iff));
+  TRY(upload(E, &d_ifo, ifo));
+  TRY(upload(E, &d_ifk, ifk));
+  TRY(upload(E, &d_ifos, ifos));
+  TRY(upload(E, &d_hg, hg));
+  TRY(upload(E, &d_hp1, hp1));
+  TRY(upload(E, &d_hp2, hp2));
+  g.blev = d_blev; g.binst = d_binst; g.bseg = d_bseg; g.bnbr = d_bnbr; g.meta = d_meta;
+  g.hl = d_hl; g.pdt = E.pdt; g.pnu = d_pnu;
+  g.n_if = int32_t(ifc.size());
+  g.if_c = d_ifc; g.if_f = d_iff; g.if_off = d_ifo; g.if_kid = d_ifk; g.if_of_slot = d_ifos;
+  g.n_hang = int32_t(hg.size());
+  g.hg = d_hg; g.hp1 = d_hp1; g.hp2 = d_hp2;
+  TRY(upload(E, &E.canon, canon));
+  TRY(upload(E, &E.in_slot, ins));
+  TRY(upload(E, &E.in_port, inp));
+  TRY(upload(E, &E.in_shape, insh));
+  TRY(upload(E, &E.ports, ports));
+  TRY(dalloc(E, &E.tc, n, true));
+  TRY(dalloc(E, &E.tn, n, true));
+  TRY(dalloc(E, &E.ok, n, true));
+
+  // ---- fields and work
+  TRY(dalloc(E, &E.ubuf[0], 3 * ns, true));
+  TRY(dalloc(E, &E.ubuf[1], 3 * ns, true));
+  TRY(dalloc(E, &E.pbuf[0], ns, true));
+  TRY(dalloc(E, &E.pbuf[1], ns, true));
+  E.u = E.ubuf[0]; E.un = E.ubuf[1]; E.p = E.pbuf[0]; E.pn = E.pbuf[1];
+  TRY(dalloc(E, &E.phi, ns, true));
+  TRY(dalloc(E, &E.ut, 3 * ns, true));
+  TRY(dalloc(E, &E.uib, 3 * ns, true));
+  TRY(dalloc(E, &E.rhs3, 3 * ns, true));
+  TRY(dalloc(E, &E.y64, 3 * ns, true));
+  TRY(dalloc(E, &E.r64, 3 * ns, true));
+  TRY(dalloc(E, &E.w64, E.mixed ? 1 : 8 * 3 * ns, true));
+  TRY(dalloc(E, &E.coef64, 15 * ns, true));
+  TRY(dalloc(E, &E.diag64, ns, true));
+  TRY(dalloc(E, &E.dK64, ns, true));
+  TRY(dalloc(E, &E.dM64, ns, true));
+  TRY(dalloc(E, &E.dA64, ns, true));
+  if (E.mixed) {
+    TRY(dalloc(E, &E.coef32, 15 * ns, true));
+    TRY(dalloc(E, &E.diag32, ns, true));
+    TRY(dalloc(E, &E.dK32, ns, true));
+    TRY(dalloc(E, &E.dM32, ns, true));
+    TRY(dalloc(E, &E.dA32, ns, true));
+    TRY(dalloc(E, &E.r32, 3 * ns, true));
+    TRY(dalloc(E, &E.e32, 3 * ns, true));
+    TRY(dalloc(E, &E.w32, 8 * 3 * ns, true));
+  }
+
+  // ---- IB, rows padded per instance to whole 256-row blocks
+  std::vector<double> X(3 * Mt, 0.0), dSv(Mt, 1.0), UB(3 * Mt, 0.0), pscale(Mt, 0.0), iorg(3 * n), ihf(3 * n),
+      icoef(n);
+  std::vector<int32_t> org(3 * Mt, 0), slot(64 * Mt, -1), pinst(Mt, 0), rowptr(Mt + 1, 0), col, segt(n + 1),
+      segw(n + 1), sps, spo(1, 0), spe;
+  std::vector<uint64_t> fb(Mt, 0);
+  for (int i = 0; i < n; ++i) {
+    const HostGrid& H = *E.H[i];
+    const int64_t R0 = E.row0[i], S0 = E.slot0[i];
+    const double h3 = H.hf[0] * H.hf[1] * H.hf[2];
+    const double sc = E.D[i].dt / (E.D[i].rho * h3);
+    segt[i] = int32_t(R0 / 256);
+    segw[i] = int32_t(R0 / 8);
+    for (int a = 0; a < 3; ++a) { iorg[3 * i + a] = H.origin[a]; ihf[3 * i + a] = H.hf[a]; }
+    icoef[i] = sc;
+    for (int64_t r = R0; r < E.row0[i + 1]; ++r) { pinst[r] = i; pscale[r] = sc; }
+    for (int64_t k = 0; k < H.M; ++k) {
+      const int64_t r = R0 + k;
+      for (int a = 0; a < 3; ++a) {
+        X[3 * r + a] = H.X[3 * k + a];
+        UB[3 * r + a] = H.UB[3 * k + a];
+        org[3 * r + a] = H.ib_origin[3 * k + a];
+      }
+      dSv[r] = H.dS[k];
+      fb[r] = H.ib_free[k];
+      for (int a = 0; a < 64; ++a) {
+        int32_t s = H.ib_slot[64 * k + a];
+        slot[64 * r + a] = s >= 0 ? int32_t(s + S0) : -1;
+      }
+    }
+  }
+  segt[n] = int32_t(Mt / 256);
+  segw[n] = int32_t(Mt / 8);
+  for (int i = 0; i < n; ++i) {   // A_F pattern and spreading lists with global rows and slots
+    const HostGrid& H = *E.H[i];
+    const int64_t R0 = E.row0[i];
+    for (int64_t k = 0; k < H.M; ++k) {
+      for (int32_t e = H.af_rowptr[k]; e < H.af_rowptr[k + 1]; ++e) col.push_back(int32_t(H.af_col[e] + R0));
+      rowptr[R0 + k + 1] = int32_t(col.size());
+    }
+    for (int64_t r = R0 + H.M; r < E.row0[i + 1]; ++r) rowptr[r + 1] = int32_t(col.size());
+    for (size_t q = 0; q < H.sp_slot.size(); ++q) {
+      sps.push_back(int32_t(H.sp_slot[q] + E.slot0[i]));
+      for (int32_t e = H.sp_off[q]; e < H.sp_off[q + 1]; ++e) {
+        const int32_t ent = H.sp_ent[e];
+        spe.push_back(int32_t(((ent >> 6) + R0) * 64 + (ent & 63)));
+      }
+      spo.push_back(int32_t(spe.size()));
+    }
+  }
+  IBDev& ib = E.ib;
+  ib = IBDev();
+  ib.M = Mt;
+  ib.ninst = n;
+  int32_t *d_org, *d_slot, *d_rp, *d_col, *d_sps, *d_spo, *d_spe, *d_pinst, *d_segt, *d_segw;
+  uint64_t* d_fb;
+  double *d_pscale, *d_iorg, *d_ihf, *d_icoef;
+  TRY(upload(E, &E.X, X));
+  TRY(upload(E, &E.dS, dSv));
+  TRY(upload(E, &E.UB, UB));
+  TRY(upload(E, &d_org, org));
+  TRY(upload(E, &d_slot, slot));
+  TRY(upload(E, &d_fb, fb));
+  TRY(upload(E, &d_rp, rowptr));
+  TRY(upload(E, &d_col, col));
+  TRY(upload(E, &d_sps, sps));
+  TRY(upload(E, &d_spo, spo));
+  TRY(upload(E, &d_spe, spe));
+  TRY(upload(E, &d_pinst, pinst));
+  TRY(upload(E, &d_segt, segt));
+  TRY(upload(E, &d_segw, segw));
+  TRY(upload(E, &d_pscale, pscale));
+  TRY(upload(E, &d_iorg, iorg));
+  TRY(upload(E, &d_ihf, ihf));
+  TRY(upload(E, &d_icoef, icoef));
+  ib.X = E.X; ib.org = d_org; ib.slot = d_slot; ib.freeb = d_fb; ib.rowptr = d_rp; ib.col = d_col;
+  ib.sp_slot = d_sps; ib.sp_off = d_spo; ib.sp_ent = d_spe; ib.n_sp = int64_t(sps.size());
+  ib.pinst = d_pinst; ib.seg_t = d_segt; ib.seg_w = d_segw; ib.pscale = d_pscale;
+  ib.iorigin = d_iorg; ib.ihf = d_ihf; ib.icoef = d_icoef; ib.binst = d_binst;
+  TRY(dalloc(E, &ib.W, 64 * Mt, true));
+  TRY(dalloc(E, &ib.val, int64_t(col.size()), true));
+  TRY(dalloc(E, &ib.dinv, Mt, true));
+  TRY(dalloc(E, &E.BF, 3 * Mt, true));
+  TRY(dalloc(E, &E.Gf, 3 * Mt, true));
+  TRY(dalloc(E, &E.ibw, 4 * 3 * Mt, true));
+
+  // ---- reductions, solver state, streams
+  const int64_t maxblk = std::max<int64_t>(E.nbricks, Mt / 8 + 1);
+  TRY(dalloc(E, &E.rb.partials, maxblk * 16 + int64_t(n) * 16 + 64, true));
+  TRY(dalloc(E, &E.rb.counter, 1, true));
+  TRY(dalloc(E, &E.ks, 3 * n, true));
+  TRY(dalloc(E, &E.os, n, true));
+  TRY(dalloc(E, &E.recs, 4 * n, true));
+  CK(cudaMallocHost(&E.ks_host, 3 * n * sizeof(KState)));
+  CK(cudaMallocHost(&E.os_host, n * sizeof(OState)));
+  CK(cudaMallocHost(&E.recs_host, 4 * n * sizeof(SolveRec)));
+  CK(cudaMallocHost(&E.ok_host, n * sizeof(int32_t)));
+  for (int k = 0; k < 4; ++k) {
+    cudaStream_t s2;
+    CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    E.cc.side.push_back(s2);
+  }
+  CK(cudaStreamCreateWithFlags(&E.cap_st, cudaStreamNonBlocking));
+
+  // ---- constant preconditioners, IB weights and force matrix
+  const DevGrid& dg = E.g;
+  fe_jacobi<double>(dg, OP_POISSON, nullptr, D_PDIR, E.diag64, E.dK64, E.st);
+  fe_jacobi<double>(dg, OP_MASS, nullptr, D_VDIR, E.diag64, E.dM64, E.st);
+  if (E.mixed) {
+    fe_jacobi<float>(dg, OP_POISSON, nullptr, D_PDIR, E.diag32, E.dK32, E.st);
+    fe_jacobi<float>(dg, OP_MASS, nullptr, D_VDIR, E.diag32, E.dM32, E.st);
+  }
+  ib_weights(E.ib, E.st);
+  ib_assemble(E.ib, E.st);
+  E.step.assign(n, 0);
+  E.time.assign(n, 0.0);
+  E.last.assign(n, ib_info{});
+  E.status.assign(n, 0);
+  cudaError_t e = cudaStreamSynchronize(E.st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) { E.err = std::string("CUDA: ") + cudaGetErrorString(e); return IB_ECUDA; }
+  return IB_OK;
 }
 
-ib_status step_once(ib_grid* g) {
-  const DevGrid& dg = g->g;
-  const int64_t ns = dg.nslots;
-  const double dt = g->d.dt, nu = g->d.nu, rho = g->d.rho;
-  const bool mixed = g->d.precision == IB_MIXED;
-  const Tols tl = tolerances(g);
-  cudaStream_t st = g->st;
-  ib_info& I = g->last;
-  int status = 0;
+SolveArgs solve_args(Engine& E, int op, bool bicg, int nc, uint16_t dmask, const double* coef64,
+                     const double* dinv64, const float* coef32, const float* dinv32, const double* b, double* x,
+                     double rtol, int rec) {
+  SolveArgs a;
+  a.g = &E.g;
+  a.op = op;
+  a.nc = nc;
+  a.dmask = dmask;
+  a.bicg = bicg;
+  a.mixed = E.mixed;
+  a.coef64 = coef64;
+  a.dinv64 = dinv64;
+  a.coef32 = coef32;
+  a.dinv32 = dinv32;
+  a.b = b;
+  a.x = x;
+  a.rtol = rtol;
+  a.rtol_inner = std::max(E.tol.inner, rtol);
+  a.max_iter = E.tol.max_iter;
+  a.w64 = E.w64;
+  a.w32 = E.w32;
+  a.y64 = E.y64;
+  a.r64 = E.r64;
+  a.r32 = E.r32;
+  a.e32 = E.e32;
+  a.ks = E.ks;
+  a.os = E.os;
+  a.rec = E.recs + rec;
+  a.rb = E.rb;
+  a.prof = E.prof.on ? &E.prof : nullptr;
+  a.pbase = op == OP_POISSON ? 0 : op == OP_MASS ? 3 : 6;
+  a.ks_host = E.ks_host;
+  a.os_host = E.os_host;
+  return a;
+}
 
-  fe_time_advance(g->tc, g->tn, dt, 0, st);
+// Enqueue one step of every instance (reading u, p; writing un, pn) on st.
+cudaError_t enqueue_step(Engine& E, double* u, double* un, double* p, double* pn, cudaStream_t st) {
+  const DevGrid& dg = E.g;
+  const int64_t ns = dg.nslots;
+  const Tols& tl = E.tol;
+  CaptureCtx* cc = &E.cc;
+  cudaError_t e;
+
+  rec_clear(E.recs, 4 * E.ninst, st);
+  fe_time_advance(E.tc, E.tn, E.pdt, E.ninst, 0, nullptr, st);
   // ---- Step 1: tentative velocity (Eq. 9)
-  fe_momentum_coef(dg, g->u, dt, nu, g->coef64, mixed ? g->coef32 : nullptr, st);
-  fe_jacobi<double>(dg, OP_COEF, g->coef64, D_VDIR, g->diag64, g->dA64, st);
-  if (mixed) fe_jacobi<float>(dg, OP_COEF, g->coef32, D_VDIR, g->diag32, g->dA32, st);
-  fe_rhs_mass_grad(dg, g->u, g->p, dt, g->rhs3, st);
-  fe_sync<double>(dg, 3, g->rhs3, D_VDIR, st);
-  fe_copy_d(3 * ns, g->u, g->ut, st);
-  fe_set_inlet(int64_t(g->H.inlet_slot.size()), g->in_slot, g->in_port, g->in_shape, g->ports, g->tn, ns, g->ut, st);
-  fe_expand<double>(dg, 3, g->ut, st);
-  int outer = 0;
-  SolveStats sm = solve(g, OP_COEF, true, 3, D_VDIR, g->coef64, g->dA64, g->coef32, g->dA32, g->rhs3, g->ut, tl.mom,
-                        tl.max_iter, &outer);
-  for (int c = 0; c < 3; ++c) I.iters_mom[c] = sm.iters[c];
-  I.outer_mom = outer;
-  I.res_mom = sm.relres;
-  if (sm.status) status = sm.status;
+  fe_momentum_coef(dg, u, E.coef64, E.mixed ? E.coef32 : nullptr, st);
+  fe_jacobi<double>(dg, OP_COEF, E.coef64, D_VDIR, E.diag64, E.dA64, st);
+  if (E.mixed) fe_jacobi<float>(dg, OP_COEF, E.coef32, D_VDIR, E.diag32, E.dA32, st);
+  fe_rhs_mass_grad(dg, u, p, E.rhs3, st);
+  fe_sync<double>(dg, 3, E.rhs3, D_VDIR, st);
+  fe_copy_d(3 * ns, u, E.ut, st);
+  fe_set_inlet(E.n_inlet, E.in_slot, E.in_port, E.in_shape, E.ports, E.tn, ns, E.ut, st);
+  fe_expand<double>(dg, 3, E.ut, st);
+  e = solve_enqueue(solve_args(E, OP_COEF, true, 3, D_VDIR, E.coef64, E.dA64, E.coef32, E.dA32, E.rhs3, E.ut,
+                               tl.mom, 0), st, cc);
+  if (e != cudaSuccess) return e;
 
   // ---- Steps 2-4: BCE-IB force and correction (Eq. 14, 19-23)
-  fe_copy_d(3 * ns, g->ut, g->uib, st);
-  if (g->H.M) {
-    ib_gather(g->ib, g->ut, ns, g->UB, g->BF, st);
-    SolveStats si = ib_solve(g->ib, g->BF, g->Gf, g->ibw, g->ks, g->ks_host, g->rb, tl.ib, tl.max_iter, st);
-    I.iters_ib = std::max(si.iters[0], std::max(si.iters[1], si.iters[2]));
-    I.res_ib = si.relres;
-    if (si.status && !status) status = si.status;
-    const double h3 = g->H.hf[0] * g->H.hf[1] * g->H.hf[2];
-    ib_spread(g->ib, g->Gf, dt / (rho * h3), g->uib, ns, st);
+  fe_copy_d(3 * ns, E.ut, E.uib, st);
+  if (E.Mtot) {
+    ib_gather(E.ib, E.ut, ns, E.UB, E.BF, st);
+    e = ib_solve(E.ib, E.BF, E.Gf, E.ibw, E.ks, E.ks_host, E.rb, tl.ib, tl.max_iter, E.recs + 1, st, cc);
+    if (e != cudaSuccess) return e;
+    ib_spread(E.ib, E.Gf, E.uib, ns, st);
   }
 
   // ---- Step 5: pressure increment (Eq. 12)
-  double* rhs1 = g->rhs3;   // component 0 of the RHS buffer
-  fe_rhs_div(dg, g->uib, -1.0 / dt, rhs1, st);
+  double* rhs1 = E.rhs3;   // component 0 of the RHS buffer
+  fe_rhs_div(dg, E.uib, rhs1, st);
   fe_sync<double>(dg, 1, rhs1, D_PDIR, st);
-  SolveStats sp = solve(g, OP_POISSON, false, 1, D_PDIR, nullptr, g->dK64, nullptr, g->dK32, rhs1, g->phi, tl.p,
-                        tl.max_iter, &outer);
-  I.iters_p = sp.iters[0];
-  I.outer_p = outer;
-  I.res_p = sp.relres;
-  if (sp.status && !status) status = sp.status;
+  e = solve_enqueue(solve_args(E, OP_POISSON, false, 1, D_PDIR, nullptr, E.dK64, nullptr, E.dK32, rhs1, E.phi,
+                               tl.p, 2), st, cc);
+  if (e != cudaSuccess) return e;
 
   // ---- Step 6: velocity correction and pressure update
-  fe_rhs_mass_grad(dg, g->uib, g->phi, dt, g->rhs3, st);
-  fe_sync<double>(dg, 3, g->rhs3, D_VDIR, st);
-  fe_copy_d(3 * ns, g->uib, g->un, st);
-  SolveStats sc = solve(g, OP_MASS, false, 3, D_VDIR, nullptr, g->dM64, nullptr, g->dM32, g->rhs3, g->un, tl.corr,
-                        tl.max_iter, &outer);
-  for (int c = 0; c < 3; ++c) I.iters_corr[c] = sc.iters[c];
-  I.outer_corr = outer;
-  I.res_corr = sc.relres;
-  if (sc.status && !status) status = sc.status;
-  fe_copy_d(ns, g->p, g->pn, st);
-  fe_add_d(ns, g->phi, g->pn, st);
+  fe_rhs_mass_grad(dg, E.uib, E.phi, E.rhs3, st);
+  fe_sync<double>(dg, 3, E.rhs3, D_VDIR, st);
+  fe_copy_d(3 * ns, E.uib, un, st);
+  e = solve_enqueue(solve_args(E, OP_MASS, false, 3, D_VDIR, nullptr, E.dM64, nullptr, E.dM32, E.rhs3, un,
+                               tl.corr, 3), st, cc);
+  if (e != cudaSuccess) return e;
+  fe_copy_d(ns, p, pn, st);
+  fe_add_d(ns, E.phi, pn, st);
+  return cudaMemcpyAsync(E.recs_host, E.recs, 4 * E.ninst * sizeof(SolveRec), cudaMemcpyDeviceToHost, st);
+}
 
+// One step of every instance.  Returns the worst status; per-instance status
+// in E.status (an instance whose solves failed keeps its previous state).
+ib_status engine_step(Engine& E) {
+  cudaStream_t st = E.st;
+  const int par = (E.u == E.ubuf[0]) ? 0 : 1;
+  if (E.use_graph) {
+    if (!E.gexec[par]) {
+      cudaGraph_t graph = nullptr;
+      cudaStream_t cs = E.cap_st;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      E.cc.capturing = true;
+      E.cc.depth = 0;
+      cudaError_t e = enqueue_step(E, E.u, E.un, E.p, E.pn, cs);
+      E.cc.capturing = false;
+      cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        E.err = std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
+        return IB_ECUDA;
+      }
+      e = cudaGraphInstantiate(&E.gexec[par], graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        E.gexec[par] = nullptr;
+        E.err = std::string("graph instantiation failed: ") + cudaGetErrorString(e);
+        return IB_ECUDA;
+      }
+    }
+    CK(cudaGraphLaunch(E.gexec[par], st));
+  } else {
+    E.cc.capturing = false;
+    cudaError_t e = enqueue_step(E, E.u, E.un, E.p, E.pn, st);
+    if (e != cudaSuccess) {
+      E.err = std::string("CUDA: ") + cudaGetErrorString(e);
+      return IB_ECUDA;
+    }
+  }
   CK(cudaStreamSynchronize(st));
   CK(cudaGetLastError());
-  if (g->prof.on) g->prof.collect();
-  if (status) {
-    g->err = status == 5 ? "Krylov breakdown in a step solve" : "a step solve did not converge";
-    return status == 5 ? IB_EBREAKDOWN : IB_ENOCONV;
+  if (E.prof.on) E.prof.collect();
+  int worst = 0;
+  bool any_fail = false;
+  for (int i = 0; i < E.ninst; ++i) {
+    const SolveRec* R = E.recs_host + 4 * i;
+    ib_info& I = E.last[i];
+    int status = 0;
+    for (int k = 0; k < 4; ++k) status = std::max(status, int(R[k].status));
+    for (int c = 0; c < 3; ++c) {
+      I.iters_mom[c] = R[0].iters[c];
+      I.iters_corr[c] = R[3].iters[c];
+    }
+    I.iters_ib = std::max(R[1].iters[0], std::max(R[1].iters[1], R[1].iters[2]));
+    I.iters_p = R[2].iters[0];
+    I.outer_mom = R[0].outer;
+    I.outer_p = R[2].outer;
+    I.outer_corr = R[3].outer;
+    I.res_mom = R[0].relres;
+    I.res_ib = R[1].relres;
+    I.res_p = R[2].relres;
+    I.res_corr = R[3].relres;
+    E.status[i] = status;
+    E.ok_host[i] = status == 0;
+    if (status) {
+      any_fail = true;
+      worst = std::max(worst, status);
+      // keep the previous state of this instance: next buffers <- current
+      const int64_t s0 = E.slot0[i], cnt = E.ns_i[i];
+      for (int c = 0; c < 3; ++c)
+        CK(cudaMemcpyAsync(E.un + c * E.ns + s0, E.u + c * E.ns + s0, cnt * sizeof(double),
+                           cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(E.pn + s0, E.p + s0, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      E.step[i] += 1;
+      E.time[i] += E.D[i].dt;
+    }
   }
-  std::swap(g->u, g->un);
-  std::swap(g->p, g->pn);
-  fe_time_advance(g->tc, g->tn, dt, 1, st);
-  g->step += 1;
-  g->time += dt;
+  if (any_fail) CK(cudaMemcpyAsync(E.ok, E.ok_host, E.ninst * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  std::swap(E.u, E.un);
+  std::swap(E.p, E.pn);
+  fe_time_advance(E.tc, E.tn, E.pdt, E.ninst, 1, any_fail ? E.ok : nullptr, st);
+  if (any_fail) CK(cudaStreamSynchronize(st));
+  if (worst) {
+    E.err = worst == 5 ? "Krylov breakdown in a step solve" : "a step solve did not converge";
+    return worst == 5 ? IB_EBREAKDOWN : IB_ENOCONV;
+  }
   return IB_OK;
 }
 
-int64_t field_bytes(const ib_grid* g, int f) {
-  const int64_t N = int64_t(g->H.canon_slot.size()), M = g->H.M;
-  const int64_t nc = g->H.n[0] * g->H.n[1] * g->H.n[2];
+int64_t field_bytes(const HostGrid& H, int f) {
+  const int64_t N = int64_t(H.canon_slot.size()), M = H.M;
+  const int64_t nc = H.n[0] * H.n[1] * H.n[2];
   switch (f) {
     case IB_FIELD_U: case IB_FIELD_U_TENT: case IB_FIELD_U_IB: return N * 3 * 8;
     case IB_FIELD_P: case IB_FIELD_PHI: return N * 8;
@@ -412,175 +689,84 @@ int64_t field_bytes(const ib_grid* g, int f) {
   }
 }
 
-}  // namespace
-
-extern "C" {
-
-ib_status ib_grid_create(const ib_grid_desc* d, ib_grid** out) {
-  if (!d || !out) return IB_EINVAL;
-  *out = nullptr;
-  auto bad = [](const char*) { return IB_EINVAL; };
-  for (int a = 0; a < 3; ++a)
-    if (d->n[a] <= 0 || !(d->extent[a] > 0) || !std::isfinite(d->origin[a])) return bad("grid");
-  if (d->max_level < 0 || d->max_level > IB_MAX_LEVEL) return bad("max_level");
-  if (d->max_level > 0 && d->refine_band < 1) return bad("refine_band");
-  if (!(d->nu > 0) || !(d->rho > 0) || !(d->dt > 0)) return bad("nu/rho/dt");
-  if (d->precision != IB_FP64 && d->precision != IB_MIXED) return bad("precision");
-  if (d->n_ports < 1 || d->n_ports > IB_MAX_PORTS) return bad("ports");
-  bool outlet = false;
-  for (int p = 0; p < d->n_ports; ++p) {
-    const ib_port& P = d->ports[p];
-    if (P.axis < 0 || P.axis > 2 || (P.side != 0 && P.side != 1) || !(P.radius > 0)) return bad("port");
-    if (P.kind != IB_INLET_VELOCITY && P.kind != IB_OUTLET_ZERO_P) return bad("port kind");
-    if (P.n_harm < 0 || P.n_harm > IB_MAX_HARMONICS) return bad("harmonics");
-    if (P.kind == IB_OUTLET_ZERO_P) outlet = true;
-  }
-  if (!outlet) return bad("no outlet");
-  int64_t nf = int64_t(d->n[0]) * d->n[1] * d->n[2] << (3 * d->max_level);
-  if (nf > (int64_t(1) << 40)) return bad("too large");
-  ib_grid* g = new (std::nothrow) ib_grid();
-  if (!g) return IB_ENOMEM;
-  g->d = *d;
-  g->st = static_cast<cudaStream_t>(d->stream);
-  cudaError_t e = fe_init_tables();
-  if (e != cudaSuccess) {
-    delete g;
-    return IB_ECUDA;
-  }
-  *out = g;
-  return IB_OK;
-}
-
-ib_status ib_set_boundary(ib_grid* g, int64_t M, const double* X, const double* dS, const double* UB,
-                          const uint8_t* inside) {
-  if (!g) return IB_EINVAL;
-  if (M < 0 || (M > 0 && (!X || !dS))) { g->err = "bad point arrays"; return IB_EINVAL; }
-  free_all(g);
-  ib_status s = build_host_grid(g->d, M, X, dS, UB, inside, g->H, g->err);
-  if (s != IB_OK) return s;
-  s = allocate_and_upload(g);
-  if (s != IB_OK) { free_all(g); return s; }
-  const DevGrid& dg = g->g;
-  cudaStream_t st = g->st;
-  // constant preconditioners, IB weights and force matrix
-  fe_jacobi<double>(dg, OP_POISSON, nullptr, D_PDIR, g->diag64, g->dK64, st);
-  fe_jacobi<double>(dg, OP_MASS, nullptr, D_VDIR, g->diag64, g->dM64, st);
-  if (g->d.precision == IB_MIXED) {
-    fe_jacobi<float>(dg, OP_POISSON, nullptr, D_PDIR, g->diag32, g->dK32, st);
-    fe_jacobi<float>(dg, OP_MASS, nullptr, D_VDIR, g->diag32, g->dM32, st);
-  }
-  ib_weights(g->ib, g->H.origin, g->H.hf, st);
-  const double h3 = g->H.hf[0] * g->H.hf[1] * g->H.hf[2];
-  ib_assemble(g->ib, g->d.dt / (g->d.rho * h3), st);
-  s = reset_state(g);
-  if (s != IB_OK) { free_all(g); return s; }
-  cudaError_t e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess) e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    g->err = std::string("CUDA: ") + cudaGetErrorString(e);
-    free_all(g);
-    return IB_ECUDA;
-  }
-  g->n_valid = 0;
-  for (uint16_t m : g->H.meta)
-    if (m & M_VALID) g->n_valid++;
-  g->prof.on = g->d.profile != 0;
-  g->ready = true;
-  g->err.clear();
-  return IB_OK;
-}
-
-ib_status ipcs_step(ib_grid* g, int32_t nsteps) {
-  if (!g) return IB_EINVAL;
-  if (!g->ready) { g->err = "ib_set_boundary has not succeeded"; return IB_ESTATE; }
-  if (nsteps < 0) { g->err = "nsteps < 0"; return IB_EINVAL; }
-  for (int32_t k = 0; k < nsteps; ++k) {
-    ib_status s = step_once(g);
-    if (s != IB_OK) return s;
-  }
-  return IB_OK;
-}
-
-ib_status ib_fields_get(ib_grid* g, int32_t field, void* dst, size_t bytes, int32_t dst_on_device) {
-  if (!g || !dst) return IB_EINVAL;
-  if (!g->ready) { g->err = "ib_set_boundary has not succeeded"; return IB_ESTATE; }
-  int64_t need = field_bytes(g, field);
-  if (need < 0 || int64_t(bytes) != need) { g->err = "bad field id or byte count"; return IB_EINVAL; }
-  const HostGrid& H = g->H;
-  const int64_t N = int64_t(H.canon_slot.size()), M = H.M, ns = g->g.nslots;
-  cudaStream_t st = g->st;
-  const cudaMemcpyKind k_out = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  const cudaMemcpyKind h_out = dst_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
-  auto host_copy = [&](const void* src) -> ib_status {
-    CK(cudaMemcpyAsync(dst, src, bytes, h_out, st));
-    CK(cudaStreamSynchronize(st));
-    return IB_OK;
+// host-only fields of a handle
+bool host_field(const HostGrid& H, int field, std::vector<uint8_t>& buf) {
+  const int64_t M = H.M;
+  auto put = [&](const void* p, size_t n) {
+    buf.resize(n);
+    if (n) std::memcpy(buf.data(), p, n);
   };
   switch (field) {
-    case IB_FIELD_U: case IB_FIELD_U_TENT: case IB_FIELD_U_IB: case IB_FIELD_P: case IB_FIELD_PHI: {
-      const double* src = field == IB_FIELD_U ? g->u : field == IB_FIELD_U_TENT ? g->ut
-                        : field == IB_FIELD_U_IB ? g->uib : field == IB_FIELD_P ? g->p : g->phi;
-      int nc = (field == IB_FIELD_P || field == IB_FIELD_PHI) ? 1 : 3;
-      double* tmp = g->y64;   // scratch of 3 * nslots >= nc * N
-      fe_gather_canon<double>(N, g->canon, nc, ns, src, tmp, st);
-      CK(cudaMemcpyAsync(dst, tmp, bytes, k_out, st));
-      CK(cudaStreamSynchronize(st));
-      return IB_OK;
-    }
-    case IB_FIELD_B_F: {
-      CK(cudaMemcpyAsync(dst, g->BF, bytes, k_out, st));
-      CK(cudaStreamSynchronize(st));
-      return IB_OK;
-    }
-    case IB_FIELD_F_LAG: {
-      std::vector<double> G(3 * M);
-      if (M) CK(cudaMemcpyAsync(G.data(), g->Gf, bytes, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      for (int64_t i = 0; i < M; ++i)
-        for (int c = 0; c < 3; ++c) G[3 * i + c] /= H.dS[i];
-      return host_copy(G.data());
-    }
-    case IB_FIELD_NODE_Q: return host_copy(H.canon_q.data());
-    case IB_FIELD_NODE_FLAGS: return host_copy(H.canon_flags.data());
-    case IB_FIELD_ACTIVE: return host_copy(H.active.data());
-    case IB_FIELD_LEVEL: return host_copy(H.level.data());
-    case IB_FIELD_IB_ORIGIN: return host_copy(H.ib_origin.data());
-    case IB_FIELD_IB_WEIGHTS: {
-      CK(cudaMemcpyAsync(dst, g->ib.W, bytes, k_out, st));
-      CK(cudaStreamSynchronize(st));
-      return IB_OK;
-    }
+    case IB_FIELD_NODE_Q: put(H.canon_q.data(), H.canon_q.size() * 4); return true;
+    case IB_FIELD_NODE_FLAGS: put(H.canon_flags.data(), H.canon_flags.size()); return true;
+    case IB_FIELD_ACTIVE: put(H.active.data(), H.active.size()); return true;
+    case IB_FIELD_LEVEL: put(H.level.data(), H.level.size()); return true;
+    case IB_FIELD_IB_ORIGIN: put(H.ib_origin.data(), H.ib_origin.size() * 4); return true;
     case IB_FIELD_IB_FREE: {
-      std::vector<uint8_t> f(64 * M);
+      buf.assign(64 * M, 0);
       for (int64_t i = 0; i < M; ++i)
         for (int a = 0; a < 64; ++a)
-          f[64 * i + a] = (H.ib_free[i] >> a & 1) ? 1 : (H.ib_slot[64 * i + a] >= 0 ? 2 : 0);
-      return host_copy(f.data());
+          buf[64 * i + a] = (H.ib_free[i] >> a & 1) ? 1 : (H.ib_slot[64 * i + a] >= 0 ? 2 : 0);
+      return true;
     }
+    default: return false;
   }
-  g->err = "field not readable";
-  return IB_EINVAL;
 }
 
-ib_status ib_fields_set(ib_grid* g, int32_t field, const void* src, size_t bytes, int32_t src_on_device) {
-  if (!g || !src) return IB_EINVAL;
-  if (!g->ready) { g->err = "ib_set_boundary has not succeeded"; return IB_ESTATE; }
-  if (field != IB_FIELD_U && field != IB_FIELD_P) { g->err = "only U and P can be set"; return IB_EINVAL; }
-  if (int64_t(bytes) != field_bytes(g, field)) { g->err = "bad byte count"; return IB_EINVAL; }
-  const int64_t N = int64_t(g->H.canon_slot.size());
-  const int nc = field == IB_FIELD_U ? 3 : 1;
-  double* tmp = g->y64;
-  CK(cudaMemcpyAsync(tmp, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->st));
-  fe_scatter_canon(g->g, N, g->canon, nc, tmp, field == IB_FIELD_U ? g->u : g->p, g->st);
-  CK(cudaStreamSynchronize(g->st));
+ib_status engine_fields_get(Engine& E, int i, int32_t field, void* dst, size_t bytes, int32_t on_dev) {
+  const HostGrid& H = *E.H[i];
+  cudaStream_t st = E.st;
+  const cudaMemcpyKind k_out = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  std::vector<uint8_t> hb;
+  if (host_field(H, field, hb)) {
+    if (bytes) CK(cudaMemcpyAsync(dst, hb.data(), bytes, on_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return IB_OK;
+  }
+  const int64_t N = int64_t(H.canon_slot.size()), M = H.M, R0 = E.row0[i];
+  switch (field) {
+    case IB_FIELD_U: case IB_FIELD_U_TENT: case IB_FIELD_U_IB: case IB_FIELD_P: case IB_FIELD_PHI: {
+      const double* src = field == IB_FIELD_U ? E.u : field == IB_FIELD_U_TENT ? E.ut
+                        : field == IB_FIELD_U_IB ? E.uib : field == IB_FIELD_P ? E.p : E.phi;
+      const int nc = (field == IB_FIELD_P || field == IB_FIELD_PHI) ? 1 : 3;
+      double* tmp = E.y64;   // 3 * ns >= nc * N
+      fe_gather_canon<double>(N, E.canon + E.canon0[i], nc, E.ns, src, tmp, st);
+      CK(cudaMemcpyAsync(dst, tmp, bytes, k_out, st));
+      break;
+    }
+    case IB_FIELD_B_F:
+      if (bytes) CK(cudaMemcpyAsync(dst, E.BF + 3 * R0, bytes, k_out, st));
+      break;
+    case IB_FIELD_IB_WEIGHTS:
+      if (bytes) CK(cudaMemcpyAsync(dst, E.ib.W + 64 * R0, bytes, k_out, st));
+      break;
+    case IB_FIELD_F_LAG: {
+      std::vector<double> G(3 * M);
+      if (M) CK(cudaMemcpyAsync(G.data(), E.Gf + 3 * R0, bytes, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int64_t k = 0; k < M; ++k)
+        for (int c = 0; c < 3; ++c) G[3 * k + c] /= H.dS[k];
+      if (bytes) CK(cudaMemcpyAsync(dst, G.data(), bytes, on_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
+      break;
+    }
+    default: E.err = "field not readable"; return IB_EINVAL;
+  }
+  CK(cudaStreamSynchronize(st));
   return IB_OK;
 }
 
-ib_status ib_grid_info(const ib_grid* g, ib_info* out) {
-  if (!g || !out) return IB_EINVAL;
-  if (!g->ready) return IB_ESTATE;
-  const HostGrid& H = g->H;
-  ib_info I = g->last;
+ib_status engine_fields_set(Engine& E, int i, int32_t field, const void* src, size_t bytes, int32_t on_dev) {
+  const HostGrid& H = *E.H[i];
+  const int64_t N = int64_t(H.canon_slot.size());
+  const int nc = field == IB_FIELD_U ? 3 : 1;
+  double* tmp = E.y64;
+  CK(cudaMemcpyAsync(tmp, src, bytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, E.st));
+  fe_scatter_canon(E.g, N, E.canon + E.canon0[i], nc, tmp, field == IB_FIELD_U ? E.u : E.p, E.st);
+  CK(cudaStreamSynchronize(E.st));
+  return IB_OK;
+}
+
+void fill_info(const HostGrid& H, const Engine* E, int64_t dev_bytes, ib_info& I) {
   I.n_nodes = int64_t(H.canon_slot.size());
   I.n_dof = H.n_dof;
   I.n_hanging = int64_t(H.hang_slot.size());
@@ -599,15 +785,224 @@ ib_status ib_grid_info(const ib_grid* g, ib_info* out) {
   for (double v : H.dS) mdS += v;
   mdS = H.M ? mdS / double(H.M) : 0.0;
   for (int a = 0; a < 3; ++a) I.a_ratio[a] = std::sqrt(mdS) / H.hf[a];
-  I.step = g->step;
-  I.time = g->time;
-  I.device_bytes = g->dev_bytes;
-  I.n_valid_slots = g->n_valid;
-  I.kernel_launches = g_launches.load();
-  for (int k = 0; k < Prof::K; ++k) {
-    I.prof_ms[k] = g->prof.ms[k];
-    I.prof_launches[k] = g->prof.n[k];
+  int64_t nv = 0;
+  for (uint16_t m : H.meta)
+    if (m & M_VALID) nv++;
+  I.n_valid_slots = nv;
+  I.device_bytes = dev_bytes;
+  I.kernel_launches = int64_t(fe_kcount() + krylov_kcount() + ib_kcount());
+  if (E) {
+    for (int k = 0; k < Prof::K; ++k) {
+      I.prof_ms[k] = E->prof.ms[k];
+      I.prof_launches[k] = E->prof.n[k];
+    }
   }
+}
+
+ib_status validate_desc(const ib_grid_desc* d) {
+  for (int a = 0; a < 3; ++a)
+    if (d->n[a] <= 0 || !(d->extent[a] > 0) || !std::isfinite(d->origin[a])) return IB_EINVAL;
+  if (d->max_level < 0 || d->max_level > IB_MAX_LEVEL) return IB_EINVAL;
+  if (d->max_level > 0 && d->refine_band < 1) return IB_EINVAL;
+  if (!(d->nu > 0) || !(d->rho > 0) || !(d->dt > 0)) return IB_EINVAL;
+  if (d->precision != IB_FP64 && d->precision != IB_MIXED) return IB_EINVAL;
+  if (d->n_ports < 1 || d->n_ports > IB_MAX_PORTS) return IB_EINVAL;
+  bool outlet = false;
+  for (int p = 0; p < d->n_ports; ++p) {
+    const ib_port& P = d->ports[p];
+    if (P.axis < 0 || P.axis > 2 || (P.side != 0 && P.side != 1) || !(P.radius > 0)) return IB_EINVAL;
+    if (P.kind != IB_INLET_VELOCITY && P.kind != IB_OUTLET_ZERO_P) return IB_EINVAL;
+    if (P.n_harm < 0 || P.n_harm > IB_MAX_HARMONICS) return IB_EINVAL;
+    if (P.kind == IB_OUTLET_ZERO_P) outlet = true;
+  }
+  if (!outlet) return IB_EINVAL;
+  int64_t nf = (int64_t(d->n[0]) * d->n[1] * d->n[2]) << (3 * d->max_level);
+  if (nf > (int64_t(1) << 40)) return IB_EINVAL;
+  return IB_OK;
+}
+
+void snap_free(ib_grid* g) {
+  for (void* p : g->snap_allocs) raw_free(g->d.dev_free, g->d.alloc_ctx, p);
+  g->snap_allocs.clear();
+  g->snap_bytes = 0;
+  g->snap = Snapshot();
+}
+
+// allocate a deferred handle's snapshot (zero state)
+ib_status snap_alloc(ib_grid* g) {
+  snap_free(g);
+  cudaStream_t st = static_cast<cudaStream_t>(g->d.stream);
+  const int64_t ns = g->H.nbricks * BV, M = g->H.M;
+  auto al = [&](void** p, size_t bytes) -> bool {
+    const size_t b = std::max<size_t>(bytes, 8);
+    *p = raw_alloc(g->d.dev_alloc, g->d.alloc_ctx, b);
+    if (!*p) return false;
+    g->snap_allocs.push_back(*p);
+    g->snap_bytes += int64_t(b);
+    return cudaMemsetAsync(*p, 0, b, st) == cudaSuccess;
+  };
+  if (!al((void**)&g->snap.u, 3 * ns * 8) || !al((void**)&g->snap.p, ns * 8) || !al((void**)&g->snap.phi, ns * 8) ||
+      !al((void**)&g->snap.G, 3 * M * 8) || !al((void**)&g->snap.canon, g->H.canon_slot.size() * 4)) {
+    g->err = "device allocation failed";
+    return IB_ENOMEM;
+  }
+  if (!g->H.canon_slot.empty())
+    cudaMemcpyAsync(g->snap.canon, g->H.canon_slot.data(), g->H.canon_slot.size() * 4, cudaMemcpyHostToDevice, st);
+  g->snap.valid = true;
+  return cudaStreamSynchronize(st) == cudaSuccess ? IB_OK : IB_ECUDA;
+}
+
+// engine instance i <-> member snapshot (u, p, Phi, G, time, step)
+ib_status snap_transfer(Engine& E, int i, ib_grid* m, bool to_engine) {
+  const int64_t s0 = E.slot0[i], n = E.ns_i[i], R0 = E.row0[i], M = m->H.M;
+  cudaStream_t st = E.st;
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  for (int c = 0; c < 3; ++c) {
+    double* a = E.u + c * E.ns + s0;
+    double* b = m->snap.u + c * n;
+    CK(cudaMemcpyAsync(to_engine ? a : b, to_engine ? b : a, n * 8, k, st));
+  }
+  CK(cudaMemcpyAsync(to_engine ? E.p + s0 : m->snap.p, to_engine ? m->snap.p : E.p + s0, n * 8, k, st));
+  CK(cudaMemcpyAsync(to_engine ? E.phi + s0 : m->snap.phi, to_engine ? m->snap.phi : E.phi + s0, n * 8, k, st));
+  if (M) CK(cudaMemcpyAsync(to_engine ? E.Gf + 3 * R0 : m->snap.G, to_engine ? m->snap.G : E.Gf + 3 * R0, 3 * M * 8, k, st));
+  if (to_engine) {
+    E.step[i] = m->snap.step;
+    E.time[i] = m->snap.time;
+    CK(cudaMemcpyAsync(E.tc + i, &E.time[i], 8, cudaMemcpyHostToDevice, st));
+  } else {
+    m->snap.step = E.step[i];
+    m->snap.time = E.time[i];
+  }
+  CK(cudaStreamSynchronize(st));
+  return IB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ib_status ib_grid_create(const ib_grid_desc* d, ib_grid** out) {
+  if (!d || !out) return IB_EINVAL;
+  *out = nullptr;
+  if (validate_desc(d) != IB_OK) return IB_EINVAL;
+  ib_grid* g = new (std::nothrow) ib_grid();
+  if (!g) return IB_ENOMEM;
+  g->d = *d;
+  if (fe_init_tables() != cudaSuccess) {
+    delete g;
+    return IB_ECUDA;
+  }
+  *out = g;
+  return IB_OK;
+}
+
+ib_status ib_set_boundary(ib_grid* g, int64_t M, const double* X, const double* dS, const double* UB,
+                          const uint8_t* inside) {
+  if (!g) return IB_EINVAL;
+  if (g->batch) { g->err = "the handle is held by a batch"; return IB_ESTATE; }
+  if (M < 0 || (M > 0 && (!X || !dS))) { g->err = "bad point arrays"; return IB_EINVAL; }
+  if (g->eng) { engine_free(*g->eng); delete g->eng; g->eng = nullptr; }
+  snap_free(g);
+  g->ready = false;
+  ib_status s = build_host_grid(g->d, M, X, dS, UB, inside, g->H, g->err);
+  if (s != IB_OK) return s;
+  if (g->d.deferred) {
+    s = snap_alloc(g);
+    if (s != IB_OK) return s;
+    g->ready = true;
+    g->err.clear();
+    return IB_OK;
+  }
+  Engine* E = new (std::nothrow) Engine();
+  if (!E) return IB_ENOMEM;
+  E->H.push_back(&g->H);
+  E->D.push_back(g->d);
+  E->ninst = 1;
+  E->st = static_cast<cudaStream_t>(g->d.stream);
+  E->alloc = g->d.dev_alloc;
+  E->freef = g->d.dev_free;
+  E->actx = g->d.alloc_ctx;
+  s = engine_build(*E);
+  if (s != IB_OK) {
+    g->err = E->err;
+    engine_free(*E);
+    delete E;
+    return s;
+  }
+  E->prof.on = g->d.profile != 0;
+  E->use_graph = !E->prof.on;
+  g->eng = E;
+  g->ready = true;
+  g->err.clear();
+  return IB_OK;
+}
+
+ib_status ipcs_step(ib_grid* g, int32_t nsteps) {
+  if (!g) return IB_EINVAL;
+  if (!g->ready) { g->err = "ib_set_boundary has not succeeded"; return IB_ESTATE; }
+  if (!g->eng) { g->err = "a deferred handle is stepped through a batch"; return IB_ESTATE; }
+  if (nsteps < 0) { g->err = "nsteps < 0"; return IB_EINVAL; }
+  for (int32_t k = 0; k < nsteps; ++k) {
+    ib_status s = engine_step(*g->eng);
+    if (s != IB_OK) { g->err = g->eng->err; return s; }
+  }
+  return IB_OK;
+}
+
+ib_status ib_fields_get(ib_grid* g, int32_t field, void* dst, size_t bytes, int32_t dst_on_device) {
+  if (!g) return IB_EINVAL;
+  if (!g->ready) { g->err = "ib_set_boundary has not succeeded"; return IB_ESTATE; }
+  int64_t need = field_bytes(g->H, field);
+  if (need < 0 || int64_t(bytes) != need) { g->err = "bad field id or byte count"; return IB_EINVAL; }
+  if (!dst && bytes) return IB_EINVAL;
+  if (g->batch) return ib_batch_fields_get(g->batch, g->batch_index, field, dst, bytes, dst_on_device);
+  if (g->eng) {
+    ib_status s = engine_fields_get(*g->eng, 0, field, dst, bytes, dst_on_device);
+    if (s != IB_OK) g->err = g->eng->err;
+    return s;
+  }
+  // deferred handle outside a batch: host fields and the state snapshot
+  cudaStream_t st = static_cast<cudaStream_t>(g->d.stream);
+  std::vector<uint8_t> hb;
+  if (host_field(g->H, field, hb)) {
+    if (bytes) cudaMemcpyAsync(dst, hb.data(), bytes, dst_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st);
+    return cudaStreamSynchronize(st) == cudaSuccess ? IB_OK : IB_ECUDA;
+  }
+  const int64_t N = int64_t(g->H.canon_slot.size()), ns = g->H.nbricks * BV;
+  if (field == IB_FIELD_U || field == IB_FIELD_P || field == IB_FIELD_PHI) {
+    const int nc = field == IB_FIELD_U ? 3 : 1;
+    const double* src = field == IB_FIELD_U ? g->snap.u : field == IB_FIELD_P ? g->snap.p : g->snap.phi;
+    double* tmp = static_cast<double*>(raw_alloc(g->d.dev_alloc, g->d.alloc_ctx, size_t(std::max<int64_t>(nc * N, 1)) * 8));
+    if (!tmp) return IB_ENOMEM;
+    fe_gather_canon<double>(N, g->snap.canon, nc, ns, src, tmp, st);
+    cudaMemcpyAsync(dst, tmp, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    raw_free(g->d.dev_free, g->d.alloc_ctx, tmp);
+    return e == cudaSuccess ? IB_OK : IB_ECUDA;
+  }
+  g->err = "field not available for a deferred handle outside a batch";
+  return IB_EINVAL;
+}
+
+ib_status ib_fields_set(ib_grid* g, int32_t field, const void* src, size_t bytes, int32_t src_on_device) {
+  if (!g || !src) return IB_EINVAL;
+  if (!g->ready) { g->err = "ib_set_boundary has not succeeded"; return IB_ESTATE; }
+  if (field != IB_FIELD_U && field != IB_FIELD_P) { g->err = "only U and P can be set"; return IB_EINVAL; }
+  if (int64_t(bytes) != field_bytes(g->H, field)) { g->err = "bad byte count"; return IB_EINVAL; }
+  if (!g->eng) { g->err = "the state of a deferred handle is set through its batch"; return IB_ESTATE; }
+  ib_status s = engine_fields_set(*g->eng, 0, field, src, bytes, src_on_device);
+  if (s != IB_OK) g->err = g->eng->err;
+  return s;
+}
+
+ib_status ib_grid_info(const ib_grid* g, ib_info* out) {
+  if (!g || !out) return IB_EINVAL;
+  if (!g->ready) return IB_ESTATE;
+  if (g->batch) return ib_batch_info(g->batch, g->batch_index, out);
+  ib_info I = g->eng ? g->eng->last[0] : ib_info{};
+  fill_info(g->H, g->eng, g->eng ? g->eng->bytes : g->snap_bytes, I);
+  I.step = g->eng ? g->eng->step[0] : g->snap.step;
+  I.time = g->eng ? g->eng->time[0] : g->snap.time;
   *out = I;
   return IB_OK;
 }
@@ -616,8 +1011,100 @@ const char* ib_last_error(const ib_grid* g) { return g ? g->err.c_str() : "null 
 
 void ib_grid_destroy(ib_grid* g) {
   if (!g) return;
-  free_all(g);
+  if (g->batch) return;   // a batch still references it: destroy the batch first
+  if (g->eng) {
+    engine_free(*g->eng);
+    delete g->eng;
+  }
+  snap_free(g);
   delete g;
+}
+
+// ---------------------------------------------------------------- batches
+ib_status ib_batch_create(ib_grid* const* members, int32_t n, ib_batch** out) {
+  if (!members || n <= 0 || !out) return IB_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    ib_grid* m = members[i];
+    if (!m || !m->ready || !m->d.deferred || m->batch) return IB_EINVAL;
+    if (m->d.precision != members[0]->d.precision) return IB_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (members[j] == m) return IB_EINVAL;
+  }
+  ib_batch* b = new (std::nothrow) ib_batch();
+  if (!b) return IB_ENOMEM;
+  Engine& E = b->E;
+  for (int i = 0; i < n; ++i) {
+    b->members.push_back(members[i]);
+    E.H.push_back(&members[i]->H);
+    E.D.push_back(members[i]->d);
+  }
+  E.ninst = n;
+  E.st = static_cast<cudaStream_t>(members[0]->d.stream);
+  E.alloc = members[0]->d.dev_alloc;
+  E.freef = members[0]->d.dev_free;
+  E.actx = members[0]->d.alloc_ctx;
+  ib_status s = engine_build(E);
+  for (int i = 0; i < n && s == IB_OK; ++i) s = snap_transfer(E, i, members[i], true);
+  if (s != IB_OK) {
+    members[0]->err = E.err;
+    engine_free(E);
+    delete b;
+    return s;
+  }
+  E.prof.on = members[0]->d.profile != 0;
+  E.use_graph = !E.prof.on;
+  for (int i = 0; i < n; ++i) {
+    members[i]->batch = b;
+    members[i]->batch_index = i;
+  }
+  *out = b;
+  return IB_OK;
+}
+
+ib_status ib_batch_step(ib_batch* b, int32_t nsteps, int32_t* status) {
+  if (!b || nsteps < 0) return IB_EINVAL;
+  ib_status worst = IB_OK;
+  for (int32_t k = 0; k < nsteps; ++k) {
+    ib_status s = engine_step(b->E);
+    if (s == IB_ECUDA) return s;
+    if (s != IB_OK) worst = s;
+  }
+  if (status)
+    for (int i = 0; i < b->E.ninst; ++i) status[i] = b->E.status[i];
+  return worst;
+}
+
+ib_status ib_batch_fields_get(ib_batch* b, int32_t member, int32_t field, void* dst, size_t bytes,
+                              int32_t dst_on_device) {
+  if (!b || member < 0 || member >= b->E.ninst) return IB_EINVAL;
+  const int64_t need = field_bytes(*b->E.H[member], field);
+  if (need < 0 || int64_t(bytes) != need || (!dst && bytes)) return IB_EINVAL;
+  return engine_fields_get(b->E, member, field, dst, bytes, dst_on_device);
+}
+
+ib_status ib_batch_info(const ib_batch* b, int32_t member, ib_info* out) {
+  if (!b || !out || member < 0 || member >= b->E.ninst) return IB_EINVAL;
+  const Engine& E = b->E;
+  ib_info I = E.last[member];
+  fill_info(*E.H[member], &E, E.bytes, I);
+  I.step = E.step[member];
+  I.time = E.time[member];
+  *out = I;
+  return IB_OK;
+}
+
+const char* ib_batch_last_error(const ib_batch* b) { return b ? b->E.err.c_str() : "null batch"; }
+
+void ib_batch_destroy(ib_batch* b) {
+  if (!b) return;
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    snap_transfer(b->E, int(i), b->members[i], false);
+    b->members[i]->batch = nullptr;
+    b->members[i]->batch_index = -1;
+  }
+  engine_free(b->E);
+  delete b;
 }
 
 }  // extern "C"

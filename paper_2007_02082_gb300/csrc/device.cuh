@@ -17,6 +17,14 @@ inline void launch_kernel(void (*k)(KArgs...), dim3 grid, dim3 block, size_t sme
   k<<<grid, block, smem, st>>>(static_cast<KArgs>(args)...);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
+// Device-side count of executed kernels: every kernel starts with KCOUNT(),
+// one relaxed atomic from thread 0 of block 0; one counter per translation unit.
+#define IBG_KCOUNT_DEFINE static __device__ unsigned long long g_kcount = 0ULL;
+#define KCOUNT()                                                  \
+  do {                                                            \
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&g_kcount, 1ULL); \
+  } while (0)
+
 #define IBG_LAUNCH(k, grid, block, smem, st, ...) \
   ::ibg::launch_kernel(k, dim3(grid), dim3(block), size_t(smem), st, __VA_ARGS__)
 
@@ -27,21 +35,30 @@ constexpr int TILE3 = 1000;
 
 // per-slot metadata bits (mirror of setup.hpp)
 constexpr uint16_t D_VALID = 1u << 8, D_HANG = 1u << 9, D_DUP = 1u << 10,
-                   D_VDIR = 1u << 11, D_PDIR = 1u << 12;
+                   D_VDIR = 1u << 11, D_PDIR = 1u << 12, D_IFACE = 1u << 13;
 
+// One or several problem instances stored side by side: every brick belongs to
+// one instance, and the bricks of an instance are contiguous
+// ([bseg[i], bseg[i+1])), so reductions are segmented per instance.
 struct DevGrid {
   int32_t nbricks;
   int64_t nslots;
+  int32_t ninst;
   const int32_t* __restrict__ blev;   // [nbricks]
+  const int32_t* __restrict__ binst;  // [nbricks] instance of each brick
+  const int32_t* __restrict__ bseg;   // [ninst + 1] brick range of each instance
   const int32_t* __restrict__ bnbr;   // [nbricks][27]
   const uint16_t* __restrict__ meta;  // [nslots]
-  double h[4][3];                     // cell spacing per level
+  const double* __restrict__ hl;      // [ninst][4][3] cell spacing per instance and level
+  const double* __restrict__ pdt;     // [ninst] time step
+  const double* __restrict__ pnu;     // [ninst] kinematic viscosity
   // nodes stored on two levels: coarse owner, fine copy, hanging children
   int32_t n_if;
   const int32_t* __restrict__ if_c;
   const int32_t* __restrict__ if_f;
   const int32_t* __restrict__ if_off;
   const int32_t* __restrict__ if_kid;
+  const int32_t* __restrict__ if_of_slot;   // [nslots] entry of an interface copy
   // hanging nodes and their parents (fine-level slots)
   int32_t n_hang;
   const int32_t* __restrict__ hg;
@@ -54,6 +71,23 @@ struct KState {
   double rz, rz_new, pq, alpha, beta, rr, bb, tol2;
   double rho, omega, rv, ts, tt;
   int32_t iter, max_iter, done, status;   // status: 0 ok, 4 no convergence, 5 breakdown
+};
+
+// FP64 defect-correction loop around an inner solve (mixed precision).
+struct OState {
+  double ref[3];     // max(||b||^2, ||r_0||^2) per component, set on the first pass
+  double rel2;       // max_c ||r||^2 / ref
+  double tol2;
+  int32_t iter, max_iter, done, status, inner_status, nc;
+};
+
+// Per-solve record of a step, read by the host after the step.
+struct SolveRec {
+  int32_t iters[3];
+  int32_t status;
+  int32_t outer;
+  int32_t pad;
+  double relres;
 };
 
 __device__ __forceinline__ int tile_index(int lx, int ly, int lz) {   // l in [-1, 8]
@@ -97,12 +131,18 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [32*NV]
   }
 }
 
-// Deterministic grid reduction: every block writes its NV partials, the last
-// block to arrive sums all partials in block order and returns true (only in
-// that block; totals in tot[] are valid in thread 0).  The counter is reset.
+// Deterministic segmented grid reduction.  Every block writes its NV partials;
+// the last block to arrive sums, for every instance i, the partials of blocks
+// [seg[i], seg[i+1]) in a fixed order (warp i mod nwarps: lane l takes blocks
+// seg[i] + l, + 32, ...; then a fixed shuffle tree) and stores the totals in
+// out[i * NV + k].  Returns true in that block only, after a __syncthreads that
+// makes out visible to all its threads.  The counter is reset.  The sum of an
+// instance depends only on its own blocks, so an instance gives bitwise the same
+// totals alone and next to others.
 template <int NV>
 __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* __restrict__ partials,
-                                              unsigned* __restrict__ counter, double (&tot)[NV]) {
+                                              unsigned* __restrict__ counter, const int32_t* __restrict__ seg,
+                                              int nseg, double* __restrict__ out) {
   __shared__ double sh[32 * NV];
   __shared__ bool last;
   block_sum<NV>(v, sh);
@@ -115,16 +155,20 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* __restric
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  double acc[NV];
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  // fixed order: thread t sums blocks t, t+blockDim, ... ; then a fixed tree
-  for (int64_t b = threadIdx.x; b < gridDim.x; b += blockDim.x)
-    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + b * NV + k);
-  block_sum<NV>(acc, sh);
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < NV; ++k) tot[k] = acc[k];
-    *counter = 0u;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = w; i < nseg; i += nw) {
+    double acc[NV];
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (int64_t b = seg[i] + lane; b < seg[i + 1]; b += 32)
+      for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + b * NV + k);
+    for (int k = 0; k < NV; ++k)
+      for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    if (lane == 0)
+      for (int k = 0; k < NV; ++k) out[(int64_t)i * NV + k] = acc[k];
   }
+  __threadfence_block();
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0u;
   return true;
 }
 

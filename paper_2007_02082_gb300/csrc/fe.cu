@@ -18,6 +18,13 @@
 
 namespace ibg {
 
+IBG_KCOUNT_DEFINE
+unsigned long long fe_kcount() {
+  unsigned long long v = 0;
+  cudaMemcpyFromSymbol(&v, g_kcount, sizeof(v));
+  return v;
+}
+
 std::atomic<long long> g_launches{0};
 
 // ---------------------------------------------------------------- tables
@@ -92,6 +99,13 @@ cudaError_t fe_init_tables() {
 }
 
 // ---------------------------------------------------------------- helpers
+__device__ __forceinline__ void spacing(const DevGrid& g, int b, double (&h)[3]) {
+  const int inst = g.binst[b], lev = g.blev[b];
+  const double* p = g.hl + (inst * 4 + lev) * 3;
+  h[0] = p[0];
+  h[1] = p[1];
+  h[2] = p[2];
+}
 __device__ __forceinline__ bool is_dof(uint16_t m, uint16_t dmask) {
   return (m & D_VALID) && !(m & (D_HANG | D_DUP | dmask));
 }
@@ -107,16 +121,68 @@ __device__ __forceinline__ T table_coef(int mask, int k, const double (&f)[3], d
 
 enum Post : int { POST_NONE = 0, POST_CG_ALPHA = 1 };
 
+// p.Ap per instance and component -> alpha = r.z / p.Ap
+template <int NC>
+__device__ __forceinline__ void cg_alpha_post(const DevGrid& g, double (&v)[NC], KState* ks, double* partials,
+                                              unsigned* counter) {
+  double* out = partials + (int64_t)gridDim.x * NC;
+  if (!grid_sum_last<NC>(v, partials, counter, g.bseg, g.ninst, out)) return;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
+    for (int c = 0; c < NC; ++c) {
+      KState& k = ks[i * NC + c];
+      if (k.done) continue;
+      const double pq = out[i * NC + c];
+      k.pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) { k.done = 1; k.status = 5; k.alpha = 0.0; continue; }
+      k.alpha = k.rz / pq;
+    }
+}
+
 // y = A x on every stored node of a brick; optional fused pre-sync x.y per
 // component, whose total gives p.Ap of the constrained operator and alpha.
-template <typename T, int OP, int NC>
+//
+// FUSEP: the CG direction update p_new = z + beta p_old is done while staging
+// the tile (halo included, so no separate kernel); p_new is written for the
+// brick's own nodes and q = A p_new is produced from it.
+template <typename T, int OP, int NC, bool FUSEP>
 __global__ void __launch_bounds__(512) k_apply(DevGrid g, const T* __restrict__ x, T* __restrict__ y,
                                                const T* __restrict__ coef, uint16_t dmask, int post,
                                                KState* __restrict__ ks, double* __restrict__ partials,
-                                               unsigned* __restrict__ counter) {
+                                               unsigned* __restrict__ counter, const T* __restrict__ zf,
+                                               T* __restrict__ pnew) {
+  KCOUNT();
   __shared__ T tile[NC * TILE3];
   const int b = blockIdx.x;
-  load_tile<T>(tile, x, g.nslots, NC, g.bnbr + 27 * b);
+  const KState* ki = ks ? ks + g.binst[b] * NC : nullptr;
+  bool skip = false;   // every component of this brick's instance has converged
+  if (FUSEP) {
+    skip = true;
+    for (int c = 0; c < NC; ++c) skip = skip && ki[c].done;
+  }
+  if (skip) {
+    if (post == POST_CG_ALPHA) {
+      double v[NC];
+      for (int c = 0; c < NC; ++c) v[c] = 0.0;
+      cg_alpha_post<NC>(g, v, ks, partials, counter);
+    }
+    return;
+  }
+  if (FUSEP) {
+    T beta[NC];
+    for (int c = 0; c < NC; ++c) beta[c] = T(ki[c].beta);
+    const int32_t* nb27 = g.bnbr + 27 * b;
+    for (int t = threadIdx.x; t < TILE3; t += blockDim.x) {
+      int hx = t % TILE, hy = (t / TILE) % TILE, hz = t / (TILE * TILE);
+      int lx = hx - 1, ly = hy - 1, lz = hz - 1;
+      int ox = lx < 0 ? -1 : (lx > 7 ? 1 : 0), oy = ly < 0 ? -1 : (ly > 7 ? 1 : 0), oz = lz < 0 ? -1 : (lz > 7 ? 1 : 0);
+      int nb = nb27[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+      int64_t s = (int64_t)nb * DBV + (((lz & 7) * DBS + (ly & 7)) * DBS + (lx & 7));
+      for (int c = 0; c < NC; ++c)
+        tile[c * TILE3 + t] = nb >= 0 ? T(zf[c * g.nslots + s] + beta[c] * x[c * g.nslots + s]) : T(0);
+    }
+  } else {
+    load_tile<T>(tile, x, g.nslots, NC, g.bnbr + 27 * b);
+  }
   __syncthreads();
   const int t = threadIdx.x;
   const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
@@ -128,8 +194,9 @@ __global__ void __launch_bounds__(512) k_apply(DevGrid g, const T* __restrict__ 
   for (int c = 0; c < NC; ++c) out[c] = T(0);
   if (m & D_VALID) {
     const int mask = m & 0xFF;
-    const int lev = g.blev[b];
-    const double hx = g.h[lev][0], hy = g.h[lev][1], hz = g.h[lev][2];
+    double hh[3];
+    spacing(g, b, hh);
+    const double hx = hh[0], hy = hh[1], hz = hh[2];
     const double V = hx * hy * hz;
     if (OP == OP_POISSON) {
       const double f[3] = {V / (6.0 * hx * hx), V / (6.0 * hy * hy), V / (6.0 * hz * hz)};
@@ -163,24 +230,21 @@ __global__ void __launch_bounds__(512) k_apply(DevGrid g, const T* __restrict__ 
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) y[c * g.nslots + s] = out[c];
+  if (FUSEP) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) pnew[c * g.nslots + s] = tile[c * TILE3 + ti];
+  }
   if (post == POST_CG_ALPHA) {
-    double v[NC], tot[NC];
+    double v[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) v[c] = double(tile[c * TILE3 + ti]) * double(out[c]);
-    if (grid_sum_last<NC>(v, partials, counter, tot) && threadIdx.x == 0) {
-      for (int c = 0; c < NC; ++c) {
-        KState& k = ks[c];
-        if (k.done) continue;
-        k.pq = tot[c];
-        if (!(tot[c] > 0.0) || !isfinite(tot[c])) { k.done = 1; k.status = 5; k.alpha = 0.0; continue; }
-        k.alpha = k.rz / tot[c];
-      }
-    }
+    cg_alpha_post<NC>(g, v, ks, partials, counter);
   }
 }
 
 template <typename T, int NC>
 __global__ void k_sync(DevGrid g, T* __restrict__ y, uint16_t dmask) {
+  KCOUNT();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.n_if) return;
   const int32_t sc = g.if_c[e], sf = g.if_f[e];
@@ -197,6 +261,7 @@ __global__ void k_sync(DevGrid g, T* __restrict__ y, uint16_t dmask) {
 
 template <typename T, int NC>
 __global__ void k_expand(DevGrid g, T* __restrict__ x, T* __restrict__ x2) {
+  KCOUNT();
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= g.n_hang) return;
   const int32_t s = g.hg[h], p1 = g.hp1[h], p2 = g.hp2[h];
@@ -210,284 +275,17 @@ __global__ void k_expand(DevGrid g, T* __restrict__ x, T* __restrict__ x2) {
   }
 }
 
-// ---------------------------------------------------------------- CG
-// start: r = b - y (DOFs only), z = D^-1 r, p = z; rz, rr, bb
-template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict__ b, const T* __restrict__ y,
-                                                  T* __restrict__ r, T* __restrict__ z, T* __restrict__ p,
-                                                  const T* __restrict__ dinv, uint16_t dmask, KState* ks,
-                                                  double* partials, unsigned* counter) {
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool dof = is_dof(m, dmask);
-  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));   // DOF or its duplicate copy
-  double v[3 * NC];
-  for (int c = 0; c < NC; ++c) {
-    const int64_t i = c * g.nslots + s;
-    T rv = keep ? T(b[i] - y[i]) : T(0);
-    T zv = rv * dinv[s];
-    r[i] = rv;
-    z[i] = zv;
-    p[i] = zv;
-    v[3 * c] = dof ? double(rv) * double(zv) : 0.0;
-    v[3 * c + 1] = dof ? double(rv) * double(rv) : 0.0;
-    v[3 * c + 2] = dof ? double(b[i]) * double(b[i]) : 0.0;
-  }
-  double tot[3 * NC];
-  if (grid_sum_last<3 * NC>(v, partials, counter, tot) && threadIdx.x == 0) {
-    for (int c = 0; c < NC; ++c) {
-      KState& k = ks[c];
-      k.rz = tot[3 * c];
-      k.rr = tot[3 * c + 1];
-      // reference norm: max(||b||, ||r0||) covers a zero right-hand side with
-      // nonzero Dirichlet lifting as well as warm starts
-      k.bb = fmax(tot[3 * c + 2], k.rr);
-      k.iter = 0;
-      k.status = 0;
-      k.alpha = 0.0;
-      k.beta = 0.0;
-      k.done = (k.rr <= k.tol2 * k.bb) ? 1 : 0;
-      if (!isfinite(k.rr)) { k.done = 1; k.status = 5; }
-    }
-  }
-}
-
-// x += alpha p, r -= alpha q, z = D^-1 r; rz_new, rr; beta
-template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_cg_update(DevGrid g, T* __restrict__ x, T* __restrict__ r,
-                                                   T* __restrict__ z, const T* __restrict__ p,
-                                                   const T* __restrict__ q, const T* __restrict__ dinv,
-                                                   uint16_t dmask, KState* ks, double* partials,
-                                                   unsigned* counter) {
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool dof = is_dof(m, dmask);
-  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
-  double v[2 * NC];
-  for (int c = 0; c < NC; ++c) {
-    v[2 * c] = v[2 * c + 1] = 0.0;
-    if (ks[c].done) continue;
-    const T a = T(ks[c].alpha);
-    const int64_t i = c * g.nslots + s;
-    if (m & D_VALID) x[i] += a * p[i];
-    T rv = keep ? T(r[i] - a * q[i]) : T(0);
-    T zv = rv * dinv[s];
-    r[i] = rv;
-    z[i] = zv;
-    if (dof) {
-      v[2 * c] = double(rv) * double(zv);
-      v[2 * c + 1] = double(rv) * double(rv);
-    }
-  }
-  double tot[2 * NC];
-  if (grid_sum_last<2 * NC>(v, partials, counter, tot) && threadIdx.x == 0) {
-    for (int c = 0; c < NC; ++c) {
-      KState& k = ks[c];
-      if (k.done) continue;
-      k.iter++;
-      k.rr = tot[2 * c + 1];
-      const double rzn = tot[2 * c];
-      if (!isfinite(k.rr) || !isfinite(rzn)) { k.done = 1; k.status = 5; continue; }
-      if (k.rr <= k.tol2 * k.bb) { k.done = 1; continue; }
-      if (k.iter >= k.max_iter) { k.done = 1; k.status = 4; continue; }
-      k.beta = rzn / k.rz;
-      k.rz = rzn;
-    }
-  }
-}
-
-template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_cg_p(DevGrid g, const T* __restrict__ z, T* __restrict__ p,
-                                              const KState* ks) {
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  for (int c = 0; c < NC; ++c) {
-    if (ks[c].done) continue;
-    const int64_t i = c * g.nslots + s;
-    p[i] = z[i] + T(ks[c].beta) * p[i];
-  }
-}
-
-// ---------------------------------------------------------------- BiCGStab
-// start: r = b - y on DOF slots (and copies), rh = r, p = v = 0; rho = (rh, r)
-template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restrict__ b, const T* __restrict__ y,
-                                                   T* __restrict__ r, T* __restrict__ rh, T* __restrict__ p,
-                                                   T* __restrict__ v, uint16_t dmask, KState* ks,
-                                                   double* partials, unsigned* counter) {
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool dof = is_dof(m, dmask);
-  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
-  double w[2 * NC];
-  for (int c = 0; c < NC; ++c) {
-    const int64_t i = c * g.nslots + s;
-    T rv = keep ? T(b[i] - y[i]) : T(0);
-    r[i] = rv;
-    rh[i] = rv;
-    p[i] = T(0);
-    v[i] = T(0);
-    w[2 * c] = dof ? double(rv) * double(rv) : 0.0;
-    w[2 * c + 1] = dof ? double(b[i]) * double(b[i]) : 0.0;
-  }
-  double tot[2 * NC];
-  if (grid_sum_last<2 * NC>(w, partials, counter, tot) && threadIdx.x == 0) {
-    for (int c = 0; c < NC; ++c) {
-      KState& k = ks[c];
-      k.rr = tot[2 * c];
-      k.bb = fmax(tot[2 * c + 1], k.rr);
-      k.rho = k.rr;
-      k.alpha = 1.0;
-      k.omega = 1.0;
-      k.beta = 0.0;
-      k.iter = 0;
-      k.status = 0;
-      k.done = (k.rr <= k.tol2 * k.bb) ? 1 : 0;
-      if (!isfinite(k.rr)) { k.done = 1; k.status = 5; }
-    }
-  }
-}
-
-// p = r + beta (p - omega v); ph = D^-1 p
-template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_bcg_p(DevGrid g, const T* __restrict__ r, T* __restrict__ p,
-                                               const T* __restrict__ v, T* __restrict__ ph,
-                                               const T* __restrict__ dinv, uint16_t dmask, const KState* ks) {
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
-  for (int c = 0; c < NC; ++c) {
-    if (ks[c].done) continue;
-    const int64_t i = c * g.nslots + s;
-    T pv = keep ? T(r[i] + T(ks[c].beta) * (p[i] - T(ks[c].omega) * v[i])) : T(0);
-    p[i] = pv;
-    ph[i] = pv * dinv[s];
-  }
-}
-
-// dot kernels with a post step: mode 0 -> alpha = rho / (rh, v); mode 1 -> omega = (t,s)/(t,t)
-template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_bcg_dot(DevGrid g, const T* __restrict__ a1, const T* __restrict__ b1,
-                                                 const T* __restrict__ a2, uint16_t dmask, int mode, KState* ks,
-                                                 double* partials, unsigned* counter) {
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool dof = is_dof(m, dmask);
-  double w[2 * NC];
-  for (int c = 0; c < NC; ++c) {
-    const int64_t i = c * g.nslots + s;
-    w[2 * c] = dof ? double(a1[i]) * double(b1[i]) : 0.0;
-    w[2 * c + 1] = (dof && mode == 1) ? double(a2[i]) * double(a2[i]) : 0.0;
-  }
-  double tot[2 * NC];
-  if (grid_sum_last<2 * NC>(w, partials, counter, tot) && threadIdx.x == 0) {
-    for (int c = 0; c < NC; ++c) {
-      KState& k = ks[c];
-      if (k.done) continue;
-      if (mode == 0) {
-        k.rv = tot[2 * c];
-        if (k.rv == 0.0 || !isfinite(k.rv)) { k.done = 1; k.status = 5; k.alpha = 0.0; continue; }
-        k.alpha = k.rho / k.rv;
-      } else {
-        k.ts = tot[2 * c];
-        k.tt = tot[2 * c + 1];
-        k.omega = (k.tt > 0.0) ? k.ts / k.tt : 0.0;
-      }
-    }
-  }
-}
-
-// s = r - alpha v; sh = D^-1 s   (s stored in r's place is avoided: separate buffer)
-template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_bcg_s(DevGrid g, const T* __restrict__ r, const T* __restrict__ v,
-                                               T* __restrict__ sv, T* __restrict__ sh, const T* __restrict__ dinv,
-                                               uint16_t dmask, const KState* ks) {
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
-  for (int c = 0; c < NC; ++c) {
-    if (ks[c].done) continue;
-    const int64_t i = c * g.nslots + s;
-    T val = keep ? T(r[i] - T(ks[c].alpha) * v[i]) : T(0);
-    sv[i] = val;
-    sh[i] = val * dinv[s];
-  }
-}
-
-// x += alpha ph + omega sh; r = s - omega t; rr, rho_new = (rh, r); beta
-template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_bcg_xr(DevGrid g, T* __restrict__ x, T* __restrict__ r,
-                                                const T* __restrict__ rh, const T* __restrict__ ph,
-                                                const T* __restrict__ sh, const T* __restrict__ sv,
-                                                const T* __restrict__ tv, uint16_t dmask, KState* ks,
-                                                double* partials, unsigned* counter) {
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool dof = is_dof(m, dmask);
-  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
-  double w[2 * NC];
-  for (int c = 0; c < NC; ++c) {
-    w[2 * c] = w[2 * c + 1] = 0.0;
-    if (ks[c].done) continue;
-    const int64_t i = c * g.nslots + s;
-    const T al = T(ks[c].alpha), om = T(ks[c].omega);
-    if (m & D_VALID) x[i] += al * ph[i] + om * sh[i];
-    T rv = keep ? T(sv[i] - om * tv[i]) : T(0);
-    r[i] = rv;
-    if (dof) {
-      w[2 * c] = double(rv) * double(rv);
-      w[2 * c + 1] = double(rh[i]) * double(rv);
-    }
-  }
-  double tot[2 * NC];
-  if (grid_sum_last<2 * NC>(w, partials, counter, tot) && threadIdx.x == 0) {
-    for (int c = 0; c < NC; ++c) {
-      KState& k = ks[c];
-      if (k.done) continue;
-      k.iter++;
-      k.rr = tot[2 * c];
-      const double rhon = tot[2 * c + 1];
-      if (!isfinite(k.rr)) { k.done = 1; k.status = 5; continue; }
-      if (k.rr <= k.tol2 * k.bb) { k.done = 1; continue; }
-      if (k.iter >= k.max_iter) { k.done = 1; k.status = 4; continue; }
-      if (k.omega == 0.0 || rhon == 0.0 || !isfinite(rhon)) { k.done = 1; k.status = 5; continue; }
-      k.beta = (rhon / k.rho) * (k.alpha / k.omega);
-      k.rho = rhon;
-    }
-  }
-}
-
-// ---------------------------------------------------------------- residual (FP64 outer loop)
-template <int NC>
-__global__ void __launch_bounds__(512) k_residual(DevGrid g, const double* __restrict__ b,
-                                                  const double* __restrict__ y, double* __restrict__ r,
-                                                  uint16_t dmask, double* partials, unsigned* counter,
-                                                  double* out) {
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool dof = is_dof(m, dmask);
-  const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
-  double w[2 * NC];
-  for (int c = 0; c < NC; ++c) {
-    const int64_t i = c * g.nslots + s;
-    double rv = keep ? b[i] - y[i] : 0.0;
-    r[i] = rv;
-    w[2 * c] = dof ? rv * rv : 0.0;
-    w[2 * c + 1] = dof ? b[i] * b[i] : 0.0;
-  }
-  double tot[2 * NC];
-  if (grid_sum_last<2 * NC>(w, partials, counter, tot) && threadIdx.x == 0)
-    for (int k = 0; k < 2 * NC; ++k) out[k] = tot[k];
-}
-
 // ---------------------------------------------------------------- Jacobi
 template <typename T, int OP>
 __global__ void __launch_bounds__(512) k_diag(DevGrid g, const T* __restrict__ coef, T* __restrict__ diag) {
+  KCOUNT();
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
   const uint16_t m = g.meta[s];
   T d = T(0);
   if (m & D_VALID) {
-    const int lev = g.blev[blockIdx.x];
-    const double hx = g.h[lev][0], hy = g.h[lev][1], hz = g.h[lev][2], V = hx * hy * hz;
+    double hh[3];
+    spacing(g, blockIdx.x, hh);
+    const double hx = hh[0], hy = hh[1], hz = hh[2], V = hx * hy * hz;
     if (OP == OP_POISSON) {
       const double f[3] = {V / (6.0 * hx * hx), V / (6.0 * hy * hy), V / (6.0 * hz * hz)};
       d = table_coef<T, OP_POISSON>(m & 0xFF, 0, f, 0.0);
@@ -504,6 +302,7 @@ __global__ void __launch_bounds__(512) k_diag(DevGrid g, const T* __restrict__ c
 template <typename T>
 __global__ void __launch_bounds__(512) k_dinv(DevGrid g, const T* __restrict__ diag, T* __restrict__ dinv,
                                               uint16_t dmask) {
+  KCOUNT();
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
   const uint16_t m = g.meta[s];
   const bool keep = (m & D_VALID) && !(m & (D_HANG | dmask));
@@ -548,8 +347,8 @@ __device__ __forceinline__ void for_each_tet(int mask, const double h[3], F&& f)
 
 // out_c = (M u_c) - dt (G_c p)
 __global__ void __launch_bounds__(512) k_rhs_mass_grad(DevGrid g, const double* __restrict__ u,
-                                                       const double* __restrict__ p, double dt,
-                                                       double* __restrict__ out) {
+                                                       const double* __restrict__ p, double* __restrict__ out) {
+  KCOUNT();
   __shared__ double tile[4 * TILE3];
   const int b = blockIdx.x;
   load_tile<double>(tile, u, g.nslots, 3, g.bnbr + 27 * b);
@@ -561,9 +360,10 @@ __global__ void __launch_bounds__(512) k_rhs_mass_grad(DevGrid g, const double* 
   double o[3] = {0, 0, 0};
   if (m & D_VALID) {
     const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
-    const int lev = g.blev[b];
-    const double h[3] = {g.h[lev][0], g.h[lev][1], g.h[lev][2]};
+    double h[3];
+    spacing(g, b, h);
     const double V = h[0] * h[1] * h[2];
+    const double dt = g.pdt[g.binst[b]];
     for_each_tet(m & 0xFF, h, [&](int kn, const int (&rel)[4], const double (&gr)[4][3], const int*, int, int, int) {
       double gp[3] = {0, 0, 0};
 #pragma unroll
@@ -584,8 +384,9 @@ __global__ void __launch_bounds__(512) k_rhs_mass_grad(DevGrid g, const double* 
 }
 
 // out = scale * (div u, q)
-__global__ void __launch_bounds__(512) k_rhs_div(DevGrid g, const double* __restrict__ u, double scale,
-                                                 double* __restrict__ out) {
+// out = -(1/dt) (div u, q) with the instance's dt
+__global__ void __launch_bounds__(512) k_rhs_div(DevGrid g, const double* __restrict__ u, double* __restrict__ out) {
+  KCOUNT();
   __shared__ double tile[3 * TILE3];
   const int b = blockIdx.x;
   load_tile<double>(tile, u, g.nslots, 3, g.bnbr + 27 * b);
@@ -596,8 +397,8 @@ __global__ void __launch_bounds__(512) k_rhs_div(DevGrid g, const double* __rest
   double o = 0.0;
   if (m & D_VALID) {
     const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
-    const int lev = g.blev[b];
-    const double h[3] = {g.h[lev][0], g.h[lev][1], g.h[lev][2]};
+    double h[3];
+    spacing(g, b, h);
     const double V = h[0] * h[1] * h[2];
     for_each_tet(m & 0xFF, h, [&](int, const int (&rel)[4], const double (&gr)[4][3], const int*, int, int, int) {
       double dv = 0.0;
@@ -608,12 +409,13 @@ __global__ void __launch_bounds__(512) k_rhs_div(DevGrid g, const double* __rest
       o += (V / 24.0) * dv;
     });
   }
-  out[s] = scale * o;
+  out[s] = -o / g.pdt[g.binst[b]];
 }
 
 // coef[k] = M + dt C(u) + dt nu K row entries (Eq. 9 operator), k over the 15 slots
-__global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __restrict__ u, double dt, double nu,
-                                                  double* __restrict__ coef, float* __restrict__ coef32) {
+__global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __restrict__ u, double* __restrict__ coef,
+                                                  float* __restrict__ coef32) {
+  KCOUNT();
   __shared__ double tile[3 * TILE3];
   const int b = blockIdx.x;
   load_tile<double>(tile, u, g.nslots, 3, g.bnbr + 27 * b);
@@ -626,9 +428,10 @@ __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __res
   for (int k = 0; k < 15; ++k) cf[k] = 0.0;
   if (m & D_VALID) {
     const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
-    const int lev = g.blev[b];
-    const double h[3] = {g.h[lev][0], g.h[lev][1], g.h[lev][2]};
+    double h[3];
+    spacing(g, b, h);
     const double V = h[0] * h[1] * h[2];
+    const double dt = g.pdt[g.binst[b]], nu = g.pnu[g.binst[b]];
     for_each_tet(m & 0xFF, h, [&](int kn, const int (&rel)[4], const double (&gr)[4][3], const int* vb, int dx, int dy,
                                   int dz) {
       double S[3] = {0, 0, 0};
@@ -659,23 +462,28 @@ __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __res
 
 // ---------------------------------------------------------------- elementwise
 __global__ void k_cast_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  KCOUNT();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = float(a[i]);
 }
 __global__ void k_add_f2d(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
+  KCOUNT();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] += double(a[i]);
 }
 __global__ void k_add_d(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  KCOUNT();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] += a[i];
 }
 __global__ void k_copy_d(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  KCOUNT();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = a[i];
 }
 template <typename T>
 __global__ void k_zero(int64_t n, T* __restrict__ a) {
+  KCOUNT();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     a[i] = T(0);
 }
@@ -683,15 +491,18 @@ __global__ void k_zero(int64_t n, T* __restrict__ a) {
 template <typename T>
 __global__ void k_gather_canon(int64_t N, const int32_t* __restrict__ cs, int nc, int64_t nslots,
                                const T* __restrict__ x, T* __restrict__ out) {
+  KCOUNT();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     for (int c = 0; c < nc; ++c) out[i * nc + c] = x[c * nslots + cs[i]];
 }
 __global__ void k_scatter_canon(int64_t N, const int32_t* __restrict__ cs, int nc, int64_t nslots,
                                 const double* __restrict__ in, double* __restrict__ x) {
+  KCOUNT();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     for (int c = 0; c < nc; ++c) x[c * nslots + cs[i]] = in[i * nc + c];
 }
 __global__ void k_copy_to_fine(DevGrid g, int nc, double* __restrict__ x) {
+  KCOUNT();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.n_if) return;
   for (int c = 0; c < nc; ++c) x[c * g.nslots + g.if_f[e]] = x[c * g.nslots + g.if_c[e]];
@@ -700,18 +511,26 @@ __global__ void k_copy_to_fine(DevGrid g, int nc, double* __restrict__ x) {
 __global__ void k_set_inlet(int64_t n, const int32_t* __restrict__ slot, const int32_t* __restrict__ port,
                             const double* __restrict__ shape, const PortDev* __restrict__ ports,
                             const double* __restrict__ tp, int64_t nslots, double* __restrict__ u) {
-  const double t = *tp;
+  KCOUNT();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const PortDev& P = ports[port[i]];
+    const double t = tp[P.inst];
     const double w = 2.0 * 3.14159265358979323846 / P.period;
     double um = P.a0;
     for (int k = 0; k < P.nh; ++k) um += P.a[k] * cos((k + 1) * w * t) + P.b[k] * sin((k + 1) * w * t);
     u[P.axis * nslots + slot[i]] = um * shape[i];
   }
 }
-__global__ void k_time(double* tc, double* tn, double dt, int commit) {
-  if (commit) *tc = *tn;
-  else *tn = *tc + dt;
+// per instance: t_next = t_commit + dt, or (commit) t_commit = t_next where ok[i]
+__global__ void k_time(double* tc, double* tn, const double* dt, int n, int commit, const int32_t* ok) {
+  KCOUNT();
+  const int i = threadIdx.x + blockIdx.x * blockDim.x;
+  if (i >= n) return;
+  if (commit) {
+    if (!ok || ok[i]) tc[i] = tn[i];
+  } else {
+    tn[i] = tc[i] + dt[i];
+  }
 }
 
 // ---------------------------------------------------------------- profiling
@@ -756,15 +575,25 @@ static inline int nblk(int64_t n, int bs = 256) {
   return int(std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 16));
 }
 
-template <typename T, int NC>
+template <typename T, int NC, bool FUSEP = false>
 static void launch_apply(const DevGrid& g, int op, const T* x, T* y, const T* coef, uint16_t dmask, int post,
-                         KState* ks, RedBuf rb, cudaStream_t st) {
+                         KState* ks, RedBuf rb, cudaStream_t st, const T* zf = nullptr, T* pnew = nullptr) {
   if (op == OP_POISSON)
-    IBG_LAUNCH((k_apply<T, OP_POISSON, NC>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks, rb.partials, rb.counter);
+    IBG_LAUNCH((k_apply<T, OP_POISSON, NC, FUSEP>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
+               rb.partials, rb.counter, zf, pnew);
   else if (op == OP_MASS)
-    IBG_LAUNCH((k_apply<T, OP_MASS, NC>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks, rb.partials, rb.counter);
+    IBG_LAUNCH((k_apply<T, OP_MASS, NC, FUSEP>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
+               rb.partials, rb.counter, zf, pnew);
   else
-    IBG_LAUNCH((k_apply<T, OP_COEF, NC>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks, rb.partials, rb.counter);
+    IBG_LAUNCH((k_apply<T, OP_COEF, NC, FUSEP>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
+               rb.partials, rb.counter, zf, pnew);
+}
+
+template <typename T>
+void fe_apply_cg(const DevGrid& g, const OpDesc<T>& A, int nc, const T* z, const T* pold, T* pnew, T* q, KState* ks,
+                 RedBuf rb, cudaStream_t st) {
+  if (nc == 1) launch_apply<T, 1, true>(g, A.op, pold, q, A.coef, A.dmask, POST_CG_ALPHA, ks, rb, st, z, pnew);
+  else launch_apply<T, 3, true>(g, A.op, pold, q, A.coef, A.dmask, POST_CG_ALPHA, ks, rb, st, z, pnew);
 }
 
 template <typename T>
@@ -776,7 +605,7 @@ void fe_sync(const DevGrid& g, int nc, T* y, uint16_t dmask, cudaStream_t st) {
 }
 
 template <typename T>
-static void expand2(const DevGrid& g, int nc, T* x, T* x2, cudaStream_t st) {
+void fe_expand2(const DevGrid& g, int nc, T* x, T* x2, cudaStream_t st) {
   if (g.n_hang == 0) return;
   int bl = (g.n_hang + 255) / 256;
   if (nc == 1) IBG_LAUNCH((k_expand<T, 1>), bl, 256, 0, st, g, x, x2);
@@ -785,7 +614,7 @@ static void expand2(const DevGrid& g, int nc, T* x, T* x2, cudaStream_t st) {
 
 template <typename T>
 void fe_expand(const DevGrid& g, int nc, T* x, cudaStream_t st) {
-  expand2<T>(g, nc, x, (T*)nullptr, st);
+  fe_expand2<T>(g, nc, x, (T*)nullptr, st);
 }
 
 template <typename T>
@@ -805,127 +634,6 @@ void fe_jacobi(const DevGrid& g, int op, const T* coef, uint16_t dmask, T* diag,
   IBG_LAUNCH((k_dinv<T>), g.nbricks, DBV, 0, st, g, diag, dinv, dmask);
 }
 
-static SolveStats read_stats(const KState* ks, KState* ks_host, int nc, cudaStream_t st, bool* all_done) {
-  cudaMemcpyAsync(ks_host, ks, nc * sizeof(KState), cudaMemcpyDeviceToHost, st);
-  cudaStreamSynchronize(st);
-  SolveStats S;
-  *all_done = true;
-  for (int c = 0; c < nc; ++c) {
-    S.iters[c] = ks_host[c].iter;
-    if (!ks_host[c].done) *all_done = false;
-    if (ks_host[c].status) S.status = ks_host[c].status;
-    double rel = ks_host[c].bb > 0 ? std::sqrt(std::max(ks_host[c].rr, 0.0) / ks_host[c].bb) : 0.0;
-    S.relres = std::max(S.relres, rel);
-  }
-  return S;
-}
-
-static void init_states(KState* ks, KState* ks_host, int nc, double rtol, int max_iter, cudaStream_t st) {
-  for (int c = 0; c < nc; ++c) {
-    std::memset(&ks_host[c], 0, sizeof(KState));
-    ks_host[c].tol2 = rtol * rtol;
-    ks_host[c].max_iter = max_iter;
-  }
-  cudaMemcpyAsync(ks, ks_host, nc * sizeof(KState), cudaMemcpyHostToDevice, st);
-}
-
-template <typename T, int NC>
-static SolveStats cg_impl(const DevGrid& g, const OpDesc<T>& A, const T* b, T* x, T* work, KState* ks,
-                          KState* ks_host, RedBuf rb, double rtol, int max_iter, cudaStream_t st) {
-  const int64_t L = NC * g.nslots;
-  T *r = work, *z = work + L, *p = work + 2 * L, *q = work + 3 * L;
-  init_states(ks, ks_host, NC, rtol, max_iter, st);
-  launch_apply<T, NC>(g, A.op, x, q, A.coef, A.dmask, POST_NONE, nullptr, rb, st);
-  fe_sync<T>(g, NC, q, A.dmask, st);
-  IBG_LAUNCH((k_cg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, q, r, z, p, A.dinv, A.dmask, ks, rb.partials, rb.counter);
-  expand2<T>(g, NC, z, p, st);
-  int it = 0, chunk = 4;
-  bool done = false;
-  SolveStats S = read_stats(ks, ks_host, NC, st, &done);
-  while (!done) {
-    Prof* pf = A.prof;
-    for (int k = 0; k < chunk; ++k) {
-      if (pf) pf->begin(A.pbase + 0, st);
-      launch_apply<T, NC>(g, A.op, p, q, A.coef, A.dmask, POST_CG_ALPHA, ks, rb, st);
-      if (pf) pf->end(st);
-      fe_sync<T>(g, NC, q, A.dmask, st);
-      if (pf) pf->begin(A.pbase + 1, st);
-      IBG_LAUNCH((k_cg_update<T, NC>), g.nbricks, DBV, 0, st, g, x, r, z, p, q, A.dinv, A.dmask, ks, rb.partials, rb.counter);
-      if (pf) pf->end(st);
-      expand2<T>(g, NC, z, (T*)nullptr, st);
-      if (pf) pf->begin(A.pbase + 2, st);
-      IBG_LAUNCH((k_cg_p<T, NC>), g.nbricks, DBV, 0, st, g, z, p, ks);
-      if (pf) pf->end(st);
-    }
-    it += chunk;
-    chunk = std::min(chunk * 2, 32);
-    S = read_stats(ks, ks_host, NC, st, &done);
-    if (it > max_iter + 64) break;
-  }
-  return S;
-}
-
-template <typename T>
-SolveStats fe_cg(const DevGrid& g, const OpDesc<T>& A, int nc, const T* b, T* x, T* work, KState* ks,
-                 KState* ks_host, RedBuf rb, double rtol, int max_iter, cudaStream_t st) {
-  if (nc == 1) return cg_impl<T, 1>(g, A, b, x, work, ks, ks_host, rb, rtol, max_iter, st);
-  return cg_impl<T, 3>(g, A, b, x, work, ks, ks_host, rb, rtol, max_iter, st);
-}
-
-template <typename T, int NC>
-static SolveStats bcg_impl(const DevGrid& g, const OpDesc<T>& A, const T* b, T* x, T* work, KState* ks,
-                           KState* ks_host, RedBuf rb, double rtol, int max_iter, cudaStream_t st) {
-  const int64_t L = NC * g.nslots;
-  T *r = work, *rh = work + L, *p = work + 2 * L, *v = work + 3 * L, *sv = work + 4 * L, *tv = work + 5 * L,
-    *ph = work + 6 * L, *sh = work + 7 * L;
-  init_states(ks, ks_host, NC, rtol, max_iter, st);
-  launch_apply<T, NC>(g, A.op, x, tv, A.coef, A.dmask, POST_NONE, nullptr, rb, st);
-  fe_sync<T>(g, NC, tv, A.dmask, st);
-  IBG_LAUNCH((k_bcg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, tv, r, rh, p, v, A.dmask, ks, rb.partials, rb.counter);
-  int it = 0, chunk = 2;
-  bool done = false;
-  SolveStats S = read_stats(ks, ks_host, NC, st, &done);
-  while (!done) {
-    for (int k = 0; k < chunk; ++k) {
-      IBG_LAUNCH((k_bcg_p<T, NC>), g.nbricks, DBV, 0, st, g, r, p, v, ph, A.dinv, A.dmask, ks);
-      expand2<T>(g, NC, ph, (T*)nullptr, st);
-      if (A.prof) A.prof->begin(A.pbase + 0, st);
-      launch_apply<T, NC>(g, A.op, ph, v, A.coef, A.dmask, POST_NONE, nullptr, rb, st);
-      if (A.prof) A.prof->end(st);
-      fe_sync<T>(g, NC, v, A.dmask, st);
-      IBG_LAUNCH((k_bcg_dot<T, NC>), g.nbricks, DBV, 0, st, g, rh, v, v, A.dmask, 0, ks, rb.partials, rb.counter);
-      IBG_LAUNCH((k_bcg_s<T, NC>), g.nbricks, DBV, 0, st, g, r, v, sv, sh, A.dinv, A.dmask, ks);
-      expand2<T>(g, NC, sh, (T*)nullptr, st);
-      launch_apply<T, NC>(g, A.op, sh, tv, A.coef, A.dmask, POST_NONE, nullptr, rb, st);
-      fe_sync<T>(g, NC, tv, A.dmask, st);
-      IBG_LAUNCH((k_bcg_dot<T, NC>), g.nbricks, DBV, 0, st, g, tv, sv, tv, A.dmask, 1, ks, rb.partials, rb.counter);
-      IBG_LAUNCH((k_bcg_xr<T, NC>), g.nbricks, DBV, 0, st, g, x, r, rh, ph, sh, sv, tv, A.dmask, ks, rb.partials, rb.counter);
-    }
-    it += chunk;
-    chunk = std::min(chunk * 2, 16);
-    S = read_stats(ks, ks_host, NC, st, &done);
-    if (it > max_iter + 32) break;
-  }
-  return S;
-}
-
-template <typename T>
-SolveStats fe_bicgstab(const DevGrid& g, const OpDesc<T>& A, int nc, const T* b, T* x, T* work, KState* ks,
-                       KState* ks_host, RedBuf rb, double rtol, int max_iter, cudaStream_t st) {
-  if (nc == 1) return bcg_impl<T, 1>(g, A, b, x, work, ks, ks_host, rb, rtol, max_iter, st);
-  return bcg_impl<T, 3>(g, A, b, x, work, ks, ks_host, rb, rtol, max_iter, st);
-}
-
-void fe_residual64(const DevGrid& g, const OpDesc<double>& A, int nc, const double* b, const double* x, double* y,
-                   double* r, RedBuf rb, double* host_rr_bb, cudaStream_t st) {
-  fe_apply<double>(g, A, nc, x, y, st);
-  double* out = rb.partials + int64_t(g.nbricks) * 16;   // after the block partials
-  if (nc == 1) IBG_LAUNCH((k_residual<1>), g.nbricks, DBV, 0, st, g, b, y, r, A.dmask, rb.partials, rb.counter, out);
-  else IBG_LAUNCH((k_residual<3>), g.nbricks, DBV, 0, st, g, b, y, r, A.dmask, rb.partials, rb.counter, out);
-  cudaMemcpyAsync(host_rr_bb, out, 2 * nc * sizeof(double), cudaMemcpyDeviceToHost, st);
-  cudaStreamSynchronize(st);
-}
-
 void fe_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t st) { IBG_LAUNCH(k_cast_d2f, nblk(n), 256, 0, st, n, a, b); }
 void fe_add_f2d(int64_t n, const float* a, double* b, cudaStream_t st) { IBG_LAUNCH(k_add_f2d, nblk(n), 256, 0, st, n, a, b); }
 void fe_copy_d(int64_t n, const double* a, double* b, cudaStream_t st) { IBG_LAUNCH(k_copy_d, nblk(n), 256, 0, st, n, a, b); }
@@ -933,15 +641,14 @@ void fe_add_d(int64_t n, const double* a, double* b, cudaStream_t st) { IBG_LAUN
 template <typename T>
 void fe_zero(int64_t n, T* a, cudaStream_t st) { IBG_LAUNCH((k_zero<T>), nblk(n), 256, 0, st, n, a); }
 
-void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double dt, double* out, cudaStream_t st) {
-  IBG_LAUNCH(k_rhs_mass_grad, g.nbricks, DBV, 0, st, g, u, p, dt, out);
+void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double* out, cudaStream_t st) {
+  IBG_LAUNCH(k_rhs_mass_grad, g.nbricks, DBV, 0, st, g, u, p, out);
 }
-void fe_rhs_div(const DevGrid& g, const double* u, double scale, double* out, cudaStream_t st) {
-  IBG_LAUNCH(k_rhs_div, g.nbricks, DBV, 0, st, g, u, scale, out);
+void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st) {
+  IBG_LAUNCH(k_rhs_div, g.nbricks, DBV, 0, st, g, u, out);
 }
-void fe_momentum_coef(const DevGrid& g, const double* u, double dt, double nu, double* coef64, float* coef32,
-                      cudaStream_t st) {
-  IBG_LAUNCH(k_mom_coef, g.nbricks, DBV, 0, st, g, u, dt, nu, coef64, coef32);
+void fe_momentum_coef(const DevGrid& g, const double* u, double* coef64, float* coef32, cudaStream_t st) {
+  IBG_LAUNCH(k_mom_coef, g.nbricks, DBV, 0, st, g, u, coef64, coef32);
 }
 
 template <typename T>
@@ -960,8 +667,9 @@ void fe_set_inlet(int64_t n, const int32_t* slot, const int32_t* port, const dou
   if (n == 0) return;
   IBG_LAUNCH(k_set_inlet, nblk(n), 256, 0, st, n, slot, port, shape, ports, t, nslots, u);
 }
-void fe_time_advance(double* tc, double* tn, double dt, int commit, cudaStream_t st) {
-  IBG_LAUNCH(k_time, 1, 1, 0, st, tc, tn, dt, commit);
+void fe_time_advance(double* tc, double* tn, const double* dt, int n, int commit, const int32_t* ok,
+                     cudaStream_t st) {
+  IBG_LAUNCH(k_time, (n + 127) / 128, 128, 0, st, tc, tn, dt, n, commit, ok);
 }
 
 // explicit instantiations
@@ -969,17 +677,15 @@ template void fe_apply<double>(const DevGrid&, const OpDesc<double>&, int, const
 template void fe_apply<float>(const DevGrid&, const OpDesc<float>&, int, const float*, float*, cudaStream_t);
 template void fe_jacobi<double>(const DevGrid&, int, const double*, uint16_t, double*, double*, cudaStream_t);
 template void fe_jacobi<float>(const DevGrid&, int, const float*, uint16_t, float*, float*, cudaStream_t);
-template SolveStats fe_cg<double>(const DevGrid&, const OpDesc<double>&, int, const double*, double*, double*,
-                                  KState*, KState*, RedBuf, double, int, cudaStream_t);
-template SolveStats fe_cg<float>(const DevGrid&, const OpDesc<float>&, int, const float*, float*, float*, KState*,
-                                 KState*, RedBuf, double, int, cudaStream_t);
-template SolveStats fe_bicgstab<double>(const DevGrid&, const OpDesc<double>&, int, const double*, double*, double*,
-                                        KState*, KState*, RedBuf, double, int, cudaStream_t);
-template SolveStats fe_bicgstab<float>(const DevGrid&, const OpDesc<float>&, int, const float*, float*, float*,
-                                       KState*, KState*, RedBuf, double, int, cudaStream_t);
 template void fe_zero<double>(int64_t, double*, cudaStream_t);
 template void fe_zero<float>(int64_t, float*, cudaStream_t);
 template void fe_expand<double>(const DevGrid&, int, double*, cudaStream_t);
+template void fe_expand2<double>(const DevGrid&, int, double*, double*, cudaStream_t);
+template void fe_expand2<float>(const DevGrid&, int, float*, float*, cudaStream_t);
+template void fe_apply_cg<double>(const DevGrid&, const OpDesc<double>&, int, const double*, const double*, double*,
+                                  double*, KState*, RedBuf, cudaStream_t);
+template void fe_apply_cg<float>(const DevGrid&, const OpDesc<float>&, int, const float*, const float*, float*,
+                                 float*, KState*, RedBuf, cudaStream_t);
 template void fe_expand<float>(const DevGrid&, int, float*, cudaStream_t);
 template void fe_sync<double>(const DevGrid&, int, double*, uint16_t, cudaStream_t);
 template void fe_sync<float>(const DevGrid&, int, float*, uint16_t, cudaStream_t);

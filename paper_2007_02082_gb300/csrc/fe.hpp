@@ -14,7 +14,7 @@ enum Op : int { OP_POISSON = 0, OP_MASS = 1, OP_COEF = 2 };
 
 // Scratch for deterministic grid reductions.
 struct RedBuf {
-  double* partials = nullptr;   // >= nblocks * 16 doubles
+  double* partials = nullptr;   // >= nblocks * 16 + ninst * 16 doubles
   unsigned* counter = nullptr;  // one zero-initialised word
 };
 
@@ -65,21 +65,11 @@ void fe_apply(const DevGrid& g, const OpDesc<T>& A, int nc, const T* x, T* y, cu
 template <typename T>
 void fe_jacobi(const DevGrid& g, int op, const T* coef, uint16_t dmask, T* diag, T* dinv, cudaStream_t st);
 
-// Preconditioned CG (symmetric A) on nc right-hand sides.  x holds the initial
-// guess (hanging-consistent, Dirichlet values set) and receives the solution.
-// work: 4 * nc * nslots elements of T.  ks: nc device KState.
+// CG iteration kernel: p_new = z + beta p_old (stored), q = A p_new local per
+// level (no interface sum), fused p.q -> alpha in ks.
 template <typename T>
-SolveStats fe_cg(const DevGrid& g, const OpDesc<T>& A, int nc, const T* b, T* x, T* work, KState* ks,
-                 KState* ks_host, RedBuf rb, double rtol, int max_iter, cudaStream_t st);
-
-// Right-preconditioned BiCGStab, nc right-hand sides.  work: 8 * nc * nslots.
-template <typename T>
-SolveStats fe_bicgstab(const DevGrid& g, const OpDesc<T>& A, int nc, const T* b, T* x, T* work,
-                       KState* ks, KState* ks_host, RedBuf rb, double rtol, int max_iter, cudaStream_t st);
-
-// r = b - A x (masked to DOFs); returns per-component ||r||^2 and ||b||^2 on the host.
-void fe_residual64(const DevGrid& g, const OpDesc<double>& A, int nc, const double* b, const double* x,
-                   double* y, double* r, RedBuf rb, double* host_rr_bb /* [2*nc] */, cudaStream_t st);
+void fe_apply_cg(const DevGrid& g, const OpDesc<T>& A, int nc, const T* z, const T* pold, T* pnew, T* q, KState* ks,
+                 RedBuf rb, cudaStream_t st);
 
 // Elementwise helpers over nc * nslots elements.
 void fe_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t st);
@@ -88,9 +78,11 @@ void fe_copy_d(int64_t n, const double* a, double* b, cudaStream_t st);
 void fe_add_d(int64_t n, const double* a, double* b, cudaStream_t st);   // b += a
 template <typename T> void fe_zero(int64_t n, T* a, cudaStream_t st);
 
-// Hanging nodes take the mean of their parents (nc components).
+// Hanging nodes take the mean of their parents (nc components; x2 optional).
 template <typename T>
 void fe_expand(const DevGrid& g, int nc, T* x, cudaStream_t st);
+template <typename T>
+void fe_expand2(const DevGrid& g, int nc, T* x, T* x2, cudaStream_t st);
 
 // The interface sum: copies of a node get the sum of their local values plus
 // half of each hanging child's; rows with a dmask bit are zeroed.
@@ -99,13 +91,13 @@ void fe_sync(const DevGrid& g, int nc, T* y, uint16_t dmask, cudaStream_t st);
 
 // Right-hand sides and operators built from fields (FP64):
 //   out_c = (M u_c) - dt (G_c p)                              (Eq. 9 / velocity correction)
-//   out   = scale * (div u, q)                                (Eq. 12 with scale = -1/dt)
+//   out   = -(1/dt) (div u, q)                                (Eq. 12)
 //   coef  = M + dt C(u) + dt nu K  as a 15-point stencil       (Eq. 9 operator)
+// with each instance's dt and nu.
 // All are local per level; callers apply fe_sync.
-void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double dt, double* out, cudaStream_t st);
-void fe_rhs_div(const DevGrid& g, const double* u, double scale, double* out, cudaStream_t st);
-void fe_momentum_coef(const DevGrid& g, const double* u, double dt, double nu, double* coef64, float* coef32,
-                      cudaStream_t st);
+void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double* out, cudaStream_t st);
+void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st);
+void fe_momentum_coef(const DevGrid& g, const double* u, double* coef64, float* coef32, cudaStream_t st);
 
 // Copy canonical node values (owner slots) out / in; in also writes the fine
 // copy of every interface node.
@@ -117,11 +109,12 @@ void fe_scatter_canon(const DevGrid& g, int64_t N, const int32_t* canon_slot, in
 
 // Inlet profile u_max(t) * shape on every inlet slot (component = port axis).
 struct PortDev {
-  int32_t axis, nh;
+  int32_t axis, nh, inst, pad;
   double a0, a[8], b[8], period;
 };
 void fe_set_inlet(int64_t n, const int32_t* slot, const int32_t* port, const double* shape, const PortDev* ports,
                   const double* t, int64_t nslots, double* u, cudaStream_t st);
-void fe_time_advance(double* t_commit, double* t_next, double dt, int commit, cudaStream_t st);
+void fe_time_advance(double* t_commit, double* t_next, const double* dt, int n, int commit, const int32_t* ok,
+                     cudaStream_t st);
 
 }  // namespace ibg

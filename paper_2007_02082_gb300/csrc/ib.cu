@@ -8,8 +8,16 @@
 #include <cstring>
 
 #include "ib.hpp"
+#include "krylov.hpp"
 
 namespace ibg {
+
+IBG_KCOUNT_DEFINE
+unsigned long long ib_kcount() {
+  unsigned long long v = 0;
+  cudaMemcpyFromSymbol(&v, g_kcount, sizeof(v));
+  return v;
+}
 
 // Eq. 18
 __device__ __forceinline__ double delta4(double r) {
@@ -20,24 +28,29 @@ __device__ __forceinline__ double delta4(double r) {
 }
 
 __global__ void k_ib_weights(int64_t M, const double* __restrict__ X, const int32_t* __restrict__ org,
-                             const int32_t* __restrict__ slot, double o0, double o1, double o2, double h0,
-                             double h1, double h2, double* __restrict__ W) {
+                             const int32_t* __restrict__ slot, const int32_t* __restrict__ pinst,
+                             const double* __restrict__ iorigin, const double* __restrict__ ihf,
+                             double* __restrict__ W) {
+  KCOUNT();
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= M * 64) return;
   const int64_t i = e >> 6;
   const int a = int(e & 63);
   if (slot[e] < 0) { W[e] = 0.0; return; }
-  const double x = o0 + double(org[3 * i] + (a & 3)) * h0;
-  const double y = o1 + double(org[3 * i + 1] + ((a >> 2) & 3)) * h1;
-  const double z = o2 + double(org[3 * i + 2] + (a >> 4)) * h2;
-  W[e] = delta4((x - X[3 * i]) / h0) * delta4((y - X[3 * i + 1]) / h1) * delta4((z - X[3 * i + 2]) / h2);
+  const double* o = iorigin + 3 * pinst[i];
+  const double* h = ihf + 3 * pinst[i];
+  const double x = o[0] + double(org[3 * i] + (a & 3)) * h[0];
+  const double y = o[1] + double(org[3 * i + 1] + ((a >> 2) & 3)) * h[1];
+  const double z = o[2] + double(org[3 * i + 2] + (a >> 4)) * h[2];
+  W[e] = delta4((x - X[3 * i]) / h[0]) * delta4((y - X[3 * i + 1]) / h[1]) * delta4((z - X[3 * i + 2]) / h[2]);
 }
 
 // one warp per row: S[i,k] = scale * sum over free common support nodes of w_ia w_kb
 __global__ void k_af_values(int64_t M, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                             const int32_t* __restrict__ org, const uint64_t* __restrict__ fb,
-                            const double* __restrict__ W, double scale, double* __restrict__ val,
-                            double* __restrict__ dinv) {
+                            const double* __restrict__ W, const double* __restrict__ pscale,
+                            double* __restrict__ val, double* __restrict__ dinv) {
+  KCOUNT();
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= M) return;
@@ -52,6 +65,7 @@ __global__ void k_af_values(int64_t M, const int32_t* __restrict__ rowptr, const
       const int bb = (bz * 4 + by) * 4 + bx;
       acc += W[i * 64 + a] * W[(int64_t)k * 64 + bb];
     }
+    const double scale = pscale[i];
     val[e] = scale * acc;
     if (k == i) dinv[i] = acc > 0.0 ? 1.0 / (scale * acc) : 0.0;
   }
@@ -61,6 +75,7 @@ __global__ void k_af_values(int64_t M, const int32_t* __restrict__ rowptr, const
 __global__ void k_ib_gather(int64_t M, const int32_t* __restrict__ slot, const double* __restrict__ W,
                             const double* __restrict__ u, int64_t nslots, const double* __restrict__ UB,
                             double* __restrict__ BF) {
+  KCOUNT();
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= M) return;
@@ -93,44 +108,45 @@ __device__ __forceinline__ void spmv_row(int64_t i, int lane, const int32_t* __r
     for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
 }
 
-// q = S p; p.q -> alpha (mode 1) | y = S x (mode 0)
-__global__ void __launch_bounds__(IBB) k_af_apply(int64_t M, const int32_t* __restrict__ rowptr,
-                                                  const int32_t* __restrict__ col, const double* __restrict__ val,
-                                                  const double* __restrict__ p, double* __restrict__ q, int mode,
-                                                  KState* ks, double* partials, unsigned* counter) {
+// q = S p; p.q -> alpha (mode 1) | y = S x (mode 0).  Warp per row, 8 rows per block.
+__global__ void __launch_bounds__(IBB) k_af_apply(IBDev ib, const double* __restrict__ p, double* __restrict__ q,
+                                                  int mode, KState* ks, double* partials, unsigned* counter) {
+  KCOUNT();
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   double acc[3] = {0, 0, 0};
-  if (i < M) spmv_row(i, lane, rowptr, col, val, p, acc);
+  if (i < ib.M) spmv_row(i, lane, ib.rowptr, ib.col, ib.val, p, acc);
   double v[3] = {0, 0, 0};
-  if (i < M && lane == 0)
+  if (i < ib.M && lane == 0)
     for (int c = 0; c < 3; ++c) {
       q[3 * i + c] = acc[c];
       v[c] = p[3 * i + c] * acc[c];
     }
   if (mode == 0) return;
-  double tot[3];
-  if (grid_sum_last<3>(v, partials, counter, tot) && threadIdx.x == 0) {
+  double* out = partials + (int64_t)gridDim.x * 3;
+  if (!grid_sum_last<3>(v, partials, counter, ib.seg_w, ib.ninst, out)) return;
+  for (int n = threadIdx.x; n < ib.ninst; n += blockDim.x)
     for (int c = 0; c < 3; ++c) {
-      KState& k = ks[c];
+      KState& k = ks[n * 3 + c];
       if (k.done) continue;
-      k.pq = tot[c];
-      if (!(tot[c] > 0.0) || !isfinite(tot[c])) { k.done = 1; k.status = 5; k.alpha = 0.0; continue; }
-      k.alpha = k.rz / tot[c];
+      const double pq = out[n * 3 + c];
+      k.pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) { k.done = 1; k.status = 5; k.alpha = 0.0; continue; }
+      k.alpha = k.rz / pq;
     }
-  }
 }
 
-__global__ void __launch_bounds__(IBB) k_af_start(int64_t M, const double* __restrict__ b, const double* __restrict__ y,
+__global__ void __launch_bounds__(IBB) k_af_start(IBDev ib, const double* __restrict__ b, const double* __restrict__ y,
                                                   double* __restrict__ r, double* __restrict__ z,
-                                                  double* __restrict__ p, const double* __restrict__ dinv, KState* ks,
-                                                  double* partials, unsigned* counter) {
+                                                  double* __restrict__ p, KState* ks, double* partials,
+                                                  unsigned* counter, Cond cond) {
+  KCOUNT();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  if (i < M)
+  if (i < ib.M)
     for (int c = 0; c < 3; ++c) {
       const double rv = b[3 * i + c] - y[3 * i + c];
-      const double zv = rv * dinv[i];
+      const double zv = rv * ib.dinv[i];
       r[3 * i + c] = rv;
       z[3 * i + c] = zv;
       p[3 * i + c] = zv;
@@ -138,67 +154,83 @@ __global__ void __launch_bounds__(IBB) k_af_start(int64_t M, const double* __res
       v[3 * c + 1] = rv * rv;
       v[3 * c + 2] = b[3 * i + c] * b[3 * i + c];
     }
-  double tot[9];
-  if (grid_sum_last<9>(v, partials, counter, tot) && threadIdx.x == 0) {
+  double* out = partials + (int64_t)gridDim.x * 9;
+  if (!grid_sum_last<9>(v, partials, counter, ib.seg_t, ib.ninst, out)) return;
+  bool any = false;
+  for (int n = threadIdx.x; n < ib.ninst; n += blockDim.x)
     for (int c = 0; c < 3; ++c) {
-      KState& k = ks[c];
-      k.rz = tot[3 * c];
-      k.rr = tot[3 * c + 1];
-      k.bb = fmax(tot[3 * c + 2], k.rr);
+      KState& k = ks[n * 3 + c];
+      const double* t = out + n * 9 + 3 * c;
+      k.rz = t[0];
+      k.rr = t[1];
+      k.bb = fmax(t[2], k.rr);
       k.iter = 0;
       k.status = 0;
       k.done = (k.rr <= k.tol2 * k.bb) ? 1 : 0;
       if (!isfinite(k.rr)) { k.done = 1; k.status = 5; }
+      any = any || !k.done;
     }
-  }
+  any = __syncthreads_or(any ? 1 : 0) != 0;
+  if (threadIdx.x == 0) set_cond(cond, any);
 }
 
-__global__ void __launch_bounds__(IBB) k_af_update(int64_t M, double* __restrict__ x, double* __restrict__ r,
+__global__ void __launch_bounds__(IBB) k_af_update(IBDev ib, double* __restrict__ x, double* __restrict__ r,
                                                    double* __restrict__ z, const double* __restrict__ p,
-                                                   const double* __restrict__ q, const double* __restrict__ dinv,
-                                                   KState* ks, double* partials, unsigned* counter) {
+                                                   const double* __restrict__ q, KState* ks, double* partials,
+                                                   unsigned* counter, Cond cond) {
+  KCOUNT();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double v[6] = {0, 0, 0, 0, 0, 0};
-  if (i < M)
+  if (i < ib.M) {
+    const KState* ki = ks + ib.pinst[i] * 3;
     for (int c = 0; c < 3; ++c) {
-      if (ks[c].done) continue;
-      const double a = ks[c].alpha;
+      if (ki[c].done) continue;
+      const double a = ki[c].alpha;
       x[3 * i + c] += a * p[3 * i + c];
       const double rv = r[3 * i + c] - a * q[3 * i + c];
-      const double zv = rv * dinv[i];
+      const double zv = rv * ib.dinv[i];
       r[3 * i + c] = rv;
       z[3 * i + c] = zv;
       v[2 * c] = rv * zv;
       v[2 * c + 1] = rv * rv;
     }
-  double tot[6];
-  if (grid_sum_last<6>(v, partials, counter, tot) && threadIdx.x == 0) {
+  }
+  double* out = partials + (int64_t)gridDim.x * 6;
+  if (!grid_sum_last<6>(v, partials, counter, ib.seg_t, ib.ninst, out)) return;
+  bool any = false;
+  for (int n = threadIdx.x; n < ib.ninst; n += blockDim.x)
     for (int c = 0; c < 3; ++c) {
-      KState& k = ks[c];
+      KState& k = ks[n * 3 + c];
       if (k.done) continue;
       k.iter++;
-      k.rr = tot[2 * c + 1];
-      const double rzn = tot[2 * c];
+      k.rr = out[n * 6 + 2 * c + 1];
+      const double rzn = out[n * 6 + 2 * c];
       if (!isfinite(k.rr)) { k.done = 1; k.status = 5; continue; }
       if (k.rr <= k.tol2 * k.bb) { k.done = 1; continue; }
       if (k.iter >= k.max_iter) { k.done = 1; k.status = 4; continue; }
       k.beta = rzn / k.rz;
       k.rz = rzn;
+      any = true;
     }
-  }
+  any = __syncthreads_or(any ? 1 : 0) != 0;
+  if (threadIdx.x == 0) set_cond(cond, any);
 }
 
-__global__ void k_af_p(int64_t M, const double* __restrict__ z, double* __restrict__ p, const KState* ks) {
+__global__ void k_af_p(IBDev ib, const double* __restrict__ z, double* __restrict__ p, const KState* ks) {
+  KCOUNT();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= M) return;
+  if (i >= ib.M) return;
+  const KState* ki = ks + ib.pinst[i] * 3;
   for (int c = 0; c < 3; ++c)
-    if (!ks[c].done) p[3 * i + c] = z[3 * i + c] + ks[c].beta * p[3 * i + c];
+    if (!ki[c].done) p[3 * i + c] = z[3 * i + c] + ki[c].beta * p[3 * i + c];
 }
 
 // one thread per free support node: u += coef * sum_e W[ent] G[point(ent)]
 __global__ void k_ib_spread(int64_t n, const int32_t* __restrict__ sp_slot, const int32_t* __restrict__ sp_off,
                             const int32_t* __restrict__ sp_ent, const double* __restrict__ W,
-                            const double* __restrict__ G, double coef, double* __restrict__ u, int64_t nslots) {
+                            const double* __restrict__ G, const int32_t* __restrict__ binst,
+                            const double* __restrict__ icoef, double* __restrict__ u, int64_t nslots) {
+  KCOUNT();
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n) return;
   double acc[3] = {0, 0, 0};
@@ -209,22 +241,23 @@ __global__ void k_ib_spread(int64_t n, const int32_t* __restrict__ sp_slot, cons
     for (int c = 0; c < 3; ++c) acc[c] += w * G[3 * i + c];
   }
   const int32_t s = sp_slot[j];
+  const double coef = icoef[binst[s >> 9]];
   for (int c = 0; c < 3; ++c) u[c * nslots + s] += coef * acc[c];
 }
 
 // ---------------------------------------------------------------- host wrappers
-void ib_weights(const IBDev& ib, const double origin[3], const double hf[3], cudaStream_t st) {
+void ib_weights(const IBDev& ib, cudaStream_t st) {
   if (ib.M == 0) return;
   const int64_t n = ib.M * 64;
-  IBG_LAUNCH(k_ib_weights, int((n + 255) / 256), 256, 0, st, ib.M, ib.X, ib.org, ib.slot, origin[0], origin[1], origin[2],
-                                                     hf[0], hf[1], hf[2], ib.W);
+  IBG_LAUNCH(k_ib_weights, int((n + 255) / 256), 256, 0, st, ib.M, ib.X, ib.org, ib.slot, ib.pinst, ib.iorigin,
+             ib.ihf, ib.W);
 }
 
-void ib_assemble(const IBDev& ib, double scale, cudaStream_t st) {
+void ib_assemble(const IBDev& ib, cudaStream_t st) {
   if (ib.M == 0) return;
   const int64_t th = ib.M * 32;
-  IBG_LAUNCH(k_af_values, int((th + 255) / 256), 256, 0, st, ib.M, ib.rowptr, ib.col, ib.org, ib.freeb, ib.W, scale, ib.val,
-                                                     ib.dinv);
+  IBG_LAUNCH(k_af_values, int((th + 255) / 256), 256, 0, st, ib.M, ib.rowptr, ib.col, ib.org, ib.freeb, ib.W,
+             ib.pscale, ib.val, ib.dinv);
 }
 
 void ib_gather(const IBDev& ib, const double* u, int64_t nslots, const double* UB, double* BF, cudaStream_t st) {
@@ -233,56 +266,36 @@ void ib_gather(const IBDev& ib, const double* u, int64_t nslots, const double* U
   IBG_LAUNCH(k_ib_gather, int((th + 255) / 256), 256, 0, st, ib.M, ib.slot, ib.W, u, nslots, UB, BF);
 }
 
-SolveStats ib_solve(const IBDev& ib, const double* BF, double* G, double* work, KState* ks, KState* ks_host,
-                    RedBuf rb, double rtol, int max_iter, cudaStream_t st) {
-  SolveStats S;
-  if (ib.M == 0) return S;
+cudaError_t ib_solve(const IBDev& ib, const double* BF, double* G, double* work, KState* ks, KState* ks_host,
+                     RedBuf rb, double rtol, int max_iter, SolveRec* rec, cudaStream_t st, CaptureCtx* cc) {
+  if (ib.M == 0) return cudaSuccess;
   const int64_t L = 3 * ib.M;
   double *r = work, *z = work + L, *p = work + 2 * L, *q = work + 3 * L;
-  for (int c = 0; c < 3; ++c) {
-    std::memset(&ks_host[c], 0, sizeof(KState));
-    ks_host[c].tol2 = rtol * rtol;
-    ks_host[c].max_iter = max_iter;
+  IBG_LAUNCH(k_init_states, (ib.ninst * 3 + 127) / 128, 128, 0, st, ks, ib.ninst * 3, rtol * rtol, max_iter);
+  Cond cond;
+  if (cc && cc->capturing) {
+    cudaError_t e = cond_handle(st, 0, &cond);
+    if (e != cudaSuccess) return e;
   }
-  cudaMemcpyAsync(ks, ks_host, 3 * sizeof(KState), cudaMemcpyHostToDevice, st);
   const int gw = int((ib.M * 32 + IBB - 1) / IBB);   // warp-per-row grids
   const int gt = int((ib.M + IBB - 1) / IBB);        // thread-per-row grids
-  IBG_LAUNCH(k_af_apply, gw, IBB, 0, st, ib.M, ib.rowptr, ib.col, ib.val, G, q, 0, ks, rb.partials, rb.counter);
-  IBG_LAUNCH(k_af_start, gt, IBB, 0, st, ib.M, BF, q, r, z, p, ib.dinv, ks, rb.partials, rb.counter);
-  int it = 0, chunk = 8;
-  bool done = false;
-  auto poll = [&]() {
-    cudaMemcpyAsync(ks_host, ks, 3 * sizeof(KState), cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
-    done = true;
-    S = SolveStats();
-    for (int c = 0; c < 3; ++c) {
-      S.iters[c] = ks_host[c].iter;
-      if (!ks_host[c].done) done = false;
-      if (ks_host[c].status) S.status = ks_host[c].status;
-      double rel = ks_host[c].bb > 0 ? std::sqrt(std::max(ks_host[c].rr, 0.0) / ks_host[c].bb) : 0.0;
-      S.relres = std::max(S.relres, rel);
-    }
-  };
-  poll();
-  while (!done) {
-    for (int k = 0; k < chunk; ++k) {
-      IBG_LAUNCH(k_af_apply, gw, IBB, 0, st, ib.M, ib.rowptr, ib.col, ib.val, p, q, 1, ks, rb.partials, rb.counter);
-      IBG_LAUNCH(k_af_update, gt, IBB, 0, st, ib.M, G, r, z, p, q, ib.dinv, ks, rb.partials, rb.counter);
-      IBG_LAUNCH(k_af_p, gt, IBB, 0, st, ib.M, z, p, ks);
-    }
-    it += chunk;
-    chunk = std::min(chunk * 2, 64);
-    poll();
-    if (it > max_iter + 128) break;
-  }
-  return S;
+  IBG_LAUNCH(k_af_apply, gw, IBB, 0, st, ib, G, q, 0, ks, rb.partials, rb.counter);
+  IBG_LAUNCH(k_af_start, gt, IBB, 0, st, ib, BF, q, r, z, p, ks, rb.partials, rb.counter, cond);
+  cudaError_t e = run_loop(cc, st, cond, ks, ks_host, ib.ninst * 3, max_iter, 8, 64,
+                           [&](cudaStream_t s, const Cond& c) {
+    IBG_LAUNCH(k_af_apply, gw, IBB, 0, s, ib, p, q, 1, ks, rb.partials, rb.counter);
+    IBG_LAUNCH(k_af_update, gt, IBB, 0, s, ib, G, r, z, p, q, ks, rb.partials, rb.counter, c);
+    IBG_LAUNCH(k_af_p, gt, IBB, 0, s, ib, z, p, ks);
+  });
+  if (e != cudaSuccess) return e;
+  IBG_LAUNCH(k_collect, (ib.ninst + 127) / 128, 128, 0, st, ks, 3, ib.ninst, rec, (OState*)nullptr);
+  return cudaSuccess;
 }
 
-void ib_spread(const IBDev& ib, const double* G, double coef, double* u, int64_t nslots, cudaStream_t st) {
+void ib_spread(const IBDev& ib, const double* G, double* u, int64_t nslots, cudaStream_t st) {
   if (ib.n_sp == 0) return;
-  IBG_LAUNCH(k_ib_spread, int((ib.n_sp + 255) / 256), 256, 0, st, ib.n_sp, ib.sp_slot, ib.sp_off, ib.sp_ent, ib.W, G, coef,
-                                                          u, nslots);
+  IBG_LAUNCH(k_ib_spread, int((ib.n_sp + 255) / 256), 256, 0, st, ib.n_sp, ib.sp_slot, ib.sp_off, ib.sp_ent, ib.W, G,
+             ib.binst, ib.icoef, u, nslots);
 }
 
 }  // namespace ibg

@@ -6,11 +6,25 @@
 
 #include "device.cuh"
 #include "fe.hpp"
+#include "graph.hpp"
 
 namespace ibg {
 
+// Points of all instances, each instance's rows padded to a multiple of 256
+// (padding rows have no support and no A_F entries), so that both the
+// thread-per-row (256 rows per block) and warp-per-row (8 rows per block)
+// kernels have whole blocks per instance for segmented reductions.
 struct IBDev {
-  int64_t M;
+  int64_t M;               // padded total
+  int32_t ninst;
+  const int32_t* pinst;    // [M] instance of each row
+  const int32_t* seg_t;    // [ninst + 1] block range, 256 rows per block
+  const int32_t* seg_w;    // [ninst + 1] block range, 8 rows per block
+  const double* pscale;    // [M] dt / (rho h^3) of the row's instance
+  const double* iorigin;   // [ninst][3] box origin
+  const double* ihf;       // [ninst][3] finest spacing
+  const double* icoef;     // [ninst] spreading coefficient dt / (rho h^3)
+  const int32_t* binst;    // [nbricks] instance of a brick (for spreading)
   const double* X;         // [M][3]
   const int32_t* org;      // [M][3] support origin, finest grid
   const int32_t* slot;     // [M][64] slot of support node a (-1 missing)
@@ -27,15 +41,17 @@ struct IBDev {
 };
 
 // Eq. 17-18: W[i][a] = phi((x_a - X_i)/hx) phi((y_a - Y_i)/hy) phi((z_a - Z_i)/hz).
-void ib_weights(const IBDev& ib, const double origin[3], const double hf[3], cudaStream_t st);
+void ib_weights(const IBDev& ib, cudaStream_t st);
 // S = (dt/(rho h^3)) W_f W_f^T over free nodes (Eq. 22); dinv = 1/diag.
-void ib_assemble(const IBDev& ib, double scale, cudaStream_t st);
+void ib_assemble(const IBDev& ib, cudaStream_t st);
 // B_F = U_B - W u (Eq. 23), u on the finest level ([3][nslots]).
 void ib_gather(const IBDev& ib, const double* u, int64_t nslots, const double* UB, double* BF, cudaStream_t st);
-// PCG on S G = B_F for the 3 components ([M][3]); G holds the warm start.
-SolveStats ib_solve(const IBDev& ib, const double* BF, double* G, double* work /* 4*3*M */, KState* ks,
-                    KState* ks_host, RedBuf rb, double rtol, int max_iter, cudaStream_t st);
+// PCG on S G = B_F for the 3 components ([M][3]); G holds the warm start.  The
+// loop is a graph WHILE node when st is capturing; the result goes to rec.
+cudaError_t ib_solve(const IBDev& ib, const double* BF, double* G, double* work /* 4*3*M */, KState* ks,
+                     KState* ks_host, RedBuf rb, double rtol, int max_iter, SolveRec* rec, cudaStream_t st,
+                     CaptureCtx* cc);
 // u_j += coef * sum_i W[i][a(j)] G_i on free support nodes (Eq. 19, Eq. 14).
-void ib_spread(const IBDev& ib, const double* G, double coef, double* u, int64_t nslots, cudaStream_t st);
+void ib_spread(const IBDev& ib, const double* G, double* u, int64_t nslots, cudaStream_t st);
 
 }  // namespace ibg

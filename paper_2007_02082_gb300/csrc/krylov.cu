@@ -1,0 +1,606 @@
+// Krylov solvers of the IPCS step.  The linear solvers are not stated in the
+// paper (Sec. 2.2); these are the build's choice: Jacobi-preconditioned CG for
+// the symmetric Poisson (Eq. 12) and mass systems, right-preconditioned
+// BiCGStab for the nonsymmetric Oseen system (Eq. 9).
+//
+// CG iteration (2 or 3 kernels):
+//   k_apply (fe.cu): p_new = z + beta p_old on the brick tile, q = A p_new
+//                    (local per level), fused p.q -> alpha;
+//   k_cg_update:     interface sum of q fused in, x += alpha p, r -= alpha q,
+//                    z = D^-1 r, FP64 r.z and r.r -> beta, convergence, loop
+//                    condition;
+//   k_expand:        hanging z = mean of parents (refined grids only).
+// The search direction ping-pongs between two buffers, so a loop body holds two
+// iterations.  All inner products accumulate in FP64 in a fixed order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "krylov.hpp"
+
+namespace ibg {
+
+IBG_KCOUNT_DEFINE
+unsigned long long krylov_kcount() {
+  unsigned long long v = 0;
+  cudaMemcpyFromSymbol(&v, g_kcount, sizeof(v));
+  return v;
+}
+
+__device__ __forceinline__ bool kdof(uint16_t m, uint16_t dmask) {
+  return (m & D_VALID) && !(m & (D_HANG | D_DUP | dmask));
+}
+__device__ __forceinline__ bool kkeep(uint16_t m, uint16_t dmask) {
+  return (m & D_VALID) && !(m & (D_HANG | dmask));
+}
+
+// block-wide OR of a per-thread flag, result valid in every thread
+__device__ __forceinline__ bool block_any(bool v) { return __syncthreads_or(v ? 1 : 0) != 0; }
+
+__global__ void k_init_states(KState* ks, int nc, double tol2, int max_iter) {
+  KCOUNT();
+  const int c = threadIdx.x + blockIdx.x * blockDim.x;
+  if (c >= nc) return;
+  KState k;
+  memset(&k, 0, sizeof(k));
+  k.tol2 = tol2;
+  k.max_iter = max_iter;
+  ks[c] = k;
+}
+
+// record a finished solve of every instance (rec[i * 4], os[i]); with os set
+// (inner solve of a defect-correction loop) iterations accumulate and a
+// breakdown stops the outer loop
+__global__ void k_collect(const KState* ks, int nc, int ninst, SolveRec* rec, OState* os) {
+  KCOUNT();
+  const int i = threadIdx.x + blockIdx.x * blockDim.x;
+  if (i >= ninst) return;
+  SolveRec& R = rec[i * 4];
+  double rel = 0.0;
+  int st = R.status;
+  for (int c = 0; c < nc; ++c) {
+    const KState& k = ks[i * nc + c];
+    R.iters[c] += k.iter;
+    st = max(st, k.status);
+    if (k.bb > 0) rel = fmax(rel, sqrt(fmax(k.rr, 0.0) / k.bb));
+  }
+  if (os) {
+    if (st == 5) { os[i].inner_status = 5; R.status = 5; }
+  } else {
+    R.status = st;
+    R.relres = rel;
+    R.outer = 1;
+  }
+}
+
+__global__ void k_init_outer(OState* os, int ninst, int nc, double tol2, int max_outer) {
+  KCOUNT();
+  const int i = threadIdx.x + blockIdx.x * blockDim.x;
+  if (i >= ninst) return;
+  OState o;
+  memset(&o, 0, sizeof(o));
+  o.tol2 = tol2;
+  o.max_iter = max_outer;
+  o.nc = nc;
+  os[i] = o;
+}
+
+__global__ void k_collect_outer(const OState* os, int ninst, SolveRec* rec) {
+  KCOUNT();
+  const int i = threadIdx.x + blockIdx.x * blockDim.x;
+  if (i >= ninst) return;
+  SolveRec& R = rec[i * 4];
+  R.outer = os[i].iter;
+  R.relres = sqrt(fmax(os[i].rel2, 0.0));
+  R.status = max(R.status, os[i].status);
+}
+
+// ---------------------------------------------------------------- CG
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict__ b, const T* __restrict__ y,
+                                                  T* __restrict__ r, T* __restrict__ z, T* __restrict__ p,
+                                                  const T* __restrict__ dinv, uint16_t dmask, KState* ks,
+                                                  double* partials, unsigned* counter, Cond cond,
+                                                  const OState* skip_os) {
+  KCOUNT();
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
+  double v[3 * NC];
+  for (int c = 0; c < NC; ++c) {
+    const int64_t i = c * g.nslots + s;
+    T rv = keep ? T(b[i] - y[i]) : T(0);
+    T zv = rv * dinv[s];
+    r[i] = rv;
+    z[i] = zv;
+    p[i] = zv;
+    v[3 * c] = dof ? double(rv) * double(zv) : 0.0;
+    v[3 * c + 1] = dof ? double(rv) * double(rv) : 0.0;
+    v[3 * c + 2] = dof ? double(b[i]) * double(b[i]) : 0.0;
+  }
+  double* out = partials + (int64_t)gridDim.x * 3 * NC;
+  if (!grid_sum_last<3 * NC>(v, partials, counter, g.bseg, g.ninst, out)) return;
+  bool any = false;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
+    const bool skip = skip_os && skip_os[i].done;
+    for (int c = 0; c < NC; ++c) {
+      KState& k = ks[i * NC + c];
+      const double* t = out + (int64_t)i * 3 * NC + 3 * c;
+      k.rz = t[0];
+      k.rr = t[1];
+      // reference norm max(||b||, ||r0||): covers a zero right-hand side with a
+      // nonzero Dirichlet lifting as well as warm starts
+      k.bb = fmax(t[2], k.rr);
+      k.iter = 0;
+      k.status = 0;
+      k.alpha = 0.0;
+      k.beta = 0.0;
+      k.done = (skip || k.rr <= k.tol2 * k.bb) ? 1 : 0;
+      if (!skip && !isfinite(k.rr)) { k.done = 1; k.status = 5; }
+      any = any || !k.done;
+    }
+  }
+  any = block_any(any);
+  if (threadIdx.x == 0) set_cond(cond, any);
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_cg_update(DevGrid g, T* __restrict__ x, T* __restrict__ r,
+                                                   T* __restrict__ z, const T* __restrict__ p,
+                                                   const T* __restrict__ q, const T* __restrict__ dinv,
+                                                   uint16_t dmask, KState* ks, double* partials, unsigned* counter,
+                                                   Cond cond) {
+  KCOUNT();
+  const KState* ki = ks + g.binst[blockIdx.x] * NC;
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
+  double v[2 * NC];
+  for (int c = 0; c < NC; ++c) {
+    v[2 * c] = v[2 * c + 1] = 0.0;
+    if (ki[c].done) continue;
+    const T a = T(ki[c].alpha);
+    const T* qc = q + c * g.nslots;
+    const int64_t i = c * g.nslots + s;
+    T qv = qc[s];
+    if (m & D_IFACE) {   // interface sum: both copies + half of each hanging child
+      const int e = g.if_of_slot[s];
+      qv = qc[g.if_c[e]] + qc[g.if_f[e]];
+      for (int k = g.if_off[e]; k < g.if_off[e + 1]; ++k) qv += T(0.5) * qc[g.if_kid[k]];
+    }
+    if (m & D_VALID) x[i] += a * p[i];
+    T rv = keep ? T(r[i] - a * qv) : T(0);
+    T zv = rv * dinv[s];
+    r[i] = rv;
+    z[i] = zv;
+    if (dof) {
+      v[2 * c] = double(rv) * double(zv);
+      v[2 * c + 1] = double(rv) * double(rv);
+    }
+  }
+  double* out = partials + (int64_t)gridDim.x * 2 * NC;
+  if (!grid_sum_last<2 * NC>(v, partials, counter, g.bseg, g.ninst, out)) return;
+  bool any = false;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
+    for (int c = 0; c < NC; ++c) {
+      KState& k = ks[i * NC + c];
+      if (k.done) continue;
+      k.iter++;
+      k.rr = out[(int64_t)i * 2 * NC + 2 * c + 1];
+      const double rzn = out[(int64_t)i * 2 * NC + 2 * c];
+      if (!isfinite(k.rr) || !isfinite(rzn)) { k.done = 1; k.status = 5; continue; }
+      if (k.rr <= k.tol2 * k.bb) { k.done = 1; continue; }
+      if (k.iter >= k.max_iter) { k.done = 1; k.status = 4; continue; }
+      k.beta = rzn / k.rz;
+      k.rz = rzn;
+      any = true;
+    }
+  any = block_any(any);
+  if (threadIdx.x == 0) set_cond(cond, any);
+}
+
+// ---------------------------------------------------------------- BiCGStab
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restrict__ b, const T* __restrict__ y,
+                                                   T* __restrict__ r, T* __restrict__ rh, T* __restrict__ p,
+                                                   T* __restrict__ v, uint16_t dmask, KState* ks,
+                                                   double* partials, unsigned* counter, Cond cond,
+                                                   const OState* skip_os) {
+  KCOUNT();
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
+  double w[2 * NC];
+  for (int c = 0; c < NC; ++c) {
+    const int64_t i = c * g.nslots + s;
+    T rv = keep ? T(b[i] - y[i]) : T(0);
+    r[i] = rv;
+    rh[i] = rv;
+    p[i] = T(0);
+    v[i] = T(0);
+    w[2 * c] = dof ? double(rv) * double(rv) : 0.0;
+    w[2 * c + 1] = dof ? double(b[i]) * double(b[i]) : 0.0;
+  }
+  double* out = partials + (int64_t)gridDim.x * 2 * NC;
+  if (!grid_sum_last<2 * NC>(w, partials, counter, g.bseg, g.ninst, out)) return;
+  bool any = false;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
+    const bool skip = skip_os && skip_os[i].done;
+    for (int c = 0; c < NC; ++c) {
+      KState& k = ks[i * NC + c];
+      k.rr = out[(int64_t)i * 2 * NC + 2 * c];
+      k.bb = fmax(out[(int64_t)i * 2 * NC + 2 * c + 1], k.rr);
+      k.rho = k.rr;
+      k.alpha = 1.0;
+      k.omega = 1.0;
+      k.beta = 0.0;
+      k.iter = 0;
+      k.status = 0;
+      k.done = (skip || k.rr <= k.tol2 * k.bb) ? 1 : 0;
+      if (!skip && !isfinite(k.rr)) { k.done = 1; k.status = 5; }
+      any = any || !k.done;
+    }
+  }
+  any = block_any(any);
+  if (threadIdx.x == 0) set_cond(cond, any);
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_bcg_p(DevGrid g, const T* __restrict__ r, T* __restrict__ p,
+                                               const T* __restrict__ v, T* __restrict__ ph,
+                                               const T* __restrict__ dinv, uint16_t dmask, const KState* ks) {
+  KCOUNT();
+  const KState* ki = ks + g.binst[blockIdx.x] * NC;
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool keep = kkeep(m, dmask);
+  for (int c = 0; c < NC; ++c) {
+    if (ki[c].done) continue;
+    const int64_t i = c * g.nslots + s;
+    T pv = keep ? T(r[i] + T(ki[c].beta) * (p[i] - T(ki[c].omega) * v[i])) : T(0);
+    p[i] = pv;
+    ph[i] = pv * dinv[s];
+  }
+}
+
+// mode 0: alpha = rho / (rh, v);  mode 1: omega = (t, s) / (t, t)
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_bcg_dot(DevGrid g, const T* __restrict__ a1, const T* __restrict__ b1,
+                                                 const T* __restrict__ a2, uint16_t dmask, int mode, KState* ks,
+                                                 double* partials, unsigned* counter) {
+  KCOUNT();
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = kdof(m, dmask);
+  double w[2 * NC];
+  for (int c = 0; c < NC; ++c) {
+    const int64_t i = c * g.nslots + s;
+    w[2 * c] = dof ? double(a1[i]) * double(b1[i]) : 0.0;
+    w[2 * c + 1] = (dof && mode == 1) ? double(a2[i]) * double(a2[i]) : 0.0;
+  }
+  double* out = partials + (int64_t)gridDim.x * 2 * NC;
+  if (!grid_sum_last<2 * NC>(w, partials, counter, g.bseg, g.ninst, out)) return;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
+    for (int c = 0; c < NC; ++c) {
+      KState& k = ks[i * NC + c];
+      if (k.done) continue;
+      const double t0 = out[(int64_t)i * 2 * NC + 2 * c], t1 = out[(int64_t)i * 2 * NC + 2 * c + 1];
+      if (mode == 0) {
+        k.rv = t0;
+        if (k.rv == 0.0 || !isfinite(k.rv)) { k.done = 1; k.status = 5; k.alpha = 0.0; continue; }
+        k.alpha = k.rho / k.rv;
+      } else {
+        k.ts = t0;
+        k.tt = t1;
+        k.omega = (k.tt > 0.0) ? k.ts / k.tt : 0.0;
+      }
+    }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_bcg_s(DevGrid g, const T* __restrict__ r, const T* __restrict__ v,
+                                               T* __restrict__ sv, T* __restrict__ sh, const T* __restrict__ dinv,
+                                               uint16_t dmask, const KState* ks) {
+  KCOUNT();
+  const KState* ki = ks + g.binst[blockIdx.x] * NC;
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool keep = kkeep(m, dmask);
+  for (int c = 0; c < NC; ++c) {
+    if (ki[c].done) continue;
+    const int64_t i = c * g.nslots + s;
+    T val = keep ? T(r[i] - T(ki[c].alpha) * v[i]) : T(0);
+    sv[i] = val;
+    sh[i] = val * dinv[s];
+  }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_bcg_xr(DevGrid g, T* __restrict__ x, T* __restrict__ r,
+                                                const T* __restrict__ rh, const T* __restrict__ ph,
+                                                const T* __restrict__ sh, const T* __restrict__ sv,
+                                                const T* __restrict__ tv, uint16_t dmask, KState* ks,
+                                                double* partials, unsigned* counter, Cond cond) {
+  KCOUNT();
+  const KState* ki = ks + g.binst[blockIdx.x] * NC;
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
+  double w[2 * NC];
+  for (int c = 0; c < NC; ++c) {
+    w[2 * c] = w[2 * c + 1] = 0.0;
+    if (ki[c].done) continue;
+    const int64_t i = c * g.nslots + s;
+    const T al = T(ki[c].alpha), om = T(ki[c].omega);
+    if (m & D_VALID) x[i] += al * ph[i] + om * sh[i];
+    T rv = keep ? T(sv[i] - om * tv[i]) : T(0);
+    r[i] = rv;
+    if (dof) {
+      w[2 * c] = double(rv) * double(rv);
+      w[2 * c + 1] = double(rh[i]) * double(rv);
+    }
+  }
+  double* out = partials + (int64_t)gridDim.x * 2 * NC;
+  if (!grid_sum_last<2 * NC>(w, partials, counter, g.bseg, g.ninst, out)) return;
+  bool any = false;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
+    for (int c = 0; c < NC; ++c) {
+      KState& k = ks[i * NC + c];
+      if (k.done) continue;
+      k.iter++;
+      k.rr = out[(int64_t)i * 2 * NC + 2 * c];
+      const double rhon = out[(int64_t)i * 2 * NC + 2 * c + 1];
+      if (!isfinite(k.rr)) { k.done = 1; k.status = 5; continue; }
+      if (k.rr <= k.tol2 * k.bb) { k.done = 1; continue; }
+      if (k.iter >= k.max_iter) { k.done = 1; k.status = 4; continue; }
+      if (k.omega == 0.0 || rhon == 0.0 || !isfinite(rhon)) { k.done = 1; k.status = 5; continue; }
+      k.beta = (rhon / k.rho) * (k.alpha / k.omega);
+      k.rho = rhon;
+      any = true;
+    }
+  any = block_any(any);
+  if (threadIdx.x == 0) set_cond(cond, any);
+}
+
+// ---------------------------------------------------------------- FP64 outer loop
+// r = b - y on DOF rows; the first pass fixes the reference norm; sets the
+// outer loop condition and the condition of the inner-solve branch.
+template <int NC>
+__global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double* __restrict__ b,
+                                                        const double* __restrict__ y, double* __restrict__ r,
+                                                        uint16_t dmask, OState* os, double* partials,
+                                                        unsigned* counter, Cond cloop, Cond cbranch) {
+  KCOUNT();
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
+  double w[2 * NC];
+  for (int c = 0; c < NC; ++c) {
+    const int64_t i = c * g.nslots + s;
+    double rv = keep ? b[i] - y[i] : 0.0;
+    r[i] = rv;
+    w[2 * c] = dof ? rv * rv : 0.0;
+    w[2 * c + 1] = dof ? b[i] * b[i] : 0.0;
+  }
+  double* out = partials + (int64_t)gridDim.x * 2 * NC;
+  if (!grid_sum_last<2 * NC>(w, partials, counter, g.bseg, g.ninst, out)) return;
+  bool any = false;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
+    OState& o = os[i];
+    if (o.done) continue;
+    double rel2 = 0.0;
+    bool finite = true;
+    for (int c = 0; c < NC; ++c) {
+      const double rr = out[(int64_t)i * 2 * NC + 2 * c], bb = out[(int64_t)i * 2 * NC + 2 * c + 1];
+      if (o.iter == 0) o.ref[c] = fmax(bb, rr);
+      if (!isfinite(rr)) finite = false;
+      if (o.ref[c] > 0.0) rel2 = fmax(rel2, rr / o.ref[c]);
+    }
+    o.rel2 = rel2;
+    if (!finite || o.inner_status == 5) { o.done = 1; o.status = 5; }
+    else if (rel2 <= o.tol2) o.done = 1;
+    else if (o.iter >= o.max_iter) { o.done = 1; o.status = 4; }
+    if (!o.done) { o.iter++; any = true; }
+  }
+  any = block_any(any);
+  if (threadIdx.x == 0) {
+    set_cond(cloop, any);
+    set_cond(cbranch, any);
+  }
+}
+
+// x += e only for instances whose outer loop is still running
+__global__ void k_add_f2d_active(DevGrid g, const float* __restrict__ e, double* __restrict__ x, int nc,
+                                 const OState* os) {
+  KCOUNT();
+  if (os[g.binst[blockIdx.x]].done) return;
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  for (int c = 0; c < nc; ++c) x[c * g.nslots + s] += double(e[c * g.nslots + s]);
+}
+
+// ---------------------------------------------------------------- drivers
+template <typename T>
+struct Work {
+  T *r, *z, *pa, *pb, *q;            // CG
+  T *rh, *p, *v, *sv, *tv, *ph, *sh; // BiCGStab (r shared)
+};
+
+template <typename T>
+static Work<T> carve(T* w, int64_t L) {
+  Work<T> k;
+  k.r = w;
+  k.z = w + L;
+  k.pa = w + 2 * L;
+  k.pb = w + 3 * L;
+  k.q = w + 4 * L;
+  k.rh = w + L;
+  k.p = w + 2 * L;
+  k.v = w + 3 * L;
+  k.sv = w + 4 * L;
+  k.tv = w + 5 * L;
+  k.ph = w + 6 * L;
+  k.sh = w + 7 * L;
+  return k;
+}
+
+static inline void pbegin(Prof* p, int c, cudaStream_t s) { if (p && p->on) p->begin(c, s); }
+static inline void pend(Prof* p, cudaStream_t s) { if (p && p->on) p->end(s); }
+
+// one CG solve of A x = b in precision T (x: initial guess in, solution out)
+template <typename T, int NC>
+static cudaError_t cg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b, T* x, T* work, cudaStream_t st,
+                              CaptureCtx* cc, double rtol, const OState* skip_os) {
+  const DevGrid& g = *a.g;
+  const int64_t L = int64_t(NC) * g.nslots;
+  Work<T> w = carve(work, L);
+  RedBuf rb = a.rb;
+  IBG_LAUNCH(k_init_states, (g.ninst * NC + 127) / 128, 128, 0, st, a.ks, g.ninst * NC, rtol * rtol, a.max_iter);
+  Cond cond;
+  const bool cap = cc && cc->capturing;
+  if (cap) {
+    cudaError_t e = cond_handle(st, 0, &cond);
+    if (e != cudaSuccess) return e;
+  }
+  fe_apply<T>(g, A, NC, x, w.q, st);
+  IBG_LAUNCH((k_cg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, w.q, w.r, w.z, w.pa, A.dinv, A.dmask, a.ks,
+             rb.partials, rb.counter, cond, skip_os);
+  fe_expand2<T>(g, NC, w.z, w.pa, st);
+  auto iter = [&](cudaStream_t s, const Cond& c, T* pold, T* pnew) {
+    pbegin(a.prof, a.pbase + 0, s);
+    fe_apply_cg<T>(g, A, NC, w.z, pold, pnew, w.q, a.ks, rb, s);
+    pend(a.prof, s);
+    pbegin(a.prof, a.pbase + 1, s);
+    IBG_LAUNCH((k_cg_update<T, NC>), g.nbricks, DBV, 0, s, g, x, w.r, w.z, pnew, w.q, A.dinv, A.dmask, a.ks,
+               rb.partials, rb.counter, c);
+    pend(a.prof, s);
+    fe_expand2<T>(g, NC, w.z, (T*)nullptr, s);
+  };
+  return run_loop(cc, st, cond, a.ks, a.ks_host, g.ninst * NC, a.max_iter, 2, 16, [&](cudaStream_t s, const Cond& c) {
+    iter(s, c, w.pa, w.pb);
+    iter(s, c, w.pb, w.pa);
+  });
+}
+
+template <typename T, int NC>
+static cudaError_t bcg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b, T* x, T* work, cudaStream_t st,
+                               CaptureCtx* cc, double rtol, const OState* skip_os) {
+  const DevGrid& g = *a.g;
+  const int64_t L = int64_t(NC) * g.nslots;
+  Work<T> w = carve(work, L);
+  RedBuf rb = a.rb;
+  IBG_LAUNCH(k_init_states, (g.ninst * NC + 127) / 128, 128, 0, st, a.ks, g.ninst * NC, rtol * rtol, a.max_iter);
+  Cond cond;
+  if (cc && cc->capturing) {
+    cudaError_t e = cond_handle(st, 0, &cond);
+    if (e != cudaSuccess) return e;
+  }
+  fe_apply<T>(g, A, NC, x, w.tv, st);
+  IBG_LAUNCH((k_bcg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, w.tv, w.r, w.rh, w.p, w.v, A.dmask, a.ks,
+             rb.partials, rb.counter, cond, skip_os);
+  return run_loop(cc, st, cond, a.ks, a.ks_host, g.ninst * NC, a.max_iter, 1, 8, [&](cudaStream_t s, const Cond& c) {
+    IBG_LAUNCH((k_bcg_p<T, NC>), g.nbricks, DBV, 0, s, g, w.r, w.p, w.v, w.ph, A.dinv, A.dmask, a.ks);
+    fe_expand2<T>(g, NC, w.ph, (T*)nullptr, s);
+    pbegin(a.prof, a.pbase + 0, s);
+    fe_apply<T>(g, A, NC, w.ph, w.v, s);
+    pend(a.prof, s);
+    IBG_LAUNCH((k_bcg_dot<T, NC>), g.nbricks, DBV, 0, s, g, w.rh, w.v, w.v, A.dmask, 0, a.ks, rb.partials,
+               rb.counter);
+    IBG_LAUNCH((k_bcg_s<T, NC>), g.nbricks, DBV, 0, s, g, w.r, w.v, w.sv, w.sh, A.dinv, A.dmask, a.ks);
+    fe_expand2<T>(g, NC, w.sh, (T*)nullptr, s);
+    pbegin(a.prof, a.pbase + 0, s);
+    fe_apply<T>(g, A, NC, w.sh, w.tv, s);
+    pend(a.prof, s);
+    IBG_LAUNCH((k_bcg_dot<T, NC>), g.nbricks, DBV, 0, s, g, w.tv, w.sv, w.tv, A.dmask, 1, a.ks, rb.partials,
+               rb.counter);
+    pbegin(a.prof, a.pbase + 1, s);
+    IBG_LAUNCH((k_bcg_xr<T, NC>), g.nbricks, DBV, 0, s, g, x, w.r, w.rh, w.ph, w.sh, w.sv, w.tv, A.dmask, a.ks,
+               rb.partials, rb.counter, c);
+    pend(a.prof, s);
+  });
+}
+
+template <typename T>
+static cudaError_t inner_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b, T* x, T* work, cudaStream_t st,
+                                 CaptureCtx* cc, double rtol, const OState* skip_os) {
+  if (a.bicg) return a.nc == 1 ? bcg_enqueue<T, 1>(a, A, b, x, work, st, cc, rtol, skip_os)
+                               : bcg_enqueue<T, 3>(a, A, b, x, work, st, cc, rtol, skip_os);
+  return a.nc == 1 ? cg_enqueue<T, 1>(a, A, b, x, work, st, cc, rtol, skip_os)
+                   : cg_enqueue<T, 3>(a, A, b, x, work, st, cc, rtol, skip_os);
+}
+
+cudaError_t solve_enqueue(const SolveArgs& a, cudaStream_t st, CaptureCtx* cc) {
+  const DevGrid& g = *a.g;
+  OpDesc<double> A64{a.op, a.coef64, a.dmask, a.dinv64, a.prof, a.pbase};
+  const int ib = (g.ninst + 127) / 128;
+  if (!a.mixed) {
+    cudaError_t e = inner_enqueue<double>(a, A64, a.b, a.x, a.w64, st, cc, a.rtol, nullptr);
+    if (e != cudaSuccess) return e;
+    IBG_LAUNCH(k_collect, ib, 128, 0, st, a.ks, a.nc, g.ninst, a.rec, (OState*)nullptr);
+    return cudaSuccess;
+  }
+  OpDesc<float> A32{a.op, a.coef32, a.dmask, a.dinv32, a.prof, a.pbase};
+  const int64_t n = int64_t(a.nc) * g.nslots;
+  IBG_LAUNCH(k_init_outer, ib, 128, 0, st, a.os, g.ninst, a.nc, a.rtol * a.rtol, a.max_outer);
+  const bool cap = cc && cc->capturing;
+  auto residual = [&](cudaStream_t s, const Cond& cl, const Cond& cb) {
+    fe_apply<double>(g, A64, a.nc, a.x, a.y64, s);
+    if (a.nc == 1)
+      IBG_LAUNCH(k_residual_outer<1>, g.nbricks, DBV, 0, s, g, a.b, a.y64, a.r64, a.dmask, a.os, a.rb.partials,
+                 a.rb.counter, cl, cb);
+    else
+      IBG_LAUNCH(k_residual_outer<3>, g.nbricks, DBV, 0, s, g, a.b, a.y64, a.r64, a.dmask, a.os, a.rb.partials,
+                 a.rb.counter, cl, cb);
+  };
+  auto correction = [&](cudaStream_t s) {
+    fe_cast_d2f(n, a.r64, a.r32, s);
+    fe_zero<float>(n, a.e32, s);
+    cudaError_t e = inner_enqueue<float>(a, A32, a.r32, a.e32, a.w32, s, cc, a.rtol_inner, a.os);
+    IBG_LAUNCH(k_collect, ib, 128, 0, s, a.ks, a.nc, g.ninst, a.rec, a.os);
+    IBG_LAUNCH(k_add_f2d_active, g.nbricks, DBV, 0, s, g, a.e32, a.x, a.nc, (const OState*)a.os);
+    return e;
+  };
+  cudaError_t err = cudaSuccess;
+  if (cap) {
+    Cond cl;
+    if ((err = cond_handle(st, 1, &cl)) != cudaSuccess) return err;
+    err = cond_node(*cc, st, cl, cudaGraphCondTypeWhile, [&](cudaStream_t s) {
+      Cond cb;
+      cudaError_t e = cond_handle(s, 0, &cb);
+      if (e != cudaSuccess) { err = e; return; }
+      residual(s, cl, cb);
+      e = cond_node(*cc, s, cb, cudaGraphCondTypeIf, [&](cudaStream_t s2) {
+        cudaError_t e2 = correction(s2);
+        if (e2 != cudaSuccess) err = e2;
+      });
+      if (e != cudaSuccess) err = e;
+    });
+    if (err != cudaSuccess) return err;
+  } else {
+    const Cond none;
+    for (int it = 0; it <= a.max_outer + 1; ++it) {
+      residual(st, none, none);
+      cudaMemcpyAsync(a.os_host, a.os, g.ninst * sizeof(OState), cudaMemcpyDeviceToHost, st);
+      if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
+      bool all = true;
+      for (int i = 0; i < g.ninst; ++i) all = all && a.os_host[i].done;
+      if (all) break;
+      if ((err = correction(st)) != cudaSuccess) return err;
+    }
+  }
+  IBG_LAUNCH(k_collect_outer, ib, 128, 0, st, a.os, g.ninst, a.rec);
+  return cudaSuccess;
+}
+
+__global__ void k_rec_clear(SolveRec* rec, int n) {
+  KCOUNT();
+  const int i = threadIdx.x + blockIdx.x * blockDim.x;
+  if (i < n) {
+    SolveRec r;
+    memset(&r, 0, sizeof(r));
+    rec[i] = r;
+  }
+}
+
+void rec_clear(SolveRec* rec, int n, cudaStream_t st) { IBG_LAUNCH(k_rec_clear, (n + 127) / 128, 128, 0, st, rec, n); }
+
+}  // namespace ibg

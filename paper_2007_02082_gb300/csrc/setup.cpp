@@ -337,6 +337,13 @@ ib_status build_host_grid(const ib_grid_desc& d, int64_t M, const double* X, con
     kids[e1].push_back(G.hang_slot[h]);
     kids[e2].push_back(G.hang_slot[h]);
   }
+  G.if_of_slot.assign(nslots, -1);
+  for (size_t e = 0; e < G.if_coarse.size(); ++e) {
+    G.if_of_slot[G.if_coarse[e]] = int32_t(e);
+    G.if_of_slot[G.if_fine[e]] = int32_t(e);
+    G.meta[G.if_coarse[e]] |= M_IFACE;
+    G.meta[G.if_fine[e]] |= M_IFACE;
+  }
   G.if_child_off.assign(kids.size() + 1, 0);
   for (size_t e = 0; e < kids.size(); ++e) {
     std::sort(kids[e].begin(), kids[e].end());

@@ -30,6 +30,7 @@ enum : uint16_t {
   M_DUP = 1u << 10,    // non-owner copy of a node stored on two levels
   M_VDIR = 1u << 11,   // velocity Dirichlet (wall or inlet)
   M_PDIR = 1u << 12,   // pressure-increment Dirichlet (outlet port)
+  M_IFACE = 1u << 13,  // either copy of a node stored on two levels
 };
 
 // Canonical node flag bits (IB_FIELD_NODE_FLAGS).
@@ -65,6 +66,7 @@ struct HostGrid {
   // interface (node stored on two levels) and hanging constraints
   std::vector<int32_t> if_coarse, if_fine;       // [n_if]
   std::vector<int32_t> if_child_off, if_child;   // CSR of hanging children (fine slots)
+  std::vector<int32_t> if_of_slot;               // [nslots] interface entry of a copy, -1 else
   std::vector<int32_t> hang_slot, hang_p1, hang_p2;
   // canonical order
   std::vector<int32_t> canon_slot;    // [N] owner slot

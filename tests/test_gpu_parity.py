@@ -189,3 +189,23 @@ def test_nonconvergence_keeps_previous_state():
     assert np.array_equal(g.ib_fields_get("U"), u0)
     assert g.ib_grid_info()["step"] == 0
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_and_eager_paths_bitwise_equal(precision):
+    """The captured step (conditional graph loops) and the eager step (host
+    polling, kernels timed one by one) launch the same kernels in the same
+    order: the results are bitwise identical."""
+    from paper_2007_02082_gb300 import IBGrid
+    case, _ = CASES["refined"]
+    a = IBGrid(case, precision=precision)
+    b = IBGrid(case, precision=precision, profile=True)
+    a.ipcs_step(2)
+    b.ipcs_step(2)
+    assert np.array_equal(a.ib_fields_get("U"), b.ib_fields_get("U"))
+    assert np.array_equal(a.ib_fields_get("P"), b.ib_fields_get("P"))
+    ia, ib_ = a.ib_grid_info(), b.ib_grid_info()
+    assert ia["iters_p"] == ib_["iters_p"] and ia["iters_mom"] == ib_["iters_mom"]
+    assert sum(ib_["prof_launches"]) > 0
+    a.close()
+    b.close()

@@ -126,6 +126,8 @@ CASES = {
                                                          seed=11, max_level=1, refine_band=2, reduce_band=2),
     "two_levels_24x24x8": lambda: W.cylinder_case(n=(24, 24, 8), length=1.0, half_width=0.75, M=1500, seed=12,
                                                   max_level=2, refine_band=1, reduce_band=3),
+    "aneurysm_L1": lambda: W.aneurysm_case(length=1.5, h=1.0 / 12, seed=13),
+    "bend_L0": lambda: W.bent_tube_case(R=0.4, Rc=1.0, l_in=0.5, l_out=0.5, h=1.0 / 10, seed=14),
 }
 
 

@@ -127,3 +127,180 @@ def cylinder_refined_small(n=(16, 16, 32), M=None, seed=7, **kw):
     args.update(kw)
     return cylinder_case(**args)
 
+
+
+# ---------------------------------------------------------------------------
+# Further synthetic vessels (serving mix and the aneurysm case)
+# ---------------------------------------------------------------------------
+def _box(lo, hi):
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    return tuple(float(v) for v in lo), tuple(float(v) for v in (hi - lo))
+
+
+def _grid_for(extent, h):
+    return tuple(max(2, int(math.ceil(e / h))) for e in extent)
+
+
+def _case(name, origin, extent, n, X, dS, inside, ports, nu, dt, steps, max_level, refine_band, reduce_band):
+    return {
+        "name": name, "origin": origin, "extent": extent, "n": tuple(int(v) for v in n),
+        "max_level": int(max_level), "refine_band": int(refine_band), "reduce_band": int(reduce_band),
+        "nu": float(nu), "rho": 1.0, "dt": float(dt), "steps": int(steps), "ports": ports,
+        "X": np.ascontiguousarray(X, dtype=np.float64), "dS": np.ascontiguousarray(dS, dtype=np.float64),
+        "UB": np.zeros((len(X), 3)), "inside": inside.astype(np.uint8),
+    }
+
+
+def aneurysm_case(R=0.5, length=4.0, Rs=0.6, offset=0.7, h=1.0 / 32, spacing=2.3, seed=3, max_level=1,
+                  refine_band=2, reduce_band=2, nu=0.01, dt=0.001, steps=2000, a0=1.0, b=(0.5,)):
+    """Saccular aneurysm: a tube of radius R along z fused with a sphere of
+    radius Rs centred `offset` off the axis at mid-length.  Points: stratified
+    jitter on the tube wall outside the sphere and on the sphere outside the
+    tube (equal-area strata in (cos phi, theta)); dS = stratum area."""
+    zc = 0.5 * length
+    margin = 4.0 * h
+    origin, extent = _box((-R - margin, -max(R, Rs) - margin, 0.0),
+                          (offset + Rs + margin, max(R, Rs) + margin, length))
+    n = _grid_for(extent, h)
+    extent = tuple(n[a] * h for a in range(3))
+    hf = h / (1 << max_level)
+    rng = np.random.default_rng(seed)
+    # tube wall
+    ds_target = (spacing * hf) ** 2
+    circ = 2 * math.pi * R
+    n_th = max(8, int(round(circ / math.sqrt(ds_target))))
+    n_z = max(4, int(round(length / math.sqrt(ds_target))))
+    th = (np.arange(n_th)[None, :] + 0.5 + rng.uniform(-0.35, 0.35, (n_z, n_th))) * (2 * math.pi / n_th)
+    zz = (np.arange(n_z)[:, None] + 0.5 + rng.uniform(-0.35, 0.35, (n_z, n_th))) * (length / n_z)
+    Xt = np.stack([R * np.cos(th), R * np.sin(th), zz], -1).reshape(-1, 3)
+    keep = np.linalg.norm(Xt - np.array([offset, 0.0, zc]), axis=1) > Rs
+    Xt = Xt[keep]
+    dSt = np.full(len(Xt), circ * length / (n_th * n_z))
+    # sphere
+    area_s = 4 * math.pi * Rs * Rs
+    n_s = max(16, int(round(area_s / ds_target)))
+    n_mu = max(4, int(round(math.sqrt(n_s / 2))))
+    n_ph = max(8, int(round(n_s / n_mu)))
+    mu = -1 + (np.arange(n_mu)[:, None] + 0.5 + rng.uniform(-0.35, 0.35, (n_mu, n_ph))) * (2.0 / n_mu)
+    ph = (np.arange(n_ph)[None, :] + 0.5 + rng.uniform(-0.35, 0.35, (n_mu, n_ph))) * (2 * math.pi / n_ph)
+    sr = np.sqrt(np.clip(1 - mu * mu, 0, 1))
+    Xs = np.stack([offset + Rs * sr * np.cos(ph), Rs * sr * np.sin(ph), zc + Rs * mu], -1).reshape(-1, 3)
+    Xs = Xs[np.hypot(Xs[:, 0], Xs[:, 1]) > R]
+    dSs = np.full(len(Xs), area_s / (n_mu * n_ph))
+    X = np.concatenate([Xt, Xs])
+    dS = np.concatenate([dSt, dSs])
+    xc, yc, zcc = cell_centres(origin, extent, n)
+    inside = (np.hypot(xc, yc) < R) | (np.sqrt((xc - offset) ** 2 + yc ** 2 + (zcc - zc) ** 2) < Rs)
+    ports = [_port(2, 0, (0.0, 0.0, 0.0), R, INLET, a0=a0, b=b, period=1.0),
+             _port(2, 1, (0.0, 0.0, length), R, OUTLET)]
+    return _case(f"aneurysm_{n[0]}x{n[1]}x{n[2]}_L{max_level}", origin, extent, n, X, dS, inside, ports, nu, dt,
+                 steps, max_level, refine_band, reduce_band)
+
+
+def bent_tube_case(R=0.5, Rc=1.5, l_in=1.5, l_out=1.5, h=1.0 / 16, spacing=2.3, seed=5, max_level=0,
+                   refine_band=2, reduce_band=2, nu=0.02, dt=0.005, steps=200, a0=1.0, b=()):
+    """90-degree bend in the xz-plane: a straight inflow leg along +z from the
+    low z face, a quarter torus of centreline radius Rc, and a straight outflow
+    leg along +x to the high x face.  Points: stratified jitter in (arclength,
+    angle) with each point's dS the local area element times the stratum size
+    (the torus area element varies with the angle)."""
+    margin = 4.0 * h
+    zb = l_in                                        # start of the bend
+    # centreline: (0,0,s) for s<zb; arc centre (Rc, 0, zb); outflow along +x at z = zb + Rc
+    xmax = Rc + l_out
+    origin, extent = _box((-R - margin, -R - margin, 0.0), (xmax, R + margin, zb + Rc + R + margin))
+    n = _grid_for(extent, h)
+    extent = (xmax - origin[0], n[1] * h, n[2] * h)
+    n = (max(2, int(round(extent[0] / h))), n[1], n[2])
+    extent = (n[0] * h, extent[1], extent[2])
+    xmax = origin[0] + extent[0]
+    l_out = xmax - Rc
+    hf = h / (1 << max_level)
+    rng = np.random.default_rng(seed)
+    ds_target = (spacing * hf) ** 2
+    L_arc = 0.5 * math.pi * Rc
+    L_tot = zb + L_arc + l_out
+    n_s = max(8, int(round(L_tot / math.sqrt(ds_target))))
+    n_th = max(8, int(round(2 * math.pi * R / math.sqrt(ds_target))))
+    s = (np.arange(n_s)[:, None] + 0.5 + rng.uniform(-0.35, 0.35, (n_s, n_th))) * (L_tot / n_s)
+    th = (np.arange(n_th)[None, :] + 0.5 + rng.uniform(-0.35, 0.35, (n_s, n_th))) * (2 * math.pi / n_th)
+    s, th = s.ravel(), th.ravel()
+    X = np.zeros((len(s), 3))
+    w = np.ones(len(s))                               # local area factor
+    # frame: binormal e_y; normal in the xz-plane
+    for k in range(len(s)):
+        sk, tk = s[k], th[k]
+        if sk < zb:
+            c, t, nrm = np.array([0.0, 0.0, sk]), np.array([0, 0, 1.0]), np.array([-1.0, 0, 0])
+        elif sk < zb + L_arc:
+            a = (sk - zb) / Rc
+            c = np.array([Rc - Rc * math.cos(a), 0.0, zb + Rc * math.sin(a)])
+            t = np.array([math.sin(a), 0.0, math.cos(a)])
+            nrm = np.array([-math.cos(a), 0.0, math.sin(a)])          # away from the bend centre
+            w[k] = 1.0 + (R / Rc) * math.cos(tk)
+        else:
+            c = np.array([Rc + (sk - zb - L_arc), 0.0, zb + Rc])
+            t, nrm = np.array([1.0, 0, 0]), np.array([0, 0, 1.0])
+        X[k] = c + R * (math.cos(tk) * nrm + math.sin(tk) * np.array([0, 1.0, 0]))
+    dS = w * (L_tot / n_s) * (2 * math.pi * R / n_th)
+    xc, yc, zcc = cell_centres(origin, extent, n)
+    # distance to the centreline
+    d_in = np.where(zcc < zb, np.hypot(xc, yc), np.inf)
+    rr = np.hypot(xc - Rc, zcc - zb)
+    ang_ok = (zcc >= zb) & (xc <= Rc)
+    d_arc = np.where(ang_ok, np.hypot(rr - Rc, yc), np.inf)
+    d_out = np.where(xc > Rc, np.hypot(zcc - (zb + Rc), yc), np.inf)
+    inside = np.minimum(np.minimum(d_in, d_arc), d_out) < R
+    ports = [_port(2, 0, (0.0, 0.0, 0.0), R, INLET, a0=a0, b=b, period=1.0),
+             _port(0, 1, (xmax, 0.0, zb + Rc), R, OUTLET)]
+    return _case(f"bend_{n[0]}x{n[1]}x{n[2]}_L{max_level}", origin, extent, n, X, dS, inside, ports, nu, dt, steps,
+                 max_level, refine_band, reduce_band)
+
+
+def serving_requests(n_req=256, rate=None, seed=5, steps=200, cells_lo=32 ** 3, cells_hi=128 ** 3):
+    """Poisson-arrival stream of seeded random vessels: kind in {straight,
+    bent, aneurysmal}, radius 0.3-1.0, length 3-10, an active grid of 32^3 to
+    128^3 equivalent cells (log-uniform), 0-2 refinement levels, nu 0.01-0.05.
+    Returns [(arrival_time, case)], arrival times in units of 1/rate seconds
+    (rate None: unit rate)."""
+    rng = np.random.default_rng(seed)
+    lam = 1.0 if rate is None else float(rate)
+    t = np.cumsum(rng.exponential(1.0 / lam, n_req))
+    out = []
+    for k in range(n_req):
+        kind = ["straight", "bent", "aneurysm"][int(rng.integers(0, 3))]
+        R = float(rng.uniform(0.3, 1.0))
+        L = float(rng.uniform(3.0, 10.0))
+        target = float(np.exp(rng.uniform(np.log(cells_lo), np.log(cells_hi))))
+        levels = int(rng.integers(0, 3))
+        nu = float(rng.uniform(0.01, 0.05))
+        sub = int(rng.integers(1 << 20))
+        if kind == "straight":
+            vol = math.pi * (R * 1.25) ** 2 * L
+        elif kind == "bent":
+            vol = math.pi * (R * 1.25) ** 2 * (0.6 * L + 0.5 * math.pi * 3 * R)
+        else:
+            vol = math.pi * (R * 1.25) ** 2 * L + 4.0 / 3.0 * math.pi * (1.2 * R * 1.2) ** 3
+        # leaf cells grow ~ 8^levels near the wall; size the coarse grid for the target
+        h = (vol / (target / (1 + 2.0 * levels))) ** (1.0 / 3.0)
+        h = max(h, 2.0 * R / 28)
+        dt = 0.25 * h / (1 << levels)
+        if kind == "straight":
+            n_ax = max(8, int(round(L / h)))
+            nxy = max(8, int(round(2 * (R + 4 * h) / h)))
+            Rl = R
+            pts = (2 * math.pi * R * L) / (2.3 * h / (1 << levels)) ** 2
+            c = cylinder_case(n=(nxy, nxy, n_ax), R=Rl, length=L, half_width=nxy * h / 2, M=max(64, int(pts)),
+                              seed=sub, max_level=levels, refine_band=2, reduce_band=2, nu=nu, dt=dt, steps=steps,
+                              name=f"req{k}_straight")
+        elif kind == "bent":
+            c = bent_tube_case(R=R, Rc=3 * R, l_in=0.3 * L, l_out=0.3 * L, h=h, seed=sub, max_level=levels,
+                               nu=nu, dt=dt, steps=steps)
+            c["name"] = f"req{k}_bent"
+        else:
+            c = aneurysm_case(R=R, length=L, Rs=1.2 * R, offset=1.4 * R, h=h, seed=sub, max_level=levels, nu=nu,
+                              dt=dt, steps=steps, b=())
+            c["name"] = f"req{k}_aneurysm"
+        out.append((float(t[k]), c))
+    return out
