@@ -288,6 +288,24 @@ def run_oracle_sample(name, steps=2):
             "sample": f"{desc}: {cells} leaf cells, {t:.1f} s"}
 
 
+def run_serving(n_req, steps):
+    """Serving comparison on a reduced request stream (the full mix is 256
+    requests x 200 steps on 32^3-128^3 grids): the continuously batched mixed
+    path vs the plain FP64 path one request at a time, same arrivals."""
+    import workloads as W
+    from paper_2007_02082_gb300.serve import serve, serve_one_at_a_time
+    stream = W.serving_requests(n_req=n_req, rate=None, seed=5, steps=steps, cells_lo=32 ** 3, cells_hi=64 ** 3)
+    # arrival rate: all requests within the first quarter of the one-at-a-time makespan is not known in
+    # advance; use a fixed mean inter-arrival of 50 ms
+    stream = [(0.05 * t, c) for t, c in stream]
+    b = serve(stream, precision="mixed", epoch_steps=10).summary()
+    o = serve_one_at_a_time(stream, precision="fp64").summary()
+    return {"requests": n_req, "steps": steps, "mean_interarrival_s": 0.05,
+            "batched_mixed": b, "one_at_a_time_fp64": o,
+            "stream": "seeded Poisson arrivals; straight/bent/aneurysmal tubes, R 0.3-1.0, L 3-10, "
+                      "32^3-64^3 equivalent cells, 0-2 levels, nu 0.01-0.05"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -298,6 +316,9 @@ def main():
     ap.add_argument("--workload", default="cylinder_64x64x256_L1")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nvtx", action="store_true", help="wrap each timed step in an NVTX range 'ipcs_step'")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="also run the serving comparison on a stream of this many requests")
+    ap.add_argument("--serve-steps", type=int, default=50)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -324,6 +345,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     out = run_native(args, rank, world, local_rank)
+    if args.serve and rank == 0:
+        out["serve"] = run_serving(args.serve, args.serve_steps)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = run_oracle_sample(args.workload)

@@ -56,11 +56,11 @@ struct Tols {
 Tols tolerances(const ib_grid_desc& d) {
   const bool mixed = d.precision == IB_MIXED;
   Tols t;
-  t.mom = d.rtol_mom > 0 ? d.rtol_mom : (mixed ? 1e-10 : 1e-13);
-  t.p = d.rtol_p > 0 ? d.rtol_p : (mixed ? 1e-10 : 1e-13);
-  t.corr = d.rtol_corr > 0 ? d.rtol_corr : (mixed ? 1e-10 : 1e-13);
+  t.mom = d.rtol_mom > 0 ? d.rtol_mom : (mixed ? 1e-12 : 1e-13);
+  t.p = d.rtol_p > 0 ? d.rtol_p : (mixed ? 1e-12 : 1e-13);
+  t.corr = d.rtol_corr > 0 ? d.rtol_corr : (mixed ? 1e-12 : 1e-13);
   t.ib = d.rtol_ib > 0 ? d.rtol_ib : 1e-13;
-  t.inner = 1e-4;
+  t.inner = 1e-5;
   t.max_iter = d.max_iter > 0 ? d.max_iter : 20000;
   return t;
 }
@@ -243,7 +243,7 @@ ib_status engine_build(Engine& E) {
   // ---- concatenated topology
   std::vector<int32_t> blev, binst, bseg(n + 1), bnbr, ifc, iff, ifo(1, 0), ifk, ifos, hg, hp1, hp2, canon, ins, inp;
   std::vector<uint16_t> meta;
-  std::vector<double> hl(size_t(n) * 12, 0.0), pdt(n), pnu(n), insh;
+  std::vector<double> hl(size_t(n) * 12, 0.0), sf(size_t(n) * 32, 0.0), pdt(n), pnu(n), insh;
   std::vector<PortDev> ports;
   for (int i = 0; i < n; ++i) {
     const HostGrid& H = *E.H[i];
@@ -260,8 +260,17 @@ ib_status engine_build(Engine& E) {
       }
     }
     meta.insert(meta.end(), H.meta.begin(), H.meta.end());
-    for (int l = 0; l <= H.L; ++l)
-      for (int a = 0; a < 3; ++a) hl[(i * 4 + l) * 3 + a] = H.levels[l].h[a];
+    for (int l = 0; l <= H.L; ++l) {
+      const double* h = H.levels[l].h;
+      const double V = h[0] * h[1] * h[2];
+      double* f = &sf[(i * 4 + l) * 8];
+      for (int a = 0; a < 3; ++a) {
+        hl[(i * 4 + l) * 3 + a] = h[a];
+        f[a] = V / (6.0 * h[a] * h[a]);
+        f[4 + a] = V / (24.0 * h[a]);
+      }
+      f[3] = V / 120.0;
+    }
     pdt[i] = d.dt;
     pnu[i] = d.nu;
     const int32_t E0 = int32_t(nif);
@@ -311,13 +320,17 @@ ib_status engine_build(Engine& E) {
   g.ninst = n;
   int32_t *d_blev, *d_binst, *d_bseg, *d_bnbr, *d_ifc, *d_iff, *d_ifo, *d_ifk, *d_ifos, *d_hg, *d_hp1, *d_hp2;
   uint16_t* d_meta;
-  double *d_hl, *d_pnu;
+  double *d_hl, *d_pnu, *d_sf64;
+  float* d_sf32;
+  std::vector<float> sf32(sf.begin(), sf.end());
   TRY(upload(E, &d_blev, blev));
   TRY(upload(E, &d_binst, binst));
   TRY(upload(E, &d_bseg, bseg));
   TRY(upload(E, &d_bnbr, bnbr));
   TRY(upload(E, &d_meta, meta));
   TRY(upload(E, &d_hl, hl));
+  TRY(upload(E, &d_sf64, sf));
+  TRY(upload(E, &d_sf32, sf32));
   TRY(upload(E, &E.pdt, pdt));
   TRY(upload(E, &d_pnu, pnu));
   TRY(upload(E, &d_ifc, ifc));
@@ -329,7 +342,7 @@ ib_status engine_build(Engine& E) {
   TRY(upload(E, &d_hp1, hp1));
   TRY(upload(E, &d_hp2, hp2));
   g.blev = d_blev; g.binst = d_binst; g.bseg = d_bseg; g.bnbr = d_bnbr; g.meta = d_meta;
-  g.hl = d_hl; g.pdt = E.pdt; g.pnu = d_pnu;
+  g.hl = d_hl; g.pdt = E.pdt; g.pnu = d_pnu; g.sf64 = d_sf64; g.sf32 = d_sf32;
   g.n_if = int32_t(ifc.size());
   g.if_c = d_ifc; g.if_f = d_iff; g.if_off = d_ifo; g.if_kid = d_ifk; g.if_of_slot = d_ifos;
   g.n_hang = int32_t(hg.size());

@@ -50,6 +50,10 @@ struct DevGrid {
   const int32_t* __restrict__ bnbr;   // [nbricks][27]
   const uint16_t* __restrict__ meta;  // [nslots]
   const double* __restrict__ hl;      // [ninst][4][3] cell spacing per instance and level
+  // stencil factors per instance and level, [ninst][4][8]:
+  //   (V/6)/hx^2, (V/6)/hy^2, (V/6)/hz^2, V/120, (V/24)/hx, (V/24)/hy, (V/24)/hz, 0
+  const double* __restrict__ sf64;
+  const float* __restrict__ sf32;
   const double* __restrict__ pdt;     // [ninst] time step
   const double* __restrict__ pnu;     // [ninst] kinematic viscosity
   // nodes stored on two levels: coarse owner, fine copy, hanging children
@@ -109,6 +113,30 @@ __device__ __forceinline__ void load_tile(T* tile, const T* __restrict__ x, int6
     int64_t s = (int64_t)nb * DBV + (((lz & 7) * DBS + (ly & 7)) * DBS + (lx & 7));
     for (int c = 0; c < ncomp; ++c) tile[c * TILE3 + t] = nb >= 0 ? x[c * cs + s] : T(0);
   }
+}
+
+// Inner-product contributions: FP32 products are summed in FP32 within each
+// warp and carried in FP64 from there on; FP64 products stay FP64.
+template <typename T, int NV>
+__device__ __forceinline__ void warp_presum(T (&tv)[NV], double (&v)[NV]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+      for (int o = 16; o > 0; o >>= 1) tv[k] += __shfl_down_sync(0xffffffffu, tv[k], o);
+    const bool l0 = (threadIdx.x & 31) == 0;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = l0 ? double(tv[k]) : 0.0;
+  } else {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = double(tv[k]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ const T* stencil_factors(const DevGrid& g, int b) {
+  const int idx = (g.binst[b] * 4 + g.blev[b]) * 8;
+  if constexpr (sizeof(T) == 4) return reinterpret_cast<const T*>(g.sf32) + idx;
+  else return reinterpret_cast<const T*>(g.sf64) + idx;
 }
 
 // Block-wide sum of NV doubles (blockDim.x a multiple of 32, <= 1024).

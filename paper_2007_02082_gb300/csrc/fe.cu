@@ -33,7 +33,7 @@ __constant__ int16_t c_toff[15];               // tile offset of each stencil sl
 __constant__ int8_t c_slot_of_rel[27];
 __constant__ uint8_t c_massw[256][15];         // sum over tets of (1 + delta_nb), units V/120
 __constant__ int8_t c_stiffw[256][7][3];       // sum over tets of g_n,a g_b,a, units (V/6)/h_a^2
-__constant__ int8_t c_kperm[6][3];
+__constant__ int8_t c_gradw[256][15][3];       // sum over tets of g_b,a (gradient of phi_b), units (V/24)/h_a
 
 static const int8_t h_sten[15][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
                                      {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {0, 1, 1},
@@ -54,8 +54,10 @@ cudaError_t fe_init_tables() {
   // -e_a1/h, e_a1/h - e_a2/h, e_a2/h - e_a3/h, e_a3/h (integers g below).
   static uint8_t massw[256][15];
   static int8_t stiffw[256][7][3];
+  static int8_t gradw[256][15][3];
   std::memset(massw, 0, sizeof(massw));
   std::memset(stiffw, 0, sizeof(stiffw));
+  std::memset(gradw, 0, sizeof(gradw));
   for (int mask = 0; mask < 256; ++mask) {
     int stf[15][3] = {};
     for (int c = 0; c < 8; ++c) {
@@ -79,7 +81,10 @@ cudaError_t fe_init_tables() {
           int sl = slot_of_rel[(rz + 1) * 9 + (ry + 1) * 3 + (rx + 1)];
           if (sl < 0) return cudaErrorInvalidValue;
           massw[mask][sl] += uint8_t(k == kn ? 2 : 1);
-          for (int a = 0; a < 3; ++a) stf[sl][a] += gr[kn][a] * gr[k][a];
+          for (int a = 0; a < 3; ++a) {
+            stf[sl][a] += gr[kn][a] * gr[k][a];
+            gradw[mask][sl][a] = int8_t(gradw[mask][sl][a] + gr[k][a]);
+          }
         }
       }
     }
@@ -95,7 +100,7 @@ cudaError_t fe_init_tables() {
   if ((e = cudaMemcpyToSymbol(c_slot_of_rel, slot_of_rel, sizeof(slot_of_rel))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_massw, massw, sizeof(massw))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_stiffw, stiffw, sizeof(stiffw))) != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_kperm, h_kperm, sizeof(h_kperm));
+  return cudaMemcpyToSymbol(c_gradw, gradw, sizeof(gradw));
 }
 
 // ---------------------------------------------------------------- helpers
@@ -110,21 +115,23 @@ __device__ __forceinline__ bool is_dof(uint16_t m, uint16_t dmask) {
   return (m & D_VALID) && !(m & (D_HANG | D_DUP | dmask));
 }
 
-// row coefficients of the mask-tabulated operators
+// row coefficient k of the mask-tabulated operators, in the kernel's precision
+// (F: the instance/level stencil factors)
 template <typename T, int OP>
-__device__ __forceinline__ T table_coef(int mask, int k, const double (&f)[3], double vm) {
+__device__ __forceinline__ T table_coef(int mask, int k, const T* F) {
   if (OP == OP_POISSON)
-    return T(double(c_stiffw[mask][k][0]) * f[0] + double(c_stiffw[mask][k][1]) * f[1] +
-             double(c_stiffw[mask][k][2]) * f[2]);
-  return T(double(c_massw[mask][k]) * vm);
+    return T(c_stiffw[mask][k][0]) * F[0] + T(c_stiffw[mask][k][1]) * F[1] + T(c_stiffw[mask][k][2]) * F[2];
+  return T(c_massw[mask][k]) * F[3];
 }
 
 enum Post : int { POST_NONE = 0, POST_CG_ALPHA = 1 };
 
 // p.Ap per instance and component -> alpha = r.z / p.Ap
-template <int NC>
-__device__ __forceinline__ void cg_alpha_post(const DevGrid& g, double (&v)[NC], KState* ks, double* partials,
+template <typename T, int NC>
+__device__ __forceinline__ void cg_alpha_post(const DevGrid& g, T (&tv)[NC], KState* ks, double* partials,
                                               unsigned* counter) {
+  double v[NC];
+  warp_presum<T, NC>(tv, v);
   double* out = partials + (int64_t)gridDim.x * NC;
   if (!grid_sum_last<NC>(v, partials, counter, g.bseg, g.ninst, out)) return;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
@@ -161,9 +168,9 @@ __global__ void __launch_bounds__(512) k_apply(DevGrid g, const T* __restrict__ 
   }
   if (skip) {
     if (post == POST_CG_ALPHA) {
-      double v[NC];
-      for (int c = 0; c < NC; ++c) v[c] = 0.0;
-      cg_alpha_post<NC>(g, v, ks, partials, counter);
+      T v[NC];
+      for (int c = 0; c < NC; ++c) v[c] = T(0);
+      cg_alpha_post<T, NC>(g, v, ks, partials, counter);
     }
     return;
   }
@@ -194,24 +201,18 @@ __global__ void __launch_bounds__(512) k_apply(DevGrid g, const T* __restrict__ 
   for (int c = 0; c < NC; ++c) out[c] = T(0);
   if (m & D_VALID) {
     const int mask = m & 0xFF;
-    double hh[3];
-    spacing(g, b, hh);
-    const double hx = hh[0], hy = hh[1], hz = hh[2];
-    const double V = hx * hy * hz;
+    const T* F = stencil_factors<T>(g, b);
     if (OP == OP_POISSON) {
-      const double f[3] = {V / (6.0 * hx * hx), V / (6.0 * hy * hy), V / (6.0 * hz * hz)};
 #pragma unroll
       for (int k = 0; k < 7; ++k) {
-        T ck = table_coef<T, OP_POISSON>(mask, k, f, 0.0);
+        T ck = table_coef<T, OP_POISSON>(mask, k, F);
 #pragma unroll
         for (int c = 0; c < NC; ++c) out[c] += ck * tile[c * TILE3 + ti + c_toff[k]];
       }
     } else if (OP == OP_MASS) {
-      const double f[3] = {0, 0, 0};
-      const double vm = V / 120.0;
 #pragma unroll
       for (int k = 0; k < 15; ++k) {
-        T ck = table_coef<T, OP_MASS>(mask, k, f, vm);
+        T ck = table_coef<T, OP_MASS>(mask, k, F);
 #pragma unroll
         for (int c = 0; c < NC; ++c) out[c] += ck * tile[c * TILE3 + ti + c_toff[k]];
       }
@@ -235,10 +236,10 @@ __global__ void __launch_bounds__(512) k_apply(DevGrid g, const T* __restrict__ 
     for (int c = 0; c < NC; ++c) pnew[c * g.nslots + s] = tile[c * TILE3 + ti];
   }
   if (post == POST_CG_ALPHA) {
-    double v[NC];
+    T v[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) v[c] = double(tile[c * TILE3 + ti]) * double(out[c]);
-    cg_alpha_post<NC>(g, v, ks, partials, counter);
+    for (int c = 0; c < NC; ++c) v[c] = tile[c * TILE3 + ti] * out[c];
+    cg_alpha_post<T, NC>(g, v, ks, partials, counter);
   }
 }
 
@@ -283,18 +284,10 @@ __global__ void __launch_bounds__(512) k_diag(DevGrid g, const T* __restrict__ c
   const uint16_t m = g.meta[s];
   T d = T(0);
   if (m & D_VALID) {
-    double hh[3];
-    spacing(g, blockIdx.x, hh);
-    const double hx = hh[0], hy = hh[1], hz = hh[2], V = hx * hy * hz;
-    if (OP == OP_POISSON) {
-      const double f[3] = {V / (6.0 * hx * hx), V / (6.0 * hy * hy), V / (6.0 * hz * hz)};
-      d = table_coef<T, OP_POISSON>(m & 0xFF, 0, f, 0.0);
-    } else if (OP == OP_MASS) {
-      const double f[3] = {0, 0, 0};
-      d = table_coef<T, OP_MASS>(m & 0xFF, 0, f, V / 120.0);
-    } else {
-      d = coef[s];
-    }
+    const T* F = stencil_factors<T>(g, blockIdx.x);
+    if (OP == OP_POISSON) d = table_coef<T, OP_POISSON>(m & 0xFF, 0, F);
+    else if (OP == OP_MASS) d = table_coef<T, OP_MASS>(m & 0xFF, 0, F);
+    else d = coef[s];
   }
   diag[s] = d;
 }
@@ -310,42 +303,8 @@ __global__ void __launch_bounds__(512) k_dinv(DevGrid g, const T* __restrict__ d
 }
 
 // ---------------------------------------------------------------- tet-loop kernels (FP64)
-// For every Kuhn tetrahedron T of an active incident leaf cell that contains
-// the node: f(T, kn, rel[4], grad[4][3], V) with kn the node's vertex index,
-// rel the tile offsets of the 4 vertices and grad the barycentric gradients.
-template <typename F>
-__device__ __forceinline__ void for_each_tet(int mask, const double h[3], F&& f) {
-  for (int c = 0; c < 8; ++c) {
-    if (!(mask >> c & 1)) continue;
-    const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
-    const int qb = (1 - dx) | ((1 - dy) << 1) | ((1 - dz) << 2);
-    for (int p = 0; p < 6; ++p) {
-      const int a1 = c_kperm[p][0], a2 = c_kperm[p][1], a3 = c_kperm[p][2];
-      const int vb[4] = {0, 1 << a1, (1 << a1) | (1 << a2), 7};
-      int kn = -1;
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (vb[k] == qb) kn = k;
-      if (kn < 0) continue;
-      int rel[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int rx = dx - 1 + (vb[k] & 1), ry = dy - 1 + ((vb[k] >> 1) & 1), rz = dz - 1 + ((vb[k] >> 2) & 1);
-        rel[k] = (rz * TILE + ry) * TILE + rx;
-      }
-      double gr[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-      gr[0][a1] = -1.0 / h[a1];
-      gr[1][a1] = 1.0 / h[a1];
-      gr[1][a2] = -1.0 / h[a2];
-      gr[2][a2] = 1.0 / h[a2];
-      gr[2][a3] = -1.0 / h[a3];
-      gr[3][a3] = 1.0 / h[a3];
-      f(kn, rel, gr, vb, dx, dy, dz);
-    }
-  }
-}
-
-// out_c = (M u_c) - dt (G_c p)
+// out_c = (M u_c) - dt (G_c p), both from the mask tables:
+//   M u_c = V/120 sum_k massw[k] u_c(k),  (G_c p) = (V/24)/h_c sum_k gradw[k][c] p(k)
 __global__ void __launch_bounds__(512) k_rhs_mass_grad(DevGrid g, const double* __restrict__ u,
                                                        const double* __restrict__ p, double* __restrict__ out) {
   KCOUNT();
@@ -359,32 +318,29 @@ __global__ void __launch_bounds__(512) k_rhs_mass_grad(DevGrid g, const double* 
   const uint16_t m = g.meta[s];
   double o[3] = {0, 0, 0};
   if (m & D_VALID) {
+    const int mask = m & 0xFF;
     const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
-    double h[3];
-    spacing(g, b, h);
-    const double V = h[0] * h[1] * h[2];
+    const double* F = stencil_factors<double>(g, b);
     const double dt = g.pdt[g.binst[b]];
-    for_each_tet(m & 0xFF, h, [&](int kn, const int (&rel)[4], const double (&gr)[4][3], const int*, int, int, int) {
-      double gp[3] = {0, 0, 0};
+    double gp[3] = {0, 0, 0};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const double pk = tile[3 * TILE3 + ti + rel[k]];
-        const double w = (k == kn ? 2.0 : 1.0) * (V / 120.0);
+    for (int k = 0; k < 15; ++k) {
+      const int j = ti + c_toff[k];
+      const double mw = double(c_massw[mask][k]);
+      const double pk = tile[3 * TILE3 + j];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          o[a] += w * tile[a * TILE3 + ti + rel[k]];
-          gp[a] += pk * gr[k][a];
-        }
+      for (int a = 0; a < 3; ++a) {
+        o[a] += mw * tile[a * TILE3 + j];
+        gp[a] += double(c_gradw[mask][k][a]) * pk;
       }
+    }
 #pragma unroll
-      for (int a = 0; a < 3; ++a) o[a] -= dt * (V / 24.0) * gp[a];
-    });
+    for (int a = 0; a < 3; ++a) o[a] = F[3] * o[a] - dt * F[4 + a] * gp[a];
   }
   for (int a = 0; a < 3; ++a) out[a * g.nslots + s] = o[a];
 }
 
-// out = scale * (div u, q)
-// out = -(1/dt) (div u, q) with the instance's dt
+// out = -(1/dt) (div u, q) = -(1/dt) sum_c (V/24)/h_c sum_k gradw[k][c] u_c(k)
 __global__ void __launch_bounds__(512) k_rhs_div(DevGrid g, const double* __restrict__ u, double* __restrict__ out) {
   KCOUNT();
   __shared__ double tile[3 * TILE3];
@@ -396,23 +352,38 @@ __global__ void __launch_bounds__(512) k_rhs_div(DevGrid g, const double* __rest
   const uint16_t m = g.meta[s];
   double o = 0.0;
   if (m & D_VALID) {
+    const int mask = m & 0xFF;
     const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
-    double h[3];
-    spacing(g, b, h);
-    const double V = h[0] * h[1] * h[2];
-    for_each_tet(m & 0xFF, h, [&](int, const int (&rel)[4], const double (&gr)[4][3], const int*, int, int, int) {
-      double dv = 0.0;
+    const double* F = stencil_factors<double>(g, b);
+    double d[3] = {0, 0, 0};
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 15; ++k) {
+      const int j = ti + c_toff[k];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) dv += tile[a * TILE3 + ti + rel[k]] * gr[k][a];
-      o += (V / 24.0) * dv;
-    });
+      for (int a = 0; a < 3; ++a) d[a] += double(c_gradw[mask][k][a]) * tile[a * TILE3 + j];
+    }
+    o = F[4] * d[0] + F[5] * d[1] + F[6] * d[2];
   }
   out[s] = -o / g.pdt[g.binst[b]];
 }
 
-// coef[k] = M + dt C(u) + dt nu K row entries (Eq. 9 operator), k over the 15 slots
+// Stencil slot of a neighbour offset (compile-time after unrolling).
+__host__ __device__ constexpr int slot_of_rel(int rx, int ry, int rz) {
+  return (rx == 0 && ry == 0 && rz == 0) ? 0
+       : (rx == 1 && ry == 0 && rz == 0) ? 1 : (rx == -1 && ry == 0 && rz == 0) ? 2
+       : (rx == 0 && ry == 1 && rz == 0) ? 3 : (rx == 0 && ry == -1 && rz == 0) ? 4
+       : (rx == 0 && ry == 0 && rz == 1) ? 5 : (rx == 0 && ry == 0 && rz == -1) ? 6
+       : (rx == 1 && ry == 1 && rz == 0) ? 7 : (rx == -1 && ry == -1 && rz == 0) ? 8
+       : (rx == 0 && ry == 1 && rz == 1) ? 9 : (rx == 0 && ry == -1 && rz == -1) ? 10
+       : (rx == 1 && ry == 0 && rz == 1) ? 11 : (rx == -1 && ry == 0 && rz == -1) ? 12
+       : (rx == 1 && ry == 1 && rz == 1) ? 13 : (rx == -1 && ry == -1 && rz == -1) ? 14 : -1;
+}
+
+// coef[k] = (M + dt C(u) + dt nu K) row entries (Eq. 9 operator), k over the
+// 15 slots.  Mass and stiffness come from the mask tables; the convection
+// entries C_nb = sum_T (|T|/20) (S_T + u_n) . grad phi_b (S_T = sum of u over
+// the tetrahedron's vertices) are accumulated tetrahedron by tetrahedron with
+// every index known at compile time.
 __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __restrict__ u, double* __restrict__ coef,
                                                   float* __restrict__ coef32) {
   KCOUNT();
@@ -427,31 +398,55 @@ __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __res
 #pragma unroll
   for (int k = 0; k < 15; ++k) cf[k] = 0.0;
   if (m & D_VALID) {
+    const int mask = m & 0xFF;
     const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
+    const double* F = stencil_factors<double>(g, b);
+    const int inst = g.binst[b];
+    const double dt = g.pdt[inst], nu = g.pnu[inst];
     double h[3];
     spacing(g, b, h);
-    const double V = h[0] * h[1] * h[2];
-    const double dt = g.pdt[g.binst[b]], nu = g.pnu[g.binst[b]];
-    for_each_tet(m & 0xFF, h, [&](int kn, const int (&rel)[4], const double (&gr)[4][3], const int* vb, int dx, int dy,
-                                  int dz) {
-      double S[3] = {0, 0, 0};
+    const double ih[3] = {1.0 / h[0], 1.0 / h[1], 1.0 / h[2]};
+    const double dnu = dt * nu;
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 15; ++k) cf[k] = double(c_massw[mask][k]) * F[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) S[a] += tile[a * TILE3 + ti + rel[k]];
-      double w[3];
+    for (int k = 0; k < 7; ++k)
+      cf[k] += dnu * (double(c_stiffw[mask][k][0]) * F[0] + double(c_stiffw[mask][k][1]) * F[1] +
+                      double(c_stiffw[mask][k][2]) * F[2]);
+    const double wv = dt * F[3];   // dt |T| / 20
+    const double un[3] = {tile[ti], tile[TILE3 + ti], tile[2 * TILE3 + ti]};
+    constexpr int KP[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 #pragma unroll
-      for (int a = 0; a < 3; ++a) w[a] = (V / 120.0) * (S[a] + tile[a * TILE3 + ti]);
+    for (int c = 0; c < 8; ++c) {
+      if (!((mask >> c) & 1)) continue;
+      const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+      const int qb = (1 - dx) | ((1 - dy) << 1) | ((1 - dz) << 2);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int rx = dx - 1 + (vb[k] & 1), ry = dy - 1 + ((vb[k] >> 1) & 1), rz = dz - 1 + ((vb[k] >> 2) & 1);
-        const int sl = c_slot_of_rel[(rz + 1) * 9 + (ry + 1) * 3 + (rx + 1)];
-        const double mass = (k == kn ? 2.0 : 1.0) * (V / 120.0);
-        const double conv = w[0] * gr[k][0] + w[1] * gr[k][1] + w[2] * gr[k][2];
-        const double visc = (V / 6.0) * (gr[kn][0] * gr[k][0] + gr[kn][1] * gr[k][1] + gr[kn][2] * gr[k][2]);
-        cf[sl] += mass + dt * conv + dt * nu * visc;
+      for (int p = 0; p < 6; ++p) {
+        const int a1 = KP[p][0], a2 = KP[p][1], a3 = KP[p][2];
+        const int vb[4] = {0, 1 << a1, (1 << a1) | (1 << a2), 7};
+        if (qb != vb[0] && qb != vb[1] && qb != vb[2] && qb != vb[3]) continue;
+        int off[4], sl[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int rx = dx - 1 + (vb[k] & 1), ry = dy - 1 + ((vb[k] >> 1) & 1), rz = dz - 1 + ((vb[k] >> 2) & 1);
+          off[k] = (rz * TILE + ry) * TILE + rx;
+          sl[k] = slot_of_rel(rx, ry, rz);
+        }
+        double w[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const double* ta = tile + a * TILE3 + ti;
+          w[a] = wv * (ta[off[0]] + ta[off[1]] + ta[off[2]] + ta[off[3]] + un[a]);
+        }
+        // grad phi_0 = -e_a1/h, grad phi_1 = e_a1/h - e_a2/h, grad phi_2 = e_a2/h - e_a3/h, grad phi_3 = e_a3/h
+        const double g1 = w[a1] * ih[a1], g2 = w[a2] * ih[a2], g3 = w[a3] * ih[a3];
+        cf[sl[0]] -= g1;
+        cf[sl[1]] += g1 - g2;
+        cf[sl[2]] += g2 - g3;
+        cf[sl[3]] += g3;
       }
-    });
+    }
   }
 #pragma unroll
   for (int k = 0; k < 15; ++k) {

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
   const uint16_t m = g.meta[s];
   const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
-  double v[3 * NC];
+  T tv[3 * NC];
   for (int c = 0; c < NC; ++c) {
     const int64_t i = c * g.nslots + s;
     T rv = keep ? T(b[i] - y[i]) : T(0);
@@ -114,10 +114,12 @@ __global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict
     r[i] = rv;
     z[i] = zv;
     p[i] = zv;
-    v[3 * c] = dof ? double(rv) * double(zv) : 0.0;
-    v[3 * c + 1] = dof ? double(rv) * double(rv) : 0.0;
-    v[3 * c + 2] = dof ? double(b[i]) * double(b[i]) : 0.0;
+    tv[3 * c] = dof ? rv * zv : T(0);
+    tv[3 * c + 1] = dof ? rv * rv : T(0);
+    tv[3 * c + 2] = dof ? b[i] * b[i] : T(0);
   }
+  double v[3 * NC];
+  warp_presum<T, 3 * NC>(tv, v);
   double* out = partials + (int64_t)gridDim.x * 3 * NC;
   if (!grid_sum_last<3 * NC>(v, partials, counter, g.bseg, g.ninst, out)) return;
   bool any = false;
@@ -155,9 +157,9 @@ __global__ void __launch_bounds__(512) k_cg_update(DevGrid g, T* __restrict__ x,
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
   const uint16_t m = g.meta[s];
   const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
-  double v[2 * NC];
+  T tv[2 * NC];
   for (int c = 0; c < NC; ++c) {
-    v[2 * c] = v[2 * c + 1] = 0.0;
+    tv[2 * c] = tv[2 * c + 1] = T(0);
     if (ki[c].done) continue;
     const T a = T(ki[c].alpha);
     const T* qc = q + c * g.nslots;
@@ -174,10 +176,12 @@ __global__ void __launch_bounds__(512) k_cg_update(DevGrid g, T* __restrict__ x,
     r[i] = rv;
     z[i] = zv;
     if (dof) {
-      v[2 * c] = double(rv) * double(zv);
-      v[2 * c + 1] = double(rv) * double(rv);
+      tv[2 * c] = rv * zv;
+      tv[2 * c + 1] = rv * rv;
     }
   }
+  double v[2 * NC];
+  warp_presum<T, 2 * NC>(tv, v);
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
   if (!grid_sum_last<2 * NC>(v, partials, counter, g.bseg, g.ninst, out)) return;
   bool any = false;
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restric
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
   const uint16_t m = g.meta[s];
   const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
-  double w[2 * NC];
+  T tw[2 * NC];
   for (int c = 0; c < NC; ++c) {
     const int64_t i = c * g.nslots + s;
     T rv = keep ? T(b[i] - y[i]) : T(0);
@@ -218,9 +222,11 @@ __global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restric
     rh[i] = rv;
     p[i] = T(0);
     v[i] = T(0);
-    w[2 * c] = dof ? double(rv) * double(rv) : 0.0;
-    w[2 * c + 1] = dof ? double(b[i]) * double(b[i]) : 0.0;
+    tw[2 * c] = dof ? rv * rv : T(0);
+    tw[2 * c + 1] = dof ? b[i] * b[i] : T(0);
   }
+  double w[2 * NC];
+  warp_presum<T, 2 * NC>(tw, w);
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
   if (!grid_sum_last<2 * NC>(w, partials, counter, g.bseg, g.ninst, out)) return;
   bool any = false;
@@ -272,12 +278,14 @@ __global__ void __launch_bounds__(512) k_bcg_dot(DevGrid g, const T* __restrict_
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
   const uint16_t m = g.meta[s];
   const bool dof = kdof(m, dmask);
-  double w[2 * NC];
+  T tw[2 * NC];
   for (int c = 0; c < NC; ++c) {
     const int64_t i = c * g.nslots + s;
-    w[2 * c] = dof ? double(a1[i]) * double(b1[i]) : 0.0;
-    w[2 * c + 1] = (dof && mode == 1) ? double(a2[i]) * double(a2[i]) : 0.0;
+    tw[2 * c] = dof ? a1[i] * b1[i] : T(0);
+    tw[2 * c + 1] = (dof && mode == 1) ? a2[i] * a2[i] : T(0);
   }
+  double w[2 * NC];
+  warp_presum<T, 2 * NC>(tw, w);
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
   if (!grid_sum_last<2 * NC>(w, partials, counter, g.bseg, g.ninst, out)) return;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
@@ -326,9 +334,9 @@ __global__ void __launch_bounds__(512) k_bcg_xr(DevGrid g, T* __restrict__ x, T*
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
   const uint16_t m = g.meta[s];
   const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
-  double w[2 * NC];
+  T tw[2 * NC];
   for (int c = 0; c < NC; ++c) {
-    w[2 * c] = w[2 * c + 1] = 0.0;
+    tw[2 * c] = tw[2 * c + 1] = T(0);
     if (ki[c].done) continue;
     const int64_t i = c * g.nslots + s;
     const T al = T(ki[c].alpha), om = T(ki[c].omega);
@@ -336,10 +344,12 @@ __global__ void __launch_bounds__(512) k_bcg_xr(DevGrid g, T* __restrict__ x, T*
     T rv = keep ? T(sv[i] - om * tv[i]) : T(0);
     r[i] = rv;
     if (dof) {
-      w[2 * c] = double(rv) * double(rv);
-      w[2 * c + 1] = double(rh[i]) * double(rv);
+      tw[2 * c] = rv * rv;
+      tw[2 * c + 1] = rh[i] * rv;
     }
   }
+  double w[2 * NC];
+  warp_presum<T, 2 * NC>(tw, w);
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
   if (!grid_sum_last<2 * NC>(w, partials, counter, g.bseg, g.ninst, out)) return;
   bool any = false;

@@ -94,3 +94,28 @@ def test_deferred_handle_rules():
         IBBatch([s])              # standalone handles cannot join
     s.close()
     g.close()
+
+
+def test_serving_loop_results_match_alone():
+    """Continuous batching: requests join and leave between epochs; every
+    request's final velocity is bitwise the one it gets alone."""
+    from paper_2007_02082_gb300 import IBBatch, IBGrid
+    from paper_2007_02082_gb300.serve import serve
+    cases = _cases()
+    stream = []
+    for k in range(6):
+        c = dict(cases[k % 3])
+        c["steps"] = 3 + (k % 3) * 2
+        stream.append((0.05 * k, c))
+    got = {}
+    res = serve(stream, precision="mixed", epoch_steps=2, keep=lambda rid, h: got.__setitem__(rid, h.ib_fields_get("U")))
+    s = res.summary()
+    assert s["requests"] == 6 and s["failed"] == 0
+    assert res.epochs >= 3 and max(res.batch_sizes) >= 2
+    for rid, (_, c) in enumerate(stream):
+        g = IBGrid(c, precision="mixed", deferred=True)
+        b = IBBatch([g])
+        b.step(c["steps"])
+        assert np.array_equal(g.ib_fields_get("U"), got[rid]), rid
+        b.close()
+        g.close()
