@@ -154,6 +154,7 @@ typedef struct {
   int32_t iters_mom[3], iters_ib, iters_p, iters_corr[3];
   int32_t outer_mom, outer_p, outer_corr;
   double res_mom, res_ib, res_p, res_corr;   /* final relative residuals */
+  int32_t status_mom, status_ib, status_p, status_corr;   /* last step, per solve */
   int64_t device_bytes;     /* device memory held by the handle */
   int64_t n_valid_slots;    /* stored node copies, all levels (hanging included) */
   /* with desc.profile: accumulated device time and launch count per kernel

@@ -53,7 +53,8 @@ class IbInfo(C.Structure):
         ("iters_mom", C.c_int32 * 3), ("iters_ib", C.c_int32), ("iters_p", C.c_int32),
         ("iters_corr", C.c_int32 * 3), ("outer_mom", C.c_int32), ("outer_p", C.c_int32),
         ("outer_corr", C.c_int32), ("res_mom", C.c_double), ("res_ib", C.c_double), ("res_p", C.c_double),
-        ("res_corr", C.c_double), ("device_bytes", C.c_int64), ("n_valid_slots", C.c_int64),
+        ("res_corr", C.c_double), ("status_mom", C.c_int32), ("status_ib", C.c_int32), ("status_p", C.c_int32),
+        ("status_corr", C.c_int32), ("device_bytes", C.c_int64), ("n_valid_slots", C.c_int64),
         ("prof_ms", C.c_double * 12), ("prof_launches", C.c_int64 * 12), ("kernel_launches", C.c_int64),
     ]
 

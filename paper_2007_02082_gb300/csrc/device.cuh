@@ -75,12 +75,26 @@ struct KState {
   double rz, rz_new, pq, alpha, beta, rr, bb, tol2;
   double rho, omega, rv, ts, tt;
   int32_t iter, max_iter, done, status;   // status: 0 ok, 4 no convergence, 5 breakdown
+  float af, bf, of;                       // alpha, beta, omega rounded once for FP32 kernels
+  float pad;
 };
+
+// scalar of KState in the kernel's precision (FP32 kernels read the mirror)
+template <typename T> __device__ __forceinline__ T k_alpha(const KState& k) {
+  if constexpr (sizeof(T) == 4) return k.af; else return k.alpha;
+}
+template <typename T> __device__ __forceinline__ T k_beta(const KState& k) {
+  if constexpr (sizeof(T) == 4) return k.bf; else return k.beta;
+}
+template <typename T> __device__ __forceinline__ T k_omega(const KState& k) {
+  if constexpr (sizeof(T) == 4) return k.of; else return k.omega;
+}
 
 // FP64 defect-correction loop around an inner solve (mixed precision).
 struct OState {
   double ref[3];     // max(||b||^2, ||r_0||^2) per component, set on the first pass
   double rel2;       // max_c ||r||^2 / ref
+  double prev2;      // rel2 of the previous pass
   double tol2;
   int32_t iter, max_iter, done, status, inner_status, nc;
 };
@@ -115,23 +129,6 @@ __device__ __forceinline__ void load_tile(T* tile, const T* __restrict__ x, int6
   }
 }
 
-// Inner-product contributions: FP32 products are summed in FP32 within each
-// warp and carried in FP64 from there on; FP64 products stay FP64.
-template <typename T, int NV>
-__device__ __forceinline__ void warp_presum(T (&tv)[NV], double (&v)[NV]) {
-  if constexpr (sizeof(T) == 4) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-      for (int o = 16; o > 0; o >>= 1) tv[k] += __shfl_down_sync(0xffffffffu, tv[k], o);
-    const bool l0 = (threadIdx.x & 31) == 0;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = l0 ? double(tv[k]) : 0.0;
-  } else {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = double(tv[k]);
-  }
-}
-
 template <typename T>
 __device__ __forceinline__ const T* stencil_factors(const DevGrid& g, int b) {
   const int idx = (g.binst[b] * 4 + g.blev[b]) * 8;
@@ -139,9 +136,10 @@ __device__ __forceinline__ const T* stencil_factors(const DevGrid& g, int b) {
   else return reinterpret_cast<const T*>(g.sf64) + idx;
 }
 
-// Block-wide sum of NV doubles (blockDim.x a multiple of 32, <= 1024).
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [32*NV] */) {
+// Block-wide sum of NV values of type T (blockDim.x a multiple of 32, <= 1024);
+// the total is valid in thread 0.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T* sh /* [32*NV] */) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k)
@@ -153,29 +151,32 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [32*NV]
   if (w == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      v[k] = lane < nw ? sh[k * 32 + lane] : 0.0;
+      v[k] = lane < nw ? sh[k * 32 + lane] : T(0);
       for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     }
   }
 }
 
-// Deterministic segmented grid reduction.  Every block writes its NV partials;
-// the last block to arrive sums, for every instance i, the partials of blocks
-// [seg[i], seg[i+1]) in a fixed order (warp i mod nwarps: lane l takes blocks
-// seg[i] + l, + 32, ...; then a fixed shuffle tree) and stores the totals in
-// out[i * NV + k].  Returns true in that block only, after a __syncthreads that
-// makes out visible to all its threads.  The counter is reset.  The sum of an
-// instance depends only on its own blocks, so an instance gives bitwise the same
-// totals alone and next to others.
-template <int NV>
-__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* __restrict__ partials,
+// Deterministic segmented grid reduction.  Every block sums its threads' NV
+// contributions in the kernel's precision T (FP32 kernels: FP32 within the
+// block; the GB300 FP64 rate would otherwise dominate) and writes the block
+// totals in FP64; the last block to arrive sums, for every instance i, the
+// partials of blocks [seg[i], seg[i+1]) in FP64 with all its threads (thread t
+// takes the instance's relative blocks t, t + blockDim, ...; then a fixed tree)
+// and stores the totals in out[i * NV + k].  Returns true in that block only,
+// after a __syncthreads that makes out visible to all its threads.  The counter
+// is reset.  An instance's totals depend only on its own blocks and their
+// order, so they are bitwise the same alone and next to other instances.
+template <typename T, int NV>
+__device__ __forceinline__ bool grid_sum_last(T (&v)[NV], double* __restrict__ partials,
                                               unsigned* __restrict__ counter, const int32_t* __restrict__ seg,
                                               int nseg, double* __restrict__ out) {
-  __shared__ double sh[32 * NV];
+  __shared__ T sht[32 * NV];
+  __shared__ double shd[32 * NV];
   __shared__ bool last;
-  block_sum<NV>(v, sh);
+  block_sum<T, NV>(v, sht);
   if (threadIdx.x == 0) {
-    for (int k = 0; k < NV; ++k) partials[(int64_t)blockIdx.x * NV + k] = v[k];
+    for (int k = 0; k < NV; ++k) partials[(int64_t)blockIdx.x * NV + k] = double(v[k]);
     __threadfence();
     unsigned prev = atomicAdd(counter, 1u);
     last = (prev == gridDim.x - 1);
@@ -183,15 +184,13 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* __restric
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = w; i < nseg; i += nw) {
+  for (int i = 0; i < nseg; ++i) {
     double acc[NV];
     for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-    for (int64_t b = seg[i] + lane; b < seg[i + 1]; b += 32)
+    for (int64_t b = seg[i] + threadIdx.x; b < seg[i + 1]; b += blockDim.x)
       for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + b * NV + k);
-    for (int k = 0; k < NV; ++k)
-      for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-    if (lane == 0)
+    block_sum<double, NV>(acc, shd);
+    if (threadIdx.x == 0)
       for (int k = 0; k < NV; ++k) out[(int64_t)i * NV + k] = acc[k];
   }
   __threadfence_block();

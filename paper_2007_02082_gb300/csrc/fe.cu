@@ -128,20 +128,19 @@ enum Post : int { POST_NONE = 0, POST_CG_ALPHA = 1 };
 
 // p.Ap per instance and component -> alpha = r.z / p.Ap
 template <typename T, int NC>
-__device__ __forceinline__ void cg_alpha_post(const DevGrid& g, T (&tv)[NC], KState* ks, double* partials,
+__device__ __forceinline__ void cg_alpha_post(const DevGrid& g, T (&v)[NC], KState* ks, double* partials,
                                               unsigned* counter) {
-  double v[NC];
-  warp_presum<T, NC>(tv, v);
   double* out = partials + (int64_t)gridDim.x * NC;
-  if (!grid_sum_last<NC>(v, partials, counter, g.bseg, g.ninst, out)) return;
+  if (!grid_sum_last<T, NC>(v, partials, counter, g.bseg, g.ninst, out)) return;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
     for (int c = 0; c < NC; ++c) {
       KState& k = ks[i * NC + c];
       if (k.done) continue;
       const double pq = out[i * NC + c];
       k.pq = pq;
-      if (!(pq > 0.0) || !isfinite(pq)) { k.done = 1; k.status = 5; k.alpha = 0.0; continue; }
+      if (!(pq > 0.0) || !isfinite(pq)) { k.done = 1; k.status = 5; k.alpha = 0.0; k.af = 0.f; continue; }
       k.alpha = k.rz / pq;
+      k.af = float(k.alpha);
     }
 }
 
@@ -176,7 +175,7 @@ __global__ void __launch_bounds__(512) k_apply(DevGrid g, const T* __restrict__ 
   }
   if (FUSEP) {
     T beta[NC];
-    for (int c = 0; c < NC; ++c) beta[c] = T(ki[c].beta);
+    for (int c = 0; c < NC; ++c) beta[c] = k_beta<T>(ki[c]);
     const int32_t* nb27 = g.bnbr + 27 * b;
     for (int t = threadIdx.x; t < TILE3; t += blockDim.x) {
       int hx = t % TILE, hy = (t / TILE) % TILE, hz = t / (TILE * TILE);

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(IBB) k_af_apply(IBDev ib, const double* __rest
     }
   if (mode == 0) return;
   double* out = partials + (int64_t)gridDim.x * 3;
-  if (!grid_sum_last<3>(v, partials, counter, ib.seg_w, ib.ninst, out)) return;
+  if (!grid_sum_last<double, 3>(v, partials, counter, ib.seg_w, ib.ninst, out)) return;
   for (int n = threadIdx.x; n < ib.ninst; n += blockDim.x)
     for (int c = 0; c < 3; ++c) {
       KState& k = ks[n * 3 + c];
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(IBB) k_af_start(IBDev ib, const double* __rest
       v[3 * c + 2] = b[3 * i + c] * b[3 * i + c];
     }
   double* out = partials + (int64_t)gridDim.x * 9;
-  if (!grid_sum_last<9>(v, partials, counter, ib.seg_t, ib.ninst, out)) return;
+  if (!grid_sum_last<double, 9>(v, partials, counter, ib.seg_t, ib.ninst, out)) return;
   bool any = false;
   for (int n = threadIdx.x; n < ib.ninst; n += blockDim.x)
     for (int c = 0; c < 3; ++c) {
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(IBB) k_af_update(IBDev ib, double* __restrict_
     }
   }
   double* out = partials + (int64_t)gridDim.x * 6;
-  if (!grid_sum_last<6>(v, partials, counter, ib.seg_t, ib.ninst, out)) return;
+  if (!grid_sum_last<double, 6>(v, partials, counter, ib.seg_t, ib.ninst, out)) return;
   bool any = false;
   for (int n = threadIdx.x; n < ib.ninst; n += blockDim.x)
     for (int c = 0; c < 3; ++c) {
