@@ -114,7 +114,10 @@ typedef struct {
  *                       snapshot only; the problem is advanced by ib_batch_step
  *                       together with other deferred problems
  *   stream              cudaStream_t on which all work is enqueued
- *   dev_alloc/dev_free  optional device allocator (ctx = alloc_ctx)
+ *   dev_alloc/dev_free  optional device allocator (ctx = alloc_ctx); every
+ *                       block it returns must start on a 256-byte boundary
+ *                       (the streaming kernels use 16-byte vector accesses);
+ *                       a misaligned block fails the call with IB_ENOMEM
  */
 typedef struct {
   double origin[3], extent[3];

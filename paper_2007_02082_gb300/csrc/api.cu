@@ -185,6 +185,7 @@ ib_status dalloc(Engine& E, T** p, int64_t n, bool zero = false) {
   void* ptr = raw_alloc(E.alloc, E.actx, bytes);
   if (!ptr) { E.err = "device allocation failed"; return IB_ENOMEM; }
   E.allocs.push_back(ptr);
+  if (reinterpret_cast<uintptr_t>(ptr) % 256) { E.err = "device allocator returned a block not 256-byte aligned"; return IB_ENOMEM; }
   E.bytes += int64_t(bytes);
   *p = static_cast<T*>(ptr);
   if (zero) CK(cudaMemsetAsync(ptr, 0, bytes, E.st));
@@ -309,6 +310,14 @@ ib_status engine_build(Engine& E) {
     nport += d.n_ports;
   }
   bseg[n] = int32_t(E.nbricks);
+  // chunks of up to 8 bricks, never straddling two instances
+  std::vector<int32_t> cbrick, cseg(n + 1);
+  for (int i = 0; i < n; ++i) {
+    cseg[i] = int32_t(cbrick.size());
+    for (int32_t b = bseg[i]; b < bseg[i + 1]; b += 8) cbrick.push_back(b);
+  }
+  cseg[n] = int32_t(cbrick.size());
+  cbrick.push_back(int32_t(E.nbricks));
   E.n_inlet = int64_t(ins.size());
   E.n_valid = 0;
   for (uint16_t m : meta)
@@ -330,6 +339,9 @@ ib_status engine_build(Engine& E) {
   TRY(upload(E, &d_bnbr, bnbr));
   TRY(upload(E, &d_meta, meta));
   TRY(upload(E, &d_hl, hl));
+  int32_t *d_cbrick, *d_cseg;
+  TRY(upload(E, &d_cbrick, cbrick));
+  TRY(upload(E, &d_cseg, cseg));
   TRY(upload(E, &d_sf64, sf));
   TRY(upload(E, &d_sf32, sf32));
   TRY(upload(E, &E.pdt, pdt));
@@ -343,6 +355,9 @@ ib_status engine_build(Engine& E) {
   TRY(upload(E, &d_hp1, hp1));
   TRY(upload(E, &d_hp2, hp2));
   g.blev = d_blev; g.binst = d_binst; g.bseg = d_bseg; g.bnbr = d_bnbr; g.meta = d_meta;
+  g.nchunks = int32_t(cbrick.size()) - 1;
+  g.cbrick = d_cbrick;
+  g.cseg = d_cseg;
   g.hl = d_hl; g.pdt = E.pdt; g.pnu = d_pnu; g.sf64 = d_sf64; g.sf32 = d_sf32;
   g.n_if = int32_t(ifc.size());
   g.if_c = d_ifc; g.if_f = d_iff; g.if_off = d_ifo; g.if_kid = d_ifk; g.if_of_slot = d_ifos;

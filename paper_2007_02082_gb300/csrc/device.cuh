@@ -48,6 +48,11 @@ struct DevGrid {
   const int32_t* __restrict__ binst;  // [nbricks] instance of each brick
   const int32_t* __restrict__ bseg;   // [ninst + 1] brick range of each instance
   const int32_t* __restrict__ bnbr;   // [nbricks][27]
+  // chunks: runs of up to 8 consecutive bricks of one instance, one CTA each
+  // for the streaming Krylov kernels; cseg gives each instance's chunk range
+  int32_t nchunks;
+  const int32_t* __restrict__ cbrick; // [nchunks + 1] first brick of each chunk
+  const int32_t* __restrict__ cseg;   // [ninst + 1]
   const uint16_t* __restrict__ meta;  // [nslots]
   const double* __restrict__ hl;      // [ninst][4][3] cell spacing per instance and level
   // stencil factors per instance and level, [ninst][4][8]:

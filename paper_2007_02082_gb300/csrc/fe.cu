@@ -569,6 +569,91 @@ static inline int nblk(int64_t n, int bs = 256) {
   return int(std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 16));
 }
 
+// CG iteration kernel for the Poisson operator (the hot loop of the step):
+// one CTA per chunk of bricks; for each brick p_new = z + beta p_old is formed
+// for the brick's own nodes (one coalesced load per array and thread) and for
+// the six face halos (threads 0..383, one face node each; index math done once
+// per thread), q = K p_new by the 7-point stencil (interior nodes: the brick
+// level's constant coefficients; boundary nodes: the incident-cell mask
+// table), and p.q is accumulated per thread across the chunk.
+template <typename T>
+__global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restrict__ z, const T* __restrict__ pold,
+                                                    T* __restrict__ pnew, T* __restrict__ q, uint16_t dmask,
+                                                    KState* __restrict__ ks, double* __restrict__ partials,
+                                                    unsigned* __restrict__ counter) {
+  KCOUNT();
+  __shared__ T tile[TILE3];
+  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const KState& k = ks[g.binst[b0]];
+  T acc = T(0);
+  if (!k.done) {
+    const T beta = k_beta<T>(k);
+    const int t = threadIdx.x;
+    const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+    const int ti = tile_index(lx, ly, lz);
+    // face halo element of this thread (t < 384)
+    int fnb = 13, fli = 0, fti = 0;
+    if (t < 384) {
+      const int f = t >> 6, u = t & 7, v = (t >> 3) & 7;
+      int hx, hy, hz, ox = 0, oy = 0, oz = 0, gx, gy, gz;
+      if (f < 2) { hx = f ? 8 : -1; hy = u; hz = v; ox = f ? 1 : -1; gx = f ? 0 : 7; gy = u; gz = v; }
+      else if (f < 4) { hx = u; hy = (f & 1) ? 8 : -1; hz = v; oy = (f & 1) ? 1 : -1; gx = u; gy = (f & 1) ? 0 : 7; gz = v; }
+      else { hx = u; hy = v; hz = (f & 1) ? 8 : -1; oz = (f & 1) ? 1 : -1; gx = u; gy = v; gz = (f & 1) ? 0 : 7; }
+      fnb = (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1);
+      fli = (gz * DBS + gy) * DBS + gx;
+      fti = tile_index(hx, hy, hz);
+    }
+    for (int bb = b0; bb < b1; ++bb) {
+      const int64_t s = (int64_t)bb * DBV + t;
+      const T pv = T(z[s] + beta * pold[s]);
+      tile[ti] = pv;
+      if (t < 384) {
+        const int nb = g.bnbr[27 * bb + fnb];
+        const int64_t fs = (int64_t)nb * DBV + fli;
+        tile[fti] = nb >= 0 ? T(z[fs] + beta * pold[fs]) : T(0);
+      }
+      const uint16_t m = g.meta[s];
+      __syncthreads();
+      T out = T(0);
+      if (m & D_VALID) {
+        const int mask = m & 0xFF;
+        const T* F = stencil_factors<T>(g, bb);
+        const T xm = tile[ti - 1], xp = tile[ti + 1], ym = tile[ti - TILE], yp = tile[ti + TILE];
+        const T zm = tile[ti - TILE * TILE], zp = tile[ti + TILE * TILE];
+        // number of Kuhn tetrahedra (weighted 2 where the edge runs from the
+        // cell's (0,0,0) or to its (1,1,1) corner, else 1) that hold each axis
+        // edge, from the incident-cell bits (bit dz*4 + dy*2 + dx): the P1
+        // stiffness is -(V/6)/h_a^2 times this weight, the diagonal their sum
+        const int b = mask;
+        auto bit = [b](int k) { return (b >> k) & 1; };
+        const int wxp = 2 * bit(1) + bit(3) + bit(5) + 2 * bit(7), wxm = 2 * bit(0) + bit(2) + bit(4) + 2 * bit(6);
+        const int wyp = 2 * bit(2) + bit(3) + bit(6) + 2 * bit(7), wym = 2 * bit(0) + bit(1) + bit(4) + 2 * bit(5);
+        const int wzp = 2 * bit(4) + bit(5) + bit(6) + 2 * bit(7), wzm = 2 * bit(0) + bit(1) + bit(2) + 2 * bit(3);
+        const T fx = F[0], fy = F[1], fz = F[2];
+        out = fx * (T(wxp) * (pv - xp) + T(wxm) * (pv - xm)) + fy * (T(wyp) * (pv - yp) + T(wym) * (pv - ym)) +
+              fz * (T(wzp) * (pv - zp) + T(wzm) * (pv - zm));
+      }
+      if (m & dmask) out = T(0);
+      q[s] = out;
+      pnew[s] = pv;
+      acc += pv * out;
+      __syncthreads();
+    }
+  }
+  T v[1] = {acc};
+  double* out = partials + (int64_t)gridDim.x;
+  if (!grid_sum_last<T, 1>(v, partials, counter, g.cseg, g.ninst, out)) return;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
+    KState& kk = ks[i];
+    if (kk.done) continue;
+    const double pq = out[i];
+    kk.pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) { kk.done = 1; kk.status = 5; kk.alpha = 0.0; kk.af = 0.f; continue; }
+    kk.alpha = kk.rz / pq;
+    kk.af = float(kk.alpha);
+  }
+}
+
 template <typename T, int NC, bool FUSEP = false>
 static void launch_apply(const DevGrid& g, int op, const T* x, T* y, const T* coef, uint16_t dmask, int post,
                          KState* ks, RedBuf rb, cudaStream_t st, const T* zf = nullptr, T* pnew = nullptr) {
@@ -586,7 +671,9 @@ static void launch_apply(const DevGrid& g, int op, const T* x, T* y, const T* co
 template <typename T>
 void fe_apply_cg(const DevGrid& g, const OpDesc<T>& A, int nc, const T* z, const T* pold, T* pnew, T* q, KState* ks,
                  RedBuf rb, cudaStream_t st) {
-  if (nc == 1) launch_apply<T, 1, true>(g, A.op, pold, q, A.coef, A.dmask, POST_CG_ALPHA, ks, rb, st, z, pnew);
+  if (nc == 1 && A.op == OP_POISSON)
+    IBG_LAUNCH(k_poisson_cg<T>, g.nchunks, DBV, 0, st, g, z, pold, pnew, q, A.dmask, ks, rb.partials, rb.counter);
+  else if (nc == 1) launch_apply<T, 1, true>(g, A.op, pold, q, A.coef, A.dmask, POST_CG_ALPHA, ks, rb, st, z, pnew);
   else launch_apply<T, 3, true>(g, A.op, pold, q, A.coef, A.dmask, POST_CG_ALPHA, ks, rb, st, z, pnew);
 }
 

@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict
   if (threadIdx.x == 0) set_cond(cond, any);
 }
 
+// One CTA per chunk of bricks; every thread walks its node of each brick.
 template <typename T, int NC>
 __global__ void __launch_bounds__(512) k_cg_update(DevGrid g, T* __restrict__ x, T* __restrict__ r,
                                                    T* __restrict__ z, const T* __restrict__ p,
@@ -152,35 +153,45 @@ __global__ void __launch_bounds__(512) k_cg_update(DevGrid g, T* __restrict__ x,
                                                    uint16_t dmask, KState* ks, double* partials, unsigned* counter,
                                                    Cond cond) {
   KCOUNT();
-  const KState* ki = ks + g.binst[blockIdx.x] * NC;
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
-  T tv[2 * NC];
+  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const KState* ki = ks + g.binst[b0] * NC;
+  bool act[NC];
+  T a[NC];
   for (int c = 0; c < NC; ++c) {
-    tv[2 * c] = tv[2 * c + 1] = T(0);
-    if (ki[c].done) continue;
-    const T a = k_alpha<T>(ki[c]);
-    const T* qc = q + c * g.nslots;
-    const int64_t i = c * g.nslots + s;
-    T qv = qc[s];
-    if (m & D_IFACE) {   // interface sum: both copies + half of each hanging child
-      const int e = g.if_of_slot[s];
-      qv = qc[g.if_c[e]] + qc[g.if_f[e]];
-      for (int k = g.if_off[e]; k < g.if_off[e + 1]; ++k) qv += T(0.5) * qc[g.if_kid[k]];
-    }
-    if (m & D_VALID) x[i] += a * p[i];
-    T rv = keep ? T(r[i] - a * qv) : T(0);
-    T zv = rv * dinv[s];
-    r[i] = rv;
-    z[i] = zv;
-    if (dof) {
-      tv[2 * c] = rv * zv;
-      tv[2 * c + 1] = rv * rv;
+    act[c] = !ki[c].done;
+    a[c] = k_alpha<T>(ki[c]);
+  }
+  T tv[2 * NC];
+  for (int c = 0; c < 2 * NC; ++c) tv[c] = T(0);
+#pragma unroll 4
+  for (int bb = b0; bb < b1; ++bb) {
+    const int64_t s = (int64_t)bb * DBV + threadIdx.x;
+    const uint16_t m = g.meta[s];
+    const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
+    const T di = dinv[s];
+    for (int c = 0; c < NC; ++c) {
+      if (!act[c]) continue;
+      const T* qc = q + c * g.nslots;
+      const int64_t i = c * g.nslots + s;
+      T qv = qc[s];
+      if (m & D_IFACE) {   // interface sum: both copies + half of each hanging child
+        const int e = g.if_of_slot[s];
+        qv = qc[g.if_c[e]] + qc[g.if_f[e]];
+        for (int k = g.if_off[e]; k < g.if_off[e + 1]; ++k) qv += T(0.5) * qc[g.if_kid[k]];
+      }
+      if (m & D_VALID) x[i] += a[c] * p[i];
+      T rv = keep ? T(r[i] - a[c] * qv) : T(0);
+      T zv = rv * di;
+      r[i] = rv;
+      z[i] = zv;
+      if (dof) {
+        tv[2 * c] += rv * zv;
+        tv[2 * c + 1] += rv * rv;
+      }
     }
   }
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
-  if (!grid_sum_last<T, 2 * NC>(tv, partials, counter, g.bseg, g.ninst, out)) return;
+  if (!grid_sum_last<T, 2 * NC>(tv, partials, counter, g.cseg, g.ninst, out)) return;
   bool any = false;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
     for (int c = 0; c < NC; ++c) {
@@ -197,6 +208,88 @@ __global__ void __launch_bounds__(512) k_cg_update(DevGrid g, T* __restrict__ x,
       k.rz = rzn;
       any = true;
     }
+  any = block_any(any);
+  if (threadIdx.x == 0) set_cond(cond, any);
+}
+
+// Streaming form of k_cg_update for one component: each thread handles W =
+// 16 / sizeof(T) consecutive slots with 16-byte loads and stores; slots of
+// interface copies take the interface sum of q one by one.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; using mt = uint2; static constexpr int W = 4; };
+template <> struct Vec16<double> { using type = double2; using mt = uint32_t; static constexpr int W = 2; };
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_cg_update_vec(DevGrid g, T* __restrict__ x, T* __restrict__ r,
+                                                       T* __restrict__ z, const T* __restrict__ p,
+                                                       const T* __restrict__ q, const T* __restrict__ dinv,
+                                                       uint16_t dmask, KState* ks, double* partials,
+                                                       unsigned* counter, Cond cond) {
+  KCOUNT();
+  using V = typename Vec16<T>::type;
+  using MT = typename Vec16<T>::mt;
+  constexpr int W = Vec16<T>::W;
+  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const KState& k = ks[g.binst[b0]];
+  T tv[2] = {T(0), T(0)};
+  if (!k.done) {
+    const T a = k_alpha<T>(k);
+    const int64_t s1 = (int64_t)b1 * DBV;
+    for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
+      const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
+      const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+      V xv = *reinterpret_cast<const V*>(x + s);
+      V rv = *reinterpret_cast<const V*>(r + s);
+      V pv = *reinterpret_cast<const V*>(p + s);
+      V qv = *reinterpret_cast<const V*>(q + s);
+      V dv = *reinterpret_cast<const V*>(dinv + s);
+      T* xe = reinterpret_cast<T*>(&xv);
+      T* re = reinterpret_cast<T*>(&rv);
+      T* pe = reinterpret_cast<T*>(&pv);
+      T* qe = reinterpret_cast<T*>(&qv);
+      T* de = reinterpret_cast<T*>(&dv);
+      V zv;
+      T* ze = reinterpret_cast<T*>(&zv);
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        const uint16_t m = mm[j];
+        T qq = qe[j];
+        if (m & D_IFACE) {
+          const int e = g.if_of_slot[s + j];
+          qq = q[g.if_c[e]] + q[g.if_f[e]];
+          for (int kk = g.if_off[e]; kk < g.if_off[e + 1]; ++kk) qq += T(0.5) * q[g.if_kid[kk]];
+        }
+        if (m & D_VALID) xe[j] += a * pe[j];
+        const T rn = kkeep(m, dmask) ? T(re[j] - a * qq) : T(0);
+        re[j] = rn;
+        ze[j] = rn * de[j];
+        if (kdof(m, dmask)) {
+          tv[0] += rn * ze[j];
+          tv[1] += rn * rn;
+        }
+      }
+      *reinterpret_cast<V*>(x + s) = xv;
+      *reinterpret_cast<V*>(r + s) = rv;
+      *reinterpret_cast<V*>(z + s) = zv;
+    }
+  }
+  double* out = partials + (int64_t)gridDim.x * 2;
+  if (!grid_sum_last<T, 2>(tv, partials, counter, g.cseg, g.ninst, out)) return;
+  bool any = false;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
+    KState& kk = ks[i];
+    if (kk.done) continue;
+    kk.iter++;
+    kk.rr = out[(int64_t)i * 2 + 1];
+    const double rzn = out[(int64_t)i * 2];
+    if (!isfinite(kk.rr) || !isfinite(rzn)) { kk.done = 1; kk.status = 5; continue; }
+    if (kk.rr <= kk.tol2 * kk.bb) { kk.done = 1; continue; }
+    if (kk.iter >= kk.max_iter) { kk.done = 1; kk.status = 4; continue; }
+    kk.beta = rzn / kk.rz;
+    kk.bf = float(kk.beta);
+    kk.rz = rzn;
+    any = true;
+  }
   any = block_any(any);
   if (threadIdx.x == 0) set_cond(cond, any);
 }
@@ -482,8 +575,12 @@ static cudaError_t cg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b
     fe_apply_cg<T>(g, A, NC, w.z, pold, pnew, w.q, a.ks, rb, s);
     pend(a.prof, s);
     pbegin(a.prof, a.pbase + 1, s);
-    IBG_LAUNCH((k_cg_update<T, NC>), g.nbricks, DBV, 0, s, g, x, w.r, w.z, pnew, w.q, A.dinv, A.dmask, a.ks,
-               rb.partials, rb.counter, c);
+    if (NC == 1)
+      IBG_LAUNCH((k_cg_update_vec<T>), g.nchunks, DBV, 0, s, g, x, w.r, w.z, pnew, w.q, A.dinv, A.dmask, a.ks,
+                 rb.partials, rb.counter, c);
+    else
+      IBG_LAUNCH((k_cg_update<T, NC>), g.nchunks, DBV, 0, s, g, x, w.r, w.z, pnew, w.q, A.dinv, A.dmask, a.ks,
+                 rb.partials, rb.counter, c);
     pend(a.prof, s);
     fe_expand2<T>(g, NC, w.z, (T*)nullptr, s);
   };
