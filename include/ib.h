@@ -274,6 +274,39 @@ ib_status ib_batch_info(const ib_batch* b, int32_t member, ib_info* out);
 const char* ib_batch_last_error(const ib_batch* b);
 void ib_batch_destroy(ib_batch* b);
 
+/*
+ * ib_fields_get_noalloc: ib_fields_get for U, P or Phi of a parked problem (a
+ * deferred handle that no batch holds) without any device allocation.  The
+ * paper has no counterpart: this is a serving-side call.  ib_fields_get on a
+ * parked problem gathers the stored node copies into canonical order in a
+ * temporary device buffer; this call gathers into a fixed 8 MiB scratch array
+ * of the library's own device memory instead.  It is for callers that cannot
+ * allocate device memory at the moment they read a result: a serving loop
+ * that has handed its whole device-memory budget to the batch it is running
+ * (an allocation would fail or would have to evict a running problem), or a
+ * caller whose dev_alloc cannot be entered from the reading thread (an
+ * allocator that the stepping thread holds locked).
+ *
+ *   field          IB_FIELD_U (3 values per node), IB_FIELD_P or IB_FIELD_PHI
+ *   dst, bytes     as ib_fields_get; dst_on_device != 0 for a device pointer
+ *   limit          components x n_nodes <= 1,048,576 values (8 MiB): larger
+ *                  fields fail with IB_EINVAL and a message naming the limit
+ *                  (read them with ib_fields_get)
+ *   errors         IB_ESTATE for a standalone handle or one that a batch
+ *                  holds (read those with ib_fields_get), IB_EINVAL for other
+ *                  fields or a wrong byte count, IB_ECUDA for a CUDA error
+ *
+ * The first call on a device, with that device current, does a one-time setup
+ * (it resolves the scratch's device address, which can load the library's
+ * device code on that device): make that first call before any stream
+ * capture begins in the process.  Nothing in the scratch has to start at
+ * zero: each call writes every value it copies out.  The scratch is shared by
+ * all handles on a device, so overlapping calls would race on it; the library
+ * serialises them with a process-wide lock held until the copy out has
+ * completed, and the call synchronises desc->stream before it returns.
+ */
+ib_status ib_fields_get_noalloc(ib_grid* g, int32_t field, void* dst, size_t bytes, int32_t dst_on_device);
+
 #ifdef __cplusplus
 }
 #endif

@@ -189,6 +189,20 @@ class IBGrid:
         self._check("ib_fields_get", self.lib.ib_fields_get(self.h, FIELD[field], arr.ctypes.data, arr.nbytes, 0))
         return arr
 
+    def ib_fields_get_noalloc(self, field, out=None):
+        """ib_fields_get_noalloc: U, P or PHI of a parked deferred handle, read
+        through the library's fixed device scratch (no device allocation)."""
+        shape, dt = self._shape(field)
+        if out is not None:
+            nbytes = out.numel() * out.element_size()
+            self._check("ib_fields_get_noalloc", self.lib.ib_fields_get_noalloc(
+                self.h, FIELD[field], C.c_void_p(out.data_ptr()), nbytes, 1))
+            return out
+        arr = np.empty(shape, dtype=dt)
+        self._check("ib_fields_get_noalloc",
+                    self.lib.ib_fields_get_noalloc(self.h, FIELD[field], arr.ctypes.data, arr.nbytes, 0))
+        return arr
+
     def ib_fields_set(self, field, values):
         shape, dt = self._shape(field)
         arr = np.ascontiguousarray(values, dtype=dt).reshape(shape)

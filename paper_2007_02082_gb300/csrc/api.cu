@@ -36,6 +36,7 @@
 #include "ib.h"
 #include "ib.hpp"
 #include "krylov.hpp"
+#include "noalloc.hpp"
 #include "setup.hpp"
 
 using namespace ibg;
@@ -1141,6 +1142,25 @@ void ib_batch_destroy(ib_batch* b) {
   }
   engine_free(b->E);
   delete b;
+}
+
+ib_status ib_fields_get_noalloc(ib_grid* g, int32_t field, void* dst, size_t bytes, int32_t dst_on_device) {
+  if (!g) return IB_EINVAL;
+  if (!g->ready) { g->err = "ib_set_boundary has not succeeded"; return IB_ESTATE; }
+  if (field != IB_FIELD_U && field != IB_FIELD_P && field != IB_FIELD_PHI) {
+    g->err = "only U, P and PHI are read without allocation";
+    return IB_EINVAL;
+  }
+  if (int64_t(bytes) != field_bytes(g->H, field)) { g->err = "bad byte count"; return IB_EINVAL; }
+  if (!dst && bytes) return IB_EINVAL;
+  if (g->eng || g->batch) {
+    g->err = "only a deferred handle that no batch holds is read without allocation; use ib_fields_get";
+    return IB_ESTATE;
+  }
+  const int nc = field == IB_FIELD_U ? 3 : 1;
+  const double* src = field == IB_FIELD_U ? g->snap.u : field == IB_FIELD_P ? g->snap.p : g->snap.phi;
+  return noalloc_gather_canon(int64_t(g->H.canon_slot.size()), g->snap.canon, nc, g->H.nbricks * BV, src, dst,
+                              bytes, dst_on_device, static_cast<cudaStream_t>(g->d.stream), g->err);
 }
 
 }  // extern "C"
