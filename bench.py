@@ -124,21 +124,25 @@ class ClockSampler:
 
 # algorithmic bytes per stored node copy and launch, by profiling class
 # (FP32 values in the mixed path's inner solves, FP64 otherwise; meta = 2 B)
-def class_bytes(cls, vb):
+def class_bytes(cls, vb, multigrid=False):
+    """Algorithmic bytes per stored valid node slot of one launch of a kernel class."""
     return {
-        0: 2 * vb + 2,                 # Poisson apply: read p, meta; write q
-        1: 7 * vb + 2,                 # Poisson CG update: x rw, r rw, p, q, D^-1 read; z write; meta
+        0: 4 * vb + 2,                 # Poisson CG stencil: read z, p_old, meta; write p_new, q
+        1: (6 if multigrid else 7) * vb + 2,   # CG update: x rw, r rw, p, q read, meta (+ D^-1 read, z write)
         2: 3 * vb,                     # p = z + beta p: z read, p rw
         3: 6 * vb + 2,                 # mass apply, 3 components
         4: 3 * 6 * vb + vb + 2,        # mass CG update, 3 components + D^-1
         5: 3 * 3 * vb,                 # mass direction update
         6: 15 * vb + 6 * vb + 2,       # momentum apply: 15 coefficients, 3 in, 3 out
+        7: 2 * vb + 2,                 # V-cycle stencil apply: read x, meta; write q
+        8: 5 * vb + 2,                 # V-cycle smoothing update: read z, r, q, D^-1, meta; write z
     }.get(cls)
 
 
-CLASS_NAMES = {0: "k_apply<Poisson> (stencil q = K p, fused p.q)", 1: "k_cg_update<Poisson>",
+CLASS_NAMES = {0: "k_poisson_cg (p = z + beta p, q = K p, fused p.q)", 1: "k_cg_update<Poisson>",
                2: "k_cg_p<Poisson>", 3: "k_apply<mass>", 4: "k_cg_update<mass>", 5: "k_cg_p<mass>",
-               6: "k_apply<momentum 15-point>"}
+               6: "k_apply<momentum 15-point>", 7: "k_poisson_cg<apply> (V-cycle smoothing stencil)",
+               8: "k_mg_c_smooth (V-cycle smoothing update)", 9: "V-cycle transfers and coarse levels"}
 
 
 def run_native(args, rank, world, local_rank):
@@ -149,7 +153,7 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     load_library(build_if_missing=True)
     case = workload(args.workload)
-    g = IBGrid(case, precision=args.precision, device=local_rank)
+    g = IBGrid(case, precision=args.precision, device=local_rank, poisson_pc=args.poisson_pc)
     info0 = g.ib_grid_info()
     cells = info0["n_leaf_cells"]
     stream = torch.cuda.current_stream()
@@ -196,7 +200,7 @@ def run_native(args, rank, world, local_rank):
     # Kernels inside the step graph cannot be bracketed by events, so the same
     # step is replayed eagerly on a second handle (same stream, same kernels,
     # same order) with CUDA events around every solver kernel launch.
-    gp = IBGrid(case, precision=args.precision, device=local_rank, profile=True)
+    gp = IBGrid(case, precision=args.precision, device=local_rank, profile=True, poisson_pc=args.poisson_pc)
     for _ in range(max(1, args.warmup)):
         gp.ipcs_step(1)
     j1 = gp.ib_grid_info()
@@ -209,10 +213,11 @@ def run_native(args, rank, world, local_rank):
     gp.close()
     dms = [j2["prof_ms"][k] - j1["prof_ms"][k] for k in range(12)]
     dn = [j2["prof_launches"][k] - j1["prof_launches"][k] for k in range(12)]
-    dom = max((k for k in CLASS_NAMES if dn[k] > 0), key=lambda k: dms[k])
-    prof_share = {CLASS_NAMES[k]: round(dms[k] / max(sum(dms), 1e-30), 4) for k in CLASS_NAMES if dn[k] > 0}
+    mgon = info0["mg_levels"] > 0
     vb = 4 if args.precision == "mixed" else 8
-    per_launch_bytes = class_bytes(dom, vb) * info0["n_valid_slots"]
+    dom = max((k for k in CLASS_NAMES if dn[k] > 0 and class_bytes(k, vb) is not None), key=lambda k: dms[k])
+    prof_share = {CLASS_NAMES[k]: round(dms[k] / max(sum(dms), 1e-30), 4) for k in CLASS_NAMES if dn[k] > 0}
+    per_launch_bytes = class_bytes(dom, vb, mgon) * info0["n_valid_slots"]
     avg_ms = dms[dom] / dn[dom]
     achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
     peak, peak_src = peaks()
@@ -258,7 +263,10 @@ def run_native(args, rank, world, local_rank):
         "data": "synthetic (seeded analytic geometry)",
         "config": {"workload": case["name"], "grid": list(case["n"]), "max_level": case["max_level"],
                    "leaf_cells": cells, "nodes": info0["n_nodes"], "points": info0["n_points"],
-                   "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                   "precision": args.precision,
+                   "poisson_pc": (f"multigrid V(2,2), {info0['mg_levels']} levels, coarsest {info0['mg_coarsest']}"
+                                  if info0["mg_levels"] else "jacobi"),
+                   "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -313,6 +321,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--poisson-pc", default="multigrid", choices=["multigrid", "jacobi"])
     ap.add_argument("--workload", default="cylinder_64x64x256_L1")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nvtx", action="store_true", help="wrap each timed step in an NVTX range 'ipcs_step'")

@@ -58,6 +58,7 @@ typedef enum {
 enum { IB_INLET_VELOCITY = 0, IB_OUTLET_ZERO_P = 1 };
 enum { IB_PARABOLIC = 0 };
 enum { IB_FP64 = 0, IB_MIXED = 1 };
+enum { IB_PC_MULTIGRID = 0, IB_PC_JACOBI = 1 };
 
 #define IB_MAX_PORTS 8
 #define IB_MAX_HARMONICS 8
@@ -113,6 +114,10 @@ typedef struct {
  *   deferred            1: ib_set_boundary builds the grid and a device state
  *                       snapshot only; the problem is advanced by ib_batch_step
  *                       together with other deferred problems
+ *   poisson_pc          preconditioner of the pressure-increment CG (Eq. 12):
+ *                       IB_PC_MULTIGRID (default; geometric V-cycle over the
+ *                       nested Kuhn meshes, falls back to Jacobi when the
+ *                       hierarchy cannot be built) or IB_PC_JACOBI
  *   stream              cudaStream_t on which all work is enqueued
  *   dev_alloc/dev_free  optional device allocator (ctx = alloc_ctx); every
  *                       block it returns must start on a 256-byte boundary
@@ -130,6 +135,7 @@ typedef struct {
   int32_t profile;          /* 1: time solver kernel launches with CUDA events */
   int32_t deferred;         /* 1: keep only the grid and a state snapshot; the
                                problem is stepped inside an ib_batch */
+  int32_t poisson_pc;       /* IB_PC_MULTIGRID | IB_PC_JACOBI */
   int32_t n_ports;
   ib_port ports[IB_MAX_PORTS];
   void* stream;
@@ -162,10 +168,14 @@ typedef struct {
   int64_t n_valid_slots;    /* stored node copies, all levels (hanging included) */
   /* with desc.profile: accumulated device time and launch count per kernel
      class since ib_set_boundary; class = base + {0 operator apply, 1 vector
-     update, 2 direction update}, base 0 Poisson, 3 mass, 6 momentum */
+     update, 2 direction update}, base 0 Poisson, 3 mass, 6 momentum; the
+     multigrid V-cycle: 7 composite stencil applies, 8 composite smoothing
+     updates, 9 transfers and coarse levels */
   double prof_ms[12];
   int64_t prof_launches[12];
   int64_t kernel_launches;  /* kernels launched by this process's library so far */
+  int32_t mg_levels;        /* multigrid levels below the composite grid (0: Jacobi) */
+  int32_t mg_coarsest;      /* nodes of the coarsest level (dense solve) */
 } ib_info;
 
 /* Field identifiers for ib_fields_get / ib_fields_set. */

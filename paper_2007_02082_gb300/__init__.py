@@ -91,7 +91,7 @@ class IBGrid:
     """One resident IB-FE-IPCS problem (an ib_grid handle)."""
 
     def __init__(self, case, precision="fp64", stream=None, torch_alloc=True, rtol=None, max_iter=0,
-                 device=0, profile=False, deferred=False):
+                 device=0, profile=False, deferred=False, poisson_pc="multigrid"):
         self.lib = load_library()
         self.case = case
         self._alloc = None
@@ -126,6 +126,9 @@ class IBGrid:
         d.max_iter = max_iter
         d.profile = 1 if profile else 0
         d.deferred = 1 if deferred else 0
+        if poisson_pc not in ("multigrid", "jacobi"):
+            raise ValueError("poisson_pc must be 'multigrid' or 'jacobi'")
+        d.poisson_pc = _abi.IB_PC_JACOBI if poisson_pc == "jacobi" else _abi.IB_PC_MULTIGRID
         d.n_ports = len(case["ports"])
         for k, port in enumerate(case["ports"]):
             d.ports[k] = _port_struct(port)

@@ -9,6 +9,7 @@ STATUS_NAMES = {0: "IB_OK", 1: "IB_EINVAL", 2: "IB_ENOMEM", 3: "IB_ESTATE", 4: "
                 5: "IB_EBREAKDOWN", 6: "IB_ECUDA", 7: "IB_ETIMEOUT"}
 IB_INLET_VELOCITY, IB_OUTLET_ZERO_P = 0, 1
 IB_FP64, IB_MIXED = 0, 1
+IB_PC_MULTIGRID, IB_PC_JACOBI = 0, 1
 IB_MAX_PORTS, IB_MAX_HARMONICS, IB_MAX_LEVEL = 8, 8, 3
 
 FIELD = {
@@ -40,7 +41,8 @@ class IbGridDesc(C.Structure):
         ("max_level", C.c_int32), ("refine_band", C.c_int32), ("reduce_band", C.c_int32),
         ("nu", C.c_double), ("rho", C.c_double), ("dt", C.c_double), ("precision", C.c_int32),
         ("rtol_mom", C.c_double), ("rtol_p", C.c_double), ("rtol_corr", C.c_double), ("rtol_ib", C.c_double),
-        ("max_iter", C.c_int32), ("profile", C.c_int32), ("deferred", C.c_int32), ("n_ports", C.c_int32), ("ports", IbPort * IB_MAX_PORTS),
+        ("max_iter", C.c_int32), ("profile", C.c_int32), ("deferred", C.c_int32), ("poisson_pc", C.c_int32),
+        ("n_ports", C.c_int32), ("ports", IbPort * IB_MAX_PORTS),
         ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]
 
@@ -57,6 +59,7 @@ class IbInfo(C.Structure):
         ("res_corr", C.c_double), ("status_mom", C.c_int32), ("status_ib", C.c_int32), ("status_p", C.c_int32),
         ("status_corr", C.c_int32), ("device_bytes", C.c_int64), ("n_valid_slots", C.c_int64),
         ("prof_ms", C.c_double * 12), ("prof_launches", C.c_int64 * 12), ("kernel_launches", C.c_int64),
+        ("mg_levels", C.c_int32), ("mg_coarsest", C.c_int32),
     ]
 
     def as_dict(self):

@@ -56,8 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     newest_hdr = max(os.path.getmtime(h) for h in hdrs)
     jobs, objs = [], []
     for s in srcs:
-        base = os.path.splitext(os.path.basename(s))[0]
-        obj = os.path.join(OUT, base + ".o")
+        obj = os.path.join(OUT, os.path.basename(s).replace(".", "_") + ".o")   # mg.cu and mg.cpp differ
         objs.append(obj)
         stale = force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(s), newest_hdr)
         if not stale:

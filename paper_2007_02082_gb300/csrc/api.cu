@@ -36,6 +36,7 @@
 #include "ib.h"
 #include "ib.hpp"
 #include "krylov.hpp"
+#include "mg.hpp"
 #include "noalloc.hpp"
 #include "setup.hpp"
 
@@ -45,6 +46,7 @@ namespace ibg {
 unsigned long long fe_kcount();
 unsigned long long krylov_kcount();
 unsigned long long ib_kcount();
+unsigned long long mg_kcount();
 }
 
 namespace {
@@ -69,6 +71,7 @@ Tols tolerances(const ib_grid_desc& d) {
 
 struct Engine {
   std::vector<const HostGrid*> H;
+  std::vector<const MGHost*> MG;   // multigrid hierarchy of each problem (ok = false: Jacobi)
   std::vector<ib_grid_desc> D;
   int ninst = 0;
   bool mixed = false;
@@ -108,6 +111,8 @@ struct Engine {
   SolveRec* recs_host = nullptr;
   int32_t* ok_host = nullptr;
   RedBuf rb{};
+  MGDev<float> mg32;
+  MGDev<double> mg64;
   Prof prof;
   bool use_graph = true;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -139,6 +144,7 @@ struct ib_grid {
   std::string err;
   bool ready = false;
   HostGrid H;
+  MGHost mg;                    // Poisson multigrid hierarchy (host)
   Engine* eng = nullptr;        // standalone handle
   Snapshot snap;                // deferred handle
   std::vector<void*> snap_allocs;
@@ -215,6 +221,126 @@ void engine_free(Engine& E) {
   if (E.os_host) { cudaFreeHost(E.os_host); E.os_host = nullptr; }
   if (E.recs_host) { cudaFreeHost(E.recs_host); E.recs_host = nullptr; }
   if (E.ok_host) { cudaFreeHost(E.ok_host); E.ok_host = nullptr; }
+}
+
+// Concatenate the members' multigrid hierarchies level by level and upload
+// them in the engine's Krylov precision T.
+template <typename T>
+ib_status mg_upload(Engine& E, MGDev<T>& D) {
+  const int n = E.ninst;
+  D = MGDev<T>();
+  D.ninst = n;
+  std::vector<uint8_t> on(n, 0);
+  std::vector<int32_t> small(n, -1), coarsest(n, -1);
+  std::vector<int64_t> coff(n, 0);
+  std::vector<T> cinv;
+  int nlev = 0;
+  for (int i = 0; i < n; ++i) {
+    const MGHost* m = E.MG[i];
+    if (!m || !m->ok || int(m->lev.size()) > MG_LEVELS_MAX) continue;
+    on[i] = 1;
+    small[i] = m->small_start;
+    coarsest[i] = int(m->lev.size()) - 1;
+    nlev = std::max(nlev, int(m->lev.size()));
+    D.max_big = std::max(D.max_big, m->small_start);
+    coff[i] = int64_t(cinv.size());
+    const int64_t nk = m->lev.back().nn;
+    for (int64_t r = 0; r < nk; ++r)   // symmetrised: the preconditioner stays symmetric
+      for (int64_t c = 0; c < nk; ++c) cinv.push_back(T(0.5 * (m->cinv[r * nk + c] + m->cinv[c * nk + r])));
+    D.any = true;
+  }
+  D.nlev = nlev;
+  if (!D.any) return IB_OK;
+  std::vector<std::vector<int32_t>> noff(nlev, std::vector<int32_t>(n + 1, 0));
+  for (int k = 0; k < nlev; ++k)
+    for (int i = 0; i < n; ++i) {
+      const MGHost* m = E.MG[i];
+      const int64_t nn = (on[i] && k < int(m->lev.size())) ? m->lev[k].nn : 0;
+      noff[k][i + 1] = int32_t(noff[k][i] + nn);
+    }
+  for (int k = 0; k < nlev; ++k) {
+    MGLevelDev<T>& L = D.lev[k];
+    const int64_t N = noff[k][n];
+    L.n = N;
+    std::vector<int32_t> inst, nbr, rptr(1, 0), rcol, pptr(1, 0), pcol;
+    std::vector<T> offd, diag, dinv, rw, pw;
+    inst.reserve(N);
+    for (int i = 0; i < n; ++i) {
+      if (!on[i] || k >= int(E.MG[i]->lev.size())) continue;
+      const MGLevelHost& M = E.MG[i]->lev[k];
+      const int32_t o = noff[k][i];
+      for (int64_t j = 0; j < M.nn; ++j) {
+        inst.push_back(i);
+        for (int d = 0; d < 6; ++d) {
+          const int32_t nb = M.nbr[6 * j + d];
+          nbr.push_back(nb >= 0 ? nb + o : -1);
+          offd.push_back(T(M.offd[6 * j + d]));
+        }
+        diag.push_back(T(M.diag[j]));
+        dinv.push_back(T(1.0 / M.diag[j]));
+        for (int32_t e = M.r_ptr[j]; e < M.r_ptr[j + 1]; ++e) {
+          const int32_t c = M.r_col[e];
+          rcol.push_back(k == 0 ? int32_t(c + E.slot0[i]) : c + noff[k - 1][i]);
+          rw.push_back(T(M.r_w[e]));
+        }
+        rptr.push_back(int32_t(rcol.size()));
+      }
+    }
+    // prolongation rows over the finer index space: composite slots or level k-1 nodes
+    const int64_t nrows = k == 0 ? E.ns : int64_t(noff[k - 1][n]);
+    pptr.assign(nrows + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      const int64_t r0 = k == 0 ? E.slot0[i] : noff[k - 1][i];
+      const int64_t r1 = k == 0 ? E.slot0[i + 1] : noff[k - 1][i + 1];
+      const bool has = on[i] && k < int(E.MG[i]->lev.size());
+      for (int64_t r = r0; r < r1; ++r) {
+        if (has) {
+          const MGLevelHost& M = E.MG[i]->lev[k];
+          const int64_t lr = r - r0;
+          for (int32_t e = M.p_ptr[lr]; e < M.p_ptr[lr + 1]; ++e) {
+            pcol.push_back(M.p_col[e] + noff[k][i]);
+            pw.push_back(T(M.p_w[e]));
+          }
+        }
+        pptr[r + 1] = int32_t(pcol.size());
+      }
+    }
+    int32_t *d_inst, *d_noff, *d_nbr, *d_rptr, *d_rcol, *d_pptr, *d_pcol;
+    T *d_offd, *d_diag, *d_dinv, *d_rw, *d_pw;
+    TRY(upload(E, &d_inst, inst));
+    TRY(upload(E, &d_noff, noff[k]));
+    TRY(upload(E, &d_nbr, nbr));
+    TRY(upload(E, &d_offd, offd));
+    TRY(upload(E, &d_diag, diag));
+    TRY(upload(E, &d_dinv, dinv));
+    TRY(upload(E, &d_rptr, rptr));
+    TRY(upload(E, &d_rcol, rcol));
+    TRY(upload(E, &d_rw, rw));
+    TRY(upload(E, &d_pptr, pptr));
+    TRY(upload(E, &d_pcol, pcol));
+    TRY(upload(E, &d_pw, pw));
+    L.inst = d_inst; L.noff = d_noff; L.nbr = d_nbr; L.offd = d_offd; L.diag = d_diag; L.dinv = d_dinv;
+    L.rptr = d_rptr; L.rcol = d_rcol; L.rw = d_rw; L.pptr = d_pptr; L.pcol = d_pcol; L.pw = d_pw;
+    TRY(dalloc(E, &L.b, N, true));
+    TRY(dalloc(E, &L.xa, N, true));
+    TRY(dalloc(E, &L.xb, N, true));
+    TRY(dalloc(E, &L.res, N, true));
+  }
+  std::vector<MGLevelDev<T>> lv(D.lev, D.lev + nlev);
+  MGLevelDev<T>* d_lev;
+  TRY(upload(E, &d_lev, lv));
+  D.dlev = d_lev;
+  uint8_t* d_on;
+  int32_t *d_small, *d_coarsest;
+  int64_t* d_coff;
+  T* d_cinv;
+  TRY(upload(E, &d_on, on));
+  TRY(upload(E, &d_small, small));
+  TRY(upload(E, &d_coarsest, coarsest));
+  TRY(upload(E, &d_coff, coff));
+  TRY(upload(E, &d_cinv, cinv));
+  D.on = d_on; D.small = d_small; D.coarsest = d_coarsest; D.cinv_off = d_coff; D.cinv = d_cinv;
+  return IB_OK;
 }
 
 // Concatenate the members' host grids, upload, and build the constant
@@ -402,6 +528,10 @@ ib_status engine_build(Engine& E) {
     TRY(dalloc(E, &E.w32, 8 * 3 * ns, true));
   }
 
+  // ---- Poisson multigrid, in the precision of the inner Krylov iterations
+  if (E.mixed) TRY(mg_upload<float>(E, E.mg32));
+  else TRY(mg_upload<double>(E, E.mg64));
+
   // ---- IB, rows padded per instance to whole 256-row blocks
   std::vector<double> X(3 * Mt, 0.0), dSv(Mt, 1.0), UB(3 * Mt, 0.0), pscale(Mt, 0.0), iorg(3 * n), ihf(3 * n),
       icoef(n);
@@ -562,6 +692,10 @@ SolveArgs solve_args(Engine& E, int op, bool bicg, int nc, uint16_t dmask, const
   a.pbase = op == OP_POISSON ? 0 : op == OP_MASS ? 3 : 6;
   a.ks_host = E.ks_host;
   a.os_host = E.os_host;
+  if (op == OP_POISSON) {
+    a.mg32 = E.mixed ? &E.mg32 : nullptr;
+    a.mg64 = E.mixed ? nullptr : &E.mg64;
+  }
   return a;
 }
 
@@ -803,8 +937,10 @@ ib_status engine_fields_set(Engine& E, int i, int32_t field, const void* src, si
   return IB_OK;
 }
 
-void fill_info(const HostGrid& H, const Engine* E, int64_t dev_bytes, ib_info& I) {
+void fill_info(const HostGrid& H, const MGHost* mg, const Engine* E, int64_t dev_bytes, ib_info& I) {
   I.n_nodes = int64_t(H.canon_slot.size());
+  I.mg_levels = (mg && mg->ok) ? int32_t(mg->lev.size()) : 0;
+  I.mg_coarsest = (mg && mg->ok) ? int32_t(mg->lev.back().nn) : 0;
   I.n_dof = H.n_dof;
   I.n_hanging = int64_t(H.hang_slot.size());
   I.n_leaf_cells = 0;
@@ -827,7 +963,7 @@ void fill_info(const HostGrid& H, const Engine* E, int64_t dev_bytes, ib_info& I
     if (m & M_VALID) nv++;
   I.n_valid_slots = nv;
   I.device_bytes = dev_bytes;
-  I.kernel_launches = int64_t(fe_kcount() + krylov_kcount() + ib_kcount());
+  I.kernel_launches = int64_t(fe_kcount() + krylov_kcount() + ib_kcount() + mg_kcount());
   if (E) {
     for (int k = 0; k < Prof::K; ++k) {
       I.prof_ms[k] = E->prof.ms[k];
@@ -843,6 +979,7 @@ ib_status validate_desc(const ib_grid_desc* d) {
   if (d->max_level > 0 && d->refine_band < 1) return IB_EINVAL;
   if (!(d->nu > 0) || !(d->rho > 0) || !(d->dt > 0)) return IB_EINVAL;
   if (d->precision != IB_FP64 && d->precision != IB_MIXED) return IB_EINVAL;
+  if (d->poisson_pc != IB_PC_MULTIGRID && d->poisson_pc != IB_PC_JACOBI) return IB_EINVAL;
   if (d->n_ports < 1 || d->n_ports > IB_MAX_PORTS) return IB_EINVAL;
   bool outlet = false;
   for (int p = 0; p < d->n_ports; ++p) {
@@ -943,6 +1080,8 @@ ib_status ib_set_boundary(ib_grid* g, int64_t M, const double* X, const double* 
   g->ready = false;
   ib_status s = build_host_grid(g->d, M, X, dS, UB, inside, g->H, g->err);
   if (s != IB_OK) return s;
+  g->mg = MGHost();
+  if (g->d.poisson_pc == IB_PC_MULTIGRID) build_mg(g->H, g->mg);
   if (g->d.deferred) {
     s = snap_alloc(g);
     if (s != IB_OK) return s;
@@ -953,6 +1092,7 @@ ib_status ib_set_boundary(ib_grid* g, int64_t M, const double* X, const double* 
   Engine* E = new (std::nothrow) Engine();
   if (!E) return IB_ENOMEM;
   E->H.push_back(&g->H);
+  E->MG.push_back(&g->mg);
   E->D.push_back(g->d);
   E->ninst = 1;
   E->st = static_cast<cudaStream_t>(g->d.stream);
@@ -1037,7 +1177,7 @@ ib_status ib_grid_info(const ib_grid* g, ib_info* out) {
   if (!g->ready) return IB_ESTATE;
   if (g->batch) return ib_batch_info(g->batch, g->batch_index, out);
   ib_info I = g->eng ? g->eng->last[0] : ib_info{};
-  fill_info(g->H, g->eng, g->eng ? g->eng->bytes : g->snap_bytes, I);
+  fill_info(g->H, &g->mg, g->eng, g->eng ? g->eng->bytes : g->snap_bytes, I);
   I.step = g->eng ? g->eng->step[0] : g->snap.step;
   I.time = g->eng ? g->eng->time[0] : g->snap.time;
   *out = I;
@@ -1074,6 +1214,7 @@ ib_status ib_batch_create(ib_grid* const* members, int32_t n, ib_batch** out) {
   for (int i = 0; i < n; ++i) {
     b->members.push_back(members[i]);
     E.H.push_back(&members[i]->H);
+    E.MG.push_back(&members[i]->mg);
     E.D.push_back(members[i]->d);
   }
   E.ninst = n;
@@ -1124,7 +1265,7 @@ ib_status ib_batch_info(const ib_batch* b, int32_t member, ib_info* out) {
   if (!b || !out || member < 0 || member >= b->E.ninst) return IB_EINVAL;
   const Engine& E = b->E;
   ib_info I = E.last[member];
-  fill_info(*E.H[member], &E, E.bytes, I);
+  fill_info(*E.H[member], E.MG[member], &E, E.bytes, I);
   I.step = E.step[member];
   I.time = E.time[member];
   *out = I;

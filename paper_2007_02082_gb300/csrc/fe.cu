@@ -576,18 +576,24 @@ static inline int nblk(int64_t n, int bs = 256) {
 // per thread), q = K p_new by the 7-point stencil (interior nodes: the brick
 // level's constant coefficients; boundary nodes: the incident-cell mask
 // table), and p.q is accumulated per thread across the chunk.
-template <typename T>
+//
+// With CG = false the kernel is a plain local apply q = K z (no direction
+// update, no reduction) over the chunks of problems that are not done and,
+// when `on` is given, use multigrid.
+template <typename T, bool CG>
 __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restrict__ z, const T* __restrict__ pold,
                                                     T* __restrict__ pnew, T* __restrict__ q, uint16_t dmask,
                                                     KState* __restrict__ ks, double* __restrict__ partials,
-                                                    unsigned* __restrict__ counter) {
+                                                    unsigned* __restrict__ counter, const uint8_t* __restrict__ on) {
   KCOUNT();
   __shared__ T tile[TILE3];
   const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
-  const KState& k = ks[g.binst[b0]];
+  const int inst = g.binst[b0];
+  const KState& k = ks[inst];
   T acc = T(0);
+  if (!CG && (k.done || (on && !on[inst]))) return;
   if (!k.done) {
-    const T beta = k_beta<T>(k);
+    const T beta = CG ? k_beta<T>(k) : T(0);
     const int t = threadIdx.x;
     const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
     const int ti = tile_index(lx, ly, lz);
@@ -605,12 +611,12 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
     }
     for (int bb = b0; bb < b1; ++bb) {
       const int64_t s = (int64_t)bb * DBV + t;
-      const T pv = T(z[s] + beta * pold[s]);
+      const T pv = CG ? T(z[s] + beta * pold[s]) : z[s];
       tile[ti] = pv;
       if (t < 384) {
         const int nb = g.bnbr[27 * bb + fnb];
         const int64_t fs = (int64_t)nb * DBV + fli;
-        tile[fti] = nb >= 0 ? T(z[fs] + beta * pold[fs]) : T(0);
+        tile[fti] = nb >= 0 ? (CG ? T(z[fs] + beta * pold[fs]) : z[fs]) : T(0);
       }
       const uint16_t m = g.meta[s];
       __syncthreads();
@@ -635,11 +641,14 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
       }
       if (m & dmask) out = T(0);
       q[s] = out;
-      pnew[s] = pv;
-      acc += pv * out;
+      if (CG) {
+        pnew[s] = pv;
+        acc += pv * out;
+      }
       __syncthreads();
     }
   }
+  if (!CG) return;
   T v[1] = {acc};
   double* out = partials + (int64_t)gridDim.x;
   if (!grid_sum_last<T, 1>(v, partials, counter, g.cseg, g.ninst, out)) return;
@@ -672,9 +681,17 @@ template <typename T>
 void fe_apply_cg(const DevGrid& g, const OpDesc<T>& A, int nc, const T* z, const T* pold, T* pnew, T* q, KState* ks,
                  RedBuf rb, cudaStream_t st) {
   if (nc == 1 && A.op == OP_POISSON)
-    IBG_LAUNCH(k_poisson_cg<T>, g.nchunks, DBV, 0, st, g, z, pold, pnew, q, A.dmask, ks, rb.partials, rb.counter);
+    IBG_LAUNCH((k_poisson_cg<T, true>), g.nchunks, DBV, 0, st, g, z, pold, pnew, q, A.dmask, ks, rb.partials,
+               rb.counter, (const uint8_t*)nullptr);
   else if (nc == 1) launch_apply<T, 1, true>(g, A.op, pold, q, A.coef, A.dmask, POST_CG_ALPHA, ks, rb, st, z, pnew);
   else launch_apply<T, 3, true>(g, A.op, pold, q, A.coef, A.dmask, POST_CG_ALPHA, ks, rb, st, z, pnew);
+}
+
+template <typename T>
+void fe_poisson_apply(const DevGrid& g, const T* x, T* q, uint16_t dmask, KState* ks, const uint8_t* on,
+                      cudaStream_t st) {
+  IBG_LAUNCH((k_poisson_cg<T, false>), g.nchunks, DBV, 0, st, g, x, (const T*)nullptr, (T*)nullptr, q, dmask, ks,
+             (double*)nullptr, (unsigned*)nullptr, on);
 }
 
 template <typename T>
@@ -768,6 +785,10 @@ template void fe_apply_cg<double>(const DevGrid&, const OpDesc<double>&, int, co
 template void fe_apply_cg<float>(const DevGrid&, const OpDesc<float>&, int, const float*, const float*, float*,
                                  float*, KState*, RedBuf, cudaStream_t);
 template void fe_expand<float>(const DevGrid&, int, float*, cudaStream_t);
+template void fe_poisson_apply<float>(const DevGrid&, const float*, float*, uint16_t, KState*, const uint8_t*,
+                                      cudaStream_t);
+template void fe_poisson_apply<double>(const DevGrid&, const double*, double*, uint16_t, KState*, const uint8_t*,
+                                       cudaStream_t);
 template void fe_sync<double>(const DevGrid&, int, double*, uint16_t, cudaStream_t);
 template void fe_sync<float>(const DevGrid&, int, float*, uint16_t, cudaStream_t);
 template void fe_gather_canon<double>(int64_t, const int32_t*, int, int64_t, const double*, double*, cudaStream_t);

@@ -78,6 +78,12 @@ void fe_copy_d(int64_t n, const double* a, double* b, cudaStream_t st);
 void fe_add_d(int64_t n, const double* a, double* b, cudaStream_t st);   // b += a
 template <typename T> void fe_zero(int64_t n, T* a, cudaStream_t st);
 
+// q = K x for the Poisson stencil (local per level; consumers add the interface
+// sums), over the chunks of problems not done that use multigrid (on[i] != 0).
+template <typename T>
+void fe_poisson_apply(const DevGrid& g, const T* x, T* q, uint16_t dmask, KState* ks, const uint8_t* on,
+                      cudaStream_t st);
+
 // Hanging nodes take the mean of their parents (nc components; x2 optional).
 template <typename T>
 void fe_expand(const DevGrid& g, int nc, T* x, cudaStream_t st);

@@ -294,6 +294,128 @@ __global__ void __launch_bounds__(512) k_cg_update_vec(DevGrid g, T* __restrict_
   if (threadIdx.x == 0) set_cond(cond, any);
 }
 
+// ---------------------------------------------------------------- CG with a multigrid preconditioner
+// The preconditioner is applied between the update and the next direction, so
+// r.z and beta move into k_cg_rz after the V-cycle.
+
+// r = b - A x on kept slots; ||r||^2, ||b||^2 -> rr, bb, done
+template <typename T>
+__global__ void __launch_bounds__(512) k_cg_start_r(DevGrid g, const T* __restrict__ b, const T* __restrict__ y,
+                                                    T* __restrict__ r, uint16_t dmask, KState* ks,
+                                                    double* partials, unsigned* counter, const OState* skip_os) {
+  KCOUNT();
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  const uint16_t m = g.meta[s];
+  const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
+  const T rv = keep ? T(b[s] - y[s]) : T(0);
+  r[s] = rv;
+  T tv[2] = {dof ? rv * rv : T(0), dof ? b[s] * b[s] : T(0)};
+  double* out = partials + (int64_t)gridDim.x * 2;
+  if (!grid_sum_last<T, 2>(tv, partials, counter, g.bseg, g.ninst, out)) return;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
+    const bool skip = skip_os && skip_os[i].done;
+    KState& k = ks[i];
+    k.rr = out[(int64_t)i * 2];
+    k.bb = fmax(out[(int64_t)i * 2 + 1], k.rr);
+    k.rz = 0.0;
+    k.iter = 0;
+    k.status = 0;
+    k.alpha = 0.0;
+    k.beta = 0.0;
+    k.af = k.bf = 0.f;
+    k.done = (skip || k.rr <= k.tol2 * k.bb) ? 1 : 0;
+    if (!skip && !isfinite(k.rr)) { k.done = 1; k.status = 5; }
+  }
+}
+
+// k_cg_update_vec without the preconditioner: x += alpha p, r -= alpha q
+// (interface sums fused in), ||r||^2 -> convergence and iteration cap
+template <typename T>
+__global__ void __launch_bounds__(512) k_cg_update_r(DevGrid g, T* __restrict__ x, T* __restrict__ r,
+                                                     const T* __restrict__ p, const T* __restrict__ q,
+                                                     uint16_t dmask, KState* ks, double* partials,
+                                                     unsigned* counter) {
+  KCOUNT();
+  using V = typename Vec16<T>::type;
+  using MT = typename Vec16<T>::mt;
+  constexpr int W = Vec16<T>::W;
+  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const KState& k = ks[g.binst[b0]];
+  T tv[1] = {T(0)};
+  if (!k.done) {
+    const T a = k_alpha<T>(k);
+    const int64_t s1 = (int64_t)b1 * DBV;
+    for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
+      const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
+      const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+      V xv = *reinterpret_cast<const V*>(x + s);
+      V rv = *reinterpret_cast<const V*>(r + s);
+      V pv = *reinterpret_cast<const V*>(p + s);
+      V qv = *reinterpret_cast<const V*>(q + s);
+      T* xe = reinterpret_cast<T*>(&xv);
+      T* re = reinterpret_cast<T*>(&rv);
+      T* pe = reinterpret_cast<T*>(&pv);
+      T* qe = reinterpret_cast<T*>(&qv);
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        const uint16_t m = mm[j];
+        T qq = qe[j];
+        if (m & D_IFACE) {
+          const int e = g.if_of_slot[s + j];
+          qq = q[g.if_c[e]] + q[g.if_f[e]];
+          for (int kk = g.if_off[e]; kk < g.if_off[e + 1]; ++kk) qq += T(0.5) * q[g.if_kid[kk]];
+        }
+        if (m & D_VALID) xe[j] += a * pe[j];
+        const T rn = kkeep(m, dmask) ? T(re[j] - a * qq) : T(0);
+        re[j] = rn;
+        if (kdof(m, dmask)) tv[0] += rn * rn;
+      }
+      *reinterpret_cast<V*>(x + s) = xv;
+      *reinterpret_cast<V*>(r + s) = rv;
+    }
+  }
+  double* out = partials + (int64_t)gridDim.x;
+  if (!grid_sum_last<T, 1>(tv, partials, counter, g.cseg, g.ninst, out)) return;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
+    KState& kk = ks[i];
+    if (kk.done) continue;
+    kk.iter++;
+    kk.rr = out[i];
+    if (!isfinite(kk.rr)) { kk.done = 1; kk.status = 5; continue; }
+    if (kk.rr <= kk.tol2 * kk.bb) { kk.done = 1; continue; }
+    if (kk.iter >= kk.max_iter) { kk.done = 1; kk.status = 4; continue; }
+  }
+}
+
+// r.z over DOF slots -> beta (0 on the first pass), rz; loop condition
+template <typename T>
+__global__ void __launch_bounds__(512) k_cg_rz(DevGrid g, const T* __restrict__ r, const T* __restrict__ z,
+                                               uint16_t dmask, KState* ks, double* partials, unsigned* counter,
+                                               Cond cond, int first) {
+  KCOUNT();
+  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const KState& k = ks[g.binst[b0]];
+  T tv[1] = {T(0)};
+  if (!k.done)
+    for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x)
+      if (kdof(g.meta[s], dmask)) tv[0] += r[s] * z[s];
+  double* out = partials + (int64_t)gridDim.x;
+  if (!grid_sum_last<T, 1>(tv, partials, counter, g.cseg, g.ninst, out)) return;
+  bool any = false;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
+    KState& kk = ks[i];
+    if (kk.done) continue;
+    const double rzn = out[i];
+    if (!isfinite(rzn) || !(rzn > 0.0)) { kk.done = 1; kk.status = 5; continue; }
+    kk.beta = first ? 0.0 : rzn / kk.rz;
+    kk.bf = float(kk.beta);
+    kk.rz = rzn;
+    any = true;
+  }
+  any = block_any(any);
+  if (threadIdx.x == 0) set_cond(cond, any);
+}
+
 // ---------------------------------------------------------------- BiCGStab
 template <typename T, int NC>
 __global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restrict__ b, const T* __restrict__ y,
@@ -590,6 +712,48 @@ static cudaError_t cg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b
   });
 }
 
+template <typename T>
+static const MGDev<T>* mg_of(const SolveArgs& a) {
+  if constexpr (sizeof(T) == 4) return a.mg32; else return a.mg64;
+}
+
+// CG with the multigrid V-cycle as preconditioner (Poisson, one component)
+template <typename T>
+static cudaError_t cg_mg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const MGDev<T>& mg, const T* b, T* x,
+                                 T* work, cudaStream_t st, CaptureCtx* cc, double rtol, const OState* skip_os) {
+  const DevGrid& g = *a.g;
+  const int64_t L = g.nslots;
+  Work<T> w = carve(work, L);
+  T* zs = work + 5 * L;
+  RedBuf rb = a.rb;
+  IBG_LAUNCH(k_init_states, (g.ninst + 127) / 128, 128, 0, st, a.ks, g.ninst, rtol * rtol, a.max_iter);
+  Cond cond;
+  if (cc && cc->capturing) {
+    cudaError_t e = cond_handle(st, 0, &cond);
+    if (e != cudaSuccess) return e;
+  }
+  fe_apply<T>(g, A, 1, x, w.q, st);
+  IBG_LAUNCH(k_cg_start_r<T>, g.nbricks, DBV, 0, st, g, b, w.q, w.r, A.dmask, a.ks, rb.partials, rb.counter,
+             skip_os);
+  mg_vcycle<T>(g, mg, w.r, w.z, zs, w.q, A.dinv, A.dmask, a.ks, st, a.prof, 7);
+  IBG_LAUNCH(k_cg_rz<T>, g.nchunks, DBV, 0, st, g, w.r, w.z, A.dmask, a.ks, rb.partials, rb.counter, cond, 1);
+  auto iter = [&](cudaStream_t s, const Cond& c, T* pold, T* pnew) {
+    pbegin(a.prof, a.pbase + 0, s);
+    fe_apply_cg<T>(g, A, 1, w.z, pold, pnew, w.q, a.ks, rb, s);
+    pend(a.prof, s);
+    pbegin(a.prof, a.pbase + 1, s);
+    IBG_LAUNCH(k_cg_update_r<T>, g.nchunks, DBV, 0, s, g, x, w.r, pnew, w.q, A.dmask, a.ks, rb.partials,
+               rb.counter);
+    pend(a.prof, s);
+    mg_vcycle<T>(g, mg, w.r, w.z, zs, w.q, A.dinv, A.dmask, a.ks, s, a.prof, 7);
+    IBG_LAUNCH(k_cg_rz<T>, g.nchunks, DBV, 0, s, g, w.r, w.z, A.dmask, a.ks, rb.partials, rb.counter, c, 0);
+  };
+  return run_loop(cc, st, cond, a.ks, a.ks_host, g.ninst, a.max_iter, 1, 4, [&](cudaStream_t s, const Cond& c) {
+    iter(s, c, w.pa, w.pb);
+    iter(s, c, w.pb, w.pa);
+  });
+}
+
 template <typename T, int NC>
 static cudaError_t bcg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b, T* x, T* work, cudaStream_t st,
                                CaptureCtx* cc, double rtol, const OState* skip_os) {
@@ -633,6 +797,10 @@ static cudaError_t inner_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T
                                  CaptureCtx* cc, double rtol, const OState* skip_os) {
   if (a.bicg) return a.nc == 1 ? bcg_enqueue<T, 1>(a, A, b, x, work, st, cc, rtol, skip_os)
                                : bcg_enqueue<T, 3>(a, A, b, x, work, st, cc, rtol, skip_os);
+  if (a.nc == 1 && a.op == OP_POISSON) {
+    const MGDev<T>* mg = mg_of<T>(a);
+    if (mg && mg->any) return cg_mg_enqueue<T>(a, A, *mg, b, x, work, st, cc, rtol, skip_os);
+  }
   return a.nc == 1 ? cg_enqueue<T, 1>(a, A, b, x, work, st, cc, rtol, skip_os)
                    : cg_enqueue<T, 3>(a, A, b, x, work, st, cc, rtol, skip_os);
 }

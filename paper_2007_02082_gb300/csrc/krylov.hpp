@@ -7,6 +7,7 @@
 
 #include "fe.hpp"
 #include "graph.hpp"
+#include "mgdev.hpp"
 
 namespace ibg {
 
@@ -38,6 +39,9 @@ struct SolveArgs {
   RedBuf rb;
   Prof* prof = nullptr;
   int pbase = 0;
+  // multigrid preconditioner of the Poisson CG (nullptr or no problem on: Jacobi)
+  const MGDev<float>* mg32 = nullptr;
+  const MGDev<double>* mg64 = nullptr;
   KState* ks_host = nullptr;   // pinned host mirrors for the polling path
   OState* os_host = nullptr;
 };

@@ -209,3 +209,37 @@ def test_graph_and_eager_paths_bitwise_equal(precision):
     assert sum(ib_["prof_launches"]) > 0
     a.close()
     b.close()
+
+
+def test_jacobi_preconditioner_parity():
+    """The Jacobi-preconditioned Poisson CG (poisson_pc='jacobi') stays a
+    supported path: FP64 parity with the oracle as for the default."""
+    from paper_2007_02082_gb300 import IBGrid
+    case, steps = CASES["refined"]
+    o, hist = oracle_run("refined")
+    g = IBGrid(case, precision="fp64", poisson_pc="jacobi")
+    g.ipcs_step(steps)
+    assert g.ib_grid_info()["mg_levels"] == 0
+    for key, field in (("u", "U"), ("p", "P"), ("phi", "PHI")):
+        e = rel_l2(g.ib_fields_get(field), hist[-1][key])
+        assert e <= TOL64, f"{key}: rel L2 {e:.3e}"
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["uniform", "refined"])
+def test_multigrid_cuts_poisson_iterations(name):
+    """Same step, same answer (to the solve tolerance), far fewer CG
+    iterations with the V-cycle than with Jacobi."""
+    from paper_2007_02082_gb300 import IBGrid
+    case, _ = CASES[name]
+    a = IBGrid(case, precision="fp64")
+    b = IBGrid(case, precision="fp64", poisson_pc="jacobi")
+    a.ipcs_step(2)
+    b.ipcs_step(2)
+    ia, ib_ = a.ib_grid_info(), b.ib_grid_info()
+    assert ia["mg_levels"] >= 2 and ia["mg_coarsest"] <= 1024
+    assert ia["iters_p"] * 4 <= ib_["iters_p"], (ia["iters_p"], ib_["iters_p"])
+    assert rel_l2(a.ib_fields_get("P"), b.ib_fields_get("P")) < TOL64
+    assert rel_l2(a.ib_fields_get("U"), b.ib_fields_get("U")) < TOL64
+    a.close()
+    b.close()

@@ -1,0 +1,192 @@
+"""Host-side multigrid hierarchy of the Poisson preconditioner (csrc/mg.cpp).
+
+Compiled with a small driver (tests/mg_probe.cpp); no GPU needed.  The
+hierarchy is pinned against what the discretisation fixes independently of
+the builder:
+
+  * G0 operator = P0^T K P0 with K the oracle's own element-by-element
+    stiffness over all nodes (hanging nodes expanded as the mean of their
+    parents): the Galerkin identity of nested P1 spaces (Sec. 3.2 refinement
+    keeps the spaces nested);
+  * every coarser operator = P^T A P of the level below (Galerkin);
+  * both identities hold exactly away from the outlet nodes (Phi = 0, Eq. 12),
+    where the coarse Dirichlet rule is an approximation, so the comparison
+    skips nodes within two cells of a Dirichlet node;
+  * prolongation is P1 interpolation: it reproduces linear functions;
+  * restriction is the transpose of prolongation on owner copies;
+  * operators are symmetric with zero row sums away from Dirichlet nodes.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import ibfe
+from tests.test_host_setup import _desc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2007_02082_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def probe(tmp_path_factory):
+    d = tmp_path_factory.mktemp("mgprobe")
+    exe = d / "mg_probe"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-I", os.path.join(ROOT, "include"),
+                    "-I", CSRC, os.path.join(CSRC, "setup.cpp"), os.path.join(CSRC, "mg.cpp"),
+                    os.path.join(ROOT, "tests", "mg_probe.cpp"), "-o", str(exe)], check=True)
+    return exe, d
+
+
+def run_probe(probe, case):
+    exe, d = probe
+    inp, out = d / "in.bin", d / "out.bin"
+    with open(inp, "wb") as f:
+        f.write(bytes(_desc(case)))
+        f.write(np.int64(len(case["X"])).tobytes())
+        for k in ("X", "dS", "UB"):
+            f.write(np.ascontiguousarray(case[k], np.float64).tobytes())
+        f.write(np.ascontiguousarray(case["inside"], np.uint8).tobytes())
+    subprocess.run([str(exe), str(inp), str(out)], check=True)
+    b = open(out, "rb").read()
+    pos = [0]
+
+    def take(n, dt):
+        dt = np.dtype(dt)
+        v = np.frombuffer(b, dt, count=n, offset=pos[0])
+        pos[0] += n * dt.itemsize
+        return v
+
+    ok, nlev, small, ns, N = (int(v) for v in take(5, np.int64))
+    res = {"ok": ok, "small": small, "ns": ns, "canon_slot": take(N, np.int32),
+           "slot_q": take(3 * ns, np.int32).reshape(ns, 3), "lev": []}
+    for _ in range(nlev):
+        nn, nd, nr, npe, n0, n1, n2 = (int(v) for v in take(7, np.int64))
+        L = {"nn": nn, "n": (n0, n1, n2), "h": take(3, np.float64)}
+        L["coord"] = take(3 * nn, np.int32).reshape(nn, 3)
+        L["dir"] = take(3 * nd, np.int32).reshape(nd, 3)
+        L["nbr"] = take(6 * nn, np.int32).reshape(nn, 6)
+        L["offd"] = take(6 * nn, np.float64).reshape(nn, 6)
+        L["diag"] = take(nn, np.float64)
+        rptr = take(nn + 1, np.int32)
+        L["R"] = (rptr, take(nr, np.int32), take(nr, np.float64))
+        prow = int(take(1, np.int64)[0])
+        pptr = take(prow, np.int32)
+        L["P"] = (pptr, take(npe, np.int32), take(npe, np.float64))
+        res["lev"].append(L)
+    return res
+
+
+def level_matrix(L):
+    nn = L["nn"]
+    rows, cols, vals = [np.arange(nn)], [np.arange(nn)], [L["diag"]]
+    m = L["nbr"] >= 0
+    r = np.repeat(np.arange(nn)[:, None], 6, axis=1)
+    rows.append(r[m]), cols.append(L["nbr"][m]), vals.append(L["offd"][m])
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(nn, nn))
+
+
+def csr(ptr, col, w, ncol):
+    return sp.csr_matrix((w, col, ptr), shape=(len(ptr) - 1, ncol))
+
+
+def far_from(coords, dirs, dist):
+    if len(dirs) == 0:
+        return np.ones(len(coords), bool)
+    far = np.ones(len(coords), bool)
+    for d in dirs:
+        far &= np.abs(coords - d[None, :]).max(axis=1) > dist
+    return far
+
+
+CASES = {
+    "uniform": W.cylinder_uniform_16x16x64(),
+    "refined": W.cylinder_refined_small(n=(16, 16, 8), seed=21),
+    "two_levels": W.cylinder_case(n=(24, 24, 8), length=1.0, half_width=0.75, M=1500, seed=12, max_level=2,
+                                  refine_band=1, reduce_band=3, nu=0.02, dt=0.002, b=(0.5,)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mg_levels_symmetric_and_galerkin(probe, name):
+    case = CASES[name]
+    res = run_probe(probe, case)
+    assert res["ok"] == 1
+    levs = res["lev"]
+    assert len(levs) >= 2
+    assert levs[-1]["nn"] <= 1024
+    checked = 0
+    for k, L in enumerate(levs):
+        A = level_matrix(L)
+        assert abs(A - A.T).max() <= 1e-14 * abs(A).max()
+        far = far_from(L["coord"], L["dir"], 1)
+        rs = np.asarray(A.sum(axis=1)).ravel()
+        assert np.abs(rs[far]).max() <= 1e-12 * abs(A).max()
+        if k == 0:
+            continue
+        F = levs[k - 1]
+        P = csr(*L["P"], L["nn"])                                # G(k) -> G(k-1)
+        assert P.shape == (F["nn"], L["nn"])
+        R = csr(*L["R"], F["nn"])
+        assert abs(R - P.T).max() == 0.0
+        Ag = (P.T @ level_matrix(F) @ P).tocsr()
+        far2 = np.nonzero(far_from(L["coord"], L["dir"], 2))[0]
+        if len(far2):   # short domains: every node of the coarsest levels is near the outlet
+            D = (Ag - A)[far2][:, far2]
+            assert abs(D).max() <= 1e-12 * abs(A).max(), (name, k)
+            checked += 1
+        # P1 interpolation reproduces linear functions (rows away from Dirichlet)
+        lin = lambda c, h: (c * h[None, :]) @ np.array([0.3, -1.1, 0.7])
+        fine = P @ lin(L["coord"].astype(float), L["h"])
+        full = np.asarray(P.sum(axis=1)).ravel() == 1.0
+        assert full.sum() > 0.5 * F["nn"]
+        assert np.abs(fine - lin(F["coord"].astype(float), F["h"]))[full].max() < 1e-12
+    assert checked >= 1
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mg_g0_is_galerkin_of_oracle_stiffness(probe, name):
+    case = CASES[name]
+    res = run_probe(probe, case)
+    L0 = res["lev"][0]
+    m = ibfe.build_mesh(case)
+    ops = ibfe.Operators(m)
+    N = m.n_nodes
+    P0 = csr(*L0["P"], L0["nn"])                                 # composite slot -> G0
+    slot = res["canon_slot"]
+    V = P0[slot].tolil()
+    V[np.nonzero(m.outlet)[0], :] = 0
+    V = V.tocsr()
+    h = np.nonzero(m.hanging)[0]
+    if len(h):
+        par = m.parents[h]
+        E = sp.identity(N, format="lil")
+        for i, (a, b) in zip(h, par):
+            E[i, i] = 0.0
+            E[i, a] = 0.5
+            E[i, b] = 0.5
+        V = (E.tocsr() @ V).tocsr()
+    A0 = level_matrix(L0)
+    Ag = (V.T @ ops.K @ V).tocsr()
+    far = np.nonzero(far_from(L0["coord"], L0["dir"], 2))[0]
+    D = (Ag - A0)[far][:, far]
+    assert abs(D).max() <= 1e-12 * abs(A0).max()
+    # linear reproduction at every composite node (away from the outlet)
+    h0 = L0["h"]
+    hf = np.array(case["extent"]) / (np.array(case["n"]) * 2 ** case["max_level"])
+    f = np.array([0.3, -1.1, 0.7])
+    coarse = (L0["coord"] * h0[None, :]) @ f
+    got = P0 @ coarse
+    rows = np.nonzero(np.diff(P0.indptr) > 0)[0]
+    full = np.asarray(P0[rows].sum(axis=1)).ravel() == 1.0
+    want = (res["slot_q"][rows] * hf[None, :]) @ f
+    assert np.abs(got[rows] - want)[full].max() < 1e-12
+    # restriction = transpose of prolongation on owner copies
+    R = csr(*L0["R"], res["ns"])
+    owner = np.zeros(res["ns"], bool)
+    owner[slot] = True
+    Pown = P0.multiply(owner[:, None]).tocsr()
+    assert abs(R - Pown.T).max() == 0.0
