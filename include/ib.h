@@ -169,8 +169,8 @@ typedef struct {
   /* with desc.profile: accumulated device time and launch count per kernel
      class since ib_set_boundary; class = base + {0 operator apply, 1 vector
      update, 2 direction update}, base 0 Poisson, 3 mass, 6 momentum; the
-     multigrid V-cycle: 7 composite stencil applies, 8 composite smoothing
-     updates, 9 transfers and coarse levels */
+     multigrid V-cycle: 9 composite stencil applies, 10 composite smoothing
+     updates, 11 transfers and coarse levels */
   double prof_ms[12];
   int64_t prof_launches[12];
   int64_t kernel_launches;  /* kernels launched by this process's library so far */

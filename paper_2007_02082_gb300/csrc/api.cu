@@ -536,7 +536,7 @@ ib_status engine_build(Engine& E) {
   std::vector<double> X(3 * Mt, 0.0), dSv(Mt, 1.0), UB(3 * Mt, 0.0), pscale(Mt, 0.0), iorg(3 * n), ihf(3 * n),
       icoef(n);
   std::vector<int32_t> org(3 * Mt, 0), slot(64 * Mt, -1), pinst(Mt, 0), rowptr(Mt + 1, 0), col, segt(n + 1),
-      segw(n + 1), sps, spo(1, 0), spe;
+      segw(n + 1), segg(n + 1), sps, spo(1, 0), spe;
   std::vector<uint64_t> fb(Mt, 0);
   for (int i = 0; i < n; ++i) {
     const HostGrid& H = *E.H[i];
@@ -545,6 +545,7 @@ ib_status engine_build(Engine& E) {
     const double sc = E.D[i].dt / (E.D[i].rho * h3);
     segt[i] = int32_t(R0 / 256);
     segw[i] = int32_t(R0 / 8);
+    segg[i] = int32_t(R0 / 32);
     for (int a = 0; a < 3; ++a) { iorg[3 * i + a] = H.origin[a]; ihf[3 * i + a] = H.hf[a]; }
     icoef[i] = sc;
     for (int64_t r = R0; r < E.row0[i + 1]; ++r) { pinst[r] = i; pscale[r] = sc; }
@@ -565,6 +566,7 @@ ib_status engine_build(Engine& E) {
   }
   segt[n] = int32_t(Mt / 256);
   segw[n] = int32_t(Mt / 8);
+  segg[n] = int32_t(Mt / 32);
   for (int i = 0; i < n; ++i) {   // A_F pattern and spreading lists with global rows and slots
     const HostGrid& H = *E.H[i];
     const int64_t R0 = E.row0[i];
@@ -586,7 +588,7 @@ ib_status engine_build(Engine& E) {
   ib = IBDev();
   ib.M = Mt;
   ib.ninst = n;
-  int32_t *d_org, *d_slot, *d_rp, *d_col, *d_sps, *d_spo, *d_spe, *d_pinst, *d_segt, *d_segw;
+  int32_t *d_org, *d_slot, *d_rp, *d_col, *d_sps, *d_spo, *d_spe, *d_pinst, *d_segt, *d_segw, *d_segg;
   uint64_t* d_fb;
   double *d_pscale, *d_iorg, *d_ihf, *d_icoef;
   TRY(upload(E, &E.X, X));
@@ -603,20 +605,21 @@ ib_status engine_build(Engine& E) {
   TRY(upload(E, &d_pinst, pinst));
   TRY(upload(E, &d_segt, segt));
   TRY(upload(E, &d_segw, segw));
+  TRY(upload(E, &d_segg, segg));
   TRY(upload(E, &d_pscale, pscale));
   TRY(upload(E, &d_iorg, iorg));
   TRY(upload(E, &d_ihf, ihf));
   TRY(upload(E, &d_icoef, icoef));
   ib.X = E.X; ib.org = d_org; ib.slot = d_slot; ib.freeb = d_fb; ib.rowptr = d_rp; ib.col = d_col;
   ib.sp_slot = d_sps; ib.sp_off = d_spo; ib.sp_ent = d_spe; ib.n_sp = int64_t(sps.size());
-  ib.pinst = d_pinst; ib.seg_t = d_segt; ib.seg_w = d_segw; ib.pscale = d_pscale;
+  ib.pinst = d_pinst; ib.seg_t = d_segt; ib.seg_w = d_segw; ib.seg_g = d_segg; ib.pscale = d_pscale;
   ib.iorigin = d_iorg; ib.ihf = d_ihf; ib.icoef = d_icoef; ib.binst = d_binst;
   TRY(dalloc(E, &ib.W, 64 * Mt, true));
   TRY(dalloc(E, &ib.val, int64_t(col.size()), true));
   TRY(dalloc(E, &ib.dinv, Mt, true));
   TRY(dalloc(E, &E.BF, 3 * Mt, true));
   TRY(dalloc(E, &E.Gf, 3 * Mt, true));
-  TRY(dalloc(E, &E.ibw, 4 * 3 * Mt, true));
+  TRY(dalloc(E, &E.ibw, 5 * 3 * Mt, true));
 
   // ---- reductions, solver state, streams
   const int64_t maxblk = std::max<int64_t>(E.nbricks, Mt / 8 + 1);

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "fe.hpp"
+#include "kuhn_weights.hpp"
 
 namespace ibg {
 
@@ -126,122 +127,8 @@ __device__ __forceinline__ T table_coef(int mask, int k, const T* F) {
 
 enum Post : int { POST_NONE = 0, POST_CG_ALPHA = 1 };
 
-// p.Ap per instance and component -> alpha = r.z / p.Ap
-template <typename T, int NC>
-__device__ __forceinline__ void cg_alpha_post(const DevGrid& g, T (&v)[NC], KState* ks, double* partials,
-                                              unsigned* counter) {
-  double* out = partials + (int64_t)gridDim.x * NC;
-  if (!grid_sum_last<T, NC>(v, partials, counter, g.bseg, g.ninst, out)) return;
-  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
-    for (int c = 0; c < NC; ++c) {
-      KState& k = ks[i * NC + c];
-      if (k.done) continue;
-      const double pq = out[i * NC + c];
-      k.pq = pq;
-      if (!(pq > 0.0) || !isfinite(pq)) { k.done = 1; k.status = 5; k.alpha = 0.0; k.af = 0.f; continue; }
-      k.alpha = k.rz / pq;
-      k.af = float(k.alpha);
-    }
-}
-
-// y = A x on every stored node of a brick; optional fused pre-sync x.y per
-// component, whose total gives p.Ap of the constrained operator and alpha.
-//
-// FUSEP: the CG direction update p_new = z + beta p_old is done while staging
-// the tile (halo included, so no separate kernel); p_new is written for the
-// brick's own nodes and q = A p_new is produced from it.
-template <typename T, int OP, int NC, bool FUSEP>
-__global__ void __launch_bounds__(512) k_apply(DevGrid g, const T* __restrict__ x, T* __restrict__ y,
-                                               const T* __restrict__ coef, uint16_t dmask, int post,
-                                               KState* __restrict__ ks, double* __restrict__ partials,
-                                               unsigned* __restrict__ counter, const T* __restrict__ zf,
-                                               T* __restrict__ pnew) {
-  KCOUNT();
-  __shared__ T tile[NC * TILE3];
-  const int b = blockIdx.x;
-  const KState* ki = ks ? ks + g.binst[b] * NC : nullptr;
-  bool skip = false;   // every component of this brick's instance has converged
-  if (FUSEP) {
-    skip = true;
-    for (int c = 0; c < NC; ++c) skip = skip && ki[c].done;
-  }
-  if (skip) {
-    if (post == POST_CG_ALPHA) {
-      T v[NC];
-      for (int c = 0; c < NC; ++c) v[c] = T(0);
-      cg_alpha_post<T, NC>(g, v, ks, partials, counter);
-    }
-    return;
-  }
-  if (FUSEP) {
-    T beta[NC];
-    for (int c = 0; c < NC; ++c) beta[c] = k_beta<T>(ki[c]);
-    const int32_t* nb27 = g.bnbr + 27 * b;
-    for (int t = threadIdx.x; t < TILE3; t += blockDim.x) {
-      int hx = t % TILE, hy = (t / TILE) % TILE, hz = t / (TILE * TILE);
-      int lx = hx - 1, ly = hy - 1, lz = hz - 1;
-      int ox = lx < 0 ? -1 : (lx > 7 ? 1 : 0), oy = ly < 0 ? -1 : (ly > 7 ? 1 : 0), oz = lz < 0 ? -1 : (lz > 7 ? 1 : 0);
-      int nb = nb27[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
-      int64_t s = (int64_t)nb * DBV + (((lz & 7) * DBS + (ly & 7)) * DBS + (lx & 7));
-      for (int c = 0; c < NC; ++c)
-        tile[c * TILE3 + t] = nb >= 0 ? T(zf[c * g.nslots + s] + beta[c] * x[c * g.nslots + s]) : T(0);
-    }
-  } else {
-    load_tile<T>(tile, x, g.nslots, NC, g.bnbr + 27 * b);
-  }
-  __syncthreads();
-  const int t = threadIdx.x;
-  const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
-  const int64_t s = (int64_t)b * DBV + t;
-  const uint16_t m = g.meta[s];
-  const int ti = tile_index(lx, ly, lz);
-  T out[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) out[c] = T(0);
-  if (m & D_VALID) {
-    const int mask = m & 0xFF;
-    const T* F = stencil_factors<T>(g, b);
-    if (OP == OP_POISSON) {
-#pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        T ck = table_coef<T, OP_POISSON>(mask, k, F);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) out[c] += ck * tile[c * TILE3 + ti + c_toff[k]];
-      }
-    } else if (OP == OP_MASS) {
-#pragma unroll
-      for (int k = 0; k < 15; ++k) {
-        T ck = table_coef<T, OP_MASS>(mask, k, F);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) out[c] += ck * tile[c * TILE3 + ti + c_toff[k]];
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 15; ++k) {
-        T ck = coef[(int64_t)k * g.nslots + s];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) out[c] += ck * tile[c * TILE3 + ti + c_toff[k]];
-      }
-    }
-  }
-  if (m & dmask) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) out[c] = T(0);
-  }
-#pragma unroll
-  for (int c = 0; c < NC; ++c) y[c * g.nslots + s] = out[c];
-  if (FUSEP) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) pnew[c * g.nslots + s] = tile[c * TILE3 + ti];
-  }
-  if (post == POST_CG_ALPHA) {
-    T v[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) v[c] = tile[c * TILE3 + ti] * out[c];
-    cg_alpha_post<T, NC>(g, v, ks, partials, counter);
-  }
-}
-
+// Interface sum of an operator output: both stored copies get the sum of their
+// level parts plus half of each hanging child's; rows with a dmask bit are zeroed.
 template <typename T, int NC>
 __global__ void k_sync(DevGrid g, T* __restrict__ y, uint16_t dmask) {
   KCOUNT();
@@ -589,11 +476,11 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
   __shared__ T tile[TILE3];
   const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
   const int inst = g.binst[b0];
-  const KState& k = ks[inst];
+  const bool done = ks ? ks[inst].done != 0 : false;   // plain applies may pass no solver state
   T acc = T(0);
-  if (!CG && (k.done || (on && !on[inst]))) return;
-  if (!k.done) {
-    const T beta = CG ? k_beta<T>(k) : T(0);
+  if (!CG && (done || (on && !on[inst]))) return;
+  if (!done) {
+    const T beta = CG ? k_beta<T>(ks[inst]) : T(0);
     const int t = threadIdx.x;
     const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
     const int ti = tile_index(lx, ly, lz);
@@ -626,15 +513,11 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
         const T* F = stencil_factors<T>(g, bb);
         const T xm = tile[ti - 1], xp = tile[ti + 1], ym = tile[ti - TILE], yp = tile[ti + TILE];
         const T zm = tile[ti - TILE * TILE], zp = tile[ti + TILE * TILE];
-        // number of Kuhn tetrahedra (weighted 2 where the edge runs from the
-        // cell's (0,0,0) or to its (1,1,1) corner, else 1) that hold each axis
-        // edge, from the incident-cell bits (bit dz*4 + dy*2 + dx): the P1
-        // stiffness is -(V/6)/h_a^2 times this weight, the diagonal their sum
-        const int b = mask;
-        auto bit = [b](int k) { return (b >> k) & 1; };
-        const int wxp = 2 * bit(1) + bit(3) + bit(5) + 2 * bit(7), wxm = 2 * bit(0) + bit(2) + bit(4) + 2 * bit(6);
-        const int wyp = 2 * bit(2) + bit(3) + bit(6) + 2 * bit(7), wym = 2 * bit(0) + bit(1) + bit(4) + 2 * bit(5);
-        const int wzp = 2 * bit(4) + bit(5) + bit(6) + 2 * bit(7), wzm = 2 * bit(0) + bit(1) + bit(2) + 2 * bit(3);
+        // Kuhn tetrahedra holding each axis edge (kuhn_weights.hpp): the P1
+        // stiffness is -(V/6)/h_a^2 times this count, the diagonal their sum
+        const int wxp = stiff_edge_count(mask, 0, 1), wxm = stiff_edge_count(mask, 0, -1);
+        const int wyp = stiff_edge_count(mask, 1, 1), wym = stiff_edge_count(mask, 1, -1);
+        const int wzp = stiff_edge_count(mask, 2, 1), wzm = stiff_edge_count(mask, 2, -1);
         const T fx = F[0], fy = F[1], fz = F[2];
         out = fx * (T(wxp) * (pv - xp) + T(wxm) * (pv - xm)) + fy * (T(wyp) * (pv - yp) + T(wym) * (pv - ym)) +
               fz * (T(wzp) * (pv - zp) + T(wzm) * (pv - zm));
@@ -663,17 +546,145 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
   }
 }
 
+// Halo element t (t < HALO15) of a brick for the 15-point Kuhn stencil: the six
+// faces (384 nodes), the six edges reached by the offsets +-(1,1,0),
+// +-(0,1,1), +-(1,0,1) (48 nodes) and the corners +-(1,1,1).  Gives the
+// neighbour-brick index (0..26), the local index in that brick and the tile index.
+constexpr int HALO15 = 434;
+__device__ __forceinline__ void halo15(int t, int& nbk, int& li, int& ti) {
+  int hx, hy, hz, ox = 0, oy = 0, oz = 0, gx, gy, gz;
+  if (t < 384) {
+    const int f = t >> 6, u = t & 7, v = (t >> 3) & 7;
+    if (f < 2) { hx = f ? 8 : -1; hy = u; hz = v; ox = f ? 1 : -1; gx = f ? 0 : 7; gy = u; gz = v; }
+    else if (f < 4) { hx = u; hy = (f & 1) ? 8 : -1; hz = v; oy = (f & 1) ? 1 : -1; gx = u; gy = (f & 1) ? 0 : 7; gz = v; }
+    else { hx = u; hy = v; hz = (f & 1) ? 8 : -1; oz = (f & 1) ? 1 : -1; gx = u; gy = v; gz = (f & 1) ? 0 : 7; }
+  } else if (t < 432) {
+    const int e = (t - 384) >> 3, u = (t - 384) & 7;
+    const int sg = (e & 1) ? -1 : 1, hi = (e & 1) ? -1 : 8, lo = (e & 1) ? 7 : 0;
+    if (e < 2) { hx = hi; hy = hi; hz = u; ox = sg; oy = sg; gx = lo; gy = lo; gz = u; }        // +-(1,1,0)
+    else if (e < 4) { hx = u; hy = hi; hz = hi; oy = sg; oz = sg; gx = u; gy = lo; gz = lo; }   // +-(0,1,1)
+    else { hx = hi; hy = u; hz = hi; ox = sg; oz = sg; gx = lo; gy = u; gz = lo; }              // +-(1,0,1)
+  } else {
+    const int sg = t == 432 ? 1 : -1, hi = t == 432 ? 8 : -1, lo = t == 432 ? 0 : 7;
+    hx = hy = hz = hi;
+    ox = oy = oz = sg;
+    gx = gy = gz = lo;
+  }
+  nbk = (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1);
+  li = (gz * DBS + gy) * DBS + gx;
+  ti = tile_index(hx, hy, hz);
+}
+
+// 15-point operators (consistent mass from the incident-cell mask, or the
+// per-slot momentum coefficients), NC components, one CTA per chunk of bricks
+// (PB = false) or per brick (PB = true: more CTAs in flight for the streaming
+// coefficient reads of a plain apply).
+// FUSEP: p_new = z + beta p_old while staging the tile (written for the
+// brick's nodes), y = A p_new, and per-component p.y -> alpha (POST_CG_ALPHA).
+template <typename T, int OP, int NC, bool FUSEP, bool PB>
+__global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict__ x, T* __restrict__ y,
+                                                 const T* __restrict__ coef, uint16_t dmask, int post,
+                                                 KState* __restrict__ ks, double* __restrict__ partials,
+                                                 unsigned* __restrict__ counter, const T* __restrict__ zf,
+                                                 T* __restrict__ pnew) {
+  KCOUNT();
+  __shared__ T tile[NC * TILE3];
+  const int b0 = PB ? int(blockIdx.x) : g.cbrick[blockIdx.x];
+  const int b1 = PB ? b0 + 1 : g.cbrick[blockIdx.x + 1];
+  const int inst = g.binst[b0];
+  bool skip = false;
+  T beta[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) beta[c] = T(0);
+  if (FUSEP) {
+    skip = true;
+    for (int c = 0; c < NC; ++c) {
+      skip = skip && ks[inst * NC + c].done;
+      beta[c] = k_beta<T>(ks[inst * NC + c]);
+    }
+  }
+  T acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = T(0);
+  if (!skip) {
+    const int t = threadIdx.x;
+    const int lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+    const int ti = tile_index(lx, ly, lz);
+    int hnb = 13, hli = 0, hti = 0;
+    if (t < HALO15) halo15(t, hnb, hli, hti);
+    for (int bb = b0; bb < b1; ++bb) {
+      const int64_t s = (int64_t)bb * DBV + t;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int64_t i = (int64_t)c * g.nslots + s;
+        tile[c * TILE3 + ti] = FUSEP ? T(zf[i] + beta[c] * x[i]) : x[i];
+      }
+      if (t < HALO15) {
+        const int nb = g.bnbr[27 * bb + hnb];
+        const int64_t hs = (int64_t)nb * DBV + hli;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int64_t i = (int64_t)c * g.nslots + hs;
+          tile[c * TILE3 + hti] = nb >= 0 ? (FUSEP ? T(zf[i] + beta[c] * x[i]) : x[i]) : T(0);
+        }
+      }
+      const uint16_t m = g.meta[s];
+      __syncthreads();
+      T out[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) out[c] = T(0);
+      if ((m & D_VALID) && !(m & dmask)) {
+        const int mask = m & 0xFF;
+        const T* F = stencil_factors<T>(g, bb);
+#pragma unroll
+        for (int k = 0; k < 15; ++k) {
+          const T ck = OP == OP_MASS ? T(mass_weight(mask, k)) * F[3] : coef[(int64_t)k * g.nslots + s];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) out[c] += ck * tile[c * TILE3 + ti + c_toff[k]];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        y[(int64_t)c * g.nslots + s] = out[c];
+        if (FUSEP) {
+          pnew[(int64_t)c * g.nslots + s] = tile[c * TILE3 + ti];
+          acc[c] += tile[c * TILE3 + ti] * out[c];
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (post != POST_CG_ALPHA) return;
+  double* out = partials + (int64_t)gridDim.x * NC;
+  if (!grid_sum_last<T, NC>(acc, partials, counter, PB ? g.bseg : g.cseg, g.ninst, out)) return;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
+    for (int c = 0; c < NC; ++c) {
+      KState& k = ks[i * NC + c];
+      if (k.done) continue;
+      const double pq = out[i * NC + c];
+      k.pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) { k.done = 1; k.status = 5; k.alpha = 0.0; k.af = 0.f; continue; }
+      k.alpha = k.rz / pq;
+      k.af = float(k.alpha);
+    }
+}
+
 template <typename T, int NC, bool FUSEP = false>
 static void launch_apply(const DevGrid& g, int op, const T* x, T* y, const T* coef, uint16_t dmask, int post,
                          KState* ks, RedBuf rb, cudaStream_t st, const T* zf = nullptr, T* pnew = nullptr) {
+  // the Poisson operator is scalar; its CG form (fused direction update and
+  // p.q) is k_poisson_cg<T, true>, launched by fe_apply_cg
   if (op == OP_POISSON)
-    IBG_LAUNCH((k_apply<T, OP_POISSON, NC, FUSEP>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
+    IBG_LAUNCH((k_poisson_cg<T, false>), g.nchunks, DBV, 0, st, g, x, (const T*)nullptr, (T*)nullptr, y, dmask,
+               (KState*)nullptr, (double*)nullptr, (unsigned*)nullptr, (const uint8_t*)nullptr);
+  else if (op == OP_MASS && FUSEP)
+    IBG_LAUNCH((k_apply15<T, OP_MASS, NC, FUSEP, false>), g.nchunks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
                rb.partials, rb.counter, zf, pnew);
   else if (op == OP_MASS)
-    IBG_LAUNCH((k_apply<T, OP_MASS, NC, FUSEP>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
+    IBG_LAUNCH((k_apply15<T, OP_MASS, NC, FUSEP, true>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
                rb.partials, rb.counter, zf, pnew);
   else
-    IBG_LAUNCH((k_apply<T, OP_COEF, NC, FUSEP>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
+    IBG_LAUNCH((k_apply15<T, OP_COEF, NC, FUSEP, true>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
                rb.partials, rb.counter, zf, pnew);
 }
 
@@ -713,6 +724,13 @@ void fe_expand2(const DevGrid& g, int nc, T* x, T* x2, cudaStream_t st) {
 template <typename T>
 void fe_expand(const DevGrid& g, int nc, T* x, cudaStream_t st) {
   fe_expand2<T>(g, nc, x, (T*)nullptr, st);
+}
+
+template <typename T>
+void fe_apply_local(const DevGrid& g, const OpDesc<T>& A, int nc, const T* x, T* y, cudaStream_t st) {
+  RedBuf none;
+  if (nc == 1) launch_apply<T, 1>(g, A.op, x, y, A.coef, A.dmask, POST_NONE, nullptr, none, st);
+  else launch_apply<T, 3>(g, A.op, x, y, A.coef, A.dmask, POST_NONE, nullptr, none, st);
 }
 
 template <typename T>
@@ -785,6 +803,9 @@ template void fe_apply_cg<double>(const DevGrid&, const OpDesc<double>&, int, co
 template void fe_apply_cg<float>(const DevGrid&, const OpDesc<float>&, int, const float*, const float*, float*,
                                  float*, KState*, RedBuf, cudaStream_t);
 template void fe_expand<float>(const DevGrid&, int, float*, cudaStream_t);
+template void fe_apply_local<float>(const DevGrid&, const OpDesc<float>&, int, const float*, float*, cudaStream_t);
+template void fe_apply_local<double>(const DevGrid&, const OpDesc<double>&, int, const double*, double*,
+                                     cudaStream_t);
 template void fe_poisson_apply<float>(const DevGrid&, const float*, float*, uint16_t, KState*, const uint8_t*,
                                       cudaStream_t);
 template void fe_poisson_apply<double>(const DevGrid&, const double*, double*, uint16_t, KState*, const uint8_t*,

@@ -61,6 +61,11 @@ cudaError_t fe_init_tables();
 template <typename T>
 void fe_apply(const DevGrid& g, const OpDesc<T>& A, int nc, const T* x, T* y, cudaStream_t st);
 
+// y = A x per level only: copies of interface nodes hold their level's part
+// (readers add the interface sums).
+template <typename T>
+void fe_apply_local(const DevGrid& g, const OpDesc<T>& A, int nc, const T* x, T* y, cudaStream_t st);
+
 // Local diagonal of A, summed over stored copies, then dinv = 1 / diag on DOFs.
 template <typename T>
 void fe_jacobi(const DevGrid& g, int op, const T* coef, uint16_t dmask, T* diag, T* dinv, cudaStream_t st);

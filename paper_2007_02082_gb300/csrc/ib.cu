@@ -136,6 +136,56 @@ __global__ void __launch_bounds__(IBB) k_af_apply(IBDev ib, const double* __rest
     }
 }
 
+// CG iteration form of the SpMV: p_new = z + beta p_old (read on the fly for
+// every column, written for the row), q = S p_new, p_new.q -> alpha.  Eight
+// lanes per row (A_F has a few dozen entries per row).
+constexpr int AFL = 8;
+static_assert(IBB / AFL == 32, "seg_g holds 32-row block ranges");
+__global__ void __launch_bounds__(IBB) k_af_apply_p(IBDev ib, const double* __restrict__ z,
+                                                    const double* __restrict__ pold, double* __restrict__ pnew,
+                                                    double* __restrict__ q, KState* ks, double* partials,
+                                                    unsigned* counter) {
+  KCOUNT();
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / AFL;
+  const int lane = threadIdx.x % AFL;
+  double v[3] = {0, 0, 0};
+  if (i < ib.M) {
+    const KState* ki = ks + ib.pinst[i] * 3;
+    const double b0 = ki[0].beta, b1 = ki[1].beta, b2 = ki[2].beta;
+    double acc[3] = {0, 0, 0};
+    for (int e = ib.rowptr[i] + lane; e < ib.rowptr[i + 1]; e += AFL) {
+      const double w = ib.val[e];
+      const int64_t k = ib.col[e];
+      acc[0] += w * (z[3 * k] + b0 * pold[3 * k]);
+      acc[1] += w * (z[3 * k + 1] + b1 * pold[3 * k + 1]);
+      acc[2] += w * (z[3 * k + 2] + b2 * pold[3 * k + 2]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      for (int o = AFL / 2; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o, AFL);
+    if (lane == 0) {
+      const double bc[3] = {b0, b1, b2};
+      for (int c = 0; c < 3; ++c) {
+        const double pv = z[3 * i + c] + bc[c] * pold[3 * i + c];
+        pnew[3 * i + c] = pv;
+        q[3 * i + c] = acc[c];
+        v[c] = pv * acc[c];
+      }
+    }
+  }
+  double* out = partials + (int64_t)gridDim.x * 3;
+  if (!grid_sum_last<double, 3>(v, partials, counter, ib.seg_g, ib.ninst, out)) return;
+  for (int n = threadIdx.x; n < ib.ninst; n += blockDim.x)
+    for (int c = 0; c < 3; ++c) {
+      KState& k = ks[n * 3 + c];
+      if (k.done) continue;
+      const double pq = out[n * 3 + c];
+      k.pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) { k.done = 1; k.status = 5; k.alpha = 0.0; continue; }
+      k.alpha = k.rz / pq;
+    }
+}
+
 __global__ void __launch_bounds__(IBB) k_af_start(IBDev ib, const double* __restrict__ b, const double* __restrict__ y,
                                                   double* __restrict__ r, double* __restrict__ z,
                                                   double* __restrict__ p, KState* ks, double* partials,
@@ -149,7 +199,7 @@ __global__ void __launch_bounds__(IBB) k_af_start(IBDev ib, const double* __rest
       const double zv = rv * ib.dinv[i];
       r[3 * i + c] = rv;
       z[3 * i + c] = zv;
-      p[3 * i + c] = zv;
+      p[3 * i + c] = 0.0;
       v[3 * c] = rv * zv;
       v[3 * c + 1] = rv * rv;
       v[3 * c + 2] = b[3 * i + c] * b[3 * i + c];
@@ -164,6 +214,7 @@ __global__ void __launch_bounds__(IBB) k_af_start(IBDev ib, const double* __rest
       k.rz = t[0];
       k.rr = t[1];
       k.bb = fmax(t[2], k.rr);
+      k.beta = 0.0;
       k.iter = 0;
       k.status = 0;
       k.done = (k.rr <= k.tol2 * k.bb) ? 1 : 0;
@@ -214,15 +265,6 @@ __global__ void __launch_bounds__(IBB) k_af_update(IBDev ib, double* __restrict_
     }
   any = __syncthreads_or(any ? 1 : 0) != 0;
   if (threadIdx.x == 0) set_cond(cond, any);
-}
-
-__global__ void k_af_p(IBDev ib, const double* __restrict__ z, double* __restrict__ p, const KState* ks) {
-  KCOUNT();
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= ib.M) return;
-  const KState* ki = ks + ib.pinst[i] * 3;
-  for (int c = 0; c < 3; ++c)
-    if (!ki[c].done) p[3 * i + c] = z[3 * i + c] + ki[c].beta * p[3 * i + c];
 }
 
 // one thread per free support node: u += coef * sum_e W[ent] G[point(ent)]
@@ -281,11 +323,18 @@ cudaError_t ib_solve(const IBDev& ib, const double* BF, double* G, double* work,
   const int gt = int((ib.M + IBB - 1) / IBB);        // thread-per-row grids
   IBG_LAUNCH(k_af_apply, gw, IBB, 0, st, ib, G, q, 0, ks, rb.partials, rb.counter);
   IBG_LAUNCH(k_af_start, gt, IBB, 0, st, ib, BF, q, r, z, p, ks, rb.partials, rb.counter, cond);
-  cudaError_t e = run_loop(cc, st, cond, ks, ks_host, ib.ninst * 3, max_iter, 8, 64,
+  // k_af_start left p = z and beta = 0; the direction ping-pongs between p and
+  // p2, two iterations per loop body
+  double* p2 = work + 4 * L;
+  const int g8 = int((ib.M * AFL + IBB - 1) / IBB);
+  auto iter = [&](cudaStream_t s, const Cond& c, const double* pold, double* pnew) {
+    IBG_LAUNCH(k_af_apply_p, g8, IBB, 0, s, ib, z, pold, pnew, q, ks, rb.partials, rb.counter);
+    IBG_LAUNCH(k_af_update, gt, IBB, 0, s, ib, G, r, z, pnew, q, ks, rb.partials, rb.counter, c);
+  };
+  cudaError_t e = run_loop(cc, st, cond, ks, ks_host, ib.ninst * 3, max_iter, 4, 32,
                            [&](cudaStream_t s, const Cond& c) {
-    IBG_LAUNCH(k_af_apply, gw, IBB, 0, s, ib, p, q, 1, ks, rb.partials, rb.counter);
-    IBG_LAUNCH(k_af_update, gt, IBB, 0, s, ib, G, r, z, p, q, ks, rb.partials, rb.counter, c);
-    IBG_LAUNCH(k_af_p, gt, IBB, 0, s, ib, z, p, ks);
+    iter(s, c, p, p2);
+    iter(s, c, p2, p);
   });
   if (e != cudaSuccess) return e;
   IBG_LAUNCH(k_collect, (ib.ninst + 127) / 128, 128, 0, st, ks, 3, ib.ninst, rec, (OState*)nullptr);

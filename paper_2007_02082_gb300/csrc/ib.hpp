@@ -20,6 +20,7 @@ struct IBDev {
   const int32_t* pinst;    // [M] instance of each row
   const int32_t* seg_t;    // [ninst + 1] block range, 256 rows per block
   const int32_t* seg_w;    // [ninst + 1] block range, 8 rows per block
+  const int32_t* seg_g;    // [ninst + 1] block range, 32 rows per block
   const double* pscale;    // [M] dt / (rho h^3) of the row's instance
   const double* iorigin;   // [ninst][3] box origin
   const double* ihf;       // [ninst][3] finest spacing
@@ -48,7 +49,7 @@ void ib_assemble(const IBDev& ib, cudaStream_t st);
 void ib_gather(const IBDev& ib, const double* u, int64_t nslots, const double* UB, double* BF, cudaStream_t st);
 // PCG on S G = B_F for the 3 components ([M][3]); G holds the warm start.  The
 // loop is a graph WHILE node when st is capturing; the result goes to rec.
-cudaError_t ib_solve(const IBDev& ib, const double* BF, double* G, double* work /* 4*3*M */, KState* ks,
+cudaError_t ib_solve(const IBDev& ib, const double* BF, double* G, double* work /* 5*3*M */, KState* ks,
                      KState* ks_host, RedBuf rb, double rtol, int max_iter, SolveRec* rec, cudaStream_t st,
                      CaptureCtx* cc);
 // u_j += coef * sum_i W[i][a(j)] G_i on free support nodes (Eq. 19, Eq. 14).

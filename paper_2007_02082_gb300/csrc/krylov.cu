@@ -145,73 +145,6 @@ __global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict
   if (threadIdx.x == 0) set_cond(cond, any);
 }
 
-// One CTA per chunk of bricks; every thread walks its node of each brick.
-template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_cg_update(DevGrid g, T* __restrict__ x, T* __restrict__ r,
-                                                   T* __restrict__ z, const T* __restrict__ p,
-                                                   const T* __restrict__ q, const T* __restrict__ dinv,
-                                                   uint16_t dmask, KState* ks, double* partials, unsigned* counter,
-                                                   Cond cond) {
-  KCOUNT();
-  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
-  const KState* ki = ks + g.binst[b0] * NC;
-  bool act[NC];
-  T a[NC];
-  for (int c = 0; c < NC; ++c) {
-    act[c] = !ki[c].done;
-    a[c] = k_alpha<T>(ki[c]);
-  }
-  T tv[2 * NC];
-  for (int c = 0; c < 2 * NC; ++c) tv[c] = T(0);
-#pragma unroll 4
-  for (int bb = b0; bb < b1; ++bb) {
-    const int64_t s = (int64_t)bb * DBV + threadIdx.x;
-    const uint16_t m = g.meta[s];
-    const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
-    const T di = dinv[s];
-    for (int c = 0; c < NC; ++c) {
-      if (!act[c]) continue;
-      const T* qc = q + c * g.nslots;
-      const int64_t i = c * g.nslots + s;
-      T qv = qc[s];
-      if (m & D_IFACE) {   // interface sum: both copies + half of each hanging child
-        const int e = g.if_of_slot[s];
-        qv = qc[g.if_c[e]] + qc[g.if_f[e]];
-        for (int k = g.if_off[e]; k < g.if_off[e + 1]; ++k) qv += T(0.5) * qc[g.if_kid[k]];
-      }
-      if (m & D_VALID) x[i] += a[c] * p[i];
-      T rv = keep ? T(r[i] - a[c] * qv) : T(0);
-      T zv = rv * di;
-      r[i] = rv;
-      z[i] = zv;
-      if (dof) {
-        tv[2 * c] += rv * zv;
-        tv[2 * c + 1] += rv * rv;
-      }
-    }
-  }
-  double* out = partials + (int64_t)gridDim.x * 2 * NC;
-  if (!grid_sum_last<T, 2 * NC>(tv, partials, counter, g.cseg, g.ninst, out)) return;
-  bool any = false;
-  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
-    for (int c = 0; c < NC; ++c) {
-      KState& k = ks[i * NC + c];
-      if (k.done) continue;
-      k.iter++;
-      k.rr = out[(int64_t)i * 2 * NC + 2 * c + 1];
-      const double rzn = out[(int64_t)i * 2 * NC + 2 * c];
-      if (!isfinite(k.rr) || !isfinite(rzn)) { k.done = 1; k.status = 5; continue; }
-      if (k.rr <= k.tol2 * k.bb) { k.done = 1; continue; }
-      if (k.iter >= k.max_iter) { k.done = 1; k.status = 4; continue; }
-      k.beta = rzn / k.rz;
-      k.bf = float(k.beta);
-      k.rz = rzn;
-      any = true;
-    }
-  any = block_any(any);
-  if (threadIdx.x == 0) set_cond(cond, any);
-}
-
 // Streaming form of k_cg_update for one component: each thread handles W =
 // 16 / sizeof(T) consecutive slots with 16-byte loads and stores; slots of
 // interface copies take the interface sum of q one by one.
@@ -219,7 +152,7 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; using mt = uint2; static constexpr int W = 4; };
 template <> struct Vec16<double> { using type = double2; using mt = uint32_t; static constexpr int W = 2; };
 
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(512) k_cg_update_vec(DevGrid g, T* __restrict__ x, T* __restrict__ r,
                                                        T* __restrict__ z, const T* __restrict__ p,
                                                        const T* __restrict__ q, const T* __restrict__ dinv,
@@ -230,66 +163,73 @@ __global__ void __launch_bounds__(512) k_cg_update_vec(DevGrid g, T* __restrict_
   using MT = typename Vec16<T>::mt;
   constexpr int W = Vec16<T>::W;
   const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
-  const KState& k = ks[g.binst[b0]];
-  T tv[2] = {T(0), T(0)};
-  if (!k.done) {
-    const T a = k_alpha<T>(k);
-    const int64_t s1 = (int64_t)b1 * DBV;
-    for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
-      const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
-      const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
-      V xv = *reinterpret_cast<const V*>(x + s);
-      V rv = *reinterpret_cast<const V*>(r + s);
-      V pv = *reinterpret_cast<const V*>(p + s);
-      V qv = *reinterpret_cast<const V*>(q + s);
-      V dv = *reinterpret_cast<const V*>(dinv + s);
+  const KState* ki = ks + g.binst[b0] * NC;
+  T tv[2 * NC];
+#pragma unroll
+  for (int c = 0; c < 2 * NC; ++c) tv[c] = T(0);
+  const int64_t s1 = (int64_t)b1 * DBV;
+  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
+    const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
+    const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+    const V dv = *reinterpret_cast<const V*>(dinv + s);
+    const T* de = reinterpret_cast<const T*>(&dv);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (ki[c].done) continue;
+      const T a = k_alpha<T>(ki[c]);
+      const int64_t i = (int64_t)c * g.nslots + s;
+      const T* qc = q + (int64_t)c * g.nslots;
+      V xv = *reinterpret_cast<const V*>(x + i);
+      V rv = *reinterpret_cast<const V*>(r + i);
+      const V pv = *reinterpret_cast<const V*>(p + i);
+      const V qv = *reinterpret_cast<const V*>(q + i);
       T* xe = reinterpret_cast<T*>(&xv);
       T* re = reinterpret_cast<T*>(&rv);
-      T* pe = reinterpret_cast<T*>(&pv);
-      T* qe = reinterpret_cast<T*>(&qv);
-      T* de = reinterpret_cast<T*>(&dv);
+      const T* pe = reinterpret_cast<const T*>(&pv);
+      const T* qe = reinterpret_cast<const T*>(&qv);
       V zv;
       T* ze = reinterpret_cast<T*>(&zv);
 #pragma unroll
       for (int j = 0; j < W; ++j) {
         const uint16_t m = mm[j];
         T qq = qe[j];
-        if (m & D_IFACE) {
+        if (m & D_IFACE) {   // interface sum: both copies + half of each hanging child
           const int e = g.if_of_slot[s + j];
-          qq = q[g.if_c[e]] + q[g.if_f[e]];
-          for (int kk = g.if_off[e]; kk < g.if_off[e + 1]; ++kk) qq += T(0.5) * q[g.if_kid[kk]];
+          qq = qc[g.if_c[e]] + qc[g.if_f[e]];
+          for (int kk = g.if_off[e]; kk < g.if_off[e + 1]; ++kk) qq += T(0.5) * qc[g.if_kid[kk]];
         }
         if (m & D_VALID) xe[j] += a * pe[j];
         const T rn = kkeep(m, dmask) ? T(re[j] - a * qq) : T(0);
         re[j] = rn;
         ze[j] = rn * de[j];
         if (kdof(m, dmask)) {
-          tv[0] += rn * ze[j];
-          tv[1] += rn * rn;
+          tv[2 * c] += rn * ze[j];
+          tv[2 * c + 1] += rn * rn;
         }
       }
-      *reinterpret_cast<V*>(x + s) = xv;
-      *reinterpret_cast<V*>(r + s) = rv;
-      *reinterpret_cast<V*>(z + s) = zv;
+      *reinterpret_cast<V*>(x + i) = xv;
+      *reinterpret_cast<V*>(r + i) = rv;
+      *reinterpret_cast<V*>(z + i) = zv;
     }
   }
-  double* out = partials + (int64_t)gridDim.x * 2;
-  if (!grid_sum_last<T, 2>(tv, partials, counter, g.cseg, g.ninst, out)) return;
+  double* out = partials + (int64_t)gridDim.x * 2 * NC;
+  if (!grid_sum_last<T, 2 * NC>(tv, partials, counter, g.cseg, g.ninst, out)) return;
   bool any = false;
-  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
-    KState& kk = ks[i];
-    if (kk.done) continue;
-    kk.iter++;
-    kk.rr = out[(int64_t)i * 2 + 1];
-    const double rzn = out[(int64_t)i * 2];
-    if (!isfinite(kk.rr) || !isfinite(rzn)) { kk.done = 1; kk.status = 5; continue; }
-    if (kk.rr <= kk.tol2 * kk.bb) { kk.done = 1; continue; }
-    if (kk.iter >= kk.max_iter) { kk.done = 1; kk.status = 4; continue; }
-    kk.beta = rzn / kk.rz;
-    kk.bf = float(kk.beta);
-    kk.rz = rzn;
-    any = true;
-  }
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
+    for (int c = 0; c < NC; ++c) {
+      KState& kk = ks[i * NC + c];
+      if (kk.done) continue;
+      kk.iter++;
+      kk.rr = out[(int64_t)i * 2 * NC + 2 * c + 1];
+      const double rzn = out[(int64_t)i * 2 * NC + 2 * c];
+      if (!isfinite(kk.rr) || !isfinite(rzn)) { kk.done = 1; kk.status = 5; continue; }
+      if (kk.rr <= kk.tol2 * kk.bb) { kk.done = 1; continue; }
+      if (kk.iter >= kk.max_iter) { kk.done = 1; kk.status = 4; continue; }
+      kk.beta = rzn / kk.rz;
+      kk.bf = float(kk.beta);
+      kk.rz = rzn;
+      any = true;
+    }
   any = block_any(any);
   if (threadIdx.x == 0) set_cond(cond, any);
 }
@@ -465,41 +405,101 @@ __global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restric
   if (threadIdx.x == 0) set_cond(cond, any);
 }
 
+// ---------------------------------------------------------------- BiCGStab, streaming form
+// Chunked, 16-byte vector forms of the BiCGStab updates.  The operator outputs
+// v = A ph and t = A sh stay local per level (no separate interface-sum
+// launch): every reader adds the interface sum of a copy's value itself.
+
+template <typename T>
+__device__ __forceinline__ T iface_sum(const DevGrid& g, const T* __restrict__ q, int64_t s) {
+  const int e = g.if_of_slot[s];
+  T v = q[g.if_c[e]] + q[g.if_f[e]];
+  for (int k = g.if_off[e]; k < g.if_off[e + 1]; ++k) v += T(0.5) * q[g.if_kid[k]];
+  return v;
+}
+
+// p = r + beta (p - omega v), ph = D^-1 p  (kept slots; 0 elsewhere)
 template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_bcg_p(DevGrid g, const T* __restrict__ r, T* __restrict__ p,
-                                               const T* __restrict__ v, T* __restrict__ ph,
-                                               const T* __restrict__ dinv, uint16_t dmask, const KState* ks) {
+__global__ void __launch_bounds__(512) k_bcgv_p(DevGrid g, const T* __restrict__ r, T* __restrict__ p,
+                                                const T* __restrict__ v, T* __restrict__ ph,
+                                                const T* __restrict__ dinv, uint16_t dmask, const KState* ks) {
   KCOUNT();
-  const KState* ki = ks + g.binst[blockIdx.x] * NC;
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool keep = kkeep(m, dmask);
-  for (int c = 0; c < NC; ++c) {
-    if (ki[c].done) continue;
-    const int64_t i = c * g.nslots + s;
-    T pv = keep ? T(r[i] + k_beta<T>(ki[c]) * (p[i] - k_omega<T>(ki[c]) * v[i])) : T(0);
-    p[i] = pv;
-    ph[i] = pv * dinv[s];
+  using V = typename Vec16<T>::type;
+  using MT = typename Vec16<T>::mt;
+  constexpr int W = Vec16<T>::W;
+  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const KState* ki = ks + g.binst[b0] * NC;
+  const int64_t s1 = (int64_t)b1 * DBV;
+  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
+    const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
+    const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+    const V dv = *reinterpret_cast<const V*>(dinv + s);
+    const T* de = reinterpret_cast<const T*>(&dv);
+    for (int c = 0; c < NC; ++c) {
+      if (ki[c].done) continue;
+      const T be = k_beta<T>(ki[c]), om = k_omega<T>(ki[c]);
+      const int64_t i = (int64_t)c * g.nslots + s;
+      const V rv = *reinterpret_cast<const V*>(r + i);
+      const V vv = *reinterpret_cast<const V*>(v + i);
+      V pv = *reinterpret_cast<const V*>(p + i);
+      V hv;
+      const T* re = reinterpret_cast<const T*>(&rv);
+      const T* ve = reinterpret_cast<const T*>(&vv);
+      T* pe = reinterpret_cast<T*>(&pv);
+      T* he = reinterpret_cast<T*>(&hv);
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        const uint16_t m = mm[j];
+        const T vs = (m & D_IFACE) ? iface_sum(g, v + (int64_t)c * g.nslots, s + j) : ve[j];
+        const T pn = kkeep(m, dmask) ? T(re[j] + be * (pe[j] - om * vs)) : T(0);
+        pe[j] = pn;
+        he[j] = pn * de[j];
+      }
+      *reinterpret_cast<V*>(p + i) = pv;
+      *reinterpret_cast<V*>(ph + i) = hv;
+    }
   }
 }
 
 // mode 0: alpha = rho / (rh, v);  mode 1: omega = (t, s) / (t, t)
 template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_bcg_dot(DevGrid g, const T* __restrict__ a1, const T* __restrict__ b1,
-                                                 const T* __restrict__ a2, uint16_t dmask, int mode, KState* ks,
-                                                 double* partials, unsigned* counter) {
+__global__ void __launch_bounds__(512) k_bcgv_dot(DevGrid g, const T* __restrict__ a1, const T* __restrict__ b1v,
+                                                  uint16_t dmask, int mode, KState* ks, double* partials,
+                                                  unsigned* counter) {
   KCOUNT();
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool dof = kdof(m, dmask);
+  using V = typename Vec16<T>::type;
+  using MT = typename Vec16<T>::mt;
+  constexpr int W = Vec16<T>::W;
+  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const KState* ki = ks + g.binst[b0] * NC;
   T tw[2 * NC];
-  for (int c = 0; c < NC; ++c) {
-    const int64_t i = c * g.nslots + s;
-    tw[2 * c] = dof ? a1[i] * b1[i] : T(0);
-    tw[2 * c + 1] = (dof && mode == 1) ? a2[i] * a2[i] : T(0);
+#pragma unroll
+  for (int c = 0; c < 2 * NC; ++c) tw[c] = T(0);
+  // b1v is the operator output (v or t, interface sums on read); a1 is rh (mode 0) or s (mode 1)
+  const int64_t s1 = (int64_t)b1 * DBV;
+  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
+    const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
+    const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (ki[c].done) continue;
+      const int64_t i = (int64_t)c * g.nslots + s;
+      const V av = *reinterpret_cast<const V*>(a1 + i);
+      const V bv = *reinterpret_cast<const V*>(b1v + i);
+      const T* ae = reinterpret_cast<const T*>(&av);
+      const T* be = reinterpret_cast<const T*>(&bv);
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        const uint16_t m = mm[j];
+        if (!kdof(m, dmask)) continue;
+        const T q = (m & D_IFACE) ? iface_sum(g, b1v + (int64_t)c * g.nslots, s + j) : be[j];
+        tw[2 * c] += ae[j] * q;
+        if (mode == 1) tw[2 * c + 1] += q * q;
+      }
+    }
   }
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
-  if (!grid_sum_last<T, 2 * NC>(tw, partials, counter, g.bseg, g.ninst, out)) return;
+  if (!grid_sum_last<T, 2 * NC>(tw, partials, counter, g.cseg, g.ninst, out)) return;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
     for (int c = 0; c < NC; ++c) {
       KState& k = ks[i * NC + c];
@@ -519,51 +519,105 @@ __global__ void __launch_bounds__(512) k_bcg_dot(DevGrid g, const T* __restrict_
     }
 }
 
+// s = r - alpha v, sh = D^-1 s
 template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_bcg_s(DevGrid g, const T* __restrict__ r, const T* __restrict__ v,
-                                               T* __restrict__ sv, T* __restrict__ sh, const T* __restrict__ dinv,
-                                               uint16_t dmask, const KState* ks) {
+__global__ void __launch_bounds__(512) k_bcgv_s(DevGrid g, const T* __restrict__ r, const T* __restrict__ v,
+                                                T* __restrict__ sv, T* __restrict__ sh, const T* __restrict__ dinv,
+                                                uint16_t dmask, const KState* ks) {
   KCOUNT();
-  const KState* ki = ks + g.binst[blockIdx.x] * NC;
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool keep = kkeep(m, dmask);
-  for (int c = 0; c < NC; ++c) {
-    if (ki[c].done) continue;
-    const int64_t i = c * g.nslots + s;
-    T val = keep ? T(r[i] - k_alpha<T>(ki[c]) * v[i]) : T(0);
-    sv[i] = val;
-    sh[i] = val * dinv[s];
+  using V = typename Vec16<T>::type;
+  using MT = typename Vec16<T>::mt;
+  constexpr int W = Vec16<T>::W;
+  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const KState* ki = ks + g.binst[b0] * NC;
+  const int64_t s1 = (int64_t)b1 * DBV;
+  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
+    const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
+    const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+    const V dv = *reinterpret_cast<const V*>(dinv + s);
+    const T* de = reinterpret_cast<const T*>(&dv);
+    for (int c = 0; c < NC; ++c) {
+      if (ki[c].done) continue;
+      const T al = k_alpha<T>(ki[c]);
+      const int64_t i = (int64_t)c * g.nslots + s;
+      const V rv = *reinterpret_cast<const V*>(r + i);
+      const V vv = *reinterpret_cast<const V*>(v + i);
+      V so, ho;
+      const T* re = reinterpret_cast<const T*>(&rv);
+      const T* ve = reinterpret_cast<const T*>(&vv);
+      T* se = reinterpret_cast<T*>(&so);
+      T* he = reinterpret_cast<T*>(&ho);
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        const uint16_t m = mm[j];
+        const T vs = (m & D_IFACE) ? iface_sum(g, v + (int64_t)c * g.nslots, s + j) : ve[j];
+        const T sn = kkeep(m, dmask) ? T(re[j] - al * vs) : T(0);
+        se[j] = sn;
+        he[j] = sn * de[j];
+      }
+      *reinterpret_cast<V*>(sv + i) = so;
+      *reinterpret_cast<V*>(sh + i) = ho;
+    }
   }
 }
 
+// x += alpha ph + omega sh, r = s - omega t; ||r||^2, (rh, r) -> beta, rho
 template <typename T, int NC>
-__global__ void __launch_bounds__(512) k_bcg_xr(DevGrid g, T* __restrict__ x, T* __restrict__ r,
-                                                const T* __restrict__ rh, const T* __restrict__ ph,
-                                                const T* __restrict__ sh, const T* __restrict__ sv,
-                                                const T* __restrict__ tv, uint16_t dmask, KState* ks,
-                                                double* partials, unsigned* counter, Cond cond) {
+__global__ void __launch_bounds__(512) k_bcgv_xr(DevGrid g, T* __restrict__ x, T* __restrict__ r,
+                                                 const T* __restrict__ rh, const T* __restrict__ ph,
+                                                 const T* __restrict__ sh, const T* __restrict__ sv,
+                                                 const T* __restrict__ tv, uint16_t dmask, KState* ks,
+                                                 double* partials, unsigned* counter, Cond cond) {
   KCOUNT();
-  const KState* ki = ks + g.binst[blockIdx.x] * NC;
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
+  using V = typename Vec16<T>::type;
+  using MT = typename Vec16<T>::mt;
+  constexpr int W = Vec16<T>::W;
+  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const KState* ki = ks + g.binst[b0] * NC;
   T tw[2 * NC];
-  for (int c = 0; c < NC; ++c) {
-    tw[2 * c] = tw[2 * c + 1] = T(0);
-    if (ki[c].done) continue;
-    const int64_t i = c * g.nslots + s;
-    const T al = k_alpha<T>(ki[c]), om = k_omega<T>(ki[c]);
-    if (m & D_VALID) x[i] += al * ph[i] + om * sh[i];
-    T rv = keep ? T(sv[i] - om * tv[i]) : T(0);
-    r[i] = rv;
-    if (dof) {
-      tw[2 * c] = rv * rv;
-      tw[2 * c + 1] = rh[i] * rv;
+#pragma unroll
+  for (int c = 0; c < 2 * NC; ++c) tw[c] = T(0);
+  const int64_t s1 = (int64_t)b1 * DBV;
+  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
+    const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
+    const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (ki[c].done) continue;
+      const T al = k_alpha<T>(ki[c]), om = k_omega<T>(ki[c]);
+      const int64_t i = (int64_t)c * g.nslots + s;
+      V xv = *reinterpret_cast<const V*>(x + i);
+      const V pv = *reinterpret_cast<const V*>(ph + i);
+      const V hv = *reinterpret_cast<const V*>(sh + i);
+      const V sv_ = *reinterpret_cast<const V*>(sv + i);
+      const V tv_ = *reinterpret_cast<const V*>(tv + i);
+      const V qv = *reinterpret_cast<const V*>(rh + i);
+      V ro;
+      T* xe = reinterpret_cast<T*>(&xv);
+      const T* pe = reinterpret_cast<const T*>(&pv);
+      const T* he = reinterpret_cast<const T*>(&hv);
+      const T* se = reinterpret_cast<const T*>(&sv_);
+      const T* te = reinterpret_cast<const T*>(&tv_);
+      const T* qe = reinterpret_cast<const T*>(&qv);
+      T* oe = reinterpret_cast<T*>(&ro);
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        const uint16_t m = mm[j];
+        if (m & D_VALID) xe[j] += al * pe[j] + om * he[j];
+        const T ts = (m & D_IFACE) ? iface_sum(g, tv + (int64_t)c * g.nslots, s + j) : te[j];
+        const T rn = kkeep(m, dmask) ? T(se[j] - om * ts) : T(0);
+        oe[j] = rn;
+        if (kdof(m, dmask)) {
+          tw[2 * c] += rn * rn;
+          tw[2 * c + 1] += qe[j] * rn;
+        }
+      }
+      *reinterpret_cast<V*>(x + i) = xv;
+      *reinterpret_cast<V*>(r + i) = ro;
     }
   }
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
-  if (!grid_sum_last<T, 2 * NC>(tw, partials, counter, g.bseg, g.ninst, out)) return;
+  if (!grid_sum_last<T, 2 * NC>(tw, partials, counter, g.cseg, g.ninst, out)) return;
   bool any = false;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
     for (int c = 0; c < NC; ++c) {
@@ -586,27 +640,41 @@ __global__ void __launch_bounds__(512) k_bcg_xr(DevGrid g, T* __restrict__ x, T*
 }
 
 // ---------------------------------------------------------------- FP64 outer loop
-// r = b - y on DOF rows; the first pass fixes the reference norm; sets the
-// outer loop condition and the condition of the inner-solve branch.
+// r = b - y on DOF rows, written rounded to FP32 as the inner right-hand side
+// (r32) with the inner initial guess zeroed (e32); ||r||^2 in FP64, and on the
+// first pass ||b||^2 for the reference norm.  Sets the outer loop condition
+// and the condition of the inner-solve branch.  One CTA per chunk of bricks.
 template <int NC>
 __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double* __restrict__ b,
-                                                        const double* __restrict__ y, double* __restrict__ r,
-                                                        uint16_t dmask, OState* os, double* partials,
-                                                        unsigned* counter, Cond cloop, Cond cbranch) {
+                                                        const double* __restrict__ y, float* __restrict__ r32,
+                                                        float* __restrict__ e32, uint16_t dmask, OState* os,
+                                                        double* partials, unsigned* counter, Cond cloop,
+                                                        Cond cbranch) {
   KCOUNT();
-  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  const uint16_t m = g.meta[s];
-  const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
+  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const OState& oi = os[g.binst[b0]];
+  const bool first = oi.iter == 0;
   double w[2 * NC];
-  for (int c = 0; c < NC; ++c) {
-    const int64_t i = c * g.nslots + s;
-    double rv = keep ? b[i] - y[i] : 0.0;
-    r[i] = rv;
-    w[2 * c] = dof ? rv * rv : 0.0;
-    w[2 * c + 1] = dof ? b[i] * b[i] : 0.0;
-  }
+#pragma unroll
+  for (int c = 0; c < 2 * NC; ++c) w[c] = 0.0;
+  if (!oi.done)
+    for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x) {
+      const uint16_t m = g.meta[s];
+      const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int64_t i = c * g.nslots + s;
+        const double rv = keep ? b[i] - y[i] : 0.0;
+        r32[i] = float(rv);
+        e32[i] = 0.f;
+        if (dof) {
+          w[2 * c] += rv * rv;
+          if (first) w[2 * c + 1] += b[i] * b[i];
+        }
+      }
+    }
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
-  if (!grid_sum_last<double, 2 * NC>(w, partials, counter, g.bseg, g.ninst, out)) return;
+  if (!grid_sum_last<double, 2 * NC>(w, partials, counter, g.cseg, g.ninst, out)) return;
   bool any = false;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
     OState& o = os[i];
@@ -697,12 +765,8 @@ static cudaError_t cg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b
     fe_apply_cg<T>(g, A, NC, w.z, pold, pnew, w.q, a.ks, rb, s);
     pend(a.prof, s);
     pbegin(a.prof, a.pbase + 1, s);
-    if (NC == 1)
-      IBG_LAUNCH((k_cg_update_vec<T>), g.nchunks, DBV, 0, s, g, x, w.r, w.z, pnew, w.q, A.dinv, A.dmask, a.ks,
-                 rb.partials, rb.counter, c);
-    else
-      IBG_LAUNCH((k_cg_update<T, NC>), g.nchunks, DBV, 0, s, g, x, w.r, w.z, pnew, w.q, A.dinv, A.dmask, a.ks,
-                 rb.partials, rb.counter, c);
+    IBG_LAUNCH((k_cg_update_vec<T, NC>), g.nchunks, DBV, 0, s, g, x, w.r, w.z, pnew, w.q, A.dinv, A.dmask, a.ks,
+               rb.partials, rb.counter, c);
     pend(a.prof, s);
     fe_expand2<T>(g, NC, w.z, (T*)nullptr, s);
   };
@@ -735,7 +799,7 @@ static cudaError_t cg_mg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const M
   fe_apply<T>(g, A, 1, x, w.q, st);
   IBG_LAUNCH(k_cg_start_r<T>, g.nbricks, DBV, 0, st, g, b, w.q, w.r, A.dmask, a.ks, rb.partials, rb.counter,
              skip_os);
-  mg_vcycle<T>(g, mg, w.r, w.z, zs, w.q, A.dinv, A.dmask, a.ks, st, a.prof, 7);
+  mg_vcycle<T>(g, mg, w.r, w.z, zs, w.q, A.dinv, A.dmask, a.ks, st, a.prof, 9);
   IBG_LAUNCH(k_cg_rz<T>, g.nchunks, DBV, 0, st, g, w.r, w.z, A.dmask, a.ks, rb.partials, rb.counter, cond, 1);
   auto iter = [&](cudaStream_t s, const Cond& c, T* pold, T* pnew) {
     pbegin(a.prof, a.pbase + 0, s);
@@ -745,7 +809,7 @@ static cudaError_t cg_mg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const M
     IBG_LAUNCH(k_cg_update_r<T>, g.nchunks, DBV, 0, s, g, x, w.r, pnew, w.q, A.dmask, a.ks, rb.partials,
                rb.counter);
     pend(a.prof, s);
-    mg_vcycle<T>(g, mg, w.r, w.z, zs, w.q, A.dinv, A.dmask, a.ks, s, a.prof, 7);
+    mg_vcycle<T>(g, mg, w.r, w.z, zs, w.q, A.dinv, A.dmask, a.ks, s, a.prof, 9);
     IBG_LAUNCH(k_cg_rz<T>, g.nchunks, DBV, 0, s, g, w.r, w.z, A.dmask, a.ks, rb.partials, rb.counter, c, 0);
   };
   return run_loop(cc, st, cond, a.ks, a.ks_host, g.ninst, a.max_iter, 1, 4, [&](cudaStream_t s, const Cond& c) {
@@ -770,23 +834,26 @@ static cudaError_t bcg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* 
   fe_apply<T>(g, A, NC, x, w.tv, st);
   IBG_LAUNCH((k_bcg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, w.tv, w.r, w.rh, w.p, w.v, A.dmask, a.ks,
              rb.partials, rb.counter, cond, skip_os);
+  // v and t hold the local operator outputs; the kernels below add their
+  // interface sums on read (the start kernel set v = 0)
   return run_loop(cc, st, cond, a.ks, a.ks_host, g.ninst * NC, a.max_iter, 1, 8, [&](cudaStream_t s, const Cond& c) {
-    IBG_LAUNCH((k_bcg_p<T, NC>), g.nbricks, DBV, 0, s, g, w.r, w.p, w.v, w.ph, A.dinv, A.dmask, a.ks);
+    pbegin(a.prof, a.pbase + 2, s);
+    IBG_LAUNCH((k_bcgv_p<T, NC>), g.nchunks, DBV, 0, s, g, w.r, w.p, w.v, w.ph, A.dinv, A.dmask, a.ks);
+    pend(a.prof, s);
     fe_expand2<T>(g, NC, w.ph, (T*)nullptr, s);
     pbegin(a.prof, a.pbase + 0, s);
-    fe_apply<T>(g, A, NC, w.ph, w.v, s);
+    fe_apply_local<T>(g, A, NC, w.ph, w.v, s);
     pend(a.prof, s);
-    IBG_LAUNCH((k_bcg_dot<T, NC>), g.nbricks, DBV, 0, s, g, w.rh, w.v, w.v, A.dmask, 0, a.ks, rb.partials,
-               rb.counter);
-    IBG_LAUNCH((k_bcg_s<T, NC>), g.nbricks, DBV, 0, s, g, w.r, w.v, w.sv, w.sh, A.dinv, A.dmask, a.ks);
+    IBG_LAUNCH((k_bcgv_dot<T, NC>), g.nchunks, DBV, 0, s, g, w.rh, w.v, A.dmask, 0, a.ks, rb.partials, rb.counter);
+    IBG_LAUNCH((k_bcgv_s<T, NC>), g.nchunks, DBV, 0, s, g, w.r, w.v, w.sv, w.sh, A.dinv, A.dmask, a.ks);
     fe_expand2<T>(g, NC, w.sh, (T*)nullptr, s);
     pbegin(a.prof, a.pbase + 0, s);
-    fe_apply<T>(g, A, NC, w.sh, w.tv, s);
+    fe_apply_local<T>(g, A, NC, w.sh, w.tv, s);
     pend(a.prof, s);
-    IBG_LAUNCH((k_bcg_dot<T, NC>), g.nbricks, DBV, 0, s, g, w.tv, w.sv, w.tv, A.dmask, 1, a.ks, rb.partials,
+    IBG_LAUNCH((k_bcgv_dot<T, NC>), g.nchunks, DBV, 0, s, g, w.sv, w.tv, A.dmask, 1, a.ks, rb.partials,
                rb.counter);
     pbegin(a.prof, a.pbase + 1, s);
-    IBG_LAUNCH((k_bcg_xr<T, NC>), g.nbricks, DBV, 0, s, g, x, w.r, w.rh, w.ph, w.sh, w.sv, w.tv, A.dmask, a.ks,
+    IBG_LAUNCH((k_bcgv_xr<T, NC>), g.nchunks, DBV, 0, s, g, x, w.r, w.rh, w.ph, w.sh, w.sv, w.tv, A.dmask, a.ks,
                rb.partials, rb.counter, c);
     pend(a.prof, s);
   });
@@ -822,15 +889,13 @@ cudaError_t solve_enqueue(const SolveArgs& a, cudaStream_t st, CaptureCtx* cc) {
   auto residual = [&](cudaStream_t s, const Cond& cl, const Cond& cb) {
     fe_apply<double>(g, A64, a.nc, a.x, a.y64, s);
     if (a.nc == 1)
-      IBG_LAUNCH(k_residual_outer<1>, g.nbricks, DBV, 0, s, g, a.b, a.y64, a.r64, a.dmask, a.os, a.rb.partials,
+      IBG_LAUNCH(k_residual_outer<1>, g.nchunks, DBV, 0, s, g, a.b, a.y64, a.r32, a.e32, a.dmask, a.os, a.rb.partials,
                  a.rb.counter, cl, cb);
     else
-      IBG_LAUNCH(k_residual_outer<3>, g.nbricks, DBV, 0, s, g, a.b, a.y64, a.r64, a.dmask, a.os, a.rb.partials,
+      IBG_LAUNCH(k_residual_outer<3>, g.nchunks, DBV, 0, s, g, a.b, a.y64, a.r32, a.e32, a.dmask, a.os, a.rb.partials,
                  a.rb.counter, cl, cb);
   };
   auto correction = [&](cudaStream_t s) {
-    fe_cast_d2f(n, a.r64, a.r32, s);
-    fe_zero<float>(n, a.e32, s);
     cudaError_t e = inner_enqueue<float>(a, A32, a.r32, a.e32, a.w32, s, cc, a.rtol_inner, a.os);
     IBG_LAUNCH(k_collect, ib, 128, 0, s, a.ks, a.nc, g.ninst, a.rec, a.os);
     IBG_LAUNCH(k_add_f2d_active, g.nbricks, DBV, 0, s, g, a.e32, a.x, a.nc, (const OState*)a.os);

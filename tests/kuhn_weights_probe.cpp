@@ -1,0 +1,15 @@
+// Test driver: prints the library's incident-cell-mask weights (kuhn_weights.hpp)
+// for every mask: 15 mass weights, then the 6 axis-edge counts (+x -x +y -y +z -z).
+#include <cstdio>
+
+#include "kuhn_weights.hpp"
+
+int main() {
+  for (int m = 0; m < 256; ++m) {
+    for (int k = 0; k < 15; ++k) std::printf("%d ", ibg::mass_weight(m, k));
+    for (int a = 0; a < 3; ++a)
+      for (int s = 1; s >= -1; s -= 2) std::printf("%d ", ibg::stiff_edge_count(m, a, s));
+    std::printf("\n");
+  }
+  return 0;
+}

@@ -1,0 +1,63 @@
+"""Incident-cell-mask weights of the P1 Kuhn operators (csrc/kuhn_weights.hpp).
+
+The library derives the consistent-mass and stiffness couplings of a node from
+the 8-bit mask of its active incident cells by closed formulas.  This test
+enumerates, for every mask, the six Kuhn tetrahedra of every active incident
+cell (one per axis order, Sec. 3.1 box mesh) and counts directly which of them
+hold the node and each neighbour: the counts must equal the formulas.
+"""
+import itertools
+import os
+import subprocess
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2007_02082_gb300", "csrc")
+
+OFFSETS = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1), (1, 1, 0), (-1, -1, 0),
+           (0, 1, 1), (0, -1, -1), (1, 0, 1), (-1, 0, -1), (1, 1, 1), (-1, -1, -1)]
+
+
+def brute_force(mask):
+    mass = np.zeros(15, int)
+    edge = np.zeros(6, int)
+    for c in range(8):
+        if not (mask >> c) & 1:
+            continue
+        d = np.array([c & 1, (c >> 1) & 1, (c >> 2) & 1])
+        lower = d - 1                                  # cell lower corner relative to the node
+        for perm in itertools.permutations(range(3)):
+            v = [lower.copy()]
+            for a in perm:
+                w = v[-1].copy()
+                w[a] += 1
+                v.append(w)
+            verts = [tuple(x) for x in v]
+            if (0, 0, 0) not in verts:
+                continue
+            for k, o in enumerate(OFFSETS):
+                if o in verts:
+                    mass[k] += 2 if k == 0 else 1
+            for i in range(3):                         # axis edges of the tetrahedron
+                p, q = verts[i], verts[i + 1]
+                if (0, 0, 0) in (p, q):
+                    other = q if p == (0, 0, 0) else p
+                    a = perm[i]
+                    s = other[a]
+                    edge[2 * a + (0 if s > 0 else 1)] += 1
+    return mass, edge
+
+
+def test_mask_weights_match_tetrahedron_enumeration(tmp_path):
+    exe = tmp_path / "kw"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-I", CSRC, os.path.join(ROOT, "tests", "kuhn_weights_probe.cpp"),
+                    "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for mask in range(256):
+        got = np.array([int(v) for v in out[mask].split()])
+        mass, edge = brute_force(mask)
+        assert np.array_equal(got[:15], mass), (mask, got[:15], mass)
+        assert np.array_equal(got[15:], edge), (mask, got[15:], edge)
+    # interior node: row of the mass matrix sums to the cell volume (120 units)
+    assert sum(int(v) for v in out[255].split()[:15]) == 120
