@@ -266,6 +266,23 @@ def run_native(args, rank, world, local_rank):
     e2e = {"value": cells * e2e_steps * world / te, "unit": UNIT,
            "h2d_bytes_per_step": int(hu.nbytes + hp.nbytes), "d2h_bytes_per_step": int(hu.nbytes + hp.nbytes)}
 
+    # accuracy of the timed path against the plain FP64 GPU path: both from the
+    # same initial state, args.accuracy_steps steps, outside the timed region
+    accuracy = None
+    if args.accuracy_steps > 0 and args.precision == "mixed":
+        ga = IBGrid(case, precision="mixed", device=local_rank, poisson_pc=args.poisson_pc)
+        gb = IBGrid(case, precision="fp64", device=local_rank, poisson_pc=args.poisson_pc)
+        ga.ipcs_step(args.accuracy_steps)
+        gb.ipcs_step(args.accuracy_steps)
+        acc = {}
+        for f in ("U", "P"):
+            xa, xb = ga.ib_fields_get(f), gb.ib_fields_get(f)
+            acc["rel_l2_" + f.lower()] = float(np.linalg.norm(xa - xb) / max(np.linalg.norm(xb), 1e-300))
+        accuracy = {"steps": args.accuracy_steps, **acc, "tolerance": 1e-6,
+                    "within": bool(max(acc.values()) <= 1e-6), "against": "plain FP64 GPU path, same start"}
+        ga.close()
+        gb.close()
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -289,6 +306,7 @@ def run_native(args, rank, world, local_rank):
         "e2e": e2e,
         "iters_last_step": {k: i2[k] for k in ("iters_mom", "iters_ib", "iters_p", "iters_corr", "outer_mom",
                                               "outer_p", "outer_corr")},
+        "accuracy": accuracy,
     }
     g.close()
     return out
@@ -333,6 +351,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--poisson-pc", default="multigrid", choices=["multigrid", "jacobi"])
+    ap.add_argument("--accuracy-steps", type=int, default=20,
+                    help="steps of the mixed vs FP64 comparison reported under 'accuracy' (0: skip)")
     ap.add_argument("--workload", default="cylinder_64x64x256_L1")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nvtx", action="store_true",

@@ -104,7 +104,10 @@ typedef struct {
  *                       and preconditioners inside FP64 defect correction; FP64
  *                       residuals, inner products and IB force solve
  *   rtol_*              relative residual tolerances of the momentum, Poisson,
- *                       velocity-correction and force solves (0 = defaults)
+ *                       velocity-correction and force solves, relative to
+ *                       max(norm of b, norm of the initial residual); 0 selects
+ *                       the defaults: 1e-13 on the FP64 path, 1e-10 on the
+ *                       mixed path (its FP64 outer loops and force solve)
  *   max_iter            iteration cap per Krylov solve (0 = default)
  *   profile             1: run each step eagerly (host-polled loops instead of
  *                       the captured step graph) and record CUDA events

@@ -59,10 +59,10 @@ struct Tols {
 Tols tolerances(const ib_grid_desc& d) {
   const bool mixed = d.precision == IB_MIXED;
   Tols t;
-  t.mom = d.rtol_mom > 0 ? d.rtol_mom : (mixed ? 1e-12 : 1e-13);
-  t.p = d.rtol_p > 0 ? d.rtol_p : (mixed ? 1e-12 : 1e-13);
-  t.corr = d.rtol_corr > 0 ? d.rtol_corr : (mixed ? 1e-12 : 1e-13);
-  t.ib = d.rtol_ib > 0 ? d.rtol_ib : 1e-13;
+  t.mom = d.rtol_mom > 0 ? d.rtol_mom : (mixed ? 1e-10 : 1e-13);
+  t.p = d.rtol_p > 0 ? d.rtol_p : (mixed ? 1e-10 : 1e-13);
+  t.corr = d.rtol_corr > 0 ? d.rtol_corr : (mixed ? 1e-10 : 1e-13);
+  t.ib = d.rtol_ib > 0 ? d.rtol_ib : (mixed ? 1e-10 : 1e-13);
   t.inner = 1e-5;
   t.inner_p = 1e-3;
   t.max_iter = d.max_iter > 0 ? d.max_iter : 20000;
@@ -445,6 +445,13 @@ ib_status engine_build(Engine& E) {
   }
   cseg[n] = int32_t(cbrick.size());
   cbrick.push_back(int32_t(E.nbricks));
+  std::vector<int32_t> scbrick, scseg(n + 1);
+  for (int i = 0; i < n; ++i) {
+    scseg[i] = int32_t(scbrick.size());
+    for (int32_t b = bseg[i]; b < bseg[i + 1]; b += 8) scbrick.push_back(b);
+  }
+  scseg[n] = int32_t(scbrick.size());
+  scbrick.push_back(int32_t(E.nbricks));
   E.n_inlet = int64_t(ins.size());
   E.n_valid = 0;
   for (uint16_t m : meta)
@@ -466,9 +473,11 @@ ib_status engine_build(Engine& E) {
   TRY(upload(E, &d_bnbr, bnbr));
   TRY(upload(E, &d_meta, meta));
   TRY(upload(E, &d_hl, hl));
-  int32_t *d_cbrick, *d_cseg;
+  int32_t *d_cbrick, *d_cseg, *d_scbrick, *d_scseg;
   TRY(upload(E, &d_cbrick, cbrick));
   TRY(upload(E, &d_cseg, cseg));
+  TRY(upload(E, &d_scbrick, scbrick));
+  TRY(upload(E, &d_scseg, scseg));
   TRY(upload(E, &d_sf64, sf));
   TRY(upload(E, &d_sf32, sf32));
   TRY(upload(E, &E.pdt, pdt));
@@ -485,6 +494,9 @@ ib_status engine_build(Engine& E) {
   g.nchunks = int32_t(cbrick.size()) - 1;
   g.cbrick = d_cbrick;
   g.cseg = d_cseg;
+  g.nschunks = int32_t(scbrick.size()) - 1;
+  g.scbrick = d_scbrick;
+  g.scseg = d_scseg;
   g.hl = d_hl; g.pdt = E.pdt; g.pnu = d_pnu; g.sf64 = d_sf64; g.sf32 = d_sf32;
   g.n_if = int32_t(ifc.size());
   g.if_c = d_ifc; g.if_f = d_iff; g.if_off = d_ifo; g.if_kid = d_ifk; g.if_of_slot = d_ifos;

@@ -32,14 +32,10 @@ std::atomic<long long> g_launches{0};
 __constant__ int8_t c_sten[15][3];
 __constant__ int16_t c_toff[15];               // tile offset of each stencil slot
 __constant__ int8_t c_slot_of_rel[27];
-__constant__ uint8_t c_massw[256][15];         // sum over tets of (1 + delta_nb), units V/120
-__constant__ int8_t c_stiffw[256][7][3];       // sum over tets of g_n,a g_b,a, units (V/6)/h_a^2
-__constant__ int8_t c_gradw[256][15][3];       // sum over tets of g_b,a (gradient of phi_b), units (V/24)/h_a
 
 static const int8_t h_sten[15][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
                                      {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {0, 1, 1},
                                      {0, -1, -1}, {1, 0, 1}, {-1, 0, -1}, {1, 1, 1},  {-1, -1, -1}};
-static const int8_t h_kperm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 
 cudaError_t fe_init_tables() {
   int8_t slot_of_rel[27];
@@ -49,62 +45,31 @@ cudaError_t fe_init_tables() {
     slot_of_rel[(h_sten[k][2] + 1) * 9 + (h_sten[k][1] + 1) * 3 + (h_sten[k][0] + 1)] = int8_t(k);
     toff[k] = int16_t((h_sten[k][2] * TILE + h_sten[k][1]) * TILE + h_sten[k][0]);
   }
-  // Per incident-cell mask: which Kuhn tetrahedra contain the node, and how
-  // they couple it to its neighbours.  Tet (a1,a2,a3) of a cell has vertices
-  // v0 = 0, v1 = e_a1, v2 = e_a1 + e_a2, v3 = (1,1,1) and barycentric gradients
-  // -e_a1/h, e_a1/h - e_a2/h, e_a2/h - e_a3/h, e_a3/h (integers g below).
-  static uint8_t massw[256][15];
-  static int8_t stiffw[256][7][3];
-  static int8_t gradw[256][15][3];
-  std::memset(massw, 0, sizeof(massw));
-  std::memset(stiffw, 0, sizeof(stiffw));
-  std::memset(gradw, 0, sizeof(gradw));
-  for (int mask = 0; mask < 256; ++mask) {
-    int stf[15][3] = {};
-    for (int c = 0; c < 8; ++c) {
-      if (!(mask >> c & 1)) continue;
-      int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
-      int qb = (1 - dx) | ((1 - dy) << 1) | ((1 - dz) << 2);
-      for (int p = 0; p < 6; ++p) {
-        int a1 = h_kperm[p][0], a2 = h_kperm[p][1], a3 = h_kperm[p][2];
-        int vb[4] = {0, 1 << a1, (1 << a1) | (1 << a2), 7};
-        int gr[4][3] = {};
-        gr[0][a1] = -1;
-        gr[1][a1] = 1; gr[1][a2] = -1;
-        gr[2][a2] = 1; gr[2][a3] = -1;
-        gr[3][a3] = 1;
-        int kn = -1;
-        for (int k = 0; k < 4; ++k)
-          if (vb[k] == qb) kn = k;
-        if (kn < 0) continue;
-        for (int k = 0; k < 4; ++k) {
-          int rx = dx - 1 + (vb[k] & 1), ry = dy - 1 + ((vb[k] >> 1) & 1), rz = dz - 1 + ((vb[k] >> 2) & 1);
-          int sl = slot_of_rel[(rz + 1) * 9 + (ry + 1) * 3 + (rx + 1)];
-          if (sl < 0) return cudaErrorInvalidValue;
-          massw[mask][sl] += uint8_t(k == kn ? 2 : 1);
-          for (int a = 0; a < 3; ++a) {
-            stf[sl][a] += gr[kn][a] * gr[k][a];
-            gradw[mask][sl][a] = int8_t(gradw[mask][sl][a] + gr[k][a]);
-          }
-        }
-      }
-    }
-    for (int sl = 7; sl < 15; ++sl)
-      for (int a = 0; a < 3; ++a)
-        if (stf[sl][a] != 0) return cudaErrorInvalidValue;   // stiffness is 7-point
-    for (int sl = 0; sl < 7; ++sl)
-      for (int a = 0; a < 3; ++a) stiffw[mask][sl][a] = int8_t(stf[sl][a]);
-  }
   cudaError_t e;
   if ((e = cudaMemcpyToSymbol(c_sten, h_sten, sizeof(h_sten))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_toff, toff, sizeof(toff))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_slot_of_rel, slot_of_rel, sizeof(slot_of_rel))) != cudaSuccess) return e;
-  if ((e = cudaMemcpyToSymbol(c_massw, massw, sizeof(massw))) != cudaSuccess) return e;
-  if ((e = cudaMemcpyToSymbol(c_stiffw, stiffw, sizeof(stiffw))) != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_gradw, gradw, sizeof(gradw));
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- helpers
+// Gradient couplings of a node, gw[k][a] = sum over its active incident cells of
+// grad_cell_weight (kuhn_weights.hpp); the arguments are compile-time after
+// unrolling, so the per-cell weights fold into constants.
+__device__ __forceinline__ void grad_weights(int mask, int (&gw)[15][3]) {
+#pragma unroll
+  for (int k = 0; k < 15; ++k)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gw[k][a] = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (!((mask >> c) & 1)) continue;
+#pragma unroll
+    for (int k = 0; k < 15; ++k)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) gw[k][a] += grad_cell_weight(c, k, a);
+  }
+}
 __device__ __forceinline__ void spacing(const DevGrid& g, int b, double (&h)[3]) {
   const int inst = g.binst[b], lev = g.blev[b];
   const double* p = g.hl + (inst * 4 + lev) * 3;
@@ -114,15 +79,6 @@ __device__ __forceinline__ void spacing(const DevGrid& g, int b, double (&h)[3])
 }
 __device__ __forceinline__ bool is_dof(uint16_t m, uint16_t dmask) {
   return (m & D_VALID) && !(m & (D_HANG | D_DUP | dmask));
-}
-
-// row coefficient k of the mask-tabulated operators, in the kernel's precision
-// (F: the instance/level stencil factors)
-template <typename T, int OP>
-__device__ __forceinline__ T table_coef(int mask, int k, const T* F) {
-  if (OP == OP_POISSON)
-    return T(c_stiffw[mask][k][0]) * F[0] + T(c_stiffw[mask][k][1]) * F[1] + T(c_stiffw[mask][k][2]) * F[2];
-  return T(c_massw[mask][k]) * F[3];
 }
 
 enum Post : int { POST_NONE = 0, POST_CG_ALPHA = 1 };
@@ -171,8 +127,12 @@ __global__ void __launch_bounds__(512) k_diag(DevGrid g, const T* __restrict__ c
   T d = T(0);
   if (m & D_VALID) {
     const T* F = stencil_factors<T>(g, blockIdx.x);
-    if (OP == OP_POISSON) d = table_coef<T, OP_POISSON>(m & 0xFF, 0, F);
-    else if (OP == OP_MASS) d = table_coef<T, OP_MASS>(m & 0xFF, 0, F);
+    const int mask = m & 0xFF;
+    if (OP == OP_POISSON)
+      d = T(stiff_edge_count(mask, 0, 1) + stiff_edge_count(mask, 0, -1)) * F[0] +
+          T(stiff_edge_count(mask, 1, 1) + stiff_edge_count(mask, 1, -1)) * F[1] +
+          T(stiff_edge_count(mask, 2, 1) + stiff_edge_count(mask, 2, -1)) * F[2];
+    else if (OP == OP_MASS) d = T(mass_weight(mask, 0)) * F[3];
     else d = coef[s];
   }
   diag[s] = d;
@@ -209,15 +169,17 @@ __global__ void __launch_bounds__(512) k_rhs_mass_grad(DevGrid g, const double* 
     const double* F = stencil_factors<double>(g, b);
     const double dt = g.pdt[g.binst[b]];
     double gp[3] = {0, 0, 0};
+    int gw[15][3];
+    grad_weights(mask, gw);
 #pragma unroll
     for (int k = 0; k < 15; ++k) {
       const int j = ti + c_toff[k];
-      const double mw = double(c_massw[mask][k]);
+      const double mw = double(mass_weight(mask, k));
       const double pk = tile[3 * TILE3 + j];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         o[a] += mw * tile[a * TILE3 + j];
-        gp[a] += double(c_gradw[mask][k][a]) * pk;
+        gp[a] += double(gw[k][a]) * pk;
       }
     }
 #pragma unroll
@@ -242,11 +204,13 @@ __global__ void __launch_bounds__(512) k_rhs_div(DevGrid g, const double* __rest
     const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
     const double* F = stencil_factors<double>(g, b);
     double d[3] = {0, 0, 0};
+    int gw[15][3];
+    grad_weights(mask, gw);
 #pragma unroll
     for (int k = 0; k < 15; ++k) {
       const int j = ti + c_toff[k];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) d[a] += double(c_gradw[mask][k][a]) * tile[a * TILE3 + j];
+      for (int a = 0; a < 3; ++a) d[a] += double(gw[k][a]) * tile[a * TILE3 + j];
     }
     o = F[4] * d[0] + F[5] * d[1] + F[6] * d[2];
   }
@@ -270,12 +234,24 @@ __host__ __device__ constexpr int slot_of_rel(int rx, int ry, int rz) {
 // entries C_nb = sum_T (|T|/20) (S_T + u_n) . grad phi_b (S_T = sum of u over
 // the tetrahedron's vertices) are accumulated tetrahedron by tetrahedron with
 // every index known at compile time.
+template <typename CT>
 __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __restrict__ u, double* __restrict__ coef,
                                                   float* __restrict__ coef32) {
   KCOUNT();
-  __shared__ double tile[3 * TILE3];
+  __shared__ CT tile[3 * TILE3];
   const int b = blockIdx.x;
-  load_tile<double>(tile, u, g.nslots, 3, g.bnbr + 27 * b);
+  {
+    const int32_t* nb27 = g.bnbr + 27 * b;
+    for (int t = threadIdx.x; t < TILE3; t += blockDim.x) {
+      const int hx = t % TILE, hy = (t / TILE) % TILE, hz = t / (TILE * TILE);
+      const int lx = hx - 1, ly = hy - 1, lz = hz - 1;
+      const int ox = lx < 0 ? -1 : (lx > 7 ? 1 : 0), oy = ly < 0 ? -1 : (ly > 7 ? 1 : 0);
+      const int oz = lz < 0 ? -1 : (lz > 7 ? 1 : 0);
+      const int nb = nb27[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+      const int64_t sl = (int64_t)nb * DBV + (((lz & 7) * DBS + (ly & 7)) * DBS + (lx & 7));
+      for (int c = 0; c < 3; ++c) tile[c * TILE3 + t] = nb >= 0 ? CT(u[c * g.nslots + sl]) : CT(0);
+    }
+  }
   __syncthreads();
   const int t = threadIdx.x;
   const int64_t s = (int64_t)b * DBV + t;
@@ -291,16 +267,28 @@ __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __res
     const double dt = g.pdt[inst], nu = g.pnu[inst];
     double h[3];
     spacing(g, b, h);
-    const double ih[3] = {1.0 / h[0], 1.0 / h[1], 1.0 / h[2]};
     const double dnu = dt * nu;
+    // M + dt nu K from the incident-cell mask (exact integer weights)
 #pragma unroll
-    for (int k = 0; k < 15; ++k) cf[k] = double(c_massw[mask][k]) * F[3];
+    for (int k = 0; k < 15; ++k) cf[k] = double(mass_weight(mask, k)) * F[3];
+    double diagK = 0.0;
 #pragma unroll
-    for (int k = 0; k < 7; ++k)
-      cf[k] += dnu * (double(c_stiffw[mask][k][0]) * F[0] + double(c_stiffw[mask][k][1]) * F[1] +
-                      double(c_stiffw[mask][k][2]) * F[2]);
-    const double wv = dt * F[3];   // dt |T| / 20
-    const double un[3] = {tile[ti], tile[TILE3 + ti], tile[2 * TILE3 + ti]};
+    for (int a = 0; a < 3; ++a) {
+      const double kp = dnu * double(stiff_edge_count(mask, a, 1)) * F[a];
+      const double km = dnu * double(stiff_edge_count(mask, a, -1)) * F[a];
+      cf[1 + 2 * a] -= kp;
+      cf[2 + 2 * a] -= km;
+      diagK += kp + km;
+    }
+    cf[0] += diagK;
+    // dt C(u^n): (u_h . grad phi_b, phi_a) on every tetrahedron holding the
+    // node, accumulated in CT (FP32 on the mixed path, FP64 on the FP64 path)
+    CT cc[15];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) cc[k] = CT(0);
+    const CT wv = CT(dt * F[3]);   // dt |T| / 20
+    const CT ih[3] = {CT(1.0 / h[0]), CT(1.0 / h[1]), CT(1.0 / h[2])};
+    const CT un[3] = {tile[ti], tile[TILE3 + ti], tile[2 * TILE3 + ti]};
     constexpr int KP[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -319,20 +307,22 @@ __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __res
           off[k] = (rz * TILE + ry) * TILE + rx;
           sl[k] = slot_of_rel(rx, ry, rz);
         }
-        double w[3];
+        CT w[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          const double* ta = tile + a * TILE3 + ti;
+          const CT* ta = tile + a * TILE3 + ti;
           w[a] = wv * (ta[off[0]] + ta[off[1]] + ta[off[2]] + ta[off[3]] + un[a]);
         }
         // grad phi_0 = -e_a1/h, grad phi_1 = e_a1/h - e_a2/h, grad phi_2 = e_a2/h - e_a3/h, grad phi_3 = e_a3/h
-        const double g1 = w[a1] * ih[a1], g2 = w[a2] * ih[a2], g3 = w[a3] * ih[a3];
-        cf[sl[0]] -= g1;
-        cf[sl[1]] += g1 - g2;
-        cf[sl[2]] += g2 - g3;
-        cf[sl[3]] += g3;
+        const CT g1 = w[a1] * ih[a1], g2 = w[a2] * ih[a2], g3 = w[a3] * ih[a3];
+        cc[sl[0]] -= g1;
+        cc[sl[1]] += g1 - g2;
+        cc[sl[2]] += g2 - g3;
+        cc[sl[3]] += g3;
       }
     }
+#pragma unroll
+    for (int k = 0; k < 15; ++k) cf[k] += double(cc[k]);
   }
 #pragma unroll
   for (int k = 0; k < 15; ++k) {
@@ -496,17 +486,32 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
       fli = (gz * DBS + gy) * DBS + gx;
       fti = tile_index(hx, hy, hz);
     }
+    // software pipeline: the next brick's value, halo value and metadata are
+    // loaded into registers while the current brick is computed
+    auto own = [&](int bb) -> T {
+      const int64_t s = (int64_t)bb * DBV + t;
+      return CG ? T(z[s] + beta * pold[s]) : z[s];
+    };
+    auto halo = [&](int bb) -> T {
+      if (t >= 384) return T(0);
+      const int nb = g.bnbr[27 * bb + fnb];
+      const int64_t fs = (int64_t)nb * DBV + fli;
+      return nb >= 0 ? (CG ? T(z[fs] + beta * pold[fs]) : z[fs]) : T(0);
+    };
+    T pn = own(b0), hn = halo(b0);
+    uint16_t mn = g.meta[(int64_t)b0 * DBV + t];
     for (int bb = b0; bb < b1; ++bb) {
       const int64_t s = (int64_t)bb * DBV + t;
-      const T pv = CG ? T(z[s] + beta * pold[s]) : z[s];
+      const T pv = pn;
+      const uint16_t m = mn;
       tile[ti] = pv;
-      if (t < 384) {
-        const int nb = g.bnbr[27 * bb + fnb];
-        const int64_t fs = (int64_t)nb * DBV + fli;
-        tile[fti] = nb >= 0 ? (CG ? T(z[fs] + beta * pold[fs]) : z[fs]) : T(0);
-      }
-      const uint16_t m = g.meta[s];
+      if (t < 384) tile[fti] = hn;
       __syncthreads();
+      if (bb + 1 < b1) {
+        pn = own(bb + 1);
+        hn = halo(bb + 1);
+        mn = g.meta[s + DBV];
+      }
       T out = T(0);
       if (m & D_VALID) {
         const int mask = m & 0xFF;
@@ -612,12 +617,15 @@ __global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict_
     const int ti = tile_index(lx, ly, lz);
     int hnb = 13, hli = 0, hti = 0;
     if (t < HALO15) halo15(t, hnb, hli, hti);
-    for (int bb = b0; bb < b1; ++bb) {
+    // software pipeline over the chunk: the next brick's values, halo values
+    // and metadata are loaded into registers while the current one is computed
+    T vo[NC], vh[NC];
+    auto fetch = [&](int bb) {
       const int64_t s = (int64_t)bb * DBV + t;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int64_t i = (int64_t)c * g.nslots + s;
-        tile[c * TILE3 + ti] = FUSEP ? T(zf[i] + beta[c] * x[i]) : x[i];
+        vo[c] = FUSEP ? T(zf[i] + beta[c] * x[i]) : x[i];
       }
       if (t < HALO15) {
         const int nb = g.bnbr[27 * bb + hnb];
@@ -625,11 +633,25 @@ __global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict_
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const int64_t i = (int64_t)c * g.nslots + hs;
-          tile[c * TILE3 + hti] = nb >= 0 ? (FUSEP ? T(zf[i] + beta[c] * x[i]) : x[i]) : T(0);
+          vh[c] = nb >= 0 ? (FUSEP ? T(zf[i] + beta[c] * x[i]) : x[i]) : T(0);
         }
       }
-      const uint16_t m = g.meta[s];
+    };
+    fetch(b0);
+    uint16_t mn = g.meta[(int64_t)b0 * DBV + t];
+    for (int bb = b0; bb < b1; ++bb) {
+      const int64_t s = (int64_t)bb * DBV + t;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        tile[c * TILE3 + ti] = vo[c];
+        if (t < HALO15) tile[c * TILE3 + hti] = vh[c];
+      }
+      const uint16_t m = mn;
       __syncthreads();
+      if (bb + 1 < b1) {
+        fetch(bb + 1);
+        mn = g.meta[s + DBV];
+      }
       T out[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) out[c] = T(0);
@@ -764,7 +786,9 @@ void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st)
   IBG_LAUNCH(k_rhs_div, g.nbricks, DBV, 0, st, g, u, out);
 }
 void fe_momentum_coef(const DevGrid& g, const double* u, double* coef64, float* coef32, cudaStream_t st) {
-  IBG_LAUNCH(k_mom_coef, g.nbricks, DBV, 0, st, g, u, coef64, coef32);
+  // the mixed path (coef32 given) evaluates the convection part in FP32
+  if (coef32) IBG_LAUNCH(k_mom_coef<float>, g.nbricks, DBV, 0, st, g, u, coef64, coef32);
+  else IBG_LAUNCH(k_mom_coef<double>, g.nbricks, DBV, 0, st, g, u, coef64, coef32);
 }
 
 template <typename T>

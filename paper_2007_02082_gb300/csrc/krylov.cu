@@ -162,12 +162,20 @@ __global__ void __launch_bounds__(512) k_cg_update_vec(DevGrid g, T* __restrict_
   using V = typename Vec16<T>::type;
   using MT = typename Vec16<T>::mt;
   constexpr int W = Vec16<T>::W;
-  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const KState* ki = ks + g.binst[b0] * NC;
+  bool act[NC];
+  T alc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    act[c] = !ki[c].done;
+    alc[c] = k_alpha<T>(ki[c]);
+  }
   T tv[2 * NC];
 #pragma unroll
   for (int c = 0; c < 2 * NC; ++c) tv[c] = T(0);
   const int64_t s1 = (int64_t)b1 * DBV;
+#pragma unroll 2
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
     const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
     const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
@@ -175,8 +183,8 @@ __global__ void __launch_bounds__(512) k_cg_update_vec(DevGrid g, T* __restrict_
     const T* de = reinterpret_cast<const T*>(&dv);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      if (ki[c].done) continue;
-      const T a = k_alpha<T>(ki[c]);
+      if (!act[c]) continue;
+      const T a = alc[c];
       const int64_t i = (int64_t)c * g.nslots + s;
       const T* qc = q + (int64_t)c * g.nslots;
       V xv = *reinterpret_cast<const V*>(x + i);
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(512) k_cg_update_vec(DevGrid g, T* __restrict_
     }
   }
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
-  if (!grid_sum_last<T, 2 * NC>(tv, partials, counter, g.cseg, g.ninst, out)) return;
+  if (!grid_sum_last<T, 2 * NC>(tv, partials, counter, g.scseg, g.ninst, out)) return;
   bool any = false;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
     for (int c = 0; c < NC; ++c) {
@@ -279,13 +287,14 @@ __global__ void __launch_bounds__(512) k_cg_update_r(DevGrid g, T* __restrict__ 
   using V = typename Vec16<T>::type;
   using MT = typename Vec16<T>::mt;
   constexpr int W = Vec16<T>::W;
-  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const KState& k = ks[g.binst[b0]];
   T tv[1] = {T(0)};
   if (!k.done) {
     const T a = k_alpha<T>(k);
     const int64_t s1 = (int64_t)b1 * DBV;
-    for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
+  #pragma unroll 2
+  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
       const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
       const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
       V xv = *reinterpret_cast<const V*>(x + s);
@@ -315,7 +324,7 @@ __global__ void __launch_bounds__(512) k_cg_update_r(DevGrid g, T* __restrict__ 
     }
   }
   double* out = partials + (int64_t)gridDim.x;
-  if (!grid_sum_last<T, 1>(tv, partials, counter, g.cseg, g.ninst, out)) return;
+  if (!grid_sum_last<T, 1>(tv, partials, counter, g.scseg, g.ninst, out)) return;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
     KState& kk = ks[i];
     if (kk.done) continue;
@@ -333,14 +342,14 @@ __global__ void __launch_bounds__(512) k_cg_rz(DevGrid g, const T* __restrict__ 
                                                uint16_t dmask, KState* ks, double* partials, unsigned* counter,
                                                Cond cond, int first) {
   KCOUNT();
-  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const KState& k = ks[g.binst[b0]];
   T tv[1] = {T(0)};
   if (!k.done)
     for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x)
       if (kdof(g.meta[s], dmask)) tv[0] += r[s] * z[s];
   double* out = partials + (int64_t)gridDim.x;
-  if (!grid_sum_last<T, 1>(tv, partials, counter, g.cseg, g.ninst, out)) return;
+  if (!grid_sum_last<T, 1>(tv, partials, counter, g.scseg, g.ninst, out)) return;
   bool any = false;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
     KState& kk = ks[i];
@@ -427,17 +436,26 @@ __global__ void __launch_bounds__(512) k_bcgv_p(DevGrid g, const T* __restrict__
   using V = typename Vec16<T>::type;
   using MT = typename Vec16<T>::mt;
   constexpr int W = Vec16<T>::W;
-  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const KState* ki = ks + g.binst[b0] * NC;
+  bool act[NC];
+  T bec[NC], omc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    act[c] = !ki[c].done;
+    bec[c] = k_beta<T>(ki[c]);
+    omc[c] = k_omega<T>(ki[c]);
+  }
   const int64_t s1 = (int64_t)b1 * DBV;
+#pragma unroll 2
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
     const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
     const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
     const V dv = *reinterpret_cast<const V*>(dinv + s);
     const T* de = reinterpret_cast<const T*>(&dv);
     for (int c = 0; c < NC; ++c) {
-      if (ki[c].done) continue;
-      const T be = k_beta<T>(ki[c]), om = k_omega<T>(ki[c]);
+      if (!act[c]) continue;
+      const T be = bec[c], om = omc[c];
       const int64_t i = (int64_t)c * g.nslots + s;
       const V rv = *reinterpret_cast<const V*>(r + i);
       const V vv = *reinterpret_cast<const V*>(v + i);
@@ -470,19 +488,23 @@ __global__ void __launch_bounds__(512) k_bcgv_dot(DevGrid g, const T* __restrict
   using V = typename Vec16<T>::type;
   using MT = typename Vec16<T>::mt;
   constexpr int W = Vec16<T>::W;
-  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const KState* ki = ks + g.binst[b0] * NC;
+  bool act[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) act[c] = !ki[c].done;
   T tw[2 * NC];
 #pragma unroll
   for (int c = 0; c < 2 * NC; ++c) tw[c] = T(0);
   // b1v is the operator output (v or t, interface sums on read); a1 is rh (mode 0) or s (mode 1)
   const int64_t s1 = (int64_t)b1 * DBV;
+#pragma unroll 2
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
     const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
     const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      if (ki[c].done) continue;
+      if (!act[c]) continue;
       const int64_t i = (int64_t)c * g.nslots + s;
       const V av = *reinterpret_cast<const V*>(a1 + i);
       const V bv = *reinterpret_cast<const V*>(b1v + i);
@@ -499,7 +521,7 @@ __global__ void __launch_bounds__(512) k_bcgv_dot(DevGrid g, const T* __restrict
     }
   }
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
-  if (!grid_sum_last<T, 2 * NC>(tw, partials, counter, g.cseg, g.ninst, out)) return;
+  if (!grid_sum_last<T, 2 * NC>(tw, partials, counter, g.scseg, g.ninst, out)) return;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
     for (int c = 0; c < NC; ++c) {
       KState& k = ks[i * NC + c];
@@ -528,17 +550,25 @@ __global__ void __launch_bounds__(512) k_bcgv_s(DevGrid g, const T* __restrict__
   using V = typename Vec16<T>::type;
   using MT = typename Vec16<T>::mt;
   constexpr int W = Vec16<T>::W;
-  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const KState* ki = ks + g.binst[b0] * NC;
+  bool act[NC];
+  T alc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    act[c] = !ki[c].done;
+    alc[c] = k_alpha<T>(ki[c]);
+  }
   const int64_t s1 = (int64_t)b1 * DBV;
+#pragma unroll 2
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
     const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
     const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
     const V dv = *reinterpret_cast<const V*>(dinv + s);
     const T* de = reinterpret_cast<const T*>(&dv);
     for (int c = 0; c < NC; ++c) {
-      if (ki[c].done) continue;
-      const T al = k_alpha<T>(ki[c]);
+      if (!act[c]) continue;
+      const T al = alc[c];
       const int64_t i = (int64_t)c * g.nslots + s;
       const V rv = *reinterpret_cast<const V*>(r + i);
       const V vv = *reinterpret_cast<const V*>(v + i);
@@ -572,19 +602,28 @@ __global__ void __launch_bounds__(512) k_bcgv_xr(DevGrid g, T* __restrict__ x, T
   using V = typename Vec16<T>::type;
   using MT = typename Vec16<T>::mt;
   constexpr int W = Vec16<T>::W;
-  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const KState* ki = ks + g.binst[b0] * NC;
+  bool act[NC];
+  T alc[NC], omc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    act[c] = !ki[c].done;
+    alc[c] = k_alpha<T>(ki[c]);
+    omc[c] = k_omega<T>(ki[c]);
+  }
   T tw[2 * NC];
 #pragma unroll
   for (int c = 0; c < 2 * NC; ++c) tw[c] = T(0);
   const int64_t s1 = (int64_t)b1 * DBV;
+#pragma unroll 2
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
     const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
     const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      if (ki[c].done) continue;
-      const T al = k_alpha<T>(ki[c]), om = k_omega<T>(ki[c]);
+      if (!act[c]) continue;
+      const T al = alc[c], om = omc[c];
       const int64_t i = (int64_t)c * g.nslots + s;
       V xv = *reinterpret_cast<const V*>(x + i);
       const V pv = *reinterpret_cast<const V*>(ph + i);
@@ -617,7 +656,7 @@ __global__ void __launch_bounds__(512) k_bcgv_xr(DevGrid g, T* __restrict__ x, T
     }
   }
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
-  if (!grid_sum_last<T, 2 * NC>(tw, partials, counter, g.cseg, g.ninst, out)) return;
+  if (!grid_sum_last<T, 2 * NC>(tw, partials, counter, g.scseg, g.ninst, out)) return;
   bool any = false;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
     for (int c = 0; c < NC; ++c) {
@@ -651,7 +690,7 @@ __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double*
                                                         double* partials, unsigned* counter, Cond cloop,
                                                         Cond cbranch) {
   KCOUNT();
-  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const OState& oi = os[g.binst[b0]];
   const bool first = oi.iter == 0;
   double w[2 * NC];
@@ -674,7 +713,7 @@ __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double*
       }
     }
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
-  if (!grid_sum_last<double, 2 * NC>(w, partials, counter, g.cseg, g.ninst, out)) return;
+  if (!grid_sum_last<double, 2 * NC>(w, partials, counter, g.scseg, g.ninst, out)) return;
   bool any = false;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
     OState& o = os[i];
@@ -765,7 +804,7 @@ static cudaError_t cg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b
     fe_apply_cg<T>(g, A, NC, w.z, pold, pnew, w.q, a.ks, rb, s);
     pend(a.prof, s);
     pbegin(a.prof, a.pbase + 1, s);
-    IBG_LAUNCH((k_cg_update_vec<T, NC>), g.nchunks, DBV, 0, s, g, x, w.r, w.z, pnew, w.q, A.dinv, A.dmask, a.ks,
+    IBG_LAUNCH((k_cg_update_vec<T, NC>), g.nschunks, DBV, 0, s, g, x, w.r, w.z, pnew, w.q, A.dinv, A.dmask, a.ks,
                rb.partials, rb.counter, c);
     pend(a.prof, s);
     fe_expand2<T>(g, NC, w.z, (T*)nullptr, s);
@@ -800,17 +839,17 @@ static cudaError_t cg_mg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const M
   IBG_LAUNCH(k_cg_start_r<T>, g.nbricks, DBV, 0, st, g, b, w.q, w.r, A.dmask, a.ks, rb.partials, rb.counter,
              skip_os);
   mg_vcycle<T>(g, mg, w.r, w.z, zs, w.q, A.dinv, A.dmask, a.ks, st, a.prof, 9);
-  IBG_LAUNCH(k_cg_rz<T>, g.nchunks, DBV, 0, st, g, w.r, w.z, A.dmask, a.ks, rb.partials, rb.counter, cond, 1);
+  IBG_LAUNCH(k_cg_rz<T>, g.nschunks, DBV, 0, st, g, w.r, w.z, A.dmask, a.ks, rb.partials, rb.counter, cond, 1);
   auto iter = [&](cudaStream_t s, const Cond& c, T* pold, T* pnew) {
     pbegin(a.prof, a.pbase + 0, s);
     fe_apply_cg<T>(g, A, 1, w.z, pold, pnew, w.q, a.ks, rb, s);
     pend(a.prof, s);
     pbegin(a.prof, a.pbase + 1, s);
-    IBG_LAUNCH(k_cg_update_r<T>, g.nchunks, DBV, 0, s, g, x, w.r, pnew, w.q, A.dmask, a.ks, rb.partials,
+    IBG_LAUNCH(k_cg_update_r<T>, g.nschunks, DBV, 0, s, g, x, w.r, pnew, w.q, A.dmask, a.ks, rb.partials,
                rb.counter);
     pend(a.prof, s);
     mg_vcycle<T>(g, mg, w.r, w.z, zs, w.q, A.dinv, A.dmask, a.ks, s, a.prof, 9);
-    IBG_LAUNCH(k_cg_rz<T>, g.nchunks, DBV, 0, s, g, w.r, w.z, A.dmask, a.ks, rb.partials, rb.counter, c, 0);
+    IBG_LAUNCH(k_cg_rz<T>, g.nschunks, DBV, 0, s, g, w.r, w.z, A.dmask, a.ks, rb.partials, rb.counter, c, 0);
   };
   return run_loop(cc, st, cond, a.ks, a.ks_host, g.ninst, a.max_iter, 1, 4, [&](cudaStream_t s, const Cond& c) {
     iter(s, c, w.pa, w.pb);
@@ -838,22 +877,22 @@ static cudaError_t bcg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* 
   // interface sums on read (the start kernel set v = 0)
   return run_loop(cc, st, cond, a.ks, a.ks_host, g.ninst * NC, a.max_iter, 1, 8, [&](cudaStream_t s, const Cond& c) {
     pbegin(a.prof, a.pbase + 2, s);
-    IBG_LAUNCH((k_bcgv_p<T, NC>), g.nchunks, DBV, 0, s, g, w.r, w.p, w.v, w.ph, A.dinv, A.dmask, a.ks);
+    IBG_LAUNCH((k_bcgv_p<T, NC>), g.nschunks, DBV, 0, s, g, w.r, w.p, w.v, w.ph, A.dinv, A.dmask, a.ks);
     pend(a.prof, s);
     fe_expand2<T>(g, NC, w.ph, (T*)nullptr, s);
     pbegin(a.prof, a.pbase + 0, s);
     fe_apply_local<T>(g, A, NC, w.ph, w.v, s);
     pend(a.prof, s);
-    IBG_LAUNCH((k_bcgv_dot<T, NC>), g.nchunks, DBV, 0, s, g, w.rh, w.v, A.dmask, 0, a.ks, rb.partials, rb.counter);
-    IBG_LAUNCH((k_bcgv_s<T, NC>), g.nchunks, DBV, 0, s, g, w.r, w.v, w.sv, w.sh, A.dinv, A.dmask, a.ks);
+    IBG_LAUNCH((k_bcgv_dot<T, NC>), g.nschunks, DBV, 0, s, g, w.rh, w.v, A.dmask, 0, a.ks, rb.partials, rb.counter);
+    IBG_LAUNCH((k_bcgv_s<T, NC>), g.nschunks, DBV, 0, s, g, w.r, w.v, w.sv, w.sh, A.dinv, A.dmask, a.ks);
     fe_expand2<T>(g, NC, w.sh, (T*)nullptr, s);
     pbegin(a.prof, a.pbase + 0, s);
     fe_apply_local<T>(g, A, NC, w.sh, w.tv, s);
     pend(a.prof, s);
-    IBG_LAUNCH((k_bcgv_dot<T, NC>), g.nchunks, DBV, 0, s, g, w.sv, w.tv, A.dmask, 1, a.ks, rb.partials,
+    IBG_LAUNCH((k_bcgv_dot<T, NC>), g.nschunks, DBV, 0, s, g, w.sv, w.tv, A.dmask, 1, a.ks, rb.partials,
                rb.counter);
     pbegin(a.prof, a.pbase + 1, s);
-    IBG_LAUNCH((k_bcgv_xr<T, NC>), g.nchunks, DBV, 0, s, g, x, w.r, w.rh, w.ph, w.sh, w.sv, w.tv, A.dmask, a.ks,
+    IBG_LAUNCH((k_bcgv_xr<T, NC>), g.nschunks, DBV, 0, s, g, x, w.r, w.rh, w.ph, w.sh, w.sv, w.tv, A.dmask, a.ks,
                rb.partials, rb.counter, c);
     pend(a.prof, s);
   });
@@ -889,10 +928,10 @@ cudaError_t solve_enqueue(const SolveArgs& a, cudaStream_t st, CaptureCtx* cc) {
   auto residual = [&](cudaStream_t s, const Cond& cl, const Cond& cb) {
     fe_apply<double>(g, A64, a.nc, a.x, a.y64, s);
     if (a.nc == 1)
-      IBG_LAUNCH(k_residual_outer<1>, g.nchunks, DBV, 0, s, g, a.b, a.y64, a.r32, a.e32, a.dmask, a.os, a.rb.partials,
+      IBG_LAUNCH(k_residual_outer<1>, g.nschunks, DBV, 0, s, g, a.b, a.y64, a.r32, a.e32, a.dmask, a.os, a.rb.partials,
                  a.rb.counter, cl, cb);
     else
-      IBG_LAUNCH(k_residual_outer<3>, g.nchunks, DBV, 0, s, g, a.b, a.y64, a.r32, a.e32, a.dmask, a.os, a.rb.partials,
+      IBG_LAUNCH(k_residual_outer<3>, g.nschunks, DBV, 0, s, g, a.b, a.y64, a.r32, a.e32, a.dmask, a.os, a.rb.partials,
                  a.rb.counter, cl, cb);
   };
   auto correction = [&](cudaStream_t s) {

@@ -43,6 +43,20 @@ __device__ __forceinline__ T q_sum(const DevGrid& g, const T* __restrict__ q, in
   return v;
 }
 
+// First two Jacobi steps from zero in one pass: x1 = w D^-1 b is pointwise, so
+// x2 = x1 + w D^-1 (b - A x1) takes the neighbours' x1 from their b and D^-1.
+template <typename T>
+__device__ __forceinline__ T level_jac2(const MGLevelDev<T>& L, T omega, int64_t j) {
+  const T x1 = omega * L.dinv[j] * L.b[j];
+  T ax = L.diag[j] * x1;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const int nb = L.nbr[6 * j + d];
+    if (nb >= 0) ax += L.offd[6 * j + d] * (omega * L.dinv[nb] * L.b[nb]);
+  }
+  return x1 + omega * L.dinv[j] * (L.b[j] - ax);
+}
+
 template <typename T>
 __device__ __forceinline__ T level_ax(const MGLevelDev<T>& L, const T* __restrict__ x, int64_t j) {
   T v = L.diag[j] * x[j];
@@ -62,7 +76,7 @@ __global__ void __launch_bounds__(512) k_mg_c_jac0(DevGrid g, const T* __restric
                                                    const T* __restrict__ dinv, uint16_t dmask,
                                                    const uint8_t* __restrict__ on, T omega, const KState* ks) {
   KCOUNT();
-  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const int inst = g.binst[b0];
   if (ks[inst].done) return;
   const T w = on[inst] ? omega : T(1);
@@ -77,7 +91,7 @@ __global__ void __launch_bounds__(512) k_mg_c_smooth(DevGrid g, const T* __restr
                                                      const T* __restrict__ dinv, uint16_t dmask,
                                                      const uint8_t* __restrict__ on, T omega, const KState* ks) {
   KCOUNT();
-  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const int inst = g.binst[b0];
   if (ks[inst].done || !on[inst]) return;
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x) {
@@ -92,7 +106,7 @@ __global__ void __launch_bounds__(512) k_mg_c_prolong(DevGrid g, MGLevelDev<T> L
                                                       T* __restrict__ zout, uint16_t dmask,
                                                       const uint8_t* __restrict__ on, const KState* ks) {
   KCOUNT();
-  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const int inst = g.binst[b0];
   if (ks[inst].done || !on[inst]) return;
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x) {
@@ -137,6 +151,15 @@ __global__ void k_mg_l_jac0(MGLevelDev<T> L, int k, T omega, const uint8_t* on, 
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= L.n || !level_node_on(L, j, k, on, small, ks)) return;
   L.xa[j] = omega * L.dinv[j] * L.b[j];
+}
+
+template <typename T>
+__global__ void k_mg_l_jac2(MGLevelDev<T> L, int k, T omega, const uint8_t* on, const int32_t* small,
+                            const KState* ks) {
+  KCOUNT();
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= L.n || !level_node_on(L, j, k, on, small, ks)) return;
+  L.xb[j] = level_jac2(L, omega, j);
 }
 
 template <typename T>
@@ -194,8 +217,10 @@ struct SmallArgs {
   int nu;
 };
 
+constexpr int SMALL_THREADS = 1024;
+
 template <typename T>
-__global__ void __launch_bounds__(512) k_mg_small(SmallArgs<T> a, const KState* ks) {
+__global__ void __launch_bounds__(SMALL_THREADS) k_mg_small(SmallArgs<T> a, const KState* ks) {
   KCOUNT();
   const int i = blockIdx.x;
   if (!a.on[i] || ks[i].done) return;
@@ -205,11 +230,19 @@ __global__ void __launch_bounds__(512) k_mg_small(SmallArgs<T> a, const KState* 
   for (int k = k0; k < K; ++k) {
     const MGLevelDev<T>& L = a.lev[k];
     const int j0 = L.noff[i], j1 = L.noff[i + 1];
-    for (int j = j0 + t; j < j1; j += nt) L.xa[j] = a.omega * L.dinv[j] * L.b[j];
-    __syncthreads();
     T* cur = L.xa;
     T* oth = L.xb;
-    for (int s = 1; s < a.nu; ++s) {
+    int s0 = 1;
+    if (a.nu >= 2) {   // the first two steps in one pass, result in xb
+      for (int j = j0 + t; j < j1; j += nt) L.xb[j] = level_jac2(L, a.omega, j);
+      cur = L.xb;
+      oth = L.xa;
+      s0 = 2;
+    } else {
+      for (int j = j0 + t; j < j1; j += nt) L.xa[j] = a.omega * L.dinv[j] * L.b[j];
+    }
+    __syncthreads();
+    for (int s = s0; s < a.nu; ++s) {
       for (int j = j0 + t; j < j1; j += nt) oth[j] = cur[j] + a.omega * L.dinv[j] * (L.b[j] - level_ax(L, cur, j));
       __syncthreads();
       T* tmp = cur; cur = oth; oth = tmp;
@@ -277,11 +310,11 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
   auto apply = [&](const T* x) { timed(0, [&] { fe_poisson_apply<T>(g, x, q, dmask, ksm, mg.on, st); }); };
   auto smooth = [&](const T* zin, T* zout) {
     timed(1, [&] {
-      IBG_LAUNCH(k_mg_c_smooth<T>, g.nchunks, DBV, 0, st, g, zin, zout, r, q, dinv, dmask, mg.on, w, ks);
+      IBG_LAUNCH(k_mg_c_smooth<T>, g.nschunks, DBV, 0, st, g, zin, zout, r, q, dinv, dmask, mg.on, w, ks);
     });
   };
   // composite pre-smoothing
-  timed(2, [&] { IBG_LAUNCH(k_mg_c_jac0<T>, g.nchunks, DBV, 0, st, g, r, z, dinv, dmask, mg.on, w, ks); });
+  timed(2, [&] { IBG_LAUNCH(k_mg_c_jac0<T>, g.nschunks, DBV, 0, st, g, r, z, dinv, dmask, mg.on, w, ks); });
   fe_expand2<T>(g, 1, z, (T*)nullptr, st);
   if (!mg.any) return;
   T* cur = z;
@@ -299,10 +332,18 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
   for (int k = 0; k < mg.max_big; ++k) {
     const MGLevelDev<T>& L = mg.lev[k];
     const unsigned nb = nblk256(L.n);
-    IBG_LAUNCH(k_mg_l_jac0<T>, nb, 256, 0, st, L, k, w, mg.on, mg.small, ks);
     T* a = L.xa;
     T* b = L.xb;
-    for (int s = 1; s < nu; ++s) {
+    int s0 = 1;
+    if (nu >= 2) {   // the first two steps in one pass, result in xb
+      IBG_LAUNCH(k_mg_l_jac2<T>, nb, 256, 0, st, L, k, w, mg.on, mg.small, ks);
+      a = L.xb;
+      b = L.xa;
+      s0 = 2;
+    } else {
+      IBG_LAUNCH(k_mg_l_jac0<T>, nb, 256, 0, st, L, k, w, mg.on, mg.small, ks);
+    }
+    for (int s = s0; s < nu; ++s) {
       IBG_LAUNCH(k_mg_l_sweep<T>, nb, 256, 0, st, L, k, (const T*)a, b, w, mg.on, mg.small, ks);
       T* tmp = a; a = b; b = tmp;
     }
@@ -312,7 +353,7 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
   }
   // small levels and the coarsest solve, one CTA per problem
   SmallArgs<T> sa{mg.dlev, mg.on, mg.small, mg.coarsest, mg.cinv_off, mg.cinv, w, nu};
-  IBG_LAUNCH(k_mg_small<T>, mg.ninst, 512, 0, st, sa, ks);
+  IBG_LAUNCH(k_mg_small<T>, mg.ninst, SMALL_THREADS, 0, st, sa, ks);
   // large levels, up
   for (int k = mg.max_big - 1; k >= 0; --k) {
     const MGLevelDev<T>& L = mg.lev[k];
@@ -328,7 +369,7 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
   }
   // composite: prolongation and post-smoothing, ending in z
   T* y = (nu % 2 == 0) ? z : zs;
-  IBG_LAUNCH(k_mg_c_prolong<T>, g.nchunks, DBV, 0, st, g, mg.lev[0], (const T*)cur, y, dmask, mg.on, ks);
+  IBG_LAUNCH(k_mg_c_prolong<T>, g.nschunks, DBV, 0, st, g, mg.lev[0], (const T*)cur, y, dmask, mg.on, ks);
   if (pr) pr->end(st);
   fe_expand2<T>(g, 1, y, (T*)nullptr, st);
   T* o = (y == z) ? zs : z;

@@ -1,5 +1,6 @@
 // Test driver: prints the library's incident-cell-mask weights (kuhn_weights.hpp)
-// for every mask: 15 mass weights, then the 6 axis-edge counts (+x -x +y -y +z -z).
+// for every mask: 15 mass weights, the 6 axis-edge counts (+x -x +y -y +z -z),
+// then the 45 gradient couplings (stencil offset major, axis minor).
 #include <cstdio>
 
 #include "kuhn_weights.hpp"
@@ -9,6 +10,13 @@ int main() {
     for (int k = 0; k < 15; ++k) std::printf("%d ", ibg::mass_weight(m, k));
     for (int a = 0; a < 3; ++a)
       for (int s = 1; s >= -1; s -= 2) std::printf("%d ", ibg::stiff_edge_count(m, a, s));
+    for (int k = 0; k < 15; ++k)       // gradient couplings: sum over the active incident cells
+      for (int a = 0; a < 3; ++a) {
+        int w = 0;
+        for (int c = 0; c < 8; ++c)
+          if ((m >> c) & 1) w += ibg::grad_cell_weight(c, k, a);
+        std::printf("%d ", w);
+      }
     std::printf("\n");
   }
   return 0;

@@ -4,7 +4,8 @@ The library derives the consistent-mass and stiffness couplings of a node from
 the 8-bit mask of its active incident cells by closed formulas.  This test
 enumerates, for every mask, the six Kuhn tetrahedra of every active incident
 cell (one per axis order, Sec. 3.1 box mesh) and counts directly which of them
-hold the node and each neighbour: the counts must equal the formulas.
+hold the node and each neighbour, and sums the neighbours' barycentric
+gradients: the counts and sums must equal the library's formulas.
 """
 import itertools
 import os
@@ -22,6 +23,7 @@ OFFSETS = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (
 def brute_force(mask):
     mass = np.zeros(15, int)
     edge = np.zeros(6, int)
+    grad = np.zeros((15, 3), int)
     for c in range(8):
         if not (mask >> c) & 1:
             continue
@@ -36,9 +38,16 @@ def brute_force(mask):
             verts = [tuple(x) for x in v]
             if (0, 0, 0) not in verts:
                 continue
+            # barycentric gradients in units 1/h: lambda_0 = 1 - x_a1, lambda_1 = x_a1 - x_a2, ...
+            gvec = np.zeros((4, 3), int)
+            gvec[0, perm[0]] = -1
+            gvec[1, perm[0]], gvec[1, perm[1]] = 1, -1
+            gvec[2, perm[1]], gvec[2, perm[2]] = 1, -1
+            gvec[3, perm[2]] = 1
             for k, o in enumerate(OFFSETS):
                 if o in verts:
                     mass[k] += 2 if k == 0 else 1
+                    grad[k] += gvec[verts.index(o)]
             for i in range(3):                         # axis edges of the tetrahedron
                 p, q = verts[i], verts[i + 1]
                 if (0, 0, 0) in (p, q):
@@ -46,7 +55,7 @@ def brute_force(mask):
                     a = perm[i]
                     s = other[a]
                     edge[2 * a + (0 if s > 0 else 1)] += 1
-    return mass, edge
+    return mass, edge, grad
 
 
 def test_mask_weights_match_tetrahedron_enumeration(tmp_path):
@@ -56,8 +65,9 @@ def test_mask_weights_match_tetrahedron_enumeration(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     for mask in range(256):
         got = np.array([int(v) for v in out[mask].split()])
-        mass, edge = brute_force(mask)
+        mass, edge, grad = brute_force(mask)
         assert np.array_equal(got[:15], mass), (mask, got[:15], mass)
-        assert np.array_equal(got[15:], edge), (mask, got[15:], edge)
+        assert np.array_equal(got[15:21], edge), (mask, got[15:21], edge)
+        assert np.array_equal(got[21:].reshape(15, 3), grad), mask
     # interior node: row of the mass matrix sums to the cell volume (120 units)
     assert sum(int(v) for v in out[255].split()[:15]) == 120
