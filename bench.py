@@ -40,6 +40,8 @@ def workload(name):
         return W.cylinder_refined_64x64x256()
     if name == "cylinder_16x16x64":
         return W.cylinder_uniform_16x16x64()
+    if name == "aneurysm_128x128x256_L2":
+        return W.aneurysm_128x128x256_L2()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -54,6 +56,8 @@ def sample_case(name):
         return W.cylinder_case(n=(64, 64, 16), length=length, M=M, seed=2, max_level=1, refine_band=2,
                                reduce_band=2, nu=c["nu"], dt=c["dt"], a0=1.0, b=(0.5,),
                                name="cylinder_64x64x16_L1_slab"), "64x64x16 coarse-cell slab of the same tube (16 of 256 cells in z), 2 steps"
+    if name == "aneurysm_128x128x256_L2":
+        raise SystemExit("no bounded oracle sample for the aneurysm workload: run it with --no-cpu-baseline")
     return workload(name), "full workload, 2 steps"
 
 
@@ -327,8 +331,9 @@ def run_oracle_sample(name, steps=2):
 
 def run_serving(n_req, steps):
     """Serving comparison on a reduced request stream (the full mix is 256
-    requests x 200 steps on 32^3-128^3 grids): the continuously batched mixed
-    path vs the plain FP64 path one request at a time, same arrivals."""
+    requests x 200 steps of 32^3-128^3 active leaf cells): the continuously
+    batched mixed path vs the plain FP64 path one request at a time, same
+    arrivals."""
     import workloads as W
     from paper_2007_02082_gb300.serve import serve, serve_one_at_a_time
     stream = W.serving_requests(n_req=n_req, rate=None, seed=5, steps=steps, cells_lo=32 ** 3, cells_hi=64 ** 3)
@@ -340,7 +345,7 @@ def run_serving(n_req, steps):
     return {"requests": n_req, "steps": steps, "mean_interarrival_s": 0.05,
             "batched_mixed": b, "one_at_a_time_fp64": o,
             "stream": "seeded Poisson arrivals; straight/bent/aneurysmal tubes, R 0.3-1.0, L 3-10, "
-                      "32^3-64^3 equivalent cells, 0-2 levels, nu 0.01-0.05"}
+                      "coarse spacing sized for 32^3-64^3 active leaf cells, 0-2 levels, nu 0.01-0.05"}
 
 
 def main():

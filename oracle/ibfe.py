@@ -188,14 +188,16 @@ class Mesh:
         return np.where(ok & inb, pos, -1)
 
 
-def build_mesh(case):
-    """Grid generation of Sec. 3 on the structured box (readings R10-R12)."""
+def level_map(case):
+    """Coarse-cell maps of the grid generation (Sec. 3.2 refinement, Sec. 4.3
+    domain reduction; readings R11-R12): the point cell of every Lagrangian
+    point, the Chebyshev distance to the nearest point cell, the 2:1-balanced
+    refinement level and the active mask, all [nz][ny][nx]."""
     L = int(case["max_level"])
     n = np.array(case["n"], dtype=np.int64)
     origin = np.array(case["origin"], dtype=np.float64)
     extent = np.array(case["extent"], dtype=np.float64)
     h0 = extent / n
-    hf = extent / (n * (1 << L)).astype(np.float64)
     X = np.asarray(case["X"], dtype=np.float64)
     nx, ny, nz = (int(v) for v in n)
 
@@ -229,6 +231,18 @@ def build_mesh(case):
     # R12: domain reduction
     inside = np.asarray(case["inside"]).astype(bool)
     active = np.ones_like(inside) if rb < 0 else (inside | (dist <= rb))
+    return pc, dist, level, active
+
+
+def build_mesh(case):
+    """Grid generation of Sec. 3 on the structured box (readings R10-R12)."""
+    L = int(case["max_level"])
+    n = np.array(case["n"], dtype=np.int64)
+    origin = np.array(case["origin"], dtype=np.float64)
+    extent = np.array(case["extent"], dtype=np.float64)
+    h0 = extent / n
+    hf = extent / (n * (1 << L)).astype(np.float64)
+    pc, dist, level, active = level_map(case)
 
     # leaf cells (finest-index corners)
     corners = []

@@ -53,23 +53,15 @@ cudaError_t fe_init_tables() {
 }
 
 // ---------------------------------------------------------------- helpers
-// Gradient couplings of a node, gw[k][a] = sum over its active incident cells of
-// grad_cell_weight (kuhn_weights.hpp); the arguments are compile-time after
-// unrolling, so the per-cell weights fold into constants.
+// Gradient couplings of a node (kuhn_weights.hpp); k and a are compile-time
+// after unrolling, so each is a short sum of mask bits.
 __device__ __forceinline__ void grad_weights(int mask, int (&gw)[15][3]) {
 #pragma unroll
   for (int k = 0; k < 15; ++k)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) gw[k][a] = 0;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    if (!((mask >> c) & 1)) continue;
-#pragma unroll
-    for (int k = 0; k < 15; ++k)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) gw[k][a] += grad_cell_weight(c, k, a);
-  }
+    for (int a = 0; a < 3; ++a) gw[k][a] = grad_weight(mask, k, a);
 }
+
 __device__ __forceinline__ void spacing(const DevGrid& g, int b, double (&h)[3]) {
   const int inst = g.binst[b], lev = g.blev[b];
   const double* p = g.hl + (inst * 4 + lev) * 3;

@@ -64,59 +64,63 @@ IBG_HD int mass_weight(int mask, int k) {
   }
 }
 
-// Stencil offset index (0..14, order as in mass_weight) of a neighbour offset
-// (each coordinate in -1..1), -1 if it is not in the 15-point Kuhn stencil.
-IBG_HD int stencil_index(int rx, int ry, int rz) {
-  const int key = (rz + 1) * 9 + (ry + 1) * 3 + (rx + 1);
-  switch (key) {
-    case 13: return 0;
-    case 14: return 1;
-    case 12: return 2;
-    case 16: return 3;
-    case 10: return 4;
-    case 22: return 5;
-    case 4: return 6;
-    case 17: return 7;
-    case 9: return 8;
-    case 25: return 9;
-    case 1: return 10;
-    case 23: return 11;
-    case 3: return 12;
-    case 26: return 13;
-    case 0: return 14;
-    default: return -1;
+// Gradient coupling of a node and its stencil neighbour k along axis a: the sum,
+// over the Kuhn tetrahedra of the active incident cells that hold both, of the
+// neighbour's barycentric gradient (integer, units 1/h_a).  Barycentric
+// gradients of tetrahedron (a1, a2, a3): v0: -e_a1, v1: e_a1 - e_a2,
+// v2: e_a2 - e_a3, v3: e_a3.  Each coupling is a fixed integer combination of
+// the mask bits (one term per incident cell); (phi_n, d_a phi_m) summed over
+// tetrahedra is this times |T|/4.
+IBG_HD int grad_weight(int mask, int k, int a) {
+  auto b = [mask](int c) { return (mask >> c) & 1; };
+  switch (k * 3 + a) {
+    case 0: return 2 * b(0) - 2 * b(1) + b(2) - b(3) + b(4) - b(5) + 2 * b(6) - 2 * b(7);
+    case 1: return 2 * b(0) + b(1) - 2 * b(2) - b(3) + b(4) + 2 * b(5) - b(6) - 2 * b(7);
+    case 2: return 2 * b(0) + b(1) + b(2) + 2 * b(3) - 2 * b(4) - b(5) - b(6) - 2 * b(7);
+    case 3: return 2 * b(1) + b(3) + b(5) + 2 * b(7);
+    case 4: return -b(3) - b(7);
+    case 5: return -b(5) - b(7);
+    case 6: return -2 * b(0) - b(2) - b(4) - 2 * b(6);
+    case 7: return b(0) + b(4);
+    case 8: return b(0) + b(2);
+    case 9: return -b(3) - b(7);
+    case 10: return 2 * b(2) + b(3) + b(6) + 2 * b(7);
+    case 11: return -b(6) - b(7);
+    case 12: return b(0) + b(4);
+    case 13: return -2 * b(0) - b(1) - b(4) - 2 * b(5);
+    case 14: return b(0) + b(1);
+    case 15: return -b(5) - b(7);
+    case 16: return -b(6) - b(7);
+    case 17: return 2 * b(4) + b(5) + b(6) + 2 * b(7);
+    case 18: return b(0) + b(2);
+    case 19: return b(0) + b(1);
+    case 20: return -2 * b(0) - b(1) - b(2) - 2 * b(3);
+    case 21: return b(3) + b(7);
+    case 22: return b(3) + b(7);
+    case 23: return -2 * b(7);
+    case 24: return -b(0) - b(4);
+    case 25: return -b(0) - b(4);
+    case 26: return 2 * b(0);
+    case 27: return -2 * b(7);
+    case 28: return b(6) + b(7);
+    case 29: return b(6) + b(7);
+    case 30: return 2 * b(0);
+    case 31: return -b(0) - b(1);
+    case 32: return -b(0) - b(1);
+    case 33: return b(5) + b(7);
+    case 34: return -2 * b(7);
+    case 35: return b(5) + b(7);
+    case 36: return -b(0) - b(2);
+    case 37: return 2 * b(0);
+    case 38: return -b(0) - b(2);
+    case 39: return 2 * b(7);
+    case 40: return 2 * b(7);
+    case 41: return 2 * b(7);
+    case 42: return -2 * b(0);
+    case 43: return -2 * b(0);
+    case 44: return -2 * b(0);
+    default: return 0;
   }
-}
-
-// Gradient coupling of one incident cell: for the cell of mask bit c, the sum
-// over its Kuhn tetrahedra that hold both the node and its stencil neighbour k
-// of the (integer) gradient of the neighbour's P1 function along axis a, in
-// units 1/h_a.  (phi_m, d_a phi_n summed over tetrahedra is this times |T|/4.)
-// Barycentric gradients of tetrahedron (a1, a2, a3): v0: -e_a1, v1: e_a1 - e_a2,
-// v2: e_a2 - e_a3, v3: e_a3.
-IBG_HD int grad_cell_weight(int c, int k, int a) {
-  const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
-  const int qb = (1 - dx) | ((1 - dy) << 1) | ((1 - dz) << 2);   // the node's corner in the cell
-  const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-  int sum = 0;
-  for (int p = 0; p < 6; ++p) {
-    const int a1 = perm[p][0], a2 = perm[p][1], a3 = perm[p][2];
-    const int vb[4] = {0, 1 << a1, (1 << a1) | (1 << a2), 7};
-    bool has = false;
-    for (int v = 0; v < 4; ++v) has = has || vb[v] == qb;
-    if (!has) continue;
-    for (int v = 0; v < 4; ++v) {
-      const int rx = dx - 1 + (vb[v] & 1), ry = dy - 1 + ((vb[v] >> 1) & 1), rz = dz - 1 + ((vb[v] >> 2) & 1);
-      if (stencil_index(rx, ry, rz) != k) continue;
-      int gvec[3] = {0, 0, 0};
-      if (v == 0) gvec[a1] = -1;
-      else if (v == 1) { gvec[a1] = 1; gvec[a2] = -1; }
-      else if (v == 2) { gvec[a2] = 1; gvec[a3] = -1; }
-      else gvec[a3] = 1;
-      sum += gvec[a];
-    }
-  }
-  return sum;
 }
 
 }  // namespace ibg

@@ -188,6 +188,24 @@ bool interp_row(const Lattice& Lt, const int64_t num[3], int64_t den, std::vecto
   return true;
 }
 
+// Mark as Dirichlet every lattice vertex of Lt that takes a nonzero
+// interpolation weight at the point num/den (a Dirichlet node of the finer
+// level): the coarse basis functions that remain then vanish on every finer
+// Dirichlet node, so each coarse space is a subspace of the finer one.
+void mark_dirichlet(Lattice& Lt, const int64_t num[3], int64_t den) {
+  int64_t c[3];
+  double f[3];
+  for (int a = 0; a < 3; ++a) {
+    c[a] = std::min(num[a] / den, Lt.n[a] - 1);
+    f[a] = double(num[a] - c[a] * den) / double(den);
+  }
+  int vb[4];
+  double wt[4];
+  kuhn_weights(f, vb, wt);
+  for (int v = 0; v < 4; ++v)
+    if (wt[v] != 0.0) Lt.dir[Lt.node(c[0] + (vb[v] & 1), c[1] + ((vb[v] >> 1) & 1), c[2] + ((vb[v] >> 2) & 1))] = 1;
+}
+
 bool dense_inverse(const MGLevelHost& M, std::vector<double>& inv) {
   const int64_t n = M.nn;
   std::vector<double> A(n * n, 0.0);
@@ -321,6 +339,9 @@ void build_mg(const HostGrid& G, MGHost& mg) {
           for (int t = 0; t < 6; ++t) C.frac[6 * C.cell(ii, jj, kk) + t] = float(acc[t] / 8.0);
         }
     const int64_t nlc = (C.n[0] + 1) * (C.n[1] + 1) * (C.n[2] + 1);
+    // coarse Dirichlet nodes: by injection (the finer node at the same position
+    // is Dirichlet) when the outlet lies on the coarse lattice; otherwise every
+    // coarse node whose interpolation reaches a finer Dirichlet node
     C.dir.assign(nlc, 0);
     int64_t ndir = 0;
     for (int64_t kk = 0; kk <= C.n[2]; ++kk)
@@ -332,6 +353,15 @@ void build_mg(const HostGrid& G, MGHost& mg) {
             ++ndir;
           }
         }
+    if (ndir == 0)
+      for (int64_t kk = 0; kk <= F.n[2]; ++kk)
+        for (int64_t jj = 0; jj <= F.n[1]; ++jj)
+          for (int64_t ii = 0; ii <= F.n[0]; ++ii)
+            if (F.lat[F.node(ii, jj, kk)] == LAT_DIRICHLET) {
+              const int64_t p[3] = {ii, jj, kk};
+              mark_dirichlet(C, p, 2);
+              ++ndir;
+            }
     if (ndir == 0) break;   // a coarse level without Dirichlet node would be singular
     MGLevelHost M;
     for (int a = 0; a < 3; ++a) M.n[a] = C.n[a], M.h[a] = 2.0 * mg.lev[k].h[a];

@@ -14,8 +14,13 @@
 // edge term is weighted by the fraction of the tetrahedron's volume covered by
 // the active domain.  The fractions are summed up the hierarchy, 8 child
 // tetrahedra per parent tetrahedron.  Pressure-Dirichlet nodes (outlets) are
-// left out of every level; a G(k+1) node is Dirichlet when the G(k) node at its
-// position is.
+// left out of every level.  A G0 node, and a coarser node where the outlet
+// lies on its lattice, is Dirichlet when the finer node at its position is
+// (this departs from Galerkin only next to the outlet and gave the fewest CG
+// iterations); where an outlet plane falls between the coarse lattice planes,
+// a coarse node is Dirichlet when its interpolation reaches any finer
+// Dirichlet node, so the coarse space lies inside the finer one and the
+// operator is the exact Galerkin product on every row.
 //
 // Transfers.  Prolongation is P1 interpolation on the coarse Kuhn tetrahedron
 // that holds the fine node (barycentric weights, multiples of 2^-L, exact in
@@ -62,10 +67,9 @@ struct MGHost {
   std::vector<double> cinv;         // dense inverse of the G(K) operator, [nn_K][nn_K]
 };
 
-// Build the hierarchy of one composite grid.  On failure (no Dirichlet node
-// left on a coarse level before the coarsest is small enough, or a transfer
-// weight that points at a missing node) ok = false and the Poisson solve of
-// that problem keeps the Jacobi preconditioner.
+// Build the hierarchy of one composite grid.  On failure (no outlet node at
+// all, or a transfer weight that points at a missing node) ok = false and the
+// Poisson solve of that problem keeps the Jacobi preconditioner.
 void build_mg(const HostGrid& G, MGHost& mg);
 
 }  // namespace ibg

@@ -10,13 +10,8 @@ int main() {
     for (int k = 0; k < 15; ++k) std::printf("%d ", ibg::mass_weight(m, k));
     for (int a = 0; a < 3; ++a)
       for (int s = 1; s >= -1; s -= 2) std::printf("%d ", ibg::stiff_edge_count(m, a, s));
-    for (int k = 0; k < 15; ++k)       // gradient couplings: sum over the active incident cells
-      for (int a = 0; a < 3; ++a) {
-        int w = 0;
-        for (int c = 0; c < 8; ++c)
-          if ((m >> c) & 1) w += ibg::grad_cell_weight(c, k, a);
-        std::printf("%d ", w);
-      }
+    for (int k = 0; k < 15; ++k)       // gradient couplings
+      for (int a = 0; a < 3; ++a) std::printf("%d ", ibg::grad_weight(m, k, a));
     std::printf("\n");
   }
   return 0;

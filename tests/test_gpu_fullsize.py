@@ -1,0 +1,77 @@
+"""Full-size cases (the 64x64x256 refined cylinder and the 128x128x256
+two-level aneurysm) through the C ABI, checked by what holds at any size:
+
+  * the coarse level map and the active-cell mask equal the oracle's (Sec. 3.2
+    refinement, Sec. 4.3 domain reduction), bit for bit;
+  * the mixed path stays within the stated 1e-6 relative L2 of the plain FP64
+    path over two steps from the same start;
+  * Phi is zero on every outlet node (Eq. 12 boundary condition);
+  * after the IB correction the velocity interpolated at the Lagrangian points
+    (the delta weights of Eq. 17-18 on the exported supports) equals U_B up to
+    the force-solve residual (Eq. 21: W u = U_B is what the force enforces).
+
+The oracle itself cannot step these sizes in test time; the small cases of
+test_gpu_parity.py compare every field with it.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ibfe
+from tests.gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "cylinder_64x64x256_L1": W.cylinder_refined_64x64x256,
+    "aneurysm_128x128x256_L2": W.aneurysm_128x128x256_L2,
+}
+
+
+def interpolate_at_points(g, u):
+    """sum_a w_ia u(node_ia) over each point's 4x4x4 support."""
+    q = g.ib_fields_get("NODE_Q").astype(np.int64) + 4               # keys of supports never alias rows
+    nf = q.max(axis=0) + 8
+    keys = (q[:, 2] * nf[1] + q[:, 1]) * nf[0] + q[:, 0]        # increasing: canonical order is (z, y, x)
+    assert np.all(np.diff(keys) > 0)
+    org = g.ib_fields_get("IB_ORIGIN").astype(np.int64) + 4
+    w = g.ib_fields_get("IB_WEIGHTS")
+    a = np.arange(64)
+    off = np.stack([a & 3, (a >> 2) & 3, a >> 4], axis=1)
+    sup = org[:, None, :] + off[None, :, :]                      # [M][64][3]
+    sk = (sup[..., 2] * nf[1] + sup[..., 1]) * nf[0] + sup[..., 0]
+    idx = np.clip(np.searchsorted(keys, sk), 0, len(keys) - 1)
+    found = keys[idx] == sk
+    assert np.all(found | (w == 0.0))                            # a weight only where the node exists
+    vals = np.where(found[..., None], u[idx], 0.0)
+    return np.einsum("ma,mac->mc", w, vals)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_full_size_invariants(name):
+    from paper_2007_02082_gb300 import IBGrid
+    case = CASES[name]()
+    _, _, level, active = ibfe.level_map(case)
+    gm = IBGrid(case, precision="mixed")
+    assert np.array_equal(gm.ib_fields_get("ACTIVE"), active.astype(np.uint8))
+    assert np.array_equal(gm.ib_fields_get("LEVEL"), level.astype(np.uint8))
+    assert gm.ib_grid_info()["mg_levels"] >= 3
+    gm.ipcs_step(2)
+    um, pm = gm.ib_fields_get("U"), gm.ib_fields_get("P")
+    gm.close()
+
+    g = IBGrid(case, precision="fp64")
+    g.ipcs_step(2)
+    info = g.ib_grid_info()
+    assert info["step"] == 2 and info["status_p"] == 0 and info["status_ib"] == 0
+    u, p = g.ib_fields_get("U"), g.ib_fields_get("P")
+    assert rel_l2(um, u) <= 1e-6 and rel_l2(pm, p) <= 1e-6
+    flags = g.ib_fields_get("NODE_FLAGS")
+    phi = g.ib_fields_get("PHI")
+    assert np.all(phi[(flags & 4) != 0] == 0.0)
+    # no-slip after the IB correction: W u_IB - U_B is the force-solve residual
+    uib = g.ib_fields_get("U_IB")
+    bf = g.ib_fields_get("B_F")
+    res = interpolate_at_points(g, uib) - np.asarray(case["UB"]).reshape(-1, 3)
+    assert np.linalg.norm(res) <= 1e-9 * np.linalg.norm(bf)
+    g.close()

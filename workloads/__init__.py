@@ -101,6 +101,21 @@ def cylinder_uniform_16x16x64(**kw):
     return cylinder_case(**kw)
 
 
+def aneurysm_128x128x256_L2(**kw):
+    """Tube R = 0.5 along z (length 4) fused with a sphere R = 0.6 centred 0.7
+    off the axis at mid-length, box [-0.6, 1.4] x [-1, 1] x [0, 4] on
+    128x128x256 coarse cells (h0 = 1/64), two refinement levels, domain
+    reduction, ~60k points (spacing 4.3 finest cells), pulsatile inflow
+    u_max(t) = 1 + 0.5 sin(2 pi t), nu = 0.01, dt = 0.001, 2000 steps."""
+    args = dict(R=0.5, length=4.0, Rs=0.6, offset=0.7, h=1.0 / 64, spacing=4.31, seed=3, max_level=2,
+                refine_band=2, reduce_band=2, nu=0.01, dt=0.001, steps=2000, a0=1.0, b=(0.5,),
+                box=((-0.6, -1.0, 0.0), (2.0, 2.0, 4.0)))
+    args.update(kw)
+    c = aneurysm_case(**args)
+    c["name"] = "aneurysm_128x128x256_L2"
+    return c
+
+
 def cylinder_refined_64x64x256(**kw):
     """64x64x256 cylinder, one refinement level in a 2h band around the wall,
     cells more than 2h outside the wall dropped, 32k points, pulsatile inflow
@@ -153,15 +168,19 @@ def _case(name, origin, extent, n, X, dS, inside, ports, nu, dt, steps, max_leve
 
 
 def aneurysm_case(R=0.5, length=4.0, Rs=0.6, offset=0.7, h=1.0 / 32, spacing=2.3, seed=3, max_level=1,
-                  refine_band=2, reduce_band=2, nu=0.01, dt=0.001, steps=2000, a0=1.0, b=(0.5,)):
+                  refine_band=2, reduce_band=2, nu=0.01, dt=0.001, steps=2000, a0=1.0, b=(0.5,), box=None):
     """Saccular aneurysm: a tube of radius R along z fused with a sphere of
     radius Rs centred `offset` off the axis at mid-length.  Points: stratified
     jitter on the tube wall outside the sphere and on the sphere outside the
-    tube (equal-area strata in (cos phi, theta)); dS = stratum area."""
+    tube (equal-area strata in (cos phi, theta)); dS = stratum area.  `box`
+    (origin, extent) fixes the domain; by default it is the vessel plus 4h."""
     zc = 0.5 * length
     margin = 4.0 * h
-    origin, extent = _box((-R - margin, -max(R, Rs) - margin, 0.0),
-                          (offset + Rs + margin, max(R, Rs) + margin, length))
+    if box is None:
+        origin, extent = _box((-R - margin, -max(R, Rs) - margin, 0.0),
+                              (offset + Rs + margin, max(R, Rs) + margin, length))
+    else:
+        origin, extent = tuple(box[0]), tuple(box[1])
     n = _grid_for(extent, h)
     extent = tuple(n[a] * h for a in range(3))
     hf = h / (1 << max_level)
@@ -260,8 +279,9 @@ def bent_tube_case(R=0.5, Rc=1.5, l_in=1.5, l_out=1.5, h=1.0 / 16, spacing=2.3, 
 
 def serving_requests(n_req=256, rate=None, seed=5, steps=200, cells_lo=32 ** 3, cells_hi=128 ** 3):
     """Poisson-arrival stream of seeded random vessels: kind in {straight,
-    bent, aneurysmal}, radius 0.3-1.0, length 3-10, an active grid of 32^3 to
-    128^3 equivalent cells (log-uniform), 0-2 refinement levels, nu 0.01-0.05.
+    bent, aneurysmal}, radius 0.3-1.0, length 3-10, about 32^3 to 128^3 active
+    leaf cells (log-uniform target; the coarse spacing is sized for it from an
+    estimate of the refined wall band), 0-2 refinement levels, nu 0.01-0.05.
     Returns [(arrival_time, case)], arrival times in units of 1/rate seconds
     (rate None: unit rate)."""
     rng = np.random.default_rng(seed)
@@ -282,8 +302,18 @@ def serving_requests(n_req=256, rate=None, seed=5, steps=200, cells_lo=32 ** 3, 
             vol = math.pi * (R * 1.25) ** 2 * (0.6 * L + 0.5 * math.pi * 3 * R)
         else:
             vol = math.pi * (R * 1.25) ** 2 * L + 4.0 / 3.0 * math.pi * (1.2 * R * 1.2) ** 3
-        # leaf cells grow ~ 8^levels near the wall; size the coarse grid for the target
-        h = (vol / (target / (1 + 2.0 * levels))) ** (1.0 / 3.0)
+        # leaf cells: the wall band (2 coarse cells each side) is refined 8^levels
+        # times, the next band 8^(levels-1) times; size the coarse spacing h so
+        # that coarse cells x this factor meet the target (fixed point in h)
+        wall = vol / (math.pi * (R * 1.25) ** 2) * 2 * math.pi * R   # wall area of the vessel
+        h = (vol / target) ** (1.0 / 3.0)
+        for _ in range(20):
+            f = 1.0
+            if levels >= 1:
+                inner = min(1.0, wall * 5 * h / vol)              # level `levels` band
+                outer = min(1.0 - inner, wall * 4 * h / vol) if levels == 2 else 0.0
+                f = 1.0 + inner * (8 ** levels - 1) + outer * (8 ** (levels - 1) - 1)
+            h = (vol * f / target) ** (1.0 / 3.0)
         h = max(h, 2.0 * R / 28)
         dt = 0.25 * h / (1 << levels)
         if kind == "straight":
