@@ -33,6 +33,11 @@ constexpr int DBV = 512;        // nodes per brick = threads per brick CTA
 constexpr int TILE = 10;        // brick plus a one-node halo
 constexpr int TILE3 = 1000;
 
+// Brick padding: a slot without D_VALID (no active leaf cell of its level
+// touches it) is zero in every vector of the library.  Every kernel writes only
+// zeros there or skips it, so the streaming kernels neither read nor write
+// such slots.
+//
 // per-slot metadata bits (mirror of setup.hpp)
 constexpr uint16_t D_VALID = 1u << 8, D_HANG = 1u << 9, D_DUP = 1u << 10,
                    D_VDIR = 1u << 11, D_PDIR = 1u << 12, D_IFACE = 1u << 13;

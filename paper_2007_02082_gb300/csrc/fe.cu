@@ -520,11 +520,11 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
               fz * (T(wzp) * (pv - zp) + T(wzm) * (pv - zm));
       }
       if (m & dmask) out = T(0);
-      q[s] = out;
-      if (CG) {
-        pnew[s] = pv;
-        acc += pv * out;
+      if (m & D_VALID) {   // brick padding stays zero: no store
+        q[s] = out;
+        if (CG) pnew[s] = pv;
       }
+      if (CG) acc += pv * out;
       __syncthreads();
     }
   }
@@ -659,11 +659,11 @@ __global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict_
       }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        y[(int64_t)c * g.nslots + s] = out[c];
-        if (FUSEP) {
-          pnew[(int64_t)c * g.nslots + s] = tile[c * TILE3 + ti];
-          acc[c] += tile[c * TILE3 + ti] * out[c];
+        if (m & D_VALID) {   // brick padding stays zero: no store
+          y[(int64_t)c * g.nslots + s] = out[c];
+          if (FUSEP) pnew[(int64_t)c * g.nslots + s] = tile[c * TILE3 + ti];
         }
+        if (FUSEP) acc[c] += tile[c * TILE3 + ti] * out[c];
       }
       __syncthreads();
     }

@@ -148,6 +148,14 @@ __global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict
 // Streaming form of k_cg_update for one component: each thread handles W =
 // 16 / sizeof(T) consecutive slots with 16-byte loads and stores; slots of
 // interface copies take the interface sum of q one by one.
+template <int W>
+__device__ __forceinline__ uint16_t vec_or_n(const uint16_t* mm) {
+  uint16_t o = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) o |= mm[j];
+  return o;
+}
+
 template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; using mt = uint2; static constexpr int W = 4; };
 template <> struct Vec16<double> { using type = double2; using mt = uint32_t; static constexpr int W = 2; };
@@ -179,6 +187,7 @@ __global__ void __launch_bounds__(512) k_cg_update_vec(DevGrid g, T* __restrict_
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
     const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
     const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+    if (!(vec_or_n<W>(mm) & D_VALID)) continue;   // brick padding: always zero, never read or written
     const V dv = *reinterpret_cast<const V*>(dinv + s);
     const T* de = reinterpret_cast<const T*>(&dv);
 #pragma unroll
@@ -297,6 +306,7 @@ __global__ void __launch_bounds__(512) k_cg_update_r(DevGrid g, T* __restrict__ 
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
       const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
       const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+      if (!(vec_or_n<W>(mm) & D_VALID)) continue;   // brick padding: always zero, never read or written
       V xv = *reinterpret_cast<const V*>(x + s);
       V rv = *reinterpret_cast<const V*>(r + s);
       V pv = *reinterpret_cast<const V*>(p + s);
@@ -451,6 +461,7 @@ __global__ void __launch_bounds__(512) k_bcgv_p(DevGrid g, const T* __restrict__
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
     const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
     const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+    if (!(vec_or_n<W>(mm) & D_VALID)) continue;   // brick padding: always zero, never read or written
     const V dv = *reinterpret_cast<const V*>(dinv + s);
     const T* de = reinterpret_cast<const T*>(&dv);
     for (int c = 0; c < NC; ++c) {
@@ -502,6 +513,7 @@ __global__ void __launch_bounds__(512) k_bcgv_dot(DevGrid g, const T* __restrict
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
     const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
     const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+    if (!(vec_or_n<W>(mm) & D_VALID)) continue;   // brick padding: always zero, never read or written
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       if (!act[c]) continue;
@@ -564,6 +576,7 @@ __global__ void __launch_bounds__(512) k_bcgv_s(DevGrid g, const T* __restrict__
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
     const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
     const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+    if (!(vec_or_n<W>(mm) & D_VALID)) continue;   // brick padding: always zero, never read or written
     const V dv = *reinterpret_cast<const V*>(dinv + s);
     const T* de = reinterpret_cast<const T*>(&dv);
     for (int c = 0; c < NC; ++c) {
@@ -620,6 +633,7 @@ __global__ void __launch_bounds__(512) k_bcgv_xr(DevGrid g, T* __restrict__ x, T
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
     const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
     const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+    if (!(vec_or_n<W>(mm) & D_VALID)) continue;   // brick padding: always zero, never read or written
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       if (!act[c]) continue;
@@ -699,6 +713,7 @@ __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double*
   if (!oi.done)
     for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x) {
       const uint16_t m = g.meta[s];
+      if (!(m & D_VALID)) continue;   // brick padding: r32 and e32 stay zero there
       const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {

@@ -80,8 +80,11 @@ __global__ void __launch_bounds__(512) k_mg_c_jac0(DevGrid g, const T* __restric
   const int inst = g.binst[b0];
   if (ks[inst].done) return;
   const T w = on[inst] ? omega : T(1);
-  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x)
-    z[s] = keep_slot(g.meta[s], dmask) ? T(w * dinv[s] * r[s]) : T(0);
+  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x) {
+    const uint16_t m = g.meta[s];
+    if (!(m & D_VALID)) continue;   // brick padding stays zero
+    z[s] = keep_slot(m, dmask) ? T(w * dinv[s] * r[s]) : T(0);
+  }
 }
 
 // zout = zin + omega D^-1 (r - A zin) on kept slots
@@ -96,6 +99,7 @@ __global__ void __launch_bounds__(512) k_mg_c_smooth(DevGrid g, const T* __restr
   if (ks[inst].done || !on[inst]) return;
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x) {
     const uint16_t m = g.meta[s];
+    if (!(m & D_VALID)) continue;   // brick padding stays zero
     zout[s] = keep_slot(m, dmask) ? T(zin[s] + omega * dinv[s] * (r[s] - q_sum(g, q, s, m))) : T(0);
   }
 }
@@ -110,7 +114,9 @@ __global__ void __launch_bounds__(512) k_mg_c_prolong(DevGrid g, MGLevelDev<T> L
   const int inst = g.binst[b0];
   if (ks[inst].done || !on[inst]) return;
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x) {
-    if (!keep_slot(g.meta[s], dmask)) { zout[s] = T(0); continue; }
+    const uint16_t m = g.meta[s];
+    if (!(m & D_VALID)) continue;   // brick padding stays zero
+    if (!keep_slot(m, dmask)) { zout[s] = T(0); continue; }
     T v = zin[s];
     for (int e = L0.pptr[s]; e < L0.pptr[s + 1]; ++e) v += L0.pw[e] * L0.xa[L0.pcol[e]];
     zout[s] = v;
