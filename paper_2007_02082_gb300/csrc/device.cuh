@@ -8,20 +8,37 @@
 namespace ibg {
 
 // Every kernel launch of the library goes through launch_kernel, which counts
-// it (ib_info.kernel_launches).
+// it (ib_info.kernel_launches).  Launches allow programmatic dependent launch:
+// a kernel's CTAs may be scheduled while the previous kernel on the stream
+// drains, and every kernel waits at its first statement (KCOUNT) until the
+// previous one has completed and its writes are visible.  This hides the
+// launch gap between the many short kernels of a step.
 extern std::atomic<long long> g_launches;
 
 template <typename... KArgs, typename... Args>
 inline void launch_kernel(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                           Args&&... args) {
-  k<<<grid, block, smem, st>>>(static_cast<KArgs>(args)...);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
-// Device-side count of executed kernels: every kernel starts with KCOUNT(),
-// one relaxed atomic from thread 0 of block 0; one counter per translation unit.
+// Every kernel starts with KCOUNT(): the wait for the previous kernel of the
+// stream (programmatic dependent launch), then the device-side count of
+// executed kernels, one relaxed atomic from thread 0 of block 0 (one counter
+// per translation unit).
 #define IBG_KCOUNT_DEFINE static __device__ unsigned long long g_kcount = 0ULL;
 #define KCOUNT()                                                  \
   do {                                                            \
+    asm volatile("griddepcontrol.wait;" ::: "memory");            \
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&g_kcount, 1ULL); \
   } while (0)
 
