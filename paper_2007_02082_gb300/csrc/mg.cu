@@ -2,9 +2,10 @@
 // (Eq. 12).  The linear solver is not fixed by the paper (Sec. 2.2); the
 // hierarchy (mg.cpp) is the geometric one of the nested Kuhn meshes.
 //
-// One V-cycle, z = B r (damped Jacobi, nu sweeps down and nu up, exact dense
-// solve on the coarsest level, restriction = transpose of prolongation), is a
-// symmetric positive definite operator, as CG requires.
+// One V-cycle, z = B r (damped Jacobi, nu sweeps down and nu up on the
+// composite level and G0, nu_coarse below; exact dense solve on the coarsest
+// level; restriction = transpose of prolongation), is a symmetric positive
+// definite operator, as CG requires.
 //
 //   composite level : sweeps with the chunked Poisson stencil and the
 //                     interface sums; hanging nodes re-expanded after each
@@ -338,10 +339,11 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
   for (int k = 0; k < mg.max_big; ++k) {
     const MGLevelDev<T>& L = mg.lev[k];
     const unsigned nb = nblk256(L.n);
+    const int nuk = k == 0 ? nu : mg.nu_coarse;
     T* a = L.xa;
     T* b = L.xb;
     int s0 = 1;
-    if (nu >= 2) {   // the first two steps in one pass, result in xb
+    if (nuk >= 2) {   // the first two steps in one pass, result in xb
       IBG_LAUNCH(k_mg_l_jac2<T>, nb, 256, 0, st, L, k, w, mg.on, mg.small, ks);
       a = L.xb;
       b = L.xa;
@@ -349,7 +351,7 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
     } else {
       IBG_LAUNCH(k_mg_l_jac0<T>, nb, 256, 0, st, L, k, w, mg.on, mg.small, ks);
     }
-    for (int s = s0; s < nu; ++s) {
+    for (int s = s0; s < nuk; ++s) {
       IBG_LAUNCH(k_mg_l_sweep<T>, nb, 256, 0, st, L, k, (const T*)a, b, w, mg.on, mg.small, ks);
       T* tmp = a; a = b; b = tmp;
     }
@@ -358,17 +360,18 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
                mg.small, ks);
   }
   // small levels and the coarsest solve, one CTA per problem
-  SmallArgs<T> sa{mg.dlev, mg.on, mg.small, mg.coarsest, mg.cinv_off, mg.cinv, w, nu};
+  SmallArgs<T> sa{mg.dlev, mg.on, mg.small, mg.coarsest, mg.cinv_off, mg.cinv, w, mg.nu_coarse};
   IBG_LAUNCH(k_mg_small<T>, mg.ninst, SMALL_THREADS, 0, st, sa, ks);
   // large levels, up
   for (int k = mg.max_big - 1; k >= 0; --k) {
     const MGLevelDev<T>& L = mg.lev[k];
     const unsigned nb = nblk256(L.n);
-    T* c = (nu % 2 == 1) ? L.xa : L.xb;
-    T* y = (nu % 2 == 0) ? L.xa : L.xb;
+    const int nuk = k == 0 ? nu : mg.nu_coarse;
+    T* c = (nuk % 2 == 1) ? L.xa : L.xb;
+    T* y = (nuk % 2 == 0) ? L.xa : L.xb;
     IBG_LAUNCH(k_mg_l_prolong<T>, nb, 256, 0, st, L, mg.lev[k + 1], k, (const T*)c, y, mg.on, mg.small, ks);
     T* o = (y == L.xa) ? L.xb : L.xa;
-    for (int s = 0; s < nu; ++s) {
+    for (int s = 0; s < nuk; ++s) {
       IBG_LAUNCH(k_mg_l_sweep<T>, nb, 256, 0, st, L, k, (const T*)y, o, w, mg.on, mg.small, ks);
       T* tmp = y; y = o; o = tmp;
     }

@@ -43,7 +43,8 @@ template <typename T>
 struct MGDev {
   int nlev = 0;                        // levels over all problems
   int ninst = 0;
-  int nu = 2;                          // Jacobi sweeps before and after the coarse correction
+  int nu = 2;                          // Jacobi sweeps before and after the coarse correction (composite, G0)
+  int nu_coarse = 2;                   // the same on the levels below G0 (1 measured 2 more CG iterations per step)
   T omega = T(0.7);                    // Jacobi damping
   MGLevelDev<T> lev[MG_LEVELS_MAX];
   const MGLevelDev<T>* dlev = nullptr; // device copy of lev (read by the per-problem kernel)
