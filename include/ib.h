@@ -55,7 +55,7 @@ typedef enum {
   IB_ETIMEOUT = 7
 } ib_status;
 
-enum { IB_INLET_VELOCITY = 0, IB_OUTLET_ZERO_P = 1 };
+enum { IB_INLET_VELOCITY = 0, IB_OUTLET_ZERO_P = 1, IB_INLET_PRESSURE = 2 };
 enum { IB_PARABOLIC = 0 };
 enum { IB_FP64 = 0, IB_MIXED = 1 };
 enum { IB_PC_MULTIGRID = 0, IB_PC_JACOBI = 1 };
@@ -70,11 +70,17 @@ enum { IB_PC_MULTIGRID = 0, IB_PC_JACOBI = 1 };
  *   center       disc centre (its coordinate along `axis` is ignored)
  *   radius       disc radius R; a face node is a port node when
  *                dx*dx + dy*dy <= R*R, evaluated in FP64 without FMA
- *   kind         IB_INLET_VELOCITY: parabolic velocity u_max(t)(1 - r^2/R^2)
+ *   kind         IB_INLET_VELOCITY: parabolic velocity w(t)(1 - r^2/R^2)
  *                along the inward normal; IB_OUTLET_ZERO_P: Phi = 0, no velocity
- *                condition (do-nothing outlet)
- *   waveform     u_max(t) = a0 + sum_{k=1..n_harm} a[k-1] cos(2 pi k t / period)
- *                                             + b[k-1] sin(2 pi k t / period)
+ *                condition (do-nothing outlet); IB_INLET_PRESSURE: the pressure
+ *                w(t) is imposed (Sec. 3.1 drives its Poiseuille tube this way):
+ *                Phi = w(t^{n+1}) - p^n on the port nodes, so p^{n+1} = w(t^{n+1})
+ *                there, and no velocity condition (the natural condition
+ *                nu du/dn = 0 of the viscous term, as at an outlet)
+ *   waveform     w(t) = a0 + sum_{k=1..n_harm} a[k-1] cos(2 pi k t / period)
+ *                                      + b[k-1] sin(2 pi k t / period)
+ * At least one port fixes Phi (an outlet or a pressure inlet); a node on two
+ * ports belongs to the first in the array.
  */
 typedef struct {
   int32_t axis, side;
@@ -192,7 +198,8 @@ enum {
   IB_FIELD_B_F = 6,         /* last right-hand side B_F, double [M][3]   (get) */
   IB_FIELD_NODE_Q = 7,      /* finest integer coordinates, int32 [n_nodes][3] */
   IB_FIELD_NODE_FLAGS = 8,  /* uint8 [n_nodes]: 1 hanging, 2 velocity Dirichlet,
-                               4 outlet (Phi = 0), 8 inlet, 16 boundary */
+                               4 Phi Dirichlet (outlet or pressure inlet),
+                               8 inlet (velocity or pressure), 16 boundary */
   IB_FIELD_ACTIVE = 9,      /* uint8 coarse active mask [n2][n1][n0] */
   IB_FIELD_LEVEL = 10,      /* uint8 coarse level map [n2][n1][n0] */
   IB_FIELD_IB_ORIGIN = 11,  /* int32 [M][3] support origin on the finest grid */

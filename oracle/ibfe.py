@@ -37,10 +37,14 @@ with its reason in the project's design notes):
   R6  kinematic pressure (rho = 1 in every synthetic case);
   R7  viscous term nu (grad u, grad v) (equal to div 2 nu eps(u) for a
       divergence-free field; do-nothing outlet);
-  R9  Phi = 0 on outlet-port nodes, homogeneous Neumann elsewhere;
+  R9  Phi = 0 on outlet-port nodes; on pressure-inlet nodes Phi takes the
+      increment p_in(t^{n+1}) - p^n that brings p^{n+1} to the imposed inlet
+      pressure; homogeneous Neumann elsewhere;
   R10 port nodes: on the port face with dx^2 + dy^2 <= R^2 in FP64, no FMA;
-      other boundary nodes of the active region are no-slip walls; outlet nodes
-      carry no velocity condition;
+      other boundary nodes of the active region are no-slip walls; outlet and
+      pressure-inlet nodes carry no velocity condition (the natural condition
+      nu du/dn = 0 of the gradient-form viscous term, as at a do-nothing
+      outlet);
   R11 refinement level per coarse cell from the Chebyshev distance d to a
       point-containing coarse cell, hanging nodes constrained to the mean of the
       two ends of the coarse edge (cube edge or Kuhn face diagonal) they bisect;
@@ -87,7 +91,9 @@ def delta4(r):
 
 
 def inflow_peak(port, t):
-    """Peak inlet speed u_max(t) = a0 + sum_k a_k cos(k w t) + b_k sin(k w t)."""
+    """Port waveform a0 + sum_k a_k cos(k w t) + b_k sin(k w t): the peak inlet
+    speed u_max(t) of a velocity inlet, the pressure p_in(t) of a pressure
+    inlet."""
     w = 2.0 * math.pi / port["period"]
     u = port["a0"]
     for k, ak in enumerate(port["a"], start=1):
@@ -158,7 +164,8 @@ class Mesh:
     hanging: np.ndarray           # (N,) bool
     parents: np.ndarray           # (N, 2) parent nodes of hanging nodes (-1 else)
     boundary: np.ndarray          # (N,) bool, on the boundary of the active region
-    inlet: np.ndarray             # (N,) port index + 1 of an inlet port, 0 else
+    inlet: np.ndarray             # (N,) port index + 1 of a velocity-inlet port, 0 else
+    pinlet: np.ndarray            # (N,) port index + 1 of a pressure-inlet port, 0 else
     outlet: np.ndarray            # (N,) bool
     node_level: np.ndarray        # (N,) coarsest level among leaf cells touching the node
     dof: np.ndarray               # (N,) DOF index of non-hanging nodes (-1 for hanging)
@@ -275,7 +282,7 @@ def build_mesh(case):
     mesh = Mesh(case=case, L=L, n=n, origin=origin, h0=h0, hf=hf, point_cell=pc,
                 dist=dist, level=level, active=active, leaf_corner=leaf_corner,
                 leaf_size=leaf_size, node_q=node_q, node_x=node_x, tets=None,
-                hanging=None, parents=None, boundary=None, inlet=None, outlet=None,
+                hanging=None, parents=None, boundary=None, inlet=None, pinlet=None, outlet=None,
                 node_level=None, dof=None)
     mesh._keys = keys
 
@@ -360,6 +367,7 @@ def build_mesh(case):
 
     # R10: port nodes
     inlet = np.zeros(len(keys), dtype=np.int32)
+    pinlet = np.zeros(len(keys), dtype=np.int32)
     outlet = np.zeros(len(keys), dtype=bool)
     nfine = n * Lf
     for pi, port in enumerate(case["ports"]):
@@ -371,14 +379,18 @@ def build_mesh(case):
         d1 = node_x[:, o[1]] - port["center"][o[1]]
         r2 = d0 * d0
         r2 = r2 + d1 * d1
-        sel = on & boundary & (r2 <= port["radius"] * port["radius"]) & (inlet == 0) & ~outlet
+        sel = on & boundary & (r2 <= port["radius"] * port["radius"]) & (inlet == 0) & (pinlet == 0) & ~outlet
         if port["kind"] == "inlet":
             inlet[sel] = pi + 1
+        elif port["kind"] == "pinlet":
+            pinlet[sel] = pi + 1
         else:
             outlet[sel] = True
     inlet[hanging] = 0
+    pinlet[hanging] = 0
     outlet[hanging] = False
     mesh.inlet = inlet
+    mesh.pinlet = pinlet
     mesh.outlet = outlet
 
     # DOFs and the constraint matrix P (hanging node = mean of its parents)
@@ -400,8 +412,26 @@ def build_mesh(case):
 
 
 def velocity_dirichlet(mesh):
-    """Non-hanging nodes with a velocity condition: walls and inlets (R10)."""
-    return (mesh.boundary & ~mesh.outlet & ~mesh.hanging) | (mesh.inlet > 0)
+    """Non-hanging nodes with a velocity condition: walls and velocity inlets
+    (R10)."""
+    return (mesh.boundary & ~mesh.outlet & (mesh.pinlet == 0) & ~mesh.hanging) | (mesh.inlet > 0)
+
+
+def pressure_dirichlet(mesh):
+    """Nodes where Phi is prescribed: outlets and pressure inlets (R9)."""
+    return mesh.outlet | (mesh.pinlet > 0)
+
+
+def phi_dirichlet_values(mesh, t, p):
+    """Prescribed Phi at time t given the old pressure p (R9): p_in(t) - p on
+    pressure-inlet nodes, so that p^{n+1} = p^n + Phi equals p_in there; zero
+    on outlet nodes (and zero elsewhere)."""
+    g = np.zeros(mesh.n_nodes)
+    for pi, port in enumerate(mesh.case["ports"]):
+        sel = mesh.pinlet == pi + 1
+        if np.any(sel):
+            g[sel] = inflow_peak(port, t) - p[sel]
+    return g
 
 
 def dirichlet_velocity_values(mesh, t):
@@ -585,7 +615,7 @@ class Oracle:
         m = self.mesh
         self.vdir_node = velocity_dirichlet(m)
         self.vdir = self.vdir_node[~m.hanging]
-        self.pdir = m.outlet[~m.hanging]
+        self.pdir = pressure_dirichlet(m)[~m.hanging]
         free = ~self.vdir_node & ~m.hanging
         self.ib = IB(m, case, free)
         N = m.n_nodes
@@ -621,10 +651,12 @@ class Oracle:
         # Step 4, Eq. 14 (R2): u = u~ + dt f / rho, f from Eq. 19
         u = ut + (dt / rho) * self.ib.spread(F)
 
-        # Step 5, Eq. 12: (grad Phi, grad q) = -(1/dt) (div u, q), Phi = 0 at outlets
+        # Step 5, Eq. 12: (grad Phi, grad q) = -(1/dt) (div u, q), Phi = 0 at
+        # outlets and p_in(t^{n+1}) - p^n at pressure inlets (R9)
         div = sum(ops.G[k] @ u[:, k] for k in range(3))
         bp = (ops.PT @ (-(1.0 / dt) * div))[:, None]
-        phi = ops.P @ solve_dirichlet(self.Kc, bp, self.pdir, np.zeros_like(bp), symmetric=True,
+        gp = self._dof(phi_dirichlet_values(m, t1, self.p))[:, None]
+        phi = ops.P @ solve_dirichlet(self.Kc, bp, self.pdir, gp, symmetric=True,
                                       factor_cache=self._cache, key="K")[:, 0]
 
         # Step 6 (R1): (u^{n+1}, v) = (u, v) - dt (grad Phi, v); p^{n+1} = p^n + Phi

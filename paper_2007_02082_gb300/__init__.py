@@ -49,7 +49,10 @@ def _port_struct(port):
     for a in range(3):
         p.center[a] = port["center"][a]
     p.radius = port["radius"]
-    p.kind = _abi.IB_INLET_VELOCITY if port["kind"] == "inlet" else _abi.IB_OUTLET_ZERO_P
+    kinds = {"inlet": _abi.IB_INLET_VELOCITY, "pinlet": _abi.IB_INLET_PRESSURE, "outlet": _abi.IB_OUTLET_ZERO_P}
+    if port["kind"] not in kinds:
+        raise ValueError(f"unknown port kind {port['kind']!r}")
+    p.kind = kinds[port["kind"]]
     p.profile = 0
     p.a0 = port.get("a0", 0.0)
     a = list(port.get("a", ()))

@@ -7,7 +7,7 @@ import os
 IB_OK, IB_EINVAL, IB_ENOMEM, IB_ESTATE, IB_ENOCONV, IB_EBREAKDOWN, IB_ECUDA, IB_ETIMEOUT = range(8)
 STATUS_NAMES = {0: "IB_OK", 1: "IB_EINVAL", 2: "IB_ENOMEM", 3: "IB_ESTATE", 4: "IB_ENOCONV",
                 5: "IB_EBREAKDOWN", 6: "IB_ECUDA", 7: "IB_ETIMEOUT"}
-IB_INLET_VELOCITY, IB_OUTLET_ZERO_P = 0, 1
+IB_INLET_VELOCITY, IB_OUTLET_ZERO_P, IB_INLET_PRESSURE = 0, 1, 2
 IB_FP64, IB_MIXED = 0, 1
 IB_PC_MULTIGRID, IB_PC_JACOBI = 0, 1
 IB_MAX_PORTS, IB_MAX_HARMONICS, IB_MAX_LEVEL = 8, 8, 3

@@ -85,12 +85,13 @@ struct Engine {
   std::string err;
   // layout
   std::vector<int64_t> brick0, slot0, ns_i, row0, canon0;
-  int64_t nbricks = 0, ns = 0, Mtot = 0, n_inlet = 0, n_valid = 0;
+  int64_t nbricks = 0, ns = 0, Mtot = 0, n_inlet = 0, n_pinlet = 0, n_valid = 0;
   DevGrid g{};
   IBDev ib{};
   int32_t* canon = nullptr;        // concatenated canonical -> global slot
   int32_t *in_slot = nullptr, *in_port = nullptr;
   double* in_shape = nullptr;
+  int32_t *pin_slot = nullptr, *pin_port = nullptr;   // pressure-inlet copies and their ports
   PortDev* ports = nullptr;
   double *tc = nullptr, *tn = nullptr, *pdt = nullptr;
   int32_t* ok = nullptr;
@@ -370,7 +371,7 @@ ib_status engine_build(Engine& E) {
   if (E.ns > (int64_t(1) << 31) - 1) { E.err = "too many node slots for 32-bit indices"; return IB_EINVAL; }
 
   // ---- concatenated topology
-  std::vector<int32_t> blev, binst, bseg(n + 1), bnbr, ifc, iff, ifo(1, 0), ifk, ifos, hg, hp1, hp2, canon, ins, inp;
+  std::vector<int32_t> blev, binst, bseg(n + 1), bnbr, ifc, iff, ifo(1, 0), ifk, ifos, hg, hp1, hp2, canon, ins, inp, pins, pinp;
   std::vector<uint16_t> meta;
   std::vector<double> hl(size_t(n) * 12, 0.0), sf(size_t(n) * 32, 0.0), pdt(n), pnu(n), insh;
   std::vector<PortDev> ports;
@@ -423,6 +424,10 @@ ib_status engine_build(Engine& E) {
       inp.push_back(int32_t(H.inlet_port[k] + nport));
       insh.push_back(H.inlet_shape[k]);
     }
+    for (size_t k = 0; k < H.pinlet_slot.size(); ++k) {
+      pins.push_back(int32_t(H.pinlet_slot[k] + S0));
+      pinp.push_back(int32_t(H.pinlet_port[k] + nport));
+    }
     for (int q = 0; q < d.n_ports; ++q) {
       const ib_port& P = d.ports[q];
       PortDev pd{};
@@ -453,6 +458,7 @@ ib_status engine_build(Engine& E) {
   scseg[n] = int32_t(scbrick.size());
   scbrick.push_back(int32_t(E.nbricks));
   E.n_inlet = int64_t(ins.size());
+  E.n_pinlet = int64_t(pins.size());
   E.n_valid = 0;
   for (uint16_t m : meta)
     if (m & M_VALID) E.n_valid++;
@@ -506,6 +512,8 @@ ib_status engine_build(Engine& E) {
   TRY(upload(E, &E.in_slot, ins));
   TRY(upload(E, &E.in_port, inp));
   TRY(upload(E, &E.in_shape, insh));
+  TRY(upload(E, &E.pin_slot, pins));
+  TRY(upload(E, &E.pin_port, pinp));
   TRY(upload(E, &E.ports, ports));
   TRY(dalloc(E, &E.tc, n, true));
   TRY(dalloc(E, &E.tn, n, true));
@@ -746,10 +754,16 @@ cudaError_t enqueue_step(Engine& E, double* u, double* un, double* p, double* pn
     ib_spread(E.ib, E.Gf, E.uib, ns, st);
   }
 
-  // ---- Step 5: pressure increment (Eq. 12)
+  // ---- Step 5: pressure increment (Eq. 12); Phi = p_in(t^{n+1}) - p^n on
+  // pressure-inlet nodes (the solve keeps the Dirichlet values of its start).
+  // The warm start's hanging values are reset to the mean of their parents for
+  // every member, with or without a pressure inlet, so that a member's bits do
+  // not depend on the batch it runs in.
   double* rhs1 = E.rhs3;   // component 0 of the RHS buffer
   fe_rhs_div(dg, E.uib, rhs1, st);
   fe_sync<double>(dg, 1, rhs1, D_PDIR, st);
+  if (E.n_pinlet) fe_set_pinlet(E.n_pinlet, E.pin_slot, E.pin_port, E.ports, E.tn, p, E.phi, st);
+  fe_expand<double>(dg, 1, E.phi, st);
   e = solve_enqueue(solve_args(E, OP_POISSON, false, 1, D_PDIR, nullptr, E.dK64, nullptr, E.dK32, rhs1, E.phi,
                                tl.p, 2), st, cc);
   if (e != cudaSuccess) return e;
@@ -1000,9 +1014,9 @@ ib_status validate_desc(const ib_grid_desc* d) {
   for (int p = 0; p < d->n_ports; ++p) {
     const ib_port& P = d->ports[p];
     if (P.axis < 0 || P.axis > 2 || (P.side != 0 && P.side != 1) || !(P.radius > 0)) return IB_EINVAL;
-    if (P.kind != IB_INLET_VELOCITY && P.kind != IB_OUTLET_ZERO_P) return IB_EINVAL;
+    if (P.kind != IB_INLET_VELOCITY && P.kind != IB_OUTLET_ZERO_P && P.kind != IB_INLET_PRESSURE) return IB_EINVAL;
     if (P.n_harm < 0 || P.n_harm > IB_MAX_HARMONICS) return IB_EINVAL;
-    if (P.kind == IB_OUTLET_ZERO_P) outlet = true;
+    if (P.kind != IB_INLET_VELOCITY) outlet = true;   // a port that fixes Phi
   }
   if (!outlet) return IB_EINVAL;
   int64_t nf = (int64_t(d->n[0]) * d->n[1] * d->n[2]) << (3 * d->max_level);

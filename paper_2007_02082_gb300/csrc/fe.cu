@@ -371,17 +371,32 @@ __global__ void k_copy_to_fine(DevGrid g, int nc, double* __restrict__ x) {
   for (int c = 0; c < nc; ++c) x[c * g.nslots + g.if_f[e]] = x[c * g.nslots + g.if_c[e]];
 }
 
+// port waveform a0 + sum_k a_k cos(k w t) + b_k sin(k w t), w = 2 pi / period
+__device__ __forceinline__ double port_wave(const PortDev& P, double t) {
+  const double w = 2.0 * 3.14159265358979323846 / P.period;
+  double v = P.a0;
+  for (int k = 0; k < P.nh; ++k) v += P.a[k] * cos((k + 1) * w * t) + P.b[k] * sin((k + 1) * w * t);
+  return v;
+}
+
 __global__ void k_set_inlet(int64_t n, const int32_t* __restrict__ slot, const int32_t* __restrict__ port,
                             const double* __restrict__ shape, const PortDev* __restrict__ ports,
                             const double* __restrict__ tp, int64_t nslots, double* __restrict__ u) {
   KCOUNT();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const PortDev& P = ports[port[i]];
-    const double t = tp[P.inst];
-    const double w = 2.0 * 3.14159265358979323846 / P.period;
-    double um = P.a0;
-    for (int k = 0; k < P.nh; ++k) um += P.a[k] * cos((k + 1) * w * t) + P.b[k] * sin((k + 1) * w * t);
-    u[P.axis * nslots + slot[i]] = um * shape[i];
+    u[P.axis * nslots + slot[i]] = port_wave(P, tp[P.inst]) * shape[i];
+  }
+}
+// Phi = p_in(t^{n+1}) - p^n on every stored copy of a pressure-inlet node
+__global__ void k_set_pinlet(int64_t n, const int32_t* __restrict__ slot, const int32_t* __restrict__ port,
+                             const PortDev* __restrict__ ports, const double* __restrict__ tp,
+                             const double* __restrict__ p, double* __restrict__ phi) {
+  KCOUNT();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const PortDev& P = ports[port[i]];
+    const int32_t s = slot[i];
+    phi[s] = port_wave(P, tp[P.inst]) - p[s];
   }
 }
 // per instance: t_next = t_commit + dt, or (commit) t_commit = t_next where ok[i]
@@ -794,6 +809,10 @@ void fe_scatter_canon(const DevGrid& g, int64_t N, const int32_t* cs, int nc, co
   fe_expand<double>(g, nc, x, st);
 }
 
+void fe_set_pinlet(int64_t n, const int32_t* slot, const int32_t* port, const PortDev* ports, const double* t,
+                   const double* p, double* phi, cudaStream_t st) {
+  IBG_LAUNCH(k_set_pinlet, nblk(n), 256, 0, st, n, slot, port, ports, t, p, phi);
+}
 void fe_set_inlet(int64_t n, const int32_t* slot, const int32_t* port, const double* shape, const PortDev* ports,
                   const double* t, int64_t nslots, double* u, cudaStream_t st) {
   if (n == 0) return;

@@ -125,6 +125,8 @@ struct PortDev {
 };
 void fe_set_inlet(int64_t n, const int32_t* slot, const int32_t* port, const double* shape, const PortDev* ports,
                   const double* t, int64_t nslots, double* u, cudaStream_t st);
+void fe_set_pinlet(int64_t n, const int32_t* slot, const int32_t* port, const PortDev* ports, const double* t,
+                   const double* p, double* phi, cudaStream_t st);
 void fe_time_advance(double* t_commit, double* t_next, const double* dt, int n, int commit, const int32_t* ok,
                      cudaStream_t st);
 

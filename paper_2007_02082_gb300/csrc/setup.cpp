@@ -304,7 +304,7 @@ ib_status build_host_grid(const ib_grid_desc& d, int64_t M, const double* X, con
       bool bnd = on_boundary(G, q);
       if (bnd) cflag[s] |= C_BOUNDARY;
       if (G.meta[s] & M_HANG) { cflag[s] |= C_HANG; continue; }
-      int inlet = -1;
+      int inlet = -1, pinlet = -1;
       bool outlet = false;
       for (int p = 0; p < d.n_ports && bnd; ++p) {
         const ib_port& P = d.ports[p];
@@ -313,11 +313,17 @@ ib_status build_host_grid(const ib_grid_desc& d, int64_t M, const double* X, con
         double r2 = port_r2(G, P, q);
         if (!(r2 <= P.radius * P.radius)) continue;
         if (P.kind == IB_INLET_VELOCITY) { inlet = p; break; }
+        if (P.kind == IB_INLET_PRESSURE) { pinlet = p; break; }
         outlet = true;
         break;
       }
-      if (outlet) { G.meta[s] |= M_PDIR; cflag[s] |= C_PDIR; }
-      if ((bnd && !outlet) || inlet >= 0) { G.meta[s] |= M_VDIR; cflag[s] |= C_VDIR; }
+      if (outlet || pinlet >= 0) { G.meta[s] |= M_PDIR; cflag[s] |= C_PDIR; }
+      if ((bnd && !outlet && pinlet < 0) || inlet >= 0) { G.meta[s] |= M_VDIR; cflag[s] |= C_VDIR; }
+      if (pinlet >= 0) {
+        cflag[s] |= C_INLET;
+        G.pinlet_slot.push_back(int32_t(s));
+        G.pinlet_port.push_back(pinlet);
+      }
       if (inlet >= 0) {
         const ib_port& P = d.ports[inlet];
         cflag[s] |= C_INLET;
@@ -373,7 +379,10 @@ ib_status build_host_grid(const ib_grid_desc& d, int64_t M, const double* X, con
   }
   bool any_pdir = false;
   for (int64_t s = 0; s < nslots && !any_pdir; ++s) any_pdir = (G.meta[s] & M_PDIR) != 0;
-  if (!any_pdir) { err = "no outlet node: the pressure Poisson problem would be singular"; return IB_EINVAL; }
+  if (!any_pdir) {
+    err = "no outlet or pressure-inlet node: the pressure Poisson problem would be singular";
+    return IB_EINVAL;
+  }
 
   // ---- IB supports on the finest level (Eq. 17: 4x4x4 nodes per point)
   G.ib_origin.assign(3 * M, 0);

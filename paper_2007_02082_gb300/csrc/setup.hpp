@@ -77,6 +77,9 @@ struct HostGrid {
   std::vector<int32_t> inlet_slot;
   std::vector<int32_t> inlet_port;
   std::vector<double> inlet_shape;    // (1 - r^2/R^2) * (+1 low face, -1 high face)
+  // pressure-inlet Phi Dirichlet entries (every stored copy)
+  std::vector<int32_t> pinlet_slot;
+  std::vector<int32_t> pinlet_port;
   // IB
   int64_t M = 0;
   std::vector<double> X, dS, UB;      // copies of the inputs

@@ -19,6 +19,9 @@ def _cases():
         W.cylinder_refined_small(n=(16, 16, 8), seed=32),
         W.cylinder_case(n=(12, 12, 24), length=3.0, half_width=0.7, M=500, seed=33, nu=0.02, dt=0.005,
                         b=(0.5,), max_level=1, refine_band=2, reduce_band=2),
+        # pressure-driven member: its port indices and times are offset in the mix
+        W.cylinder_case(n=(8, 8, 16), length=2.0, M=250, seed=34, nu=0.05, dt=0.01, inlet=W.PINLET, a0=0.8,
+                        b=(0.2,)),
     ]
 
 
@@ -58,7 +61,7 @@ def test_state_carries_across_batches():
     """Member B steps 2 times with A, then 2 times with C: bitwise B stepped 4
     times alone (u, p and the warm starts Phi, F travel in the snapshot)."""
     from paper_2007_02082_gb300 import IBBatch, IBGrid
-    a, b, c = _cases()
+    a, b, c = _cases()[:3]
     ref = IBGrid(b, precision="mixed", deferred=True)
     rb = IBBatch([ref])
     rb.step(4)
@@ -104,7 +107,7 @@ def test_serving_loop_results_match_alone():
     cases = _cases()
     stream = []
     for k in range(6):
-        c = dict(cases[k % 3])
+        c = dict(cases[k % 4])
         c["steps"] = 3 + (k % 3) * 2
         stream.append((0.05 * k, c))
     got = {}

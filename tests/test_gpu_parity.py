@@ -29,6 +29,9 @@ def _cases():
         "two_levels": (W.cylinder_case(n=(24, 24, 8), length=1.0, half_width=0.75, M=1500, seed=12,
                                        max_level=2, refine_band=1, reduce_band=3, nu=0.02, dt=0.002,
                                        b=(0.5,)), 2),
+        # pressure inlet (Sec. 3.1's driving), pulsating, on a refined face; U_max ~ 1
+        "pressure_inlet": (W.cylinder_refined_small(n=(16, 16, 8), seed=23, inlet=W.PINLET, a0=0.16, b=(0.08,)),
+                           4),
     }
 
 
@@ -63,7 +66,8 @@ def test_structures_bit_exact(name):
     vdir = ibfe.velocity_dirichlet(m)
     free = ~vdir & ~m.hanging
     ib = ibfe.IB(m, case, free)
-    flags = (m.hanging * 1 + vdir * 2 + m.outlet * 4 + (m.inlet > 0) * 8 + m.boundary * 16).astype(np.uint8)
+    flags = (m.hanging * 1 + vdir * 2 + ibfe.pressure_dirichlet(m) * 4 + ((m.inlet > 0) | (m.pinlet > 0)) * 8
+             + m.boundary * 16).astype(np.uint8)
     assert np.array_equal(g.ib_fields_get("ACTIVE"), m.active.astype(np.uint8))
     assert np.array_equal(g.ib_fields_get("LEVEL"), m.level.astype(np.uint8))
     assert np.array_equal(g.ib_fields_get("NODE_Q"), m.node_q.astype(np.int32))
@@ -99,7 +103,7 @@ def test_fp64_step_parity(name):
     g.close()
 
 
-@pytest.mark.parametrize("name", ["uniform", "refined"])
+@pytest.mark.parametrize("name", ["uniform", "refined", "pressure_inlet"])
 def test_mixed_step_parity(name):
     _, steps = CASES[name]
     o, hist = oracle_run(name)
@@ -130,6 +134,25 @@ def test_noslip_and_constraints_hold_on_gpu():
     assert np.abs(u[h] - 0.5 * (u[par[:, 0]] + u[par[:, 1]])).max() < 1e-14
     phi = g.ib_fields_get("PHI")
     assert np.all(phi[m.outlet] == 0.0)
+    g.close()
+
+
+def test_pressure_inlet_holds_port_pressure_on_gpu():
+    """After every step p equals the imposed inlet pressure at t^{n+1} on every
+    pressure-inlet node and zero on the outlet (Phi Dirichlet values of R9)."""
+    case, _ = CASES["pressure_inlet"]
+    g = gpu_grid("pressure_inlet", "fp64")
+    flags = g.ib_fields_get("NODE_FLAGS")
+    pin = ((flags & 4) != 0) & ((flags & 8) != 0)
+    out = ((flags & 4) != 0) & ((flags & 8) == 0)
+    assert pin.sum() > 0 and out.sum() > 0 and not np.any(flags[pin] & 2)
+    for _ in range(3):
+        g.ipcs_step(1)
+        t = g.ib_grid_info()["time"]
+        want = 0.16 + 0.08 * np.sin(2.0 * np.pi * t)
+        p = g.ib_fields_get("P")
+        assert np.abs(p[pin] - want).max() <= 1e-15
+        assert np.all(p[out] == 0.0)
     g.close()
 
 

@@ -113,7 +113,8 @@ def oracle_structures(case):
     vdir = ibfe.velocity_dirichlet(m)
     free = ~vdir & ~m.hanging
     ib = ibfe.IB(m, case, free)
-    flags = (m.hanging * 1 + vdir * 2 + m.outlet * 4 + (m.inlet > 0) * 8 + m.boundary * 16).astype(np.uint8)
+    flags = (m.hanging * 1 + vdir * 2 + ibfe.pressure_dirichlet(m) * 4 + ((m.inlet > 0) | (m.pinlet > 0)) * 8
+             + m.boundary * 16).astype(np.uint8)
     exists = ib.support_idx >= 0
     fr = np.where(exists, np.where(free[np.maximum(ib.support_idx, 0)], 1, 2), 0).astype(np.uint8)
     return m, flags, ib.origin, fr
@@ -128,6 +129,8 @@ CASES = {
                                                   max_level=2, refine_band=1, reduce_band=3),
     "aneurysm_L1": lambda: W.aneurysm_case(length=1.5, h=1.0 / 12, seed=13),
     "bend_L0": lambda: W.bent_tube_case(R=0.4, Rc=1.0, l_in=0.5, l_out=0.5, h=1.0 / 10, seed=14),
+    # pressure inlet on a refined face: port nodes next to hanging nodes
+    "pressure_inlet_refined": lambda: W.cylinder_refined_small(n=(16, 16, 8), seed=23, inlet=W.PINLET, a0=0.16),
 }
 
 

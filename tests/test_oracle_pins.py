@@ -234,8 +234,9 @@ def test_noslip_exact_after_correction():
 
 
 # ---------------------------------------------------------------- the full step
-def _poiseuille(n, M, steps=20, dt=0.05):
-    c = W.cylinder_case(n=n, M=M, dt=dt)
+def _poiseuille(n, M, steps=20, dt=0.05, inlet=W.INLET):
+    # U_max = R^2 dp / (4 nu L) = 1 for R = 0.5, nu = 0.1, L = 4 and dp = 6.4
+    c = W.cylinder_case(n=n, M=M, dt=dt, inlet=inlet, a0=6.4 if inlet == W.PINLET else 1.0)
     m = ibfe.build_mesh(c)
     x = m.node_x
     r2 = x[:, 0] ** 2 + x[:, 1] ** 2
@@ -281,3 +282,58 @@ def test_projection_reduces_divergence_and_flux_balances():
     qin, qout = flux(0), flux(m.n[2])
     assert qin > 0.2
     assert abs(qin - qout) < 0.1 * qin
+
+
+# ---------------------------------------------------------------- pressure inlet
+def test_pressure_driven_poiseuille_error_falls_under_refinement():
+    """Sec. 3.1 drives its tube by the inlet pressure (p_outlet = 0).  With
+    p_in = 6.4 over L = 4, nu = 0.1 and R = 0.5 the exact flow is again
+    u_z = 1 - 4 r^2 (U_max = R^2 dp / (4 nu L)), now with a free inlet
+    velocity; the discrete solution started from it stays close, its RMSE
+    falling at least first order when h halves."""
+    _, e1 = _poiseuille((8, 8, 32), 300, steps=20, inlet=W.PINLET)
+    _, e2 = _poiseuille((16, 16, 64), 1200, steps=20, inlet=W.PINLET)
+    assert e2 < 0.05
+    assert math.log2(e1 / e2) > 1.0
+
+
+def test_pressure_inlet_imposes_the_port_pressure():
+    """Started from rest with a pulsating inlet pressure 6.4 + sin(pi t): after
+    every step p equals the imposed pressure at t^{n+1} on the port nodes and
+    zero on the outlet, the port nodes carry no velocity condition, and the
+    fluid moves from the high to the low pressure."""
+    c = W.cylinder_case(n=(8, 8, 32), M=300, dt=0.05, inlet=W.PINLET, a0=6.4, b=(1.0,), period=2.0)
+    o = ibfe.Oracle(c)
+    m = o.mesh
+    pin = m.pinlet > 0
+    assert pin.sum() == 37 and not np.any(m.inlet > 0)
+    assert not np.any(ibfe.velocity_dirichlet(m)[pin]) and np.all(ibfe.pressure_dirichlet(m)[pin])
+    for _ in range(4):
+        o.step()
+        want = 6.4 + math.sin(math.pi * o.t)
+        assert np.abs(o.p[pin] - want).max() <= 4e-16 * want
+        assert np.all(o.p[m.outlet] == 0.0)
+    r2 = m.node_x[:, 0] ** 2 + m.node_x[:, 1] ** 2
+    tube = r2 < 0.4 ** 2
+    assert o.u[pin & tube, 2].min() > 0.1
+    assert o.u[tube, 2].mean() > 0.1
+
+
+def test_zero_pressure_inlet_is_an_outlet():
+    """With p_in = 0 and p = 0 on the port, a pressure inlet's conditions (Phi =
+    p_in - p^n = 0, no velocity condition) are the do-nothing outlet's: the two
+    runs agree bit for bit (a decaying Poiseuille start between two
+    zero-pressure ends)."""
+    runs = []
+    for kind in (W.PINLET, W.OUTLET):
+        c = W.cylinder_case(n=(8, 8, 32), M=300, dt=0.05, inlet=kind, a0=0.0)
+        m = ibfe.build_mesh(c)
+        r2 = m.node_x[:, 0] ** 2 + m.node_x[:, 1] ** 2
+        u0 = np.zeros((m.n_nodes, 3))
+        u0[:, 2] = np.where(r2 < 0.25, 1.0 - 4.0 * r2, 0.0)
+        o = ibfe.Oracle(c, u0=u0).run(3)
+        runs.append((o.u, o.p, o.mesh.pinlet > 0, o.mesh.outlet))
+    (ua, pa, pin, outa), (ub, pb, _, outb) = runs
+    assert pin.sum() > 0 and np.array_equal(pin | outa, outb)
+    assert np.array_equal(ua, ub) and np.array_equal(pa, pb)
+    assert np.abs(ua[:, 2]).max() > 0.1

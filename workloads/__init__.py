@@ -9,9 +9,10 @@ the method's arithmetic (no delta kernel, no element integrals, no solver).
 Conventions shared by every consumer:
   * coarse-cell arrays are numpy arrays shaped [nz, ny, nx] (x fastest);
   * a port is a disc on a box face: axis (0/1/2), side (0 = low face, 1 = high
-    face), centre, radius, kind ('inlet' | 'outlet'), and for an inlet a
-    parabolic profile of peak u_max(t) = a0 + sum_k a_k cos(2 pi k t / T)
-    + b_k sin(2 pi k t / T);
+    face), centre, radius, kind ('inlet' | 'pinlet' | 'outlet') and a waveform
+    w(t) = a0 + sum_k a_k cos(2 pi k t / T) + b_k sin(2 pi k t / T): the peak
+    of the parabolic profile of a velocity inlet ('inlet'), the imposed
+    pressure of a pressure inlet ('pinlet'); an outlet holds zero pressure;
   * the area element follows the paper's uniform rule (Sec. 2.5): every point
     carries dS = (wall area) / M.
 Point sampling is stratified jitter: M equal-area strata in (theta, z), one
@@ -25,6 +26,7 @@ import math
 import numpy as np
 
 INLET = "inlet"
+PINLET = "pinlet"
 OUTLET = "outlet"
 
 
@@ -67,7 +69,7 @@ def cell_centres(origin, extent, n):
 def cylinder_case(n=(16, 16, 64), R=0.5, length=4.0, half_width=0.6, M=2000,
                   seed=1, max_level=0, refine_band=2, reduce_band=-1,
                   nu=0.1, dt=0.01, steps=50, a0=1.0, b=(), period=1.0,
-                  name=None):
+                  name=None, inlet=INLET):
     """Straight tube of radius R along z, immersed in [-w, w]^2 x [0, length].
 
     Defaults: the uniform 16x16x64 cylinder, nu = 0.1, dt = 0.01, steady
@@ -75,6 +77,9 @@ def cylinder_case(n=(16, 16, 64), R=0.5, length=4.0, half_width=0.6, M=2000,
     ratio a = sqrt(dS)/h at 1.06 (x, y) and 1.27 (z), the regime of the paper's
     Table 1 (a = 0.98).  At M = 4000 (a = 0.75) the force matrix A_F of Eq. 22 is
     numerically rank-deficient on this grid (Sec. 2.5 warns of exactly this).
+    inlet = PINLET drives the flow by the inlet pressure a0 (+ harmonics)
+    instead; a0 = 16 nu L / R^2 (6.4 with the defaults) gives the same
+    Poiseuille flow of peak 1 (the pressure-driven tube of Sec. 3.1).
     """
     origin = (-half_width, -half_width, 0.0)
     extent = (2.0 * half_width, 2.0 * half_width, float(length))
@@ -82,7 +87,7 @@ def cylinder_case(n=(16, 16, 64), R=0.5, length=4.0, half_width=0.6, M=2000,
     xc, yc, zc = cell_centres(origin, extent, n)
     inside = (np.hypot(xc, yc) < R).astype(np.uint8)
     ports = [
-        _port(2, 0, (0.0, 0.0, 0.0), R, INLET, a0=a0, b=b, period=period),
+        _port(2, 0, (0.0, 0.0, 0.0), R, inlet, a0=a0, b=b, period=period),
         _port(2, 1, (0.0, 0.0, length), R, OUTLET),
     ]
     return {
