@@ -148,7 +148,8 @@ def class_bytes(cls, vb, multigrid=False):
 CLASS_NAMES = {0: "k_poisson_cg (p = z + beta p, q = K p, fused p.q)", 1: "k_cg_update<Poisson>",
                2: "k_cg_p<Poisson>", 3: "k_apply15<mass> (fused p = z + beta p, p.q)", 4: "k_cg_update<mass>",
                5: "k_cg_p<mass>",
-               6: "k_apply15<momentum> (15-point coefficients, 3 comps)", 7: "k_bcgv_xr<momentum>",
+               6: "momentum apply, 15 coefficients, 3 comps (k_apply15_mom32 on the mixed path)",
+               7: "k_bcgv_xr<momentum>",
                8: "k_bcgv_p<momentum>", 9: "k_poisson_cg<apply> (V-cycle smoothing stencil)",
                10: "k_mg_c_smooth (V-cycle smoothing update)", 11: "V-cycle transfers and coarse levels"}
 

@@ -32,6 +32,7 @@
 #include <string>
 #include <vector>
 
+#include "async.cuh"
 #include "fe.hpp"
 #include "ib.h"
 #include "ib.hpp"
@@ -85,7 +86,7 @@ struct Engine {
   std::string err;
   // layout
   std::vector<int64_t> brick0, slot0, ns_i, row0, canon0;
-  int64_t nbricks = 0, ns = 0, Mtot = 0, n_inlet = 0, n_pinlet = 0, n_valid = 0;
+  int64_t nbricks = 0, ns = 0, Mtot = 0, n_inlet = 0, n_pinlet = 0, n_valid = 0, ncomp = 0;
   DevGrid g{};
   IBDev ib{};
   int32_t* canon = nullptr;        // concatenated canonical -> global slot
@@ -95,6 +96,8 @@ struct Engine {
   PortDev* ports = nullptr;
   double *tc = nullptr, *tn = nullptr, *pdt = nullptr;
   int32_t* ok = nullptr;
+  int32_t* aerr = nullptr;        // [ninst] device error word of the step
+  int32_t* aerr_host = nullptr;   // pinned copy
   // fields [3][ns] / [ns]
   double *ubuf[2] = {nullptr, nullptr}, *pbuf[2] = {nullptr, nullptr};
   double *u = nullptr, *un = nullptr, *p = nullptr, *pn = nullptr, *phi = nullptr, *ut = nullptr, *uib = nullptr;
@@ -222,6 +225,7 @@ void engine_free(Engine& E) {
   if (E.os_host) { cudaFreeHost(E.os_host); E.os_host = nullptr; }
   if (E.recs_host) { cudaFreeHost(E.recs_host); E.recs_host = nullptr; }
   if (E.ok_host) { cudaFreeHost(E.ok_host); E.ok_host = nullptr; }
+  if (E.aerr_host) { cudaFreeHost(E.aerr_host); E.aerr_host = nullptr; }
 }
 
 // Concatenate the members' multigrid hierarchies level by level and upload
@@ -462,6 +466,20 @@ ib_status engine_build(Engine& E) {
   E.n_valid = 0;
   for (uint16_t m : meta)
     if (m & M_VALID) E.n_valid++;
+  // compact arrays: per brick a run of its valid slots, starting on a multiple of 4
+  std::vector<int32_t> cwo(16 * (E.nbricks + 1));
+  int64_t ncomp = 0;
+  for (int64_t b = 0; b < E.nbricks; ++b) {
+    ncomp = (ncomp + 3) & ~int64_t(3);
+    for (int w = 0; w < 16; ++w) {
+      cwo[16 * b + w] = int32_t(ncomp);
+      for (int l = 0; l < 32; ++l) ncomp += (meta[b * 512 + w * 32 + l] & M_VALID) ? 1 : 0;
+    }
+  }
+  ncomp = (ncomp + 3) & ~int64_t(3);
+  if (ncomp >= (int64_t(1) << 31) / 15) { E.err = "grid too large for the compact coefficient arrays"; return IB_EINVAL; }
+  for (int w = 0; w < 16; ++w) cwo[16 * E.nbricks + w] = int32_t(ncomp);
+  E.ncomp = ncomp;
 
   DevGrid& g = E.g;
   g = DevGrid();
@@ -496,6 +514,12 @@ ib_status engine_build(Engine& E) {
   TRY(upload(E, &d_hg, hg));
   TRY(upload(E, &d_hp1, hp1));
   TRY(upload(E, &d_hp2, hp2));
+  int32_t* d_cwo;
+  TRY(upload(E, &d_cwo, cwo));
+  TRY(dalloc(E, &E.aerr, n, true));
+  g.cwo = d_cwo;
+  g.ncomp = E.ncomp;
+  g.aerr = E.aerr;
   g.blev = d_blev; g.binst = d_binst; g.bseg = d_bseg; g.bnbr = d_bnbr; g.meta = d_meta;
   g.nchunks = int32_t(cbrick.size()) - 1;
   g.cbrick = d_cbrick;
@@ -538,7 +562,7 @@ ib_status engine_build(Engine& E) {
   TRY(dalloc(E, &E.dM64, ns, true));
   TRY(dalloc(E, &E.dA64, ns, true));
   if (E.mixed) {
-    TRY(dalloc(E, &E.coef32, 15 * ns, true));
+    TRY(dalloc(E, &E.coef32, 15 * E.ncomp, true));   // compact layout (valid slots only)
     TRY(dalloc(E, &E.diag32, ns, true));
     TRY(dalloc(E, &E.dK32, ns, true));
     TRY(dalloc(E, &E.dM32, ns, true));
@@ -549,6 +573,7 @@ ib_status engine_build(Engine& E) {
   }
 
   // ---- Poisson multigrid, in the precision of the inner Krylov iterations
+  CK(fe_configure());
   if (E.mixed) TRY(mg_upload<float>(E, E.mg32));
   else TRY(mg_upload<double>(E, E.mg64));
 
@@ -652,6 +677,7 @@ ib_status engine_build(Engine& E) {
   CK(cudaMallocHost(&E.os_host, n * sizeof(OState)));
   CK(cudaMallocHost(&E.recs_host, 4 * n * sizeof(SolveRec)));
   CK(cudaMallocHost(&E.ok_host, n * sizeof(int32_t)));
+  CK(cudaMallocHost(&E.aerr_host, n * sizeof(int32_t)));
   for (int k = 0; k < 4; ++k) {
     cudaStream_t s2;
     CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
@@ -731,6 +757,7 @@ cudaError_t enqueue_step(Engine& E, double* u, double* un, double* p, double* pn
   cudaError_t e;
 
   rec_clear(E.recs, 4 * E.ninst, st);
+  if ((e = cudaMemsetAsync(E.aerr, 0, E.ninst * sizeof(int32_t), st)) != cudaSuccess) return e;
   fe_time_advance(E.tc, E.tn, E.pdt, E.ninst, 0, nullptr, st);
   // ---- Step 1: tentative velocity (Eq. 9)
   fe_momentum_coef(dg, u, E.coef64, E.mixed ? E.coef32 : nullptr, st);
@@ -777,6 +804,8 @@ cudaError_t enqueue_step(Engine& E, double* u, double* un, double* p, double* pn
   if (e != cudaSuccess) return e;
   fe_copy_d(ns, p, pn, st);
   fe_add_d(ns, E.phi, pn, st);
+  e = cudaMemcpyAsync(E.aerr_host, E.aerr, E.ninst * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
   return cudaMemcpyAsync(E.recs_host, E.recs, 4 * E.ninst * sizeof(SolveRec), cudaMemcpyDeviceToHost, st);
 }
 
@@ -827,6 +856,7 @@ ib_status engine_step(Engine& E) {
     ib_info& I = E.last[i];
     int status = 0;
     for (int k = 0; k < 4; ++k) status = std::max(status, int(R[k].status));
+    status = std::max(status, int(E.aerr_host[i]));   // a bounded wait that ran out
     for (int c = 0; c < 3; ++c) {
       I.iters_mom[c] = R[0].iters[c];
       I.iters_corr[c] = R[3].iters[c];
@@ -866,6 +896,10 @@ ib_status engine_step(Engine& E) {
   fe_time_advance(E.tc, E.tn, E.pdt, E.ninst, 1, any_fail ? E.ok : nullptr, st);
   if (any_fail) CK(cudaStreamSynchronize(st));
   if (worst) {
+    if (worst == ASYNC_TIMEOUT) {
+      E.err = "internal: an asynchronous copy of a step kernel did not complete within its wait limit";
+      return IB_ETIMEOUT;
+    }
     E.err = worst == 5 ? "Krylov breakdown in a step solve" : "a step solve did not converge";
     return worst == 5 ? IB_EBREAKDOWN : IB_ENOCONV;
   }

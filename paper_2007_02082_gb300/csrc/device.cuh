@@ -100,7 +100,24 @@ struct DevGrid {
   const int32_t* __restrict__ hg;
   const int32_t* __restrict__ hp1;
   const int32_t* __restrict__ hp2;
+  // compact per-slot arrays (valid slots only, brick by brick): cwo[16 b + w]
+  // is the index of the first valid slot of warp w of brick b; a brick's run
+  // starts on a multiple of 4 entries (16 bytes in FP32) and ends where the
+  // next brick's starts; cwo[16 nbricks] = ncomp, the plane stride
+  const int32_t* __restrict__ cwo;    // [16 (nbricks + 1)]
+  int64_t ncomp;
+  // per-instance error word of the step (ASYNC_TIMEOUT when a bounded wait ran out)
+  int32_t* aerr;                      // [ninst]
 };
+
+// Index in the compact arrays of thread t's slot of brick b (a valid slot);
+// every lane of the warp must call it (warp ballot).
+__device__ __forceinline__ int32_t compact_index(const DevGrid& g, int b, int t, bool valid) {
+  const unsigned bal = __ballot_sync(0xffffffffu, valid);
+  unsigned lt;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+  return g.cwo[16 * b + (t >> 5)] + __popc(bal & lt);
+}
 
 // Krylov scalars of one right-hand side (one velocity component or Phi).
 struct KState {

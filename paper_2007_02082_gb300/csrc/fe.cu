@@ -14,6 +14,7 @@
 #include <cstring>
 #include <vector>
 
+#include "async.cuh"
 #include "fe.hpp"
 #include "kuhn_weights.hpp"
 
@@ -116,6 +117,9 @@ __global__ void __launch_bounds__(512) k_diag(DevGrid g, const T* __restrict__ c
   KCOUNT();
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
   const uint16_t m = g.meta[s];
+  // FP32 momentum coefficients are stored compactly (valid slots only)
+  constexpr bool compact = OP != OP_POISSON && OP != OP_MASS && sizeof(T) == 4;
+  const int64_t ci = compact ? compact_index(g, blockIdx.x, threadIdx.x, (m & D_VALID) != 0) : s;
   T d = T(0);
   if (m & D_VALID) {
     const T* F = stencil_factors<T>(g, blockIdx.x);
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(512) k_diag(DevGrid g, const T* __restrict__ c
           T(stiff_edge_count(mask, 1, 1) + stiff_edge_count(mask, 1, -1)) * F[1] +
           T(stiff_edge_count(mask, 2, 1) + stiff_edge_count(mask, 2, -1)) * F[2];
     else if (OP == OP_MASS) d = T(mass_weight(mask, 0)) * F[3];
-    else d = coef[s];
+    else d = coef[ci];
   }
   diag[s] = d;
 }
@@ -316,10 +320,12 @@ __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __res
 #pragma unroll
     for (int k = 0; k < 15; ++k) cf[k] += double(cc[k]);
   }
+  // FP32 copy in the compact layout (valid slots only) read by k_apply15_mom32
+  const int64_t ci = coef32 ? compact_index(g, b, t, (m & D_VALID) != 0) : 0;
 #pragma unroll
   for (int k = 0; k < 15; ++k) {
     coef[(int64_t)k * g.nslots + s] = cf[k];
-    if (coef32) coef32[(int64_t)k * g.nslots + s] = float(cf[k]);
+    if (coef32 && (m & D_VALID)) coef32[(int64_t)k * g.ncomp + ci] = float(cf[k]);
   }
 }
 
@@ -698,6 +704,76 @@ __global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict_
     }
 }
 
+// FP32 momentum operator, 3 components (the inner BiCGStab of the mixed path),
+// one CTA per brick, four CTAs per SM:
+//  * the 15 coefficient planes are stored compactly (valid slots only; per
+//    brick a run starting on a 16-byte boundary); warp 0 copies them into
+//    shared memory with bulk asynchronous copies (cp.async.bulk, completion on
+//    an mbarrier) issued first, so they are in flight together with the
+//    brick's x values and halo, and no register holds a coefficient in transit;
+//  * the tile holds one float4 per node (3 components and a pad), so each
+//    stencil neighbour is one 16-byte shared load.
+// Same arithmetic, in the same order, as k_apply15<float, OP_COEF, 3>.
+__global__ void __launch_bounds__(512, 4) k_apply15_mom32(DevGrid g, const float* __restrict__ x,
+                                                          float* __restrict__ y, const float* __restrict__ coef,
+                                                          uint16_t dmask) {
+  KCOUNT();
+  __shared__ __align__(16) float cf[15 * DBV];
+  __shared__ float4 tile[TILE3];
+  __shared__ __align__(8) uint64_t bar;
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int32_t c0 = g.cwo[16 * b];
+  if (t < 32) {
+    const uint32_t bytes = uint32_t(g.cwo[16 * (b + 1)] - c0) * 4u;   // a multiple of 16, at most 2 KB
+    if (t == 0) {
+      mbar_init(&bar);
+      mbar_arrive_expect_tx(&bar, 15u * bytes);
+    }
+    __syncwarp();
+    if (t < 15 && bytes) bulk_g2s(cf + t * DBV, coef + (int64_t)t * g.ncomp + c0, bytes, &bar);
+  }
+  const int64_t s = (int64_t)b * DBV + t;
+  const uint16_t m = g.meta[s];
+  const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
+  int hnb = 13, hli = 0, hti = 0;
+  if (t < HALO15) halo15(t, hnb, hli, hti);
+  float vo[3], vh[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) vo[c] = x[(int64_t)c * g.nslots + s];
+  if (t < HALO15) {
+    const int nb = g.bnbr[27 * b + hnb];
+    if (nb >= 0) {
+      const int64_t hs = (int64_t)nb * DBV + hli;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) vh[c] = x[(int64_t)c * g.nslots + hs];
+    }
+  }
+  tile[ti] = make_float4(vo[0], vo[1], vo[2], 0.f);
+  if (t < HALO15) tile[hti] = make_float4(vh[0], vh[1], vh[2], 0.f);
+  const bool valid = (m & D_VALID) != 0;
+  const int32_t r = compact_index(g, b, t, valid) - c0;
+  // one thread waits for the copies (every thread spinning on the mbarrier
+  // would crowd the shared-memory pipe); the CTA barrier then orders the
+  // copied coefficients before every thread's reads
+  if (t == 0) mbar_wait_or_flag(&bar, 0, g.aerr + g.binst[b]);
+  __syncthreads();
+  float out[3] = {0.f, 0.f, 0.f};
+  if (valid && !(m & dmask)) {
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+      const float ck = cf[k * DBV + r];
+      const float4 v = tile[ti + c_toff[k]];
+      out[0] += ck * v.x;
+      out[1] += ck * v.y;
+      out[2] += ck * v.z;
+    }
+  }
+  if (valid) {   // brick padding stays zero: no store
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[(int64_t)c * g.nslots + s] = out[c];
+  }
+}
+
 template <typename T, int NC, bool FUSEP = false>
 static void launch_apply(const DevGrid& g, int op, const T* x, T* y, const T* coef, uint16_t dmask, int post,
                          KState* ks, RedBuf rb, cudaStream_t st, const T* zf = nullptr, T* pnew = nullptr) {
@@ -712,6 +788,8 @@ static void launch_apply(const DevGrid& g, int op, const T* x, T* y, const T* co
   else if (op == OP_MASS)
     IBG_LAUNCH((k_apply15<T, OP_MASS, NC, FUSEP, true>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
                rb.partials, rb.counter, zf, pnew);
+  else if constexpr (sizeof(T) == 4 && NC == 3 && !FUSEP)
+    IBG_LAUNCH(k_apply15_mom32, g.nbricks, DBV, 0, st, g, x, y, coef, dmask);
   else
     IBG_LAUNCH((k_apply15<T, OP_COEF, NC, FUSEP, true>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
                rb.partials, rb.counter, zf, pnew);
@@ -792,6 +870,12 @@ void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double
 void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st) {
   IBG_LAUNCH(k_rhs_div, g.nbricks, DBV, 0, st, g, u, out);
 }
+cudaError_t fe_configure() {
+  // four 46 KB CTAs per SM: prefer the largest shared-memory carveout
+  return cudaFuncSetAttribute(k_apply15_mom32, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              int(cudaSharedmemCarveoutMaxShared));
+}
+
 void fe_momentum_coef(const DevGrid& g, const double* u, double* coef64, float* coef32, cudaStream_t st) {
   // the mixed path (coef32 given) evaluates the convection part in FP32
   if (coef32) IBG_LAUNCH(k_mom_coef<float>, g.nbricks, DBV, 0, st, g, u, coef64, coef32);

@@ -109,6 +109,8 @@ void fe_sync(const DevGrid& g, int nc, T* y, uint16_t dmask, cudaStream_t st);
 void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double* out, cudaStream_t st);
 void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st);
 void fe_momentum_coef(const DevGrid& g, const double* u, double* coef64, float* coef32, cudaStream_t st);
+// once per process and device: kernel attributes (shared-memory carveout)
+cudaError_t fe_configure();
 
 // Copy canonical node values (owner slots) out / in; in also writes the fine
 // copy of every interface node.
