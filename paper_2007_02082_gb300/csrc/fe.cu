@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "async.cuh"
@@ -63,6 +64,26 @@ __device__ __forceinline__ void grad_weights(int mask, int (&gw)[15][3]) {
     for (int a = 0; a < 3; ++a) gw[k][a] = grad_weight(mask, k, a);
 }
 
+// Warp-uniform dispatch on the incident-cell mask.  Where every lane's eight
+// incident cells are active (the bulk of a grid) the body runs with the mask as
+// a compile-time constant: every closed-form weight folds to a constant, zero
+// couplings drop out, and no integer weight is converted at run time (a
+// conversion to FP64 costs as much as an FP64 FMA).  Elsewhere the body runs
+// with the runtime mask.  Every lane of the warp must call it.
+struct FullMask {
+  __host__ __device__ constexpr operator int() const { return 0xFF; }
+};
+template <typename Body>
+__device__ __forceinline__ void with_mask(int mask, Body&& body) {
+  if (__all_sync(0xffffffffu, mask == 0xFF)) body(FullMask{});
+  else body(mask);
+}
+// true when the mask argument of a with_mask body is the compile-time constant
+template <typename MK>
+__device__ __forceinline__ constexpr bool const_mask() {
+  return !std::is_same_v<std::decay_t<MK>, int>;
+}
+
 __device__ __forceinline__ void spacing(const DevGrid& g, int b, double (&h)[3]) {
   const int inst = g.binst[b], lev = g.blev[b];
   const double* p = g.hl + (inst * 4 + lev) * 3;
@@ -78,20 +99,30 @@ enum Post : int { POST_NONE = 0, POST_CG_ALPHA = 1 };
 
 // Interface sum of an operator output: both stored copies get the sum of their
 // level parts plus half of each hanging child's; rows with a dmask bit are zeroed.
+// The indices are loaded once and every component's values together, so one
+// entry costs three dependent loads (indices, values and children's slots,
+// children's values) whatever NC is.
 template <typename T, int NC>
 __global__ void k_sync(DevGrid g, T* __restrict__ y, uint16_t dmask) {
   KCOUNT();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.n_if) return;
   const int32_t sc = g.if_c[e], sf = g.if_f[e];
+  const int32_t k0 = g.if_off[e], k1 = g.if_off[e + 1];
   const bool zero = (g.meta[sc] & dmask) != 0;
+  T tot[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) tot[c] = y[c * g.nslots + sc] + y[c * g.nslots + sf];
+  for (int k = k0; k < k1; ++k) {
+    const int32_t kid = g.if_kid[k];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) tot[c] += T(0.5) * y[c * g.nslots + kid];
+  }
+#pragma unroll
   for (int c = 0; c < NC; ++c) {
-    T* yc = y + c * g.nslots;
-    T tot = yc[sc] + yc[sf];
-    for (int k = g.if_off[e]; k < g.if_off[e + 1]; ++k) tot += T(0.5) * yc[g.if_kid[k]];
-    if (zero) tot = T(0);
-    yc[sc] = tot;
-    yc[sf] = tot;
+    const T v = zero ? T(0) : tot[c];
+    y[c * g.nslots + sc] = v;
+    y[c * g.nslots + sf] = v;
   }
 }
 
@@ -158,29 +189,29 @@ __global__ void __launch_bounds__(512) k_rhs_mass_grad(DevGrid g, const double* 
   const int t = threadIdx.x;
   const int64_t s = (int64_t)b * DBV + t;
   const uint16_t m = g.meta[s];
+  const bool valid = (m & D_VALID) != 0;
   double o[3] = {0, 0, 0};
-  if (m & D_VALID) {
-    const int mask = m & 0xFF;
+  with_mask(valid ? (m & 0xFF) : 0, [&](auto mk) {
+    if (!valid) return;
     const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
     const double* F = stencil_factors<double>(g, b);
     const double dt = g.pdt[g.binst[b]];
     double gp[3] = {0, 0, 0};
-    int gw[15][3];
-    grad_weights(mask, gw);
 #pragma unroll
     for (int k = 0; k < 15; ++k) {
       const int j = ti + c_toff[k];
-      const double mw = double(mass_weight(mask, k));
+      const int mw = mass_weight(mk, k);
       const double pk = tile[3 * TILE3 + j];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        o[a] += mw * tile[a * TILE3 + j];
-        gp[a] += double(gw[k][a]) * pk;
+        if (!const_mask<decltype(mk)>() || mw != 0) o[a] += double(mw) * tile[a * TILE3 + j];
+        const int gw = grad_weight(mk, k, a);
+        if (!const_mask<decltype(mk)>() || gw != 0) gp[a] += double(gw) * pk;
       }
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) o[a] = F[3] * o[a] - dt * F[4 + a] * gp[a];
-  }
+  });
   for (int a = 0; a < 3; ++a) out[a * g.nslots + s] = o[a];
 }
 
@@ -194,22 +225,24 @@ __global__ void __launch_bounds__(512) k_rhs_div(DevGrid g, const double* __rest
   const int t = threadIdx.x;
   const int64_t s = (int64_t)b * DBV + t;
   const uint16_t m = g.meta[s];
+  const bool valid = (m & D_VALID) != 0;
   double o = 0.0;
-  if (m & D_VALID) {
-    const int mask = m & 0xFF;
+  with_mask(valid ? (m & 0xFF) : 0, [&](auto mk) {
+    if (!valid) return;
     const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
     const double* F = stencil_factors<double>(g, b);
     double d[3] = {0, 0, 0};
-    int gw[15][3];
-    grad_weights(mask, gw);
 #pragma unroll
     for (int k = 0; k < 15; ++k) {
       const int j = ti + c_toff[k];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) d[a] += double(gw[k][a]) * tile[a * TILE3 + j];
+      for (int a = 0; a < 3; ++a) {
+        const int gw = grad_weight(mk, k, a);
+        if (!const_mask<decltype(mk)>() || gw != 0) d[a] += double(gw) * tile[a * TILE3 + j];
+      }
     }
     o = F[4] * d[0] + F[5] * d[1] + F[6] * d[2];
-  }
+  });
   out[s] = -o / g.pdt[g.binst[b]];
 }
 
@@ -255,8 +288,9 @@ __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __res
   double cf[15];
 #pragma unroll
   for (int k = 0; k < 15; ++k) cf[k] = 0.0;
-  if (m & D_VALID) {
-    const int mask = m & 0xFF;
+  const bool valid = (m & D_VALID) != 0;
+  with_mask(valid ? (m & 0xFF) : 0, [&](auto mask) {
+    if (!valid) return;
     const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
     const double* F = stencil_factors<double>(g, b);
     const int inst = g.binst[b];
@@ -319,7 +353,7 @@ __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __res
     }
 #pragma unroll
     for (int k = 0; k < 15; ++k) cf[k] += double(cc[k]);
-  }
+  });
   // FP32 copy in the compact layout (valid slots only) read by k_apply15_mom32
   const int64_t ci = coef32 ? compact_index(g, b, t, (m & D_VALID) != 0) : 0;
 #pragma unroll
@@ -526,20 +560,21 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
         mn = g.meta[s + DBV];
       }
       T out = T(0);
-      if (m & D_VALID) {
-        const int mask = m & 0xFF;
+      const bool valid = (m & D_VALID) != 0;
+      with_mask(valid ? (m & 0xFF) : 0, [&](auto mk) {
+        if (!valid) return;
         const T* F = stencil_factors<T>(g, bb);
         const T xm = tile[ti - 1], xp = tile[ti + 1], ym = tile[ti - TILE], yp = tile[ti + TILE];
         const T zm = tile[ti - TILE * TILE], zp = tile[ti + TILE * TILE];
         // Kuhn tetrahedra holding each axis edge (kuhn_weights.hpp): the P1
         // stiffness is -(V/6)/h_a^2 times this count, the diagonal their sum
-        const int wxp = stiff_edge_count(mask, 0, 1), wxm = stiff_edge_count(mask, 0, -1);
-        const int wyp = stiff_edge_count(mask, 1, 1), wym = stiff_edge_count(mask, 1, -1);
-        const int wzp = stiff_edge_count(mask, 2, 1), wzm = stiff_edge_count(mask, 2, -1);
+        const int wxp = stiff_edge_count(mk, 0, 1), wxm = stiff_edge_count(mk, 0, -1);
+        const int wyp = stiff_edge_count(mk, 1, 1), wym = stiff_edge_count(mk, 1, -1);
+        const int wzp = stiff_edge_count(mk, 2, 1), wzm = stiff_edge_count(mk, 2, -1);
         const T fx = F[0], fy = F[1], fz = F[2];
         out = fx * (T(wxp) * (pv - xp) + T(wxm) * (pv - xm)) + fy * (T(wyp) * (pv - yp) + T(wym) * (pv - ym)) +
               fz * (T(wzp) * (pv - zp) + T(wzm) * (pv - zm));
-      }
+      });
       if (m & dmask) out = T(0);
       if (m & D_VALID) {   // brick padding stays zero: no store
         q[s] = out;
@@ -668,12 +703,25 @@ __global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict_
       T out[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) out[c] = T(0);
-      if ((m & D_VALID) && !(m & dmask)) {
-        const int mask = m & 0xFF;
-        const T* F = stencil_factors<T>(g, bb);
+      const bool act = (m & D_VALID) && !(m & dmask);
+      if constexpr (OP == OP_MASS) {
+        // M x = (V/120) sum_k w_k x_k with integer weights w_k
+        with_mask(act ? (m & 0xFF) : 0, [&](auto mk) {
+          if (!act) return;
+#pragma unroll
+          for (int k = 0; k < 15; ++k) {
+            const T wk = T(mass_weight(mk, k));
+#pragma unroll
+            for (int c = 0; c < NC; ++c) out[c] += wk * tile[c * TILE3 + ti + c_toff[k]];
+          }
+          const T f3 = stencil_factors<T>(g, bb)[3];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) out[c] *= f3;
+        });
+      } else if (act) {
 #pragma unroll
         for (int k = 0; k < 15; ++k) {
-          const T ck = OP == OP_MASS ? T(mass_weight(mask, k)) * F[3] : coef[(int64_t)k * g.nslots + s];
+          const T ck = coef[(int64_t)k * g.nslots + s];
 #pragma unroll
           for (int c = 0; c < NC; ++c) out[c] += ck * tile[c * TILE3 + ti + c_toff[k]];
         }

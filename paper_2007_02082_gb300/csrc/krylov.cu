@@ -3,13 +3,18 @@
 // the symmetric Poisson (Eq. 12) and mass systems, right-preconditioned
 // BiCGStab for the nonsymmetric Oseen system (Eq. 9).
 //
-// CG iteration (2 or 3 kernels):
+// CG iteration (3 or 4 kernels):
 //   k_apply (fe.cu): p_new = z + beta p_old on the brick tile, q = A p_new
 //                    (local per level), fused p.q -> alpha;
-//   k_cg_update:     interface sum of q fused in, x += alpha p, r -= alpha q,
-//                    z = D^-1 r, FP64 r.z and r.r -> beta, convergence, loop
-//                    condition;
+//   k_sync (fe.cu):  interface sum of q into both stored copies (refined
+//                    grids only; one thread per interface node);
+//   k_cg_update:     x += alpha p, r -= alpha q, z = D^-1 r, FP64 r.z and r.r
+//                    -> beta, convergence, loop condition;
 //   k_expand:        hanging z = mean of parents (refined grids only).
+// Summing the interface copies in their own small kernel keeps the streaming
+// updates free of the chain of dependent index loads an interface sum needs
+// (measured: the in-line sums stalled 43 % of the warps of the refined
+// 64x64x256 tube for most of each update).
 // The search direction ping-pongs between two buffers, so a loop body holds two
 // iterations.  All inner products accumulate in FP64 in a fixed order.
 #include <algorithm>
@@ -145,9 +150,8 @@ __global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict
   if (threadIdx.x == 0) set_cond(cond, any);
 }
 
-// Streaming form of k_cg_update for one component: each thread handles W =
-// 16 / sizeof(T) consecutive slots with 16-byte loads and stores; slots of
-// interface copies take the interface sum of q one by one.
+// Streaming form of k_cg_update: each thread handles W = 16 / sizeof(T)
+// consecutive slots with 16-byte loads and stores (q interface-summed).
 template <int W>
 __device__ __forceinline__ uint16_t vec_or_n(const uint16_t* mm) {
   uint16_t o = 0;
@@ -209,12 +213,7 @@ __global__ void __launch_bounds__(512) k_cg_update_vec(DevGrid g, T* __restrict_
 #pragma unroll
       for (int j = 0; j < W; ++j) {
         const uint16_t m = mm[j];
-        T qq = qe[j];
-        if (m & D_IFACE) {   // interface sum: both copies + half of each hanging child
-          const int e = g.if_of_slot[s + j];
-          qq = qc[g.if_c[e]] + qc[g.if_f[e]];
-          for (int kk = g.if_off[e]; kk < g.if_off[e + 1]; ++kk) qq += T(0.5) * qc[g.if_kid[kk]];
-        }
+        const T qq = qe[j];
         if (m & D_VALID) xe[j] += a * pe[j];
         const T rn = kkeep(m, dmask) ? T(re[j] - a * qq) : T(0);
         re[j] = rn;
@@ -286,7 +285,7 @@ __global__ void __launch_bounds__(512) k_cg_start_r(DevGrid g, const T* __restri
 }
 
 // k_cg_update_vec without the preconditioner: x += alpha p, r -= alpha q
-// (interface sums fused in), ||r||^2 -> convergence and iteration cap
+// (q interface-summed), ||r||^2 -> convergence and iteration cap
 template <typename T>
 __global__ void __launch_bounds__(512) k_cg_update_r(DevGrid g, T* __restrict__ x, T* __restrict__ r,
                                                      const T* __restrict__ p, const T* __restrict__ q,
@@ -318,12 +317,7 @@ __global__ void __launch_bounds__(512) k_cg_update_r(DevGrid g, T* __restrict__ 
 #pragma unroll
       for (int j = 0; j < W; ++j) {
         const uint16_t m = mm[j];
-        T qq = qe[j];
-        if (m & D_IFACE) {
-          const int e = g.if_of_slot[s + j];
-          qq = q[g.if_c[e]] + q[g.if_f[e]];
-          for (int kk = g.if_off[e]; kk < g.if_off[e + 1]; ++kk) qq += T(0.5) * q[g.if_kid[kk]];
-        }
+        const T qq = qe[j];
         if (m & D_VALID) xe[j] += a * pe[j];
         const T rn = kkeep(m, dmask) ? T(re[j] - a * qq) : T(0);
         re[j] = rn;
@@ -426,16 +420,7 @@ __global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restric
 
 // ---------------------------------------------------------------- BiCGStab, streaming form
 // Chunked, 16-byte vector forms of the BiCGStab updates.  The operator outputs
-// v = A ph and t = A sh stay local per level (no separate interface-sum
-// launch): every reader adds the interface sum of a copy's value itself.
-
-template <typename T>
-__device__ __forceinline__ T iface_sum(const DevGrid& g, const T* __restrict__ q, int64_t s) {
-  const int e = g.if_of_slot[s];
-  T v = q[g.if_c[e]] + q[g.if_f[e]];
-  for (int k = g.if_off[e]; k < g.if_off[e + 1]; ++k) v += T(0.5) * q[g.if_kid[k]];
-  return v;
-}
+// v = A ph and t = A sh are interface-summed (fe_apply) before they are read.
 
 // p = r + beta (p - omega v), ph = D^-1 p  (kept slots; 0 elsewhere)
 template <typename T, int NC>
@@ -479,7 +464,7 @@ __global__ void __launch_bounds__(512) k_bcgv_p(DevGrid g, const T* __restrict__
 #pragma unroll
       for (int j = 0; j < W; ++j) {
         const uint16_t m = mm[j];
-        const T vs = (m & D_IFACE) ? iface_sum(g, v + (int64_t)c * g.nslots, s + j) : ve[j];
+        const T vs = ve[j];
         const T pn = kkeep(m, dmask) ? T(re[j] + be * (pe[j] - om * vs)) : T(0);
         pe[j] = pn;
         he[j] = pn * de[j];
@@ -507,7 +492,7 @@ __global__ void __launch_bounds__(512) k_bcgv_dot(DevGrid g, const T* __restrict
   T tw[2 * NC];
 #pragma unroll
   for (int c = 0; c < 2 * NC; ++c) tw[c] = T(0);
-  // b1v is the operator output (v or t, interface sums on read); a1 is rh (mode 0) or s (mode 1)
+  // b1v is the operator output (v or t); a1 is rh (mode 0) or s (mode 1)
   const int64_t s1 = (int64_t)b1 * DBV;
 #pragma unroll 2
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
@@ -526,7 +511,7 @@ __global__ void __launch_bounds__(512) k_bcgv_dot(DevGrid g, const T* __restrict
       for (int j = 0; j < W; ++j) {
         const uint16_t m = mm[j];
         if (!kdof(m, dmask)) continue;
-        const T q = (m & D_IFACE) ? iface_sum(g, b1v + (int64_t)c * g.nslots, s + j) : be[j];
+        const T q = be[j];
         tw[2 * c] += ae[j] * q;
         if (mode == 1) tw[2 * c + 1] += q * q;
       }
@@ -593,7 +578,7 @@ __global__ void __launch_bounds__(512) k_bcgv_s(DevGrid g, const T* __restrict__
 #pragma unroll
       for (int j = 0; j < W; ++j) {
         const uint16_t m = mm[j];
-        const T vs = (m & D_IFACE) ? iface_sum(g, v + (int64_t)c * g.nslots, s + j) : ve[j];
+        const T vs = ve[j];
         const T sn = kkeep(m, dmask) ? T(re[j] - al * vs) : T(0);
         se[j] = sn;
         he[j] = sn * de[j];
@@ -657,7 +642,7 @@ __global__ void __launch_bounds__(512) k_bcgv_xr(DevGrid g, T* __restrict__ x, T
       for (int j = 0; j < W; ++j) {
         const uint16_t m = mm[j];
         if (m & D_VALID) xe[j] += al * pe[j] + om * he[j];
-        const T ts = (m & D_IFACE) ? iface_sum(g, tv + (int64_t)c * g.nslots, s + j) : te[j];
+        const T ts = te[j];
         const T rn = kkeep(m, dmask) ? T(se[j] - om * ts) : T(0);
         oe[j] = rn;
         if (kdof(m, dmask)) {
@@ -818,6 +803,7 @@ static cudaError_t cg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b
     pbegin(a.prof, a.pbase + 0, s);
     fe_apply_cg<T>(g, A, NC, w.z, pold, pnew, w.q, a.ks, rb, s);
     pend(a.prof, s);
+    fe_sync<T>(g, NC, w.q, A.dmask, s);
     pbegin(a.prof, a.pbase + 1, s);
     IBG_LAUNCH((k_cg_update_vec<T, NC>), g.nschunks, DBV, 0, s, g, x, w.r, w.z, pnew, w.q, A.dinv, A.dmask, a.ks,
                rb.partials, rb.counter, c);
@@ -859,6 +845,7 @@ static cudaError_t cg_mg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const M
     pbegin(a.prof, a.pbase + 0, s);
     fe_apply_cg<T>(g, A, 1, w.z, pold, pnew, w.q, a.ks, rb, s);
     pend(a.prof, s);
+    fe_sync<T>(g, 1, w.q, A.dmask, s);
     pbegin(a.prof, a.pbase + 1, s);
     IBG_LAUNCH(k_cg_update_r<T>, g.nschunks, DBV, 0, s, g, x, w.r, pnew, w.q, A.dmask, a.ks, rb.partials,
                rb.counter);
@@ -888,8 +875,7 @@ static cudaError_t bcg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* 
   fe_apply<T>(g, A, NC, x, w.tv, st);
   IBG_LAUNCH((k_bcg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, w.tv, w.r, w.rh, w.p, w.v, A.dmask, a.ks,
              rb.partials, rb.counter, cond, skip_os);
-  // v and t hold the local operator outputs; the kernels below add their
-  // interface sums on read (the start kernel set v = 0)
+  // v and t hold the interface-summed operator outputs (the start kernel set v = 0)
   return run_loop(cc, st, cond, a.ks, a.ks_host, g.ninst * NC, a.max_iter, 1, 8, [&](cudaStream_t s, const Cond& c) {
     pbegin(a.prof, a.pbase + 2, s);
     IBG_LAUNCH((k_bcgv_p<T, NC>), g.nschunks, DBV, 0, s, g, w.r, w.p, w.v, w.ph, A.dinv, A.dmask, a.ks);
@@ -898,12 +884,14 @@ static cudaError_t bcg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* 
     pbegin(a.prof, a.pbase + 0, s);
     fe_apply_local<T>(g, A, NC, w.ph, w.v, s);
     pend(a.prof, s);
+    fe_sync<T>(g, NC, w.v, A.dmask, s);
     IBG_LAUNCH((k_bcgv_dot<T, NC>), g.nschunks, DBV, 0, s, g, w.rh, w.v, A.dmask, 0, a.ks, rb.partials, rb.counter);
     IBG_LAUNCH((k_bcgv_s<T, NC>), g.nschunks, DBV, 0, s, g, w.r, w.v, w.sv, w.sh, A.dinv, A.dmask, a.ks);
     fe_expand2<T>(g, NC, w.sh, (T*)nullptr, s);
     pbegin(a.prof, a.pbase + 0, s);
     fe_apply_local<T>(g, A, NC, w.sh, w.tv, s);
     pend(a.prof, s);
+    fe_sync<T>(g, NC, w.tv, A.dmask, s);
     IBG_LAUNCH((k_bcgv_dot<T, NC>), g.nschunks, DBV, 0, s, g, w.sv, w.tv, A.dmask, 1, a.ks, rb.partials,
                rb.counter);
     pbegin(a.prof, a.pbase + 1, s);

@@ -33,17 +33,6 @@ __device__ __forceinline__ bool keep_slot(uint16_t m, uint16_t dmask) {
   return (m & D_VALID) && !(m & (D_HANG | dmask));
 }
 
-// q at slot s with the interface sum (both stored copies plus half of each
-// hanging child) when s is a copy of a node stored on two levels
-template <typename T>
-__device__ __forceinline__ T q_sum(const DevGrid& g, const T* __restrict__ q, int64_t s, uint16_t m) {
-  if (!(m & D_IFACE)) return q[s];
-  const int e = g.if_of_slot[s];
-  T v = q[g.if_c[e]] + q[g.if_f[e]];
-  for (int k = g.if_off[e]; k < g.if_off[e + 1]; ++k) v += T(0.5) * q[g.if_kid[k]];
-  return v;
-}
-
 // First two Jacobi steps from zero in one pass: x1 = w D^-1 b is pointwise, so
 // x2 = x1 + w D^-1 (b - A x1) takes the neighbours' x1 from their b and D^-1.
 template <typename T>
@@ -101,7 +90,7 @@ __global__ void __launch_bounds__(512) k_mg_c_smooth(DevGrid g, const T* __restr
   for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x) {
     const uint16_t m = g.meta[s];
     if (!(m & D_VALID)) continue;   // brick padding stays zero
-    zout[s] = keep_slot(m, dmask) ? T(zin[s] + omega * dinv[s] * (r[s] - q_sum(g, q, s, m))) : T(0);
+    zout[s] = keep_slot(m, dmask) ? T(zin[s] + omega * dinv[s] * (r[s] - q[s])) : T(0);
   }
 }
 
@@ -136,7 +125,7 @@ __global__ void k_mg_restrict0(DevGrid g, MGLevelDev<T> L0, const T* __restrict_
   T v = T(0);
   for (int e = L0.rptr[j]; e < L0.rptr[j + 1]; ++e) {
     const int64_t s = L0.rcol[e];
-    v += L0.rw[e] * (r[s] - q_sum(g, q, s, g.meta[s]));
+    v += L0.rw[e] * (r[s] - q[s]);
   }
   L0.b[j] = v;
 }
@@ -314,7 +303,11 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
     f();
     if (pr) pr->end(st);
   };
-  auto apply = [&](const T* x) { timed(0, [&] { fe_poisson_apply<T>(g, x, q, dmask, ksm, mg.on, st); }); };
+  // q = A x, then its interface sums into both stored copies
+  auto apply = [&](const T* x) {
+    timed(0, [&] { fe_poisson_apply<T>(g, x, q, dmask, ksm, mg.on, st); });
+    fe_sync<T>(g, 1, q, dmask, st);
+  };
   auto smooth = [&](const T* zin, T* zout) {
     timed(1, [&] {
       IBG_LAUNCH(k_mg_c_smooth<T>, g.nschunks, DBV, 0, st, g, zin, zout, r, q, dinv, dmask, mg.on, w, ks);
