@@ -78,6 +78,23 @@ __device__ __forceinline__ void with_mask(int mask, Body&& body) {
   if (__all_sync(0xffffffffu, mask == 0xFF)) body(FullMask{});
   else body(mask);
 }
+// A small integer weight (|w| < 2^20) as T.  For FP64 the IEEE-754 bits are
+// built with 32-bit integer operations (sign, the exponent from the leading
+// bit, the mantissa below it in the high word, a zero low word): exact, and it
+// keeps the conversion off the FP64 pipe, which issues at a small fraction of
+// the FP32 and integer rates on this GPU.
+template <typename T>
+__device__ __forceinline__ T wconv(int w) {
+  if constexpr (sizeof(T) == 8) {
+    const unsigned a = unsigned(w < 0 ? -w : w);
+    const int e = 31 - __clz(a);   // a in [2^e, 2^(e+1)) for a > 0
+    const unsigned hi = (unsigned(1023 + e) << 20) | ((a << ((20 - e) & 31)) & 0xFFFFFu) | (w < 0 ? 0x80000000u : 0u);
+    return __hiloint2double(a ? int(hi) : 0, 0);
+  } else {
+    return T(w);
+  }
+}
+
 // true when the mask argument of a with_mask body is the compile-time constant
 template <typename MK>
 __device__ __forceinline__ constexpr bool const_mask() {
@@ -204,9 +221,9 @@ __global__ void __launch_bounds__(512) k_rhs_mass_grad(DevGrid g, const double* 
       const double pk = tile[3 * TILE3 + j];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        if (!const_mask<decltype(mk)>() || mw != 0) o[a] += double(mw) * tile[a * TILE3 + j];
+        if (!const_mask<decltype(mk)>() || mw != 0) o[a] += wconv<double>(mw) * tile[a * TILE3 + j];
         const int gw = grad_weight(mk, k, a);
-        if (!const_mask<decltype(mk)>() || gw != 0) gp[a] += double(gw) * pk;
+        if (!const_mask<decltype(mk)>() || gw != 0) gp[a] += wconv<double>(gw) * pk;
       }
     }
 #pragma unroll
@@ -238,7 +255,7 @@ __global__ void __launch_bounds__(512) k_rhs_div(DevGrid g, const double* __rest
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int gw = grad_weight(mk, k, a);
-        if (!const_mask<decltype(mk)>() || gw != 0) d[a] += double(gw) * tile[a * TILE3 + j];
+        if (!const_mask<decltype(mk)>() || gw != 0) d[a] += wconv<double>(gw) * tile[a * TILE3 + j];
       }
     }
     o = F[4] * d[0] + F[5] * d[1] + F[6] * d[2];
@@ -300,12 +317,12 @@ __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __res
     const double dnu = dt * nu;
     // M + dt nu K from the incident-cell mask (exact integer weights)
 #pragma unroll
-    for (int k = 0; k < 15; ++k) cf[k] = double(mass_weight(mask, k)) * F[3];
+    for (int k = 0; k < 15; ++k) cf[k] = wconv<double>(mass_weight(mask, k)) * F[3];
     double diagK = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double kp = dnu * double(stiff_edge_count(mask, a, 1)) * F[a];
-      const double km = dnu * double(stiff_edge_count(mask, a, -1)) * F[a];
+      const double kp = dnu * wconv<double>(stiff_edge_count(mask, a, 1)) * F[a];
+      const double km = dnu * wconv<double>(stiff_edge_count(mask, a, -1)) * F[a];
       cf[1 + 2 * a] -= kp;
       cf[2 + 2 * a] -= km;
       diagK += kp + km;
@@ -572,8 +589,9 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
         const int wyp = stiff_edge_count(mk, 1, 1), wym = stiff_edge_count(mk, 1, -1);
         const int wzp = stiff_edge_count(mk, 2, 1), wzm = stiff_edge_count(mk, 2, -1);
         const T fx = F[0], fy = F[1], fz = F[2];
-        out = fx * (T(wxp) * (pv - xp) + T(wxm) * (pv - xm)) + fy * (T(wyp) * (pv - yp) + T(wym) * (pv - ym)) +
-              fz * (T(wzp) * (pv - zp) + T(wzm) * (pv - zm));
+        out = fx * (wconv<T>(wxp) * (pv - xp) + wconv<T>(wxm) * (pv - xm)) +
+              fy * (wconv<T>(wyp) * (pv - yp) + wconv<T>(wym) * (pv - ym)) +
+              fz * (wconv<T>(wzp) * (pv - zp) + wconv<T>(wzm) * (pv - zm));
       });
       if (m & dmask) out = T(0);
       if (m & D_VALID) {   // brick padding stays zero: no store
@@ -641,7 +659,15 @@ __global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict_
                                                  unsigned* __restrict__ counter, const T* __restrict__ zf,
                                                  T* __restrict__ pnew) {
   KCOUNT();
-  __shared__ T tile[NC * TILE3];
+  // FP32 with 3 components: one float4 per tile node (one 16-byte shared load
+  // per stencil neighbour); otherwise one plane per component
+  constexpr bool V4 = sizeof(T) == 4 && NC == 3;
+  __shared__ __align__(16) T tile[V4 ? 4 * TILE3 : NC * TILE3];
+  float4* tile4 = reinterpret_cast<float4*>(tile);
+  auto tval = [&](int c, int j) -> T {
+    if constexpr (V4) return reinterpret_cast<const T*>(tile4 + j)[c];
+    else return tile[c * TILE3 + j];
+  };
   const int b0 = PB ? int(blockIdx.x) : g.cbrick[blockIdx.x];
   const int b1 = PB ? b0 + 1 : g.cbrick[blockIdx.x + 1];
   const int inst = g.binst[b0];
@@ -689,10 +715,15 @@ __global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict_
     uint16_t mn = g.meta[(int64_t)b0 * DBV + t];
     for (int bb = b0; bb < b1; ++bb) {
       const int64_t s = (int64_t)bb * DBV + t;
+      if constexpr (V4) {
+        tile4[ti] = make_float4(vo[0], vo[1], vo[2], 0.f);
+        if (t < HALO15) tile4[hti] = make_float4(vh[0], vh[1], vh[2], 0.f);
+      } else {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        tile[c * TILE3 + ti] = vo[c];
-        if (t < HALO15) tile[c * TILE3 + hti] = vh[c];
+        for (int c = 0; c < NC; ++c) {
+          tile[c * TILE3 + ti] = vo[c];
+          if (t < HALO15) tile[c * TILE3 + hti] = vh[c];
+        }
       }
       const uint16_t m = mn;
       __syncthreads();
@@ -710,9 +741,16 @@ __global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict_
           if (!act) return;
 #pragma unroll
           for (int k = 0; k < 15; ++k) {
-            const T wk = T(mass_weight(mk, k));
+            const T wk = wconv<T>(mass_weight(mk, k));
+            if constexpr (V4) {
+              const float4 v = tile4[ti + c_toff[k]];
+              out[0] += wk * v.x;
+              out[1] += wk * v.y;
+              out[2] += wk * v.z;
+            } else {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) out[c] += wk * tile[c * TILE3 + ti + c_toff[k]];
+              for (int c = 0; c < NC; ++c) out[c] += wk * tile[c * TILE3 + ti + c_toff[k]];
+            }
           }
           const T f3 = stencil_factors<T>(g, bb)[3];
 #pragma unroll
@@ -723,16 +761,17 @@ __global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict_
         for (int k = 0; k < 15; ++k) {
           const T ck = coef[(int64_t)k * g.nslots + s];
 #pragma unroll
-          for (int c = 0; c < NC; ++c) out[c] += ck * tile[c * TILE3 + ti + c_toff[k]];
+          for (int c = 0; c < NC; ++c) out[c] += ck * tval(c, ti + c_toff[k]);
         }
       }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
+        const T own = tval(c, ti);
         if (m & D_VALID) {   // brick padding stays zero: no store
           y[(int64_t)c * g.nslots + s] = out[c];
-          if (FUSEP) pnew[(int64_t)c * g.nslots + s] = tile[c * TILE3 + ti];
+          if (FUSEP) pnew[(int64_t)c * g.nslots + s] = own;
         }
-        if (FUSEP) acc[c] += tile[c * TILE3 + ti] * out[c];
+        if (FUSEP) acc[c] += own * out[c];
       }
       __syncthreads();
     }
