@@ -695,23 +695,34 @@ __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double*
   double w[2 * NC];
 #pragma unroll
   for (int c = 0; c < 2 * NC; ++c) w[c] = 0.0;
-  if (!oi.done)
-    for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x) {
-      const uint16_t m = g.meta[s];
-      if (!(m & D_VALID)) continue;   // brick padding: r32 and e32 stay zero there
-      const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
+  // pairs of slots: 16-byte FP64 loads, 8-byte FP32 stores
+  const int64_t s1 = (int64_t)b1 * DBV;
+  if (!oi.done) {
+#pragma unroll 2
+    for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * 2; s < s1; s += (int64_t)blockDim.x * 2) {
+      const uint32_t mv = *reinterpret_cast<const uint32_t*>(g.meta + s);
+      const uint16_t mm[2] = {uint16_t(mv & 0xFFFFu), uint16_t(mv >> 16)};
+      if (!((mm[0] | mm[1]) & D_VALID)) continue;   // brick padding: r32 and e32 stay zero there
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int64_t i = c * g.nslots + s;
-        const double rv = keep ? b[i] - y[i] : 0.0;
-        r32[i] = float(rv);
-        e32[i] = 0.f;
-        if (dof) {
-          w[2 * c] += rv * rv;
-          if (first) w[2 * c + 1] += b[i] * b[i];
+        const double2 bv = *reinterpret_cast<const double2*>(b + i);
+        const double2 yv = *reinterpret_cast<const double2*>(y + i);
+        const double be[2] = {bv.x, bv.y}, ye[2] = {yv.x, yv.y};
+        double rv[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          rv[j] = kkeep(mm[j], dmask) ? be[j] - ye[j] : 0.0;
+          if (kdof(mm[j], dmask)) {
+            w[2 * c] += rv[j] * rv[j];
+            if (first) w[2 * c + 1] += be[j] * be[j];
+          }
         }
+        *reinterpret_cast<float2*>(r32 + i) = make_float2(float(rv[0]), float(rv[1]));
+        *reinterpret_cast<float2*>(e32 + i) = make_float2(0.f, 0.f);
       }
     }
+  }
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
   if (!grid_sum_last<double, 2 * NC>(w, partials, counter, g.scseg, g.ninst, out)) return;
   bool any = false;

@@ -59,6 +59,13 @@ __device__ __forceinline__ T level_ax(const MGLevelDev<T>& L, const T* __restric
 }
 
 // ---------------------------------------------------------------- composite level
+// The pointwise composite kernels move 16-byte vectors of W = 16 / sizeof(T)
+// consecutive slots; a vector without a valid slot (brick padding) is skipped,
+// and padding slots inside a vector are written with their value, zero.
+template <typename T> struct V16;
+template <> struct V16<float> { using v = float4; using m = uint2; static constexpr int W = 4; };
+template <> struct V16<double> { using v = double2; using m = uint32_t; static constexpr int W = 2; };
+
 // z = w D^-1 r on kept slots (w = omega with multigrid, 1 for the Jacobi
 // preconditioner), 0 elsewhere
 template <typename T>
@@ -66,14 +73,30 @@ __global__ void __launch_bounds__(512) k_mg_c_jac0(DevGrid g, const T* __restric
                                                    const T* __restrict__ dinv, uint16_t dmask,
                                                    const uint8_t* __restrict__ on, T omega, const KState* ks) {
   KCOUNT();
+  using V = typename V16<T>::v;
+  using MT = typename V16<T>::m;
+  constexpr int W = V16<T>::W;
   const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const int inst = g.binst[b0];
   if (ks[inst].done) return;
   const T w = on[inst] ? omega : T(1);
-  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x) {
-    const uint16_t m = g.meta[s];
-    if (!(m & D_VALID)) continue;   // brick padding stays zero
-    z[s] = keep_slot(m, dmask) ? T(w * dinv[s] * r[s]) : T(0);
+  const int64_t s1 = (int64_t)b1 * DBV;
+#pragma unroll 2
+  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
+    const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
+    const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+    uint16_t mor = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) mor |= mm[j];
+    if (!(mor & D_VALID)) continue;
+    const V rv = *reinterpret_cast<const V*>(r + s), dv = *reinterpret_cast<const V*>(dinv + s);
+    const T* re = reinterpret_cast<const T*>(&rv);
+    const T* de = reinterpret_cast<const T*>(&dv);
+    V zv;
+    T* ze = reinterpret_cast<T*>(&zv);
+#pragma unroll
+    for (int j = 0; j < W; ++j) ze[j] = keep_slot(mm[j], dmask) ? T(w * de[j] * re[j]) : T(0);
+    *reinterpret_cast<V*>(z + s) = zv;
   }
 }
 
@@ -84,13 +107,32 @@ __global__ void __launch_bounds__(512) k_mg_c_smooth(DevGrid g, const T* __restr
                                                      const T* __restrict__ dinv, uint16_t dmask,
                                                      const uint8_t* __restrict__ on, T omega, const KState* ks) {
   KCOUNT();
+  using V = typename V16<T>::v;
+  using MT = typename V16<T>::m;
+  constexpr int W = V16<T>::W;
   const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const int inst = g.binst[b0];
   if (ks[inst].done || !on[inst]) return;
-  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x) {
-    const uint16_t m = g.meta[s];
-    if (!(m & D_VALID)) continue;   // brick padding stays zero
-    zout[s] = keep_slot(m, dmask) ? T(zin[s] + omega * dinv[s] * (r[s] - q[s])) : T(0);
+  const int64_t s1 = (int64_t)b1 * DBV;
+#pragma unroll 2
+  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * W; s < s1; s += (int64_t)blockDim.x * W) {
+    const MT mv = *reinterpret_cast<const MT*>(g.meta + s);
+    const uint16_t* mm = reinterpret_cast<const uint16_t*>(&mv);
+    uint16_t mor = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) mor |= mm[j];
+    if (!(mor & D_VALID)) continue;
+    const V zv = *reinterpret_cast<const V*>(zin + s), rv = *reinterpret_cast<const V*>(r + s);
+    const V qv = *reinterpret_cast<const V*>(q + s), dv = *reinterpret_cast<const V*>(dinv + s);
+    const T* ze = reinterpret_cast<const T*>(&zv);
+    const T* re = reinterpret_cast<const T*>(&rv);
+    const T* qe = reinterpret_cast<const T*>(&qv);
+    const T* de = reinterpret_cast<const T*>(&dv);
+    V ov;
+    T* oe = reinterpret_cast<T*>(&ov);
+#pragma unroll
+    for (int j = 0; j < W; ++j) oe[j] = keep_slot(mm[j], dmask) ? T(ze[j] + omega * de[j] * (re[j] - qe[j])) : T(0);
+    *reinterpret_cast<V*>(zout + s) = ov;
   }
 }
 
