@@ -36,7 +36,10 @@ with its reason in the project's design notes):
       of the finest level;
   R6  kinematic pressure (rho = 1 in every synthetic case);
   R7  viscous term nu (grad u, grad v) (equal to div 2 nu eps(u) for a
-      divergence-free field; do-nothing outlet);
+      divergence-free field; do-nothing outlet); with case["viscous"] ==
+      "sym" the symmetric form 2 nu (eps(u), eps(v)) of Eq. 1 and Eq. 9, minus
+      the boundary term nu ((grad u)^T n, v) on the outlet and pressure-inlet
+      faces, which keeps the do-nothing condition of the gradient form;
   R9  Phi = 0 on outlet-port nodes; on pressure-inlet nodes Phi takes the
       increment p_in(t^{n+1}) - p^n that brings p^{n+1} to the imposed inlet
       pressure; homogeneous Neumann elsewhere;
@@ -490,6 +493,52 @@ class Operators:
         self.P = mesh.P
         self.PT = mesh.P.T.tocsr()
 
+    def transpose_blocks(self):
+        """Kt[i][j][a, b] = int (d_j phi_a)(d_i phi_b): the blocks of
+        (grad u^T : grad v) for test phi_a e_i and trial phi_b e_j, so that
+        2 (eps(u), eps(v)) = (grad u, grad v) + sum_ij Kt[i][j] (Eq. 1 read with
+        the symmetric strain rate)."""
+        if not hasattr(self, "_kt"):
+            g, v = self.grads, self.vol
+            self._kt = [[_assemble(self.mesh, v[:, None, None] * np.einsum("ta,tb->tab", g[:, :, j], g[:, :, i]))
+                         for j in range(3)] for i in range(3)]
+        return self._kt
+
+    def natural_boundary_blocks(self):
+        """Bn[i][j][a, b] = int_F n_j (d_i phi_b) phi_a over the tetrahedron faces
+        F lying in the plane of an outlet or pressure-inlet port (outward normal
+        n = -e_axis on the low face, +e_axis on the high face), so that
+        sum_ij Bn[i][j] u_j is the boundary term ((grad u)^T n, v).  Rows of
+        nodes with a velocity condition are eliminated by the solve."""
+        if hasattr(self, "_bn"):
+            return self._bn
+        m = self.mesh
+        N = m.n_nodes
+        rows = {(i, j): ([], [], []) for i in range(3) for j in range(3)}
+        Lf = 1 << m.L
+        for port in m.case["ports"]:
+            if port["kind"] == "inlet":
+                continue
+            ax = port["axis"]
+            plane = 0 if port["side"] == 0 else int(m.n[ax]) * Lf
+            nrm = -1.0 if port["side"] == 0 else 1.0
+            on = m.node_q[m.tets][:, :, ax] == plane                 # (T, 4)
+            for t in np.nonzero(on.sum(axis=1) == 3)[0]:
+                face = m.tets[t][on[t]]
+                x = m.node_x[face]
+                area = 0.5 * np.linalg.norm(np.cross(x[1] - x[0], x[2] - x[0]))
+                for a in face:
+                    for bi, b in enumerate(m.tets[t]):
+                        for i in range(3):
+                            r, cidx, val = rows[(i, ax)]
+                            r.append(a)
+                            cidx.append(b)
+                            val.append(nrm * self.grads[t, bi, i] * area / 3.0)
+        self._bn = [[sp.csr_matrix((np.asarray(rows[(i, j)][2], float),
+                                    (np.asarray(rows[(i, j)][0], np.int64), np.asarray(rows[(i, j)][1], np.int64))),
+                                   shape=(N, N)) for j in range(3)] for i in range(3)]
+        return self._bn
+
     def convection(self, u):
         """C(u)[a, b] = int_T (u_h . grad phi_b) phi_a, u_h the P1 interpolant."""
         uT = u[self.mesh.tets]                                  # (T, 4, 3)
@@ -641,9 +690,12 @@ class Oracle:
 
         # Step 1, Eq. 9: (M + dt C(u^n) + dt nu K) u~ = M u^n - dt G p^n
         Am = ops.M + dt * ops.convection(self.u) + (dt * nu) * ops.K
-        Ac = ops.condense(Am)
         b = np.stack([ops.PT @ (ops.M @ self.u[:, k] - dt * (ops.G[k] @ self.p)) for k in range(3)], 1)
-        ut = ops.P @ solve_dirichlet(Ac, b, self.vdir, g, symmetric=False)
+        if c.get("viscous", "grad") == "sym":
+            ut = self._momentum_sym(Am, b, g, dt * nu)
+        else:
+            Ac = ops.condense(Am)
+            ut = ops.P @ solve_dirichlet(Ac, b, self.vdir, g, symmetric=False)
 
         # Steps 2-3: B_F = U_B - h^3 D^T u~ (Eq. 23), A_F F = B_F (Eq. 21)
         BF = self.ib.UB - self.ib.W @ ut
@@ -670,6 +722,20 @@ class Oracle:
         self.F = F
         self.t = t1
         self.nstep += 1
+
+    def _momentum_sym(self, Am, b, g, dtnu):
+        """Eq. 9 with the symmetric viscous form (R7): the three components
+        couple through dt nu (Kt - Bn); one block system on 3 Ndof unknowns,
+        component-major."""
+        ops = self.ops
+        Kt, Bn = ops.transpose_blocks(), ops.natural_boundary_blocks()
+        blocks = [[ops.condense((Am if i == j else 0 * Am) + dtnu * (Kt[i][j] - Bn[i][j])) for j in range(3)]
+                  for i in range(3)]
+        A3 = sp.bmat(blocks, format="csr")
+        nd = b.shape[0]
+        d3 = np.concatenate([self.vdir] * 3)
+        x3 = solve_dirichlet(A3, b.T.reshape(-1, 1), d3, g.T.reshape(-1, 1), symmetric=False)[:, 0]
+        return ops.P @ x3.reshape(3, nd).T
 
     def run(self, steps):
         for _ in range(steps):

@@ -337,3 +337,73 @@ def test_zero_pressure_inlet_is_an_outlet():
     assert pin.sum() > 0 and np.array_equal(pin | outa, outb)
     assert np.array_equal(ua, ub) and np.array_equal(pa, pb)
     assert np.abs(ua[:, 2]).max() > 0.1
+
+
+# ---------------------------------------------------------------- symmetric viscous form
+def _linear_field(x, S):
+    return x @ S.T          # u_i = sum_j S_ij x_j
+
+
+def test_transpose_blocks_on_linear_fields():
+    """2 (eps(u), eps(v)) = (grad u, grad v) + (grad u^T, grad v) (Eq. 1 with
+    the symmetric strain rate).  For a linear field u = S x, grad u^T = S^T:
+    the transpose blocks reproduce the Laplacian of the symmetric part of S and
+    minus that of the antisymmetric part, row by row, hanging nodes included
+    (so a rigid rotation, eps(u) = 0, gives zero); their trace is the
+    Laplacian stiffness and the block operator is symmetric."""
+    c = W.cylinder_refined_small(n=(16, 16, 8), seed=21)
+    m = ibfe.build_mesh(c)
+    assert m.hanging.any()
+    ops = ibfe.Operators(m)
+    Kt = ops.transpose_blocks()
+    S = np.random.default_rng(0).normal(size=(3, 3))
+    for part, sign in ((0.5 * (S + S.T), 1.0), (0.5 * (S - S.T), -1.0)):
+        u = _linear_field(m.node_x, part)
+        for i in range(3):
+            lhs = sum(Kt[i][j] @ u[:, j] for j in range(3))
+            rhs = sign * (ops.K @ u[:, i])
+            assert np.abs(lhs - rhs).max() <= 1e-13 * np.abs(ops.K @ u[:, i]).max() + 1e-18
+    scale = abs(ops.K).max()
+    assert abs(sum(Kt[i][i] for i in range(3)) - ops.K).max() <= 1e-14 * scale
+    for i in range(3):
+        for j in range(3):
+            assert abs(Kt[i][j] - Kt[j][i].T).max() <= 1e-14 * scale
+
+
+def test_natural_boundary_term_closes_linear_fields():
+    """For a linear field the volume term (grad u^T, grad phi_a) equals the
+    boundary integral ((grad u)^T n, phi_a): on an outlet node every face of
+    that boundary lies in the outlet plane, so subtracting the natural
+    boundary term leaves exactly zero there (and does not without it)."""
+    c = W.cylinder_uniform_16x16x64()
+    m = ibfe.build_mesh(c)
+    ops = ibfe.Operators(m)
+    Kt, Bn = ops.transpose_blocks(), ops.natural_boundary_blocks()
+    u = _linear_field(m.node_x, np.random.default_rng(1).normal(size=(3, 3)))
+    rows = np.nonzero(m.outlet)[0]
+    assert len(rows) > 100
+    for i in range(3):
+        vol = sum(Kt[i][j] @ u[:, j] for j in range(3))[rows]
+        res = vol - sum(Bn[i][j] @ u[:, j] for j in range(3))[rows]
+        assert np.abs(vol).max() > 1e-4
+        assert np.abs(res).max() <= 1e-13 * np.abs(vol).max()
+
+
+def test_symmetric_form_keeps_poiseuille():
+    """With the boundary term the symmetric form keeps the do-nothing outlet,
+    which the Poiseuille flow satisfies: started from it, the velocity- and
+    the pressure-driven tube stay as close to it as with the gradient form."""
+    for inlet in (W.INLET, W.PINLET):
+        errs = {}
+        for form in ("grad", "sym"):
+            c = W.cylinder_case(n=(8, 8, 32), M=300, dt=0.05, inlet=inlet, a0=6.4 if inlet == W.PINLET else 1.0)
+            c["viscous"] = form
+            m = ibfe.build_mesh(c)
+            x = m.node_x
+            r2 = x[:, 0] ** 2 + x[:, 1] ** 2
+            u0 = np.zeros((m.n_nodes, 3))
+            u0[:, 2] = np.where(r2 < 0.25, 1.0 - 4.0 * r2, 0.0)
+            o = ibfe.Oracle(c, u0=u0, p0=1.6 * (4.0 - x[:, 2])).run(20)
+            ins = r2 < 0.4 ** 2
+            errs[form] = math.sqrt(np.mean((o.u[ins, 2] - u0[ins, 2]) ** 2))
+        assert abs(errs["sym"] - errs["grad"]) <= 0.02 * errs["grad"], (inlet, errs)

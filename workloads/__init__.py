@@ -69,7 +69,7 @@ def cell_centres(origin, extent, n):
 def cylinder_case(n=(16, 16, 64), R=0.5, length=4.0, half_width=0.6, M=2000,
                   seed=1, max_level=0, refine_band=2, reduce_band=-1,
                   nu=0.1, dt=0.01, steps=50, a0=1.0, b=(), period=1.0,
-                  name=None, inlet=INLET):
+                  name=None, inlet=INLET, viscous="grad"):
     """Straight tube of radius R along z, immersed in [-w, w]^2 x [0, length].
 
     Defaults: the uniform 16x16x64 cylinder, nu = 0.1, dt = 0.01, steady
@@ -80,6 +80,7 @@ def cylinder_case(n=(16, 16, 64), R=0.5, length=4.0, half_width=0.6, M=2000,
     inlet = PINLET drives the flow by the inlet pressure a0 (+ harmonics)
     instead; a0 = 16 nu L / R^2 (6.4 with the defaults) gives the same
     Poiseuille flow of peak 1 (the pressure-driven tube of Sec. 3.1).
+    viscous = "sym" selects the symmetric viscous form 2 nu (eps(u), eps(v)).
     """
     origin = (-half_width, -half_width, 0.0)
     extent = (2.0 * half_width, 2.0 * half_width, float(length))
@@ -97,7 +98,7 @@ def cylinder_case(n=(16, 16, 64), R=0.5, length=4.0, half_width=0.6, M=2000,
         "reduce_band": int(reduce_band),
         "nu": float(nu), "rho": 1.0, "dt": float(dt), "steps": int(steps),
         "ports": ports, "X": X, "dS": dS, "UB": np.zeros_like(X),
-        "inside": inside,
+        "inside": inside, "viscous": viscous,
     }
 
 
