@@ -123,4 +123,116 @@ IBG_HD int grad_weight(int mask, int k, int a) {
   }
 }
 
+// Transpose-gradient coupling of a node and its stencil neighbour k: the sum,
+// over the Kuhn tetrahedra of the active incident cells that hold both, of
+// (d_j phi_node)(d_i phi_neighbour), in units 1/(h_i h_j).  It is the block
+// (test component i, trial component j) of (grad u^T, grad v) per |T|, the
+// term the symmetric viscous form 2 (eps(u), eps(v)) adds to (grad u, grad v).
+// Each tetrahedron belongs to one cell, so the sum is linear in the mask bits.
+IBG_HD int trans_weight(int mask, int k, int i, int j) {
+  auto b = [mask](int c) { return (mask >> c) & 1; };
+  switch (k * 9 + i * 3 + j) {
+    case 0: return 2 * b(0) + 2 * b(1) + b(2) + b(3) + b(4) + b(5) + 2 * b(6) + 2 * b(7);
+    case 1: return -b(1) - b(2) - b(5) - b(6);
+    case 2: return -b(1) - b(3) - b(4) - b(6);
+    case 3: return -b(1) - b(2) - b(5) - b(6);
+    case 4: return 2 * b(0) + b(1) + 2 * b(2) + b(3) + b(4) + 2 * b(5) + b(6) + 2 * b(7);
+    case 5: return -b(2) - b(3) - b(4) - b(5);
+    case 6: return -b(1) - b(3) - b(4) - b(6);
+    case 7: return -b(2) - b(3) - b(4) - b(5);
+    case 8: return 2 * b(0) + b(1) + b(2) + 2 * b(3) + 2 * b(4) + b(5) + b(6) + 2 * b(7);
+    case 9: return -2 * b(1) - b(3) - b(5) - 2 * b(7);
+    case 10: return b(1) + b(5);
+    case 11: return b(1) + b(3);
+    case 12: return b(3) + b(7);
+    case 14: return -b(3);
+    case 15: return b(5) + b(7);
+    case 16: return -b(5);
+    case 18: return -2 * b(0) - b(2) - b(4) - 2 * b(6);
+    case 19: return b(2) + b(6);
+    case 20: return b(4) + b(6);
+    case 21: return b(0) + b(4);
+    case 23: return -b(4);
+    case 24: return b(0) + b(2);
+    case 25: return -b(2);
+    case 28: return b(3) + b(7);
+    case 29: return -b(3);
+    case 30: return b(2) + b(6);
+    case 31: return -2 * b(2) - b(3) - b(6) - 2 * b(7);
+    case 32: return b(2) + b(3);
+    case 33: return -b(6);
+    case 34: return b(6) + b(7);
+    case 37: return b(0) + b(4);
+    case 38: return -b(4);
+    case 39: return b(1) + b(5);
+    case 40: return -2 * b(0) - b(1) - b(4) - 2 * b(5);
+    case 41: return b(4) + b(5);
+    case 42: return -b(1);
+    case 43: return b(0) + b(1);
+    case 46: return -b(5);
+    case 47: return b(5) + b(7);
+    case 48: return -b(6);
+    case 50: return b(6) + b(7);
+    case 51: return b(4) + b(6);
+    case 52: return b(4) + b(5);
+    case 53: return -2 * b(4) - b(5) - b(6) - 2 * b(7);
+    case 55: return -b(2);
+    case 56: return b(0) + b(2);
+    case 57: return -b(1);
+    case 59: return b(0) + b(1);
+    case 60: return b(1) + b(3);
+    case 61: return b(2) + b(3);
+    case 62: return -2 * b(0) - b(1) - b(2) - 2 * b(3);
+    case 64: return -b(3) - b(7);
+    case 65: return b(3);
+    case 66: return -b(3) - b(7);
+    case 68: return b(3);
+    case 69: return b(7);
+    case 70: return b(7);
+    case 73: return -b(0) - b(4);
+    case 74: return b(4);
+    case 75: return -b(0) - b(4);
+    case 77: return b(4);
+    case 78: return b(0);
+    case 79: return b(0);
+    case 82: return b(7);
+    case 83: return b(7);
+    case 84: return b(6);
+    case 86: return -b(6) - b(7);
+    case 87: return b(6);
+    case 88: return -b(6) - b(7);
+    case 91: return b(0);
+    case 92: return b(0);
+    case 93: return b(1);
+    case 95: return -b(0) - b(1);
+    case 96: return b(1);
+    case 97: return -b(0) - b(1);
+    case 100: return b(5);
+    case 101: return -b(5) - b(7);
+    case 102: return b(7);
+    case 104: return b(7);
+    case 105: return -b(5) - b(7);
+    case 106: return b(5);
+    case 109: return b(2);
+    case 110: return -b(0) - b(2);
+    case 111: return b(0);
+    case 113: return b(0);
+    case 114: return -b(0) - b(2);
+    case 115: return b(2);
+    case 118: return -b(7);
+    case 119: return -b(7);
+    case 120: return -b(7);
+    case 122: return -b(7);
+    case 123: return -b(7);
+    case 124: return -b(7);
+    case 127: return -b(0);
+    case 128: return -b(0);
+    case 129: return -b(0);
+    case 131: return -b(0);
+    case 132: return -b(0);
+    case 133: return -b(0);
+    default: return 0;
+  }
+}
+
 }  // namespace ibg
