@@ -59,6 +59,7 @@ enum { IB_INLET_VELOCITY = 0, IB_OUTLET_ZERO_P = 1, IB_INLET_PRESSURE = 2 };
 enum { IB_PARABOLIC = 0 };
 enum { IB_FP64 = 0, IB_MIXED = 1 };
 enum { IB_PC_MULTIGRID = 0, IB_PC_JACOBI = 1 };
+enum { IB_VISCOUS_GRAD = 0, IB_VISCOUS_SYM = 1 };
 
 #define IB_MAX_PORTS 8
 #define IB_MAX_HARMONICS 8
@@ -127,6 +128,16 @@ typedef struct {
  *                       IB_PC_MULTIGRID (default; geometric V-cycle over the
  *                       nested Kuhn meshes, falls back to Jacobi when the
  *                       hierarchy cannot be built) or IB_PC_JACOBI
+ *   viscous_form        viscous term of the momentum step (Eq. 9):
+ *                       IB_VISCOUS_GRAD (default): nu (grad u, grad v), the
+ *                       components decouple; IB_VISCOUS_SYM: the symmetric
+ *                       form 2 nu (eps(u), eps(v)) of Eq. 1, which couples the
+ *                       three components, minus the boundary term
+ *                       nu ((grad u)^T n, v) on outlet and pressure-inlet faces
+ *                       so that those keep the do-nothing condition; the
+ *                       momentum BiCGStab then runs on the coupled system (one
+ *                       set of scalars for the three components).  The members
+ *                       of a batch share one form.
  *   stream              cudaStream_t on which all work is enqueued
  *   dev_alloc/dev_free  optional device allocator (ctx = alloc_ctx); every
  *                       block it returns must start on a 256-byte boundary
@@ -145,6 +156,7 @@ typedef struct {
   int32_t deferred;         /* 1: keep only the grid and a state snapshot; the
                                problem is stepped inside an ib_batch */
   int32_t poisson_pc;       /* IB_PC_MULTIGRID | IB_PC_JACOBI */
+  int32_t viscous_form;     /* IB_VISCOUS_GRAD | IB_VISCOUS_SYM */
   int32_t n_ports;
   ib_port ports[IB_MAX_PORTS];
   void* stream;
@@ -274,10 +286,11 @@ void ib_grid_destroy(ib_grid* g);
  *   (zero for a new problem).  One step of the batch is one captured graph in
  *   which every kernel runs over the concatenated bricks of all members and
  *   every Krylov reduction is segmented per member, so each member's result is
- *   bitwise the same alone and in any mix.  Members must share the precision;
- *   each keeps its own grid, nu, dt, rho, ports and tolerances of member 0.
- *   Errors: IB_EINVAL (a member not deferred, not ready, repeated, or already
- *   in a batch), IB_ENOMEM, IB_ECUDA.
+ *   bitwise the same alone and in any mix.  Members must share the precision
+ *   and the viscous form; each keeps its own grid, nu, dt, rho, ports and
+ *   tolerances of member 0.
+ *   Errors: IB_EINVAL (a member not deferred, not ready, repeated, already in
+ *   a batch, or of another precision or viscous form), IB_ENOMEM, IB_ECUDA.
  * ib_batch_step: nsteps steps of every member; status[i] (if not NULL, n
  *   entries) receives each member's status of the last step.  A member whose
  *   solves failed keeps its previous state; the call returns the worst status.

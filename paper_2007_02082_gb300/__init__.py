@@ -43,6 +43,13 @@ def load_library(build_if_missing: bool = False) -> C.CDLL:
     return _LIB
 
 
+def _viscous_form(case):
+    form = case.get("viscous", "grad")
+    if form not in ("grad", "sym"):
+        raise ValueError(f"viscous must be 'grad' or 'sym', not {form!r}")
+    return _abi.IB_VISCOUS_SYM if form == "sym" else _abi.IB_VISCOUS_GRAD
+
+
 def _port_struct(port):
     p = _abi.IbPort()
     p.axis, p.side = port["axis"], port["side"]
@@ -132,6 +139,7 @@ class IBGrid:
         if poisson_pc not in ("multigrid", "jacobi"):
             raise ValueError("poisson_pc must be 'multigrid' or 'jacobi'")
         d.poisson_pc = _abi.IB_PC_JACOBI if poisson_pc == "jacobi" else _abi.IB_PC_MULTIGRID
+        d.viscous_form = _viscous_form(case)
         d.n_ports = len(case["ports"])
         for k, port in enumerate(case["ports"]):
             d.ports[k] = _port_struct(port)

@@ -8,6 +8,7 @@ IB_OK, IB_EINVAL, IB_ENOMEM, IB_ESTATE, IB_ENOCONV, IB_EBREAKDOWN, IB_ECUDA, IB_
 STATUS_NAMES = {0: "IB_OK", 1: "IB_EINVAL", 2: "IB_ENOMEM", 3: "IB_ESTATE", 4: "IB_ENOCONV",
                 5: "IB_EBREAKDOWN", 6: "IB_ECUDA", 7: "IB_ETIMEOUT"}
 IB_INLET_VELOCITY, IB_OUTLET_ZERO_P, IB_INLET_PRESSURE = 0, 1, 2
+IB_VISCOUS_GRAD, IB_VISCOUS_SYM = 0, 1
 IB_FP64, IB_MIXED = 0, 1
 IB_PC_MULTIGRID, IB_PC_JACOBI = 0, 1
 IB_MAX_PORTS, IB_MAX_HARMONICS, IB_MAX_LEVEL = 8, 8, 3
@@ -42,6 +43,7 @@ class IbGridDesc(C.Structure):
         ("nu", C.c_double), ("rho", C.c_double), ("dt", C.c_double), ("precision", C.c_int32),
         ("rtol_mom", C.c_double), ("rtol_p", C.c_double), ("rtol_corr", C.c_double), ("rtol_ib", C.c_double),
         ("max_iter", C.c_int32), ("profile", C.c_int32), ("deferred", C.c_int32), ("poisson_pc", C.c_int32),
+        ("viscous_form", C.c_int32),
         ("n_ports", C.c_int32), ("ports", IbPort * IB_MAX_PORTS),
         ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]

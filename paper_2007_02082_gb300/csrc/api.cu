@@ -76,6 +76,7 @@ struct Engine {
   std::vector<ib_grid_desc> D;
   int ninst = 0;
   bool mixed = false;
+  bool sym = false;   // symmetric viscous form (all members)
   Tols tol{};
   cudaStream_t st = nullptr;
   void* (*alloc)(size_t, void*) = nullptr;
@@ -353,6 +354,7 @@ ib_status mg_upload(Engine& E, MGDev<T>& D) {
 ib_status engine_build(Engine& E) {
   const int n = E.ninst;
   E.mixed = E.D[0].precision == IB_MIXED;
+  E.sym = E.D[0].viscous_form == IB_VISCOUS_SYM;
   E.tol = tolerances(E.D[0]);
   E.brick0.assign(n + 1, 0);
   E.slot0.assign(n + 1, 0);
@@ -377,7 +379,11 @@ ib_status engine_build(Engine& E) {
   // ---- concatenated topology
   std::vector<int32_t> blev, binst, bseg(n + 1), bnbr, ifc, iff, ifo(1, 0), ifk, ifos, hg, hp1, hp2, canon, ins, inp, pins, pinp;
   std::vector<uint16_t> meta;
-  std::vector<double> hl(size_t(n) * 12, 0.0), sf(size_t(n) * 32, 0.0), pdt(n), pnu(n), insh;
+  std::vector<double> hl(size_t(n) * 12, 0.0), sf(size_t(n) * 4 * SF_STRIDE, 0.0), pdt(n), pnu(n), insh;
+  // natural boundary rows of the symmetric viscous form
+  std::vector<int32_t> natslot, natoff(1, 0), natent;
+  std::vector<int8_t> natcomp;
+  std::vector<double> natw;
   std::vector<PortDev> ports;
   for (int i = 0; i < n; ++i) {
     const HostGrid& H = *E.H[i];
@@ -397,13 +403,29 @@ ib_status engine_build(Engine& E) {
     for (int l = 0; l <= H.L; ++l) {
       const double* h = H.levels[l].h;
       const double V = h[0] * h[1] * h[2];
-      double* f = &sf[(i * 4 + l) * 8];
+      double* f = &sf[(i * 4 + l) * SF_STRIDE];
       for (int a = 0; a < 3; ++a) {
         hl[(i * 4 + l) * 3 + a] = h[a];
         f[a] = V / (6.0 * h[a] * h[a]);
         f[4 + a] = V / (24.0 * h[a]);
       }
       f[3] = V / 120.0;
+      f[8] = V / (6.0 * h[0] * h[1]);
+      f[9] = V / (6.0 * h[1] * h[2]);
+      f[10] = V / (6.0 * h[0] * h[2]);
+    }
+    if (E.sym) {
+      NaturalRows R;
+      build_natural_rows(d, H, R);
+      for (size_t r = 0; r < R.row_slot.size(); ++r) {
+        natslot.push_back(int32_t(R.row_slot[r] + S0));
+        for (int32_t e = R.row_off[r]; e < R.row_off[r + 1]; ++e) {
+          natent.push_back(int32_t(R.ent_slot[e] + S0));
+          natcomp.push_back(R.ent_comp[e]);
+          natw.push_back(R.ent_w[e]);
+        }
+        natoff.push_back(int32_t(natent.size()));
+      }
     }
     pdt[i] = d.dt;
     pnu[i] = d.nu;
@@ -516,6 +538,27 @@ ib_status engine_build(Engine& E) {
   TRY(upload(E, &d_hp2, hp2));
   int32_t* d_cwo;
   TRY(upload(E, &d_cwo, cwo));
+  {
+    int32_t *d_ns, *d_no, *d_ne;
+    int8_t* d_nc;
+    double* d_nw;
+    float* d_nw32;
+    std::vector<float> natw32(natw.begin(), natw.end());
+    TRY(upload(E, &d_ns, natslot));
+    TRY(upload(E, &d_no, natoff));
+    TRY(upload(E, &d_ne, natent));
+    TRY(upload(E, &d_nc, natcomp));
+    TRY(upload(E, &d_nw, natw));
+    TRY(upload(E, &d_nw32, natw32));
+    g.sym = E.sym ? 1 : 0;
+    g.n_nat = int32_t(natslot.size());
+    g.nat_slot = d_ns;
+    g.nat_off = d_no;
+    g.nat_ent = d_ne;
+    g.nat_comp = d_nc;
+    g.nat_w64 = d_nw;
+    g.nat_w32 = d_nw32;
+  }
   TRY(dalloc(E, &E.aerr, n, true));
   g.cwo = d_cwo;
   g.ncomp = E.ncomp;
@@ -715,6 +758,7 @@ SolveArgs solve_args(Engine& E, int op, bool bicg, int nc, uint16_t dmask, const
   a.dmask = dmask;
   a.bicg = bicg;
   a.mixed = E.mixed;
+  a.coupled = bicg && nc == 3 && E.sym;   // the symmetric viscous form couples the momentum components
   a.coef64 = coef64;
   a.dinv64 = dinv64;
   a.coef32 = coef32;
@@ -1043,6 +1087,7 @@ ib_status validate_desc(const ib_grid_desc* d) {
   if (!(d->nu > 0) || !(d->rho > 0) || !(d->dt > 0)) return IB_EINVAL;
   if (d->precision != IB_FP64 && d->precision != IB_MIXED) return IB_EINVAL;
   if (d->poisson_pc != IB_PC_MULTIGRID && d->poisson_pc != IB_PC_JACOBI) return IB_EINVAL;
+  if (d->viscous_form != IB_VISCOUS_GRAD && d->viscous_form != IB_VISCOUS_SYM) return IB_EINVAL;
   if (d->n_ports < 1 || d->n_ports > IB_MAX_PORTS) return IB_EINVAL;
   bool outlet = false;
   for (int p = 0; p < d->n_ports; ++p) {
@@ -1268,6 +1313,7 @@ ib_status ib_batch_create(ib_grid* const* members, int32_t n, ib_batch** out) {
     ib_grid* m = members[i];
     if (!m || !m->ready || !m->d.deferred || m->batch) return IB_EINVAL;
     if (m->d.precision != members[0]->d.precision) return IB_EINVAL;
+    if (m->d.viscous_form != members[0]->d.viscous_form) return IB_EINVAL;
     for (int j = 0; j < i; ++j)
       if (members[j] == m) return IB_EINVAL;
   }

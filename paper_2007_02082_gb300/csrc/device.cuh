@@ -49,6 +49,7 @@ constexpr int DBS = 8;          // brick edge (nodes)
 constexpr int DBV = 512;        // nodes per brick = threads per brick CTA
 constexpr int TILE = 10;        // brick plus a one-node halo
 constexpr int TILE3 = 1000;
+constexpr int SF_STRIDE = 16;   // stencil factors per instance and level
 
 // Brick padding: a slot without D_VALID (no active leaf cell of its level
 // touches it) is zero in every vector of the library.  Every kernel writes only
@@ -82,8 +83,9 @@ struct DevGrid {
   const int32_t* __restrict__ scseg;   // [ninst + 1]
   const uint16_t* __restrict__ meta;  // [nslots]
   const double* __restrict__ hl;      // [ninst][4][3] cell spacing per instance and level
-  // stencil factors per instance and level, [ninst][4][8]:
-  //   (V/6)/hx^2, (V/6)/hy^2, (V/6)/hz^2, V/120, (V/24)/hx, (V/24)/hy, (V/24)/hz, 0
+  // stencil factors per instance and level, [ninst][4][SF_STRIDE]:
+  //   (V/6)/hx^2, (V/6)/hy^2, (V/6)/hz^2, V/120, (V/24)/hx, (V/24)/hy, (V/24)/hz, 0,
+  //   (V/6)/(hx hy), (V/6)/(hy hz), (V/6)/(hx hz), 0 ...
   const double* __restrict__ sf64;
   const float* __restrict__ sf32;
   const double* __restrict__ pdt;     // [ninst] time step
@@ -108,6 +110,18 @@ struct DevGrid {
   int64_t ncomp;
   // per-instance error word of the step (ASYNC_TIMEOUT when a bounded wait ran out)
   int32_t* aerr;                      // [ninst]
+  // symmetric viscous form (every instance): transpose-gradient couplings in
+  // the momentum operator and the natural boundary term on outlet and
+  // pressure-inlet rows (row r: slot nat_slot[r], entries nat_off[r] ..
+  // nat_off[r+1], trial slot nat_ent, 3 test + trial component nat_comp)
+  int32_t sym;
+  int32_t n_nat;
+  const int32_t* __restrict__ nat_slot;
+  const int32_t* __restrict__ nat_off;
+  const int32_t* __restrict__ nat_ent;
+  const int8_t* __restrict__ nat_comp;
+  const double* __restrict__ nat_w64;
+  const float* __restrict__ nat_w32;
 };
 
 // Index in the compact arrays of thread t's slot of brick b (a valid slot);
@@ -180,7 +194,7 @@ __device__ __forceinline__ void load_tile(T* tile, const T* __restrict__ x, int6
 
 template <typename T>
 __device__ __forceinline__ const T* stencil_factors(const DevGrid& g, int b) {
-  const int idx = (g.binst[b] * 4 + g.blev[b]) * 8;
+  const int idx = (g.binst[b] * 4 + g.blev[b]) * SF_STRIDE;
   if constexpr (sizeof(T) == 4) return reinterpret_cast<const T*>(g.sf32) + idx;
   else return reinterpret_cast<const T*>(g.sf64) + idx;
 }

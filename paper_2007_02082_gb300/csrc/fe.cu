@@ -101,6 +101,34 @@ __device__ __forceinline__ constexpr bool const_mask() {
   return !std::is_same_v<std::decay_t<MK>, int>;
 }
 
+// Symmetric viscous form: out_i += dt nu sum_k sum_j F_ij w(mask, k, i, j)
+// x_j(neighbour k), the transpose-gradient couplings (grad u^T, grad v) per
+// Kuhn tetrahedron (kuhn_weights.hpp), F_ij = (V/6)/(h_i h_j) from the
+// stencil factors.  xk(k, v) loads the three components at neighbour k.
+template <typename T, typename MK, typename XK>
+__device__ __forceinline__ void add_transpose(MK mk, const T* F, T dtnu, XK&& xk, T (&out)[3]) {
+  T acc[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc[i][j] = T(0);
+#pragma unroll
+  for (int k = 0; k < 15; ++k) {
+    T v[3];
+    xk(k, v);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int w = trans_weight(mk, k, i, j);
+        if (!const_mask<MK>() || w != 0) acc[i][j] += wconv<T>(w) * v[j];
+      }
+  }
+  const T fij[3][3] = {{F[0], F[8], F[10]}, {F[8], F[1], F[9]}, {F[10], F[9], F[2]}};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) out[i] += dtnu * (fij[i][0] * acc[i][0] + fij[i][1] * acc[i][1] + fij[i][2] * acc[i][2]);
+}
+
 __device__ __forceinline__ void spacing(const DevGrid& g, int b, double (&h)[3]) {
   const int inst = g.binst[b], lev = g.blev[b];
   const double* p = g.hl + (inst * 4 + lev) * 3;
@@ -652,7 +680,7 @@ __device__ __forceinline__ void halo15(int t, int& nbk, int& li, int& ti) {
 // coefficient reads of a plain apply).
 // FUSEP: p_new = z + beta p_old while staging the tile (written for the
 // brick's nodes), y = A p_new, and per-component p.y -> alpha (POST_CG_ALPHA).
-template <typename T, int OP, int NC, bool FUSEP, bool PB>
+template <typename T, int OP, int NC, bool FUSEP, bool PB, bool SYM = false>
 __global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict__ x, T* __restrict__ y,
                                                  const T* __restrict__ coef, uint16_t dmask, int post,
                                                  KState* __restrict__ ks, double* __restrict__ partials,
@@ -756,12 +784,26 @@ __global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict_
 #pragma unroll
           for (int c = 0; c < NC; ++c) out[c] *= f3;
         });
-      } else if (act) {
+      } else {
+        if (act) {
 #pragma unroll
-        for (int k = 0; k < 15; ++k) {
-          const T ck = coef[(int64_t)k * g.nslots + s];
+          for (int k = 0; k < 15; ++k) {
+            const T ck = coef[(int64_t)k * g.nslots + s];
 #pragma unroll
-          for (int c = 0; c < NC; ++c) out[c] += ck * tval(c, ti + c_toff[k]);
+            for (int c = 0; c < NC; ++c) out[c] += ck * tval(c, ti + c_toff[k]);
+          }
+        }
+        if constexpr (SYM && NC == 3) {   // symmetric viscous form
+            with_mask(act ? (m & 0xFF) : 0, [&](auto mk) {
+              if (!act) return;
+              const int inst = g.binst[bb];
+              add_transpose<T>(mk, stencil_factors<T>(g, bb), T(g.pdt[inst] * g.pnu[inst]),
+                               [&](int k, T (&v)[3]) {
+#pragma unroll
+                                 for (int c = 0; c < 3; ++c) v[c] = tval(c, ti + c_toff[k]);
+                               },
+                               out);
+            });
         }
       }
 #pragma unroll
@@ -801,9 +843,12 @@ __global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict_
 //  * the tile holds one float4 per node (3 components and a pad), so each
 //    stencil neighbour is one 16-byte shared load.
 // Same arithmetic, in the same order, as k_apply15<float, OP_COEF, 3>.
-__global__ void __launch_bounds__(512, 4) k_apply15_mom32(DevGrid g, const float* __restrict__ x,
-                                                          float* __restrict__ y, const float* __restrict__ coef,
-                                                          uint16_t dmask) {
+// SYM adds the transpose-gradient couplings of the symmetric viscous form
+// (two CTAs per SM: the couplings need more than 32 registers).
+template <bool SYM>
+__global__ void __launch_bounds__(512, SYM ? 2 : 4) k_apply15_mom32(DevGrid g, const float* __restrict__ x,
+                                                                   float* __restrict__ y,
+                                                                   const float* __restrict__ coef, uint16_t dmask) {
   KCOUNT();
   __shared__ __align__(16) float cf[15 * DBV];
   __shared__ float4 tile[TILE3];
@@ -845,7 +890,8 @@ __global__ void __launch_bounds__(512, 4) k_apply15_mom32(DevGrid g, const float
   if (t == 0) mbar_wait_or_flag(&bar, 0, g.aerr + g.binst[b]);
   __syncthreads();
   float out[3] = {0.f, 0.f, 0.f};
-  if (valid && !(m & dmask)) {
+  const bool act = valid && !(m & dmask);
+  if (act) {
 #pragma unroll
     for (int k = 0; k < 15; ++k) {
       const float ck = cf[k * DBV + r];
@@ -855,10 +901,48 @@ __global__ void __launch_bounds__(512, 4) k_apply15_mom32(DevGrid g, const float
       out[2] += ck * v.z;
     }
   }
+  if constexpr (SYM)
+    with_mask(act ? (m & 0xFF) : 0, [&](auto mk) {
+      if (!act) return;
+      const int inst = g.binst[b];
+      add_transpose<float>(mk, stencil_factors<float>(g, b), float(g.pdt[inst] * g.pnu[inst]),
+                           [&](int k, float (&v)[3]) {
+                             const float4 t4 = tile[ti + c_toff[k]];
+                             v[0] = t4.x;
+                             v[1] = t4.y;
+                             v[2] = t4.z;
+                           },
+                           out);
+    });
   if (valid) {   // brick padding stays zero: no store
 #pragma unroll
     for (int c = 0; c < 3; ++c) y[(int64_t)c * g.nslots + s] = out[c];
   }
+}
+
+// y_i(a) -= dt nu sum_e w_e x_j(b_e) on the natural boundary rows of the
+// symmetric viscous form (outlet and pressure-inlet faces), one thread per
+// row; runs after the stencil apply and before the interface sums.
+template <typename T>
+__global__ void k_natural_bterm(DevGrid g, const T* __restrict__ x, T* __restrict__ y) {
+  KCOUNT();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.n_nat) return;
+  const int32_t a = g.nat_slot[r];
+  const int inst = g.binst[a / DBV];
+  const T* w = sizeof(T) == 4 ? reinterpret_cast<const T*>(g.nat_w32) : reinterpret_cast<const T*>(g.nat_w64);
+  T acc[3] = {T(0), T(0), T(0)};
+  for (int e = g.nat_off[r]; e < g.nat_off[r + 1]; ++e) {
+    const int ij = g.nat_comp[e];
+    const int i = ij / 3, j = ij - 3 * (ij / 3);
+    const T v = w[e] * x[(int64_t)j * g.nslots + g.nat_ent[e]];
+    if (i == 0) acc[0] += v;
+    else if (i == 1) acc[1] += v;
+    else acc[2] += v;
+  }
+  const T dtnu = T(g.pdt[inst] * g.pnu[inst]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y[(int64_t)i * g.nslots + a] -= dtnu * acc[i];
 }
 
 template <typename T, int NC, bool FUSEP = false>
@@ -875,11 +959,20 @@ static void launch_apply(const DevGrid& g, int op, const T* x, T* y, const T* co
   else if (op == OP_MASS)
     IBG_LAUNCH((k_apply15<T, OP_MASS, NC, FUSEP, true>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
                rb.partials, rb.counter, zf, pnew);
-  else if constexpr (sizeof(T) == 4 && NC == 3 && !FUSEP)
-    IBG_LAUNCH(k_apply15_mom32, g.nbricks, DBV, 0, st, g, x, y, coef, dmask);
-  else
-    IBG_LAUNCH((k_apply15<T, OP_COEF, NC, FUSEP, true>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
-               rb.partials, rb.counter, zf, pnew);
+  else {
+    if constexpr (sizeof(T) == 4 && NC == 3 && !FUSEP) {
+      if (g.sym) IBG_LAUNCH(k_apply15_mom32<true>, g.nbricks, DBV, 0, st, g, x, y, coef, dmask);
+      else IBG_LAUNCH(k_apply15_mom32<false>, g.nbricks, DBV, 0, st, g, x, y, coef, dmask);
+    } else if (NC == 3 && g.sym) {
+      IBG_LAUNCH((k_apply15<T, OP_COEF, NC, FUSEP, true, true>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post,
+                 ks, rb.partials, rb.counter, zf, pnew);
+    } else {
+      IBG_LAUNCH((k_apply15<T, OP_COEF, NC, FUSEP, true>), g.nbricks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
+                 rb.partials, rb.counter, zf, pnew);
+    }
+    if (NC == 3 && g.sym && g.n_nat > 0)
+      IBG_LAUNCH(k_natural_bterm<T>, (g.n_nat + 127) / 128, 128, 0, st, g, x, y);
+  }
 }
 
 template <typename T>
@@ -959,7 +1052,10 @@ void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st)
 }
 cudaError_t fe_configure() {
   // four 46 KB CTAs per SM: prefer the largest shared-memory carveout
-  return cudaFuncSetAttribute(k_apply15_mom32, cudaFuncAttributePreferredSharedMemoryCarveout,
+  cudaError_t e = cudaFuncSetAttribute(k_apply15_mom32<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       int(cudaSharedmemCarveoutMaxShared));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_apply15_mom32<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                               int(cudaSharedmemCarveoutMaxShared));
 }
 

@@ -100,6 +100,22 @@ __global__ void k_collect_outer(const OState* os, int ninst, SolveRec* rec) {
   R.status = max(R.status, os[i].status);
 }
 
+// Coupled components (one system in NC unknowns per node, the momentum
+// operator of the symmetric viscous form): each component's partial sums
+// become the sums over the components, so the NC states take the same
+// scalars and converge together, which is BiCGStab on the whole vector.
+template <int NC, int NQ>
+__device__ __forceinline__ void couple_sums(double* o) {
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double t = 0.0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) t += o[NQ * c + q];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) o[NQ * c + q] = t;
+  }
+}
+
 // ---------------------------------------------------------------- CG
 template <typename T, int NC>
 __global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict__ b, const T* __restrict__ y,
@@ -375,7 +391,7 @@ __global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restric
                                                    T* __restrict__ r, T* __restrict__ rh, T* __restrict__ p,
                                                    T* __restrict__ v, uint16_t dmask, KState* ks,
                                                    double* partials, unsigned* counter, Cond cond,
-                                                   const OState* skip_os) {
+                                                   const OState* skip_os, int coupled) {
   KCOUNT();
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
   const uint16_t m = g.meta[s];
@@ -396,6 +412,7 @@ __global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restric
   bool any = false;
   for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
     const bool skip = skip_os && skip_os[i].done;
+    if (coupled) couple_sums<NC, 2>(out + (int64_t)i * 2 * NC);
     for (int c = 0; c < NC; ++c) {
       KState& k = ks[i * NC + c];
       k.rr = out[(int64_t)i * 2 * NC + 2 * c];
@@ -479,7 +496,7 @@ __global__ void __launch_bounds__(512) k_bcgv_p(DevGrid g, const T* __restrict__
 template <typename T, int NC>
 __global__ void __launch_bounds__(512) k_bcgv_dot(DevGrid g, const T* __restrict__ a1, const T* __restrict__ b1v,
                                                   uint16_t dmask, int mode, KState* ks, double* partials,
-                                                  unsigned* counter) {
+                                                  unsigned* counter, int coupled) {
   KCOUNT();
   using V = typename Vec16<T>::type;
   using MT = typename Vec16<T>::mt;
@@ -519,7 +536,8 @@ __global__ void __launch_bounds__(512) k_bcgv_dot(DevGrid g, const T* __restrict
   }
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
   if (!grid_sum_last<T, 2 * NC>(tw, partials, counter, g.scseg, g.ninst, out)) return;
-  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
+    if (coupled) couple_sums<NC, 2>(out + (int64_t)i * 2 * NC);
     for (int c = 0; c < NC; ++c) {
       KState& k = ks[i * NC + c];
       if (k.done) continue;
@@ -536,6 +554,7 @@ __global__ void __launch_bounds__(512) k_bcgv_dot(DevGrid g, const T* __restrict
         k.of = float(k.omega);
       }
     }
+  }
 }
 
 // s = r - alpha v, sh = D^-1 s
@@ -595,7 +614,7 @@ __global__ void __launch_bounds__(512) k_bcgv_xr(DevGrid g, T* __restrict__ x, T
                                                  const T* __restrict__ rh, const T* __restrict__ ph,
                                                  const T* __restrict__ sh, const T* __restrict__ sv,
                                                  const T* __restrict__ tv, uint16_t dmask, KState* ks,
-                                                 double* partials, unsigned* counter, Cond cond) {
+                                                 double* partials, unsigned* counter, Cond cond, int coupled) {
   KCOUNT();
   using V = typename Vec16<T>::type;
   using MT = typename Vec16<T>::mt;
@@ -657,7 +676,8 @@ __global__ void __launch_bounds__(512) k_bcgv_xr(DevGrid g, T* __restrict__ x, T
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
   if (!grid_sum_last<T, 2 * NC>(tw, partials, counter, g.scseg, g.ninst, out)) return;
   bool any = false;
-  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x)
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
+    if (coupled) couple_sums<NC, 2>(out + (int64_t)i * 2 * NC);
     for (int c = 0; c < NC; ++c) {
       KState& k = ks[i * NC + c];
       if (k.done) continue;
@@ -673,6 +693,7 @@ __global__ void __launch_bounds__(512) k_bcgv_xr(DevGrid g, T* __restrict__ x, T
       k.rho = rhon;
       any = true;
     }
+  }
   any = block_any(any);
   if (threadIdx.x == 0) set_cond(cond, any);
 }
@@ -884,8 +905,9 @@ static cudaError_t bcg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* 
     if (e != cudaSuccess) return e;
   }
   fe_apply<T>(g, A, NC, x, w.tv, st);
+  const int cpl = a.coupled ? 1 : 0;
   IBG_LAUNCH((k_bcg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, w.tv, w.r, w.rh, w.p, w.v, A.dmask, a.ks,
-             rb.partials, rb.counter, cond, skip_os);
+             rb.partials, rb.counter, cond, skip_os, cpl);
   // v and t hold the interface-summed operator outputs (the start kernel set v = 0)
   return run_loop(cc, st, cond, a.ks, a.ks_host, g.ninst * NC, a.max_iter, 1, 8, [&](cudaStream_t s, const Cond& c) {
     pbegin(a.prof, a.pbase + 2, s);
@@ -896,7 +918,8 @@ static cudaError_t bcg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* 
     fe_apply_local<T>(g, A, NC, w.ph, w.v, s);
     pend(a.prof, s);
     fe_sync<T>(g, NC, w.v, A.dmask, s);
-    IBG_LAUNCH((k_bcgv_dot<T, NC>), g.nschunks, DBV, 0, s, g, w.rh, w.v, A.dmask, 0, a.ks, rb.partials, rb.counter);
+    IBG_LAUNCH((k_bcgv_dot<T, NC>), g.nschunks, DBV, 0, s, g, w.rh, w.v, A.dmask, 0, a.ks, rb.partials, rb.counter,
+               cpl);
     IBG_LAUNCH((k_bcgv_s<T, NC>), g.nschunks, DBV, 0, s, g, w.r, w.v, w.sv, w.sh, A.dinv, A.dmask, a.ks);
     fe_expand2<T>(g, NC, w.sh, (T*)nullptr, s);
     pbegin(a.prof, a.pbase + 0, s);
@@ -904,10 +927,10 @@ static cudaError_t bcg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* 
     pend(a.prof, s);
     fe_sync<T>(g, NC, w.tv, A.dmask, s);
     IBG_LAUNCH((k_bcgv_dot<T, NC>), g.nschunks, DBV, 0, s, g, w.sv, w.tv, A.dmask, 1, a.ks, rb.partials,
-               rb.counter);
+               rb.counter, cpl);
     pbegin(a.prof, a.pbase + 1, s);
     IBG_LAUNCH((k_bcgv_xr<T, NC>), g.nschunks, DBV, 0, s, g, x, w.r, w.rh, w.ph, w.sh, w.sv, w.tv, A.dmask, a.ks,
-               rb.partials, rb.counter, c);
+               rb.partials, rb.counter, c, cpl);
     pend(a.prof, s);
   });
 }
@@ -936,7 +959,6 @@ cudaError_t solve_enqueue(const SolveArgs& a, cudaStream_t st, CaptureCtx* cc) {
     return cudaSuccess;
   }
   OpDesc<float> A32{a.op, a.coef32, a.dmask, a.dinv32, a.prof, a.pbase};
-  const int64_t n = int64_t(a.nc) * g.nslots;
   IBG_LAUNCH(k_init_outer, ib, 128, 0, st, a.os, g.ninst, a.nc, a.rtol * a.rtol, a.max_outer);
   const bool cap = cc && cc->capturing;
   auto residual = [&](cudaStream_t s, const Cond& cl, const Cond& cb) {

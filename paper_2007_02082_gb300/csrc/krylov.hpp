@@ -18,6 +18,7 @@ struct SolveArgs {
   uint16_t dmask = 0;
   bool bicg = false;       // BiCGStab (nonsymmetric) instead of CG
   bool mixed = false;      // FP32 iterations inside FP64 defect correction
+  bool coupled = false;    // BiCGStab on the NC components as one system (shared scalars)
   const double* coef64 = nullptr;
   const double* dinv64 = nullptr;
   const float* coef32 = nullptr;

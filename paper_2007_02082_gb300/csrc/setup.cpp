@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <numeric>
 #include <unordered_map>
 
@@ -461,6 +462,80 @@ ib_status build_host_grid(const ib_grid_desc& d, int64_t M, const double* X, con
     if (!ent.empty()) G.sp_off.push_back(int32_t(ent.size()));
   }
   return IB_OK;
+}
+
+void build_natural_rows(const ib_grid_desc& d, const HostGrid& G, NaturalRows& out) {
+  out = NaturalRows();
+  out.row_off.push_back(0);
+  const int L = G.L;
+  for (int l = 0; l <= L; ++l) {
+    const HostLevel& HL = G.levels[l];
+    const double* h = HL.h;
+    for (int32_t b = HL.brick_begin; b < HL.brick_end; ++b) {
+      for (int t = 0; t < BV; ++t) {
+        const int64_t s = int64_t(b) * BV + t;
+        const uint16_t m = G.meta[s];
+        if (!(m & M_VALID) || (m & M_VDIR)) continue;
+        const int64_t q[3] = {int64_t(G.brick_coord[3 * b]) * BS + (t % BS),
+                              int64_t(G.brick_coord[3 * b + 1]) * BS + ((t / BS) % BS),
+                              int64_t(G.brick_coord[3 * b + 2]) * BS + t / (BS * BS)};
+        std::map<std::pair<int32_t, int>, double> acc;   // (trial slot, 3 i + j) -> weight
+        for (int p = 0; p < d.n_ports; ++p) {
+          const ib_port& P = d.ports[p];
+          if (P.kind == IB_INLET_VELOCITY) continue;
+          const int ax = P.axis;
+          const int64_t plane = P.side == 0 ? 0 : (G.n[ax] << l);   // in level-l lattice units
+          if (q[ax] != plane) continue;
+          const double nrm = P.side == 0 ? -1.0 : 1.0;
+          const int u = (ax + 1) % 3, v = (ax + 2) % 3;
+          const double area = 0.5 * h[u] * h[v];
+          for (int c = 0; c < 8; ++c) {
+            if (!((m >> c) & 1)) continue;   // incident cell c (bit order x, y, z) active
+            const int64_t lo[3] = {q[0] + (c & 1) - 1, q[1] + ((c >> 1) & 1) - 1, q[2] + ((c >> 2) & 1) - 1};
+            static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+            for (const auto& pm : perms) {
+              int64_t vx[4][3];
+              for (int a = 0; a < 3; ++a) vx[0][a] = lo[a];
+              for (int k = 1; k < 4; ++k) {
+                for (int a = 0; a < 3; ++a) vx[k][a] = vx[k - 1][a];
+                vx[k][pm[k - 1]] += 1;
+              }
+              int self = -1, nplane = 0;
+              for (int k = 0; k < 4; ++k) {
+                if (vx[k][0] == q[0] && vx[k][1] == q[1] && vx[k][2] == q[2]) self = k;
+                if (vx[k][ax] == plane) nplane++;
+              }
+              if (self < 0 || nplane != 3) continue;   // no face of this tetrahedron in the plane at the node
+              // barycentric gradients in units 1/h: -e_p0, e_p0 - e_p1, e_p1 - e_p2, e_p2
+              int gv[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+              gv[0][pm[0]] = -1;
+              gv[1][pm[0]] = 1;
+              gv[1][pm[1]] = -1;
+              gv[2][pm[1]] = 1;
+              gv[2][pm[2]] = -1;
+              gv[3][pm[2]] = 1;
+              for (int k = 0; k < 4; ++k) {
+                const int32_t sb = slot_of(G, l, vx[k][0], vx[k][1], vx[k][2]);
+                if (sb < 0) continue;
+                for (int i = 0; i < 3; ++i) {
+                  if (!gv[k][i]) continue;
+                  acc[{sb, 3 * i + ax}] += nrm * (double(gv[k][i]) / h[i]) * area / 3.0;
+                }
+              }
+            }
+          }
+        }
+        if (acc.empty()) continue;
+        out.row_slot.push_back(int32_t(s));
+        for (const auto& kv : acc) {
+          out.ent_slot.push_back(kv.first.first);
+          out.ent_comp.push_back(int8_t(kv.first.second));
+          out.ent_w.push_back(kv.second);
+        }
+        out.row_off.push_back(int32_t(out.ent_slot.size()));
+      }
+    }
+  }
 }
 
 }  // namespace ibg

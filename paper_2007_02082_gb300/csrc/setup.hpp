@@ -94,4 +94,19 @@ struct HostGrid {
 ib_status build_host_grid(const ib_grid_desc& d, int64_t M, const double* X, const double* dS,
                           const double* UB, const uint8_t* inside, HostGrid& G, std::string& err);
 
+// Natural boundary term of the symmetric viscous form: ((grad u)^T n, phi_a)
+// over the tetrahedron faces in the plane of an outlet or pressure-inlet port
+// (n the outward normal).  One row per stored slot without a velocity
+// condition that is a vertex of such a face, at that slot's level; entry e
+// adds w_e * u_{comp_e % 3}(slot_e) to component comp_e / 3 of the row's term
+// (test component, trial component).  The step subtracts nu times the term.
+struct NaturalRows {
+  std::vector<int32_t> row_slot;   // [rows]
+  std::vector<int32_t> row_off;    // [rows + 1]
+  std::vector<int32_t> ent_slot;   // trial slot
+  std::vector<int8_t> ent_comp;    // 3 * test component + trial component
+  std::vector<double> ent_w;
+};
+void build_natural_rows(const ib_grid_desc& d, const HostGrid& G, NaturalRows& out);
+
 }  // namespace ibg

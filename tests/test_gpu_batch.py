@@ -57,6 +57,36 @@ def test_member_bitwise_alone_and_in_mix(precision):
         m.close()
 
 
+def test_symmetric_form_members_alone_and_in_mix():
+    """Members of the symmetric viscous form (coupled momentum components,
+    natural boundary rows) keep their bits alone and in a mix; a batch cannot
+    mix the two viscous forms."""
+    from paper_2007_02082_gb300 import IBBatch, IBError, IBGrid
+    cases = [W.cylinder_case(n=(8, 8, 8), length=1.0, half_width=0.6, M=300, seed=61, max_level=1, refine_band=1,
+                             reduce_band=1, nu=0.02, dt=0.002, b=(0.5,), viscous="sym"),
+             W.cylinder_case(n=(8, 8, 16), length=2.0, M=250, seed=62, nu=0.05, dt=0.01, inlet=W.PINLET, a0=0.8,
+                             viscous="sym")]
+    alone = []
+    for c in cases:
+        g = IBGrid(c, precision="mixed", deferred=True)
+        b = IBBatch([g])
+        assert np.all(b.step(2) == 0)
+        alone.append(g.ib_fields_get("U"))
+        b.close()
+        g.close()
+    mem = [IBGrid(c, precision="mixed", deferred=True) for c in cases]
+    batch = IBBatch(mem)
+    assert np.all(batch.step(2) == 0)
+    for i, m in enumerate(mem):
+        assert np.array_equal(m.ib_fields_get("U"), alone[i]), i
+    batch.close()
+    other = IBGrid(_cases()[0], precision="mixed", deferred=True)
+    with pytest.raises(IBError):
+        IBBatch([mem[0], other])
+    for m in mem + [other]:
+        m.close()
+
+
 def test_state_carries_across_batches():
     """Member B steps 2 times with A, then 2 times with C: bitwise B stepped 4
     times alone (u, p and the warm starts Phi, F travel in the snapshot)."""

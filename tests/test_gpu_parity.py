@@ -32,6 +32,14 @@ def _cases():
         # pressure inlet (Sec. 3.1's driving), pulsating, on a refined face; U_max ~ 1
         "pressure_inlet": (W.cylinder_refined_small(n=(16, 16, 8), seed=23, inlet=W.PINLET, a0=0.16, b=(0.08,)),
                            4),
+        # symmetric viscous form 2 nu (eps(u), eps(v)) (Eq. 1): coupled momentum
+        # components, natural boundary term on the outlet (refined grid)
+        "sym_refined": (W.cylinder_case(n=(8, 8, 8), length=1.0, half_width=0.6, M=300, seed=51, max_level=1,
+                                        refine_band=1, reduce_band=1, nu=0.02, dt=0.002, b=(0.5,), viscous="sym"), 3),
+        # ... and on a refined pressure inlet as well
+        "sym_pressure_inlet": (W.cylinder_case(n=(10, 10, 6), length=0.75, half_width=0.6, M=300, seed=52,
+                                               max_level=1, refine_band=1, reduce_band=2, nu=0.02, dt=0.005,
+                                               inlet=W.PINLET, a0=1.2, b=(0.6,), viscous="sym"), 3),
     }
 
 
@@ -103,7 +111,7 @@ def test_fp64_step_parity(name):
     g.close()
 
 
-@pytest.mark.parametrize("name", ["uniform", "refined", "pressure_inlet"])
+@pytest.mark.parametrize("name", ["uniform", "refined", "pressure_inlet", "sym_refined", "sym_pressure_inlet"])
 def test_mixed_step_parity(name):
     _, steps = CASES[name]
     o, hist = oracle_run(name)

@@ -71,6 +71,7 @@ def _desc(case):
         d.n[a] = case["n"][a]
     d.max_level, d.refine_band, d.reduce_band = case["max_level"], case["refine_band"], case["reduce_band"]
     d.nu, d.rho, d.dt = case["nu"], case["rho"], case["dt"]
+    d.viscous_form = 1 if case.get("viscous", "grad") == "sym" else 0
     d.n_ports = len(case["ports"])
     for k, p in enumerate(case["ports"]):
         d.ports[k] = _port_struct(p)
