@@ -45,6 +45,18 @@ def workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def apply_variant(case, args):
+    """The viscous form and the inlet condition of the timed workload."""
+    case["viscous"] = args.viscous
+    if args.inlet == "pressure":
+        p = case["ports"][0]
+        if p["kind"] != "inlet":
+            raise SystemExit("--inlet pressure needs a workload whose first port is a velocity inlet")
+        f = 16.0 * case["nu"] * case["extent"][p["axis"]] / p["radius"] ** 2
+        p.update(kind="pinlet", a0=p["a0"] * f, a=tuple(v * f for v in p["a"]), b=tuple(v * f for v in p["b"]))
+    return case
+
+
 def sample_case(name):
     """Bounded sample of the workload for the CPU oracle: the same cross-section,
     grid, bands and point density over 8 coarse cells of the tube's length."""
@@ -161,7 +173,7 @@ def run_native(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     load_library(build_if_missing=True)
-    case = workload(args.workload)
+    case = apply_variant(workload(args.workload), args)
     g = IBGrid(case, precision=args.precision, device=local_rank, poisson_pc=args.poisson_pc)
     info0 = g.ib_grid_info()
     cells = info0["n_leaf_cells"]
@@ -242,6 +254,8 @@ def run_native(args, rank, world, local_rank):
         try:
             tj = json.load(open(tfile))
             key = f"{args.workload}:{args.precision}:{dom}"
+            if args.viscous != "grad" or args.inlet != "velocity":
+                key += f":{args.viscous}:{args.inlet}"
             traffic = tj.get(key)
         except Exception:
             traffic = None
@@ -298,6 +312,7 @@ def run_native(args, rank, world, local_rank):
                    "precision": args.precision,
                    "poisson_pc": (f"multigrid V(2,2), {info0['mg_levels']} levels, coarsest {info0['mg_coarsest']}"
                                   if info0["mg_levels"] else "jacobi"),
+                   "viscous": args.viscous, "inlet": args.inlet,
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": int(launches),
@@ -360,6 +375,11 @@ def main():
     ap.add_argument("--accuracy-steps", type=int, default=20,
                     help="steps of the mixed vs FP64 comparison reported under 'accuracy' (0: skip)")
     ap.add_argument("--workload", default="cylinder_64x64x256_L1")
+    ap.add_argument("--viscous", default="grad", choices=["grad", "sym"],
+                    help="viscous form: nu (grad u, grad v) or the symmetric 2 nu (eps(u), eps(v))")
+    ap.add_argument("--inlet", default="velocity", choices=["velocity", "pressure"],
+                    help="drive the tube by its inlet velocity or by the inlet pressure that gives the same "
+                         "Poiseuille peak (16 nu L / R^2 per unit of peak speed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nvtx", action="store_true",
                     help="wrap each timed step in an NVTX range 'ipcs_step' and each eagerly replayed step "
