@@ -268,6 +268,27 @@ ib_status ipcs_step(ib_grid* g, int32_t nsteps);
 ib_status ib_fields_get(ib_grid* g, int32_t field, void* dst, size_t bytes, int32_t dst_on_device);
 ib_status ib_fields_set(ib_grid* g, int32_t field, const void* src, size_t bytes, int32_t src_on_device);
 
+/*
+ * ib_set_points: move the Lagrangian points of a standalone handle (a moving
+ * or deforming wall, the case the IB method exists for: the Eulerian grid does
+ * not follow the wall, Sec. 1).  For the following steps the points are at
+ *   X        double [M][3], coordinates inside the box
+ *   UB       double [M][3] prescribed wall velocities, or NULL for zero
+ * (host pointers, or device pointers when on_device = 1; M as given to
+ * ib_set_boundary, dS unchanged).  The supports (Eq. 17), delta weights
+ * (Eq. 18), the A_F pattern and values (Eq. 22) and the spreading lists
+ * (Eq. 19) are rebuilt on the device, every list in sorted order, so the
+ * result equals a fresh ib_set_boundary at X except for the refinement and
+ * domain reduction, which stay those of the first geometry.  The step graph is
+ * captured again at the next step.  Synchronises the handle's stream.
+ * Errors: IB_EINVAL (M differs, a point outside the box, a support touching a
+ * hanging node or a coarser level: the points must stay inside the finest
+ * refined band; a point without a free support node), IB_ESTATE (not ready,
+ * or a deferred handle: batches keep their geometry), IB_ENOMEM, IB_ECUDA.
+ * After IB_EINVAL the handle keeps stepping with the points it had.
+ */
+ib_status ib_set_points(ib_grid* g, int64_t M, const double* X, const double* UB, int32_t on_device);
+
 /* ib_grid_info: counts and the last step's statistics. */
 ib_status ib_grid_info(const ib_grid* g, ib_info* out);
 

@@ -681,6 +681,21 @@ class Oracle:
     def _dof(self, v):
         return v[~self.mesh.hanging]
 
+    def set_points(self, X, UB=None):
+        """Moving or deforming wall: the Lagrangian points take positions X
+        (M, 3) and prescribed velocities U_B (zero if None) for the following
+        steps; the supports, W, W_f and A_F are rebuilt there (Eq. 17-22 at the
+        new positions; the area elements dS stay).  The IB method's reason to
+        exist is that the Eulerian grid does not follow the wall (Sec. 1)."""
+        X = np.asarray(X, dtype=np.float64)
+        if X.shape != (self.ib.M, 3):
+            raise ValueError("set_points keeps the number of points")
+        case = dict(self.case)
+        case["X"] = X
+        case["UB"] = np.zeros_like(X) if UB is None else np.asarray(UB, dtype=np.float64)
+        self.case = case
+        self.ib = IB(self.mesh, case, ~self.vdir_node & ~self.mesh.hanging)
+
     def step(self):
         m, ops, c = self.mesh, self.ops, self.case
         dt, nu, rho = c["dt"], c["nu"], c["rho"]

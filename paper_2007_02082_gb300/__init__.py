@@ -222,6 +222,27 @@ class IBGrid:
         arr = np.ascontiguousarray(values, dtype=dt).reshape(shape)
         self._check("ib_fields_set", self.lib.ib_fields_set(self.h, FIELD[field], arr.ctypes.data, arr.nbytes, 0))
 
+    def ib_set_points(self, X, UB=None):
+        """Move the Lagrangian points (moving or deforming wall): X and U_B of
+        shape (M, 3), numpy arrays or CUDA tensors; U_B None means a wall at
+        rest.  The supports, weights, A_F and spreading lists are rebuilt on
+        the device for the following steps."""
+        if hasattr(X, "is_cuda") and X.is_cuda:
+            import torch
+            x = X.detach().to(torch.float64).contiguous().reshape(-1, 3)
+            u = None if UB is None else UB.detach().to(device=x.device, dtype=torch.float64).contiguous().reshape(-1, 3)
+            if u is not None and u.shape != x.shape:
+                raise ValueError("X and UB differ in shape")
+            self._check("ib_set_points", self.lib.ib_set_points(self.h, x.shape[0], C.c_void_p(x.data_ptr()),
+                                                                None if u is None else C.c_void_p(u.data_ptr()), 1))
+            return
+        x = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+        u = None if UB is None else np.ascontiguousarray(UB, dtype=np.float64).reshape(-1, 3)
+        if u is not None and u.shape != x.shape:
+            raise ValueError("X and UB differ in shape")
+        self._check("ib_set_points", self.lib.ib_set_points(self.h, x.shape[0], x.ctypes.data,
+                                                            None if u is None else u.ctypes.data, 0))
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.ib_grid_destroy(self.h)

@@ -36,6 +36,7 @@
 #include "fe.hpp"
 #include "ib.h"
 #include "ib.hpp"
+#include "ibmove.hpp"
 #include "krylov.hpp"
 #include "mg.hpp"
 #include "noalloc.hpp"
@@ -48,6 +49,7 @@ unsigned long long fe_kcount();
 unsigned long long krylov_kcount();
 unsigned long long ib_kcount();
 unsigned long long mg_kcount();
+unsigned long long move_kcount();
 }
 
 namespace {
@@ -99,6 +101,16 @@ struct Engine {
   int32_t* ok = nullptr;
   int32_t* aerr = nullptr;        // [ninst] device error word of the step
   int32_t* aerr_host = nullptr;   // pinned copy
+  // moving points (standalone engines): finest-level brick map and rebuild buffers
+  bool mv_ready = false;
+  int32_t* mv_bmap = nullptr;
+  uint8_t* mv_cells = nullptr;    // coarse cells: level when active, 255 otherwise
+  int32_t mv_nb[3] = {0, 0, 0};
+  int64_t mv_nf[3] = {0, 0, 0};
+  int32_t *mv_bins = nullptr, *mv_rcnt = nullptr, *mv_scratch = nullptr, *mv_err = nullptr;
+  int32_t *mv_scnt = nullptr, *mv_sstart = nullptr, *mv_sfill = nullptr, *mv_sflag = nullptr, *mv_sidx = nullptr;
+  double *mv_xprev = nullptr, *mv_ubprev = nullptr;
+  int64_t af_cap = 0;             // capacity of ib.col / ib.val
   // fields [3][ns] / [ns]
   double *ubuf[2] = {nullptr, nullptr}, *pbuf[2] = {nullptr, nullptr};
   double *u = nullptr, *un = nullptr, *p = nullptr, *pn = nullptr, *phi = nullptr, *ut = nullptr, *uib = nullptr;
@@ -704,6 +716,7 @@ ib_status engine_build(Engine& E) {
   ib.iorigin = d_iorg; ib.ihf = d_ihf; ib.icoef = d_icoef; ib.binst = d_binst;
   TRY(dalloc(E, &ib.W, 64 * Mt, true));
   TRY(dalloc(E, &ib.val, int64_t(col.size()), true));
+  E.af_cap = int64_t(col.size());
   TRY(dalloc(E, &ib.dinv, Mt, true));
   TRY(dalloc(E, &E.BF, 3 * Mt, true));
   TRY(dalloc(E, &E.Gf, 3 * Mt, true));
@@ -1070,7 +1083,7 @@ void fill_info(const HostGrid& H, const MGHost* mg, const Engine* E, int64_t dev
     if (m & M_VALID) nv++;
   I.n_valid_slots = nv;
   I.device_bytes = dev_bytes;
-  I.kernel_launches = int64_t(fe_kcount() + krylov_kcount() + ib_kcount() + mg_kcount());
+  I.kernel_launches = int64_t(fe_kcount() + krylov_kcount() + ib_kcount() + mg_kcount() + move_kcount());
   if (E) {
     for (int k = 0; k < Prof::K; ++k) {
       I.prof_ms[k] = E->prof.ms[k];
@@ -1303,6 +1316,163 @@ void ib_grid_destroy(ib_grid* g) {
   }
   snap_free(g);
   delete g;
+}
+
+// ---------------------------------------------------------------- moving points
+namespace {
+
+MoveGrid move_grid(const Engine& E) {
+  MoveGrid G{};
+  G.bmap = E.mv_bmap;
+  for (int a = 0; a < 3; ++a) {
+    G.nb[a] = E.mv_nb[a];
+    G.nf[a] = E.mv_nf[a];
+  }
+  G.meta = E.g.meta;
+  G.origin = E.ib.iorigin;
+  G.hf = E.ib.ihf;
+  G.cell_level = E.mv_cells;
+  const HostGrid& H = *E.H[0];
+  for (int a = 0; a < 3; ++a) G.n[a] = int32_t(H.n[a]);
+  G.L = H.L;
+  return G;
+}
+
+ib_status move_alloc(Engine& E) {
+  if (E.mv_ready) return IB_OK;
+  const HostGrid& H = *E.H[0];
+  const HostLevel& HL = H.levels[H.L];
+  for (int a = 0; a < 3; ++a) {
+    E.mv_nb[a] = int32_t(HL.nb[a]);
+    E.mv_nf[a] = H.n[a] << H.L;
+  }
+  TRY(upload(E, &E.mv_bmap, HL.brick_map));
+  std::vector<uint8_t> cells(H.active.size());
+  for (size_t c = 0; c < cells.size(); ++c) cells[c] = H.active[c] ? uint8_t(H.level[c]) : uint8_t(255);
+  TRY(upload(E, &E.mv_cells, cells));
+  const MoveGrid G = move_grid(E);
+  const int64_t nb = mv_nbins(G), Mt = E.Mtot, ns = E.ns, M = H.M;
+  TRY(dalloc(E, &E.mv_bins, 3 * (nb + 1) + M + 1, true));
+  TRY(dalloc(E, &E.mv_rcnt, Mt + 1, true));
+  const int64_t sc = std::max(scan_scratch_len(nb), std::max(scan_scratch_len(Mt), scan_scratch_len(ns)));
+  TRY(dalloc(E, &E.mv_scratch, sc, true));
+  TRY(dalloc(E, &E.mv_err, 4, true));
+  TRY(dalloc(E, &E.mv_scnt, ns + 1, true));
+  TRY(dalloc(E, &E.mv_sstart, ns + 1, true));
+  TRY(dalloc(E, &E.mv_sfill, ns + 1, true));
+  TRY(dalloc(E, &E.mv_sflag, ns + 1, true));
+  TRY(dalloc(E, &E.mv_sidx, ns + 1, true));
+  TRY(dalloc(E, &E.mv_xprev, 3 * M + 1, true));
+  TRY(dalloc(E, &E.mv_ubprev, 3 * M + 1, true));
+  // spreading lists at their largest (every support node of every point free)
+  int32_t *sp_ent, *sp_slot, *sp_off;
+  TRY(dalloc(E, &sp_ent, 64 * M + 1, true));
+  TRY(dalloc(E, &sp_slot, std::min<int64_t>(64 * M, ns) + 1, true));
+  TRY(dalloc(E, &sp_off, std::min<int64_t>(64 * M, ns) + 2, true));
+  E.ib.sp_ent = sp_ent;
+  E.ib.sp_slot = sp_slot;
+  E.ib.sp_off = sp_off;
+  E.mv_ready = true;
+  return IB_OK;
+}
+
+// Rebuild every structure of the IB step from the positions in E.X.
+ib_status move_rebuild(Engine& E) {
+  const HostGrid& H = *E.H[0];
+  const int64_t M = H.M, Mt = E.Mtot, ns = E.ns;
+  cudaStream_t st = E.st;
+  IBDev& ib = E.ib;
+  const MoveGrid G = move_grid(E);
+  int32_t* org = const_cast<int32_t*>(ib.org);
+  int32_t* slot = const_cast<int32_t*>(ib.slot);
+  uint64_t* fb = const_cast<uint64_t*>(ib.freeb);
+  int32_t* rowptr = const_cast<int32_t*>(ib.rowptr);
+  CK(cudaMemsetAsync(E.mv_err, 0, sizeof(int32_t), st));
+  mv_supports(G, M, E.X, org, slot, fb, E.mv_err, st);
+  mv_af_count(G, M, Mt, org, E.mv_bins, E.mv_rcnt, rowptr, E.mv_scratch, st);
+  int32_t hv[2] = {0, 0};
+  CK(cudaMemcpyAsync(hv, E.mv_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hv + 1, rowptr + Mt, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hv[0] != MV_OK) {
+    E.err = hv[0] == MV_OUTSIDE ? "a Lagrangian point outside the box"
+          : hv[0] == MV_NOFREE  ? "a Lagrangian point has no free support node"
+                                : "an IB support touches a hanging node or a coarser level (the points left "
+                                  "the finest refined band)";
+    return IB_EINVAL;
+  }
+  if (hv[1] > E.af_cap) {   // more overlapping pairs than ever before: grow A_F
+    const int64_t cap = int64_t(hv[1]) + int64_t(hv[1]) / 2;
+    int32_t* col;
+    double* val;
+    TRY(dalloc(E, &col, cap, true));
+    TRY(dalloc(E, &val, cap, true));
+    ib.col = col;
+    ib.val = val;
+    E.af_cap = cap;
+  }
+  mv_af_fill(G, M, org, E.mv_bins, rowptr, const_cast<int32_t*>(ib.col), st);
+  ib_weights(ib, st);
+  ib_assemble(ib, st);
+  mv_spread(M, ns, slot, fb, E.mv_scnt, E.mv_sstart, E.mv_sfill, E.mv_sflag, E.mv_sidx,
+            const_cast<int32_t*>(ib.sp_ent), const_cast<int32_t*>(ib.sp_slot), const_cast<int32_t*>(ib.sp_off),
+            E.mv_scratch, st);
+  int32_t nsp = 0;
+  CK(cudaMemcpyAsync(&nsp, E.mv_sidx + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ib.n_sp = nsp;
+  return IB_OK;
+}
+
+}  // namespace
+
+ib_status ib_set_points(ib_grid* g, int64_t M, const double* X, const double* UB, int32_t on_device) {
+  if (!g || !X) return IB_EINVAL;
+  if (!g->ready) { g->err = "ib_set_boundary has not succeeded"; return IB_ESTATE; }
+  if (!g->eng) { g->err = "a deferred handle keeps its geometry"; return IB_ESTATE; }
+  if (M != g->H.M) { g->err = "ib_set_points keeps the number of points"; return IB_EINVAL; }
+  Engine& E = *g->eng;
+  cudaStream_t st = E.st;
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  ib_status s = move_alloc(E);
+  if (s != IB_OK) { g->err = E.err; return s; }
+  auto fail = [&](ib_status code) { g->err = E.err; return code; };
+#define CKG(x)                                                                                    \
+  do {                                                                                            \
+    cudaError_t e_ = (x);                                                                         \
+    if (e_ != cudaSuccess) { E.err = std::string("CUDA: ") + cudaGetErrorString(e_); return fail(IB_ECUDA); } \
+  } while (0)
+  if (M) {
+    CKG(cudaMemcpyAsync(E.mv_xprev, E.X, 3 * M * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CKG(cudaMemcpyAsync(E.mv_ubprev, E.UB, 3 * M * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CKG(cudaMemcpyAsync(E.X, X, 3 * M * sizeof(double), kin, st));
+    if (UB) CKG(cudaMemcpyAsync(E.UB, UB, 3 * M * sizeof(double), kin, st));
+    else CKG(cudaMemsetAsync(E.UB, 0, 3 * M * sizeof(double), st));
+  }
+  s = move_rebuild(E);
+  if (s == IB_EINVAL) {   // keep the previous points
+    const std::string why = E.err;
+    CKG(cudaMemcpyAsync(E.X, E.mv_xprev, 3 * M * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CKG(cudaMemcpyAsync(E.UB, E.mv_ubprev, 3 * M * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (move_rebuild(E) != IB_OK) return fail(IB_ECUDA);
+    E.err = why;
+  }
+  if (s != IB_OK) return fail(s);
+  // the captured step graphs hold the old list lengths and buffers
+  for (int k = 0; k < 2; ++k)
+    if (E.gexec[k]) { cudaGraphExecDestroy(E.gexec[k]); E.gexec[k] = nullptr; }
+  // host copies of the inputs and supports (exported by ib_fields_get)
+  HostGrid& H = g->H;
+  if (M) {
+    CKG(cudaMemcpyAsync(H.X.data(), E.X, 3 * M * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CKG(cudaMemcpyAsync(H.UB.data(), E.UB, 3 * M * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CKG(cudaMemcpyAsync(H.ib_origin.data(), E.ib.org, 3 * M * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CKG(cudaMemcpyAsync(H.ib_slot.data(), E.ib.slot, 64 * M * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CKG(cudaMemcpyAsync(H.ib_free.data(), E.ib.freeb, M * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  }
+  CKG(cudaStreamSynchronize(st));
+#undef CKG
+  return IB_OK;
 }
 
 // ---------------------------------------------------------------- batches

@@ -407,3 +407,34 @@ def test_symmetric_form_keeps_poiseuille():
             ins = r2 < 0.4 ** 2
             errs[form] = math.sqrt(np.mean((o.u[ins, 2] - u0[ins, 2]) ** 2))
         assert abs(errs["sym"] - errs["grad"]) <= 0.02 * errs["grad"], (inlet, errs)
+
+
+# ---------------------------------------------------------------- moving wall
+def _translated(case, shift):
+    return np.asarray(case["X"]) + np.asarray(shift)[None, :]
+
+
+def test_moving_wall_rebuild_is_static_when_points_stay():
+    """Setting the points to where they are changes nothing, bit for bit."""
+    c = W.cylinder_case(n=(8, 8, 16), length=2.0, M=250, seed=3, nu=0.1, dt=0.01)
+    a = ibfe.Oracle(c).run(1)
+    b = ibfe.Oracle(c).run(1)
+    b.set_points(c["X"], c["UB"])
+    a.run(2)
+    b.run(2)
+    assert np.array_equal(a.u, b.u) and np.array_equal(a.p, b.p)
+
+
+def test_moving_wall_enforces_the_new_wall_velocity():
+    """After a move the corrected velocity interpolated with the delta kernel at
+    the NEW positions equals the NEW wall velocity (Eq. 15-16 with the
+    supports rebuilt), and differs from it at the old positions."""
+    c = W.cylinder_case(n=(8, 8, 32), M=300, dt=0.05)
+    o = ibfe.Oracle(c).run(1)
+    old = ibfe.IB(o.mesh, c, ~o.vdir_node & ~o.mesh.hanging)
+    X1 = _translated(c, (0.037, -0.021, 0.013))
+    UB1 = np.tile([0.2, -0.1, 0.05], (len(X1), 1))
+    o.set_points(X1, UB1)
+    o.step()
+    assert np.abs(o.ib.W @ o.u_ib - UB1).max() < 1e-11
+    assert np.abs(old.W @ o.u_ib - UB1).max() > 1e-3
