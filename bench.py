@@ -57,6 +57,27 @@ def apply_variant(case, args):
     return case
 
 
+def moving_wall(case, device):
+    """Wall motion for --moving: every point oscillates along x with amplitude
+    0.4 finest cells and period 25 steps, wall velocity the time derivative.
+    Returns n -> (X, U_B) at t = (n + 1) dt as CUDA tensors."""
+    import math
+    import torch
+    X0 = torch.tensor(case["X"], dtype=torch.float64, device=device)
+    hf = case["extent"][0] / (case["n"][0] * 2 ** case["max_level"])
+    amp, period, dt = 0.4 * hf, 25 * case["dt"], case["dt"]
+    w = 2.0 * math.pi / period
+
+    def at(n):
+        t = (n + 1) * dt
+        X = X0.clone()
+        X[:, 0] += amp * math.sin(w * t)
+        UB = torch.zeros_like(X0)
+        UB[:, 0] = amp * w * math.cos(w * t)
+        return X, UB
+    return at
+
+
 def sample_case(name):
     """Bounded sample of the workload for the CPU oracle: the same cross-section,
     grid, bands and point density over 8 coarse cells of the tube's length."""
@@ -184,10 +205,28 @@ def run_native(args, rank, world, local_rank):
         import torch.distributed as dist_mod
         dist = dist_mod
 
+    wall = moving_wall(case, f"cuda:{local_rank}") if args.moving else None
+    nstep = [0]
+    rebuild_ms = [0.0]
+
+    def step():
+        if wall is not None:
+            X, UB = wall(nstep[0])
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.ib_set_points(X, UB)
+            e1.record(stream)
+            e1.synchronize()
+            rebuild_ms[0] += e0.elapsed_time(e1)
+        g.ipcs_step(1)
+        nstep[0] += 1
+
     for _ in range(args.warmup):
         flush.zero_()
-        g.ipcs_step(1)
+        step()
     torch.cuda.synchronize()
+    rebuild_ms[0] = 0.0
     i1 = g.ib_grid_info()
     clocks = ClockSampler(local_rank)
     if dist:
@@ -201,7 +240,7 @@ def run_native(args, rank, world, local_rank):
         flush.zero_()                     # evict the working set from L2 between steps
         if args.nvtx:
             torch.cuda.nvtx.range_push("ipcs_step")
-        g.ipcs_step(1)
+        step()
         if args.nvtx:
             torch.cuda.nvtx.range_pop()
     t1.record(stream)
@@ -291,8 +330,15 @@ def run_native(args, rank, world, local_rank):
     if args.accuracy_steps > 0 and args.precision == "mixed":
         ga = IBGrid(case, precision="mixed", device=local_rank, poisson_pc=args.poisson_pc)
         gb = IBGrid(case, precision="fp64", device=local_rank, poisson_pc=args.poisson_pc)
-        ga.ipcs_step(args.accuracy_steps)
-        gb.ipcs_step(args.accuracy_steps)
+        if wall is None:
+            ga.ipcs_step(args.accuracy_steps)
+            gb.ipcs_step(args.accuracy_steps)
+        else:   # the same wall motion on both paths
+            for n in range(args.accuracy_steps):
+                X, UB = wall(n)
+                for h in (ga, gb):
+                    h.ib_set_points(X, UB)
+                    h.ipcs_step(1)
         acc = {}
         for f in ("U", "P"):
             xa, xb = ga.ib_fields_get(f), gb.ib_fields_get(f)
@@ -313,6 +359,9 @@ def run_native(args, rank, world, local_rank):
                    "poisson_pc": (f"multigrid V(2,2), {info0['mg_levels']} levels, coarsest {info0['mg_coarsest']}"
                                   if info0["mg_levels"] else "jacobi"),
                    "viscous": args.viscous, "inlet": args.inlet,
+                   "moving": ("wall oscillating along x, amplitude 0.4 finest cells, period 25 steps; "
+                              f"device rebuild {rebuild_ms[0] / args.steps:.3f} ms per step, inside the timed step")
+                   if wall is not None else None,
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": int(launches),
@@ -381,6 +430,9 @@ def main():
                     help="drive the tube by its inlet velocity or by the inlet pressure that gives the same "
                          "Poiseuille peak (16 nu L / R^2 per unit of peak speed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--moving", action="store_true",
+                    help="move the wall every step (ib_set_points: device rebuild of the IB structures), "
+                         "timed with the step")
     ap.add_argument("--nvtx", action="store_true",
                     help="wrap each timed step in an NVTX range 'ipcs_step' and each eagerly replayed step "
                          "in 'ipcs_step_eager'")

@@ -279,8 +279,10 @@ ib_status ib_fields_set(ib_grid* g, int32_t field, const void* src, size_t bytes
  * (Eq. 18), the A_F pattern and values (Eq. 22) and the spreading lists
  * (Eq. 19) are rebuilt on the device, every list in sorted order, so the
  * result equals a fresh ib_set_boundary at X except for the refinement and
- * domain reduction, which stay those of the first geometry.  The step graph is
- * captured again at the next step.  Synchronises the handle's stream.
+ * domain reduction, which stay those of the first geometry.  The captured step
+ * graph stays valid (list lengths are read on the device) except after the
+ * first move or when A_F outgrows its buffer, when the next step captures it
+ * again.  Synchronises the handle's stream.
  * Errors: IB_EINVAL (M differs, a point outside the box, a support touching a
  * hanging node or a coarser level: the points must stay inside the finest
  * refined band; a point without a free support node), IB_ESTATE (not ready,

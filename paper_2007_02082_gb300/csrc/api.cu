@@ -111,6 +111,7 @@ struct Engine {
   int32_t *mv_scnt = nullptr, *mv_sstart = nullptr, *mv_sfill = nullptr, *mv_sflag = nullptr, *mv_sidx = nullptr;
   double *mv_xprev = nullptr, *mv_ubprev = nullptr;
   int64_t af_cap = 0;             // capacity of ib.col / ib.val
+  bool mv_graph_stale = false;    // a rebuild reallocated a list the step graphs hold
   // fields [3][ns] / [ns]
   double *ubuf[2] = {nullptr, nullptr}, *pbuf[2] = {nullptr, nullptr};
   double *u = nullptr, *un = nullptr, *p = nullptr, *pn = nullptr, *phi = nullptr, *ut = nullptr, *uib = nullptr;
@@ -1372,7 +1373,10 @@ ib_status move_alloc(Engine& E) {
   E.ib.sp_ent = sp_ent;
   E.ib.sp_slot = sp_slot;
   E.ib.sp_off = sp_off;
+  E.ib.sp_cap = std::min<int64_t>(64 * M, ns);
+  E.ib.n_sp_dev = E.mv_sidx + ns;   // the compaction's total
   E.mv_ready = true;
+  E.mv_graph_stale = true;          // the step graphs hold the host-built lists
   return IB_OK;
 }
 
@@ -1410,6 +1414,7 @@ ib_status move_rebuild(Engine& E) {
     ib.col = col;
     ib.val = val;
     E.af_cap = cap;
+    E.mv_graph_stale = true;
   }
   mv_af_fill(G, M, org, E.mv_bins, rowptr, const_cast<int32_t*>(ib.col), st);
   ib_weights(ib, st);
@@ -1417,11 +1422,7 @@ ib_status move_rebuild(Engine& E) {
   mv_spread(M, ns, slot, fb, E.mv_scnt, E.mv_sstart, E.mv_sfill, E.mv_sflag, E.mv_sidx,
             const_cast<int32_t*>(ib.sp_ent), const_cast<int32_t*>(ib.sp_slot), const_cast<int32_t*>(ib.sp_off),
             E.mv_scratch, st);
-  int32_t nsp = 0;
-  CK(cudaMemcpyAsync(&nsp, E.mv_sidx + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  ib.n_sp = nsp;
-  return IB_OK;
+  return IB_OK;   // the spreading length stays on the device (ib.n_sp_dev)
 }
 
 }  // namespace
@@ -1458,9 +1459,13 @@ ib_status ib_set_points(ib_grid* g, int64_t M, const double* X, const double* UB
     E.err = why;
   }
   if (s != IB_OK) return fail(s);
-  // the captured step graphs hold the old list lengths and buffers
-  for (int k = 0; k < 2; ++k)
-    if (E.gexec[k]) { cudaGraphExecDestroy(E.gexec[k]); E.gexec[k] = nullptr; }
+  // the captured step graphs read the list lengths from the device; only a
+  // reallocated buffer (first move, a larger A_F) needs a new capture
+  if (E.mv_graph_stale) {
+    for (int k = 0; k < 2; ++k)
+      if (E.gexec[k]) { cudaGraphExecDestroy(E.gexec[k]); E.gexec[k] = nullptr; }
+    E.mv_graph_stale = false;
+  }
   // host copies of the inputs and supports (exported by ib_fields_get)
   HostGrid& H = g->H;
   if (M) {

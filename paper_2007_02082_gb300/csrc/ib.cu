@@ -268,13 +268,14 @@ __global__ void __launch_bounds__(IBB) k_af_update(IBDev ib, double* __restrict_
 }
 
 // one thread per free support node: u += coef * sum_e W[ent] G[point(ent)]
-__global__ void k_ib_spread(int64_t n, const int32_t* __restrict__ sp_slot, const int32_t* __restrict__ sp_off,
-                            const int32_t* __restrict__ sp_ent, const double* __restrict__ W,
-                            const double* __restrict__ G, const int32_t* __restrict__ binst,
-                            const double* __restrict__ icoef, double* __restrict__ u, int64_t nslots) {
+__global__ void k_ib_spread(int64_t n, const int32_t* __restrict__ n_dev, const int32_t* __restrict__ sp_slot,
+                            const int32_t* __restrict__ sp_off, const int32_t* __restrict__ sp_ent,
+                            const double* __restrict__ W, const double* __restrict__ G,
+                            const int32_t* __restrict__ binst, const double* __restrict__ icoef,
+                            double* __restrict__ u, int64_t nslots) {
   KCOUNT();
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j >= n) return;
+  if (j >= (n_dev ? int64_t(*n_dev) : n)) return;
   double acc[3] = {0, 0, 0};
   for (int e = sp_off[j]; e < sp_off[j + 1]; ++e) {
     const int32_t ent = sp_ent[e];
@@ -342,9 +343,10 @@ cudaError_t ib_solve(const IBDev& ib, const double* BF, double* G, double* work,
 }
 
 void ib_spread(const IBDev& ib, const double* G, double* u, int64_t nslots, cudaStream_t st) {
-  if (ib.n_sp == 0) return;
-  IBG_LAUNCH(k_ib_spread, int((ib.n_sp + 255) / 256), 256, 0, st, ib.n_sp, ib.sp_slot, ib.sp_off, ib.sp_ent, ib.W, G,
-             ib.binst, ib.icoef, u, nslots);
+  const int64_t n = ib.n_sp_dev ? ib.sp_cap : ib.n_sp;
+  if (n == 0) return;
+  IBG_LAUNCH(k_ib_spread, int((n + 255) / 256), 256, 0, st, ib.n_sp, ib.n_sp_dev, ib.sp_slot, ib.sp_off, ib.sp_ent,
+             ib.W, G, ib.binst, ib.icoef, u, nslots);
 }
 
 }  // namespace ibg

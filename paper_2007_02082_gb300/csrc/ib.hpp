@@ -39,6 +39,10 @@ struct IBDev {
   const int32_t* sp_off;
   const int32_t* sp_ent;
   int64_t n_sp;
+  // after a device rebuild (moving points): the list length lives on the
+  // device and launches cover sp_cap entries, so a captured step stays valid
+  const int32_t* n_sp_dev = nullptr;
+  int64_t sp_cap = 0;
 };
 
 // Eq. 17-18: W[i][a] = phi((x_a - X_i)/hx) phi((y_a - Y_i)/hy) phi((z_a - Z_i)/hz).
