@@ -438,3 +438,44 @@ def test_moving_wall_enforces_the_new_wall_velocity():
     o.step()
     assert np.abs(o.ib.W @ o.u_ib - UB1).max() < 1e-11
     assert np.abs(old.W @ o.u_ib - UB1).max() > 1e-3
+
+
+# ---------------------------------------------------------------- wall shear stress (Sec. 2.6)
+def _radial_normals(X):
+    n = np.zeros_like(X)
+    r = np.hypot(X[:, 0], X[:, 1])
+    n[:, 0], n[:, 1] = X[:, 0] / r, X[:, 1] / r
+    return n
+
+
+def test_dcpse_differentiates_quadratics_exactly():
+    """Second-order DC-PSE reproduces the derivatives of any quadratic field
+    exactly (the moment conditions cancel every Taylor term up to degree 2)."""
+    c = W.cylinder_refined_small(n=(16, 16, 8), seed=21)
+    m = ibfe.build_mesh(c)
+    rng = np.random.default_rng(5)
+    g, H = rng.normal(size=(3, 3)), rng.normal(size=(3, 3, 3))
+    H = 0.5 * (H + np.transpose(H, (0, 2, 1)))
+    def field(x):
+        return x @ g.T + np.einsum("ni,kij,nj->nk", x, H, x)
+    X = np.asarray(c["X"])[:40]
+    _, grad = ibfe.wall_shear_stress(m, field(m.node_x), X, field(X), _radial_normals(X), nu=0.02)
+    exact = g[None] + 2.0 * np.einsum("kij,nj->nki", H, X)
+    assert np.abs(grad - exact).max() <= 1e-9 * np.abs(exact).max()
+
+
+def test_poiseuille_wall_shear_stress():
+    """u_z = U (1 - r^2/R^2): WSS = mu |du_z/dr| at r = R = 2 mu U / R at every
+    wall point (quadratic, hence exact), and zero for a rigid rotation."""
+    c = W.cylinder_uniform_16x16x64()
+    m = ibfe.build_mesh(c)
+    x = m.node_x
+    u = np.zeros((m.n_nodes, 3))
+    u[:, 2] = 1.0 - 4.0 * (x[:, 0] ** 2 + x[:, 1] ** 2)
+    X = np.asarray(c["X"])[::20]
+    wss, _ = ibfe.wall_shear_stress(m, u, X, np.zeros_like(X), _radial_normals(X), nu=0.1)
+    assert np.abs(wss - 2 * 0.1 * 1.0 / 0.5).max() <= 1e-9
+    rot = np.stack([-x[:, 1], x[:, 0], np.zeros(m.n_nodes)], axis=1)
+    Xr = np.stack([-X[:, 1], X[:, 0], np.zeros(len(X))], axis=1)
+    wss0, _ = ibfe.wall_shear_stress(m, rot, X, Xr, _radial_normals(X), nu=0.1)
+    assert np.abs(wss0).max() <= 1e-9
