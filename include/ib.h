@@ -291,6 +291,25 @@ ib_status ib_fields_set(ib_grid* g, int32_t field, const void* src, size_t bytes
  */
 ib_status ib_set_points(ib_grid* g, int64_t M, const double* X, const double* UB, int32_t on_device);
 
+/*
+ * ib_wss: wall shear stress at the Lagrangian points from the current velocity
+ * (Sec. 2.6): WSS = |t - (t.n) n| with t = 2 mu eps(u) n, mu = rho nu,
+ * eps(u) = (grad u + grad u^T) / 2.  The derivatives come from second-order
+ * DC-PSE operators (the meshless method Sec. 2.6 cites) over the finest-level
+ * nodes within 3.5 e of the point (e the largest finest spacing) on the fluid
+ * side ((x_q - X).n < 0), with the point's own value U_B; polynomials of
+ * degree 2 are differentiated exactly.
+ *   normals   double [M][3] unit outward wall normals at the points
+ *   wss       double [M] result
+ *   grad      double [M][3][3] d u_i / d x_j, or NULL
+ *   on_device 1: the three arrays are device pointers, 0: host pointers
+ * Standalone handles; the paper has no such call (it evaluates WSS on the
+ * surface of a visualisation mesh), the Lagrangian points stand in for it.
+ * Synchronises the handle's stream.  Errors: IB_EINVAL (a point with too few
+ * fluid nodes for the nine moment conditions), IB_ESTATE, IB_ENOMEM, IB_ECUDA.
+ */
+ib_status ib_wss(ib_grid* g, const double* normals, double* wss, double* grad, int32_t on_device);
+
 /* ib_grid_info: counts and the last step's statistics. */
 ib_status ib_grid_info(const ib_grid* g, ib_info* out);
 

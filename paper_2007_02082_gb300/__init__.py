@@ -243,6 +243,18 @@ class IBGrid:
         self._check("ib_set_points", self.lib.ib_set_points(self.h, x.shape[0], x.ctypes.data,
                                                             None if u is None else u.ctypes.data, 0))
 
+    def ib_wss(self, normals, with_grad=False):
+        """Wall shear stress at the Lagrangian points (Sec. 2.6) from the
+        current velocity; normals (M, 3) unit outward.  Returns wss (M,) and,
+        with with_grad, the velocity gradient (M, 3, 3), [p, i, j] = d u_i / d x_j."""
+        M = self.ib_grid_info()["n_points"]
+        n = np.ascontiguousarray(normals, dtype=np.float64).reshape(M, 3)
+        w = np.empty(M)
+        g = np.empty((M, 3, 3)) if with_grad else None
+        self._check("ib_wss", self.lib.ib_wss(self.h, n.ctypes.data, w.ctypes.data,
+                                              None if g is None else g.ctypes.data, 0))
+        return (w, g) if with_grad else w
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.ib_grid_destroy(self.h)

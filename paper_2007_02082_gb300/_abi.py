@@ -21,7 +21,7 @@ FIELD = {
 EXPORTS = ("ib_grid_create", "ib_set_boundary", "ipcs_step", "ib_fields_get", "ib_fields_set",
            "ib_grid_info", "ib_last_error", "ib_grid_destroy", "ib_batch_create", "ib_batch_step",
            "ib_batch_fields_get", "ib_batch_info", "ib_batch_last_error", "ib_batch_destroy",
-           "ib_fields_get_noalloc", "ib_set_points")
+           "ib_fields_get_noalloc", "ib_set_points", "ib_wss")
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -89,6 +89,8 @@ def bind(lib: C.CDLL) -> C.CDLL:
     lib.ib_fields_set.restype = C.c_int
     lib.ib_set_points.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32]
     lib.ib_set_points.restype = C.c_int
+    lib.ib_wss.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+    lib.ib_wss.restype = C.c_int
     lib.ib_grid_info.argtypes = [C.c_void_p, P(IbInfo)]
     lib.ib_grid_info.restype = C.c_int
     lib.ib_last_error.argtypes = [C.c_void_p]

@@ -37,6 +37,7 @@
 #include "ib.h"
 #include "ib.hpp"
 #include "ibmove.hpp"
+#include "wss.hpp"
 #include "krylov.hpp"
 #include "mg.hpp"
 #include "noalloc.hpp"
@@ -50,6 +51,7 @@ unsigned long long krylov_kcount();
 unsigned long long ib_kcount();
 unsigned long long mg_kcount();
 unsigned long long move_kcount();
+unsigned long long wss_kcount();
 }
 
 namespace {
@@ -112,6 +114,7 @@ struct Engine {
   double *mv_xprev = nullptr, *mv_ubprev = nullptr;
   int64_t af_cap = 0;             // capacity of ib.col / ib.val
   bool mv_graph_stale = false;    // a rebuild reallocated a list the step graphs hold
+  double *wss_n = nullptr, *wss_w = nullptr, *wss_g = nullptr;   // wall shear stress buffers
   // fields [3][ns] / [ns]
   double *ubuf[2] = {nullptr, nullptr}, *pbuf[2] = {nullptr, nullptr};
   double *u = nullptr, *un = nullptr, *p = nullptr, *pn = nullptr, *phi = nullptr, *ut = nullptr, *uib = nullptr;
@@ -1084,7 +1087,7 @@ void fill_info(const HostGrid& H, const MGHost* mg, const Engine* E, int64_t dev
     if (m & M_VALID) nv++;
   I.n_valid_slots = nv;
   I.device_bytes = dev_bytes;
-  I.kernel_launches = int64_t(fe_kcount() + krylov_kcount() + ib_kcount() + mg_kcount() + move_kcount());
+  I.kernel_launches = int64_t(fe_kcount() + krylov_kcount() + ib_kcount() + mg_kcount() + move_kcount() + wss_kcount());
   if (E) {
     for (int k = 0; k < Prof::K; ++k) {
       I.prof_ms[k] = E->prof.ms[k];
@@ -1339,8 +1342,9 @@ MoveGrid move_grid(const Engine& E) {
   return G;
 }
 
-ib_status move_alloc(Engine& E) {
-  if (E.mv_ready) return IB_OK;
+// finest level's brick map and the coarse cell levels (point lookups)
+ib_status finest_map(Engine& E) {
+  if (E.mv_bmap) return IB_OK;
   const HostGrid& H = *E.H[0];
   const HostLevel& HL = H.levels[H.L];
   for (int a = 0; a < 3; ++a) {
@@ -1351,13 +1355,20 @@ ib_status move_alloc(Engine& E) {
   std::vector<uint8_t> cells(H.active.size());
   for (size_t c = 0; c < cells.size(); ++c) cells[c] = H.active[c] ? uint8_t(H.level[c]) : uint8_t(255);
   TRY(upload(E, &E.mv_cells, cells));
+  if (!E.mv_err) TRY(dalloc(E, &E.mv_err, 4, true));
+  return IB_OK;
+}
+
+ib_status move_alloc(Engine& E) {
+  if (E.mv_ready) return IB_OK;
+  TRY(finest_map(E));
+  const HostGrid& H = *E.H[0];
   const MoveGrid G = move_grid(E);
   const int64_t nb = mv_nbins(G), Mt = E.Mtot, ns = E.ns, M = H.M;
   TRY(dalloc(E, &E.mv_bins, 3 * (nb + 1) + M + 1, true));
   TRY(dalloc(E, &E.mv_rcnt, Mt + 1, true));
   const int64_t sc = std::max(scan_scratch_len(nb), std::max(scan_scratch_len(Mt), scan_scratch_len(ns)));
   TRY(dalloc(E, &E.mv_scratch, sc, true));
-  TRY(dalloc(E, &E.mv_err, 4, true));
   TRY(dalloc(E, &E.mv_scnt, ns + 1, true));
   TRY(dalloc(E, &E.mv_sstart, ns + 1, true));
   TRY(dalloc(E, &E.mv_sfill, ns + 1, true));
@@ -1477,6 +1488,41 @@ ib_status ib_set_points(ib_grid* g, int64_t M, const double* X, const double* UB
   }
   CKG(cudaStreamSynchronize(st));
 #undef CKG
+  return IB_OK;
+}
+
+ib_status ib_wss(ib_grid* g, const double* normals, double* wss, double* grad, int32_t on_device) {
+  if (!g || !normals || !wss) return IB_EINVAL;
+  if (!g->ready) { g->err = "ib_set_boundary has not succeeded"; return IB_ESTATE; }
+  if (!g->eng) { g->err = "the wall shear stress of a deferred handle is read through its batch"; return IB_ESTATE; }
+  Engine& E = *g->eng;
+  const HostGrid& H = g->H;
+  const int64_t M = H.M;
+  if (M == 0) return IB_OK;
+  cudaStream_t st = E.st;
+  ib_status s = finest_map(E);
+  if (s == IB_OK && !E.wss_n) {
+    s = dalloc(E, &E.wss_n, 3 * M);
+    if (s == IB_OK) s = dalloc(E, &E.wss_w, M);
+    if (s == IB_OK) s = dalloc(E, &E.wss_g, 9 * M);
+  }
+  if (s != IB_OK) { g->err = E.err; return s; }
+  double *dn = E.wss_n, *dw = E.wss_w, *dg = grad ? E.wss_g : nullptr;
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  int32_t herr = 0;
+  cudaError_t e = cudaMemcpyAsync(dn, normals, 3 * M * sizeof(double), kin, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(E.mv_err, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) {
+    wss_compute(move_grid(E), H.hf, M, E.X, E.UB, dn, E.u, E.ns, E.D[0].nu * E.D[0].rho, dw, dg, E.mv_err, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(wss, dw, M * sizeof(double), kout, st);
+  if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, dg, 9 * M * sizeof(double), kout, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, E.mv_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { g->err = std::string("CUDA: ") + cudaGetErrorString(e); return IB_ECUDA; }
+  if (herr) { g->err = "a wall point has too few fluid nodes around it for the DC-PSE moments"; return IB_EINVAL; }
   return IB_OK;
 }
 
