@@ -377,6 +377,27 @@ def run_native(args, rank, world, local_rank):
                                               "outer_p", "outer_corr")},
         "accuracy": accuracy,
     }
+    if args.wss:
+        X = torch.tensor(case["X"], dtype=torch.float64, device=f"cuda:{local_rank}")
+        if args.moving:
+            X = wall(nstep[0] - 1)[0]
+        nrm = torch.zeros_like(X)
+        r = torch.sqrt(X[:, 0] ** 2 + X[:, 1] ** 2)
+        nrm[:, 0], nrm[:, 1] = X[:, 0] / r, X[:, 1] / r
+        w = torch.empty(X.shape[0], dtype=torch.float64, device=X.device)
+        gr = torch.empty((X.shape[0], 3, 3), dtype=torch.float64, device=X.device)
+        for _ in range(2):
+            g.lib.ib_wss(g.h, nrm.data_ptr(), w.data_ptr(), gr.data_ptr(), 1)
+        reps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g.lib.ib_wss(g.h, nrm.data_ptr(), w.data_ptr(), gr.data_ptr(), 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["wss"] = {"ms": e0.elapsed_time(e1) / reps, "points": int(X.shape[0]),
+                      "max": float(w.max()), "mean": float(w.mean()),
+                      "method": "second-order DC-PSE over finest-level fluid nodes within 3.5 finest spacings"}
     g.close()
     return out
 
@@ -430,6 +451,9 @@ def main():
                     help="drive the tube by its inlet velocity or by the inlet pressure that gives the same "
                          "Poiseuille peak (16 nu L / R^2 per unit of peak speed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--wss", action="store_true",
+                    help="also time the wall shear stress at the wall points (ib_wss, device buffers) after the "
+                         "timed steps; tubes along z, radial normals")
     ap.add_argument("--moving", action="store_true",
                     help="move the wall every step (ib_set_points: device rebuild of the IB structures), "
                          "timed with the step")
