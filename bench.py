@@ -57,6 +57,19 @@ def apply_variant(case, args):
     return case
 
 
+def job_aggregate(t_local, units_per_step, steps, world, dist=None, device="cuda"):
+    """Replicas: every rank steps its own problem; the job's time is the
+    slowest rank's (max over ranks) and its value the units of all ranks over
+    that time.  Returns (time, value per second of that time unit)."""
+    import torch
+    t = float(t_local)
+    if dist is not None and world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t, units_per_step * steps * world / t
+
+
 def moving_wall(case, device):
     """Wall motion for --moving: every point oscillates along x with amplitude
     0.4 finest cells and period 25 steps, wall velocity the time derivative.
@@ -251,11 +264,8 @@ def run_native(args, rank, world, local_rank):
     ck = clocks.stop()
     i2 = g.ib_grid_info()
     launches = i2["kernel_launches"] - i1["kernel_launches"]
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = cells * args.steps * world / (ms / 1e3)
+    ms, value = job_aggregate(ms / 1e3, cells, args.steps, world, dist)
+    ms *= 1e3
 
     # Kernels inside the step graph cannot be bracketed by events, so the same
     # step is replayed eagerly on a second handle (same stream, same kernels,
@@ -317,11 +327,8 @@ def run_native(args, rank, world, local_rank):
         hp[:] = g.ib_fields_get("P")
     torch.cuda.synchronize()
     te = time.perf_counter() - te
-    if dist:
-        tt = torch.tensor([te], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
-    e2e = {"value": cells * e2e_steps * world / te, "unit": UNIT,
+    te, e2e_value = job_aggregate(te, cells, e2e_steps, world, dist)
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(hu.nbytes + hp.nbytes), "d2h_bytes_per_step": int(hu.nbytes + hp.nbytes)}
 
     # accuracy of the timed path against the plain FP64 GPU path: both from the
