@@ -123,6 +123,8 @@ struct Engine {
   float *coef32 = nullptr, *diag32 = nullptr, *dK32 = nullptr, *dM32 = nullptr, *dA32 = nullptr;
   float *r32 = nullptr, *e32 = nullptr, *w32 = nullptr;
   double *X = nullptr, *dS = nullptr, *UB = nullptr, *BF = nullptr, *Gf = nullptr, *ibw = nullptr;
+  double* ib_y64 = nullptr;       // mixed force solve: FP64 S G
+  float* ib_w32 = nullptr;        // mixed force solve: FP32 work (7 x 3 M)
   // solver state
   KState* ks = nullptr;
   KState* ks_host = nullptr;
@@ -721,6 +723,12 @@ ib_status engine_build(Engine& E) {
   TRY(dalloc(E, &ib.W, 64 * Mt, true));
   TRY(dalloc(E, &ib.val, int64_t(col.size()), true));
   E.af_cap = int64_t(col.size());
+  if (E.mixed) {
+    TRY(dalloc(E, &ib.val32, int64_t(col.size()), true));
+    TRY(dalloc(E, &ib.dinv32, Mt, true));
+    TRY(dalloc(E, &E.ib_y64, 3 * Mt, true));
+    TRY(dalloc(E, &E.ib_w32, 7 * 3 * Mt, true));
+  }
   TRY(dalloc(E, &ib.dinv, Mt, true));
   TRY(dalloc(E, &E.BF, 3 * Mt, true));
   TRY(dalloc(E, &E.Gf, 3 * Mt, true));
@@ -837,7 +845,11 @@ cudaError_t enqueue_step(Engine& E, double* u, double* un, double* p, double* pn
   fe_copy_d(3 * ns, E.ut, E.uib, st);
   if (E.Mtot) {
     ib_gather(E.ib, E.ut, ns, E.UB, E.BF, st);
-    e = ib_solve(E.ib, E.BF, E.Gf, E.ibw, E.ks, E.ks_host, E.rb, tl.ib, tl.max_iter, E.recs + 1, st, cc);
+    if (E.mixed)   // FP32 iterations inside FP64 defect correction, as the field solves
+      e = ib_solve_mixed(E.ib, E.BF, E.Gf, E.ib_y64, E.ib_w32, E.ks, E.ks_host, E.os, E.os_host, E.rb, tl.ib,
+                         std::max(tl.inner, tl.ib), tl.max_iter, 30, E.recs + 1, st, cc);
+    else
+      e = ib_solve(E.ib, E.BF, E.Gf, E.ibw, E.ks, E.ks_host, E.rb, tl.ib, tl.max_iter, E.recs + 1, st, cc);
     if (e != cudaSuccess) return e;
     ib_spread(E.ib, E.Gf, E.uib, ns, st);
   }
@@ -1424,6 +1436,11 @@ ib_status move_rebuild(Engine& E) {
     TRY(dalloc(E, &val, cap, true));
     ib.col = col;
     ib.val = val;
+    if (E.mixed) {
+      float* v32;
+      TRY(dalloc(E, &v32, cap, true));
+      ib.val32 = v32;
+    }
     E.af_cap = cap;
     E.mv_graph_stale = true;
   }

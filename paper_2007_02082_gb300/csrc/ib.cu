@@ -49,7 +49,8 @@ __global__ void k_ib_weights(int64_t M, const double* __restrict__ X, const int3
 __global__ void k_af_values(int64_t M, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                             const int32_t* __restrict__ org, const uint64_t* __restrict__ fb,
                             const double* __restrict__ W, const double* __restrict__ pscale,
-                            double* __restrict__ val, double* __restrict__ dinv) {
+                            double* __restrict__ val, double* __restrict__ dinv, float* __restrict__ val32,
+                            float* __restrict__ dinv32) {
   KCOUNT();
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -67,7 +68,11 @@ __global__ void k_af_values(int64_t M, const int32_t* __restrict__ rowptr, const
     }
     const double scale = pscale[i];
     val[e] = scale * acc;
-    if (k == i) dinv[i] = acc > 0.0 ? 1.0 / (scale * acc) : 0.0;
+    if (val32) val32[e] = float(scale * acc);
+    if (k == i) {
+      dinv[i] = acc > 0.0 ? 1.0 / (scale * acc) : 0.0;
+      if (dinv32) dinv32[i] = float(dinv[i]);
+    }
   }
 }
 
@@ -141,20 +146,21 @@ __global__ void __launch_bounds__(IBB) k_af_apply(IBDev ib, const double* __rest
 // lanes per row (A_F has a few dozen entries per row).
 constexpr int AFL = 8;
 static_assert(IBB / AFL == 32, "seg_g holds 32-row block ranges");
-__global__ void __launch_bounds__(IBB) k_af_apply_p(IBDev ib, const double* __restrict__ z,
-                                                    const double* __restrict__ pold, double* __restrict__ pnew,
-                                                    double* __restrict__ q, KState* ks, double* partials,
+template <typename T>
+__global__ void __launch_bounds__(IBB) k_af_apply_p(IBDev ib, const T* __restrict__ val, const T* __restrict__ z,
+                                                    const T* __restrict__ pold, T* __restrict__ pnew,
+                                                    T* __restrict__ q, KState* ks, double* partials,
                                                     unsigned* counter) {
   KCOUNT();
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / AFL;
   const int lane = threadIdx.x % AFL;
-  double v[3] = {0, 0, 0};
+  T v[3] = {0, 0, 0};
   if (i < ib.M) {
     const KState* ki = ks + ib.pinst[i] * 3;
-    const double b0 = ki[0].beta, b1 = ki[1].beta, b2 = ki[2].beta;
-    double acc[3] = {0, 0, 0};
+    const T b0 = k_beta<T>(ki[0]), b1 = k_beta<T>(ki[1]), b2 = k_beta<T>(ki[2]);
+    T acc[3] = {0, 0, 0};
     for (int e = ib.rowptr[i] + lane; e < ib.rowptr[i + 1]; e += AFL) {
-      const double w = ib.val[e];
+      const T w = val[e];
       const int64_t k = ib.col[e];
       acc[0] += w * (z[3 * k] + b0 * pold[3 * k]);
       acc[1] += w * (z[3 * k + 1] + b1 * pold[3 * k + 1]);
@@ -164,9 +170,9 @@ __global__ void __launch_bounds__(IBB) k_af_apply_p(IBDev ib, const double* __re
     for (int c = 0; c < 3; ++c)
       for (int o = AFL / 2; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o, AFL);
     if (lane == 0) {
-      const double bc[3] = {b0, b1, b2};
+      const T bc[3] = {b0, b1, b2};
       for (int c = 0; c < 3; ++c) {
-        const double pv = z[3 * i + c] + bc[c] * pold[3 * i + c];
+        const T pv = z[3 * i + c] + bc[c] * pold[3 * i + c];
         pnew[3 * i + c] = pv;
         q[3 * i + c] = acc[c];
         v[c] = pv * acc[c];
@@ -174,72 +180,79 @@ __global__ void __launch_bounds__(IBB) k_af_apply_p(IBDev ib, const double* __re
     }
   }
   double* out = partials + (int64_t)gridDim.x * 3;
-  if (!grid_sum_last<double, 3>(v, partials, counter, ib.seg_g, ib.ninst, out)) return;
+  if (!grid_sum_last<T, 3>(v, partials, counter, ib.seg_g, ib.ninst, out)) return;
   for (int n = threadIdx.x; n < ib.ninst; n += blockDim.x)
     for (int c = 0; c < 3; ++c) {
       KState& k = ks[n * 3 + c];
       if (k.done) continue;
       const double pq = out[n * 3 + c];
       k.pq = pq;
-      if (!(pq > 0.0) || !isfinite(pq)) { k.done = 1; k.status = 5; k.alpha = 0.0; continue; }
+      if (!(pq > 0.0) || !isfinite(pq)) { k.done = 1; k.status = 5; k.alpha = 0.0; k.af = 0.f; continue; }
       k.alpha = k.rz / pq;
+      k.af = float(k.alpha);
     }
 }
 
-__global__ void __launch_bounds__(IBB) k_af_start(IBDev ib, const double* __restrict__ b, const double* __restrict__ y,
-                                                  double* __restrict__ r, double* __restrict__ z,
-                                                  double* __restrict__ p, KState* ks, double* partials,
-                                                  unsigned* counter, Cond cond) {
+// r = b - y (y may be null: zero initial guess), z = D^-1 r, p = 0; skip_os:
+// instances whose FP64 outer loop is done take no inner iterations
+template <typename T>
+__global__ void __launch_bounds__(IBB) k_af_start(IBDev ib, const T* __restrict__ dinv, const T* __restrict__ b,
+                                                  const T* __restrict__ y, T* __restrict__ r, T* __restrict__ z,
+                                                  T* __restrict__ p, KState* ks, double* partials,
+                                                  unsigned* counter, Cond cond, const OState* skip_os) {
   KCOUNT();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  T v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (i < ib.M)
     for (int c = 0; c < 3; ++c) {
-      const double rv = b[3 * i + c] - y[3 * i + c];
-      const double zv = rv * ib.dinv[i];
+      const T rv = y ? T(b[3 * i + c] - y[3 * i + c]) : b[3 * i + c];
+      const T zv = rv * dinv[i];
       r[3 * i + c] = rv;
       z[3 * i + c] = zv;
-      p[3 * i + c] = 0.0;
+      p[3 * i + c] = T(0);
       v[3 * c] = rv * zv;
       v[3 * c + 1] = rv * rv;
       v[3 * c + 2] = b[3 * i + c] * b[3 * i + c];
     }
   double* out = partials + (int64_t)gridDim.x * 9;
-  if (!grid_sum_last<double, 9>(v, partials, counter, ib.seg_t, ib.ninst, out)) return;
+  if (!grid_sum_last<T, 9>(v, partials, counter, ib.seg_t, ib.ninst, out)) return;
   bool any = false;
   for (int n = threadIdx.x; n < ib.ninst; n += blockDim.x)
     for (int c = 0; c < 3; ++c) {
       KState& k = ks[n * 3 + c];
       const double* t = out + n * 9 + 3 * c;
+      const bool skip = skip_os && skip_os[n].done;
       k.rz = t[0];
       k.rr = t[1];
       k.bb = fmax(t[2], k.rr);
       k.beta = 0.0;
+      k.bf = 0.f;
       k.iter = 0;
       k.status = 0;
-      k.done = (k.rr <= k.tol2 * k.bb) ? 1 : 0;
-      if (!isfinite(k.rr)) { k.done = 1; k.status = 5; }
+      k.done = (skip || k.rr <= k.tol2 * k.bb) ? 1 : 0;
+      if (!skip && !isfinite(k.rr)) { k.done = 1; k.status = 5; }
       any = any || !k.done;
     }
   any = __syncthreads_or(any ? 1 : 0) != 0;
   if (threadIdx.x == 0) set_cond(cond, any);
 }
 
-__global__ void __launch_bounds__(IBB) k_af_update(IBDev ib, double* __restrict__ x, double* __restrict__ r,
-                                                   double* __restrict__ z, const double* __restrict__ p,
-                                                   const double* __restrict__ q, KState* ks, double* partials,
+template <typename T>
+__global__ void __launch_bounds__(IBB) k_af_update(IBDev ib, const T* __restrict__ dinv, T* __restrict__ x,
+                                                   T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
+                                                   const T* __restrict__ q, KState* ks, double* partials,
                                                    unsigned* counter, Cond cond) {
   KCOUNT();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double v[6] = {0, 0, 0, 0, 0, 0};
+  T v[6] = {0, 0, 0, 0, 0, 0};
   if (i < ib.M) {
     const KState* ki = ks + ib.pinst[i] * 3;
     for (int c = 0; c < 3; ++c) {
       if (ki[c].done) continue;
-      const double a = ki[c].alpha;
+      const T a = k_alpha<T>(ki[c]);
       x[3 * i + c] += a * p[3 * i + c];
-      const double rv = r[3 * i + c] - a * q[3 * i + c];
-      const double zv = rv * ib.dinv[i];
+      const T rv = r[3 * i + c] - a * q[3 * i + c];
+      const T zv = rv * dinv[i];
       r[3 * i + c] = rv;
       z[3 * i + c] = zv;
       v[2 * c] = rv * zv;
@@ -247,7 +260,7 @@ __global__ void __launch_bounds__(IBB) k_af_update(IBDev ib, double* __restrict_
     }
   }
   double* out = partials + (int64_t)gridDim.x * 6;
-  if (!grid_sum_last<double, 6>(v, partials, counter, ib.seg_t, ib.ninst, out)) return;
+  if (!grid_sum_last<T, 6>(v, partials, counter, ib.seg_t, ib.ninst, out)) return;
   bool any = false;
   for (int n = threadIdx.x; n < ib.ninst; n += blockDim.x)
     for (int c = 0; c < 3; ++c) {
@@ -260,6 +273,7 @@ __global__ void __launch_bounds__(IBB) k_af_update(IBDev ib, double* __restrict_
       if (k.rr <= k.tol2 * k.bb) { k.done = 1; continue; }
       if (k.iter >= k.max_iter) { k.done = 1; k.status = 4; continue; }
       k.beta = rzn / k.rz;
+      k.bf = float(k.beta);
       k.rz = rzn;
       any = true;
     }
@@ -300,7 +314,7 @@ void ib_assemble(const IBDev& ib, cudaStream_t st) {
   if (ib.M == 0) return;
   const int64_t th = ib.M * 32;
   IBG_LAUNCH(k_af_values, int((th + 255) / 256), 256, 0, st, ib.M, ib.rowptr, ib.col, ib.org, ib.freeb, ib.W,
-             ib.pscale, ib.val, ib.dinv);
+             ib.pscale, ib.val, ib.dinv, ib.val32, ib.dinv32);
 }
 
 void ib_gather(const IBDev& ib, const double* u, int64_t nslots, const double* UB, double* BF, cudaStream_t st) {
@@ -323,14 +337,17 @@ cudaError_t ib_solve(const IBDev& ib, const double* BF, double* G, double* work,
   const int gw = int((ib.M * 32 + IBB - 1) / IBB);   // warp-per-row grids
   const int gt = int((ib.M + IBB - 1) / IBB);        // thread-per-row grids
   IBG_LAUNCH(k_af_apply, gw, IBB, 0, st, ib, G, q, 0, ks, rb.partials, rb.counter);
-  IBG_LAUNCH(k_af_start, gt, IBB, 0, st, ib, BF, q, r, z, p, ks, rb.partials, rb.counter, cond);
+  IBG_LAUNCH((k_af_start<double>), gt, IBB, 0, st, ib, ib.dinv, BF, (const double*)q, r, z, p, ks, rb.partials,
+             rb.counter, cond, (const OState*)nullptr);
   // k_af_start left p = z and beta = 0; the direction ping-pongs between p and
   // p2, two iterations per loop body
   double* p2 = work + 4 * L;
   const int g8 = int((ib.M * AFL + IBB - 1) / IBB);
   auto iter = [&](cudaStream_t s, const Cond& c, const double* pold, double* pnew) {
-    IBG_LAUNCH(k_af_apply_p, g8, IBB, 0, s, ib, z, pold, pnew, q, ks, rb.partials, rb.counter);
-    IBG_LAUNCH(k_af_update, gt, IBB, 0, s, ib, G, r, z, pnew, q, ks, rb.partials, rb.counter, c);
+    IBG_LAUNCH((k_af_apply_p<double>), g8, IBB, 0, s, ib, (const double*)ib.val, (const double*)z, pold, pnew, q,
+               ks, rb.partials, rb.counter);
+    IBG_LAUNCH((k_af_update<double>), gt, IBB, 0, s, ib, ib.dinv, G, r, z, (const double*)pnew, (const double*)q,
+               ks, rb.partials, rb.counter, c);
   };
   cudaError_t e = run_loop(cc, st, cond, ks, ks_host, ib.ninst * 3, max_iter, 4, 32,
                            [&](cudaStream_t s, const Cond& c) {
@@ -339,6 +356,140 @@ cudaError_t ib_solve(const IBDev& ib, const double* BF, double* G, double* work,
   });
   if (e != cudaSuccess) return e;
   IBG_LAUNCH(k_collect, (ib.ninst + 127) / 128, 128, 0, st, ks, 3, ib.ninst, rec, (OState*)nullptr);
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- mixed precision
+// FP64 outer loop of the mixed force solve: r = B_F - S G on every row, FP64
+// norms per instance and component, r rounded to FP32 as the inner right-hand
+// side with a zero inner guess; the loop and branch conditions as for the
+// field solves (converged, stagnated near the FP64 floor, or out of passes).
+__global__ void __launch_bounds__(IBB) k_af_resid_outer(IBDev ib, const double* __restrict__ b,
+                                                        const double* __restrict__ y, float* __restrict__ r32,
+                                                        float* __restrict__ e32, OState* os, double* partials,
+                                                        unsigned* counter, Cond cloop, Cond cbranch) {
+  KCOUNT();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double w[6] = {0, 0, 0, 0, 0, 0};
+  if (i < ib.M) {
+    const OState& oi = os[ib.pinst[i]];
+    for (int c = 0; c < 3; ++c) {
+      const double rv = b[3 * i + c] - y[3 * i + c];
+      r32[3 * i + c] = float(rv);
+      e32[3 * i + c] = 0.f;
+      w[2 * c] = rv * rv;
+      w[2 * c + 1] = oi.iter == 0 ? b[3 * i + c] * b[3 * i + c] : 0.0;
+    }
+  }
+  double* out = partials + (int64_t)gridDim.x * 6;
+  if (!grid_sum_last<double, 6>(w, partials, counter, ib.seg_t, ib.ninst, out)) return;
+  bool any = false;
+  for (int n = threadIdx.x; n < ib.ninst; n += blockDim.x) {
+    OState& o = os[n];
+    if (o.done) continue;
+    double rel2 = 0.0;
+    bool finite = true;
+    for (int c = 0; c < 3; ++c) {
+      const double rr = out[n * 6 + 2 * c], bb = out[n * 6 + 2 * c + 1];
+      if (o.iter == 0) o.ref[c] = fmax(bb, rr);
+      if (!isfinite(rr)) finite = false;
+      if (o.ref[c] > 0.0) rel2 = fmax(rel2, rr / o.ref[c]);
+    }
+    o.rel2 = rel2;
+    const bool stagnated = o.iter > 0 && rel2 > 0.0625 * o.prev2 && rel2 <= 1e6 * o.tol2;
+    if (!finite || o.inner_status == 5) { o.done = 1; o.status = 5; }
+    else if (rel2 <= o.tol2 || stagnated) o.done = 1;
+    else if (o.iter >= o.max_iter) { o.done = 1; o.status = 4; }
+    o.prev2 = rel2;
+    if (!o.done) { o.iter++; any = true; }
+  }
+  any = __syncthreads_or(any ? 1 : 0) != 0;
+  if (threadIdx.x == 0) {
+    set_cond(cloop, any);
+    set_cond(cbranch, any);
+  }
+}
+
+// G += e for the instances whose outer loop is still running
+__global__ void k_af_add(IBDev ib, const float* __restrict__ e, double* __restrict__ G, const OState* os) {
+  KCOUNT();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ib.M || os[ib.pinst[i]].done) return;
+  for (int c = 0; c < 3; ++c) G[3 * i + c] += double(e[3 * i + c]);
+}
+
+cudaError_t ib_solve_mixed(const IBDev& ib, const double* BF, double* G, double* y64, float* w32, KState* ks,
+                           KState* ks_host, OState* os, OState* os_host, RedBuf rb, double rtol, double rtol_inner,
+                           int max_iter, int max_outer, SolveRec* rec, cudaStream_t st, CaptureCtx* cc) {
+  if (ib.M == 0) return cudaSuccess;
+  const int64_t L = 3 * ib.M;
+  float *r32 = w32, *e32 = w32 + L, *r = w32 + 2 * L, *z = w32 + 3 * L, *pa = w32 + 4 * L, *pb = w32 + 5 * L,
+        *q = w32 + 6 * L;
+  const int gw = int((ib.M * 32 + IBB - 1) / IBB);
+  const int gt = int((ib.M + IBB - 1) / IBB);
+  const int g8 = int((ib.M * AFL + IBB - 1) / IBB);
+  const int gi = (ib.ninst + 127) / 128;
+  IBG_LAUNCH(k_init_outer, gi, 128, 0, st, os, ib.ninst, 3, rtol * rtol, max_outer);
+  auto residual = [&](cudaStream_t s, const Cond& cl, const Cond& cb) {
+    IBG_LAUNCH(k_af_apply, gw, IBB, 0, s, ib, (const double*)G, y64, 0, ks, rb.partials, rb.counter);
+    IBG_LAUNCH(k_af_resid_outer, gt, IBB, 0, s, ib, BF, (const double*)y64, r32, e32, os, rb.partials, rb.counter,
+               cl, cb);
+  };
+  cudaError_t err = cudaSuccess;
+  auto correction = [&](cudaStream_t s) {
+    IBG_LAUNCH(k_init_states, (ib.ninst * 3 + 127) / 128, 128, 0, s, ks, ib.ninst * 3, rtol_inner * rtol_inner,
+               max_iter);
+    Cond ci;
+    if (cc && cc->capturing) {
+      cudaError_t e = cond_handle(s, 0, &ci);
+      if (e != cudaSuccess) return e;
+    }
+    IBG_LAUNCH((k_af_start<float>), gt, IBB, 0, s, ib, (const float*)ib.dinv32, (const float*)r32,
+               (const float*)nullptr, r, z, pa, ks, rb.partials, rb.counter, ci, (const OState*)os);
+    auto iter = [&](cudaStream_t s2, const Cond& c2, const float* pold, float* pnew) {
+      IBG_LAUNCH((k_af_apply_p<float>), g8, IBB, 0, s2, ib, (const float*)ib.val32, (const float*)z, pold, pnew, q,
+                 ks, rb.partials, rb.counter);
+      IBG_LAUNCH((k_af_update<float>), gt, IBB, 0, s2, ib, (const float*)ib.dinv32, e32, r, z, (const float*)pnew,
+                 (const float*)q, ks, rb.partials, rb.counter, c2);
+    };
+    cudaError_t e = run_loop(cc, s, ci, ks, ks_host, ib.ninst * 3, max_iter, 4, 32, [&](cudaStream_t s2, const Cond& c2) {
+      iter(s2, c2, pa, pb);
+      iter(s2, c2, pb, pa);
+    });
+    if (e != cudaSuccess) return e;
+    IBG_LAUNCH(k_collect, gi, 128, 0, s, (const KState*)ks, 3, ib.ninst, rec, os);
+    IBG_LAUNCH(k_af_add, gt, IBB, 0, s, ib, (const float*)e32, G, (const OState*)os);
+    return cudaSuccess;
+  };
+  if (cc && cc->capturing) {
+    Cond cl;
+    if ((err = cond_handle(st, 1, &cl)) != cudaSuccess) return err;
+    cudaError_t e = cond_node(*cc, st, cl, cudaGraphCondTypeWhile, [&](cudaStream_t s) {
+      Cond cb;
+      cudaError_t e1 = cond_handle(s, 0, &cb);
+      if (e1 != cudaSuccess) { err = e1; return; }
+      residual(s, cl, cb);
+      e1 = cond_node(*cc, s, cb, cudaGraphCondTypeIf, [&](cudaStream_t s2) {
+        cudaError_t e2 = correction(s2);
+        if (e2 != cudaSuccess) err = e2;
+      });
+      if (e1 != cudaSuccess) err = e1;
+    });
+    if (e != cudaSuccess) return e;
+    if (err != cudaSuccess) return err;
+  } else {
+    const Cond none;
+    for (int it = 0; it <= max_outer + 1; ++it) {
+      residual(st, none, none);
+      cudaMemcpyAsync(os_host, os, ib.ninst * sizeof(OState), cudaMemcpyDeviceToHost, st);
+      if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
+      bool all = true;
+      for (int i = 0; i < ib.ninst; ++i) all = all && os_host[i].done;
+      if (all) break;
+      if ((err = correction(st)) != cudaSuccess) return err;
+    }
+  }
+  IBG_LAUNCH(k_collect_outer, gi, 128, 0, st, (const OState*)os, ib.ninst, rec);
   return cudaSuccess;
 }
 

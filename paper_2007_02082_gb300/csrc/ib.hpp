@@ -22,6 +22,8 @@ struct IBDev {
   const int32_t* seg_w;    // [ninst + 1] block range, 8 rows per block
   const int32_t* seg_g;    // [ninst + 1] block range, 32 rows per block
   const double* pscale;    // [M] dt / (rho h^3) of the row's instance
+  float* val32 = nullptr;  // FP32 copies of val and dinv (mixed path)
+  float* dinv32 = nullptr;
   const double* iorigin;   // [ninst][3] box origin
   const double* ihf;       // [ninst][3] finest spacing
   const double* icoef;     // [ninst] spreading coefficient dt / (rho h^3)
@@ -56,6 +58,13 @@ void ib_gather(const IBDev& ib, const double* u, int64_t nslots, const double* U
 cudaError_t ib_solve(const IBDev& ib, const double* BF, double* G, double* work /* 5*3*M */, KState* ks,
                      KState* ks_host, RedBuf rb, double rtol, int max_iter, SolveRec* rec, cudaStream_t st,
                      CaptureCtx* cc);
+// The same solve in mixed precision: FP64 defect correction (r = B_F - S G,
+// FP64 norms, relative tolerance rtol) around FP32 PCG iterations on the FP32
+// copy of S (relative tolerance rtol_inner).  y64: 3*M doubles; w32: 7*3*M
+// floats; os: one outer state per instance.
+cudaError_t ib_solve_mixed(const IBDev& ib, const double* BF, double* G, double* y64, float* w32, KState* ks,
+                           KState* ks_host, OState* os, OState* os_host, RedBuf rb, double rtol, double rtol_inner,
+                           int max_iter, int max_outer, SolveRec* rec, cudaStream_t st, CaptureCtx* cc);
 // u_j += coef * sum_i W[i][a(j)] G_i on free support nodes (Eq. 19, Eq. 14).
 void ib_spread(const IBDev& ib, const double* G, double* u, int64_t nslots, cudaStream_t st);
 

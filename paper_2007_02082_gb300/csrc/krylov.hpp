@@ -78,5 +78,7 @@ cudaError_t run_loop(CaptureCtx* cc, cudaStream_t st, const Cond& cond, const KS
 // Device-side helpers shared with the IB solver.
 __global__ void k_init_states(KState* ks, int nc, double tol2, int max_iter);
 __global__ void k_collect(const KState* ks, int nc, int ninst, SolveRec* rec, OState* os);
+__global__ void k_init_outer(OState* os, int ninst, int nc, double tol2, int max_outer);
+__global__ void k_collect_outer(const OState* os, int ninst, SolveRec* rec);
 
 }  // namespace ibg
