@@ -139,9 +139,13 @@ def test_serving_loop_results_match_alone():
     for k in range(6):
         c = dict(cases[k % 4])
         c["steps"] = 3 + (k % 3) * 2
-        stream.append((0.05 * k, c))
+        stream.append((0.0, c))
     got = {}
-    res = serve(stream, precision="mixed", epoch_steps=2, keep=lambda rid, h: got.__setitem__(rid, h.ib_fields_get("U")))
+    # every request arrives at once and is set up concurrently, so some join
+    # while others are active (arrivals spaced in time may never overlap when
+    # a request finishes within the spacing)
+    res = serve(stream, precision="mixed", epoch_steps=2, setup_workers=6,
+                keep=lambda rid, h: got.__setitem__(rid, h.ib_fields_get("U")))
     s = res.summary()
     assert s["requests"] == 6 and s["failed"] == 0
     assert res.epochs >= 3 and max(res.batch_sizes) >= 2
