@@ -23,9 +23,12 @@ import numpy as np
 from . import IBBatch, IBGrid
 
 # device bytes per stored node slot of a batch (fields, FP64 work, coefficients,
-# and in mixed precision the FP32 Krylov work) and per Lagrangian row
+# and in mixed precision the FP32 Krylov work), per Lagrangian row (in mixed
+# precision with the force solve's FP64 product, FP32 work and FP32 Jacobi
+# diagonal) and per nonzero of A_F (column, FP64 value, FP32 copy if mixed)
 BYTES_PER_SLOT = {"mixed": 540, "fp64": 530}
-BYTES_PER_ROW = 1400
+BYTES_PER_ROW = {"mixed": 1400 + 24 + 84 + 4, "fp64": 1400}
+BYTES_PER_NNZ = {"mixed": 16, "fp64": 12}
 
 
 @dataclass
@@ -45,8 +48,9 @@ class Request:
 
 
 def footprint(info, precision):
-    return int(info["n_slots"] * BYTES_PER_SLOT[precision] + ((info["n_points"] + 255) // 256 * 256) * BYTES_PER_ROW
-               + 12 * info["af_nnz"])
+    return int(info["n_slots"] * BYTES_PER_SLOT[precision]
+               + ((info["n_points"] + 255) // 256 * 256) * BYTES_PER_ROW[precision]
+               + BYTES_PER_NNZ[precision] * info["af_nnz"])
 
 
 @dataclass
