@@ -108,8 +108,10 @@ typedef struct {
  *                       cell; < 0 keeps the whole box
  *   nu, rho, dt         kinematic viscosity, density, time step
  *   precision           IB_FP64: every solve in FP64.  IB_MIXED: FP32 operators
- *                       and preconditioners inside FP64 defect correction; FP64
- *                       residuals, inner products and IB force solve
+ *                       and preconditioners inside FP64 defect correction for
+ *                       the momentum, Poisson, velocity-correction and force
+ *                       (A_F, Eq. 22) solves; FP64 residuals, norms, IB
+ *                       interpolation and spreading
  *   rtol_*              relative residual tolerances of the momentum, Poisson,
  *                       velocity-correction and force solves, relative to
  *                       max(norm of b, norm of the initial residual); 0 selects
