@@ -137,13 +137,14 @@ def test_serving_loop_results_match_alone():
     cases = _cases()
     stream = []
     for k in range(6):
-        c = dict(cases[k % 4])
+        # the first request, the pressure-driven tube (a slowly accelerating
+        # flow), runs for about 30 epochs so that the others join while it is
+        # active; short requests spaced in time may never overlap
+        c = dict(cases[3] if k == 0 else cases[k % 4])
         c["steps"] = 61 if k == 0 else 3 + (k % 3) * 2
         stream.append((0.0, c))
     got = {}
-    # every request arrives at once and is set up concurrently; the first one
-    # runs for about 30 epochs, so the others join while it is active (short
-    # requests spaced in time may never overlap)
+    # every request arrives at once and is set up concurrently
     res = serve(stream, precision="mixed", epoch_steps=2, setup_workers=6,
                 keep=lambda rid, h: got.__setitem__(rid, h.ib_fields_get("U")))
     s = res.summary()
