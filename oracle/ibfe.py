@@ -47,7 +47,8 @@ with its reason in the project's design notes):
       other boundary nodes of the active region are no-slip walls; outlet and
       pressure-inlet nodes carry no velocity condition (the natural condition
       nu du/dn = 0 of the gradient-form viscous term, as at a do-nothing
-      outlet);
+      outlet); opt-in case["port_tangential"] = "zero" holds their tangential
+      components at zero instead (the paper is silent on them);
   R11 refinement level per coarse cell from the Chebyshev distance d to a
       point-containing coarse cell, hanging nodes constrained to the mean of the
       two ends of the coarse edge (cube edge or Kuhn face diagonal) they bisect;
@@ -420,6 +421,35 @@ def velocity_dirichlet(mesh):
     return (mesh.boundary & ~mesh.outlet & (mesh.pinlet == 0) & ~mesh.hanging) | (mesh.inlet > 0)
 
 
+def velocity_dirichlet_components(mesh):
+    """(N, 3) bool: the velocity condition per component.  Every component of a
+    wall or velocity-inlet node (R10).  With case["port_tangential"] == "zero"
+    also the components tangential to an outlet or pressure-inlet port on its
+    nodes (held at zero): Sec. 3.1 imposes the pressure on the ports and says
+    nothing of the tangential velocity there; the default ("free") leaves
+    every component of a port node free, as R10 reads it."""
+    d = np.repeat(velocity_dirichlet(mesh)[:, None], 3, axis=1)
+    if mesh.case.get("port_tangential", "free") != "zero":
+        return d
+    taken = np.zeros(mesh.n_nodes, dtype=bool)
+    for pi, port in enumerate(mesh.case["ports"]):
+        a = port["axis"]
+        plane = 0 if port["side"] == 0 else int(mesh.n[a]) << mesh.L
+        o = [b for b in range(3) if b != a]
+        d0 = mesh.node_x[:, o[0]] - port["center"][o[0]]
+        d1 = mesh.node_x[:, o[1]] - port["center"][o[1]]
+        r2 = d0 * d0
+        r2 = r2 + d1 * d1
+        sel = (mesh.node_q[:, a] == plane) & (r2 <= port["radius"] * port["radius"]) & ~taken
+        sel &= mesh.outlet | (mesh.pinlet > 0) | (mesh.inlet > 0)
+        taken |= sel
+        if port["kind"] == "inlet":
+            continue
+        for k in o:
+            d[sel & ~mesh.hanging, k] = True
+    return d
+
+
 def pressure_dirichlet(mesh):
     """Nodes where Phi is prescribed: outlets and pressure inlets (R9)."""
     return mesh.outlet | (mesh.pinlet > 0)
@@ -731,6 +761,13 @@ class Oracle:
         m = self.mesh
         self.vdir_node = velocity_dirichlet(m)
         self.vdir = self.vdir_node[~m.hanging]
+        # per component: differs from vdir only on pressure ports when their
+        # tangential velocity is held at zero
+        vdir_c = velocity_dirichlet_components(m)
+        self.vdir_c = vdir_c[~m.hanging]
+        self.split = not all(np.array_equal(self.vdir_c[:, k], self.vdir) for k in range(3))
+        if self.split:
+            self.vdir_node = vdir_c.any(axis=1)   # the force spreads to nodes free in every component
         self.pdir = pressure_dirichlet(m)[~m.hanging]
         free = ~self.vdir_node & ~m.hanging
         self.ib = IB(m, case, free)
@@ -777,7 +814,7 @@ class Oracle:
             ut = self._momentum_sym(Am, b, g, dt * nu)
         else:
             Ac = ops.condense(Am)
-            ut = ops.P @ solve_dirichlet(Ac, b, self.vdir, g, symmetric=False)
+            ut = ops.P @ self._solve_velocity(Ac, b, g, symmetric=False)
 
         # Steps 2-3: B_F = U_B - h^3 D^T u~ (Eq. 23), A_F F = B_F (Eq. 21)
         BF = self.ib.UB - self.ib.W @ ut
@@ -795,8 +832,7 @@ class Oracle:
 
         # Step 6 (R1): (u^{n+1}, v) = (u, v) - dt (grad Phi, v); p^{n+1} = p^n + Phi
         bc = np.stack([ops.PT @ (ops.M @ u[:, k] - dt * (ops.G[k] @ phi)) for k in range(3)], 1)
-        un = ops.P @ solve_dirichlet(self.Mc, bc, self.vdir, g, symmetric=True,
-                                     factor_cache=self._cache, key="M")
+        un = ops.P @ self._solve_velocity(self.Mc, bc, g, symmetric=True, key="M")
         self.ut, self.u_ib, self.BF = ut, u, BF
         self.u = un
         self.p = self.p + phi
@@ -804,6 +840,16 @@ class Oracle:
         self.F = F
         self.t = t1
         self.nstep += 1
+
+    def _solve_velocity(self, A, b, g, symmetric, key=None):
+        """The three velocity components with their Dirichlet rows; one solve
+        for all three when every component has the same condition."""
+        cache = self._cache if key is not None else None
+        if not self.split:
+            return solve_dirichlet(A, b, self.vdir, g, symmetric, factor_cache=cache, key=key)
+        return np.stack([solve_dirichlet(A, b[:, k:k + 1], self.vdir_c[:, k], g[:, k:k + 1], symmetric,
+                                         factor_cache=cache, key=None if key is None else f"{key}{k}")[:, 0]
+                         for k in range(3)], axis=1)
 
     def _momentum_sym(self, Am, b, g, dtnu):
         """Eq. 9 with the symmetric viscous form (R7): the three components
@@ -815,7 +861,7 @@ class Oracle:
                   for i in range(3)]
         A3 = sp.bmat(blocks, format="csr")
         nd = b.shape[0]
-        d3 = np.concatenate([self.vdir] * 3)
+        d3 = np.concatenate([self.vdir_c[:, k] for k in range(3)])
         x3 = solve_dirichlet(A3, b.T.reshape(-1, 1), d3, g.T.reshape(-1, 1), symmetric=False)[:, 0]
         return ops.P @ x3.reshape(3, nd).T
 

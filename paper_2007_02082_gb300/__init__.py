@@ -44,6 +44,9 @@ def load_library(build_if_missing: bool = False) -> C.CDLL:
 
 
 def _viscous_form(case):
+    if case.get("port_tangential", "free") != "free":
+        # the library leaves every velocity component of a pressure port free
+        raise ValueError("port_tangential: the library implements 'free' only")
     form = case.get("viscous", "grad")
     if form not in ("grad", "sym"):
         raise ValueError(f"viscous must be 'grad' or 'sym', not {form!r}")

@@ -156,3 +156,13 @@ def test_point_outside_box_is_rejected(probe):
     case["X"][5] = (10.0, 0.0, 1.0)
     rc, err = run_probe(probe, case)
     assert rc == 10 + 1 and "outside" in err
+
+
+def test_binding_rejects_options_the_library_lacks():
+    """The oracle's opt-in tangential port condition has no library
+    counterpart: the binding refuses such a case instead of ignoring the key."""
+    from paper_2007_02082_gb300 import _abi, _viscous_form
+    assert _viscous_form({}) == _abi.IB_VISCOUS_GRAD
+    assert _viscous_form({"viscous": "sym", "port_tangential": "free"}) == _abi.IB_VISCOUS_SYM
+    with pytest.raises(ValueError):
+        _viscous_form({"port_tangential": "zero"})

@@ -277,9 +277,10 @@ def test_noslip_exact_after_correction():
 
 
 # ---------------------------------------------------------------- the full step
-def _poiseuille(n, M, steps=20, dt=0.05, inlet=W.INLET):
+def _poiseuille(n, M, steps=20, dt=0.05, inlet=W.INLET, tangential="free"):
     # U_max = R^2 dp / (4 nu L) = 1 for R = 0.5, nu = 0.1, L = 4 and dp = 6.4
     c = W.cylinder_case(n=n, M=M, dt=dt, inlet=inlet, a0=6.4 if inlet == W.PINLET else 1.0)
+    c["port_tangential"] = tangential
     m = ibfe.build_mesh(c)
     x = m.node_x
     r2 = x[:, 0] ** 2 + x[:, 1] ** 2
@@ -385,6 +386,27 @@ def test_pressure_driven_poiseuille_error_falls_under_refinement():
     falling at least first order when h halves."""
     _, e1 = _poiseuille((8, 8, 32), 300, steps=20, inlet=W.PINLET)
     _, e2 = _poiseuille((16, 16, 64), 1200, steps=20, inlet=W.PINLET)
+    assert e2 < 0.05
+    assert math.log2(e1 / e2) > 1.0
+
+
+def test_tangential_port_condition_holds_and_keeps_poiseuille():
+    """Sec. 3.1 imposes the pressure on the ports and says nothing of the
+    tangential velocity there.  Under the opt-in reading port_tangential =
+    "zero" the components tangential to an outlet or pressure-inlet port are
+    exactly zero on its nodes every step while the normal component carries
+    the flow, the IB force spreads onto no port node, and the pressure-driven
+    Poiseuille flow (whose exact solution satisfies both readings) still
+    converges under refinement."""
+    o1, e1 = _poiseuille((8, 8, 32), 300, steps=10, inlet=W.PINLET, tangential="zero")
+    o2, e2 = _poiseuille((16, 16, 64), 1200, steps=10, inlet=W.PINLET, tangential="zero")
+    for o in (o1, o2):
+        m = o.mesh
+        port = ((m.pinlet > 0) | m.outlet) & ~m.hanging
+        assert port.sum() > 20 and o.split
+        assert np.all(o.u[port][:, :2] == 0.0)
+        assert np.abs(o.u[port, 2]).max() > 0.5
+        assert np.all(o.ib.spread(o.F)[port] == 0.0)
     assert e2 < 0.05
     assert math.log2(e1 / e2) > 1.0
 
