@@ -191,6 +191,24 @@ def class_bytes(cls, vb, multigrid=False):
     }.get(cls)
 
 
+def timed_class_bandwidth(dms, dn, vb, multigrid, n_valid, peak):
+    """Per timed class with a byte model (every class but the V-cycle
+    transfers), the achieved fraction of `peak`, and over all of them together
+    the algorithmic bytes per step over their time: dms / dn are the
+    milliseconds and launches per class, n_valid the valid node slots."""
+    ks = [k for k in CLASS_NAMES if dn[k] > 0 and class_bytes(k, vb, multigrid) is not None]
+    frac = {}
+    total_b = total_ms = 0.0
+    for k in ks:
+        b = class_bytes(k, vb, multigrid) * n_valid * dn[k]
+        frac[CLASS_NAMES[k]] = round(b / (dms[k] / 1e3) / 1e9 / peak, 3) if dms[k] > 0 else None
+        total_b += b
+        total_ms += dms[k]
+    gbs = total_b / (total_ms / 1e3) / 1e9 if total_ms > 0 else None
+    return {"gbs": gbs, "frac": gbs / peak if gbs else None,
+            "time_share": total_ms / sum(dms) if sum(dms) > 0 else None, "per_class_frac": frac}
+
+
 CLASS_NAMES = {0: "k_poisson_cg (p = z + beta p, q = K p, fused p.q)", 1: "k_cg_update<Poisson>",
                2: "k_cg_p<Poisson>", 3: "k_apply15<mass> (fused p = z + beta p, p.q)", 4: "k_cg_update<mass>",
                5: "k_cg_p<mass>",
@@ -377,7 +395,8 @@ def run_native(args, rank, world, local_rank):
                      "avg_launch_us": avg_ms * 1e3, "bytes_per_launch": per_launch_bytes,
                      "timing": "CUDA events around each launch, eager replay of the same step",
                      "solver_kernel_time_share": prof_share, "solver_kernel_avg_us": prof_us,
-                     "solver_kernel_ms_per_step": prof_ms_step},
+                     "solver_kernel_ms_per_step": prof_ms_step,
+                     "timed_classes": timed_class_bandwidth(dms, dn, vb, mgon, info0["n_valid_slots"], peak)},
         "clocks": ck,
         "e2e": e2e,
         "iters_last_step": {k: i2[k] for k in ("iters_mom", "iters_ib", "iters_p", "iters_corr", "outer_mom",
