@@ -78,6 +78,7 @@ enum { IB_VISCOUS_GRAD = 0, IB_VISCOUS_SYM = 1 };
  *                Phi = w(t^{n+1}) - p^n on the port nodes, so p^{n+1} = w(t^{n+1})
  *                there, and no velocity condition (the natural condition
  *                nu du/dn = 0 of the viscous term, as at an outlet)
+ *   profile      IB_PARABOLIC, the only inlet profile (any other value: IB_EINVAL)
  *   waveform     w(t) = a0 + sum_{k=1..n_harm} a[k-1] cos(2 pi k t / period)
  *                                      + b[k-1] sin(2 pi k t / period)
  * At least one port fixes Phi (an outlet or a pressure inlet); a node on two

@@ -1124,6 +1124,7 @@ ib_status validate_desc(const ib_grid_desc* d) {
     if (P.axis < 0 || P.axis > 2 || (P.side != 0 && P.side != 1) || !(P.radius > 0)) return IB_EINVAL;
     if (P.kind != IB_INLET_VELOCITY && P.kind != IB_OUTLET_ZERO_P && P.kind != IB_INLET_PRESSURE) return IB_EINVAL;
     if (P.n_harm < 0 || P.n_harm > IB_MAX_HARMONICS) return IB_EINVAL;
+    if (P.profile != IB_PARABOLIC) return IB_EINVAL;
     if (P.kind != IB_INLET_VELOCITY) outlet = true;   // a port that fixes Phi
   }
   if (!outlet) return IB_EINVAL;

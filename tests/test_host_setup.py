@@ -166,3 +166,42 @@ def test_binding_rejects_options_the_library_lacks():
     assert _viscous_form({"viscous": "sym", "port_tangential": "free"}) == _abi.IB_VISCOUS_SYM
     with pytest.raises(ValueError):
         _viscous_form({"port_tangential": "zero"})
+
+
+def test_grid_create_rejects_invalid_descriptions(lib_path):
+    """ib_grid_create validates the description before it touches the device:
+    every invalid field returns IB_EINVAL and no handle (no GPU needed)."""
+    from paper_2007_02082_gb300 import _abi
+    lib = _abi.bind(C.CDLL(lib_path))
+    case = W.cylinder_case(n=(8, 8, 16), M=100)
+
+    def create(edit):
+        d = _desc(case)
+        d.precision, d.poisson_pc = _abi.IB_MIXED, 0
+        edit(d)
+        h = C.c_void_p(0)
+        st = lib.ib_grid_create(C.byref(d), C.byref(h))
+        return st, h.value
+
+    def port0(field, v):
+        return lambda d: setattr(d.ports[0], field, v)
+
+    bad = [
+        port0("profile", 1),                                   # only the parabolic inlet profile exists
+        port0("axis", 3),
+        port0("side", 2),
+        port0("radius", 0.0),
+        port0("kind", 7),
+        port0("n_harm", _abi.IB_MAX_HARMONICS + 1),
+        lambda d: setattr(d, "n_ports", 0),
+        lambda d: setattr(d.ports[1], "kind", _abi.IB_INLET_VELOCITY),   # no port fixes Phi
+        lambda d: setattr(d, "precision", 2),
+        lambda d: setattr(d, "viscous_form", 2),
+        lambda d: setattr(d, "nu", 0.0),
+        lambda d: setattr(d, "dt", -1.0),
+        lambda d: setattr(d, "max_level", 9),
+        lambda d: (setattr(d, "max_level", 1), setattr(d, "refine_band", 0)),
+    ]
+    for k, edit in enumerate(bad):
+        st, h = create(edit)
+        assert st == _abi.IB_EINVAL and not h, k
