@@ -205,3 +205,33 @@ def test_grid_create_rejects_invalid_descriptions(lib_path):
     for k, edit in enumerate(bad):
         st, h = create(edit)
         assert st == _abi.IB_EINVAL and not h, k
+
+
+def test_null_handles_are_rejected(lib_path):
+    """Every entry point checks its handle before any device work: a null grid
+    or batch gives IB_EINVAL (or a message / no-op for the error and destroy
+    calls), as include/ib.h states."""
+    from paper_2007_02082_gb300 import _abi
+    lib = _abi.bind(C.CDLL(lib_path))
+    E = _abi.IB_EINVAL
+    buf = (C.c_double * 8)()
+    info = _abi.IbInfo()
+    assert lib.ib_set_boundary(None, 1, buf, buf, None, None) == E
+    assert lib.ipcs_step(None, 1) == E
+    assert lib.ib_fields_get(None, 0, buf, 8, 0) == E
+    assert lib.ib_fields_get_noalloc(None, 0, buf, 8, 0) == E
+    assert lib.ib_fields_set(None, 0, buf, 8, 0) == E
+    assert lib.ib_set_points(None, 1, buf, None, 0) == E
+    assert lib.ib_wss(None, buf, buf, None, 0) == E
+    assert lib.ib_grid_info(None, C.byref(info)) == E
+    assert lib.ib_last_error(None) == b"null handle"
+    lib.ib_grid_destroy(None)
+    out = C.c_void_p(0)
+    assert lib.ib_batch_create(None, 1, C.byref(out)) == E and not out.value
+    members = (C.c_void_p * 1)(None)
+    assert lib.ib_batch_create(members, 0, C.byref(out)) == E and not out.value
+    assert lib.ib_batch_step(None, 1, None) == E
+    assert lib.ib_batch_fields_get(None, 0, 0, buf, 8, 0) == E
+    assert lib.ib_batch_info(None, 0, C.byref(info)) == E
+    assert lib.ib_batch_last_error(None) == b"null batch"
+    lib.ib_batch_destroy(None)
