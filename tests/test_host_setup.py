@@ -158,6 +158,23 @@ def test_point_outside_box_is_rejected(probe):
     assert rc == 10 + 1 and "outside" in err
 
 
+def test_invalid_points_and_ports_are_rejected(probe):
+    """The host grid builder refuses, with IB_EINVAL and a message, a
+    non-finite point, a non-positive area element and an outlet whose disc
+    meets no boundary node (the Poisson problem would be singular)."""
+    base = W.cylinder_uniform_16x16x64()
+
+    def bad(edit, msg):
+        c = dict(base, X=base["X"].copy(), dS=base["dS"].copy(), ports=[dict(p) for p in base["ports"]])
+        edit(c)
+        rc, err = run_probe(probe, c)
+        assert rc == 10 + 1 and msg in err, (rc, err)
+
+    bad(lambda c: c["X"].__setitem__((7, 1), np.nan), "non-finite")
+    bad(lambda c: c["dS"].__setitem__(3, 0.0), "positive")
+    bad(lambda c: c["ports"][1].update(center=(5.0, 5.0, 4.0)), "singular")
+
+
 def test_binding_rejects_options_the_library_lacks():
     """The oracle's opt-in tangential port condition has no library
     counterpart: the binding refuses such a case instead of ignoring the key."""
