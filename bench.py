@@ -341,8 +341,8 @@ def run_native(args, rank, world, local_rank):
         g.ib_fields_set("U", hu)
         g.ib_fields_set("P", hp)
         g.ipcs_step(1)
-        hu[:] = g.ib_fields_get("U")
-        hp[:] = g.ib_fields_get("P")
+        g.ib_fields_get("U", out=hu)        # straight into the pinned buffers
+        g.ib_fields_get("P", out=hp)
     torch.cuda.synchronize()
     te = time.perf_counter() - te
     te, e2e_value = job_aggregate(te, cells, e2e_steps, world, dist)

@@ -195,8 +195,16 @@ class IBGrid:
         }[field]
 
     def ib_fields_get(self, field, out=None):
-        """Copy a field to a new host numpy array (or into a device tensor `out`)."""
+        """Copy a field to a new host numpy array, or into `out`: a device
+        tensor, or a host numpy array of the field's shape and dtype (for
+        example pinned memory), which the library writes directly."""
         shape, dt = self._shape(field)
+        if isinstance(out, np.ndarray):                  # host destination
+            if out.shape != tuple(shape) or out.dtype != np.dtype(dt) or not out.flags.c_contiguous \
+                    or not out.flags.writeable:
+                raise ValueError(f"out must be a writable C-contiguous {np.dtype(dt)} array of shape {shape}")
+            self._check("ib_fields_get", self.lib.ib_fields_get(self.h, FIELD[field], out.ctypes.data, out.nbytes, 0))
+            return out
         if out is not None:                              # device tensor destination
             nbytes = out.numel() * out.element_size()
             self._check("ib_fields_get", self.lib.ib_fields_get(self.h, FIELD[field], C.c_void_p(out.data_ptr()),

@@ -252,3 +252,36 @@ def test_null_handles_are_rejected(lib_path):
     assert lib.ib_batch_info(None, 0, C.byref(info)) == E
     assert lib.ib_batch_last_error(None) == b"null batch"
     lib.ib_batch_destroy(None)
+
+
+def test_fields_get_writes_into_a_host_array():
+    """Marshalling of ib_fields_get(out=numpy array): the library receives the
+    array's own pointer and byte count with the host flag and writes into it
+    (no intermediate copy); a destination of the wrong shape, dtype or layout
+    is refused before the call."""
+    from paper_2007_02082_gb300 import IBGrid, _abi
+
+    class FakeLib:
+        calls = []
+
+        def ib_fields_get(self, h, field, ptr, nbytes, on_dev):
+            self.calls.append((field, ptr, nbytes, on_dev))
+            src = np.arange(nbytes // 8, dtype=np.float64)
+            C.memmove(ptr, src.ctypes.data, nbytes)
+            return 0
+
+        def ib_last_error(self, h):
+            return b""
+
+    g = object.__new__(IBGrid)
+    g.lib, g.h, g.case = FakeLib(), None, {"n": (2, 2, 2)}
+    g.ib_grid_info = lambda: {"n_nodes": 5, "n_points": 2}
+    out = np.zeros((5, 3))
+    assert g.ib_fields_get("U", out=out) is out
+    assert g.lib.calls[-1] == (_abi.FIELD["U"], out.ctypes.data, out.nbytes, 0)
+    assert np.array_equal(out.ravel(), np.arange(15.0))
+    p = g.ib_fields_get("P")
+    assert p.shape == (5,) and np.array_equal(p, np.arange(5.0))
+    for bad in (np.zeros((5, 2)), np.zeros((5, 3), np.float32), np.zeros((3, 5)).T):
+        with pytest.raises(ValueError):
+            g.ib_fields_get("U", out=bad)
