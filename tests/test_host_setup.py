@@ -121,7 +121,19 @@ def oracle_structures(case):
     return m, flags, ib.origin, fr
 
 
+def _duct_no_points():
+    """A pressure-driven square duct without an immersed boundary (M = 0)."""
+    n = (6, 6, 12)
+    return {"name": "duct_6x6x12", "origin": (-0.5, -0.5, 0.0), "extent": (1.0, 1.0, 2.0), "n": n,
+            "max_level": 0, "refine_band": 2, "reduce_band": -1, "nu": 0.1, "rho": 1.0, "dt": 0.01,
+            "ports": [W._port(2, 0, (0.0, 0.0, 0.0), 0.499, W.PINLET, a0=1.0),
+                      W._port(2, 1, (0.0, 0.0, 2.0), 0.499, W.OUTLET)],
+            "X": np.zeros((0, 3)), "dS": np.zeros(0), "UB": np.zeros((0, 3)),
+            "inside": np.ones((n[2], n[1], n[0]), np.uint8)}
+
+
 CASES = {
+    "duct_no_points": _duct_no_points,
     "uniform_16x16x64": lambda: W.cylinder_uniform_16x16x64(),
     "refined_16x16x32": lambda: W.cylinder_refined_small(),
     "refined_reduced_20x20x12": lambda: W.cylinder_case(n=(20, 20, 12), length=1.5, half_width=0.75, M=900,
