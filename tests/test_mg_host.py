@@ -115,6 +115,14 @@ CASES = {
     # lattice planes of every coarser level
     "odd_outlet": W.cylinder_case(n=(12, 12, 37), length=3.7, half_width=0.6, M=800, seed=14, max_level=1,
                                   refine_band=1, reduce_band=2, nu=0.05, dt=0.005),
+    # no immersed boundary (M = 0), Phi prescribed on a pressure inlet and an outlet
+    "duct_no_points": {"name": "duct_8x8x24", "origin": (-0.5, -0.5, 0.0), "extent": (1.0, 1.0, 3.0),
+                       "n": (8, 8, 24), "max_level": 0, "refine_band": 2, "reduce_band": -1, "nu": 0.1,
+                       "rho": 1.0, "dt": 0.01,
+                       "ports": [W._port(2, 0, (0.0, 0.0, 0.0), 0.499, W.PINLET, a0=1.0),
+                                 W._port(2, 1, (0.0, 0.0, 3.0), 0.499, W.OUTLET)],
+                       "X": np.zeros((0, 3)), "dS": np.zeros(0), "UB": np.zeros((0, 3)),
+                       "inside": np.ones((24, 8, 8), np.uint8)},
 }
 
 
