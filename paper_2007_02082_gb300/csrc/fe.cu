@@ -680,8 +680,12 @@ __device__ __forceinline__ void halo15(int t, int& nbk, int& li, int& ti) {
 // coefficient reads of a plain apply).
 // FUSEP: p_new = z + beta p_old while staging the tile (written for the
 // brick's nodes), y = A p_new, and per-component p.y -> alpha (POST_CG_ALPHA).
+// One CTA per chunk, the FP32 mass operator fits 40 registers without spilling
+// when asked for 3 CTAs of 512 threads per SM (57-71 and 2 CTAs otherwise);
+// every other instance keeps the compiler's own choice (a minimum of 0).
 template <typename T, int OP, int NC, bool FUSEP, bool PB, bool SYM = false>
-__global__ void __launch_bounds__(512) k_apply15(DevGrid g, const T* __restrict__ x, T* __restrict__ y,
+__global__ void __launch_bounds__(512, (sizeof(T) == 4 && OP == OP_MASS && !PB) ? 3 : 0)
+    k_apply15(DevGrid g, const T* __restrict__ x, T* __restrict__ y,
                                                  const T* __restrict__ coef, uint16_t dmask, int post,
                                                  KState* __restrict__ ks, double* __restrict__ partials,
                                                  unsigned* __restrict__ counter, const T* __restrict__ zf,
