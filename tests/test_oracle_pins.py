@@ -4,6 +4,7 @@ Every test here runs on the CPU only.  Each one is chosen so that a plausible
 slip in the oracle (a dropped term, a wrong sign or index, a transposed
 operand, a wrong hanging-node parent) fails it.
 """
+import functools
 import json
 import math
 import os
@@ -277,6 +278,7 @@ def test_noslip_exact_after_correction():
 
 
 # ---------------------------------------------------------------- the full step
+@functools.lru_cache(maxsize=None)
 def _poiseuille(n, M, steps=20, dt=0.05, inlet=W.INLET, tangential="free"):
     # U_max = R^2 dp / (4 nu L) = 1 for R = 0.5, nu = 0.1, L = 4 and dp = 6.4
     c = W.cylinder_case(n=n, M=M, dt=dt, inlet=inlet, a0=6.4 if inlet == W.PINLET else 1.0)
@@ -388,6 +390,54 @@ def test_pressure_driven_poiseuille_error_falls_under_refinement():
     _, e2 = _poiseuille((16, 16, 64), 1200, steps=20, inlet=W.PINLET)
     assert e2 < 0.05
     assert math.log2(e1 / e2) > 1.0
+
+
+def test_pressure_driven_tube_force_balances_the_pressure_drop():
+    """The magnitude of the Lagrangian force F (Eq. 19-22).  In steady
+    pressure-driven Poiseuille flow the wall holds the fluid against the
+    pressure drop: the total force of the wall on the fluid, sum_k F_k dS_k,
+    balances -dp pi R^2 along the axis.  The IB force acts over the kernel's
+    width (two fine cells each side of the wall), and the continuous P1
+    pressure carries the drop into the fluid just outside the tube, so the
+    discrete total exceeds dp pi R^2 by a part that shrinks with h (about
+    2 h / R of it: 2.2 at h = 0.15, 1.4 at h = 0.075).  Pinned: the ratio is
+    above 1, falls towards 1 at least first order when h halves, and is
+    within 60 % at 16x16x64.  A common factor 2 on A_F and on the spreading
+    (which leaves every velocity unchanged) fails it, as does any slip of
+    h^3, dS or dt in the force scale."""
+    dp, R = 6.4, 0.5
+    ratios = []
+    for n, M in (((8, 8, 32), 300), ((16, 16, 64), 1200)):
+        o, _ = _poiseuille(n, M, steps=20, inlet=W.PINLET)
+        fz = float(o.ib.dS @ o.F[:, 2])
+        fxy = float(np.abs(o.ib.dS @ o.F[:, :2]).max())
+        assert fxy < 0.05 * abs(fz)                # no net sideways force on a straight tube
+        ratios.append(fz / (-dp * math.pi * R * R))
+    r1, r2 = ratios
+    assert 1.0 < r2 < r1 and r2 < 1.6
+    assert (r1 - 1.0) / (r2 - 1.0) > 2.0
+
+
+def test_ib_impulse_equals_total_boundary_force():
+    """Eq. 14 and Eq. 19: the correction u = u~ + (dt / rho) f adds to the
+    fluid the momentum rho int (u - u~) dV = dt int f dV, and f spreads each
+    point's force F_k dS_k with a kernel of unit integral (the 4-point kernel
+    sums to 1 over its support), so the impulse of one step is dt sum_k F_k dS_k
+    exactly when every support node is a free interior node.  Together with the
+    no-slip pin this fixes the scale of F: a factor on both A_F and the
+    spreading, or a dropped h^3, dS or dt in either, breaks the equality."""
+    for n, R, M in (((8, 8, 16), 0.25, 60), ((16, 16, 32), 0.35, 400)):
+        c = W.cylinder_case(n=n, R=R, M=M, dt=0.05, length=2.0)
+        X, dS = W.cylinder_wall_points(R, 0.6, 1.4, M, 4)     # supports clear of the end faces
+        c["X"], c["dS"], c["UB"] = X, dS, np.zeros_like(X)
+        o = ibfe.Oracle(c).run(3)
+        sup = o.ib.support_idx
+        assert np.all(sup >= 0) and not np.any(o.vdir_node[sup.ravel()])
+        vol = o.ops.M @ np.ones(o.mesh.n_nodes)     # int phi_j dV
+        impulse = c["rho"] * ((o.u_ib - o.ut).T @ vol)
+        force = c["dt"] * (o.ib.dS @ o.F)
+        assert abs(force[2]) > 0.01
+        assert np.allclose(impulse, force, rtol=1e-10, atol=1e-12 * abs(force[2]))
 
 
 def test_tangential_port_condition_holds_and_keeps_poiseuille():
