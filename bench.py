@@ -93,17 +93,14 @@ def moving_wall(case, device):
 
 def sample_case(name):
     """Bounded sample of the workload for the CPU oracle: the same cross-section,
-    grid, bands and point density over 8 coarse cells of the tube's length."""
+    grid, bands and point density over a slab of the tube's length."""
     import workloads as W
     if name == "cylinder_64x64x256_L1":
-        c = W.cylinder_refined_64x64x256()
-        length = 4.0 * 16 / 256
-        M = max(64, int(round(32000 * 16 / 256)))
-        return W.cylinder_case(n=(64, 64, 16), length=length, M=M, seed=2, max_level=1, refine_band=2,
-                               reduce_band=2, nu=c["nu"], dt=c["dt"], a0=1.0, b=(0.5,),
-                               name="cylinder_64x64x16_L1_slab"), "64x64x16 coarse-cell slab of the same tube (16 of 256 cells in z), 2 steps"
+        return (W.cylinder_refined_slab_64x64x16(),
+                "64x64x16 coarse-cell slab of the same tube (16 of 256 cells in z, 2000 points), 2 steps")
     if name == "aneurysm_128x128x256_L2":
-        raise SystemExit("no bounded oracle sample for the aneurysm workload: run it with --no-cpu-baseline")
+        return (W.aneurysm_slab_128x128x16_L2(),
+                "128x128x16 coarse-cell slab of the aneurysm through the sac centre (16 of 256 cells in z), 2 steps")
     return workload(name), "full workload, 2 steps"
 
 

@@ -133,6 +133,29 @@ def cylinder_refined_64x64x256(**kw):
     return cylinder_case(**args)
 
 
+def cylinder_refined_slab_64x64x16(**kw):
+    """A slab of the refined 64x64x256 cylinder: the same cross-section, grid
+    spacing, bands, viscosity, time step and wall-point density over 16 of its
+    256 coarse cells along the axis (length 0.25, 2000 points).  The oracle
+    steps it in seconds; it still spans thousands of bricks and a five-level
+    multigrid hierarchy."""
+    length = 4.0 * 16 / 256
+    args = dict(n=(64, 64, 16), length=length, M=2000, seed=2, max_level=1, refine_band=2, reduce_band=2,
+                nu=0.02, dt=0.002, steps=2, a0=1.0, b=(0.5,), period=1.0, name="cylinder_64x64x16_L1_slab")
+    args.update(kw)
+    return cylinder_case(**args)
+
+
+def square_duct_case(n=(8, 8, 32), L=4.0, nu=0.1, p_in=1.0, dt=1.0, steps=15, name=None):
+    """Square duct [-1/2, 1/2]^2 x [0, L] without an immersed boundary (M = 0):
+    no-slip box walls, a pressure inlet and an outlet (discs just inside the
+    walls) on the end faces, the whole box active."""
+    ports = [_port(2, 0, (0.0, 0.0, 0.0), 0.499, PINLET, a0=p_in), _port(2, 1, (0.0, 0.0, L), 0.499, OUTLET)]
+    return _case(name or f"duct_{n[0]}x{n[1]}x{n[2]}", (-0.5, -0.5, 0.0), (1.0, 1.0, float(L)), n,
+                 np.zeros((0, 3)), np.zeros(0), np.ones((n[2], n[1], n[0]), np.uint8), ports, nu, dt, steps,
+                 0, 2, -1)
+
+
 def cylinder_refined_small(n=(16, 16, 32), M=None, seed=7, **kw):
     """A reduced copy of the refined cylinder: same geometry rules and bands,
     a coarse grid small enough for the oracle's direct solves in seconds."""
@@ -221,6 +244,31 @@ def aneurysm_case(R=0.5, length=4.0, Rs=0.6, offset=0.7, h=1.0 / 32, spacing=2.3
              _port(2, 1, (0.0, 0.0, length), R, OUTLET)]
     return _case(f"aneurysm_{n[0]}x{n[1]}x{n[2]}_L{max_level}", origin, extent, n, X, dS, inside, ports, nu, dt,
                  steps, max_level, refine_band, reduce_band)
+
+
+def aneurysm_slab_128x128x16_L2(nz=16, **kw):
+    """A slab of `nz` coarse cells of the 128x128x256 aneurysm, centred on the
+    sac (mid-length): the same box cross-section, coarse spacing, levels,
+    bands, viscosity, time step and wall points (those inside the slab), with
+    a velocity inlet and an outlet on the tube's disc at the slab's end faces.
+    The oracle steps it in seconds to a minute."""
+    c = aneurysm_128x128x256_L2(**kw)
+    h = c["extent"][2] / c["n"][2]
+    k0 = c["n"][2] // 2 - nz // 2
+    z0, z1 = k0 * h, (k0 + nz) * h
+    X, dS = c["X"], c["dS"]
+    keep = (X[:, 2] >= z0) & (X[:, 2] <= z1)
+    X = X[keep].copy()
+    X[:, 2] -= z0
+    n = (c["n"][0], c["n"][1], nz)
+    origin = (c["origin"][0], c["origin"][1], 0.0)
+    extent = (c["extent"][0], c["extent"][1], nz * h)
+    R = c["ports"][0]["radius"]
+    ports = [_port(2, 0, (0.0, 0.0, 0.0), R, INLET, a0=1.0, b=(0.5,), period=1.0),
+             _port(2, 1, (0.0, 0.0, extent[2]), R, OUTLET)]
+    inside = np.ascontiguousarray(c["inside"][k0:k0 + nz])
+    return _case(f"aneurysm_128x128x{nz}_L2_slab", origin, extent, n, X, dS[keep], inside, ports, c["nu"], c["dt"],
+                 2, c["max_level"], c["refine_band"], c["reduce_band"])
 
 
 def bent_tube_case(R=0.5, Rc=1.5, l_in=1.5, l_out=1.5, h=1.0 / 16, spacing=2.3, seed=5, max_level=0,
