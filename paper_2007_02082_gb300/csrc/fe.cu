@@ -645,6 +645,273 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
   }
 }
 
+// ---------------------------------------------------------------- staged Poisson stencil
+// The FP32 7-point Poisson kernels of the mixed path (the CG iteration form and
+// the plain apply of the V-cycle).  One CTA of 128 threads walks a chunk of
+// bricks through a ring of P7_STAGES stages in shared memory, P7_STAGES - 1
+// bricks ahead of the one it computes.  Per brick a stage receives
+//   * the brick's own values of each input vector and its metadata: bulk
+//     copies of contiguous 2 KB / 1 KB runs (cp.async.bulk, the TMA unit's
+//     untiled form) completing on the stage's mbarrier;
+//   * the six face halos of each input vector by asynchronous copies
+//     (cp.async, zero-filled where there is no neighbour): 16-byte pieces of
+//     the y and z faces, single values of the x faces; each thread waits for
+//     its own copy groups.  (Face boxes of a tensor map were measured slower:
+//     their 16-32 byte rows bound the copies by the TMA unit's request rate.)
+// No register holds a value in transit.  Each thread computes four
+// consecutive nodes of an x row straight from the stage with 16-byte shared
+// loads, and stores them as one 16-byte vector; one CTA barrier per brick.
+// The single-node form of this kernel was bound by instruction issue, not by
+// memory.  Where every node of a warp has all eight incident cells active the
+// stiffness edge counts are the constant 6; elsewhere they come from a table
+// of the 256 incident-cell masks in shared memory.  The arithmetic is that of
+// k_poisson_cg, in the same order.
+constexpr int P7_STAGES = 4;
+constexpr int P7_THREADS = 128;
+constexpr int P7_CHUNK = 8;    // bricks per chunk at most (the chunk table's)
+template <int NV>   // input vectors: 2 (z and p_old) for the CG form, 1 for the apply
+struct P7Stage {
+  // per vector 896 floats: the brick's own 512 values, then the face halos,
+  // face f (-x, +x, -y, +y, -z, +z) at 512 + 64 f, its element (u, v) at 8 v + u
+  static constexpr int VEC = 896;
+  static constexpr int META = NV * VEC * 4;       // 512 x uint16
+  static constexpr int BYTES = META + 1024;
+};
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool fill) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(fill ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool fill) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(fill ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// The face copies of one thread: copy A (every thread) is a 16-byte piece of a
+// y or z face (threads 0..63) or an -x face value (64..127); copy B (threads
+// 0..63) a +x face value.  fa/fb: face, ha/hb: node index in the neighbour
+// brick, da/db: float offset in the vector block.
+struct P7Copies {
+  int fa, ha, da, hb, db;
+};
+__device__ __forceinline__ P7Copies p7_copies(int t) {
+  P7Copies c;
+  if (t < 64) {
+    const int f = 2 + (t >> 4), q = t & 15, v = q >> 1, u0 = (q & 1) * 4;
+    const int far = (f & 1) ? 0 : 7;           // the neighbour's plane next to this brick
+    c.fa = f;
+    c.ha = f < 4 ? (v * DBS + far) * DBS + u0 : (far * DBS + v) * DBS + u0;
+    c.da = DBV + 64 * f + 8 * v + u0;
+    const int e = t, u = e & 7, w = e >> 3;    // +x face element (u, w): x = 0 of the neighbour
+    c.hb = (w * DBS + u) * DBS;
+    c.db = DBV + 64 + 8 * w + u;
+  } else {
+    const int e = t - 64, u = e & 7, w = e >> 3;   // -x face element: x = 7 of the neighbour
+    c.fa = 0;
+    c.ha = (w * DBS + u) * DBS + 7;
+    c.da = DBV + 8 * w + u;
+    c.hb = c.db = 0;
+  }
+  return c;
+}
+
+// Fill one stage with brick i of the chunk (every thread calls it): warp 0
+// issues the bulk copies, every thread its face copies.  nbf[6 i + f] is the
+// neighbour brick across face f.
+template <int NV>
+__device__ __forceinline__ void p7_issue(const DevGrid& g, unsigned char* stage, uint64_t* bar, int b,
+                                         const int* nbf, int i, const float* v0, const float* v1,
+                                         const P7Copies& c) {
+  const int t = threadIdx.x;
+  float* sv = reinterpret_cast<float*>(stage);
+  if (t < 32) {
+    if (t == 0) mbar_arrive_expect_tx(bar, uint32_t(NV * 2048 + 1024));
+    __syncwarp();
+    if (t < NV) bulk_g2s(sv + t * P7Stage<NV>::VEC, (t ? v1 : v0) + (int64_t)b * DBV, 2048u, bar);
+    else if (t == NV) bulk_g2s(stage + P7Stage<NV>::META, g.meta + (int64_t)b * DBV, 1024u, bar);
+  }
+  const int na = nbf[6 * i + c.fa];
+  const int64_t sa = na >= 0 ? (int64_t)na * DBV + c.ha : 0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float* src = (v ? v1 : v0);
+    float* dst = sv + v * P7Stage<NV>::VEC;
+    if (t < 64) {
+      cp_async16(dst + c.da, src + sa, na >= 0);
+      const int nb = nbf[6 * i + 1];
+      cp_async4(dst + c.db, src + (nb >= 0 ? (int64_t)nb * DBV + c.hb : 0), nb >= 0);
+    } else {
+      cp_async4(dst + c.da, src + sa, na >= 0);
+    }
+  }
+  cp_async_commit();
+}
+
+template <bool CG>
+__global__ void __launch_bounds__(P7_THREADS, 8)
+    k_poisson7_staged(DevGrid g, const float* __restrict__ z, const float* __restrict__ pold,
+                      float* __restrict__ pnew, float* __restrict__ q, uint16_t dmask, KState* __restrict__ ks,
+                      double* __restrict__ partials, unsigned* __restrict__ counter, const uint8_t* __restrict__ on) {
+  KCOUNT();
+  constexpr int NV = CG ? 2 : 1;
+  constexpr int VEC = P7Stage<NV>::VEC;
+  using S = P7Stage<NV>;
+  extern __shared__ unsigned char p7_dyn[];
+  __shared__ __align__(8) uint64_t full[P7_STAGES];
+  __shared__ int nbf[6 * P7_CHUNK];
+  __shared__ float fac[3 * P7_CHUNK];   // stencil factors (V/6)/h_a^2 of each brick
+  __shared__ uint32_t ecnt[256];        // per mask: edge counts, 4 bits each, (+x, -x, +y, -y, +z, -z)
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p7_dyn) + 127) & ~uintptr_t(127));
+  const int b0 = g.cbrick[blockIdx.x], b1 = g.cbrick[blockIdx.x + 1];
+  const int inst = g.binst[b0];
+  const bool done = ks ? ks[inst].done != 0 : false;
+  float acc = 0.f;
+  if (!CG && (done || (on && !on[inst]))) return;
+  if (!done) {
+    const float beta = CG ? k_beta<float>(ks[inst]) : 0.f;
+    const int t = threadIdx.x;
+    const int n = b1 - b0;
+    if (t < 6 * n) {
+      // face f: -x, +x, -y, +y, -z, +z -> entry of the 27-entry neighbour table
+      const int f = t % 6;
+      nbf[t] = g.bnbr[27 * (b0 + t / 6) + (f == 0 ? 12 : f == 1 ? 14 : f == 2 ? 10 : f == 3 ? 16 : f == 4 ? 4 : 22)];
+    } else if (t >= 64 && t < 64 + 3 * n) {
+      const int j = t - 64;
+      fac[j] = stencil_factors<float>(g, b0 + j / 3)[j % 3];
+    }
+    for (int mk = t; mk < 256; mk += P7_THREADS) {
+      uint32_t w = 0;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) w |= uint32_t(stiff_edge_count(mk, e >> 1, (e & 1) ? -1 : 1)) << (4 * e);
+      ecnt[mk] = w;
+    }
+    if (t == 0)
+      for (int k = 0; k < P7_STAGES; ++k) mbar_init(&full[k]);
+    __syncthreads();
+    const P7Copies cc = p7_copies(t);
+    // this thread's four nodes: x = 4 seg .. 4 seg + 3 of row (ly, lz); offsets
+    // in a vector block of the node, of the rows and planes next to it and of
+    // the x neighbours of its first and last node
+    const int seg = t & 1, ly = (t >> 1) & 7, lz = t >> 4;
+    const int o = (lz * 8 + ly) * 8 + 4 * seg;
+    const int oym = ly > 0 ? o - 8 : DBV + 128 + 8 * lz + 4 * seg, oyp = ly < 7 ? o + 8 : DBV + 192 + 8 * lz + 4 * seg;
+    const int ozm = lz > 0 ? o - 64 : DBV + 256 + 8 * ly + 4 * seg, ozp = lz < 7 ? o + 64 : DBV + 320 + 8 * ly + 4 * seg;
+    const int oxl = seg ? o - 1 : DBV + 8 * lz + ly, oxr = seg ? DBV + 64 + 8 * lz + ly : o + 4;
+    for (int k = 0; k < P7_STAGES - 1; ++k) {
+      if (k < n) p7_issue<NV>(g, sm + k * S::BYTES, &full[k], b0 + k, nbf, k, z, pold, cc);
+      else cp_async_commit();
+    }
+    for (int i = 0; i < n; ++i) {
+      const int k = i % P7_STAGES;
+      cp_async_wait<P7_STAGES - 2>();   // this thread's face copies of brick i
+      if (t == 0) mbar_wait_or_flag(&full[k], uint32_t(i / P7_STAGES) & 1u, g.aerr + inst);
+      __syncthreads();   // stage k complete and visible; every thread is past brick i - 1
+      {
+        const int ir = i + P7_STAGES - 1, kr = ir % P7_STAGES;   // the stage of brick i - 1
+        if (ir < n) p7_issue<NV>(g, sm + kr * S::BYTES, &full[kr], b0 + ir, nbf, ir, z, pold, cc);
+        else cp_async_commit();
+      }
+      const unsigned char* st = sm + k * S::BYTES;
+      const float* vb = reinterpret_cast<const float*>(st);
+      // p (= z + beta p_old for the CG form): four nodes, or one value
+      auto p4 = [&](int off) -> float4 {
+        float4 a = *reinterpret_cast<const float4*>(vb + off);
+        if constexpr (CG) {
+          const float4 b = *reinterpret_cast<const float4*>(vb + off + VEC);
+          a = make_float4(float(a.x + beta * b.x), float(a.y + beta * b.y), float(a.z + beta * b.z),
+                          float(a.w + beta * b.w));
+        }
+        return a;
+      };
+      auto p1 = [&](int off) -> float {
+        if constexpr (CG) return float(vb[off] + beta * vb[off + VEC]);
+        else return vb[off];
+      };
+      const float4 pc = p4(o), ym = p4(oym), yp = p4(oyp), zm = p4(ozm), zp = p4(ozp);
+      const float xl = p1(oxl), xr = p1(oxr);
+      const uint2 mm = *reinterpret_cast<const uint2*>(st + S::META + 2 * o);
+      const uint16_t m[4] = {uint16_t(mm.x & 0xFFFFu), uint16_t(mm.x >> 16), uint16_t(mm.y & 0xFFFFu),
+                             uint16_t(mm.y >> 16)};
+      const float fx = fac[3 * i], fy = fac[3 * i + 1], fz = fac[3 * i + 2];
+      const float pv[4] = {pc.x, pc.y, pc.z, pc.w};
+      const float xv[6] = {xl, pc.x, pc.y, pc.z, pc.w, xr};
+      const float ymv[4] = {ym.x, ym.y, ym.z, ym.w}, ypv[4] = {yp.x, yp.y, yp.z, yp.w};
+      const float zmv[4] = {zm.x, zm.y, zm.z, zm.w}, zpv[4] = {zp.x, zp.y, zp.z, zp.w};
+      float out[4];
+      const bool full4 = ((m[0] & m[1] & m[2] & m[3] & (D_VALID | 0xFF)) == (D_VALID | 0xFF));
+      if (__all_sync(0xffffffffu, full4)) {
+        // every node of the warp: all eight incident cells active, edge counts 6
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float w = 6.f;
+          out[j] = fx * (w * (pv[j] - xv[j + 2]) + w * (pv[j] - xv[j])) + fy * (w * (pv[j] - ypv[j]) + w * (pv[j] - ymv[j])) +
+                   fz * (w * (pv[j] - zpv[j]) + w * (pv[j] - zmv[j]));
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          out[j] = 0.f;
+          if (m[j] & D_VALID) {
+            const uint32_t w = ecnt[m[j] & 0xFF];
+            const float wxp = float(w & 15u), wxm = float((w >> 4) & 15u), wyp = float((w >> 8) & 15u);
+            const float wym = float((w >> 12) & 15u), wzp = float((w >> 16) & 15u), wzm = float((w >> 20) & 15u);
+            out[j] = fx * (wxp * (pv[j] - xv[j + 2]) + wxm * (pv[j] - xv[j])) +
+                     fy * (wyp * (pv[j] - ypv[j]) + wym * (pv[j] - ymv[j])) +
+                     fz * (wzp * (pv[j] - zpv[j]) + wzm * (pv[j] - zmv[j]));
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (m[j] & dmask) out[j] = 0.f;
+      // brick padding: the inputs are zero there, so are p and the output
+      const int64_t s = (int64_t)(b0 + i) * DBV + o;
+      *reinterpret_cast<float4*>(q + s) = make_float4(out[0], out[1], out[2], out[3]);
+      if constexpr (CG) {
+        *reinterpret_cast<float4*>(pnew + s) = pc;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc += pv[j] * out[j];
+      }
+    }
+  }
+  if (!CG) return;
+  float v[1] = {acc};
+  double* out = partials + (int64_t)gridDim.x;
+  if (!grid_sum_last<float, 1>(v, partials, counter, g.cseg, g.ninst, out)) return;
+  for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
+    KState& kk = ks[i];
+    if (kk.done) continue;
+    const double pq = out[i];
+    kk.pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) { kk.done = 1; kk.status = 5; kk.alpha = 0.0; kk.af = 0.f; continue; }
+    kk.alpha = kk.rz / pq;
+    kk.af = float(kk.alpha);
+  }
+}
+
+template <int NV>
+static constexpr size_t p7_smem() { return size_t(P7_STAGES) * P7Stage<NV>::BYTES + 128; }
+
+// The staged kernel serves FP32 vectors on 16-byte boundaries (every vector of
+// the library; the bulk and 16-byte copies need it) over the chunks of at most
+// P7_CHUNK bricks; returns false (nothing launched) otherwise.
+template <typename T, bool CG>
+static bool launch_p7(const DevGrid& g, const T* z, const T* pold, T* pnew, T* q, uint16_t dmask, KState* ks,
+                      double* partials, unsigned* counter, const uint8_t* on, cudaStream_t st) {
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
+    auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    if (!a16(z) || !a16(q) || (CG && (!a16(pold) || !a16(pnew)))) return false;
+    IBG_LAUNCH((k_poisson7_staged<CG>), g.nchunks, P7_THREADS, p7_smem<CG ? 2 : 1>(), st, g, z, pold, pnew, q, dmask,
+               ks, partials, counter, on);
+    return true;
+  }
+}
+
 // Halo element t (t < HALO15) of a brick for the 15-point Kuhn stencil: the six
 // faces (384 nodes), the six edges reached by the offsets +-(1,1,0),
 // +-(0,1,1), +-(1,0,1) (48 nodes) and the corners +-(1,1,1).  Gives the
@@ -954,9 +1221,12 @@ static void launch_apply(const DevGrid& g, int op, const T* x, T* y, const T* co
                          KState* ks, RedBuf rb, cudaStream_t st, const T* zf = nullptr, T* pnew = nullptr) {
   // the Poisson operator is scalar; its CG form (fused direction update and
   // p.q) is k_poisson_cg<T, true>, launched by fe_apply_cg
-  if (op == OP_POISSON)
-    IBG_LAUNCH((k_poisson_cg<T, false>), g.nchunks, DBV, 0, st, g, x, (const T*)nullptr, (T*)nullptr, y, dmask,
-               (KState*)nullptr, (double*)nullptr, (unsigned*)nullptr, (const uint8_t*)nullptr);
+  if (op == OP_POISSON) {
+    if (!launch_p7<T, false>(g, x, (const T*)nullptr, (T*)nullptr, y, dmask, (KState*)nullptr, (double*)nullptr,
+                             (unsigned*)nullptr, (const uint8_t*)nullptr, st))
+      IBG_LAUNCH((k_poisson_cg<T, false>), g.nchunks, DBV, 0, st, g, x, (const T*)nullptr, (T*)nullptr, y, dmask,
+                 (KState*)nullptr, (double*)nullptr, (unsigned*)nullptr, (const uint8_t*)nullptr);
+  }
   else if (op == OP_MASS && FUSEP)
     IBG_LAUNCH((k_apply15<T, OP_MASS, NC, FUSEP, false>), g.nchunks, DBV, 0, st, g, x, y, coef, dmask, post, ks,
                rb.partials, rb.counter, zf, pnew);
@@ -982,9 +1252,11 @@ static void launch_apply(const DevGrid& g, int op, const T* x, T* y, const T* co
 template <typename T>
 void fe_apply_cg(const DevGrid& g, const OpDesc<T>& A, int nc, const T* z, const T* pold, T* pnew, T* q, KState* ks,
                  RedBuf rb, cudaStream_t st) {
-  if (nc == 1 && A.op == OP_POISSON)
-    IBG_LAUNCH((k_poisson_cg<T, true>), g.nchunks, DBV, 0, st, g, z, pold, pnew, q, A.dmask, ks, rb.partials,
-               rb.counter, (const uint8_t*)nullptr);
+  if (nc == 1 && A.op == OP_POISSON) {
+    if (!launch_p7<T, true>(g, z, pold, pnew, q, A.dmask, ks, rb.partials, rb.counter, (const uint8_t*)nullptr, st))
+      IBG_LAUNCH((k_poisson_cg<T, true>), g.nchunks, DBV, 0, st, g, z, pold, pnew, q, A.dmask, ks, rb.partials,
+                 rb.counter, (const uint8_t*)nullptr);
+  }
   else if (nc == 1) launch_apply<T, 1, true>(g, A.op, pold, q, A.coef, A.dmask, POST_CG_ALPHA, ks, rb, st, z, pnew);
   else launch_apply<T, 3, true>(g, A.op, pold, q, A.coef, A.dmask, POST_CG_ALPHA, ks, rb, st, z, pnew);
 }
@@ -992,8 +1264,10 @@ void fe_apply_cg(const DevGrid& g, const OpDesc<T>& A, int nc, const T* z, const
 template <typename T>
 void fe_poisson_apply(const DevGrid& g, const T* x, T* q, uint16_t dmask, KState* ks, const uint8_t* on,
                       cudaStream_t st) {
-  IBG_LAUNCH((k_poisson_cg<T, false>), g.nchunks, DBV, 0, st, g, x, (const T*)nullptr, (T*)nullptr, q, dmask, ks,
-             (double*)nullptr, (unsigned*)nullptr, on);
+  if (!launch_p7<T, false>(g, x, (const T*)nullptr, (T*)nullptr, q, dmask, ks, (double*)nullptr, (unsigned*)nullptr,
+                           on, st))
+    IBG_LAUNCH((k_poisson_cg<T, false>), g.nchunks, DBV, 0, st, g, x, (const T*)nullptr, (T*)nullptr, q, dmask, ks,
+               (double*)nullptr, (unsigned*)nullptr, on);
 }
 
 template <typename T>
@@ -1059,6 +1333,13 @@ cudaError_t fe_configure() {
   cudaError_t e = cudaFuncSetAttribute(k_apply15_mom32<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        int(cudaSharedmemCarveoutMaxShared));
   if (e != cudaSuccess) return e;
+  for (auto k : {k_poisson7_staged<true>, k_poisson7_staged<false>}) {
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  int(cudaSharedmemCarveoutMaxShared))) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(p7_smem<2>()))) != cudaSuccess)
+      return e;
+  }
   return cudaFuncSetAttribute(k_apply15_mom32<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                               int(cudaSharedmemCarveoutMaxShared));
 }
