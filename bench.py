@@ -1,14 +1,19 @@
 """Throughput of the IB-FE-IPCS time step on GB300.
 
 A step is one full IPCS time step (tentative-velocity BiCGStab, BCE-IB force
-solve and correction, pressure-increment PCG, velocity-correction PCG) of the
-64x64x256 immersed cylinder with one refinement level in a 2-cell band around
-the wall and domain reduction (32k wall points, pulsatile inflow, nu = 0.02,
-dt = 0.002), mixed precision (FP32 Krylov iterations inside FP64 defect
-correction).  Metric: active leaf cells x steps / second.
+solve and correction, pressure-increment PCG with the multigrid V-cycle,
+velocity-correction PCG) of the default workload: the synthetic saccular
+aneurysm on a 128x128x256 coarse grid with two refinement levels in a band
+around the wall and domain reduction (27 M active leaf cells, 54k wall points,
+pulsatile inflow, nu = 0.01, dt = 0.001), mixed precision (FP32 Krylov
+iterations inside FP64 defect correction).  Metric: active leaf cells x steps
+/ second.  The same line carries the plain FP64 GPU path timed on the same
+steps (`fp64`), the continuously batched serving run against the FP64 path
+one request at a time (`serve`), the dominant kernel's roofline and the CPU
+oracle on a bounded slab of the same workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                    [--precision mixed|fp64] [--workload NAME]
+                    [--precision mixed|fp64] [--workload NAME] [--serve N | --no-serve]
 
 Under torchrun each rank runs an independent replica on its own GPU (the path
 has no exchange step between problems): value = all ranks' cell-steps / the
@@ -32,6 +37,9 @@ if ROOT not in sys.path:
 METRIC = "IPCS cell-steps/s at 1e-6 vs plain FP64 GPU path; %HBM peak; serve p50/p99"
 UNIT = "cell-steps/s"
 FALLBACK_HBM_GBS = 6800.0
+
+
+DEFAULT_WORKLOAD = "aneurysm_128x128x256_L2"
 
 
 def workload(name):
@@ -99,9 +107,9 @@ def sample_case(name):
         return (W.cylinder_refined_slab_64x64x16(),
                 "64x64x16 coarse-cell slab of the same tube (16 of 256 cells in z, 2000 points), 2 steps")
     if name == "aneurysm_128x128x256_L2":
-        return (W.aneurysm_slab_128x128x16_L2(),
-                "128x128x16 coarse-cell slab of the aneurysm through the sac centre (16 of 256 cells in z), 2 steps")
-    return workload(name), "full workload, 2 steps"
+        return (W.aneurysm_slab_128x128x16_L2(nz=4),
+                "128x128x4 coarse-cell slab of the aneurysm through the sac centre (4 of 256 cells in z)")
+    return workload(name), "full workload"
 
 
 def peaks():
@@ -346,29 +354,12 @@ def run_native(args, rank, world, local_rank):
     e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(hu.nbytes + hp.nbytes), "d2h_bytes_per_step": int(hu.nbytes + hp.nbytes)}
 
-    # accuracy of the timed path against the plain FP64 GPU path: both from the
-    # same initial state, args.accuracy_steps steps, outside the timed region
-    accuracy = None
+    # the plain FP64 GPU path on the same steps from the same start, timed with
+    # CUDA events like the timed region, and the accuracy of the mixed path
+    # against it (outside the timed region)
+    fp64 = None
     if args.accuracy_steps > 0 and args.precision == "mixed":
-        ga = IBGrid(case, precision="mixed", device=local_rank, poisson_pc=args.poisson_pc)
-        gb = IBGrid(case, precision="fp64", device=local_rank, poisson_pc=args.poisson_pc)
-        if wall is None:
-            ga.ipcs_step(args.accuracy_steps)
-            gb.ipcs_step(args.accuracy_steps)
-        else:   # the same wall motion on both paths
-            for n in range(args.accuracy_steps):
-                X, UB = wall(n)
-                for h in (ga, gb):
-                    h.ib_set_points(X, UB)
-                    h.ipcs_step(1)
-        acc = {}
-        for f in ("U", "P"):
-            xa, xb = ga.ib_fields_get(f), gb.ib_fields_get(f)
-            acc["rel_l2_" + f.lower()] = float(np.linalg.norm(xa - xb) / max(np.linalg.norm(xb), 1e-300))
-        accuracy = {"steps": args.accuracy_steps, **acc, "tolerance": 1e-6,
-                    "within": bool(max(acc.values()) <= 1e-6), "against": "plain FP64 GPU path, same start"}
-        ga.close()
-        gb.close()
+        fp64 = fp64_comparison(case, args, local_rank, wall, flush, stream)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -398,7 +389,9 @@ def run_native(args, rank, world, local_rank):
         "e2e": e2e,
         "iters_last_step": {k: i2[k] for k in ("iters_mom", "iters_ib", "iters_p", "iters_corr", "outer_mom",
                                               "outer_p", "outer_corr")},
-        "accuracy": accuracy,
+        "fp64": fp64,
+        "fp64_ms_per_step": fp64["fp64_ms_per_step"] if fp64 else None,
+        "mixed_vs_fp64_speedup": fp64["speedup"] if fp64 else None,
     }
     if args.wss:
         X = torch.tensor(case["X"], dtype=torch.float64, device=f"cuda:{local_rank}")
@@ -425,7 +418,46 @@ def run_native(args, rank, world, local_rank):
     return out
 
 
-def run_oracle_sample(name, steps=2):
+def fp64_comparison(case, args, local_rank, wall, flush, stream):
+    """The mixed path and the plain FP64 GPU path stepped from the same start
+    for args.accuracy_steps steps, each step timed with CUDA events on the
+    library's stream (L2 flushed before each); returns the per-step times,
+    the speed-up and the relative L2 distance of U and P after the last step."""
+    import numpy as np
+    import torch
+    from paper_2007_02082_gb300 import IBGrid
+    n = args.accuracy_steps
+    res = {}
+    fields = {}
+    for prec in ("mixed", "fp64"):
+        h = IBGrid(case, precision=prec, device=local_rank, poisson_pc=args.poisson_pc)
+        cells = h.ib_grid_info()["n_leaf_cells"]
+        ms = 0.0
+        for k in range(n):
+            if wall is not None:            # the same wall motion on both paths
+                X, UB = wall(k)
+                h.ib_set_points(X, UB)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.ipcs_step(1)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        res[prec] = ms / n
+        fields[prec] = {f: h.ib_fields_get(f) for f in ("U", "P")}
+        h.close()
+    acc = {"rel_l2_" + f.lower(): float(np.linalg.norm(fields["mixed"][f] - fields["fp64"][f])
+                                        / max(np.linalg.norm(fields["fp64"][f]), 1e-300)) for f in ("U", "P")}
+    return {"steps": n, "from": "rest (the same start on both paths)", "mixed_ms_per_step": res["mixed"],
+            "fp64_ms_per_step": res["fp64"], "fp64_cell_steps_per_s": cells / (res["fp64"] / 1e3),
+            "speedup": res["fp64"] / res["mixed"], **acc, "tolerance": 1e-6,
+            "within": bool(max(acc.values()) <= 1e-6),
+            "accuracy_against": "plain FP64 GPU path, same start (each path matches the FP64 oracle: "
+                                "FP64 <= 1e-10, mixed <= 1e-6, in the parity tests)"}
+
+
+def run_oracle_sample(name, steps=1):
     """Time the CPU oracle (as it stands) on a bounded sample of the workload."""
     from oracle import ibfe
     case, desc = sample_case(name)
@@ -439,26 +471,34 @@ def run_oracle_sample(name, steps=2):
     # the oracle's numpy / scipy calls may run library threads: the cores it
     # used are measured as the process CPU time over the wall time
     return {"value": cells * steps / t, "unit": UNIT, "cores": max(1, round(c / t)), "kind": "oracle",
-            "sample": f"{desc}: {cells} leaf cells, {t:.1f} s wall, {c:.1f} s CPU"}
+            "sample": f"{desc}, {steps} step(s): {cells} leaf cells, {t:.1f} s wall, {c:.1f} s CPU "
+                      f"(numpy / scipy library threads on {os.cpu_count()} host cores; cores = CPU / wall)"}
 
 
-def run_serving(n_req, steps):
-    """Serving comparison on a reduced request stream (the full mix is 256
-    requests x 200 steps of 32^3-128^3 active leaf cells): the continuously
-    batched mixed path vs the plain FP64 path one request at a time, same
-    arrivals."""
+def run_serving(n_req, steps, seed=5):
+    """Serving comparison on a reduced config-5 stream (the full mix is 256
+    requests x 200 steps of 32^3-128^3 active leaf cells): seeded vessels of
+    32^3-96^3 active leaf cells, 0-2 levels, Poisson arrivals at 0.8 x the
+    batched path's capacity, measured first on the same requests all arriving
+    at once.  The continuously batched mixed path and the plain FP64 path one
+    request at a time serve the same arrivals."""
     import workloads as W
     from paper_2007_02082_gb300.serve import serve, serve_one_at_a_time
-    stream = W.serving_requests(n_req=n_req, rate=None, seed=5, steps=steps, cells_lo=32 ** 3, cells_hi=64 ** 3)
-    # arrival rate: all requests within the first quarter of the one-at-a-time makespan is not known in
-    # advance; use a fixed mean inter-arrival of 50 ms
-    stream = [(0.05 * t, c) for t, c in stream]
+    base = W.serving_requests(n_req=n_req, rate=None, seed=seed, steps=steps, cells_lo=32 ** 3,
+                              cells_hi=96 ** 3)
+    # capacity of the batched path: the whole stream at t = 0
+    cal = serve([(0.0, c) for _, c in base], precision="mixed", epoch_steps=10).summary()
+    capacity = n_req / cal["makespan_s"]
+    lam = 0.8 * capacity
+    stream = [(t / lam, c) for t, c in base]      # unit-rate arrivals scaled to rate lam
     b = serve(stream, precision="mixed", epoch_steps=10).summary()
     o = serve_one_at_a_time(stream, precision="fp64").summary()
-    return {"requests": n_req, "steps": steps, "mean_interarrival_s": 0.05,
+    return {"requests": n_req, "steps": steps, "capacity_req_per_s": capacity, "rate_req_per_s": lam,
             "batched_mixed": b, "one_at_a_time_fp64": o,
-            "stream": "seeded Poisson arrivals; straight/bent/aneurysmal tubes, R 0.3-1.0, L 3-10, "
-                      "coarse spacing sized for 32^3-64^3 active leaf cells, 0-2 levels, nu 0.01-0.05"}
+            "p99_speedup": o["p99_s"] / b["p99_s"], "throughput_speedup": b["cell_steps_per_s"] / o["cell_steps_per_s"],
+            "stream": "seeded Poisson arrivals at 0.8 x the measured capacity of the batched path; straight, bent "
+                      "and aneurysmal tubes, R 0.3-1.0, L 3-10, coarse spacing sized for 32^3-96^3 active leaf "
+                      "cells, 0-2 levels, nu 0.01-0.05; mixed path at the 1e-6 accuracy of the parity tests"}
 
 
 def main():
@@ -469,9 +509,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--poisson-pc", default="multigrid", choices=["multigrid", "jacobi"])
-    ap.add_argument("--accuracy-steps", type=int, default=20,
-                    help="steps of the mixed vs FP64 comparison reported under 'accuracy' (0: skip)")
-    ap.add_argument("--workload", default="cylinder_64x64x256_L1")
+    ap.add_argument("--accuracy-steps", type=int, default=10,
+                    help="steps of the timed mixed vs plain FP64 comparison reported under 'fp64' (0: skip)")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--viscous", default="grad", choices=["grad", "sym"],
                     help="viscous form: nu (grad u, grad v) or the symmetric 2 nu (eps(u), eps(v))")
     ap.add_argument("--inlet", default="velocity", choices=["velocity", "pressure"],
@@ -487,9 +527,10 @@ def main():
     ap.add_argument("--nvtx", action="store_true",
                     help="wrap each timed step in an NVTX range 'ipcs_step' and each eagerly replayed step "
                          "in 'ipcs_step_eager'")
-    ap.add_argument("--serve", type=int, default=0,
-                    help="also run the serving comparison on a stream of this many requests")
-    ap.add_argument("--serve-steps", type=int, default=50)
+    ap.add_argument("--serve", type=int, default=24,
+                    help="requests of the serving comparison run after the timed steps (0: skip)")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-steps", type=int, default=40)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -499,7 +540,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = run_oracle_sample(args.workload)
+        cb = run_oracle_sample(args.workload, steps=max(1, min(args.steps, 2)))
         v = cb["value"]
         out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
@@ -516,7 +557,7 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     out = run_native(args, rank, world, local_rank)
-    if args.serve and rank == 0:
+    if args.serve and not args.no_serve and rank == 0 and world == 1:
         out["serve"] = run_serving(args.serve, args.serve_steps)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:

@@ -372,7 +372,10 @@ void ib_batch_destroy(ib_batch* b);
  *                  (read them with ib_fields_get)
  *   errors         IB_ESTATE for a standalone handle or one that a batch
  *                  holds (read those with ib_fields_get), IB_EINVAL for other
- *                  fields or a wrong byte count, IB_ECUDA for a CUDA error
+ *                  fields, a wrong byte count, or a current CUDA device other
+ *                  than the one current at ib_grid_create (the scratch and
+ *                  the snapshot are per device: make the handle's device
+ *                  current first), IB_ECUDA for a CUDA error
  *
  * The first call on a device, with that device current, does a one-time setup
  * (it resolves the scratch's device address, which can load the library's

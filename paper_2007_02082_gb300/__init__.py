@@ -86,8 +86,10 @@ class _TorchAllocator:
         self.stream = stream
         self.alloc = _abi.ALLOC_FN(self._alloc)
         self.free = _abi.FREE_FN(self._free)
+        self.calls = 0          # device allocations the library asked for
 
     def _alloc(self, nbytes, ctx):
+        self.calls += 1
         try:
             return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
         except Exception:
@@ -216,9 +218,15 @@ class IBGrid:
 
     def ib_fields_get_noalloc(self, field, out=None):
         """ib_fields_get_noalloc: U, P or PHI of a parked deferred handle, read
-        through the library's fixed device scratch (no device allocation)."""
+        through the library's fixed device scratch (no device allocation).
+        `out`, if given, is a contiguous float64 CUDA tensor of the field's
+        shape on the handle's device."""
         shape, dt = self._shape(field)
         if out is not None:
+            import torch
+            if (not out.is_cuda or out.dtype != torch.float64 or not out.is_contiguous()
+                    or tuple(out.shape) != tuple(shape)):
+                raise ValueError(f"out must be a contiguous float64 CUDA tensor of shape {shape}")
             nbytes = out.numel() * out.element_size()
             self._check("ib_fields_get_noalloc", self.lib.ib_fields_get_noalloc(
                 self.h, FIELD[field], C.c_void_p(out.data_ptr()), nbytes, 1))

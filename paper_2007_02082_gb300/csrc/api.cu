@@ -174,6 +174,7 @@ struct ib_grid {
   int64_t snap_bytes = 0;
   ib_batch* batch = nullptr;    // batch currently holding a deferred handle
   int batch_index = -1;
+  int device = -1;              // CUDA device current at ib_grid_create
 };
 
 struct ib_batch {
@@ -1200,7 +1201,7 @@ ib_status ib_grid_create(const ib_grid_desc* d, ib_grid** out) {
   ib_grid* g = new (std::nothrow) ib_grid();
   if (!g) return IB_ENOMEM;
   g->d = *d;
-  if (fe_init_tables() != cudaSuccess) {
+  if (cudaGetDevice(&g->device) != cudaSuccess || fe_init_tables() != cudaSuccess) {
     delete g;
     return IB_ECUDA;
   }
@@ -1645,6 +1646,13 @@ ib_status ib_fields_get_noalloc(ib_grid* g, int32_t field, void* dst, size_t byt
   if (g->eng || g->batch) {
     g->err = "only a deferred handle that no batch holds is read without allocation; use ib_fields_get";
     return IB_ESTATE;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != g->device) {
+    // the scratch is per device and the snapshot lives on the handle's device
+    g->err = "the handle was created on CUDA device " + std::to_string(g->device) + " but device " +
+             std::to_string(dev) + " is current: make the handle's device current first";
+    return IB_EINVAL;
   }
   const int nc = field == IB_FIELD_U ? 3 : 1;
   const double* src = field == IB_FIELD_U ? g->snap.u : field == IB_FIELD_P ? g->snap.p : g->snap.phi;

@@ -157,3 +157,24 @@ def test_serving_loop_results_match_alone():
         assert np.array_equal(g.ib_fields_get("U"), got[rid]), rid
         b.close()
         g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_serving_footprint_covers_the_batch_bytes(precision):
+    """The serving loop admits requests by footprint(): for single members and
+    for a mix, the estimate is at least the device bytes the batch engine
+    reports holding (ib_batch_info), so admission never plans with less memory
+    than the library takes."""
+    from paper_2007_02082_gb300 import IBBatch, IBGrid
+    from paper_2007_02082_gb300.serve import footprint
+    cases = _cases() + [W.aneurysm_case(R=0.4, length=3.0, Rs=0.5, offset=0.55, h=1.0 / 12, max_level=2, seed=35,
+                                        dt=0.002, b=())]
+    mem = [IBGrid(c, precision=precision, deferred=True) for c in cases]
+    for group in [[m] for m in mem] + [mem]:
+        b = IBBatch(group)
+        est = sum(footprint(m.ib_grid_info(), precision) for m in group)
+        measured = b.info(0)["device_bytes"]
+        b.close()
+        assert measured <= est <= 1.6 * measured, (len(group), measured, est)
+    for m in mem:
+        m.close()

@@ -21,7 +21,8 @@ class FakeGrid:
 
     def ib_grid_info(self):
         c = self.case
-        return {"n_slots": c["slots"], "n_points": c["points"], "af_nnz": c["nnz"], "n_leaf_cells": c["cells"]}
+        return {"n_slots": c["slots"], "n_points": c["points"], "af_nnz": c["nnz"], "n_leaf_cells": c["cells"],
+                "device_bytes": c.get("snap", 0)}
 
     def close(self):
         assert not self.closed and self.batch is None
@@ -46,6 +47,11 @@ class FakeBatch:
             fail_at = h.case.get("fail_at")
             st.append(5 if fail_at is not None and h.steps >= fail_at else 0)
         return st
+
+    def info(self, i):
+        # a batch engine reporting `engine_factor` times the estimated bytes
+        est = sum(S.footprint(h.ib_grid_info(), "mixed") for h in self.handles)
+        return {"device_bytes": int(est * max(h.case.get("engine_factor", 1.0) for h in self.handles))}
 
     def close(self):
         for h in self.handles:
@@ -120,4 +126,52 @@ def test_footprint_counts_the_mixed_force_solve():
     info = {"n_slots": 0, "n_points": 256, "af_nnz": 1000}
     d = S.footprint(info, "mixed") - S.footprint(info, "fp64")
     assert d == 256 * (24 + 84 + 4) + 1000 * 4
+    # the coarsest multigrid level's dense inverse, in the Krylov precision
+    mg = dict(info, mg_levels=3, mg_coarsest=100)
+    assert S.footprint(mg, "fp64") - S.footprint(info, "fp64") == 8 * 100 * 100
+    assert S.footprint(mg, "mixed") - S.footprint(info, "mixed") == 4 * 100 * 100
     assert np.all([S.footprint(dict(info, n_slots=n), "fp64") > 0 for n in (0, 512)])
+
+
+def test_snapshots_of_built_requests_count_against_the_budget():
+    """Each built request holds a device snapshot until it leaves: with the
+    budget at two footprints plus a snapshot's worth, snapshots as large as a
+    footprint leave room for one member at a time."""
+    c = _case(0, 4)
+    one = S.footprint({"n_slots": c["slots"], "n_points": c["points"], "af_nnz": c["nnz"]}, "mixed")
+    stream = [(0.0, _case(k, 4, snap=one)) for k in range(4)]
+    res = S.serve(stream, hbm_budget=3 * one + 1, epoch_steps=2, setup_workers=4)
+    assert res.summary()["failed"] == 0 and res.summary()["requests"] == 4
+    assert max(res.batch_sizes) == 1
+    assert FakeGrid.live == 0
+
+
+def test_ready_backlog_is_bounded():
+    """At most max_ready requests are built ahead of admission."""
+    peak = [0]
+    orig = FakeGrid.__init__
+
+    def counting(self, *a, **k):
+        orig(self, *a, **k)
+        peak[0] = max(peak[0], FakeGrid.live)
+
+    FakeGrid.__init__ = counting
+    try:
+        stream = [(0.0, _case(k, 6)) for k in range(10)]
+        res = S.serve(stream, max_members=2, max_ready=2, epoch_steps=2, setup_workers=10)
+    finally:
+        FakeGrid.__init__ = orig
+    assert res.summary()["requests"] == 10 and FakeGrid.live == 0
+    assert peak[0] <= 4          # two members and two built ahead
+
+
+def test_admission_follows_the_reported_batch_bytes():
+    """A batch engine that reports more device bytes than the estimate scales
+    the footprint used for admission from then on."""
+    c = _case(0, 4)
+    one = S.footprint({"n_slots": c["slots"], "n_points": c["points"], "af_nnz": c["nnz"]}, "mixed")
+    stream = [(0.0, _case(k, 4, engine_factor=3.0)) for k in range(6)]
+    res = S.serve(stream, hbm_budget=4 * one, epoch_steps=2, setup_workers=1)
+    assert res.summary()["failed"] == 0
+    assert res.footprint_scale == pytest.approx(3.0)
+    assert max(res.batch_sizes[1:]) <= 1       # 3 x one each: one member fits the budget

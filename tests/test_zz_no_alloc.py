@@ -45,6 +45,36 @@ def test_noalloc_device_destination():
         out.zero_()
         g.ib_fields_get_noalloc("U", out=out)
         assert np.array_equal(out.cpu().numpy(), ref)
+    # the binding refuses a destination of the wrong dtype, layout or shape
+    with pytest.raises(ValueError):
+        g.ib_fields_get_noalloc("U", out=torch.empty(ref.shape, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        g.ib_fields_get_noalloc("U", out=torch.empty((3, ref.shape[0]), dtype=torch.float64, device="cuda").t())
+    with pytest.raises(ValueError):
+        g.ib_fields_get_noalloc("U", out=torch.empty(ref.size, dtype=torch.float64, device="cuda"))
+    g.close()
+
+
+def test_noalloc_read_allocates_nothing():
+    """The defining property: no device allocation, neither through the
+    library's allocator callback nor in PyTorch's caching allocator."""
+    import torch
+    g = _parked(W.cylinder_refined_small(n=(16, 16, 8), seed=43), 1)
+    ref = g.ib_fields_get("P")
+    out = torch.empty(ref.shape, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    calls = g._alloc.calls
+    before = torch.cuda.memory_stats()["allocation.all.allocated"]
+    for _ in range(2):
+        g.ib_fields_get_noalloc("P", out=out)
+        host = g.ib_fields_get_noalloc("P")
+    torch.cuda.synchronize()
+    assert g._alloc.calls == calls
+    assert torch.cuda.memory_stats()["allocation.all.allocated"] == before
+    assert np.array_equal(out.cpu().numpy(), ref) and np.array_equal(host, ref)
+    # ib_fields_get on the same parked handle does allocate (a temporary gather buffer)
+    g.ib_fields_get("P")
+    assert g._alloc.calls > calls
     g.close()
 
 
