@@ -2,15 +2,16 @@
 
 A step is one full IPCS time step (tentative-velocity BiCGStab, BCE-IB force
 solve and correction, pressure-increment PCG with the multigrid V-cycle,
-velocity-correction PCG) of the default workload: the synthetic saccular
-aneurysm on a 128x128x256 coarse grid with two refinement levels in a band
-around the wall and domain reduction (27 M active leaf cells, 54k wall points,
-pulsatile inflow, nu = 0.01, dt = 0.001), mixed precision (FP32 Krylov
-iterations inside FP64 defect correction).  Metric: active leaf cells x steps
-/ second.  The same line carries the plain FP64 GPU path timed on the same
-steps (`fp64`), the continuously batched serving run against the FP64 path
-one request at a time (`serve`), the dominant kernel's roofline and the CPU
-oracle on a bounded slab of the same workload.
+velocity-correction PCG) of the default workload: the synthetic aorta-like
+vessel (arched, tapered, three branches) on a 256x256x384 coarse grid with two
+refinement levels in a band around the wall and domain reduction (56 M active
+leaf cells, 204k wall points, cardiac inflow waveform of peak Re 1500,
+dt = 5e-4), mixed precision (FP32 Krylov iterations inside FP64 defect
+correction).  Metric: active leaf cells x steps / second.  The same line
+carries the plain FP64 GPU path timed on the same steps (`fp64`), the
+continuously batched serving run against the FP64 path one request at a time
+(`serve`), the dominant kernel's roofline and the CPU oracle on a bounded slab
+of the same workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
                     [--precision mixed|fp64] [--workload NAME] [--serve N | --no-serve]
@@ -39,7 +40,7 @@ UNIT = "cell-steps/s"
 FALLBACK_HBM_GBS = 6800.0
 
 
-DEFAULT_WORKLOAD = "aneurysm_128x128x256_L2"
+DEFAULT_WORKLOAD = "aorta_256x256x384_L2"
 
 
 def workload(name):
@@ -50,6 +51,8 @@ def workload(name):
         return W.cylinder_uniform_16x16x64()
     if name == "aneurysm_128x128x256_L2":
         return W.aneurysm_128x128x256_L2()
+    if name == "aorta_256x256x384_L2":
+        return W.aorta_256x256x384_L2()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -109,7 +112,38 @@ def sample_case(name):
     if name == "aneurysm_128x128x256_L2":
         return (W.aneurysm_slab_128x128x16_L2(nz=4),
                 "128x128x4 coarse-cell slab of the aneurysm through the sac centre (4 of 256 cells in z)")
+    if name == "aorta_256x256x384_L2":
+        # 4 of 384 coarse cells in z across the two straight limbs (z = -3):
+        # each limb gets an inlet on the slab's low face and an outlet on its high face
+        c = W.aorta_256x256x384_L2()
+        h = c["extent"][2] / c["n"][2]
+        k0 = int((-3.0 - c["origin"][2]) / h)
+        return (_slab(c, k0, 4, [(-3.0, 1.0), (3.0, None)]),
+                "256x256x4 coarse-cell slab of the aorta across its two straight limbs (4 of 384 cells in z)")
     return workload(name), "full workload"
+
+
+def _slab(c, k0, nz, tubes):
+    """A slab of nz coarse cells of a case from coarse layer k0: the wall
+    points there, the inside mask cut to the slab, and for each z-aligned tube
+    (x centre, radius or None for the largest wall distance there) a velocity
+    inlet on the slab's low face and an outlet on its high face."""
+    import numpy as np
+    import workloads as W
+    h = c["extent"][2] / c["n"][2]
+    z0 = c["origin"][2] + k0 * h
+    keep = (c["X"][:, 2] >= z0) & (c["X"][:, 2] <= z0 + nz * h)
+    X = c["X"][keep].copy()
+    ports = []
+    for x0, r in tubes:
+        if r is None:
+            near = np.abs(X[:, 0] - x0) < 2.0
+            r = float(np.hypot(X[near, 0] - x0, X[near, 1]).max())
+        ports.append(W._port(2, 0, (x0, 0.0, z0), r, W.INLET, a0=1.0))
+        ports.append(W._port(2, 1, (x0, 0.0, z0 + nz * h), r, W.OUTLET))
+    return W._case(c["name"] + "_slab", (c["origin"][0], c["origin"][1], z0), (c["extent"][0], c["extent"][1], nz * h),
+                   (c["n"][0], c["n"][1], nz), X, c["dS"][keep], np.ascontiguousarray(c["inside"][k0:k0 + nz]),
+                   ports, c["nu"], c["dt"], 2, c["max_level"], c["refine_band"], c["reduce_band"])
 
 
 def peaks():

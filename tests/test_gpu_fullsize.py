@@ -1,5 +1,6 @@
-"""Full-size cases (the 64x64x256 refined cylinder and the 128x128x256
-two-level aneurysm) through the C ABI, checked by what holds at any size:
+"""Full-size cases (the 64x64x256 refined cylinder, the 128x128x256
+two-level aneurysm and the 256x256x384 two-level aorta) through the C ABI,
+checked by what holds at any size:
 
   * the coarse level map and the active-cell mask equal the oracle's (Sec. 3.2
     refinement, Sec. 4.3 domain reduction), bit for bit;
@@ -25,6 +26,7 @@ pytestmark = pytest.mark.gpu
 CASES = {
     "cylinder_64x64x256_L1": W.cylinder_refined_64x64x256,
     "aneurysm_128x128x256_L2": W.aneurysm_128x128x256_L2,
+    "aorta_256x256x384_L2": W.aorta_256x256x384_L2,
 }
 
 

@@ -8,6 +8,9 @@
 * A square duct without an immersed boundary (M = 0; Eq. 9, Eq. 12 and the
   velocity correction alone, pressure-driven as in Sec. 3.1), the case the
   oracle pins against the closed-form duct flow.
+* A reduced copy of the synthetic aorta (arched, tapered, three branches,
+  five ports on two faces, the cardiac inflow waveform): 40x40x60 coarse
+  cells, one level, 3k wall points, two steps.
 """
 import numpy as np
 import pytest
@@ -24,6 +27,8 @@ TOLMIX = 1e-6
 CASES = {
     "slab": (W.cylinder_refined_slab_64x64x16, 2),
     "duct_no_ib": (lambda: W.square_duct_case(n=(8, 8, 32), dt=0.5), 3),
+    "aorta_small": (lambda: W.aorta_case(n=(40, 40, 60), max_level=1, M=3000, seed=44, dt=0.002,
+                                         name="aorta_40x40x60_L1"), 2),
 }
 _ORACLE = {}
 

@@ -331,6 +331,145 @@ def bent_tube_case(R=0.5, Rc=1.5, l_in=1.5, l_out=1.5, h=1.0 / 16, spacing=2.3, 
                  max_level, refine_band, reduce_band)
 
 
+def aorta_waveform():
+    """The synthetic aorta's inflow waveform (aorta_waveform.json): period,
+    a0, a_k, b_k of the peak velocity, the peak Reynolds number and the inlet
+    diameter it refers to."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "aorta_waveform.json")) as f:
+        return json.load(f)
+
+
+def _tube_points(centre, tangent, normal, radius, dradius, s0, s1, ds_target, rng, curvature=0.0):
+    """Stratified jitter on a tube of varying radius around a planar
+    centreline: strata in (arclength s, angle theta), one point each,
+    displaced by at most +-0.35 stratum; theta measured from `normal(s)`
+    towards e_y.  dS = the local area element R (1 - kappa R cos theta)
+    sqrt(1 + R'^2) times the stratum size."""
+    L = s1 - s0
+    rmax = max(radius(s0), radius(s1))
+    n_s = max(4, int(round(L / math.sqrt(ds_target))))
+    n_th = max(8, int(round(2 * math.pi * rmax / math.sqrt(ds_target))))
+    s = s0 + (np.arange(n_s)[:, None] + 0.5 + rng.uniform(-0.35, 0.35, (n_s, n_th))) * (L / n_s)
+    th = (np.arange(n_th)[None, :] + 0.5 + rng.uniform(-0.35, 0.35, (n_s, n_th))) * (2 * math.pi / n_th)
+    s, th = s.ravel(), th.ravel()
+    C, N, R, dR = centre(s), normal(s), radius(s), dradius(s)
+    ey = np.array([0.0, 1.0, 0.0])
+    X = C + R[:, None] * (np.cos(th)[:, None] * N + np.sin(th)[:, None] * ey[None, :])
+    dS = R * (1.0 - curvature * R * np.cos(th)) * np.sqrt(1.0 + dR * dR) * (L / n_s) * (2 * math.pi / n_th)
+    return X, dS
+
+
+def aorta_case(n=(256, 256, 384), max_level=2, M=200000, seed=4, Rc=3.0, l_down=6.0, r_in=1.0, r_out=0.7,
+               r_branch=0.25, branch_deg=(110.0, 90.0, 70.0), refine_band=2, reduce_band=2, dt=5e-4, steps=2000,
+               name=None):
+    """Synthetic aorta-like vessel.  The centreline arches over 180 degrees in
+    the xz-plane (a circle of radius Rc about the origin, from (-Rc, 0, 0)
+    up over (0, 0, Rc) to (Rc, 0, 0)), then descends straight for l_down.
+    The radius tapers linearly from r_in to r_out along the arch and the
+    descent.  Three branch tubes of radius r_branch rise along +z from the
+    arch centreline at the given arch angles to the top of the box.  The
+    ascending limb continues straight down, radius r_in, to the low-z face of
+    the box at z = -l_down: the inlet and the descending outlet both lie on
+    that face and the branch outlets on the high-z face (ports lie on box
+    faces).  Box: x and y within +-(Rc + r_in) plus a margin of 4 cubic
+    cells, cubic spacing h = 2 (Rc + r_in + 4 h) / n_x, extent n h per axis.
+    Inflow: the 5-harmonic waveform of aorta_waveform.json (peak 1);
+    nu = U_peak D_in / Re_peak = 2 / 1500."""
+    wf = aorta_waveform()
+    nu = 1.0 * wf["inlet_diameter"] / wf["peak_reynolds"]
+    half = Rc + r_in
+    h = 2.0 * half / (n[0] - 8)                          # x: the vessel plus 4 cells each side
+    origin = (-half - 4 * h, -0.5 * n[1] * h, -l_down)
+    extent = (n[0] * h, n[1] * h, n[2] * h)
+    z_top = origin[2] + extent[2]
+    hf = h / (1 << max_level)
+    L_arc = math.pi * Rc
+    L_tot = L_arc + l_down
+    rad = lambda s: r_in + (r_out - r_in) * np.clip(s, 0.0, L_tot) / L_tot
+    drad = lambda s: np.where((s >= 0) & (s <= L_tot), (r_out - r_in) / L_tot, 0.0)
+    # centreline by arclength s: s < 0 the inflow extension, [0, L_arc] the
+    # arch, beyond it the descent
+    def centre(s):
+        s = np.asarray(s, dtype=np.float64)
+        phi = math.pi - np.clip(s, 0.0, L_arc) / Rc
+        c = np.stack([Rc * np.cos(phi), np.zeros_like(s), Rc * np.sin(phi)], -1)
+        c = np.where((s < 0)[..., None], np.stack([-Rc + 0 * s, 0 * s, s], -1), c)
+        c = np.where((s > L_arc)[..., None], np.stack([Rc + 0 * s, 0 * s, -(s - L_arc)], -1), c)
+        return c
+    def normal(s):   # in the xz-plane, away from the arch centre (and -x / +x on the straight limbs)
+        s = np.asarray(s, dtype=np.float64)
+        phi = math.pi - np.clip(s, 0.0, L_arc) / Rc
+        return np.stack([np.cos(phi), np.zeros_like(s), np.sin(phi)], -1)
+    rng = np.random.default_rng(seed)
+    # area to spread the M points over (estimated), then each part
+    A_arch = 2 * math.pi * 0.5 * (r_in + rad(L_arc)) * L_arc
+    A_down = 2 * math.pi * 0.5 * (rad(L_arc) + r_out) * l_down
+    A_in = 2 * math.pi * r_in * l_down
+    br_len = [z_top - Rc * math.sin(math.radians(d)) for d in branch_deg]
+    A_br = sum(2 * math.pi * r_branch * L for L in br_len)
+    ds_target = (A_arch + A_down + A_in + A_br) / M
+    parts = [
+        _tube_points(centre, None, normal, rad, drad, 0.0, L_arc, ds_target, rng, curvature=1.0 / Rc),
+        _tube_points(centre, None, normal, rad, drad, L_arc, L_tot, ds_target, rng),
+        _tube_points(centre, None, normal, rad, drad, -l_down, 0.0, ds_target, rng),
+    ]
+    bx = []
+    for d, L in zip(branch_deg, br_len):
+        x0, z0 = Rc * math.cos(math.radians(d)), Rc * math.sin(math.radians(d))
+        bx.append(x0)
+        cb = lambda s, x0=x0, z0=z0: np.stack([x0 + 0 * np.asarray(s), 0 * np.asarray(s), z0 + np.asarray(s)], -1)
+        nb = lambda s: np.stack([np.ones_like(np.asarray(s)), 0 * np.asarray(s), 0 * np.asarray(s)], -1)
+        parts.append(_tube_points(cb, None, nb, lambda s: r_branch + 0 * np.asarray(s),
+                                  lambda s: 0 * np.asarray(s), 0.0, L, ds_target, rng))
+    # signed inside tests: distance to each centreline piece below its radius
+    def in_main(P):
+        x, y, z = P[..., 0], P[..., 1], P[..., 2]
+        # arch: nearest point on the circle in the xz-plane, upper half
+        rr = np.hypot(x, z)
+        phi = np.arctan2(z, x)
+        on_arch = (z >= 0) & (phi >= 0) & (phi <= math.pi)
+        s_arch = (math.pi - np.clip(phi, 0, math.pi)) * Rc
+        d_arch = np.where(on_arch, np.hypot(rr - Rc, y), np.inf)
+        ins = d_arch < rad(s_arch)
+        ins |= (z < 0) & (np.hypot(x + Rc, y) < r_in)                              # inflow extension
+        s_down = L_arc - z
+        ins |= (z < 0) & (np.hypot(x - Rc, y) < rad(s_down))                      # descent
+        return ins
+    def in_branch(P):
+        x, y, z = P[..., 0], P[..., 1], P[..., 2]
+        ins = np.zeros(P.shape[:-1], dtype=bool)
+        for d, x0 in zip(branch_deg, bx):
+            z0 = Rc * math.sin(math.radians(d))
+            ins |= (z >= z0) & (np.hypot(x - x0, y) < r_branch)
+        return ins
+    Xs, dSs = [], []
+    for k, (X, dS) in enumerate(parts):
+        keep = ~in_branch(X) if k < 3 else ~in_main(X)
+        Xs.append(X[keep])
+        dSs.append(dS[keep])
+    X = np.concatenate(Xs)
+    dS = np.concatenate(dSs)
+    xc, yc, zc = cell_centres(origin, extent, n)
+    P = np.stack([xc, yc, zc], -1)
+    inside = in_main(P) | in_branch(P)
+    a, b = tuple(wf["a"]), tuple(wf["b"])
+    ports = [_port(2, 0, (-Rc, 0.0, origin[2]), r_in, INLET, a0=wf["a0"], a=a, b=b, period=wf["period"]),
+             _port(2, 0, (Rc, 0.0, origin[2]), r_out, OUTLET)]
+    for x0 in bx:
+        ports.append(_port(2, 1, (x0, 0.0, z_top), r_branch, OUTLET))
+    return _case(name or f"aorta_{n[0]}x{n[1]}x{n[2]}_L{max_level}", origin, extent, n, X, dS, inside, ports, nu,
+                 dt, steps, max_level, refine_band, reduce_band)
+
+
+def aorta_256x256x384_L2(**kw):
+    """The synthetic aorta on 256x256x384 coarse cells with two refinement
+    levels, domain reduction, 200k wall points, the cardiac waveform inflow
+    (peak Re 1500), dt = 5e-4, 2000 steps."""
+    return aorta_case(**kw)
+
+
 def serving_requests(n_req=256, rate=None, seed=5, steps=200, cells_lo=32 ** 3, cells_hi=128 ** 3):
     """Poisson-arrival stream of seeded random vessels: kind in {straight,
     bent, aneurysmal}, radius 0.3-1.0, length 3-10, about 32^3 to 128^3 active
