@@ -257,6 +257,33 @@ CLASS_NAMES = {0: "k_poisson_cg (p = z + beta p, q = K p, fused p.q)", 1: "k_cg_
                10: "k_mg_c_smooth (V-cycle smoothing update)", 11: "V-cycle transfers and coarse levels"}
 
 
+TUNE_CACHE = os.path.join(ROOT, "paper_2007_02082_gb300", "tune_cache.json")
+
+
+def resolve_tune(case, precision, args, local_rank):
+    """Launch choices of the timed handles: the autotuner's cached choice for
+    the workload's class (--tune cache, the default), a fresh tuning run that
+    updates the cache (--tune run), or the library's defaults (--tune off)."""
+    from paper_2007_02082_gb300 import tune as T
+    if args.tune == "off":
+        return None, {"source": "library defaults", "choice": dict(T.DEFAULTS)}
+    cache = T.TuneCache(TUNE_CACHE)
+    if args.tune == "run":
+        cache.table.pop(_tune_key(case, precision, local_rank), None)
+    choice, key, hit, timings = T.tune_case(case, precision, cache=cache, device=local_rank, steps=3, warmup=2)
+    return choice, {"source": "cache" if hit else "tuned now", "key": key, "choice": choice,
+                    "candidates": [{"overrides": o, "ms_per_step": t} for o, t in timings] or None}
+
+
+def _tune_key(case, precision, local_rank):
+    from paper_2007_02082_gb300 import IBGrid
+    from paper_2007_02082_gb300 import tune as T
+    h = IBGrid(case, precision=precision, device=local_rank, deferred=True)
+    k = T.class_key(h.ib_grid_info(), precision, case["max_level"])
+    h.close()
+    return k
+
+
 def run_native(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -265,7 +292,9 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     load_library(build_if_missing=True)
     case = apply_variant(workload(args.workload), args)
-    g = IBGrid(case, precision=args.precision, device=local_rank, poisson_pc=args.poisson_pc)
+    tune, tune_meta = resolve_tune(case, args.precision, args, local_rank)
+    args.tune_choice = tune
+    g = IBGrid(case, precision=args.precision, device=local_rank, poisson_pc=args.poisson_pc, tune=tune)
     info0 = g.ib_grid_info()
     cells = info0["n_leaf_cells"]
     stream = torch.cuda.current_stream()
@@ -327,7 +356,8 @@ def run_native(args, rank, world, local_rank):
     # Kernels inside the step graph cannot be bracketed by events, so the same
     # step is replayed eagerly on a second handle (same stream, same kernels,
     # same order) with CUDA events around every solver kernel launch.
-    gp = IBGrid(case, precision=args.precision, device=local_rank, profile=True, poisson_pc=args.poisson_pc)
+    gp = IBGrid(case, precision=args.precision, device=local_rank, profile=True, poisson_pc=args.poisson_pc,
+                tune=tune)
     for _ in range(max(1, args.warmup)):
         gp.ipcs_step(1)
     j1 = gp.ib_grid_info()
@@ -410,6 +440,7 @@ def run_native(args, rank, world, local_rank):
                               f"device rebuild {rebuild_ms[0] / args.steps:.3f} ms per step, inside the timed step")
                    if wall is not None else None,
                    "l2": "flushed between steps (256 MB write)",
+                   "launch_choices": tune_meta,
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -464,7 +495,8 @@ def fp64_comparison(case, args, local_rank, wall, flush, stream):
     res = {}
     fields = {}
     for prec in ("mixed", "fp64"):
-        h = IBGrid(case, precision=prec, device=local_rank, poisson_pc=args.poisson_pc)
+        h = IBGrid(case, precision=prec, device=local_rank, poisson_pc=args.poisson_pc,
+                   tune=getattr(args, "tune_choice", None) if prec == "mixed" else None)
         cells = h.ib_grid_info()["n_leaf_cells"]
         ms = 0.0
         for k in range(n):
@@ -552,6 +584,9 @@ def main():
                     help="drive the tube by its inlet velocity or by the inlet pressure that gives the same "
                          "Poiseuille peak (16 nu L / R^2 per unit of peak speed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", default="cache", choices=["cache", "run", "off"],
+                    help="launch choices: the autotuner's cached choice for the workload class (tuning it when "
+                         "the class is new), a fresh tuning run, or the library defaults")
     ap.add_argument("--wss", action="store_true",
                     help="also time the wall shear stress at the wall points (ib_wss, device buffers) after the "
                          "timed steps; tubes along z, radial normals")

@@ -62,6 +62,11 @@ enum { IB_PC_MULTIGRID = 0, IB_PC_JACOBI = 1 };
 enum { IB_VISCOUS_GRAD = 0, IB_VISCOUS_SYM = 1 };
 
 #define IB_MAX_PORTS 8
+#define IB_TUNE_N 4
+#define IB_TUNE_POISSON_KERNEL 0
+#define IB_TUNE_STREAM_CHUNK 1
+#define IB_TUNE_MG_SMALL 2
+#define IB_TUNE_MG_SWEEPS 3
 #define IB_MAX_HARMONICS 8
 #define IB_MAX_LEVEL 3
 
@@ -146,6 +151,23 @@ typedef struct {
  *                       block it returns must start on a 256-byte boundary
  *                       (the streaming kernels use 16-byte vector accesses);
  *                       a misaligned block fails the call with IB_ENOMEM
+ *   tune                launch choices that change speed, not the method (0 =
+ *                       the library's default; the package's autotuner picks
+ *                       them per workload class); a batch takes its first
+ *                       member's:
+ *     [IB_TUNE_POISSON_KERNEL]  FP32 Poisson stencil: 1 staged asynchronously
+ *                               (default), 2 register-pipelined
+ *     [IB_TUNE_STREAM_CHUNK]    bricks per CTA of the streaming Krylov
+ *                               kernels: 4 or 8 (default)
+ *     [IB_TUNE_MG_SMALL]        multigrid levels with at most this many nodes
+ *                               (64 .. 1048576, default 8192) run in one CTA
+ *                               per problem
+ *     [IB_TUNE_MG_SWEEPS]       damped-Jacobi sweeps before and after the
+ *                               coarse correction on the composite level and
+ *                               G0: 1 .. 4 (default 2); the V-cycle stays a
+ *                               symmetric preconditioner, so the solution is
+ *                               the same to the solver tolerance
+ *                       Invalid values fail ib_grid_create with IB_EINVAL.
  */
 typedef struct {
   double origin[3], extent[3];
@@ -166,6 +188,7 @@ typedef struct {
   void* (*dev_alloc)(size_t bytes, void* ctx);
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
+  int32_t tune[IB_TUNE_N];
 } ib_grid_desc;
 
 /* Counts, spacing ratio and the last step's solver statistics. */

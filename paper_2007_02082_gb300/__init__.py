@@ -106,7 +106,11 @@ class IBGrid:
     """One resident IB-FE-IPCS problem (an ib_grid handle)."""
 
     def __init__(self, case, precision="fp64", stream=None, torch_alloc=True, rtol=None, max_iter=0,
-                 device=0, profile=False, deferred=False, poisson_pc="multigrid"):
+                 device=0, profile=False, deferred=False, poisson_pc="multigrid", tune=None):
+        """tune: launch choices (ib_grid_desc.tune), a dict with any of
+        "poisson_kernel" (1 staged, 2 register-pipelined), "stream_chunk"
+        (4 or 8), "mg_small" (nodes) and "mg_sweeps" (1-4); None or 0 keeps
+        the library's defaults (see paper_2007_02082_gb300.tune)."""
         self.lib = load_library()
         self.case = case
         self._alloc = None
@@ -145,6 +149,11 @@ class IBGrid:
             raise ValueError("poisson_pc must be 'multigrid' or 'jacobi'")
         d.poisson_pc = _abi.IB_PC_JACOBI if poisson_pc == "jacobi" else _abi.IB_PC_MULTIGRID
         d.viscous_form = _viscous_form(case)
+        for k, v in (tune or {}).items():
+            if k not in _abi.TUNE_INDEX:
+                raise ValueError(f"unknown launch choice {k!r}")
+            d.tune[_abi.TUNE_INDEX[k]] = int(v or 0)
+        self.tune = dict(tune or {})
         d.n_ports = len(case["ports"])
         for k, port in enumerate(case["ports"]):
             d.ports[k] = _port_struct(port)

@@ -12,6 +12,8 @@ IB_VISCOUS_GRAD, IB_VISCOUS_SYM = 0, 1
 IB_FP64, IB_MIXED = 0, 1
 IB_PC_MULTIGRID, IB_PC_JACOBI = 0, 1
 IB_MAX_PORTS, IB_MAX_HARMONICS, IB_MAX_LEVEL = 8, 8, 3
+IB_TUNE_N = 4
+TUNE_INDEX = {"poisson_kernel": 0, "stream_chunk": 1, "mg_small": 2, "mg_sweeps": 3}
 
 FIELD = {
     "U": 0, "P": 1, "PHI": 2, "U_TENT": 3, "U_IB": 4, "F_LAG": 5, "B_F": 6, "NODE_Q": 7,
@@ -46,6 +48,7 @@ class IbGridDesc(C.Structure):
         ("viscous_form", C.c_int32),
         ("n_ports", C.c_int32), ("ports", IbPort * IB_MAX_PORTS),
         ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
+        ("tune", C.c_int32 * IB_TUNE_N),
     ]
 
 

@@ -250,11 +250,93 @@ void engine_free(Engine& E) {
 
 // Concatenate the members' multigrid hierarchies level by level and upload
 // them in the engine's Krylov precision T.
+// Level 0's weight-free transfer tables (MGHost::lat0 and following),
+// concatenated over the problems with multigrid.
+template <typename T>
+ib_status mg_upload_level0(Engine& E, const std::vector<uint8_t>& on, const std::vector<int32_t>& noff0,
+                           MGLevelDev<T>& L) {
+  const int n = E.ninst;
+  std::vector<int32_t> bco, lat, latn(3 * n, 0), pbase, fbr, r0slot, r0ptr(1, 0), r0idx, fnode;
+  std::vector<int64_t> latoff(n, 0), fbase;
+  int64_t npart = 0;
+  for (int i = 0; i < n; ++i) {
+    const HostGrid& H = *E.H[i];
+    bco.insert(bco.end(), H.brick_coord.begin(), H.brick_coord.end());
+    const int32_t B0 = int32_t(E.brick0[i]);
+    if (!on[i]) {
+      pbase.insert(pbase.end(), size_t(H.nbricks), -1);
+      fbase.insert(fbase.end(), size_t(H.nbricks), int64_t(0));
+      continue;
+    }
+    const MGHost& m = *E.MG[i];
+    latoff[i] = int64_t(lat.size());
+    lat.insert(lat.end(), m.lat0.begin(), m.lat0.end());
+    for (int a = 0; a < 3; ++a) latn[3 * i + a] = int32_t(m.lat_n[a]);
+    for (int32_t b = 0; b < int32_t(H.nbricks); ++b) {
+      const int32_t pb = m.pbase[b];
+      pbase.push_back(pb >= 0 ? int32_t(pb + npart) : -1);
+      if (pb >= 0) fbr.push_back(b + B0);
+      // prolongation footprint: the G0 nodes the brick's slots interpolate from
+      fbase.push_back(int64_t(fnode.size()));
+      const int l = H.brick_level[b], sc = 1 << l;
+      const int nt = l == 0 ? BS : mg_targets_per_axis(l);
+      int64_t q0[3];
+      for (int a = 0; a < 3; ++a) {
+        q0[a] = int64_t(H.brick_coord[3 * b + a]) * BS / sc;
+        if (l > 0) q0[a] = std::min<int64_t>(q0[a], m.lat_n[a] - 2);
+      }
+      for (int tz = 0; tz < nt; ++tz)
+        for (int ty = 0; ty < nt; ++ty)
+          for (int tx = 0; tx < nt; ++tx) {
+            const int64_t q[3] = {q0[0] + tx, q0[1] + ty, q0[2] + tz};
+            int32_t id = -1;
+            if (q[0] < m.lat_n[0] && q[1] < m.lat_n[1] && q[2] < m.lat_n[2]) {
+              const int32_t v = m.lat0[(q[2] * m.lat_n[1] + q[1]) * m.lat_n[0] + q[0]];
+              if (v >= 0) id = v + noff0[i];
+            }
+            fnode.push_back(id);
+          }
+    }
+    for (size_t j = 0; j < m.r0slot.size(); ++j) {
+      r0slot.push_back(m.r0slot[j] >= 0 ? int32_t(m.r0slot[j] + E.slot0[i]) : -1);
+      for (int32_t e = m.r0ptr[j]; e < m.r0ptr[j + 1]; ++e) r0idx.push_back(int32_t(m.r0idx[e] + npart));
+      r0ptr.push_back(int32_t(r0idx.size()));
+    }
+    npart += m.npart;
+  }
+  if (npart >= (int64_t(1) << 31) || int64_t(r0slot.size()) != int64_t(noff0[n])) {
+    E.err = "multigrid transfer tables do not match the G0 levels";
+    return IB_EINVAL;
+  }
+  int32_t *d_bco, *d_lat, *d_latn, *d_pbase, *d_fbr, *d_r0slot, *d_r0ptr, *d_r0idx, *d_fnode;
+  int64_t *d_latoff, *d_fbase;
+  T *d_part, *d_fp;
+  TRY(upload(E, &d_fbase, fbase));
+  TRY(upload(E, &d_fnode, fnode));
+  TRY(dalloc(E, &d_fp, std::max<int64_t>(int64_t(fnode.size()), 1), true));
+  L.fbase = d_fbase; L.fnode = d_fnode; L.fp = d_fp; L.nfp = int64_t(fnode.size());
+  TRY(upload(E, &d_bco, bco));
+  TRY(upload(E, &d_lat, lat));
+  TRY(upload(E, &d_latoff, latoff));
+  TRY(upload(E, &d_latn, latn));
+  TRY(upload(E, &d_pbase, pbase));
+  TRY(upload(E, &d_fbr, fbr));
+  TRY(upload(E, &d_r0slot, r0slot));
+  TRY(upload(E, &d_r0ptr, r0ptr));
+  TRY(upload(E, &d_r0idx, r0idx));
+  TRY(dalloc(E, &d_part, std::max<int64_t>(npart, 1), true));
+  L.bco = d_bco; L.lat = d_lat; L.lat_off = d_latoff; L.lat_n = d_latn; L.pbase = d_pbase;
+  L.fbr = d_fbr; L.nfb = int32_t(fbr.size()); L.part = d_part;
+  L.r0slot = d_r0slot; L.r0ptr = d_r0ptr; L.r0idx = d_r0idx;
+  return IB_OK;
+}
+
 template <typename T>
 ib_status mg_upload(Engine& E, MGDev<T>& D) {
   const int n = E.ninst;
   D = MGDev<T>();
   D.ninst = n;
+  if (E.D[0].tune[IB_TUNE_MG_SWEEPS] > 0) D.nu = E.D[0].tune[IB_TUNE_MG_SWEEPS];
   std::vector<uint8_t> on(n, 0);
   std::vector<int32_t> small(n, -1), coarsest(n, -1);
   std::vector<int64_t> coff(n, 0);
@@ -303,20 +385,22 @@ ib_status mg_upload(Engine& E, MGDev<T>& D) {
         }
         diag.push_back(T(M.diag[j]));
         dinv.push_back(T(1.0 / M.diag[j]));
-        for (int32_t e = M.r_ptr[j]; e < M.r_ptr[j + 1]; ++e) {
-          const int32_t c = M.r_col[e];
-          rcol.push_back(k == 0 ? int32_t(c + E.slot0[i]) : c + noff[k - 1][i]);
-          rw.push_back(T(M.r_w[e]));
-        }
+        if (k > 0)   // level 0 computes its transfers from lattice positions
+          for (int32_t e = M.r_ptr[j]; e < M.r_ptr[j + 1]; ++e) {
+            rcol.push_back(M.r_col[e] + noff[k - 1][i]);
+            rw.push_back(T(M.r_w[e]));
+          }
         rptr.push_back(int32_t(rcol.size()));
       }
     }
-    // prolongation rows over the finer index space: composite slots or level k-1 nodes
-    const int64_t nrows = k == 0 ? E.ns : int64_t(noff[k - 1][n]);
+    if (k == 0) TRY(mg_upload_level0<T>(E, on, noff[0], L));
+    // prolongation rows over the finer index space: the nodes of level k-1
+    // (level 0 computes its transfers from lattice positions)
+    const int64_t nrows = k == 0 ? 0 : int64_t(noff[k - 1][n]);
     pptr.assign(nrows + 1, 0);
-    for (int i = 0; i < n; ++i) {
-      const int64_t r0 = k == 0 ? E.slot0[i] : noff[k - 1][i];
-      const int64_t r1 = k == 0 ? E.slot0[i + 1] : noff[k - 1][i + 1];
+    for (int i = 0; i < n && k > 0; ++i) {
+      const int64_t r0 = noff[k - 1][i];
+      const int64_t r1 = noff[k - 1][i + 1];
       const bool has = on[i] && k < int(E.MG[i]->lev.size());
       for (int64_t r = r0; r < r1; ++r) {
         if (has) {
@@ -495,10 +579,12 @@ ib_status engine_build(Engine& E) {
   }
   cseg[n] = int32_t(cbrick.size());
   cbrick.push_back(int32_t(E.nbricks));
+  // streaming chunks: a launch choice (IB_TUNE_STREAM_CHUNK), 8 bricks by default
+  const int sch = E.D[0].tune[IB_TUNE_STREAM_CHUNK] > 0 ? E.D[0].tune[IB_TUNE_STREAM_CHUNK] : 8;
   std::vector<int32_t> scbrick, scseg(n + 1);
   for (int i = 0; i < n; ++i) {
     scseg[i] = int32_t(scbrick.size());
-    for (int32_t b = bseg[i]; b < bseg[i + 1]; b += 8) scbrick.push_back(b);
+    for (int32_t b = bseg[i]; b < bseg[i + 1]; b += sch) scbrick.push_back(b);
   }
   scseg[n] = int32_t(scbrick.size());
   scbrick.push_back(int32_t(E.nbricks));
@@ -589,6 +675,7 @@ ib_status engine_build(Engine& E) {
   g.nschunks = int32_t(scbrick.size()) - 1;
   g.scbrick = d_scbrick;
   g.scseg = d_scseg;
+  g.poisson_kernel = E.D[0].tune[IB_TUNE_POISSON_KERNEL];
   g.hl = d_hl; g.pdt = E.pdt; g.pnu = d_pnu; g.sf64 = d_sf64; g.sf32 = d_sf32;
   g.n_if = int32_t(ifc.size());
   g.if_c = d_ifc; g.if_f = d_iff; g.if_off = d_ifo; g.if_kid = d_ifk; g.if_of_slot = d_ifos;
@@ -1131,6 +1218,11 @@ ib_status validate_desc(const ib_grid_desc* d) {
   if (!outlet) return IB_EINVAL;
   int64_t nf = (int64_t(d->n[0]) * d->n[1] * d->n[2]) << (3 * d->max_level);
   if (nf > (int64_t(1) << 40)) return IB_EINVAL;
+  const int32_t* tu = d->tune;
+  if (tu[IB_TUNE_POISSON_KERNEL] < 0 || tu[IB_TUNE_POISSON_KERNEL] > 2) return IB_EINVAL;
+  if (tu[IB_TUNE_STREAM_CHUNK] != 0 && tu[IB_TUNE_STREAM_CHUNK] != 4 && tu[IB_TUNE_STREAM_CHUNK] != 8) return IB_EINVAL;
+  if (tu[IB_TUNE_MG_SMALL] != 0 && (tu[IB_TUNE_MG_SMALL] < 64 || tu[IB_TUNE_MG_SMALL] > (1 << 20))) return IB_EINVAL;
+  if (tu[IB_TUNE_MG_SWEEPS] < 0 || tu[IB_TUNE_MG_SWEEPS] > 4) return IB_EINVAL;
   return IB_OK;
 }
 
@@ -1220,7 +1312,8 @@ ib_status ib_set_boundary(ib_grid* g, int64_t M, const double* X, const double* 
   ib_status s = build_host_grid(g->d, M, X, dS, UB, inside, g->H, g->err);
   if (s != IB_OK) return s;
   g->mg = MGHost();
-  if (g->d.poisson_pc == IB_PC_MULTIGRID) build_mg(g->H, g->mg);
+  if (g->d.poisson_pc == IB_PC_MULTIGRID)
+    build_mg(g->H, g->mg, g->d.tune[IB_TUNE_MG_SMALL] > 0 ? g->d.tune[IB_TUNE_MG_SMALL] : MG_SMALL_NODES);
   if (g->d.deferred) {
     s = snap_alloc(g);
     if (s != IB_OK) return s;

@@ -122,6 +122,8 @@ struct DevGrid {
   const int8_t* __restrict__ nat_comp;
   const double* __restrict__ nat_w64;
   const float* __restrict__ nat_w32;
+  // launch choice: 2 selects the register-pipelined FP32 Poisson stencil
+  int32_t poisson_kernel;
 };
 
 // Index in the compact arrays of thread t's slot of brick b (a valid slot);

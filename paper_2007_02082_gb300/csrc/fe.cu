@@ -905,6 +905,7 @@ static bool launch_p7(const DevGrid& g, const T* z, const T* pold, T* pnew, T* q
     return false;
   } else {
     auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    if (g.poisson_kernel == 2) return false;
     if (!a16(z) || !a16(q) || (CG && (!a16(pold) || !a16(pnew)))) return false;
     IBG_LAUNCH((k_poisson7_staged<CG>), g.nchunks, P7_THREADS, p7_smem<CG ? 2 : 1>(), st, g, z, pold, pnew, q, dmask,
                ks, partials, counter, on);

@@ -246,7 +246,7 @@ bool dense_inverse(const MGLevelHost& M, std::vector<double>& inv) {
 
 }  // namespace
 
-void build_mg(const HostGrid& G, MGHost& mg) {
+void build_mg(const HostGrid& G, MGHost& mg, int64_t small_nodes) {
   mg = MGHost();
   const int L = G.L;
   const int64_t Lf = int64_t(1) << L;
@@ -310,6 +310,53 @@ void build_mg(const HostGrid& G, MGHost& mg) {
       rptr[s + 1] = int32_t(rcol.size());
     }
     transpose(ns, rptr, rcol, rw, M.nn, M.r_ptr, M.r_col, M.r_w);
+  }
+
+  // ---- the same transfers in the device's weight-free form
+  {
+    const Lattice& Lt = lats[0];
+    const MGLevelHost& M = mg.lev[0];
+    mg.lat0 = Lt.lat;
+    for (int a = 0; a < 3; ++a) mg.lat_n[a] = Lt.n[a] + 1;
+    mg.pbase.assign(G.nbricks, -1);
+    mg.r0slot.assign(M.nn, -1);
+    std::vector<int64_t> node_of, part_of;   // (G0 node, partial index) pairs in brick order
+    int64_t np = 0;
+    for (int32_t b = 0; b < int32_t(G.nbricks); ++b) {
+      const int l = G.brick_level[b];
+      const int64_t bc[3] = {G.brick_coord[3 * b], G.brick_coord[3 * b + 1], G.brick_coord[3 * b + 2]};
+      if (l == 0) {
+        for (int t = 0; t < BV; ++t) {
+          const int64_t s = int64_t(b) * BV + t;
+          const uint16_t m = G.meta[s];
+          if (!(m & M_VALID) || (m & (M_HANG | M_PDIR | M_DUP))) continue;
+          const int32_t id = Lt.lat[Lt.node(bc[0] * BS + t % BS, bc[1] * BS + (t / BS) % BS, bc[2] * BS + t / (BS * BS))];
+          if (id >= 0) mg.r0slot[id] = int32_t(s);
+        }
+        continue;
+      }
+      const int sc = 1 << l, T = mg_targets_per_axis(l);
+      mg.pbase[b] = int32_t(np);
+      for (int tz = 0; tz < T; ++tz)
+        for (int ty = 0; ty < T; ++ty)
+          for (int tx = 0; tx < T; ++tx) {
+            const int64_t q[3] = {bc[0] * BS / sc + tx, bc[1] * BS / sc + ty, bc[2] * BS / sc + tz};
+            if (q[0] > Lt.n[0] || q[1] > Lt.n[1] || q[2] > Lt.n[2]) continue;
+            const int32_t id = Lt.lat[Lt.node(q[0], q[1], q[2])];
+            if (id < 0) continue;
+            node_of.push_back(id);
+            part_of.push_back(np + (tz * T + ty) * T + tx);
+          }
+      np += int64_t(T) * T * T;
+    }
+    mg.npart = np;
+    if (np >= (int64_t(1) << 31)) { mg.why = "too many partial restriction sums"; return; }
+    mg.r0ptr.assign(M.nn + 1, 0);
+    for (int64_t id : node_of) mg.r0ptr[id + 1]++;
+    for (int64_t j = 0; j < M.nn; ++j) mg.r0ptr[j + 1] += mg.r0ptr[j];
+    mg.r0idx.assign(node_of.size(), 0);
+    std::vector<int32_t> fill(mg.r0ptr.begin(), mg.r0ptr.end() - 1);
+    for (size_t e = 0; e < node_of.size(); ++e) mg.r0idx[fill[node_of[e]]++] = int32_t(part_of[e]);
   }
 
   // ---- coarser levels
@@ -394,7 +441,7 @@ void build_mg(const HostGrid& G, MGHost& mg) {
   }
   mg.small_start = int(mg.lev.size()) - 1;
   for (int k = 0; k < int(mg.lev.size()); ++k)
-    if (mg.lev[k].nn <= MG_SMALL_NODES) { mg.small_start = k; break; }
+    if (mg.lev[k].nn <= small_nodes) { mg.small_start = k; break; }
   mg.ok = true;
 }
 

@@ -136,39 +136,198 @@ __global__ void __launch_bounds__(512) k_mg_c_smooth(DevGrid g, const T* __restr
   }
 }
 
-// zout = zin + P0 x0 on kept slots
+// Composite <-> G0 transfers.  The weights are those of P1 interpolation on
+// the G0 Kuhn tetrahedron holding a composite node (multiples of 2^-l, exact
+// in floating point), computed per node from lattice positions instead of
+// read from stored CSR rows: the transfers stream the composite vectors once
+// and read only the small G0 vectors and lattice map besides.
+
+// zout = zin + P0 x0 on kept slots, in two passes.  Pass 1 gathers, for
+// every brick, the G0 values of its footprint (the G0 nodes its slots
+// interpolate from: 8^3 own positions at level 0, T^3 nodes at level l >= 1)
+// into a flat array, one thread per entry.  Pass 2 streams the composite
+// slots and reads the footprint values (cached per brick).  Vertices in the
+// order of the reference CSR rows (v0 .. v3 of the tetrahedron, zero weights
+// and Dirichlet G0 nodes skipped), so the sums are those of the stored form,
+// bit for bit.
 template <typename T>
-__global__ void __launch_bounds__(512) k_mg_c_prolong(DevGrid g, MGLevelDev<T> L0, const T* __restrict__ zin,
+__global__ void k_mg_fp_gather(MGLevelDev<T> L0, const uint8_t* __restrict__ on, const KState* ks) {
+  KCOUNT();
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= L0.nfp) return;
+  const int32_t id = L0.fnode[f];
+  L0.fp[f] = id >= 0 ? L0.xa[id] : T(0);
+}
+
+// Pass 2: a CTA per chunk of up to 8 bricks; thread t takes node t of every
+// brick of the chunk, so that the bricks' constants come from shared memory
+// and all of a thread's loads of one pass are in flight together.
+template <typename T>
+__global__ void __launch_bounds__(512, 3) k_mg_c_prolong(DevGrid g, MGLevelDev<T> L0, const T* __restrict__ zin,
                                                       T* __restrict__ zout, uint16_t dmask,
                                                       const uint8_t* __restrict__ on, const KState* ks) {
   KCOUNT();
+  constexpr int CH = 8;
+  __shared__ int sl[CH], sq[CH][3], sc0[CH][3];
+  __shared__ int64_t sfb[CH];
   const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const int inst = g.binst[b0];
   if (ks[inst].done || !on[inst]) return;
-  for (int64_t s = (int64_t)b0 * DBV + threadIdx.x; s < (int64_t)b1 * DBV; s += blockDim.x) {
-    const uint16_t m = g.meta[s];
-    if (!(m & D_VALID)) continue;   // brick padding stays zero
-    if (!keep_slot(m, dmask)) { zout[s] = T(0); continue; }
-    T v = zin[s];
-    for (int e = L0.pptr[s]; e < L0.pptr[s + 1]; ++e) v += L0.pw[e] * L0.xa[L0.pcol[e]];
+  const int nb = min(b1 - b0, CH);
+  const int t = threadIdx.x;
+  // this thread's nodes first: their loads overlap those of the brick constants
+  uint16_t m[CH];
+  T z[CH];
+#pragma unroll
+  for (int i = 0; i < CH; ++i) {
+    m[i] = 0;
+    z[i] = T(0);
+    if (i < nb) {
+      const int64_t s = (int64_t)(b0 + i) * DBV + t;
+      m[i] = g.meta[s];
+      z[i] = zin[s];
+    }
+  }
+  if (t < nb) {
+    const int b = b0 + t, l = g.blev[b], sc = 1 << l;
+    sl[t] = l;
+    sfb[t] = L0.fbase[b];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int nla = L0.lat_n[3 * inst + a];
+      sq[t][a] = L0.bco[3 * b + a] * DBS;                                  // brick origin, level lattice
+      sc0[t][a] = l ? min(L0.bco[3 * b + a] * DBS / sc, nla - 2) : 0;     // the footprint's first G0 node
+    }
+  }
+  __syncthreads();
+  const int nl[3] = {L0.lat_n[3 * inst], L0.lat_n[3 * inst + 1], L0.lat_n[3 * inst + 2]};
+  const int lt[3] = {t & 7, (t >> 3) & 7, t >> 6};
+#pragma unroll
+  for (int i = 0; i < CH; ++i) {
+    if (i >= nb || !(m[i] & D_VALID)) continue;   // brick padding stays zero
+    const int64_t s = (int64_t)(b0 + i) * DBV + t;
+    if (!keep_slot(m[i], dmask)) { zout[s] = T(0); continue; }
+    const T* fp = L0.fp + sfb[i];
+    const int l = sl[i];
+    if (l == 0) {   // a G0 node itself: weight 1 on its own footprint entry
+      zout[s] = z[i] + T(1) * fp[t];
+      continue;
+    }
+    const int sc = 1 << l, nt = (6 + sc) / sc + 1;
+    int c[3], f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int p = sq[i][a] + lt[a];
+      c[a] = min(p >> l, nl[a] - 2);   // the last cell holds the far lattice plane
+      f[a] = p - (c[a] << l);
+      c[a] -= sc0[i][a];
+    }
+    // axes by decreasing offset, ties in axis order: a stable three-element
+    // sort (swaps on strict inequality only)
+    int a0 = 0, a1 = 1, a2 = 2, f0 = f[0], f1 = f[1], f2 = f[2];
+    if (f1 > f0) { int x = a0; a0 = a1; a1 = x; x = f0; f0 = f1; f1 = x; }
+    if (f2 > f1) { int x = a1; a1 = a2; a2 = x; x = f1; f1 = f2; f2 = x; }
+    if (f1 > f0) { int x = a0; a0 = a1; a1 = x; x = f0; f0 = f1; f1 = x; }
+    const int vb[4] = {0, 1 << a0, (1 << a0) | (1 << a1), 7};
+    const int wn[4] = {sc - f0, f0 - f1, f1 - f2, f2};
+    const T inv = T(1) / T(sc);   // a power of two: exact
+    T v = z[i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (wn[k] == 0) continue;
+      const int e = ((c[2] + ((vb[k] >> 2) & 1)) * nt + (c[1] + ((vb[k] >> 1) & 1))) * nt + (c[0] + (vb[k] & 1));
+      v += (T(wn[k]) * inv) * fp[e];   // a Dirichlet G0 node's entry is zero
+    }
     zout[s] = v;
   }
 }
 
-// b0 = R0 (r - A z): G0 rows gather owner slots of the composite level
+// b0 = R0 (r - A z), R0 = P0^T over owner slots, in two passes.
+// Pass 1, one CTA per composite brick of level l >= 1: the brick's residual
+// values (owner copies that are neither hanging nor Dirichlet) in shared
+// memory, then l restrictions by one level each down to the G0 nodes of the
+// brick's footprint.  The nested Kuhn meshes make P0 the product of one-level
+// interpolations, each of which takes a coarse node with weight 1 and the
+// midpoint of each of the seven Kuhn edge directions (+-x, +-y, +-z, +-(1,1,0),
+// +-(0,1,1), +-(1,0,1), +-(1,1,1)) with weight 1/2; its transpose gathers, for
+// a coarse node at fine position 2t, the value there plus half of its 14
+// Kuhn neighbours.  An array of w nodes per axis becomes one of w / 2 + 1
+// (8 -> 5 -> 3 -> 2), each sum in a fixed order.
+__device__ __forceinline__ void kuhn_dir(int k, int& dx, int& dy, int& dz) {
+  // k = 0..13: +-x, +-y, +-z, +-(1,1,0), +-(0,1,1), +-(1,0,1), +-(1,1,1)
+  const int sg = (k & 1) ? -1 : 1, a = k >> 1;
+  dx = sg * (a == 0 || a == 3 || a == 5 || a == 6);
+  dy = sg * (a == 1 || a == 3 || a == 4 || a == 6);
+  dz = sg * (a == 2 || a == 4 || a == 5 || a == 6);
+}
+
 template <typename T>
-__global__ void k_mg_restrict0(DevGrid g, MGLevelDev<T> L0, const T* __restrict__ r, const T* __restrict__ q,
-                               const uint8_t* __restrict__ on, const KState* ks) {
+__device__ __forceinline__ void restrict_one_level(const T* in, int w, T* out, int wo) {
+  for (int j = threadIdx.x; j < wo * wo * wo; j += blockDim.x) {
+    const int tx = j % wo, ty = (j / wo) % wo, tz = j / (wo * wo);
+    const int cx = 2 * tx, cy = 2 * ty, cz = 2 * tz;
+    auto at = [&](int x, int y, int z) -> T {
+      return (x >= 0 && x < w && y >= 0 && y < w && z >= 0 && z < w) ? in[(z * w + y) * w + x] : T(0);
+    };
+    T acc = at(cx, cy, cz);
+    T half = T(0);
+#pragma unroll
+    for (int k = 0; k < 14; ++k) {
+      int dx, dy, dz;
+      kuhn_dir(k, dx, dy, dz);
+      half += at(cx + dx, cy + dy, cz + dz);
+    }
+    out[j] = acc + T(0.5) * half;
+  }
+}
+
+// One CTA of 128 threads per brick (each thread four slots, 16-byte loads),
+// so that many bricks' loads are in flight per SM.
+constexpr int R0_THREADS = 128;
+template <typename T>
+__global__ void __launch_bounds__(R0_THREADS) k_mg_r0_part(DevGrid g, MGLevelDev<T> L0, const T* __restrict__ r,
+                                                           const T* __restrict__ q, uint16_t dmask,
+                                                           const uint8_t* __restrict__ on, const KState* ks) {
+  KCOUNT();
+  __shared__ T bufa[DBV];
+  __shared__ T bufb[125];
+  const int b = L0.fbr[blockIdx.x];
+  const int inst = g.binst[b];
+  if (ks[inst].done || !on[inst]) return;
+  for (int t = threadIdx.x; t < DBV; t += R0_THREADS) {
+    const int64_t s = (int64_t)b * DBV + t;
+    const uint16_t m = g.meta[s];
+    bufa[t] = ((m & D_VALID) && !(m & (D_HANG | D_DUP | dmask))) ? T(r[s] - q[s]) : T(0);
+  }
+  __syncthreads();
+  int l = g.blev[b], w = DBS;
+  T* in = bufa;
+  T* out = bufb;
+  while (l > 1) {   // down to level 1 inside shared memory, alternating buffers
+    const int wo = w / 2 + 1;
+    restrict_one_level(in, w, out, wo);
+    __syncthreads();
+    T* tmp = in; in = out; out = tmp;
+    w = wo;
+    --l;
+  }
+  // the last level straight into the partial sums of the brick's G0 nodes
+  restrict_one_level(in, w, L0.part + L0.pbase[b], w / 2 + 1);
+}
+
+// Pass 2, one thread per G0 node: the level-0 owner copy at its position
+// (weight 1) plus the partial sums of the finer bricks around it, in brick order.
+template <typename T>
+__global__ void k_mg_r0_sum(MGLevelDev<T> L0, const T* __restrict__ r, const T* __restrict__ q,
+                            const uint8_t* __restrict__ on, const KState* ks) {
   KCOUNT();
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= L0.n) return;
   const int inst = L0.inst[j];
   if (ks[inst].done || !on[inst]) return;
-  T v = T(0);
-  for (int e = L0.rptr[j]; e < L0.rptr[j + 1]; ++e) {
-    const int64_t s = L0.rcol[e];
-    v += L0.rw[e] * (r[s] - q[s]);
-  }
+  const int32_t sl = L0.r0slot[j];
+  T v = sl >= 0 ? T(r[sl] - q[sl]) : T(0);
+  for (int e = L0.r0ptr[j]; e < L0.r0ptr[j + 1]; ++e) v += L0.part[L0.r0idx[e]];
   L0.b[j] = v;
 }
 
@@ -369,7 +528,9 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
   }
   apply(cur);
   if (pr) pr->begin(pcls + 2, st);
-  IBG_LAUNCH(k_mg_restrict0<T>, nblk256(mg.lev[0].n), 256, 0, st, g, mg.lev[0], r, q, mg.on, ks);
+  if (mg.lev[0].nfb > 0)
+    IBG_LAUNCH(k_mg_r0_part<T>, mg.lev[0].nfb, R0_THREADS, 0, st, g, mg.lev[0], r, (const T*)q, dmask, mg.on, ks);
+  IBG_LAUNCH(k_mg_r0_sum<T>, nblk256(mg.lev[0].n), 256, 0, st, mg.lev[0], r, (const T*)q, mg.on, ks);
   // large levels, down
   for (int k = 0; k < mg.max_big; ++k) {
     const MGLevelDev<T>& L = mg.lev[k];
@@ -413,6 +574,8 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
   }
   // composite: prolongation and post-smoothing, ending in z
   T* y = (nu % 2 == 0) ? z : zs;
+  if (mg.lev[0].nfp > 0)
+    IBG_LAUNCH(k_mg_fp_gather<T>, nblk256(mg.lev[0].nfp), 256, 0, st, mg.lev[0], mg.on, ks);
   IBG_LAUNCH(k_mg_c_prolong<T>, g.nschunks, DBV, 0, st, g, mg.lev[0], (const T*)cur, y, dmask, mg.on, ks);
   if (pr) pr->end(st);
   fe_expand2<T>(g, 1, y, (T*)nullptr, st);

@@ -65,11 +65,29 @@ struct MGHost {
   std::vector<MGLevelHost> lev;     // G0 .. G(K)
   int small_start = 0;              // first level with at most MG_SMALL_NODES nodes
   std::vector<double> cinv;         // dense inverse of the G(K) operator, [nn_K][nn_K]
+  // Composite <-> G0 transfers without stored weights (the device computes
+  // each weight from lattice positions; the CSR of lev[0] is the reference):
+  //   lat0      G0 lattice, [(n2+1)][(n1+1)][(n0+1)]: G0 node, -1 Dirichlet, -2 absent
+  //   pbase     per composite brick of level >= 1, the first of its partial
+  //             restriction sums (one per G0 node of its footprint, T^3 with
+  //             T = (6 + 2^l) / 2^l + 1 per axis), -1 for level-0 bricks
+  //   r0slot    per G0 node, the level-0 owner slot at its position, or -1
+  //   r0ptr/idx per G0 node, the partial sums that make up its restriction,
+  //             in brick order
+  std::vector<int32_t> lat0;
+  int64_t lat_n[3] = {0, 0, 0};
+  std::vector<int32_t> pbase;
+  int64_t npart = 0;
+  std::vector<int32_t> r0slot, r0ptr, r0idx;
 };
 
-// Build the hierarchy of one composite grid.  On failure (no outlet node at
+// Footprint of a level-l brick in G0 nodes per axis (see MGHost::pbase).
+inline int mg_targets_per_axis(int l) { return (6 + (1 << l)) / (1 << l) + 1; }
+
+// Build the hierarchy of one composite grid; levels with at most small_nodes
+// nodes run in one CTA per problem (small_start).  On failure (no outlet node at
 // all, or a transfer weight that points at a missing node) ok = false and the
 // Poisson solve of that problem keeps the Jacobi preconditioner.
-void build_mg(const HostGrid& G, MGHost& mg);
+void build_mg(const HostGrid& G, MGHost& mg, int64_t small_nodes = MG_SMALL_NODES);
 
 }  // namespace ibg

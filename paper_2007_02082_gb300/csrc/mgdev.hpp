@@ -37,6 +37,23 @@ struct MGLevelDev {
   T* xa = nullptr;                     // iterate; the level's result ends here
   T* xb = nullptr;                     // second iterate buffer
   T* res = nullptr;                    // residual
+  // level 0 only: the composite <-> G0 transfers computed from lattice
+  // positions (no stored weights; MGHost::lat0 and following)
+  const int32_t* bco = nullptr;        // [nbricks][3] brick coordinates in the brick's level lattice
+  const int32_t* lat = nullptr;        // concatenated G0 lattices: local G0 node, -1 Dirichlet, -2 absent
+  const int64_t* lat_off = nullptr;    // [ninst] offset of each problem's lattice
+  const int32_t* lat_n = nullptr;      // [ninst][3] lattice nodes per axis
+  const int32_t* pbase = nullptr;      // [nbricks] first partial restriction sum of a brick, -1 at level 0
+  const int32_t* fbr = nullptr;        // [nfb] the bricks with pbase >= 0, in order
+  int32_t nfb = 0;
+  T* part = nullptr;                   // partial restriction sums
+  const int64_t* fbase = nullptr;      // [nbricks] first footprint entry of a brick (prolongation)
+  const int32_t* fnode = nullptr;      // [nfp] global G0 node of each footprint entry, -1 Dirichlet/none
+  int64_t nfp = 0;
+  T* fp = nullptr;                     // [nfp] the G0 values of the footprints
+  const int32_t* r0slot = nullptr;     // [n] level-0 owner slot at the G0 node, -1
+  const int32_t* r0ptr = nullptr;      // [n + 1] partial sums of each G0 node
+  const int32_t* r0idx = nullptr;
 };
 
 template <typename T>

@@ -5,7 +5,10 @@
 //                then per level: int64 nn, nd, nr, np, n[3]; double h[3];
 //                coord (int32 nn*3), dir_coord (int32 nd*3), nbr (int32 nn*6),
 //                offd (double nn*6), diag (double nn), r_ptr (int32 nn+1),
-//                r_col/r_w (nr), p_ptr (int32 rows+1), p_col/p_w (np)
+//                r_col/r_w (nr), p_ptr (int32 rows+1), p_col/p_w (np);
+//                then (hierarchy built) nbricks, meta (uint16 nslots), brick_level,
+//                brick_coord, lat_n[3], nlat, lat0, npart, pbase, r0slot, r0ptr,
+//                nidx, r0idx
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -73,6 +76,24 @@ int main(int argc, char** argv) {
     put(o, L.p_ptr);
     put(o, L.p_col);
     put(o, L.p_w);
+  }
+  // the weight-free form of the composite <-> G0 transfers
+  if (mg.ok) {
+    const int64_t nb = G.nbricks, nl = mg.lat_n[0] * mg.lat_n[1] * mg.lat_n[2];
+    std::fwrite(&nb, 8, 1, o);
+    put(o, G.meta);
+    put(o, G.brick_level);
+    put(o, G.brick_coord);
+    std::fwrite(mg.lat_n, 8, 3, o);
+    std::fwrite(&nl, 8, 1, o);
+    put(o, mg.lat0);
+    std::fwrite(&mg.npart, 8, 1, o);
+    put(o, mg.pbase);
+    put(o, mg.r0slot);
+    put(o, mg.r0ptr);
+    const int64_t ni = int64_t(mg.r0idx.size());
+    std::fwrite(&ni, 8, 1, o);
+    put(o, mg.r0idx);
   }
   std::fclose(o);
   return 0;

@@ -274,3 +274,32 @@ def test_multigrid_cuts_poisson_iterations(name):
     assert rel_l2(a.ib_fields_get("U"), b.ib_fields_get("U")) < TOL64
     a.close()
     b.close()
+
+
+NON_DEFAULT_TUNE = {"poisson_kernel": 2, "stream_chunk": 4, "mg_small": 256, "mg_sweeps": 3}
+
+
+@pytest.mark.parametrize("name", ["refined", "two_levels"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_parity_under_other_launch_choices(name, precision):
+    """Launch choices (the autotuner's space) change speed, not results: with
+    every choice off its default the fields still match the oracle at the
+    stated tolerance."""
+    from paper_2007_02082_gb300 import IBGrid
+    case, steps = CASES[name]
+    o, hist = oracle_run(name)
+    g = IBGrid(case, precision=precision, tune=NON_DEFAULT_TUNE)
+    g.ipcs_step(steps)
+    tol = TOL64 if precision == "fp64" else TOLMIX
+    for key, field in (("u", "U"), ("p", "P"), ("phi", "PHI"), ("F", "F_LAG")):
+        e = rel_l2(g.ib_fields_get(field), hist[-1][key])
+        assert e <= tol, f"{key}: rel L2 {e:.3e}"
+    g.close()
+
+
+def test_invalid_launch_choices_are_refused():
+    from paper_2007_02082_gb300 import IBError, IBGrid
+    case, _ = CASES["refined"]
+    for bad in ({"stream_chunk": 5}, {"mg_sweeps": 9}, {"poisson_kernel": 3}, {"mg_small": 10}):
+        with pytest.raises(IBError):
+            IBGrid(case, precision="mixed", tune=bad)

@@ -230,6 +230,11 @@ def test_grid_create_rejects_invalid_descriptions(lib_path):
         lambda d: setattr(d, "dt", -1.0),
         lambda d: setattr(d, "max_level", 9),
         lambda d: (setattr(d, "max_level", 1), setattr(d, "refine_band", 0)),
+        # launch choices outside their ranges
+        lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["poisson_kernel"], 3),
+        lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["stream_chunk"], 5),
+        lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["mg_small"], 10),
+        lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["mg_sweeps"], 5),
     ]
     for k, edit in enumerate(bad):
         st, h = create(edit)

@@ -81,6 +81,20 @@ def run_probe(probe, case):
         pptr = take(prow, np.int32)
         L["P"] = (pptr, take(npe, np.int32), take(npe, np.float64))
         res["lev"].append(L)
+    if ok:
+        nb = int(take(1, np.int64)[0])
+        wf = {"meta": take(ns, np.uint16), "blev": take(nb, np.int32), "bco": take(3 * nb, np.int32).reshape(nb, 3)}
+        wf["lat_n"] = tuple(int(v) for v in take(3, np.int64))
+        nl = int(take(1, np.int64)[0])
+        wf["lat0"] = take(nl, np.int32)
+        wf["npart"] = int(take(1, np.int64)[0])
+        nn0 = res["lev"][0]["nn"]
+        wf["pbase"] = take(nb, np.int32)
+        wf["r0slot"] = take(nn0, np.int32)
+        wf["r0ptr"] = take(nn0 + 1, np.int32)
+        ni = int(take(1, np.int64)[0])
+        wf["r0idx"] = take(ni, np.int32)
+        res["wf"] = wf
     return res
 
 
@@ -210,3 +224,115 @@ def test_mg_g0_is_galerkin_of_oracle_stiffness(probe, name):
     owner[slot] = True
     Pown = P0.multiply(owner[:, None]).tocsr()
     assert abs(R - Pown.T).max() == 0.0
+
+
+M_VALID, M_HANG, M_DUP, M_PDIR = 1 << 8, 1 << 9, 1 << 10, 1 << 12
+
+
+def _hat(e, sc):
+    """The G0 hat function of the Kuhn mesh at lattice offset e (level units,
+    sc per coarse cell): 1 - (max(0, e) - min(0, e)) / sc, clipped at 0."""
+    span = np.maximum(0, e.max(axis=-1)) - np.minimum(0, e.min(axis=-1))
+    return np.clip(sc - span, 0, None) / sc
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_weight_free_transfers_equal_the_stored_ones(probe, name):
+    """The device computes the composite <-> G0 transfers from lattice
+    positions instead of reading stored weights.  Rebuilt here from the
+    tables the builder gives it (the G0 lattice map, each fine brick's
+    partial sums and the G0 nodes they feed, the level-0 owner slots) with the
+    hat-function weight, both transfers equal the stored CSR exactly."""
+    res = run_probe(probe, CASES[name])
+    assert res["ok"] == 1
+    wf, L0 = res["wf"], res["lev"][0]
+    ns, nn0 = res["ns"], L0["nn"]
+    meta, blev, bco = wf["meta"].astype(np.int64), wf["blev"], wf["bco"].astype(np.int64)
+    nx, ny, nz = wf["lat_n"]
+    lat = wf["lat0"].reshape(nz, ny, nx)
+    t = np.arange(512)
+    local = np.stack([t & 7, (t >> 3) & 7, t >> 6], -1)
+    owner = ((meta & M_VALID) != 0) & ((meta & (M_HANG | M_DUP | M_PDIR)) == 0)
+    kept = ((meta & M_VALID) != 0) & ((meta & (M_HANG | M_PDIR)) == 0)
+    # restriction
+    rows, cols, vals = [], [], []
+    for j in np.nonzero(wf["r0slot"] >= 0)[0]:
+        rows.append([j]), cols.append([wf["r0slot"][j]]), vals.append([1.0])
+    fine = np.nonzero(wf["pbase"] >= 0)[0]
+    owner_brick = np.searchsorted(wf["pbase"][fine], np.arange(wf["npart"]), side="right") - 1
+    for j in range(nn0):
+        for p in wf["r0idx"][wf["r0ptr"][j]:wf["r0ptr"][j + 1]]:
+            b = fine[owner_brick[p]]
+            l = int(blev[b]); sc = 1 << l; T = (6 + sc) // sc + 1
+            k = p - wf["pbase"][b]
+            tq = np.array([k % T, (k // T) % T, k // (T * T)])
+            Q = bco[b] * 8 // sc + tq
+            assert lat[Q[2], Q[1], Q[0]] == j
+            pos = bco[b] * 8 + local
+            w = _hat(pos - sc * Q, sc)
+            sl = b * 512 + t
+            m = owner[sl] & (w > 0)
+            rows.append(np.full(m.sum(), j)), cols.append(sl[m]), vals.append(w[m])
+    Rwf = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(nn0, ns))
+    R = csr(*L0["R"], ns)
+    assert abs(Rwf - R).max() == 0.0
+    # prolongation: the hat weights of the eight corners of the G0 cell holding each kept slot
+    s = np.nonzero(kept)[0]
+    b = s // 512
+    sc = (1 << blev[b].astype(np.int64))[:, None]
+    pos = bco[b] * 8 + local[s % 512]
+    c = np.minimum(pos // sc, np.array([nx, ny, nz]) - 2)
+    rows, cols, vals = [], [], []
+    for bits in range(8):
+        corner = c + np.array([bits & 1, (bits >> 1) & 1, (bits >> 2) & 1])
+        w = _hat(pos - sc * corner, sc[:, 0])
+        id_ = lat[corner[:, 2], corner[:, 1], corner[:, 0]]
+        m = (w > 0) & (id_ >= 0)
+        assert np.all(id_[w > 0] != -2)     # a weight never falls on an absent node
+        rows.append(s[m]), cols.append(id_[m]), vals.append(w[m])
+    Pwf = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(ns, nn0))
+    P = csr(*L0["P"], nn0)
+    assert abs(Pwf - P).max() == 0.0
+
+
+KUHN_DIRS = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (0, 1, 1), (1, 0, 1), (1, 1, 1)]
+
+
+def _one_level(w):
+    """Transpose of one-level Kuhn interpolation from a coarse array of
+    w // 2 + 1 nodes per axis to the fine array of w: a coarse node at fine
+    position 2t takes the fine value there and half of each Kuhn-direction
+    neighbour."""
+    wo = w // 2 + 1
+    R = np.zeros((wo ** 3, w ** 3))
+    for tz in range(wo):
+        for ty in range(wo):
+            for tx in range(wo):
+                j = (tz * wo + ty) * wo + tx
+                for (dx, dy, dz), wt in [((0, 0, 0), 1.0)] + [((s * a, s * b, s * c), 0.5) for (a, b, c) in KUHN_DIRS
+                                                              for s in (1, -1)]:
+                    x, y, z = 2 * tx + dx, 2 * ty + dy, 2 * tz + dz
+                    if 0 <= x < w and 0 <= y < w and 0 <= z < w:
+                        R[j, (z * w + y) * w + x] += wt
+    return R
+
+
+@pytest.mark.parametrize("level", [1, 2, 3])
+def test_brick_restriction_by_levels_equals_the_hat_function(level):
+    """The device restricts a level-l brick to its G0 footprint by l one-level
+    Kuhn restrictions (8 -> 5 -> 3 -> 2 nodes per axis).  Nested P1 spaces make
+    that product the direct hat-function weight of every brick node for every
+    G0 node of the footprint."""
+    R = np.eye(512)
+    w = 8
+    for _ in range(level):
+        R = _one_level(w) @ R
+        w = w // 2 + 1
+    sc = 1 << level
+    T = (6 + sc) // sc + 1
+    assert w == T
+    t = np.arange(512)
+    pos = np.stack([t & 7, (t >> 3) & 7, t >> 6], -1)
+    for j in range(T ** 3):
+        q = np.array([j % T, (j // T) % T, j // (T * T)])
+        assert np.array_equal(R[j], _hat(pos - sc * q, sc)), (level, j)
