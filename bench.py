@@ -567,6 +567,49 @@ def run_serving(n_req, steps, seed=5):
                       "cells, 0-2 levels, nu 0.01-0.05; mixed path at the 1e-6 accuracy of the parity tests"}
 
 
+def run_batch_gaps(n_req, seed=5):
+    """How busy the GPU is inside a batched serving step: a batch of n_req
+    serving requests steps through its captured graph (CUDA events, mean of 5
+    steps), then steps once eagerly inside the NVTX range 'batch_step_eager'
+    (a launch-list capture of that range gives the sum of the kernels'
+    durations).  Returns the graph time per step and the kernel launches per
+    step; the gaps are the graph time minus the kernels' summed durations."""
+    import torch
+    import workloads as W
+    from paper_2007_02082_gb300 import IBBatch, IBGrid
+    stream = W.serving_requests(n_req=n_req, rate=None, seed=seed, steps=40, cells_lo=32 ** 3, cells_hi=96 ** 3)
+    out = {}
+    for mode in ("graph", "eager"):
+        mem = [IBGrid(c, precision="mixed", deferred=True, profile=(mode == "eager")) for _, c in stream]
+        b = IBBatch(mem)
+        b.step(2)
+        torch.cuda.synchronize()
+        k0 = b.info(0)["kernel_launches"]
+        if mode == "graph":
+            st = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push("batch_step_graph")
+            e0.record(st)
+            b.step(5)
+            e1.record(st)
+            torch.cuda.nvtx.range_pop()
+            torch.cuda.synchronize()
+            out["graph_ms_per_step"] = e0.elapsed_time(e1) / 5
+            out["launches_per_step"] = (b.info(0)["kernel_launches"] - k0) / 5
+            out["cells"] = sum(b.info(i)["n_leaf_cells"] for i in range(len(mem)))
+        else:
+            torch.cuda.nvtx.range_push("batch_step_eager")
+            b.step(1)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+            out["eager_launches_per_step"] = b.info(0)["kernel_launches"] - k0
+        b.close()
+        for m in mem:
+            m.close()
+    out["requests"] = n_req
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -600,7 +643,16 @@ def main():
                     help="requests of the serving comparison run after the timed steps (0: skip)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-steps", type=int, default=40)
+    ap.add_argument("--batch-gaps", type=int, default=0,
+                    help="only time a batch of this many serving requests (graph step, and one eager step in the "
+                         "NVTX range 'batch_step_eager' for a launch-list capture) and print the result")
     args = ap.parse_args()
+
+    if args.batch_gaps:
+        from paper_2007_02082_gb300 import load_library
+        load_library(build_if_missing=True)
+        print(json.dumps({"batch_gaps": run_batch_gaps(args.batch_gaps)}))
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
