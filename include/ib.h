@@ -67,6 +67,8 @@ enum { IB_VISCOUS_GRAD = 0, IB_VISCOUS_SYM = 1 };
 #define IB_TUNE_STREAM_CHUNK 1
 #define IB_TUNE_MG_SMALL 2
 #define IB_TUNE_MG_SWEEPS 3
+#define IB_TANGENTIAL_FREE 0
+#define IB_TANGENTIAL_ZERO 1
 #define IB_MAX_HARMONICS 8
 #define IB_MAX_LEVEL 3
 
@@ -151,6 +153,15 @@ typedef struct {
  *                       block it returns must start on a 256-byte boundary
  *                       (the streaming kernels use 16-byte vector accesses);
  *                       a misaligned block fails the call with IB_ENOMEM
+ *   port_tangential     velocity condition on outlet and pressure-inlet port
+ *                       nodes (Sec. 3.1 imposes the pressure there and says
+ *                       nothing of the tangential velocity):
+ *                       IB_TANGENTIAL_FREE (default): every velocity
+ *                       component is free (the natural condition of the
+ *                       viscous form); IB_TANGENTIAL_ZERO: the components
+ *                       tangential to the port plane are held at zero (the
+ *                       normal component carries the flow) and the IB force
+ *                       is not spread onto those nodes
  *   tune                launch choices that change speed, not the method (0 =
  *                       the library's default; the package's autotuner picks
  *                       them per workload class); a batch takes its first
@@ -189,6 +200,7 @@ typedef struct {
   void (*dev_free)(void* ptr, void* ctx);
   void* alloc_ctx;
   int32_t tune[IB_TUNE_N];
+  int32_t port_tangential;  /* IB_TANGENTIAL_FREE (default) | IB_TANGENTIAL_ZERO */
 } ib_grid_desc;
 
 /* Counts, spacing ratio and the last step's solver statistics. */

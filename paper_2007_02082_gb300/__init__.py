@@ -43,10 +43,14 @@ def load_library(build_if_missing: bool = False) -> C.CDLL:
     return _LIB
 
 
+def _port_tangential(case):
+    t = case.get("port_tangential", "free")
+    if t not in ("free", "zero"):
+        raise ValueError(f"port_tangential must be 'free' or 'zero', not {t!r}")
+    return _abi.IB_TANGENTIAL_ZERO if t == "zero" else _abi.IB_TANGENTIAL_FREE
+
+
 def _viscous_form(case):
-    if case.get("port_tangential", "free") != "free":
-        # the library leaves every velocity component of a pressure port free
-        raise ValueError("port_tangential: the library implements 'free' only")
     form = case.get("viscous", "grad")
     if form not in ("grad", "sym"):
         raise ValueError(f"viscous must be 'grad' or 'sym', not {form!r}")
@@ -149,6 +153,7 @@ class IBGrid:
             raise ValueError("poisson_pc must be 'multigrid' or 'jacobi'")
         d.poisson_pc = _abi.IB_PC_JACOBI if poisson_pc == "jacobi" else _abi.IB_PC_MULTIGRID
         d.viscous_form = _viscous_form(case)
+        d.port_tangential = _port_tangential(case)
         for k, v in (tune or {}).items():
             if k not in _abi.TUNE_INDEX:
                 raise ValueError(f"unknown launch choice {k!r}")

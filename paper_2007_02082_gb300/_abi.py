@@ -13,6 +13,7 @@ IB_FP64, IB_MIXED = 0, 1
 IB_PC_MULTIGRID, IB_PC_JACOBI = 0, 1
 IB_MAX_PORTS, IB_MAX_HARMONICS, IB_MAX_LEVEL = 8, 8, 3
 IB_TUNE_N = 4
+IB_TANGENTIAL_FREE, IB_TANGENTIAL_ZERO = 0, 1
 TUNE_INDEX = {"poisson_kernel": 0, "stream_chunk": 1, "mg_small": 2, "mg_sweeps": 3}
 
 FIELD = {
@@ -48,7 +49,7 @@ class IbGridDesc(C.Structure):
         ("viscous_form", C.c_int32),
         ("n_ports", C.c_int32), ("ports", IbPort * IB_MAX_PORTS),
         ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
-        ("tune", C.c_int32 * IB_TUNE_N),
+        ("tune", C.c_int32 * IB_TUNE_N), ("port_tangential", C.c_int32),
     ]
 
 

@@ -933,10 +933,13 @@ cudaError_t enqueue_step(Engine& E, double* u, double* un, double* p, double* pn
   fe_copy_d(3 * ns, E.ut, E.uib, st);
   if (E.Mtot) {
     ib_gather(E.ib, E.ut, ns, E.UB, E.BF, st);
-    if (E.mixed)   // FP32 iterations inside FP64 defect correction, as the field solves
+    if (E.mixed) {   // FP32 iterations inside FP64 defect correction, as the field solves
       e = ib_solve_mixed(E.ib, E.BF, E.Gf, E.ib_y64, E.ib_w32, E.ks, E.ks_host, E.os, E.os_host, E.rb, tl.ib,
                          std::max(tl.inner, tl.ib), tl.max_iter, 30, E.recs + 1, st, cc);
-    else
+      if (e == cudaSuccess)
+        e = ib_fp64_fallback(E.ib, E.BF, E.Gf, E.ibw, E.ks, E.ks_host, E.os, E.os_host, E.rb, tl.ib, tl.max_iter,
+                             E.recs + 1, st, cc);
+    } else
       e = ib_solve(E.ib, E.BF, E.Gf, E.ibw, E.ks, E.ks_host, E.rb, tl.ib, tl.max_iter, E.recs + 1, st, cc);
     if (e != cudaSuccess) return e;
     ib_spread(E.ib, E.Gf, E.uib, ns, st);
@@ -1223,6 +1226,7 @@ ib_status validate_desc(const ib_grid_desc* d) {
   if (tu[IB_TUNE_STREAM_CHUNK] != 0 && tu[IB_TUNE_STREAM_CHUNK] != 4 && tu[IB_TUNE_STREAM_CHUNK] != 8) return IB_EINVAL;
   if (tu[IB_TUNE_MG_SMALL] != 0 && (tu[IB_TUNE_MG_SMALL] < 64 || tu[IB_TUNE_MG_SMALL] > (1 << 20))) return IB_EINVAL;
   if (tu[IB_TUNE_MG_SWEEPS] < 0 || tu[IB_TUNE_MG_SWEEPS] > 4) return IB_EINVAL;
+  if (d->port_tangential != IB_TANGENTIAL_FREE && d->port_tangential != IB_TANGENTIAL_ZERO) return IB_EINVAL;
   return IB_OK;
 }
 

@@ -59,6 +59,15 @@ constexpr int SF_STRIDE = 16;   // stencil factors per instance and level
 // per-slot metadata bits (mirror of setup.hpp)
 constexpr uint16_t D_VALID = 1u << 8, D_HANG = 1u << 9, D_DUP = 1u << 10,
                    D_VDIR = 1u << 11, D_PDIR = 1u << 12, D_IFACE = 1u << 13;
+// bits 14-15: 1 + the normal axis of a port node whose tangential velocity
+// components are Dirichlet (zero); the normal component stays free
+constexpr uint16_t D_TAX = 3u << 14;
+// component c of a velocity solve (dmask holds D_VDIR) is Dirichlet at a
+// slot with metadata m through the tangential port condition
+__device__ __forceinline__ bool tan_dir(uint16_t m, uint16_t dmask, int c) {
+  const int ax = (m >> 14) & 3;
+  return (dmask & D_VDIR) && ax != 0 && c != ax - 1;
+}
 
 // One or several problem instances stored side by side: every brick belongs to
 // one instance, and the bricks of an instance are contiguous
@@ -158,6 +167,8 @@ template <typename T> __device__ __forceinline__ T k_omega(const KState& k) {
 // FP64 defect-correction loop around an inner solve (mixed precision).
 struct OState {
   double ref[3];     // max(||b||^2, ||r_0||^2) per component, set on the first pass
+  int32_t sexp[3];   // the pass's inner right-hand side is r * 2^-sexp (norm in [0.5, 1))
+  int32_t spad;
   double rel2;       // max_c ||r||^2 / ref
   double prev2;      // rel2 of the previous pass
   double tol2;

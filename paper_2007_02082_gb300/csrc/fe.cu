@@ -154,7 +154,8 @@ __global__ void k_sync(DevGrid g, T* __restrict__ y, uint16_t dmask) {
   if (e >= g.n_if) return;
   const int32_t sc = g.if_c[e], sf = g.if_f[e];
   const int32_t k0 = g.if_off[e], k1 = g.if_off[e + 1];
-  const bool zero = (g.meta[sc] & dmask) != 0;
+  const uint16_t mc = g.meta[sc];
+  const bool zero = (mc & dmask) != 0;
   T tot[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) tot[c] = y[c * g.nslots + sc] + y[c * g.nslots + sf];
@@ -165,7 +166,7 @@ __global__ void k_sync(DevGrid g, T* __restrict__ y, uint16_t dmask) {
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    const T v = zero ? T(0) : tot[c];
+    const T v = (zero || (NC == 3 && tan_dir(mc, dmask, c))) ? T(0) : tot[c];
     y[c * g.nslots + sc] = v;
     y[c * g.nslots + sf] = v;
   }

@@ -397,10 +397,16 @@ __global__ void __launch_bounds__(IBB) k_af_resid_outer(IBDev ib, const double* 
     }
     o.rel2 = rel2;
     const bool stagnated = o.iter > 0 && rel2 > 0.0625 * o.prev2 && rel2 <= 1e6 * o.tol2;
-    if (!finite || o.inner_status == 5) { o.done = 1; o.status = 5; }
+    // An FP32 inner breakdown (A_F can be too ill-conditioned for FP32 when
+    // the points are denser than the grid, Sec. 2.5) ends that pass with the
+    // correction it has built; the FP64 loop goes on while every such pass
+    // still reduces the residual by 4x.
+    const bool inner_stuck = o.inner_status == 5 && !(rel2 < 0.0625 * o.prev2);
+    if (!finite || (inner_stuck && !(rel2 <= o.tol2))) { o.done = 1; o.status = 5; }
     else if (rel2 <= o.tol2 || stagnated) o.done = 1;
     else if (o.iter >= o.max_iter) { o.done = 1; o.status = 4; }
     o.prev2 = rel2;
+    o.inner_status = 0;
     if (!o.done) { o.iter++; any = true; }
   }
   any = __syncthreads_or(any ? 1 : 0) != 0;
@@ -491,6 +497,45 @@ cudaError_t ib_solve_mixed(const IBDev& ib, const double* BF, double* G, double*
   }
   IBG_LAUNCH(k_collect_outer, gi, 128, 0, st, (const OState*)os, ib.ninst, rec);
   return cudaSuccess;
+}
+
+// Condition of the FP64 fallback: some instance's mixed force solve failed;
+// the records of those instances are cleared for the fallback's own status.
+__global__ void k_af_failed(const OState* os, int ninst, SolveRec* rec, Cond cond) {
+  KCOUNT();
+  bool any = false;
+  for (int i = threadIdx.x; i < ninst; i += blockDim.x)
+    if (os[i].status != 0) {
+      any = true;
+      rec[i * 4].status = 0;
+    }
+  any = __syncthreads_or(any ? 1 : 0) != 0;
+  if (threadIdx.x == 0) set_cond(cond, any);
+}
+
+cudaError_t ib_fp64_fallback(const IBDev& ib, const double* BF, double* G, double* work, KState* ks,
+                             KState* ks_host, const OState* os, OState* os_host, RedBuf rb, double rtol, int max_iter,
+                             SolveRec* rec, cudaStream_t st, CaptureCtx* cc) {
+  if (ib.M == 0) return cudaSuccess;
+  if (cc && cc->capturing) {
+    Cond cf;
+    cudaError_t e = cond_handle(st, 0, &cf);
+    if (e != cudaSuccess) return e;
+    IBG_LAUNCH(k_af_failed, 1, 128, 0, st, os, ib.ninst, rec, cf);
+    cudaError_t err = cudaSuccess;
+    e = cond_node(*cc, st, cf, cudaGraphCondTypeIf, [&](cudaStream_t s) {
+      err = ib_solve(ib, BF, G, work, ks, ks_host, rb, rtol, max_iter, rec, s, cc);
+    });
+    return e != cudaSuccess ? e : err;
+  }
+  cudaMemcpyAsync(os_host, os, ib.ninst * sizeof(OState), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  bool any = false;
+  for (int i = 0; i < ib.ninst; ++i) any = any || os_host[i].status != 0;
+  if (!any) return cudaSuccess;
+  IBG_LAUNCH(k_af_failed, 1, 128, 0, st, os, ib.ninst, rec, Cond());
+  return ib_solve(ib, BF, G, work, ks, ks_host, rb, rtol, max_iter, rec, st, cc);
 }
 
 void ib_spread(const IBDev& ib, const double* G, double* u, int64_t nslots, cudaStream_t st) {

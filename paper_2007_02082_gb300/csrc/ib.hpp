@@ -58,6 +58,13 @@ void ib_gather(const IBDev& ib, const double* u, int64_t nslots, const double* U
 cudaError_t ib_solve(const IBDev& ib, const double* BF, double* G, double* work /* 5*3*M */, KState* ks,
                      KState* ks_host, RedBuf rb, double rtol, int max_iter, SolveRec* rec, cudaStream_t st,
                      CaptureCtx* cc);
+// After a mixed force solve: the FP64 PCG (warm-started from G) for the
+// instances whose FP32-inner defect correction failed (A_F too
+// ill-conditioned for FP32: points denser than the grid, Sec. 2.5); the
+// others start converged and stop at once.  A device-side IF node in a graph.
+cudaError_t ib_fp64_fallback(const IBDev& ib, const double* BF, double* G, double* work, KState* ks,
+                             KState* ks_host, const OState* os, OState* os_host, RedBuf rb, double rtol, int max_iter,
+                             SolveRec* rec, cudaStream_t st, CaptureCtx* cc);
 // The same solve in mixed precision: FP64 defect correction (r = B_F - S G,
 // FP64 norms, relative tolerance rtol) around FP32 PCG iterations on the FP32
 // copy of S (relative tolerance rtol_inner).  y64: 3*M doubles; w32: 7*3*M

@@ -120,7 +120,7 @@ __global__ void k_mv_supports(MoveGrid G, int64_t M, const double* __restrict__ 
         if (m & D_VALID) {
           if (m & (D_HANG | D_DUP)) code = max(code, int32_t(MV_COARSE));
           s = int32_t(sl);
-          if (!(m & D_VDIR)) fb |= uint64_t(1) << a;
+          if (!(m & (D_VDIR | D_TAX))) fb |= uint64_t(1) << a;
         }
       }
       if (s < 0) {   // no finest-level node here: is it a vertex of an active coarser cell?

@@ -32,11 +32,14 @@ unsigned long long krylov_kcount() {
   return v;
 }
 
-__device__ __forceinline__ bool kdof(uint16_t m, uint16_t dmask) {
-  return (m & D_VALID) && !(m & (D_HANG | D_DUP | dmask));
+// Component c of a slot is an unknown (dof: owner copies only; keep: every
+// stored copy) unless it is hanging, Dirichlet by the solve's mask, or, in a
+// velocity solve, a tangential component held by the port condition.
+__device__ __forceinline__ bool kdof(uint16_t m, uint16_t dmask, int c = 0) {
+  return (m & D_VALID) && !(m & (D_HANG | D_DUP | dmask)) && !tan_dir(m, dmask, c);
 }
-__device__ __forceinline__ bool kkeep(uint16_t m, uint16_t dmask) {
-  return (m & D_VALID) && !(m & (D_HANG | dmask));
+__device__ __forceinline__ bool kkeep(uint16_t m, uint16_t dmask, int c = 0) {
+  return (m & D_VALID) && !(m & (D_HANG | dmask)) && !tan_dir(m, dmask, c);
 }
 
 // block-wide OR of a per-thread flag, result valid in every thread
@@ -55,7 +58,9 @@ __global__ void k_init_states(KState* ks, int nc, double tol2, int max_iter) {
 
 // record a finished solve of every instance (rec[i * 4], os[i]); with os set
 // (inner solve of a defect-correction loop) iterations accumulate and a
-// breakdown stops the outer loop
+// breakdown is passed to the outer loop, which decides (the field solves
+// stop; the force solve goes on while its passes still make progress) and
+// records the status
 __global__ void k_collect(const KState* ks, int nc, int ninst, SolveRec* rec, OState* os) {
   KCOUNT();
   const int i = threadIdx.x + blockIdx.x * blockDim.x;
@@ -70,7 +75,7 @@ __global__ void k_collect(const KState* ks, int nc, int ninst, SolveRec* rec, OS
     if (k.bb > 0) rel = fmax(rel, sqrt(fmax(k.rr, 0.0) / k.bb));
   }
   if (os) {
-    if (st == 5) { os[i].inner_status = 5; R.status = 5; }
+    if (st == 5) os[i].inner_status = 5;
   } else {
     R.status = st;
     R.relres = rel;
@@ -126,9 +131,9 @@ __global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict
   KCOUNT();
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
   const uint16_t m = g.meta[s];
-  const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
   T tv[3 * NC];
   for (int c = 0; c < NC; ++c) {
+    const bool dof = kdof(m, dmask, c), keep = kkeep(m, dmask, c);
     const int64_t i = c * g.nslots + s;
     T rv = keep ? T(b[i] - y[i]) : T(0);
     T zv = rv * dinv[s];
@@ -231,10 +236,10 @@ __global__ void __launch_bounds__(512) k_cg_update_vec(DevGrid g, T* __restrict_
         const uint16_t m = mm[j];
         const T qq = qe[j];
         if (m & D_VALID) xe[j] += a * pe[j];
-        const T rn = kkeep(m, dmask) ? T(re[j] - a * qq) : T(0);
+        const T rn = kkeep(m, dmask, c) ? T(re[j] - a * qq) : T(0);
         re[j] = rn;
         ze[j] = rn * de[j];
-        if (kdof(m, dmask)) {
+        if (kdof(m, dmask, c)) {
           tv[2 * c] += rn * ze[j];
           tv[2 * c + 1] += rn * rn;
         }
@@ -395,9 +400,9 @@ __global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restric
   KCOUNT();
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
   const uint16_t m = g.meta[s];
-  const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
   T tw[2 * NC];
   for (int c = 0; c < NC; ++c) {
+    const bool dof = kdof(m, dmask, c), keep = kkeep(m, dmask, c);
     const int64_t i = c * g.nslots + s;
     T rv = keep ? T(b[i] - y[i]) : T(0);
     r[i] = rv;
@@ -482,7 +487,7 @@ __global__ void __launch_bounds__(512) k_bcgv_p(DevGrid g, const T* __restrict__
       for (int j = 0; j < W; ++j) {
         const uint16_t m = mm[j];
         const T vs = ve[j];
-        const T pn = kkeep(m, dmask) ? T(re[j] + be * (pe[j] - om * vs)) : T(0);
+        const T pn = kkeep(m, dmask, c) ? T(re[j] + be * (pe[j] - om * vs)) : T(0);
         pe[j] = pn;
         he[j] = pn * de[j];
       }
@@ -527,7 +532,7 @@ __global__ void __launch_bounds__(512) k_bcgv_dot(DevGrid g, const T* __restrict
 #pragma unroll
       for (int j = 0; j < W; ++j) {
         const uint16_t m = mm[j];
-        if (!kdof(m, dmask)) continue;
+        if (!kdof(m, dmask, c)) continue;
         const T q = be[j];
         tw[2 * c] += ae[j] * q;
         if (mode == 1) tw[2 * c + 1] += q * q;
@@ -598,7 +603,7 @@ __global__ void __launch_bounds__(512) k_bcgv_s(DevGrid g, const T* __restrict__
       for (int j = 0; j < W; ++j) {
         const uint16_t m = mm[j];
         const T vs = ve[j];
-        const T sn = kkeep(m, dmask) ? T(re[j] - al * vs) : T(0);
+        const T sn = kkeep(m, dmask, c) ? T(re[j] - al * vs) : T(0);
         se[j] = sn;
         he[j] = sn * de[j];
       }
@@ -662,9 +667,9 @@ __global__ void __launch_bounds__(512) k_bcgv_xr(DevGrid g, T* __restrict__ x, T
         const uint16_t m = mm[j];
         if (m & D_VALID) xe[j] += al * pe[j] + om * he[j];
         const T ts = te[j];
-        const T rn = kkeep(m, dmask) ? T(se[j] - om * ts) : T(0);
+        const T rn = kkeep(m, dmask, c) ? T(se[j] - om * ts) : T(0);
         oe[j] = rn;
-        if (kdof(m, dmask)) {
+        if (kdof(m, dmask, c)) {
           tw[2 * c] += rn * rn;
           tw[2 * c + 1] += qe[j] * rn;
         }
@@ -699,13 +704,17 @@ __global__ void __launch_bounds__(512) k_bcgv_xr(DevGrid g, T* __restrict__ x, T
 }
 
 // ---------------------------------------------------------------- FP64 outer loop
-// r = b - y on DOF rows, written rounded to FP32 as the inner right-hand side
-// (r32) with the inner initial guess zeroed (e32); ||r||^2 in FP64, and on the
-// first pass ||b||^2 for the reference norm.  Sets the outer loop condition
-// and the condition of the inner-solve branch.  One CTA per chunk of bricks.
+// r = b - y on DOF rows in FP64 (r64), the inner initial guess zeroed (e32);
+// ||r||^2 in FP64, and on the first pass ||b||^2 for the reference norm; per
+// component the power of two that brings ||r|| into [0.5, 1) (sexp), by which
+// k_scale_residual divides r when it rounds it to FP32 as the inner
+// right-hand side, so that the FP32 iterations never see values whose
+// squares leave the FP32 range (a problem in SI units has velocity
+// residuals near 1e-20).  Sets the outer loop condition and the condition of
+// the inner-solve branch.  One CTA per chunk of bricks.
 template <int NC>
 __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double* __restrict__ b,
-                                                        const double* __restrict__ y, float* __restrict__ r32,
+                                                        const double* __restrict__ y, double* __restrict__ r64,
                                                         float* __restrict__ e32, uint16_t dmask, OState* os,
                                                         double* partials, unsigned* counter, Cond cloop,
                                                         Cond cbranch) {
@@ -733,13 +742,13 @@ __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double*
         double rv[2];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          rv[j] = kkeep(mm[j], dmask) ? be[j] - ye[j] : 0.0;
-          if (kdof(mm[j], dmask)) {
+          rv[j] = kkeep(mm[j], dmask, c) ? be[j] - ye[j] : 0.0;
+          if (kdof(mm[j], dmask, c)) {
             w[2 * c] += rv[j] * rv[j];
             if (first) w[2 * c + 1] += be[j] * be[j];
           }
         }
-        *reinterpret_cast<float2*>(r32 + i) = make_float2(float(rv[0]), float(rv[1]));
+        *reinterpret_cast<double2*>(r64 + i) = make_double2(rv[0], rv[1]);
         *reinterpret_cast<float2*>(e32 + i) = make_float2(0.f, 0.f);
       }
     }
@@ -757,6 +766,9 @@ __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double*
       if (o.iter == 0) o.ref[c] = fmax(bb, rr);
       if (!isfinite(rr)) finite = false;
       if (o.ref[c] > 0.0) rel2 = fmax(rel2, rr / o.ref[c]);
+      int ex = 0;
+      if (rr > 0.0 && isfinite(rr)) frexp(sqrt(rr), &ex);
+      o.sexp[c] = ex;
     }
     o.rel2 = rel2;
     // converged; or stagnated at the attainable FP64 accuracy (the residual
@@ -775,13 +787,26 @@ __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double*
   }
 }
 
-// x += e only for instances whose outer loop is still running
+// r32 = r64 * 2^-sexp, rounded to FP32: the scaled inner right-hand side
+// (only instances whose outer loop is still running)
+__global__ void k_scale_residual(DevGrid g, const double* __restrict__ r64, float* __restrict__ r32, int nc,
+                                 const OState* os) {
+  KCOUNT();
+  const OState& o = os[g.binst[blockIdx.x]];
+  if (o.done) return;
+  const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
+  for (int c = 0; c < nc; ++c) r32[c * g.nslots + s] = float(ldexp(r64[c * g.nslots + s], -o.sexp[c]));
+}
+
+// x += e * 2^sexp (the inner solution of the scaled right-hand side), only
+// for instances whose outer loop is still running
 __global__ void k_add_f2d_active(DevGrid g, const float* __restrict__ e, double* __restrict__ x, int nc,
                                  const OState* os) {
   KCOUNT();
-  if (os[g.binst[blockIdx.x]].done) return;
+  const OState& o = os[g.binst[blockIdx.x]];
+  if (o.done) return;
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  for (int c = 0; c < nc; ++c) x[c * g.nslots + s] += double(e[c * g.nslots + s]);
+  for (int c = 0; c < nc; ++c) x[c * g.nslots + s] += ldexp(double(e[c * g.nslots + s]), o.sexp[c]);
 }
 
 // ---------------------------------------------------------------- drivers
@@ -964,13 +989,14 @@ cudaError_t solve_enqueue(const SolveArgs& a, cudaStream_t st, CaptureCtx* cc) {
   auto residual = [&](cudaStream_t s, const Cond& cl, const Cond& cb) {
     fe_apply<double>(g, A64, a.nc, a.x, a.y64, s);
     if (a.nc == 1)
-      IBG_LAUNCH(k_residual_outer<1>, g.nschunks, DBV, 0, s, g, a.b, a.y64, a.r32, a.e32, a.dmask, a.os, a.rb.partials,
+      IBG_LAUNCH(k_residual_outer<1>, g.nschunks, DBV, 0, s, g, a.b, a.y64, a.r64, a.e32, a.dmask, a.os, a.rb.partials,
                  a.rb.counter, cl, cb);
     else
-      IBG_LAUNCH(k_residual_outer<3>, g.nschunks, DBV, 0, s, g, a.b, a.y64, a.r32, a.e32, a.dmask, a.os, a.rb.partials,
+      IBG_LAUNCH(k_residual_outer<3>, g.nschunks, DBV, 0, s, g, a.b, a.y64, a.r64, a.e32, a.dmask, a.os, a.rb.partials,
                  a.rb.counter, cl, cb);
   };
   auto correction = [&](cudaStream_t s) {
+    IBG_LAUNCH(k_scale_residual, g.nbricks, DBV, 0, s, g, (const double*)a.r64, a.r32, a.nc, (const OState*)a.os);
     cudaError_t e = inner_enqueue<float>(a, A32, a.r32, a.e32, a.w32, s, cc, a.rtol_inner, a.os);
     IBG_LAUNCH(k_collect, ib, 128, 0, s, a.ks, a.nc, g.ninst, a.rec, a.os);
     IBG_LAUNCH(k_add_f2d_active, g.nbricks, DBV, 0, s, g, a.e32, a.x, a.nc, (const OState*)a.os);

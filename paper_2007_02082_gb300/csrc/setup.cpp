@@ -305,7 +305,7 @@ ib_status build_host_grid(const ib_grid_desc& d, int64_t M, const double* X, con
       bool bnd = on_boundary(G, q);
       if (bnd) cflag[s] |= C_BOUNDARY;
       if (G.meta[s] & M_HANG) { cflag[s] |= C_HANG; continue; }
-      int inlet = -1, pinlet = -1;
+      int inlet = -1, pinlet = -1, pport = -1;
       bool outlet = false;
       for (int p = 0; p < d.n_ports && bnd; ++p) {
         const ib_port& P = d.ports[p];
@@ -314,11 +314,14 @@ ib_status build_host_grid(const ib_grid_desc& d, int64_t M, const double* X, con
         double r2 = port_r2(G, P, q);
         if (!(r2 <= P.radius * P.radius)) continue;
         if (P.kind == IB_INLET_VELOCITY) { inlet = p; break; }
+        pport = p;
         if (P.kind == IB_INLET_PRESSURE) { pinlet = p; break; }
         outlet = true;
         break;
       }
       if (outlet || pinlet >= 0) { G.meta[s] |= M_PDIR; cflag[s] |= C_PDIR; }
+      if ((outlet || pinlet >= 0) && d.port_tangential == IB_TANGENTIAL_ZERO)
+        G.meta[s] |= uint16_t((d.ports[pport].axis + 1) << 14);
       if ((bnd && !outlet && pinlet < 0) || inlet >= 0) { G.meta[s] |= M_VDIR; cflag[s] |= C_VDIR; }
       if (pinlet >= 0) {
         cflag[s] |= C_INLET;
@@ -407,7 +410,7 @@ ib_status build_host_grid(const ib_grid_desc& d, int64_t M, const double* X, con
         return IB_EINVAL;
       }
       G.ib_slot[64 * i + a] = s;
-      if (!(G.meta[s] & M_VDIR)) { G.ib_free[i] |= (uint64_t(1) << a); anyfree = true; }
+      if (!(G.meta[s] & (M_VDIR | M_TAX))) { G.ib_free[i] |= (uint64_t(1) << a); anyfree = true; }
     }
     if (!anyfree) { err = "a Lagrangian point has no free support node"; return IB_EINVAL; }
   }

@@ -31,6 +31,9 @@ enum : uint16_t {
   M_VDIR = 1u << 11,   // velocity Dirichlet (wall or inlet)
   M_PDIR = 1u << 12,   // pressure-increment Dirichlet (outlet port)
   M_IFACE = 1u << 13,  // either copy of a node stored on two levels
+  // bits 14-15: 1 + the normal axis of an outlet or pressure-inlet port node
+  // whose tangential velocity components are held at zero (0: none)
+  M_TAX = 3u << 14,
 };
 
 // Canonical node flag bits (IB_FIELD_NODE_FLAGS).

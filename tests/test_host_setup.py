@@ -187,14 +187,18 @@ def test_invalid_points_and_ports_are_rejected(probe):
     bad(lambda c: c["ports"][1].update(center=(5.0, 5.0, 4.0)), "singular")
 
 
-def test_binding_rejects_options_the_library_lacks():
-    """The oracle's opt-in tangential port condition has no library
-    counterpart: the binding refuses such a case instead of ignoring the key."""
-    from paper_2007_02082_gb300 import _abi, _viscous_form
+def test_binding_maps_the_case_options():
+    """The viscous form and the tangential port condition map to their
+    descriptor values; an unknown value is refused rather than ignored."""
+    from paper_2007_02082_gb300 import _abi, _port_tangential, _viscous_form
     assert _viscous_form({}) == _abi.IB_VISCOUS_GRAD
     assert _viscous_form({"viscous": "sym", "port_tangential": "free"}) == _abi.IB_VISCOUS_SYM
+    assert _port_tangential({}) == _abi.IB_TANGENTIAL_FREE
+    assert _port_tangential({"port_tangential": "zero"}) == _abi.IB_TANGENTIAL_ZERO
     with pytest.raises(ValueError):
-        _viscous_form({"port_tangential": "zero"})
+        _port_tangential({"port_tangential": "slip"})
+    with pytest.raises(ValueError):
+        _viscous_form({"viscous": "cubic"})
 
 
 def test_grid_create_rejects_invalid_descriptions(lib_path):
@@ -235,6 +239,7 @@ def test_grid_create_rejects_invalid_descriptions(lib_path):
         lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["stream_chunk"], 5),
         lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["mg_small"], 10),
         lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["mg_sweeps"], 5),
+        lambda d: setattr(d, "port_tangential", 2),
     ]
     for k, edit in enumerate(bad):
         st, h = create(edit)

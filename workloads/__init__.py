@@ -133,6 +133,20 @@ def cylinder_refined_64x64x256(**kw):
     return cylinder_case(**args)
 
 
+def paper_tube_sec31(p_in=1.0, M=1632, seed=31, port_tangential="zero", dt=2.5e-3, steps=400):
+    """The pressure-driven tube of Sec. 3.1 in SI units: radius 5 mm, length
+    50 mm, box -6..6 mm across (Table 1's box), the 12x12x50 grid of Table 1's
+    first row (h = 1 mm) with its 1632 wall points, blood density 1050 and
+    viscosity 0.00345 (kinematic nu = mu / rho), inlet pressure p_in Pa over a
+    zero-pressure outlet (kinematic pressure p_in / rho).  The exact flow has
+    U_max = R^2 p_in / (4 mu L) = 0.0362 m/s for p_in = 1."""
+    rho, mu = 1050.0, 0.00345
+    c = cylinder_case(n=(12, 12, 50), R=0.005, length=0.05, half_width=0.006, M=M, seed=seed, nu=mu / rho, dt=dt,
+                      steps=steps, inlet=PINLET, a0=p_in / rho, name=f"paper_tube_p{p_in:g}_12x12x50")
+    c["port_tangential"] = port_tangential
+    return c
+
+
 def cylinder_refined_slab_64x64x16(**kw):
     """A slab of the refined 64x64x256 cylinder: the same cross-section, grid
     spacing, bands, viscosity, time step and wall-point density over 16 of its
