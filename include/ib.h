@@ -166,8 +166,12 @@ typedef struct {
  *                       the library's default; the package's autotuner picks
  *                       them per workload class); a batch takes its first
  *                       member's:
- *     [IB_TUNE_POISSON_KERNEL]  FP32 Poisson stencil: 1 staged asynchronously
- *                               (default), 2 register-pipelined
+ *     [IB_TUNE_POISSON_KERNEL]  FP32 Poisson stencil: 1 staged asynchronously,
+ *                               one CTA per chunk of bricks (default), 2
+ *                               register-pipelined, 3 staged and persistent
+ *                               (a whole number of CTAs per SM walk a
+ *                               schedule of chunks written at set-up; the
+ *                               same bits as 1)
  *     [IB_TUNE_STREAM_CHUNK]    bricks per CTA of the streaming Krylov
  *                               kernels: 4 or 8 (default)
  *     [IB_TUNE_MG_SMALL]        multigrid levels with at most this many nodes

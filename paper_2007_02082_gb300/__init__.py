@@ -112,7 +112,7 @@ class IBGrid:
     def __init__(self, case, precision="fp64", stream=None, torch_alloc=True, rtol=None, max_iter=0,
                  device=0, profile=False, deferred=False, poisson_pc="multigrid", tune=None):
         """tune: launch choices (ib_grid_desc.tune), a dict with any of
-        "poisson_kernel" (1 staged, 2 register-pipelined), "stream_chunk"
+        "poisson_kernel" (1 staged, 2 register-pipelined, 3 persistent), "stream_chunk"
         (4 or 8), "mg_small" (nodes) and "mg_sweeps" (1-4); None or 0 keeps
         the library's defaults (see paper_2007_02082_gb300.tune)."""
         self.lib = load_library()

@@ -723,6 +723,41 @@ ib_status engine_build(Engine& E) {
 
   // ---- Poisson multigrid, in the precision of the inner Krylov iterations
   CK(fe_configure());
+  {
+    // schedule of the persistent staged Poisson stencil: a whole number of
+    // CTAs per SM (never more than chunks); CTA c takes the chunks c, c + G, ...
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int per_sm = fe_p7_ctas_per_sm();
+    const int nch = g.nchunks;
+    const int G = std::min<int64_t>(int64_t(nsm) * per_sm, nch);
+    std::vector<int32_t> poff(size_t(std::max(G, 0)) + 1, 0);
+    std::vector<P7Hdr> phdr;
+    phdr.reserve(size_t(E.nbricks));
+    static const int face27[6] = {12, 14, 10, 16, 4, 22};   // -x, +x, -y, +y, -z, +z
+    for (int c0 = 0; c0 < G; ++c0) {
+      for (int c = c0; c < nch; c += G)
+        for (int32_t b = cbrick[c]; b < cbrick[c + 1]; ++b) {
+          P7Hdr h{};
+          h.b = b;
+          for (int f = 0; f < 6; ++f) h.nb[f] = bnbr[27 * int64_t(b) + face27[f]];
+          h.inst = binst[b];
+          h.chunk = c;
+          h.last = b == cbrick[c + 1] - 1;
+          for (int a = 0; a < 3; ++a) h.fac[a] = sf32[size_t((binst[b] * 4 + blev[b]) * SF_STRIDE + a)];
+          phdr.push_back(h);
+        }
+      poff[c0 + 1] = int32_t(phdr.size());
+    }
+    int32_t* d_poff;
+    TRY(upload(E, &d_poff, poff));
+    P7Hdr* d_phdr;
+    TRY(upload(E, &d_phdr, phdr));
+    g.p7_ctas = G;
+    g.p7_off = d_poff;
+    g.p7_hdr = reinterpret_cast<const int4*>(d_phdr);
+  }
   if (E.mixed) TRY(mg_upload<float>(E, E.mg32));
   else TRY(mg_upload<double>(E, E.mg64));
 
@@ -1222,7 +1257,7 @@ ib_status validate_desc(const ib_grid_desc* d) {
   int64_t nf = (int64_t(d->n[0]) * d->n[1] * d->n[2]) << (3 * d->max_level);
   if (nf > (int64_t(1) << 40)) return IB_EINVAL;
   const int32_t* tu = d->tune;
-  if (tu[IB_TUNE_POISSON_KERNEL] < 0 || tu[IB_TUNE_POISSON_KERNEL] > 2) return IB_EINVAL;
+  if (tu[IB_TUNE_POISSON_KERNEL] < 0 || tu[IB_TUNE_POISSON_KERNEL] > 3) return IB_EINVAL;
   if (tu[IB_TUNE_STREAM_CHUNK] != 0 && tu[IB_TUNE_STREAM_CHUNK] != 4 && tu[IB_TUNE_STREAM_CHUNK] != 8) return IB_EINVAL;
   if (tu[IB_TUNE_MG_SMALL] != 0 && (tu[IB_TUNE_MG_SMALL] < 64 || tu[IB_TUNE_MG_SMALL] > (1 << 20))) return IB_EINVAL;
   if (tu[IB_TUNE_MG_SWEEPS] < 0 || tu[IB_TUNE_MG_SWEEPS] > 4) return IB_EINVAL;

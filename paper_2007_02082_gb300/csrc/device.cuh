@@ -34,7 +34,9 @@ inline void launch_kernel(void (*k)(KArgs...), dim3 grid, dim3 block, size_t sme
 // Every kernel starts with KCOUNT(): the wait for the previous kernel of the
 // stream (programmatic dependent launch), then the device-side count of
 // executed kernels, one relaxed atomic from thread 0 of block 0 (one counter
-// per translation unit).
+// per translation unit).  (An explicit early trigger, letting the next
+// kernel's CTAs take SMs as this one's last CTAs drain, measured slower: 56.0
+// against 51.9 ms for a batched step of 8 serving requests.)
 #define IBG_KCOUNT_DEFINE static __device__ unsigned long long g_kcount = 0ULL;
 #define KCOUNT()                                                  \
   do {                                                            \
@@ -131,9 +133,28 @@ struct DevGrid {
   const int8_t* __restrict__ nat_comp;
   const double* __restrict__ nat_w64;
   const float* __restrict__ nat_w32;
-  // launch choice: 2 selects the register-pipelined FP32 Poisson stencil
+  // launch choice: 2 selects the register-pipelined FP32 Poisson stencil, 3
+  // the persistent staged one
   int32_t poisson_kernel;
+  // schedule of the persistent Poisson stencil (launch choice 3): p7_ctas CTAs (a whole
+  // number of CTAs per SM); CTA c walks the chunks c, c + p7_ctas, ... and
+  // their bricks, one 64-byte P7Hdr per brick in that order, positions
+  // [p7_off[c], p7_off[c + 1])
+  int32_t p7_ctas;
+  const int32_t* __restrict__ p7_off;   // [p7_ctas + 1]
+  const int4* __restrict__ p7_hdr;      // [nbricks][4]
 };
+
+// Per brick of the persistent Poisson schedule: the brick, its face neighbours
+// (-x, +x, -y, +y, -z, +z; -1 where missing), its instance, its chunk and
+// whether it is the chunk's last brick, and the FP32 stencil factors
+// (V/6)/h_a^2 of its level.  Written once per grid by the host.
+struct P7Hdr {
+  int32_t b, nb[6], inst;
+  int32_t chunk, last, pad0, pad1;
+  float fac[3], pad2;
+};
+static_assert(sizeof(P7Hdr) == 64, "P7Hdr is four 16-byte pieces");
 
 // Index in the compact arrays of thread t's slot of brick b (a valid slot);
 // every lane of the warp must call it (warp ballot).
@@ -233,26 +254,21 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T* sh /* [32*NV] */) {
   }
 }
 
-// Deterministic segmented grid reduction.  Every block sums its threads' NV
-// contributions in the kernel's precision T (FP32 kernels: FP32 within the
-// block; the GB300 FP64 rate would otherwise dominate) and writes the block
-// totals in FP64; the last block to arrive sums, for every instance i, the
-// partials of blocks [seg[i], seg[i+1]) in FP64 with all its threads (thread t
-// takes the instance's relative blocks t, t + blockDim, ...; then a fixed tree)
-// and stores the totals in out[i * NV + k].  Returns true in that block only,
-// after a __syncthreads that makes out visible to all its threads.  The counter
-// is reset.  An instance's totals depend only on its own blocks and their
-// order, so they are bitwise the same alone and next to other instances.
-template <typename T, int NV>
-__device__ __forceinline__ bool grid_sum_last(T (&v)[NV], double* __restrict__ partials,
-                                              unsigned* __restrict__ counter, const int32_t* __restrict__ seg,
-                                              int nseg, double* __restrict__ out) {
-  __shared__ T sht[32 * NV];
+// The second half of grid_sum_last, for kernels that write their partials
+// themselves (partials[NV * p + k] for p over the instances' partial ranges
+// seg[i] .. seg[i+1]): every CTA arrives once; the last one sums, for every
+// instance, its partials in FP64 with all its threads (thread t takes the
+// relative partials t, t + blockDim, ...; then a fixed tree) into
+// out[i * NV + k], and returns true after a __syncthreads that makes out
+// visible to all its threads.  The counter is reset.  The caller's partial
+// writes must come from thread 0.
+template <int NV>
+__device__ __forceinline__ bool segment_sums_last(const double* __restrict__ partials, unsigned* __restrict__ counter,
+                                                  const int32_t* __restrict__ seg, int nseg,
+                                                  double* __restrict__ out) {
   __shared__ double shd[32 * NV];
   __shared__ bool last;
-  block_sum<T, NV>(v, sht);
   if (threadIdx.x == 0) {
-    for (int k = 0; k < NV; ++k) partials[(int64_t)blockIdx.x * NV + k] = double(v[k]);
     __threadfence();
     unsigned prev = atomicAdd(counter, 1u);
     last = (prev == gridDim.x - 1);
@@ -273,6 +289,26 @@ __device__ __forceinline__ bool grid_sum_last(T (&v)[NV], double* __restrict__ p
   __syncthreads();
   if (threadIdx.x == 0) *counter = 0u;
   return true;
+}
+
+// Deterministic segmented grid reduction.  Every block sums its threads' NV
+// contributions in the kernel's precision T (FP32 kernels: FP32 within the
+// block; the GB300 FP64 rate would otherwise dominate) and writes the block
+// totals in FP64; the last block to arrive sums, for every instance i, the
+// partials of blocks [seg[i], seg[i+1]) in FP64 (segment_sums_last) and
+// stores the totals in out[i * NV + k].  Returns true in that block only,
+// after a __syncthreads that makes out visible to all its threads.  The
+// counter is reset.  An instance's totals depend only on its own blocks and
+// their order, so they are bitwise the same alone and next to other instances.
+template <typename T, int NV>
+__device__ __forceinline__ bool grid_sum_last(T (&v)[NV], double* __restrict__ partials,
+                                              unsigned* __restrict__ counter, const int32_t* __restrict__ seg,
+                                              int nseg, double* __restrict__ out) {
+  __shared__ T sht[32 * NV];
+  block_sum<T, NV>(v, sht);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < NV; ++k) partials[(int64_t)blockIdx.x * NV + k] = double(v[k]);
+  return segment_sums_last<NV>(partials, counter, seg, nseg, out);
 }
 
 }  // namespace ibg

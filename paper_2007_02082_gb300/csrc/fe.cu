@@ -896,9 +896,240 @@ __global__ void __launch_bounds__(P7_THREADS, 8)
 template <int NV>
 static constexpr size_t p7_smem() { return size_t(P7_STAGES) * P7Stage<NV>::BYTES + 128; }
 
-// The staged kernel serves FP32 vectors on 16-byte boundaries (every vector of
+// ---------------------------------------------------------------- persistent Poisson stencil
+// A launch choice (IB_TUNE_POISSON_KERNEL = 3): the staged kernel above made
+// persistent.  A whole number of CTAs per SM (DevGrid::p7_ctas), each walking
+// the chunks c, c + p7_ctas, ... brick by brick through one ring of
+// shared-memory stages that runs on across chunk boundaries, so that no CTA
+// start, table set-up or ring fill sits between chunks.  The per-brick schedule
+// (brick, face neighbours, instance, chunk, stencil factors: P7Hdr, written by
+// the host once per grid) is read by 16-byte asynchronous copies
+// 2 (stages - 1) bricks ahead into a ring of headers.  Per brick the copies,
+// the four-nodes-per-thread arithmetic and the CG form's per-chunk p.q partial
+// are those of k_poisson7_staged, so both give the same bits.  Measured on the
+// two-level aorta (59 M valid slots) it is slower than one CTA per chunk (the
+// static schedule leaves SMs idle while the slowest CTAs finish; the hardware
+// scheduler balances per chunk), so the default stays k_poisson7_staged.
+// ring depth (stages) of the persistent form
+template <int NV>
+__host__ __device__ constexpr int p7p_stages() { return 4; }
+constexpr int P7_HRING = 16;      // header ring: headers run 2 (stages - 1) bricks ahead
+constexpr int P7_MAXINST = 256;   // instances whose flags a CTA keeps in shared memory
+static_assert(P7_HRING >= 2 * (p7p_stages<1>() - 1) + 2 && P7_HRING >= 2 * (p7p_stages<2>() - 1) + 2,
+              "header ring too short for its look-ahead");
+// Fill one data stage with brick h.b (every thread calls it; no commit here):
+// warp 0 issues the bulk copies, every thread its face copies.
+template <int NV>
+__device__ __forceinline__ void p7p_issue(const DevGrid& g, unsigned char* stage, uint64_t* bar, const P7Hdr& h,
+                                         const float* v0, const float* v1, const P7Copies& c) {
+  const int t = threadIdx.x;
+  float* sv = reinterpret_cast<float*>(stage);
+  if (t < 32) {
+    if (t == 0) mbar_arrive_expect_tx(bar, uint32_t(NV * 2048 + 1024));
+    __syncwarp();
+    if (t < NV) bulk_g2s(sv + t * P7Stage<NV>::VEC, (t ? v1 : v0) + (int64_t)h.b * DBV, 2048u, bar);
+    else if (t == NV) bulk_g2s(stage + P7Stage<NV>::META, g.meta + (int64_t)h.b * DBV, 1024u, bar);
+  }
+  const int na = h.nb[c.fa], nb = h.nb[1];
+  const int64_t sa = na >= 0 ? (int64_t)na * DBV + c.ha : 0;
+  const int64_t sb = nb >= 0 ? (int64_t)nb * DBV + c.hb : 0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float* src = (v ? v1 : v0);
+    float* dst = sv + v * P7Stage<NV>::VEC;
+    if (t < 64) {
+      cp_async16(dst + c.da, src + sa, na >= 0);
+      cp_async4(dst + c.db, src + sb, nb >= 0);
+    } else {
+      cp_async4(dst + c.da, src + sa, na >= 0);
+    }
+  }
+}
+
+template <bool CG>
+__global__ void __launch_bounds__(P7_THREADS, 6)
+    k_poisson7_persist(DevGrid g, const float* __restrict__ z, const float* __restrict__ pold,
+                      float* __restrict__ pnew, float* __restrict__ q, uint16_t dmask, KState* __restrict__ ks,
+                      double* __restrict__ partials, unsigned* __restrict__ counter, const uint8_t* __restrict__ on) {
+  constexpr int NV = CG ? 2 : 1;
+  constexpr int VEC = P7Stage<NV>::VEC;
+  using S = P7Stage<NV>;
+  constexpr int ST = p7p_stages<NV>();
+  extern __shared__ unsigned char p7p_dyn[];
+  __shared__ __align__(8) uint64_t full[ST];
+  __shared__ __align__(16) P7Hdr hdr[P7_HRING];
+  __shared__ uint32_t ecnt[256];        // per mask: edge counts, 4 bits each, (+x, -x, +y, -y, +z, -z)
+  __shared__ float bet[P7_MAXINST];     // beta of each instance (CG form)
+  __shared__ uint8_t act[P7_MAXINST];   // instance still iterating (and selected by `on`)
+  __shared__ float sred[32];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p7p_dyn) + 127) & ~uintptr_t(127));
+  const int t = threadIdx.x;
+  const int j0 = g.p7_off[blockIdx.x], n = g.p7_off[blockIdx.x + 1] - j0;
+  const int4* hsrc = g.p7_hdr + 4 * (int64_t)j0;
+  // until KCOUNT only data written at set-up: the mask table, the barriers,
+  // the headers of the first ST - 1 bricks
+  for (int mk = t; mk < 256; mk += P7_THREADS) {
+    uint32_t w = 0;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) w |= uint32_t(stiff_edge_count(mk, e >> 1, (e & 1) ? -1 : 1)) << (4 * e);
+    ecnt[mk] = w;
+  }
+  if (t == 0)
+    for (int k = 0; k < ST; ++k) mbar_init(&full[k]);
+  if (t < 4 * (ST - 1) && (t >> 2) < n)
+    cp_async16(reinterpret_cast<int4*>(&hdr[t >> 2]) + (t & 3), hsrc + t, true);
+  cp_async_commit();
+  KCOUNT();
+  for (int i = t; i < g.ninst; i += P7_THREADS) {
+    const bool live = !(ks && ks[i].done) && (CG || !on || on[i]);
+    act[i] = live ? 1 : 0;
+    if constexpr (CG) bet[i] = k_beta<float>(ks[i]);
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  const P7Copies cc = p7_copies(t);
+  // this thread's four nodes: x = 4 seg .. 4 seg + 3 of row (ly, lz); offsets
+  // in a vector block of the node, of the rows and planes next to it and of
+  // the x neighbours of its first and last node
+  const int seg = t & 1, ly = (t >> 1) & 7, lz = t >> 4;
+  const int o = (lz * 8 + ly) * 8 + 4 * seg;
+  const int oym = ly > 0 ? o - 8 : DBV + 128 + 8 * lz + 4 * seg, oyp = ly < 7 ? o + 8 : DBV + 192 + 8 * lz + 4 * seg;
+  const int ozm = lz > 0 ? o - 64 : DBV + 256 + 8 * ly + 4 * seg, ozp = lz < 7 ? o + 64 : DBV + 320 + 8 * ly + 4 * seg;
+  const int oxl = seg ? o - 1 : DBV + 8 * lz + ly, oxr = seg ? DBV + 64 + 8 * lz + ly : o + 4;
+  // data of brick j into stage j % ST (a plain arrival where its
+  // instance is idle), and the header of brick j + ST - 1; one copy
+  // group per call, so that the group of brick i is complete ST - 1
+  // calls later
+  auto issue = [&](int j) {
+    if (j < n) {
+      const P7Hdr& h = hdr[j % P7_HRING];
+      const int k = j % ST;
+      if (act[h.inst]) p7p_issue<NV>(g, sm + k * S::BYTES, &full[k], h, z, pold, cc);
+      else if (t == 0) mbar_arrive(&full[k]);
+      const int jh = j + ST - 1;
+      if (t < 4 && jh < n)
+        cp_async16(reinterpret_cast<int4*>(&hdr[jh % P7_HRING]) + t, hsrc + 4 * (int64_t)jh + t, true);
+    }
+    cp_async_commit();
+  };
+  for (int k = 0; k < ST - 1; ++k) issue(k);
+  float acc = 0.f;
+  for (int i = 0; i < n; ++i) {
+    const int k = i % ST;
+    const P7Hdr& h = hdr[i % P7_HRING];   // visible since the barrier of brick i - ST + 1
+    const int inst = h.inst;
+    const bool live = act[inst] != 0;
+    cp_async_wait<ST - 2>();   // this thread's face copies of brick i, the header of i + ST - 1
+    if (t == 0) mbar_wait_or_flag(&full[k], uint32_t(i / ST) & 1u, g.aerr + inst);
+    __syncthreads();   // stage k complete and visible; every thread is past brick i - 1
+    issue(i + ST - 1);
+    if (live) {
+      const float beta = CG ? bet[inst] : 0.f;
+      const unsigned char* st = sm + k * S::BYTES;
+      const float* vb = reinterpret_cast<const float*>(st);
+      // p (= z + beta p_old for the CG form): four nodes, or one value
+      auto p4 = [&](int off) -> float4 {
+        float4 a = *reinterpret_cast<const float4*>(vb + off);
+        if constexpr (CG) {
+          const float4 b = *reinterpret_cast<const float4*>(vb + off + VEC);
+          a = make_float4(float(a.x + beta * b.x), float(a.y + beta * b.y), float(a.z + beta * b.z),
+                          float(a.w + beta * b.w));
+        }
+        return a;
+      };
+      auto p1 = [&](int off) -> float {
+        if constexpr (CG) return float(vb[off] + beta * vb[off + VEC]);
+        else return vb[off];
+      };
+      const float4 pc = p4(o), ym = p4(oym), yp = p4(oyp), zm = p4(ozm), zp = p4(ozp);
+      const float xl = p1(oxl), xr = p1(oxr);
+      const uint2 mm = *reinterpret_cast<const uint2*>(st + S::META + 2 * o);
+      const uint16_t m[4] = {uint16_t(mm.x & 0xFFFFu), uint16_t(mm.x >> 16), uint16_t(mm.y & 0xFFFFu),
+                             uint16_t(mm.y >> 16)};
+      const float fx = h.fac[0], fy = h.fac[1], fz = h.fac[2];
+      const float pv[4] = {pc.x, pc.y, pc.z, pc.w};
+      const float xv[6] = {xl, pc.x, pc.y, pc.z, pc.w, xr};
+      const float ymv[4] = {ym.x, ym.y, ym.z, ym.w}, ypv[4] = {yp.x, yp.y, yp.z, yp.w};
+      const float zmv[4] = {zm.x, zm.y, zm.z, zm.w}, zpv[4] = {zp.x, zp.y, zp.z, zp.w};
+      float out[4];
+      const bool full4 = ((m[0] & m[1] & m[2] & m[3] & (D_VALID | 0xFF)) == (D_VALID | 0xFF));
+      if (__all_sync(0xffffffffu, full4)) {
+        // every node of the warp: all eight incident cells active, edge counts 6
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float w = 6.f;
+          out[j] = fx * (w * (pv[j] - xv[j + 2]) + w * (pv[j] - xv[j])) + fy * (w * (pv[j] - ypv[j]) + w * (pv[j] - ymv[j])) +
+                   fz * (w * (pv[j] - zpv[j]) + w * (pv[j] - zmv[j]));
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          out[j] = 0.f;
+          if (m[j] & D_VALID) {
+            const uint32_t w = ecnt[m[j] & 0xFF];
+            const float wxp = float(w & 15u), wxm = float((w >> 4) & 15u), wyp = float((w >> 8) & 15u);
+            const float wym = float((w >> 12) & 15u), wzp = float((w >> 16) & 15u), wzm = float((w >> 20) & 15u);
+            out[j] = fx * (wxp * (pv[j] - xv[j + 2]) + wxm * (pv[j] - xv[j])) +
+                     fy * (wyp * (pv[j] - ypv[j]) + wym * (pv[j] - ymv[j])) +
+                     fz * (wzp * (pv[j] - zpv[j]) + wzm * (pv[j] - zmv[j]));
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (m[j] & dmask) out[j] = 0.f;
+      // brick padding: the inputs are zero there, so are p and the output
+      const int64_t s = (int64_t)h.b * DBV + o;
+      *reinterpret_cast<float4*>(q + s) = make_float4(out[0], out[1], out[2], out[3]);
+      if constexpr (CG) {
+        *reinterpret_cast<float4*>(pnew + s) = pc;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc += pv[j] * out[j];
+      }
+    }
+    if constexpr (CG) {
+      if (h.last) {   // the chunk's p.q partial (zero for an idle instance)
+        float v[1] = {acc};
+        block_sum<float, 1>(v, sred);
+        if (t == 0) partials[h.chunk] = double(v[0]);
+        acc = 0.f;
+      }
+    }
+  }
+  if constexpr (CG) {
+    double* out = partials + (int64_t)g.nchunks;
+    if (!segment_sums_last<1>(partials, counter, g.cseg, g.ninst, out)) return;
+    for (int i = threadIdx.x; i < g.ninst; i += blockDim.x) {
+      KState& kk = ks[i];
+      if (kk.done) continue;
+      const double pq = out[i];
+      kk.pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) { kk.done = 1; kk.status = 5; kk.alpha = 0.0; kk.af = 0.f; continue; }
+      kk.alpha = kk.rz / pq;
+      kk.af = float(kk.alpha);
+    }
+  }
+}
+
+template <int NV>
+static constexpr size_t p7p_smem() { return size_t(p7p_stages<NV>()) * P7Stage<NV>::BYTES + 128; }
+
+// CTAs per SM of the persistent Poisson kernels (the smaller of the two forms'
+// occupancies), for the schedule the host writes per grid.
+int fe_p7_ctas_per_sm() {
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_poisson7_persist<true>, P7_THREADS, p7p_smem<2>()) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_poisson7_persist<false>, P7_THREADS, p7p_smem<1>()) !=
+          cudaSuccess)
+    return 0;
+  return std::min(a, b);
+}
+
+// The staged kernels serve FP32 vectors on 16-byte boundaries (every vector of
 // the library; the bulk and 16-byte copies need it) over the chunks of at most
-// P7_CHUNK bricks; returns false (nothing launched) otherwise.
+// P7_CHUNK bricks (the persistent one also needs its schedule and at most
+// P7_MAXINST instances); returns false (nothing launched) otherwise.
 template <typename T, bool CG>
 static bool launch_p7(const DevGrid& g, const T* z, const T* pold, T* pnew, T* q, uint16_t dmask, KState* ks,
                       double* partials, unsigned* counter, const uint8_t* on, cudaStream_t st) {
@@ -908,6 +1139,11 @@ static bool launch_p7(const DevGrid& g, const T* z, const T* pold, T* pnew, T* q
     auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     if (g.poisson_kernel == 2) return false;
     if (!a16(z) || !a16(q) || (CG && (!a16(pold) || !a16(pnew)))) return false;
+    if (g.poisson_kernel == 3 && g.p7_ctas > 0 && g.ninst <= P7_MAXINST) {
+      IBG_LAUNCH((k_poisson7_persist<CG>), g.p7_ctas, P7_THREADS, p7p_smem<CG ? 2 : 1>(), st, g, z, pold, pnew, q,
+                 dmask, ks, partials, counter, on);
+      return true;
+    }
     IBG_LAUNCH((k_poisson7_staged<CG>), g.nchunks, P7_THREADS, p7_smem<CG ? 2 : 1>(), st, g, z, pold, pnew, q, dmask,
                ks, partials, counter, on);
     return true;
@@ -1335,11 +1571,13 @@ cudaError_t fe_configure() {
   cudaError_t e = cudaFuncSetAttribute(k_apply15_mom32<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        int(cudaSharedmemCarveoutMaxShared));
   if (e != cudaSuccess) return e;
-  for (auto k : {k_poisson7_staged<true>, k_poisson7_staged<false>}) {
+  for (auto k : {k_poisson7_staged<true>, k_poisson7_staged<false>, k_poisson7_persist<true>,
+                 k_poisson7_persist<false>}) {
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   int(cudaSharedmemCarveoutMaxShared))) != cudaSuccess)
       return e;
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(p7_smem<2>()))) != cudaSuccess)
+    const size_t mx = std::max(std::max(p7_smem<1>(), p7_smem<2>()), std::max(p7p_smem<1>(), p7p_smem<2>()));
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(mx))) != cudaSuccess)
       return e;
   }
   return cudaFuncSetAttribute(k_apply15_mom32<true>, cudaFuncAttributePreferredSharedMemoryCarveout,

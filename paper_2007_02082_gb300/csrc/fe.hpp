@@ -111,6 +111,8 @@ void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st)
 void fe_momentum_coef(const DevGrid& g, const double* u, double* coef64, float* coef32, cudaStream_t st);
 // once per process and device: kernel attributes (shared-memory carveout)
 cudaError_t fe_configure();
+// CTAs per SM of the persistent staged Poisson kernels (0 if the query fails)
+int fe_p7_ctas_per_sm();
 
 // Copy canonical node values (owner slots) out / in; in also writes the fine
 // copy of every interface node.

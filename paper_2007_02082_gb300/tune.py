@@ -26,6 +26,7 @@ DEFAULTS = {"poisson_kernel": 1, "stream_chunk": 8, "mg_small": 8192, "mg_sweeps
 CANDIDATES = [
     {},
     {"poisson_kernel": 2},
+    {"poisson_kernel": 3},
     {"stream_chunk": 4},
     {"mg_small": 2048},
     {"mg_small": 32768},

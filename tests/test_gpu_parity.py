@@ -297,9 +297,27 @@ def test_parity_under_other_launch_choices(name, precision):
     g.close()
 
 
+@pytest.mark.parametrize("name", ["refined", "two_levels"])
+def test_persistent_poisson_stencil_gives_the_same_bits(name):
+    """The persistent form of the FP32 Poisson stencil (launch choice 3)
+    computes every brick and every chunk's p.q partial as the one-CTA-per-chunk
+    form does: the mixed path's fields are bitwise equal under both."""
+    from paper_2007_02082_gb300 import IBGrid
+    case, steps = CASES[name]
+    a = IBGrid(case, precision="mixed", tune={"poisson_kernel": 1})
+    b = IBGrid(case, precision="mixed", tune={"poisson_kernel": 3})
+    a.ipcs_step(steps)
+    b.ipcs_step(steps)
+    for field in ("U", "P", "PHI", "F_LAG"):
+        assert np.array_equal(a.ib_fields_get(field), b.ib_fields_get(field)), field
+    assert a.ib_grid_info()["iters_p"] == b.ib_grid_info()["iters_p"]
+    a.close()
+    b.close()
+
+
 def test_invalid_launch_choices_are_refused():
     from paper_2007_02082_gb300 import IBError, IBGrid
     case, _ = CASES["refined"]
-    for bad in ({"stream_chunk": 5}, {"mg_sweeps": 9}, {"poisson_kernel": 3}, {"mg_small": 10}):
+    for bad in ({"stream_chunk": 5}, {"mg_sweeps": 9}, {"poisson_kernel": 4}, {"mg_small": 10}):
         with pytest.raises(IBError):
             IBGrid(case, precision="mixed", tune=bad)

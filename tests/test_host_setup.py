@@ -235,7 +235,7 @@ def test_grid_create_rejects_invalid_descriptions(lib_path):
         lambda d: setattr(d, "max_level", 9),
         lambda d: (setattr(d, "max_level", 1), setattr(d, "refine_band", 0)),
         # launch choices outside their ranges
-        lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["poisson_kernel"], 3),
+        lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["poisson_kernel"], 4),
         lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["stream_chunk"], 5),
         lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["mg_small"], 10),
         lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["mg_sweeps"], 5),
