@@ -955,7 +955,7 @@ cudaError_t enqueue_step(Engine& E, double* u, double* un, double* p, double* pn
   fe_momentum_coef(dg, u, E.coef64, E.mixed ? E.coef32 : nullptr, st);
   fe_jacobi<double>(dg, OP_COEF, E.coef64, D_VDIR, E.diag64, E.dA64, st);
   if (E.mixed) fe_jacobi<float>(dg, OP_COEF, E.coef32, D_VDIR, E.diag32, E.dA32, st);
-  fe_rhs_mass_grad(dg, u, p, E.rhs3, st);
+  fe_rhs_mass_grad(dg, u, p, E.rhs3, st, E.mixed);
   fe_sync<double>(dg, 3, E.rhs3, D_VDIR, st);
   fe_copy_d(3 * ns, u, E.ut, st);
   fe_set_inlet(E.n_inlet, E.in_slot, E.in_port, E.in_shape, E.ports, E.tn, ns, E.ut, st);
@@ -986,7 +986,7 @@ cudaError_t enqueue_step(Engine& E, double* u, double* un, double* p, double* pn
   // every member, with or without a pressure inlet, so that a member's bits do
   // not depend on the batch it runs in.
   double* rhs1 = E.rhs3;   // component 0 of the RHS buffer
-  fe_rhs_div(dg, E.uib, rhs1, st);
+  fe_rhs_div(dg, E.uib, rhs1, st, E.mixed);
   fe_sync<double>(dg, 1, rhs1, D_PDIR, st);
   if (E.n_pinlet) fe_set_pinlet(E.n_pinlet, E.pin_slot, E.pin_port, E.ports, E.tn, p, E.phi, st);
   fe_expand<double>(dg, 1, E.phi, st);
@@ -995,7 +995,7 @@ cudaError_t enqueue_step(Engine& E, double* u, double* un, double* p, double* pn
   if (e != cudaSuccess) return e;
 
   // ---- Step 6: velocity correction and pressure update
-  fe_rhs_mass_grad(dg, E.uib, E.phi, E.rhs3, st);
+  fe_rhs_mass_grad(dg, E.uib, E.phi, E.rhs3, st, E.mixed);
   fe_sync<double>(dg, 3, E.rhs3, D_VDIR, st);
   fe_copy_d(3 * ns, E.uib, un, st);
   e = solve_enqueue(solve_args(E, OP_MASS, false, 3, D_VDIR, nullptr, E.dM64, nullptr, E.dM32, E.rhs3, un,

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "async.cuh"
+#include "ff.cuh"
 #include "fe.hpp"
 #include "kuhn_weights.hpp"
 
@@ -290,6 +291,203 @@ __global__ void __launch_bounds__(512) k_rhs_div(DevGrid g, const double* __rest
     o = F[4] * d[0] + F[5] * d[1] + F[6] * d[2];
   });
   out[s] = -o / g.pdt[g.binst[b]];
+}
+
+// ---------------------------------------------------------------- FP64-accurate sums in FP32 pairs
+// The mixed path's right-hand sides (Eq. 9, Eq. 12, the velocity correction)
+// and the operator products of its FP64 outer residuals, with FP64 inputs and
+// outputs and the stencil sums carried in double-FP32 (ff.cuh): every node
+// value is split once into a pair when its tile is loaded, integer weights
+// multiply exactly, and each partial sum keeps its rounding errors, so a sum
+// is accurate to about 2^-46 of the sum of its terms' magnitudes.  Where the
+// weights sum to zero (gradient, divergence, stiffness) the sums run over
+// differences to the node's own value, formed exactly (ff_diff), so the result
+// keeps that accuracy relative to itself rather than to the node values.
+// The FP64 path keeps the FP64 kernels above.
+
+// tile of ncomp FP64 components as FP32 pairs; missing neighbours read as zero
+__device__ __forceinline__ void load_tile_ff(ff* tile, const double* __restrict__ x, int64_t cs, int ncomp,
+                                             const int32_t* __restrict__ nb27) {
+  for (int t = threadIdx.x; t < TILE3; t += blockDim.x) {
+    const int hx = t % TILE, hy = (t / TILE) % TILE, hz = t / (TILE * TILE);
+    const int lx = hx - 1, ly = hy - 1, lz = hz - 1;
+    const int ox = lx < 0 ? -1 : (lx > 7 ? 1 : 0), oy = ly < 0 ? -1 : (ly > 7 ? 1 : 0);
+    const int oz = lz < 0 ? -1 : (lz > 7 ? 1 : 0);
+    const int nb = nb27[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+    const int64_t s = (int64_t)nb * DBV + (((lz & 7) * DBS + (ly & 7)) * DBS + (lx & 7));
+    for (int c = 0; c < ncomp; ++c) tile[c * TILE3 + t] = nb >= 0 ? dsplit(x[c * cs + s]) : ff{0.f, 0.f};
+  }
+}
+
+// per-CTA constants as pairs: F[3] (V/120) and dt F[4 + a] ((V/24)/h_a dt)
+__device__ __forceinline__ void ff_brick_factors(const DevGrid& g, int b, ff* sf) {
+  if (threadIdx.x < 4) {
+    const double* F = stencil_factors<double>(g, b);
+    const double dt = g.pdt[g.binst[b]];
+    sf[threadIdx.x] = dsplit(threadIdx.x == 0 ? F[3] : dt * F[3 + threadIdx.x]);
+  }
+}
+
+// out_c = M u_c - dt G_c p (k_rhs_mass_grad's operation)
+__global__ void __launch_bounds__(512) k_rhs_mass_grad_ff(DevGrid g, const double* __restrict__ u,
+                                                          const double* __restrict__ p, double* __restrict__ out) {
+  KCOUNT();
+  __shared__ ff tile[4 * TILE3];
+  __shared__ ff sf[4];
+  const int b = blockIdx.x;
+  load_tile_ff(tile, u, g.nslots, 3, g.bnbr + 27 * b);
+  load_tile_ff(tile + 3 * TILE3, p, g.nslots, 1, g.bnbr + 27 * b);
+  ff_brick_factors(g, b, sf);
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int64_t s = (int64_t)b * DBV + t;
+  const uint16_t m = g.meta[s];
+  const bool valid = (m & D_VALID) != 0;
+  double o[3] = {0, 0, 0};
+  with_mask(valid ? (m & 0xFF) : 0, [&](auto mk) {
+    if (!valid) return;
+    const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
+    ff ms[3], gp[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ms[a] = gp[a] = ff{0.f, 0.f};
+    const ff p0 = tile[3 * TILE3 + ti];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+      const int j = ti + c_toff[k];
+      const int mw = mass_weight(mk, k);
+      if (!const_mask<decltype(mk)>() || mw != 0)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ff_madd_int(ms[a], wf(mw), tile[a * TILE3 + j]);
+      if (k == 0) continue;   // the gradient weights sum to zero: differences to p at the node
+      const ff dp = ff_diff(tile[3 * TILE3 + j], p0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int gw = grad_weight(mk, k, a);
+        if (!const_mask<decltype(mk)>() || gw != 0) ff_madd_int(gp[a], wf(gw), dp);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) o[a] = ff2d(ff_add(ff_mul(ms[a], sf[0]), ff_neg(ff_mul(gp[a], sf[1 + a]))));
+  });
+  for (int a = 0; a < 3; ++a) out[a * g.nslots + s] = o[a];
+}
+
+// out = -(1/dt) (div u, q) (k_rhs_div's operation)
+__global__ void __launch_bounds__(512) k_rhs_div_ff(DevGrid g, const double* __restrict__ u,
+                                                    double* __restrict__ out) {
+  KCOUNT();
+  __shared__ ff tile[3 * TILE3];
+  __shared__ ff sf[4];
+  const int b = blockIdx.x;
+  load_tile_ff(tile, u, g.nslots, 3, g.bnbr + 27 * b);
+  if (threadIdx.x < 3) {
+    // (V/24)/h_a / dt as a pair
+    const double* F = stencil_factors<double>(g, b);
+    sf[threadIdx.x] = dsplit(F[4 + threadIdx.x] / g.pdt[g.binst[b]]);
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int64_t s = (int64_t)b * DBV + t;
+  const uint16_t m = g.meta[s];
+  const bool valid = (m & D_VALID) != 0;
+  double o = 0.0;
+  with_mask(valid ? (m & 0xFF) : 0, [&](auto mk) {
+    if (!valid) return;
+    const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
+    ff d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = ff{0.f, 0.f};
+#pragma unroll
+    for (int k = 1; k < 15; ++k) {   // zero-sum weights: differences to the node's own value
+      const int j = ti + c_toff[k];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int gw = grad_weight(mk, k, a);
+        if (!const_mask<decltype(mk)>() || gw != 0)
+          ff_madd_int(d[a], wf(gw), ff_diff(tile[a * TILE3 + j], tile[a * TILE3 + ti]));
+      }
+    }
+    o = -ff2d(ff_add(ff_add(ff_mul(d[0], sf[0]), ff_mul(d[1], sf[1])), ff_mul(d[2], sf[2])));
+  });
+  out[s] = o;
+}
+
+// Residual operator products of the mixed path, one CTA per brick:
+//   OP_MASS:    y_c = M x_c (3 components)
+//   OP_COEF:    y_c = sum_k coef_k x_c(k), FP64 coefficients (momentum, gradient form)
+//   OP_POISSON: y = K x (7-point)
+// Rows with the dmask flag give zero; brick padding is not written.
+template <int OP>
+__global__ void __launch_bounds__(512) k_apply_ff(DevGrid g, const double* __restrict__ x, double* __restrict__ y,
+                                                  const double* __restrict__ coef, uint16_t dmask) {
+  KCOUNT();
+  constexpr int NC = OP == OP_POISSON ? 1 : 3;
+  __shared__ ff tile[NC * TILE3];
+  __shared__ ff sf[4];
+  const int b = blockIdx.x;
+  load_tile_ff(tile, x, g.nslots, NC, g.bnbr + 27 * b);
+  if (threadIdx.x < 4) {
+    const double* F = stencil_factors<double>(g, b);
+    sf[threadIdx.x] = dsplit(OP == OP_POISSON ? F[threadIdx.x] : F[3]);
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int64_t s = (int64_t)b * DBV + t;
+  const uint16_t m = g.meta[s];
+  const bool act = (m & D_VALID) && !(m & dmask);
+  double o[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) o[c] = 0.0;
+  const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
+  if constexpr (OP == OP_COEF) {
+    if (act) {
+      ff acc[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[c] = ff{0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < 15; ++k) {
+        const ff ck = dsplit(coef[(int64_t)k * g.nslots + s]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ff_madd(acc[c], ck, tile[c * TILE3 + ti + c_toff[k]]);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) o[c] = ff2d(acc[c]);
+    }
+  } else {
+    with_mask(act ? (m & 0xFF) : 0, [&](auto mk) {
+      if (!act) return;
+      if constexpr (OP == OP_MASS) {
+        ff acc[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] = ff{0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 15; ++k) {
+          const int mw = mass_weight(mk, k);
+          if (!const_mask<decltype(mk)>() || mw != 0)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ff_madd_int(acc[c], wf(mw), tile[c * TILE3 + ti + c_toff[k]]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[c] = ff2d(ff_mul(acc[c], sf[0]));
+      } else {
+        // sum over the axes of (V/6)/h_a^2 (w_a+ (x - x_a+) + w_a- (x - x_a-))
+        const ff x0 = tile[ti];
+        ff tot{0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int st = a == 0 ? 1 : a == 1 ? TILE : TILE * TILE;
+          ff acc{0.f, 0.f};
+          ff_madd_int(acc, wf(stiff_edge_count(mk, a, 1)), ff_diff(x0, tile[ti + st]));
+          ff_madd_int(acc, wf(stiff_edge_count(mk, a, -1)), ff_diff(x0, tile[ti - st]));
+          tot = ff_add(tot, ff_mul(acc, sf[a]));
+        }
+        o[0] = ff2d(tot);
+      }
+    });
+  }
+  if (m & D_VALID)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) y[(int64_t)c * g.nslots + s] = o[c];
 }
 
 // Stencil slot of a neighbour offset (compile-time after unrolling).
@@ -1544,6 +1742,20 @@ void fe_apply(const DevGrid& g, const OpDesc<T>& A, int nc, const T* x, T* y, cu
   fe_sync<T>(g, nc, y, A.dmask, st);
 }
 
+void fe_apply_resid(const DevGrid& g, const OpDesc<double>& A, int nc, const double* x, double* y, cudaStream_t st) {
+  if (A.op == OP_POISSON && nc == 1)
+    IBG_LAUNCH(k_apply_ff<OP_POISSON>, g.nbricks, DBV, 0, st, g, x, y, A.coef, A.dmask);
+  else if (A.op == OP_MASS && nc == 3)
+    IBG_LAUNCH(k_apply_ff<OP_MASS>, g.nbricks, DBV, 0, st, g, x, y, A.coef, A.dmask);
+  else if (A.op == OP_COEF && nc == 3 && !g.sym)
+    IBG_LAUNCH(k_apply_ff<OP_COEF>, g.nbricks, DBV, 0, st, g, x, y, A.coef, A.dmask);
+  else {
+    fe_apply<double>(g, A, nc, x, y, st);
+    return;
+  }
+  fe_sync<double>(g, nc, y, A.dmask, st);
+}
+
 template <typename T>
 void fe_jacobi(const DevGrid& g, int op, const T* coef, uint16_t dmask, T* diag, T* dinv, cudaStream_t st) {
   if (op == OP_POISSON) IBG_LAUNCH((k_diag<T, OP_POISSON>), g.nbricks, DBV, 0, st, g, coef, diag);
@@ -1560,11 +1772,13 @@ void fe_add_d(int64_t n, const double* a, double* b, cudaStream_t st) { IBG_LAUN
 template <typename T>
 void fe_zero(int64_t n, T* a, cudaStream_t st) { IBG_LAUNCH((k_zero<T>), nblk(n), 256, 0, st, n, a); }
 
-void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double* out, cudaStream_t st) {
-  IBG_LAUNCH(k_rhs_mass_grad, g.nbricks, DBV, 0, st, g, u, p, out);
+void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double* out, cudaStream_t st, bool pairs) {
+  if (pairs) IBG_LAUNCH(k_rhs_mass_grad_ff, g.nbricks, DBV, 0, st, g, u, p, out);
+  else IBG_LAUNCH(k_rhs_mass_grad, g.nbricks, DBV, 0, st, g, u, p, out);
 }
-void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st) {
-  IBG_LAUNCH(k_rhs_div, g.nbricks, DBV, 0, st, g, u, out);
+void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st, bool pairs) {
+  if (pairs) IBG_LAUNCH(k_rhs_div_ff, g.nbricks, DBV, 0, st, g, u, out);
+  else IBG_LAUNCH(k_rhs_div, g.nbricks, DBV, 0, st, g, u, out);
 }
 cudaError_t fe_configure() {
   // four 46 KB CTAs per SM: prefer the largest shared-memory carveout

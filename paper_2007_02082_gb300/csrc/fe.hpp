@@ -60,6 +60,9 @@ cudaError_t fe_init_tables();
 // y = A x (NC components, stride nslots) followed by the interface sum.
 template <typename T>
 void fe_apply(const DevGrid& g, const OpDesc<T>& A, int nc, const T* x, T* y, cudaStream_t st);
+// the mixed path's FP64 outer-residual product y = A x, the stencil sums in
+// double-FP32 (the symmetric viscous form keeps the FP64 kernels)
+void fe_apply_resid(const DevGrid& g, const OpDesc<double>& A, int nc, const double* x, double* y, cudaStream_t st);
 
 // y = A x per level only: copies of interface nodes hold their level's part
 // (readers add the interface sums).
@@ -106,8 +109,10 @@ void fe_sync(const DevGrid& g, int nc, T* y, uint16_t dmask, cudaStream_t st);
 //   coef  = M + dt C(u) + dt nu K  as a 15-point stencil       (Eq. 9 operator)
 // with each instance's dt and nu.
 // All are local per level; callers apply fe_sync.
-void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double* out, cudaStream_t st);
-void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st);
+// right-hand sides in FP64; pairs: the mixed path's double-FP32 stencil sums
+// (FP64 inputs and outputs, sums accurate to about 2^-46)
+void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double* out, cudaStream_t st, bool pairs);
+void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st, bool pairs);
 void fe_momentum_coef(const DevGrid& g, const double* u, double* coef64, float* coef32, cudaStream_t st);
 // once per process and device: kernel attributes (shared-memory carveout)
 cudaError_t fe_configure();
