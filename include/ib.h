@@ -62,11 +62,12 @@ enum { IB_PC_MULTIGRID = 0, IB_PC_JACOBI = 1 };
 enum { IB_VISCOUS_GRAD = 0, IB_VISCOUS_SYM = 1 };
 
 #define IB_MAX_PORTS 8
-#define IB_TUNE_N 4
+#define IB_TUNE_N 5
 #define IB_TUNE_POISSON_KERNEL 0
 #define IB_TUNE_STREAM_CHUNK 1
 #define IB_TUNE_MG_SMALL 2
 #define IB_TUNE_MG_SWEEPS 3
+#define IB_TUNE_MG_PERSIST 4
 #define IB_TANGENTIAL_FREE 0
 #define IB_TANGENTIAL_ZERO 1
 #define IB_MAX_HARMONICS 8
@@ -182,6 +183,11 @@ typedef struct {
  *                               G0: 1 .. 4 (default 2); the V-cycle stays a
  *                               symmetric preconditioner, so the solution is
  *                               the same to the solver tolerance
+ *     [IB_TUNE_MG_PERSIST]      the V-cycle below the composite grid: 1 one
+ *                               launch per level step (default), 2 one
+ *                               cooperative launch with grid barriers (the
+ *                               same bits as 1; a barrier wait that runs out
+ *                               fails the step with IB_ETIMEOUT)
  *                       Invalid values fail ib_grid_create with IB_EINVAL.
  */
 typedef struct {

@@ -113,7 +113,8 @@ class IBGrid:
                  device=0, profile=False, deferred=False, poisson_pc="multigrid", tune=None):
         """tune: launch choices (ib_grid_desc.tune), a dict with any of
         "poisson_kernel" (1 staged, 2 register-pipelined, 3 persistent), "stream_chunk"
-        (4 or 8), "mg_small" (nodes) and "mg_sweeps" (1-4); None or 0 keeps
+        (4 or 8), "mg_small" (nodes), "mg_sweeps" (1-4) and "mg_persist" (1
+        separate launches, 2 one cooperative launch); None or 0 keeps
         the library's defaults (see paper_2007_02082_gb300.tune)."""
         self.lib = load_library()
         self.case = case

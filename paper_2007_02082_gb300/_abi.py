@@ -12,9 +12,9 @@ IB_VISCOUS_GRAD, IB_VISCOUS_SYM = 0, 1
 IB_FP64, IB_MIXED = 0, 1
 IB_PC_MULTIGRID, IB_PC_JACOBI = 0, 1
 IB_MAX_PORTS, IB_MAX_HARMONICS, IB_MAX_LEVEL = 8, 8, 3
-IB_TUNE_N = 4
+IB_TUNE_N = 5
 IB_TANGENTIAL_FREE, IB_TANGENTIAL_ZERO = 0, 1
-TUNE_INDEX = {"poisson_kernel": 0, "stream_chunk": 1, "mg_small": 2, "mg_sweeps": 3}
+TUNE_INDEX = {"poisson_kernel": 0, "stream_chunk": 1, "mg_small": 2, "mg_sweeps": 3, "mg_persist": 4}
 
 FIELD = {
     "U": 0, "P": 1, "PHI": 2, "U_TENT": 3, "U_IB": 4, "F_LAG": 5, "B_F": 6, "NODE_Q": 7,

@@ -121,6 +121,9 @@ struct Engine {
   double *rhs3 = nullptr, *y64 = nullptr, *r64 = nullptr, *w64 = nullptr;
   double *coef64 = nullptr, *diag64 = nullptr, *dK64 = nullptr, *dM64 = nullptr, *dA64 = nullptr;
   float *coef32 = nullptr, *diag32 = nullptr, *dK32 = nullptr, *dM32 = nullptr, *dA32 = nullptr;
+  // mixed path, gradient viscous form: the lo parts of the momentum
+  // coefficient pairs (coef32 holds the hi parts); coef64 is not held then
+  float* coeflo32 = nullptr;
   float *r32 = nullptr, *e32 = nullptr, *w32 = nullptr;
   double *X = nullptr, *dS = nullptr, *UB = nullptr, *BF = nullptr, *Gf = nullptr, *ibw = nullptr;
   double* ib_y64 = nullptr;       // mixed force solve: FP64 S G
@@ -449,6 +452,11 @@ ib_status mg_upload(Engine& E, MGDev<T>& D) {
   TRY(upload(E, &d_coff, coff));
   TRY(upload(E, &d_cinv, cinv));
   D.on = d_on; D.small = d_small; D.coarsest = d_coarsest; D.cinv_off = d_coff; D.cinv = d_cinv;
+  if (E.D[0].tune[IB_TUNE_MG_PERSIST] == 2) {
+    D.lv_ctas = mg_levels_ctas<T>();
+    if (D.lv_ctas <= 0) { E.err = "no resident grid for the cooperative multigrid kernel"; return IB_ECUDA; }
+    TRY(dalloc(E, &D.bar, 2, true));
+  }
   return IB_OK;
 }
 
@@ -705,13 +713,17 @@ ib_status engine_build(Engine& E) {
   TRY(dalloc(E, &E.y64, 3 * ns, true));
   TRY(dalloc(E, &E.r64, 3 * ns, true));
   TRY(dalloc(E, &E.w64, E.mixed ? 1 : 8 * 3 * ns, true));
-  TRY(dalloc(E, &E.coef64, 15 * ns, true));
+  // the FP64 momentum coefficients: FP64 path, and the symmetric form's FP64
+  // residual on the mixed path; otherwise the mixed path keeps FP32 pairs
+  const bool coef_pairs = E.mixed && !E.sym;
+  if (!coef_pairs) TRY(dalloc(E, &E.coef64, 15 * ns, true));
   TRY(dalloc(E, &E.diag64, ns, true));
   TRY(dalloc(E, &E.dK64, ns, true));
   TRY(dalloc(E, &E.dM64, ns, true));
   TRY(dalloc(E, &E.dA64, ns, true));
   if (E.mixed) {
     TRY(dalloc(E, &E.coef32, 15 * E.ncomp, true));   // compact layout (valid slots only)
+    if (coef_pairs) TRY(dalloc(E, &E.coeflo32, 15 * E.ncomp, true));
     TRY(dalloc(E, &E.diag32, ns, true));
     TRY(dalloc(E, &E.dK32, ns, true));
     TRY(dalloc(E, &E.dM32, ns, true));
@@ -910,6 +922,7 @@ SolveArgs solve_args(Engine& E, int op, bool bicg, int nc, uint16_t dmask, const
   a.coef64 = coef64;
   a.dinv64 = dinv64;
   a.coef32 = coef32;
+  a.coeflo32 = op == OP_COEF ? E.coeflo32 : nullptr;
   a.dinv32 = dinv32;
   a.b = b;
   a.x = x;
@@ -950,11 +963,17 @@ cudaError_t enqueue_step(Engine& E, double* u, double* un, double* p, double* pn
 
   rec_clear(E.recs, 4 * E.ninst, st);
   if ((e = cudaMemsetAsync(E.aerr, 0, E.ninst * sizeof(int32_t), st)) != cudaSuccess) return e;
+  {
+    unsigned* bar = E.mixed ? E.mg32.bar : E.mg64.bar;
+    if (bar && (e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return e;
+  }
   fe_time_advance(E.tc, E.tn, E.pdt, E.ninst, 0, nullptr, st);
   // ---- Step 1: tentative velocity (Eq. 9)
-  fe_momentum_coef(dg, u, E.coef64, E.mixed ? E.coef32 : nullptr, st);
-  fe_jacobi<double>(dg, OP_COEF, E.coef64, D_VDIR, E.diag64, E.dA64, st);
-  if (E.mixed) fe_jacobi<float>(dg, OP_COEF, E.coef32, D_VDIR, E.diag32, E.dA32, st);
+  // (the mixed path's FP64 outer loop needs no FP64 Jacobi diagonal)
+  if (E.coeflo32) fe_momentum_coef_ff(dg, u, E.coef32, E.coeflo32, st);
+  else fe_momentum_coef(dg, u, E.coef64, E.mixed ? E.coef32 : nullptr, st);
+  if (!E.mixed) fe_jacobi<double>(dg, OP_COEF, E.coef64, D_VDIR, E.diag64, E.dA64, st);
+  else fe_jacobi<float>(dg, OP_COEF, E.coef32, D_VDIR, E.diag32, E.dA32, st);
   fe_rhs_mass_grad(dg, u, p, E.rhs3, st, E.mixed);
   fe_sync<double>(dg, 3, E.rhs3, D_VDIR, st);
   fe_copy_d(3 * ns, u, E.ut, st);
@@ -1261,6 +1280,7 @@ ib_status validate_desc(const ib_grid_desc* d) {
   if (tu[IB_TUNE_STREAM_CHUNK] != 0 && tu[IB_TUNE_STREAM_CHUNK] != 4 && tu[IB_TUNE_STREAM_CHUNK] != 8) return IB_EINVAL;
   if (tu[IB_TUNE_MG_SMALL] != 0 && (tu[IB_TUNE_MG_SMALL] < 64 || tu[IB_TUNE_MG_SMALL] > (1 << 20))) return IB_EINVAL;
   if (tu[IB_TUNE_MG_SWEEPS] < 0 || tu[IB_TUNE_MG_SWEEPS] > 4) return IB_EINVAL;
+  if (tu[IB_TUNE_MG_PERSIST] < 0 || tu[IB_TUNE_MG_PERSIST] > 2) return IB_EINVAL;
   if (d->port_tangential != IB_TANGENTIAL_FREE && d->port_tangential != IB_TANGENTIAL_ZERO) return IB_EINVAL;
   return IB_OK;
 }

@@ -44,6 +44,25 @@ inline void launch_kernel(void (*k)(KArgs...), dim3 grid, dim3 block, size_t sme
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&g_kcount, 1ULL); \
   } while (0)
 
+// A cooperative launch (every CTA resident at once, for kernels whose CTAs
+// wait on one another), without programmatic dependent launch.
+template <typename... KArgs, typename... Args>
+inline void launch_cooperative(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                               Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 #define IBG_LAUNCH(k, grid, block, smem, st, ...) \
   ::ibg::launch_kernel(k, dim3(grid), dim3(block), size_t(smem), st, __VA_ARGS__)
 

@@ -414,12 +414,14 @@ __global__ void __launch_bounds__(512) k_rhs_div_ff(DevGrid g, const double* __r
 
 // Residual operator products of the mixed path, one CTA per brick:
 //   OP_MASS:    y_c = M x_c (3 components)
-//   OP_COEF:    y_c = sum_k coef_k x_c(k), FP64 coefficients (momentum, gradient form)
+//   OP_COEF:    y_c = sum_k coef_k x_c(k), the coefficients as compact FP32 pairs
+//               (k_mom_coef_ff; momentum, gradient form)
 //   OP_POISSON: y = K x (7-point)
 // Rows with the dmask flag give zero; brick padding is not written.
 template <int OP>
 __global__ void __launch_bounds__(512) k_apply_ff(DevGrid g, const double* __restrict__ x, double* __restrict__ y,
-                                                  const double* __restrict__ coef, uint16_t dmask) {
+                                                  const float* __restrict__ chi, const float* __restrict__ clo,
+                                                  uint16_t dmask) {
   KCOUNT();
   constexpr int NC = OP == OP_POISSON ? 1 : 3;
   __shared__ ff tile[NC * TILE3];
@@ -440,13 +442,14 @@ __global__ void __launch_bounds__(512) k_apply_ff(DevGrid g, const double* __res
   for (int c = 0; c < NC; ++c) o[c] = 0.0;
   const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
   if constexpr (OP == OP_COEF) {
+    const int64_t ci = compact_index(g, b, t, (m & D_VALID) != 0);
     if (act) {
       ff acc[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc[c] = ff{0.f, 0.f};
 #pragma unroll
       for (int k = 0; k < 15; ++k) {
-        const ff ck = dsplit(coef[(int64_t)k * g.nslots + s]);
+        const ff ck{chi[(int64_t)k * g.ncomp + ci], clo[(int64_t)k * g.ncomp + ci]};
 #pragma unroll
         for (int c = 0; c < 3; ++c) ff_madd(acc[c], ck, tile[c * TILE3 + ti + c_toff[k]]);
       }
@@ -502,11 +505,55 @@ __host__ __device__ constexpr int slot_of_rel(int rx, int ry, int rz) {
        : (rx == 1 && ry == 1 && rz == 1) ? 13 : (rx == -1 && ry == -1 && rz == -1) ? 14 : -1;
 }
 
+// dt C(u^n) row entries of a node: (u_h . grad phi_b, phi_a) on every
+// tetrahedron holding the node, C_nb = sum_T (|T|/20) (S_T + u_n) . grad phi_b
+// (S_T = sum of u over the tetrahedron's vertices), accumulated tetrahedron by
+// tetrahedron with every index known at compile time.  tile: 3 components of
+// u on the brick's 10^3 tile; wv = dt |T| / 20 = dt V / 120; ih = 1 / h.
+template <typename CT, typename MK>
+__device__ __forceinline__ void conv_coef(MK mask, const CT* tile, int ti, CT wv, CT ihx, CT ihy, CT ihz,
+                                          CT (&cc)[15]) {
+#pragma unroll
+  for (int k = 0; k < 15; ++k) cc[k] = CT(0);
+  const CT ih[3] = {ihx, ihy, ihz};
+  const CT un[3] = {tile[ti], tile[TILE3 + ti], tile[2 * TILE3 + ti]};
+  constexpr int KP[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (!((mask >> c) & 1)) continue;
+    const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+    const int qb = (1 - dx) | ((1 - dy) << 1) | ((1 - dz) << 2);
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      const int a1 = KP[p][0], a2 = KP[p][1], a3 = KP[p][2];
+      const int vb[4] = {0, 1 << a1, (1 << a1) | (1 << a2), 7};
+      if (qb != vb[0] && qb != vb[1] && qb != vb[2] && qb != vb[3]) continue;
+      int off[4], sl[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int rx = dx - 1 + (vb[k] & 1), ry = dy - 1 + ((vb[k] >> 1) & 1), rz = dz - 1 + ((vb[k] >> 2) & 1);
+        off[k] = (rz * TILE + ry) * TILE + rx;
+        sl[k] = slot_of_rel(rx, ry, rz);
+      }
+      CT w[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const CT* ta = tile + a * TILE3 + ti;
+        w[a] = wv * (ta[off[0]] + ta[off[1]] + ta[off[2]] + ta[off[3]] + un[a]);
+      }
+      // grad phi_0 = -e_a1/h, grad phi_1 = e_a1/h - e_a2/h, grad phi_2 = e_a2/h - e_a3/h, grad phi_3 = e_a3/h
+      const CT g1 = w[a1] * ih[a1], g2 = w[a2] * ih[a2], g3 = w[a3] * ih[a3];
+      cc[sl[0]] -= g1;
+      cc[sl[1]] += g1 - g2;
+      cc[sl[2]] += g2 - g3;
+      cc[sl[3]] += g3;
+    }
+  }
+}
+
 // coef[k] = (M + dt C(u) + dt nu K) row entries (Eq. 9 operator), k over the
-// 15 slots.  Mass and stiffness come from the mask tables; the convection
-// entries C_nb = sum_T (|T|/20) (S_T + u_n) . grad phi_b (S_T = sum of u over
-// the tetrahedron's vertices) are accumulated tetrahedron by tetrahedron with
-// every index known at compile time.
+// 15 slots.  Mass and stiffness come from the mask tables, the convection
+// entries from conv_coef.
 template <typename CT>
 __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __restrict__ u, double* __restrict__ coef,
                                                   float* __restrict__ coef32) {
@@ -555,46 +602,9 @@ __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __res
       diagK += kp + km;
     }
     cf[0] += diagK;
-    // dt C(u^n): (u_h . grad phi_b, phi_a) on every tetrahedron holding the
-    // node, accumulated in CT (FP32 on the mixed path, FP64 on the FP64 path)
+    // dt C(u^n), accumulated in CT (FP32 on the mixed path, FP64 on the FP64 path)
     CT cc[15];
-#pragma unroll
-    for (int k = 0; k < 15; ++k) cc[k] = CT(0);
-    const CT wv = CT(dt * F[3]);   // dt |T| / 20
-    const CT ih[3] = {CT(1.0 / h[0]), CT(1.0 / h[1]), CT(1.0 / h[2])};
-    const CT un[3] = {tile[ti], tile[TILE3 + ti], tile[2 * TILE3 + ti]};
-    constexpr int KP[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      if (!((mask >> c) & 1)) continue;
-      const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
-      const int qb = (1 - dx) | ((1 - dy) << 1) | ((1 - dz) << 2);
-#pragma unroll
-      for (int p = 0; p < 6; ++p) {
-        const int a1 = KP[p][0], a2 = KP[p][1], a3 = KP[p][2];
-        const int vb[4] = {0, 1 << a1, (1 << a1) | (1 << a2), 7};
-        if (qb != vb[0] && qb != vb[1] && qb != vb[2] && qb != vb[3]) continue;
-        int off[4], sl[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int rx = dx - 1 + (vb[k] & 1), ry = dy - 1 + ((vb[k] >> 1) & 1), rz = dz - 1 + ((vb[k] >> 2) & 1);
-          off[k] = (rz * TILE + ry) * TILE + rx;
-          sl[k] = slot_of_rel(rx, ry, rz);
-        }
-        CT w[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const CT* ta = tile + a * TILE3 + ti;
-          w[a] = wv * (ta[off[0]] + ta[off[1]] + ta[off[2]] + ta[off[3]] + un[a]);
-        }
-        // grad phi_0 = -e_a1/h, grad phi_1 = e_a1/h - e_a2/h, grad phi_2 = e_a2/h - e_a3/h, grad phi_3 = e_a3/h
-        const CT g1 = w[a1] * ih[a1], g2 = w[a2] * ih[a2], g3 = w[a3] * ih[a3];
-        cc[sl[0]] -= g1;
-        cc[sl[1]] += g1 - g2;
-        cc[sl[2]] += g2 - g3;
-        cc[sl[3]] += g3;
-      }
-    }
+    conv_coef<CT>(mask, tile, ti, CT(dt * F[3]), CT(1.0 / h[0]), CT(1.0 / h[1]), CT(1.0 / h[2]), cc);
 #pragma unroll
     for (int k = 0; k < 15; ++k) cf[k] += double(cc[k]);
   });
@@ -605,6 +615,91 @@ __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __res
     coef[(int64_t)k * g.nslots + s] = cf[k];
     if (coef32 && (m & D_VALID)) coef32[(int64_t)k * g.ncomp + ci] = float(cf[k]);
   }
+}
+
+// The mixed path's momentum coefficients (gradient viscous form): the mass and
+// stiffness parts as FP32 pairs from the FP64 stencil factors, the convection
+// part in FP32 (conv_coef<float>, as k_mom_coef<float>), each sum kept as a
+// pair and stored as two compact planes: hi (coef32, rounded to nearest: the
+// FP32 operator of the inner iterations) and lo (coeflo), hi + lo within
+// about 2^-46 of the coefficient, for the outer residual (k_apply_ff<OP_COEF>).
+// Per-brick constants come from one thread; no FP64 arithmetic per node.
+__global__ void __launch_bounds__(512) k_mom_coef_ff(DevGrid g, const double* __restrict__ u,
+                                                     float* __restrict__ coef32, float* __restrict__ coeflo) {
+  KCOUNT();
+  __shared__ float tile[3 * TILE3];
+  __shared__ ff sm3, sk[3];
+  __shared__ float swv, sih[3];
+  const int b = blockIdx.x;
+  {
+    const int32_t* nb27 = g.bnbr + 27 * b;
+    for (int t = threadIdx.x; t < TILE3; t += blockDim.x) {
+      const int hx = t % TILE, hy = (t / TILE) % TILE, hz = t / (TILE * TILE);
+      const int lx = hx - 1, ly = hy - 1, lz = hz - 1;
+      const int ox = lx < 0 ? -1 : (lx > 7 ? 1 : 0), oy = ly < 0 ? -1 : (ly > 7 ? 1 : 0);
+      const int oz = lz < 0 ? -1 : (lz > 7 ? 1 : 0);
+      const int nb = nb27[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+      const int64_t sl = (int64_t)nb * DBV + (((lz & 7) * DBS + (ly & 7)) * DBS + (lx & 7));
+      for (int c = 0; c < 3; ++c) {
+        float v = 0.f;
+        if (nb >= 0) {
+          const ff x = dsplit(u[c * g.nslots + sl]);
+          v = __fadd_rn(x.h, x.l);   // u rounded to FP32
+        }
+        tile[c * TILE3 + t] = v;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    const double* F = stencil_factors<double>(g, b);
+    const int inst = g.binst[b];
+    const double dt = g.pdt[inst], dnu = dt * g.pnu[inst];
+    double h[3];
+    spacing(g, b, h);
+    sm3 = dsplit(F[3]);
+    for (int a = 0; a < 3; ++a) {
+      sk[a] = dsplit(dnu * F[a]);
+      sih[a] = float(1.0 / h[a]);
+    }
+    swv = float(dt * F[3]);
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int64_t s = (int64_t)b * DBV + t;
+  const uint16_t m = g.meta[s];
+  const bool valid = (m & D_VALID) != 0;
+  ff cf[15];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) cf[k] = ff{0.f, 0.f};
+  with_mask(valid ? (m & 0xFF) : 0, [&](auto mask) {
+    if (!valid) return;
+    const int ti = tile_index(t & 7, (t >> 3) & 7, t >> 6);
+    // M + dt nu K: integer weights times the factors, as pairs
+#pragma unroll
+    for (int k = 0; k < 15; ++k) cf[k] = ff_mul(ff{wf(mass_weight(mask, k)), 0.f}, sm3);
+    ff diagK{0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const ff kp = ff_mul(ff{wf(stiff_edge_count(mask, a, 1)), 0.f}, sk[a]);
+      const ff km = ff_mul(ff{wf(stiff_edge_count(mask, a, -1)), 0.f}, sk[a]);
+      cf[1 + 2 * a] = ff_add(cf[1 + 2 * a], ff_neg(kp));
+      cf[2 + 2 * a] = ff_add(cf[2 + 2 * a], ff_neg(km));
+      diagK = ff_add(diagK, ff_add(kp, km));
+    }
+    cf[0] = ff_add(cf[0], diagK);
+    float cc[15];
+    conv_coef<float>(mask, tile, ti, swv, sih[0], sih[1], sih[2], cc);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) cf[k] = ff_add(cf[k], ff{cc[k], 0.f});
+  });
+  const int64_t ci = compact_index(g, b, t, valid);
+  if (valid)
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+      const float hi = __fadd_rn(cf[k].h, cf[k].l);
+      coef32[(int64_t)k * g.ncomp + ci] = hi;
+      coeflo[(int64_t)k * g.ncomp + ci] = __fadd_rn(__fsub_rn(cf[k].h, hi), cf[k].l);
+    }
 }
 
 // ---------------------------------------------------------------- elementwise
@@ -1742,13 +1837,15 @@ void fe_apply(const DevGrid& g, const OpDesc<T>& A, int nc, const T* x, T* y, cu
   fe_sync<T>(g, nc, y, A.dmask, st);
 }
 
-void fe_apply_resid(const DevGrid& g, const OpDesc<double>& A, int nc, const double* x, double* y, cudaStream_t st) {
+void fe_apply_resid(const DevGrid& g, const OpDesc<double>& A, int nc, const double* x, double* y,
+                    const float* chi, const float* clo, cudaStream_t st) {
+  const float* none = nullptr;
   if (A.op == OP_POISSON && nc == 1)
-    IBG_LAUNCH(k_apply_ff<OP_POISSON>, g.nbricks, DBV, 0, st, g, x, y, A.coef, A.dmask);
+    IBG_LAUNCH(k_apply_ff<OP_POISSON>, g.nbricks, DBV, 0, st, g, x, y, none, none, A.dmask);
   else if (A.op == OP_MASS && nc == 3)
-    IBG_LAUNCH(k_apply_ff<OP_MASS>, g.nbricks, DBV, 0, st, g, x, y, A.coef, A.dmask);
-  else if (A.op == OP_COEF && nc == 3 && !g.sym)
-    IBG_LAUNCH(k_apply_ff<OP_COEF>, g.nbricks, DBV, 0, st, g, x, y, A.coef, A.dmask);
+    IBG_LAUNCH(k_apply_ff<OP_MASS>, g.nbricks, DBV, 0, st, g, x, y, none, none, A.dmask);
+  else if (A.op == OP_COEF && nc == 3 && !g.sym && chi && clo)
+    IBG_LAUNCH(k_apply_ff<OP_COEF>, g.nbricks, DBV, 0, st, g, x, y, chi, clo, A.dmask);
   else {
     fe_apply<double>(g, A, nc, x, y, st);
     return;
@@ -1796,6 +1893,10 @@ cudaError_t fe_configure() {
   }
   return cudaFuncSetAttribute(k_apply15_mom32<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                               int(cudaSharedmemCarveoutMaxShared));
+}
+
+void fe_momentum_coef_ff(const DevGrid& g, const double* u, float* coef32, float* coeflo, cudaStream_t st) {
+  IBG_LAUNCH(k_mom_coef_ff, g.nbricks, DBV, 0, st, g, u, coef32, coeflo);
 }
 
 void fe_momentum_coef(const DevGrid& g, const double* u, double* coef64, float* coef32, cudaStream_t st) {

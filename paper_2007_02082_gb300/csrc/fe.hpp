@@ -62,7 +62,10 @@ template <typename T>
 void fe_apply(const DevGrid& g, const OpDesc<T>& A, int nc, const T* x, T* y, cudaStream_t st);
 // the mixed path's FP64 outer-residual product y = A x, the stencil sums in
 // double-FP32 (the symmetric viscous form keeps the FP64 kernels)
-void fe_apply_resid(const DevGrid& g, const OpDesc<double>& A, int nc, const double* x, double* y, cudaStream_t st);
+// (momentum: the coefficients as the compact FP32 pairs chi + clo of
+// fe_momentum_coef_ff; nullptr selects the FP64 kernel on A.coef)
+void fe_apply_resid(const DevGrid& g, const OpDesc<double>& A, int nc, const double* x, double* y,
+                    const float* chi, const float* clo, cudaStream_t st);
 
 // y = A x per level only: copies of interface nodes hold their level's part
 // (readers add the interface sums).
@@ -114,6 +117,9 @@ void fe_sync(const DevGrid& g, int nc, T* y, uint16_t dmask, cudaStream_t st);
 void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double* out, cudaStream_t st, bool pairs);
 void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st, bool pairs);
 void fe_momentum_coef(const DevGrid& g, const double* u, double* coef64, float* coef32, cudaStream_t st);
+// the mixed path's momentum coefficients (gradient viscous form) as compact
+// FP32 pairs: coef32 (the inner FP32 operator) + coeflo, no FP64 plane
+void fe_momentum_coef_ff(const DevGrid& g, const double* u, float* coef32, float* coeflo, cudaStream_t st);
 // once per process and device: kernel attributes (shared-memory carveout)
 cudaError_t fe_configure();
 // CTAs per SM of the persistent staged Poisson kernels (0 if the query fails)

@@ -987,7 +987,7 @@ cudaError_t solve_enqueue(const SolveArgs& a, cudaStream_t st, CaptureCtx* cc) {
   IBG_LAUNCH(k_init_outer, ib, 128, 0, st, a.os, g.ninst, a.nc, a.rtol * a.rtol, a.max_outer);
   const bool cap = cc && cc->capturing;
   auto residual = [&](cudaStream_t s, const Cond& cl, const Cond& cb) {
-    fe_apply_resid(g, A64, a.nc, a.x, a.y64, s);
+    fe_apply_resid(g, A64, a.nc, a.x, a.y64, a.coeflo32 ? a.coef32 : nullptr, a.coeflo32, s);
     if (a.nc == 1)
       IBG_LAUNCH(k_residual_outer<1>, g.nschunks, DBV, 0, s, g, a.b, a.y64, a.r64, a.e32, a.dmask, a.os, a.rb.partials,
                  a.rb.counter, cl, cb);

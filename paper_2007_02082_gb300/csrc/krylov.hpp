@@ -22,6 +22,7 @@ struct SolveArgs {
   const double* coef64 = nullptr;
   const double* dinv64 = nullptr;
   const float* coef32 = nullptr;
+  const float* coeflo32 = nullptr;   // lo parts of the momentum coefficient pairs (mixed, gradient form)
   const float* dinv32 = nullptr;
   const double* b = nullptr;   // FP64 right-hand side (DOF rows; copies equal)
   double* x = nullptr;         // FP64 solution (initial guess in, hanging-consistent)

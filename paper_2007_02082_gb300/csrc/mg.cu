@@ -15,6 +15,9 @@
 //   small levels    : one CTA per problem runs the rest of the cycle (every
 //                     level with at most MG_SMALL_NODES nodes, and the dense
 //                     coarsest solve) with block barriers between steps.
+#include <algorithm>
+
+#include "async.cuh"
 #include "fe.hpp"
 #include "mgdev.hpp"
 
@@ -161,33 +164,27 @@ __global__ void k_mg_fp_gather(MGLevelDev<T> L0, const uint8_t* __restrict__ on,
 
 // Pass 2: a CTA per chunk of up to 8 bricks; thread t takes node t of every
 // brick of the chunk, so that the bricks' constants come from shared memory
-// and all of a thread's loads of one pass are in flight together.
+// and all of a thread's loads of one pass are in flight together.  The
+// set-up data is read before the wait for the previous kernel (programmatic
+// dependent launch), so the first wave's reads overlap that kernel's tail.
 template <typename T>
 __global__ void __launch_bounds__(512, 3) k_mg_c_prolong(DevGrid g, MGLevelDev<T> L0, const T* __restrict__ zin,
                                                       T* __restrict__ zout, uint16_t dmask,
                                                       const uint8_t* __restrict__ on, const KState* ks) {
-  KCOUNT();
   constexpr int CH = 8;
   __shared__ int sl[CH], sq[CH][3], sc0[CH][3];
   __shared__ int64_t sfb[CH];
+  // set-up data (the chunk, its instance, the metadata and the bricks'
+  // lattice constants) before the wait for the previous kernel; then this
+  // thread's values and the solver flags, all in flight together
   const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const int inst = g.binst[b0];
-  if (ks[inst].done || !on[inst]) return;
   const int nb = min(b1 - b0, CH);
   const int t = threadIdx.x;
-  // this thread's nodes first: their loads overlap those of the brick constants
   uint16_t m[CH];
   T z[CH];
 #pragma unroll
-  for (int i = 0; i < CH; ++i) {
-    m[i] = 0;
-    z[i] = T(0);
-    if (i < nb) {
-      const int64_t s = (int64_t)(b0 + i) * DBV + t;
-      m[i] = g.meta[s];
-      z[i] = zin[s];
-    }
-  }
+  for (int i = 0; i < CH; ++i) m[i] = i < nb ? g.meta[(int64_t)(b0 + i) * DBV + t] : uint16_t(0);
   if (t < nb) {
     const int b = b0 + t, l = g.blev[b], sc = 1 << l;
     sl[t] = l;
@@ -199,7 +196,12 @@ __global__ void __launch_bounds__(512, 3) k_mg_c_prolong(DevGrid g, MGLevelDev<T
       sc0[t][a] = l ? min(L0.bco[3 * b + a] * DBS / sc, nla - 2) : 0;     // the footprint's first G0 node
     }
   }
+  KCOUNT();
+#pragma unroll
+  for (int i = 0; i < CH; ++i) z[i] = i < nb ? zin[(int64_t)(b0 + i) * DBV + t] : T(0);
+  const bool skip = ks[inst].done || !on[inst];
   __syncthreads();
+  if (skip) return;
   const int nl[3] = {L0.lat_n[3 * inst], L0.lat_n[3 * inst + 1], L0.lat_n[3 * inst + 2]};
   const int lt[3] = {t & 7, (t >> 3) & 7, t >> 6};
 #pragma unroll
@@ -253,6 +255,9 @@ __global__ void __launch_bounds__(512, 3) k_mg_c_prolong(DevGrid g, MGLevelDev<T
 // a coarse node at fine position 2t, the value there plus half of its 14
 // Kuhn neighbours.  An array of w nodes per axis becomes one of w / 2 + 1
 // (8 -> 5 -> 3 -> 2), each sum in a fixed order.
+constexpr int R0_GROUP = 128;                    // threads per brick of the restriction
+constexpr int R0_BRICKS = 4;                     // bricks per CTA
+constexpr int R0_THREADS = R0_GROUP * R0_BRICKS;
 __device__ __forceinline__ void kuhn_dir(int k, int& dx, int& dy, int& dz) {
   // k = 0..13: +-x, +-y, +-z, +-(1,1,0), +-(0,1,1), +-(1,0,1), +-(1,1,1)
   const int sg = (k & 1) ? -1 : 1, a = k >> 1;
@@ -261,9 +266,11 @@ __device__ __forceinline__ void kuhn_dir(int k, int& dx, int& dy, int& dz) {
   dz = sg * (a == 2 || a == 4 || a == 5 || a == 6);
 }
 
+// One level of the restriction for the 128 threads of a brick group (lt =
+// the thread's index in the group).
 template <typename T>
-__device__ __forceinline__ void restrict_one_level(const T* in, int w, T* out, int wo) {
-  for (int j = threadIdx.x; j < wo * wo * wo; j += blockDim.x) {
+__device__ __forceinline__ void restrict_one_level(const T* in, int w, T* out, int wo, int lt) {
+  for (int j = lt; j < wo * wo * wo; j += R0_GROUP) {
     const int tx = j % wo, ty = (j / wo) % wo, tz = j / (wo * wo);
     const int cx = 2 * tx, cy = 2 * ty, cz = 2 * tz;
     auto at = [&](int x, int y, int z) -> T {
@@ -281,38 +288,58 @@ __device__ __forceinline__ void restrict_one_level(const T* in, int w, T* out, i
   }
 }
 
-// One CTA of 128 threads per brick (each thread four slots, 16-byte loads),
-// so that many bricks' loads are in flight per SM.
-constexpr int R0_THREADS = 128;
+// Barrier of the 128 threads (4 warps) of brick group grp (named barrier grp + 1).
+__device__ __forceinline__ void group_sync(int grp) {
+  asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(R0_GROUP) : "memory");
+}
+
+// Four fine bricks per CTA of 512 threads, one group of 128 threads (four
+// slots per thread) per brick with its own named barrier, so that a CTA has
+// four bricks' loads in flight after two dependent rounds (the brick index,
+// then its residual values, metadata, level and instance together; the
+// instance's solver flags decide only whether the sums are written).
 template <typename T>
 __global__ void __launch_bounds__(R0_THREADS) k_mg_r0_part(DevGrid g, MGLevelDev<T> L0, const T* __restrict__ r,
                                                            const T* __restrict__ q, uint16_t dmask,
                                                            const uint8_t* __restrict__ on, const KState* ks) {
   KCOUNT();
-  __shared__ T bufa[DBV];
-  __shared__ T bufb[125];
-  const int b = L0.fbr[blockIdx.x];
-  const int inst = g.binst[b];
-  if (ks[inst].done || !on[inst]) return;
-  for (int t = threadIdx.x; t < DBV; t += R0_THREADS) {
-    const int64_t s = (int64_t)b * DBV + t;
-    const uint16_t m = g.meta[s];
-    bufa[t] = ((m & D_VALID) && !(m & (D_HANG | D_DUP | dmask))) ? T(r[s] - q[s]) : T(0);
+  __shared__ T bufa[R0_BRICKS][DBV];
+  __shared__ T bufb[R0_BRICKS][125];
+  const int grp = threadIdx.x / R0_GROUP, lt = threadIdx.x % R0_GROUP;
+  const int fi = blockIdx.x * R0_BRICKS + grp;
+  if (fi >= L0.nfb) return;   // the whole group: its barrier is its own
+  const int b = L0.fbr[fi];
+  T v[DBV / R0_GROUP];
+  uint16_t mm[DBV / R0_GROUP];
+#pragma unroll
+  for (int k = 0; k < DBV / R0_GROUP; ++k) {
+    const int64_t s = (int64_t)b * DBV + lt + k * R0_GROUP;
+    mm[k] = g.meta[s];
+    v[k] = T(r[s] - q[s]);
   }
-  __syncthreads();
-  int l = g.blev[b], w = DBS;
-  T* in = bufa;
-  T* out = bufb;
+  const int inst = g.binst[b];
+  int l = g.blev[b];
+  const int pb = L0.pbase[b];
+  if (ks[inst].done || !on[inst]) return;
+#pragma unroll
+  for (int k = 0; k < DBV / R0_GROUP; ++k) {
+    const uint16_t m = mm[k];
+    bufa[grp][lt + k * R0_GROUP] = ((m & D_VALID) && !(m & (D_HANG | D_DUP | dmask))) ? v[k] : T(0);
+  }
+  group_sync(grp);
+  int w = DBS;
+  T* in = bufa[grp];
+  T* out = bufb[grp];
   while (l > 1) {   // down to level 1 inside shared memory, alternating buffers
     const int wo = w / 2 + 1;
-    restrict_one_level(in, w, out, wo);
-    __syncthreads();
+    restrict_one_level(in, w, out, wo, lt);
+    group_sync(grp);
     T* tmp = in; in = out; out = tmp;
     w = wo;
     --l;
   }
   // the last level straight into the partial sums of the brick's G0 nodes
-  restrict_one_level(in, w, L0.part + L0.pbase[b], w / 2 + 1);
+  restrict_one_level(in, w, L0.part + pb, w / 2 + 1, lt);
 }
 
 // Pass 2, one thread per G0 node: the level-0 owner copy at its position
@@ -416,10 +443,11 @@ struct SmallArgs {
 
 constexpr int SMALL_THREADS = 1024;
 
+// The small levels and the coarsest solve of problem i, by the whole CTA
+// (block barriers between steps); each node's value is computed by one
+// thread, in an order that does not depend on the CTA's size.
 template <typename T>
-__global__ void __launch_bounds__(SMALL_THREADS) k_mg_small(SmallArgs<T> a, const KState* ks) {
-  KCOUNT();
-  const int i = blockIdx.x;
+__device__ void small_cycle(const SmallArgs<T>& a, int i, const KState* ks) {
   if (!a.on[i] || ks[i].done) return;
   const int k0 = a.small[i], K = a.coarsest[i];
   const int t = threadIdx.x, nt = blockDim.x;
@@ -488,6 +516,138 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_mg_small(SmallArgs<T> a, cons
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(SMALL_THREADS) k_mg_small(SmallArgs<T> a, const KState* ks) {
+  KCOUNT();
+  small_cycle(a, blockIdx.x, ks);
+}
+
+// ---------------------------------------------------------------- persistent coarse levels
+// Launch choice IB_TUNE_MG_PERSIST = 2: the part of the V-cycle below the
+// composite grid in one cooperative launch instead of about 25 small ones:
+// the grid-wide levels down (pre-smoothing, residual, restriction), every
+// problem's small levels and coarsest solve (CTA i takes problem i, as
+// k_mg_small does), and the grid-wide levels up (prolongation,
+// post-smoothing), with a grid barrier wherever the separate launches had a
+// kernel boundary.  Every node's arithmetic is that of the separate kernels in
+// the same order, so the result is bitwise the same.  All CTAs are resident
+// (cooperative launch); each barrier wait is bounded in wall-clock time, and
+// on expiry the CTA records ASYNC_TIMEOUT for every problem and returns.
+constexpr int LV_THREADS = 512;
+
+template <typename T>
+struct LevelsArgs {
+  SmallArgs<T> sa;       // levels (device copy), flags, coarsest inverses, omega, nu_coarse
+  int nu;                // sweeps on G0 (level 0 of the list)
+  int max_big;           // levels run grid-wide
+  int ninst;
+  unsigned* bar;         // [2]: arrivals, generation (zero at the start of a step)
+  int32_t* aerr;         // [ninst] error words of the step
+};
+
+// Barrier over all CTAs of a cooperative launch: arrivals on bar[0], release
+// by the generation word bar[1]; the last CTA to arrive resets the count and
+// advances the generation.  Returns false (after recording the timeout) when
+// the wait ran out.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int ninst, int32_t* aerr) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* gen = bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*gen == g0) {
+        if (global_ns() - t0 > ASYNC_WAIT_NS) {
+          for (int i = 0; i < ninst; ++i) atomicMax(aerr + i, ASYNC_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(LV_THREADS) k_mg_levels(LevelsArgs<T> a, const KState* ks) {
+  KCOUNT();
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, nth = int64_t(gridDim.x) * blockDim.x;
+  const SmallArgs<T>& S = a.sa;
+  const T w = S.omega;
+  // levels down: pre-smoothing, residual, restriction
+  for (int k = 0; k < a.max_big; ++k) {
+    const MGLevelDev<T>& L = S.lev[k];
+    const int nuk = k == 0 ? a.nu : S.nu;
+    T* x = L.xa;
+    T* y = L.xb;
+    int s0 = 1;
+    if (nuk >= 2) {   // the first two steps in one pass, result in xb
+      for (int64_t j = tid; j < L.n; j += nth)
+        if (level_node_on(L, j, k, S.on, S.small, ks)) L.xb[j] = level_jac2(L, w, j);
+      x = L.xb;
+      y = L.xa;
+      s0 = 2;
+    } else {
+      for (int64_t j = tid; j < L.n; j += nth)
+        if (level_node_on(L, j, k, S.on, S.small, ks)) L.xa[j] = w * L.dinv[j] * L.b[j];
+    }
+    if (!grid_barrier(a.bar, a.ninst, a.aerr)) return;
+    for (int s = s0; s < nuk; ++s) {
+      for (int64_t j = tid; j < L.n; j += nth)
+        if (level_node_on(L, j, k, S.on, S.small, ks)) y[j] = x[j] + w * L.dinv[j] * (L.b[j] - level_ax(L, x, j));
+      if (!grid_barrier(a.bar, a.ninst, a.aerr)) return;
+      T* tmp = x; x = y; y = tmp;
+    }
+    for (int64_t j = tid; j < L.n; j += nth)
+      if (level_node_on(L, j, k, S.on, S.small, ks)) L.res[j] = L.b[j] - level_ax(L, x, j);
+    if (!grid_barrier(a.bar, a.ninst, a.aerr)) return;
+    const MGLevelDev<T>& C = S.lev[k + 1];
+    for (int64_t j = tid; j < C.n; j += nth) {
+      if (!level_node_on(C, j, k, S.on, S.small, ks)) continue;
+      T v = T(0);
+      for (int e = C.rptr[j]; e < C.rptr[j + 1]; ++e) v += C.rw[e] * L.res[C.rcol[e]];
+      C.b[j] = v;
+    }
+    if (!grid_barrier(a.bar, a.ninst, a.aerr)) return;
+  }
+  // small levels and the coarsest solve, a CTA per problem
+  for (int i = blockIdx.x; i < a.ninst; i += gridDim.x) small_cycle(S, i, ks);
+  if (!grid_barrier(a.bar, a.ninst, a.aerr)) return;
+  // levels up: prolongation, post-smoothing; each level's result ends in xa
+  for (int k = a.max_big - 1; k >= 0; --k) {
+    const MGLevelDev<T>& L = S.lev[k];
+    const MGLevelDev<T>& C = S.lev[k + 1];
+    const int nuk = k == 0 ? a.nu : S.nu;
+    T* c = (nuk % 2 == 1) ? L.xa : L.xb;
+    T* y = (nuk % 2 == 0) ? L.xa : L.xb;
+    for (int64_t j = tid; j < L.n; j += nth) {
+      if (!level_node_on(L, j, k, S.on, S.small, ks)) continue;
+      T v = c[j];
+      for (int e = C.pptr[j]; e < C.pptr[j + 1]; ++e) v += C.pw[e] * C.xa[C.pcol[e]];
+      y[j] = v;
+    }
+    if (!grid_barrier(a.bar, a.ninst, a.aerr)) return;
+    T* o = (y == L.xa) ? L.xb : L.xa;
+    for (int s = 0; s < nuk; ++s) {
+      for (int64_t j = tid; j < L.n; j += nth)
+        if (level_node_on(L, j, k, S.on, S.small, ks)) o[j] = y[j] + w * L.dinv[j] * (L.b[j] - level_ax(L, y, j));
+      if (k > 0 || s + 1 < nuk)
+        if (!grid_barrier(a.bar, a.ninst, a.aerr)) return;
+      T* tmp = y; y = o; o = tmp;
+    }
+  }
+}
+
 inline unsigned nblk256(int64_t n) { return unsigned((n + 255) / 256); }
 
 }  // namespace
@@ -529,8 +689,15 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
   apply(cur);
   if (pr) pr->begin(pcls + 2, st);
   if (mg.lev[0].nfb > 0)
-    IBG_LAUNCH(k_mg_r0_part<T>, mg.lev[0].nfb, R0_THREADS, 0, st, g, mg.lev[0], r, (const T*)q, dmask, mg.on, ks);
+    IBG_LAUNCH(k_mg_r0_part<T>, (mg.lev[0].nfb + R0_BRICKS - 1) / R0_BRICKS, R0_THREADS, 0, st, g, mg.lev[0], r,
+               (const T*)q, dmask, mg.on, ks);
   IBG_LAUNCH(k_mg_r0_sum<T>, nblk256(mg.lev[0].n), 256, 0, st, mg.lev[0], r, (const T*)q, mg.on, ks);
+  SmallArgs<T> sa{mg.dlev, mg.on, mg.small, mg.coarsest, mg.cinv_off, mg.cinv, w, mg.nu_coarse};
+  if (mg.lv_ctas > 0 && mg.bar) {
+    // levels down, small levels, levels up: one cooperative launch
+    LevelsArgs<T> la{sa, nu, mg.max_big, mg.ninst, mg.bar, g.aerr};
+    launch_cooperative(k_mg_levels<T>, mg.lv_ctas, LV_THREADS, 0, st, la, ks);
+  } else {
   // large levels, down
   for (int k = 0; k < mg.max_big; ++k) {
     const MGLevelDev<T>& L = mg.lev[k];
@@ -556,7 +723,6 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
                mg.small, ks);
   }
   // small levels and the coarsest solve, one CTA per problem
-  SmallArgs<T> sa{mg.dlev, mg.on, mg.small, mg.coarsest, mg.cinv_off, mg.cinv, w, mg.nu_coarse};
   IBG_LAUNCH(k_mg_small<T>, mg.ninst, SMALL_THREADS, 0, st, sa, ks);
   // large levels, up
   for (int k = mg.max_big - 1; k >= 0; --k) {
@@ -571,6 +737,7 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
       IBG_LAUNCH(k_mg_l_sweep<T>, nb, 256, 0, st, L, k, (const T*)y, o, w, mg.on, mg.small, ks);
       T* tmp = y; y = o; o = tmp;
     }
+  }
   }
   // composite: prolongation and post-smoothing, ending in z
   T* y = (nu % 2 == 0) ? z : zs;
@@ -587,6 +754,18 @@ void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T*
     T* tmp = y; y = o; o = tmp;
   }
 }
+
+template <typename T>
+int mg_levels_ctas() {
+  int dev = 0, nsm = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mg_levels<T>, LV_THREADS, 0) != cudaSuccess)
+    return 0;
+  return nsm * std::min(per, 2);
+}
+template int mg_levels_ctas<float>();
+template int mg_levels_ctas<double>();
 
 template void mg_vcycle<float>(const DevGrid&, const MGDev<float>&, const float*, float*, float*, float*,
                                const float*, uint16_t, const KState*, cudaStream_t, Prof*, int);

@@ -71,6 +71,10 @@ struct MGDev {
   const int64_t* cinv_off = nullptr;   // [ninst] offset of the dense inverse of the coarsest level
   const T* cinv = nullptr;
   int max_big = 0;                     // max over problems of small (levels run grid-wide)
+  // launch choice: the levels below the composite grid in one cooperative
+  // launch of lv_ctas CTAs (all resident), barrier words bar[2] zeroed per step
+  int lv_ctas = 0;
+  unsigned* bar = nullptr;
   bool any = false;                    // some problem uses multigrid
 };
 
@@ -79,6 +83,11 @@ struct MGDev {
 // the composite Jacobi inverse.  Problems whose KState is done are skipped.
 // With prof set, launches are timed by class: pcls + 0 the composite stencil
 // applies, pcls + 1 the composite smoothing updates, pcls + 2 the rest.
+// CTAs of the cooperative coarse-level kernel that fit on the device at once
+// (at most two per SM), 0 if the query fails
+template <typename T>
+int mg_levels_ctas();
+
 template <typename T>
 void mg_vcycle(const DevGrid& g, const MGDev<T>& mg, const T* r, T* z, T* zs, T* q, const T* dinv, uint16_t dmask,
                const KState* ks, cudaStream_t st, Prof* prof = nullptr, int pcls = 0);

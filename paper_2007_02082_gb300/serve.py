@@ -26,14 +26,14 @@ import numpy as np
 
 from . import IBBatch, IBGrid
 
-# device bytes per stored node slot of a batch (fields, FP64 work, coefficients,
-# in mixed precision the FP32 Krylov work, and the multigrid levels and
-# transfers), per Lagrangian row (in mixed precision with the force solve's
+# device bytes per stored node slot of a batch (fields, FP64 work, coefficients:
+# FP64 planes on the FP64 path, compact FP32 pairs on the mixed path; in mixed
+# precision the FP32 Krylov work; the multigrid levels and transfers), per Lagrangian row (in mixed precision with the force solve's
 # FP64 product, FP32 work and FP32 Jacobi diagonal), per nonzero of A_F
 # (column, FP64 value, FP32 copy if mixed), per entry of the coarsest
 # multigrid level's dense inverse (in the Krylov precision), and per problem
 # (solver states, reduction buffers, small tables)
-BYTES_PER_SLOT = {"mixed": 620, "fp64": 660}
+BYTES_PER_SLOT = {"mixed": 560, "fp64": 660}
 BYTES_PER_ROW = {"mixed": 1400 + 24 + 84 + 4, "fp64": 1400}
 BYTES_PER_NNZ = {"mixed": 16, "fp64": 12}
 BYTES_PER_CINV = {"mixed": 4, "fp64": 8}

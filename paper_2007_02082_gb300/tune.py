@@ -20,7 +20,7 @@ import json
 import math
 import os
 
-DEFAULTS = {"poisson_kernel": 1, "stream_chunk": 8, "mg_small": 8192, "mg_sweeps": 2}
+DEFAULTS = {"poisson_kernel": 1, "stream_chunk": 8, "mg_small": 8192, "mg_sweeps": 2, "mg_persist": 1}
 
 # candidates, each a set of overrides of the defaults; the first is the default
 CANDIDATES = [
@@ -32,6 +32,7 @@ CANDIDATES = [
     {"mg_small": 32768},
     {"mg_sweeps": 1},
     {"mg_sweeps": 3},
+    {"mg_persist": 2},
 ]
 
 

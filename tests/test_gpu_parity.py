@@ -276,7 +276,7 @@ def test_multigrid_cuts_poisson_iterations(name):
     b.close()
 
 
-NON_DEFAULT_TUNE = {"poisson_kernel": 2, "stream_chunk": 4, "mg_small": 256, "mg_sweeps": 3}
+NON_DEFAULT_TUNE = {"poisson_kernel": 2, "stream_chunk": 4, "mg_small": 256, "mg_sweeps": 3, "mg_persist": 2}
 
 
 @pytest.mark.parametrize("name", ["refined", "two_levels"])
@@ -339,9 +339,29 @@ def test_persistent_poisson_stencil_gives_the_same_bits(name):
     b.close()
 
 
+@pytest.mark.parametrize("name", ["refined", "two_levels"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_persistent_coarse_levels_give_the_same_bits(name, precision):
+    """The V-cycle below the composite grid as one cooperative launch with
+    grid barriers (launch choice mg_persist = 2) computes every node as the
+    separate launches do: the fields are bitwise equal, with the small-level
+    threshold low enough that several levels run grid-wide."""
+    from paper_2007_02082_gb300 import IBGrid
+    case, steps = CASES[name]
+    a = IBGrid(case, precision=precision, tune={"mg_small": 256, "mg_persist": 1})
+    b = IBGrid(case, precision=precision, tune={"mg_small": 256, "mg_persist": 2})
+    a.ipcs_step(steps)
+    b.ipcs_step(steps)
+    assert a.ib_grid_info()["mg_levels"] >= 2
+    for field in ("U", "P", "PHI", "F_LAG"):
+        assert np.array_equal(a.ib_fields_get(field), b.ib_fields_get(field)), field
+    a.close()
+    b.close()
+
+
 def test_invalid_launch_choices_are_refused():
     from paper_2007_02082_gb300 import IBError, IBGrid
     case, _ = CASES["refined"]
-    for bad in ({"stream_chunk": 5}, {"mg_sweeps": 9}, {"poisson_kernel": 4}, {"mg_small": 10}):
+    for bad in ({"stream_chunk": 5}, {"mg_sweeps": 9}, {"poisson_kernel": 4}, {"mg_small": 10}, {"mg_persist": 3}):
         with pytest.raises(IBError):
             IBGrid(case, precision="mixed", tune=bad)

@@ -239,6 +239,7 @@ def test_grid_create_rejects_invalid_descriptions(lib_path):
         lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["stream_chunk"], 5),
         lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["mg_small"], 10),
         lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["mg_sweeps"], 5),
+        lambda d: d.tune.__setitem__(_abi.TUNE_INDEX["mg_persist"], 3),
         lambda d: setattr(d, "port_tangential", 2),
     ]
     for k, edit in enumerate(bad):
