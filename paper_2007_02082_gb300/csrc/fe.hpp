@@ -113,7 +113,7 @@ void fe_sync(const DevGrid& g, int nc, T* y, uint16_t dmask, cudaStream_t st);
 // with each instance's dt and nu.
 // All are local per level; callers apply fe_sync.
 // right-hand sides in FP64; pairs: the mixed path's double-FP32 stencil sums
-// (FP64 inputs and outputs, sums accurate to about 2^-46)
+// (FP64 inputs and outputs, sums accurate to about 2^-44 of their terms' magnitudes)
 void fe_rhs_mass_grad(const DevGrid& g, const double* u, const double* p, double* out, cudaStream_t st, bool pairs);
 void fe_rhs_div(const DevGrid& g, const double* u, double* out, cudaStream_t st, bool pairs);
 void fe_momentum_coef(const DevGrid& g, const double* u, double* coef64, float* coef32, cudaStream_t st);
