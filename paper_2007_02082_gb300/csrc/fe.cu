@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(512) k_rhs_div(DevGrid g, const double* __rest
 // outputs and the stencil sums carried in double-FP32 (ff.cuh): every node
 // value is split once into a pair when its tile is loaded, integer weights
 // multiply exactly, and each partial sum keeps its rounding errors, so a sum
-// is accurate to about 2^-46 of the sum of its terms' magnitudes.  Where the
+// is accurate to about 2^-44 of the sum of its terms' magnitudes.  Where the
 // weights sum to zero (gradient, divergence, stiffness) the sums run over
 // differences to the node's own value, formed exactly (ff_diff), so the result
 // keeps that accuracy relative to itself rather than to the node values.
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(512) k_mom_coef(DevGrid g, const double* __res
 // part in FP32 (conv_coef<float>, as k_mom_coef<float>), each sum kept as a
 // pair and stored as two compact planes: hi (coef32, rounded to nearest: the
 // FP32 operator of the inner iterations) and lo (coeflo), hi + lo within
-// about 2^-46 of the coefficient, for the outer residual (k_apply_ff<OP_COEF>).
+// about 2^-44 of the coefficient, for the outer residual (k_apply_ff<OP_COEF>).
 // Per-brick constants come from one thread; no FP64 arithmetic per node.
 __global__ void __launch_bounds__(512) k_mom_coef_ff(DevGrid g, const double* __restrict__ u,
                                                      float* __restrict__ coef32, float* __restrict__ coeflo) {
@@ -942,7 +942,7 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
 // ---------------------------------------------------------------- staged Poisson stencil
 // The FP32 7-point Poisson kernels of the mixed path (the CG iteration form and
 // the plain apply of the V-cycle).  One CTA of 128 threads walks a chunk of
-// bricks through a ring of P7_STAGES stages in shared memory, P7_STAGES - 1
+// bricks through a ring of stages in shared memory (p7_stages), stages - 1
 // bricks ahead of the one it computes.  Per brick a stage receives
 //   * the brick's own values of each input vector and its metadata: bulk
 //     copies of contiguous 2 KB / 1 KB runs (cp.async.bulk, the TMA unit's
@@ -960,7 +960,9 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
 // stiffness edge counts are the constant 6; elsewhere they come from a table
 // of the 256 incident-cell masks in shared memory.  The arithmetic is that of
 // k_poisson_cg, in the same order.
-constexpr int P7_STAGES = 4;
+// ring depth (stages)
+template <int NV>
+__host__ __device__ constexpr int p7_stages() { return 4; }
 constexpr int P7_THREADS = 128;
 constexpr int P7_CHUNK = 8;    // bricks per chunk at most (the chunk table's)
 template <int NV>   // input vectors: 2 (z and p_old) for the CG form, 1 for the apply
@@ -1053,6 +1055,7 @@ __global__ void __launch_bounds__(P7_THREADS, 8)
   constexpr int NV = CG ? 2 : 1;
   constexpr int VEC = P7Stage<NV>::VEC;
   using S = P7Stage<NV>;
+  constexpr int P7_STAGES = p7_stages<NV>();
   extern __shared__ unsigned char p7_dyn[];
   __shared__ __align__(8) uint64_t full[P7_STAGES];
   __shared__ int nbf[6 * P7_CHUNK];
@@ -1187,7 +1190,7 @@ __global__ void __launch_bounds__(P7_THREADS, 8)
 }
 
 template <int NV>
-static constexpr size_t p7_smem() { return size_t(P7_STAGES) * P7Stage<NV>::BYTES + 128; }
+static constexpr size_t p7_smem() { return size_t(p7_stages<NV>()) * P7Stage<NV>::BYTES + 128; }
 
 // ---------------------------------------------------------------- persistent Poisson stencil
 // A launch choice (IB_TUNE_POISSON_KERNEL = 3): the staged kernel above made
@@ -1488,19 +1491,25 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 && OP == OP_MASS && !PB) 
                                                  KState* __restrict__ ks, double* __restrict__ partials,
                                                  unsigned* __restrict__ counter, const T* __restrict__ zf,
                                                  T* __restrict__ pnew) {
-  KCOUNT();
   // FP32 with 3 components: one float4 per tile node (one 16-byte shared load
   // per stencil neighbour); otherwise one plane per component
   constexpr bool V4 = sizeof(T) == 4 && NC == 3;
+  constexpr int NBR = PB ? 1 : 8;   // bricks per CTA at most (the chunk table's)
   __shared__ __align__(16) T tile[V4 ? 4 * TILE3 : NC * TILE3];
+  __shared__ int snb[NBR * 27];     // the chunk's neighbour tables
   float4* tile4 = reinterpret_cast<float4*>(tile);
   auto tval = [&](int c, int j) -> T {
     if constexpr (V4) return reinterpret_cast<const T*>(tile4 + j)[c];
     else return tile[c * TILE3 + j];
   };
+  // set-up data before the wait for the previous kernel: the chunk, its
+  // instance and its bricks' neighbour tables (so that no halo load waits on
+  // a neighbour-table load)
   const int b0 = PB ? int(blockIdx.x) : g.cbrick[blockIdx.x];
   const int b1 = PB ? b0 + 1 : g.cbrick[blockIdx.x + 1];
   const int inst = g.binst[b0];
+  for (int e = threadIdx.x; e < (b1 - b0) * 27; e += blockDim.x) snb[e] = g.bnbr[27 * b0 + e];
+  KCOUNT();
   bool skip = false;
   T beta[NC];
 #pragma unroll
@@ -1532,7 +1541,7 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 && OP == OP_MASS && !PB) 
         vo[c] = FUSEP ? T(zf[i] + beta[c] * x[i]) : x[i];
       }
       if (t < HALO15) {
-        const int nb = g.bnbr[27 * bb + hnb];
+        const int nb = snb[27 * (bb - b0) + hnb];
         const int64_t hs = (int64_t)nb * DBV + hli;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
@@ -1541,6 +1550,7 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 && OP == OP_MASS && !PB) 
         }
       }
     };
+    __syncthreads();   // snb complete
     fetch(b0);
     uint16_t mn = g.meta[(int64_t)b0 * DBV + t];
     for (int bb = b0; bb < b1; ++bb) {

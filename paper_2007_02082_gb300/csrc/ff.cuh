@@ -29,10 +29,11 @@ __device__ __forceinline__ ff two_sum(float a, float b) {
 }
 
 // x as hi + lo: hi = x with its mantissa cut to 24 bits (exact), lo = the
-// remaining 29 bits rounded to FP32, so hi + lo is within 2^-48 |x| of x.
-// |x| < 2^-126 reads as 0 (an absolute error below 1.2e-38), lo is dropped
-// where |x| < 2^-74 (relative error 2^-24 for such values), and |x| >= 2^128,
-// infinities and NaN go through the conversion instruction.
+// remaining 29 bits rounded to FP32, so hi + lo is within 2^-48 |x| of x for
+// |x| >= 2^-100 (below, lo loses bits to the FP32 subnormal range: within
+// 2^-149 absolute).  |x| < 2^-126 reads as 0 (an absolute error below
+// 1.2e-38); |x| >= 2^128, infinities and NaN go through the conversion
+// instruction.
 __device__ __forceinline__ ff dsplit(double x) {
   const unsigned uh = unsigned(__double2hiint(x)), ul = unsigned(__double2loint(x));
   const int e = int((uh >> 20) & 0x7FFu);
@@ -40,16 +41,16 @@ __device__ __forceinline__ ff dsplit(double x) {
   if (e <= 896) return {0.f, 0.f};
   if (e >= 1151) return {__double2float_rn(x), 0.f};
   const float h = __uint_as_float(sign | (unsigned(e - 896) << 23) | ((uh & 0xFFFFFu) << 3) | (ul >> 29));
-  float l = 0.f;
-  if (e > 948) {
-    // the low 29 mantissa bits r = r1 * 64 + r0, each part < 2^23 made exact
-    // by the 2^23 constant, then scaled by 2^(e - 1075)
-    const unsigned r = ul & 0x1FFFFFFFu;
-    const float r1 = __fsub_rn(__uint_as_float(0x4B000000u | (r >> 6)), 8388608.f);
-    const float r0 = __fsub_rn(__uint_as_float(0x4B000000u | (r & 63u)), 8388608.f);
-    l = __fmul_rn(fmaf(r1, 64.f, r0), __uint_as_float(unsigned(e - 948) << 23));
-    l = __uint_as_float(__float_as_uint(l) | sign);
-  }
+  // the low 29 mantissa bits r = r1 * 64 + r0, each part < 2^23 made exact by
+  // the 2^23 constant, then scaled by 2^(e - 1075) (in two steps where that
+  // power of two is below the normal FP32 range)
+  const unsigned r = ul & 0x1FFFFFFFu;
+  const float r1 = __fsub_rn(__uint_as_float(0x4B000000u | (r >> 6)), 8388608.f);
+  const float r0 = __fsub_rn(__uint_as_float(0x4B000000u | (r & 63u)), 8388608.f);
+  const float rr = fmaf(r1, 64.f, r0);
+  float l = e > 948 ? __fmul_rn(rr, __uint_as_float(unsigned(e - 948) << 23))
+                    : __fmul_rn(__fmul_rn(rr, __uint_as_float(unsigned(e - 884) << 23)), 5.421010862427522e-20f);
+  l = __uint_as_float(__float_as_uint(l) | sign);
   return {h, l};
 }
 
@@ -60,6 +61,23 @@ __device__ __forceinline__ double f2d(float f) {
   if ((u << 1) == 0u) return __hiloint2double(int(u), 0);
   if (E == 0u || E == 255u) return double(f);
   return __hiloint2double(int((u & 0x80000000u) | ((E + 896u) << 20) | ((u & 0x7FFFFFu) >> 3)), int(u << 29));
+}
+
+// x * 2^s, exact, by the exponent field where the result stays a normal
+// number (zeros pass through); otherwise the library's ldexp.
+__device__ __forceinline__ double scale2(double x, int s) {
+  const int hw = __double2hiint(x), lw = __double2loint(x);
+  const int e = (hw >> 20) & 0x7FF;
+  if (e == 0 && ((hw & 0x7FFFFFFF) | lw) == 0) return x;
+  if (e > 0 && e < 2047 && e + s > 0 && e + s < 2047) return __hiloint2double(hw + (s << 20), lw);
+  return ldexp(x, s);
+}
+
+// x rounded to FP32 (nearest) without the conversion instruction, for
+// 2^-126 <= |x| < 2^128 (smaller values read as zero)
+__device__ __forceinline__ float d2f(double x) {
+  const ff p = dsplit(x);
+  return __fadd_rn(p.h, p.l);
 }
 
 // hi + lo in FP64 (one FP64 addition)

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "ff.cuh"
 #include "krylov.hpp"
 
 namespace ibg {
@@ -789,24 +790,28 @@ __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double*
 
 // r32 = r64 * 2^-sexp, rounded to FP32: the scaled inner right-hand side
 // (only instances whose outer loop is still running)
+// (the power of two on the exponent field, the rounding from the bits: no
+// FP64 instruction per element unless a value leaves the normal range)
 __global__ void k_scale_residual(DevGrid g, const double* __restrict__ r64, float* __restrict__ r32, int nc,
                                  const OState* os) {
   KCOUNT();
   const OState& o = os[g.binst[blockIdx.x]];
   if (o.done) return;
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  for (int c = 0; c < nc; ++c) r32[c * g.nslots + s] = float(ldexp(r64[c * g.nslots + s], -o.sexp[c]));
+  for (int c = 0; c < nc; ++c) r32[c * g.nslots + s] = d2f(scale2(r64[c * g.nslots + s], -o.sexp[c]));
 }
 
 // x += e * 2^sexp (the inner solution of the scaled right-hand side), only
 // for instances whose outer loop is still running
+// (e exactly in FP64 from its bits, the power of two on the exponent field:
+// one FP64 instruction per element, the addition)
 __global__ void k_add_f2d_active(DevGrid g, const float* __restrict__ e, double* __restrict__ x, int nc,
                                  const OState* os) {
   KCOUNT();
   const OState& o = os[g.binst[blockIdx.x]];
   if (o.done) return;
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  for (int c = 0; c < nc; ++c) x[c * g.nslots + s] += ldexp(double(e[c * g.nslots + s]), o.sexp[c]);
+  for (int c = 0; c < nc; ++c) x[c * g.nslots + s] += scale2(f2d(e[c * g.nslots + s]), o.sexp[c]);
 }
 
 // ---------------------------------------------------------------- drivers

@@ -50,10 +50,10 @@ static void report(const char* name, long n, long bad) { std::printf("%s %ld %ld
 
 int main() {
   const long N = 200000;
-  // 1. dsplit: hi is x cut to 24 bits, hi + lo within 2^-48 |x| (|x| >= 2^-74)
+  // 1. dsplit: hi is x cut to 24 bits, hi + lo within 2^-48 |x| (|x| >= 2^-100)
   long bad = 0;
   for (long i = 0; i < N; ++i) {
-    const double x = rnd(-74, 100);
+    const double x = rnd(-100, 100);
     const ff s = dsplit(x);
     const long double sum = (long double)s.h + (long double)s.l;
     const bool trunc = std::fabs(double(s.h)) <= std::fabs(x) && std::signbit(s.h) == std::signbit(x) &&
@@ -61,13 +61,14 @@ int main() {
     if (!trunc || std::fabs((long double)x - sum) > std::ldexp((long double)std::fabs(x), -48)) ++bad;
   }
   report("dsplit", N, bad);
-  // tiny values read as zero; lo dropped below 2^-74
+  // tiny values read as zero; near the bottom of the FP32 range hi + lo stays
+  // within 2^-149 of x
   bad = 0;
   if (dsplit(1e-40).h != 0.f || dsplit(-0.0).h != 0.f || dsplit(0.0).l != 0.f) ++bad;
   {
-    const double x = std::ldexp(1.0 + unit(), -80);
+    const double x = std::ldexp(1.0 + unit(), -120);
     const ff s = dsplit(x);
-    if (s.l != 0.f || std::fabs(x - double(s.h)) > std::ldexp(x, -22)) ++bad;
+    if (std::fabs((long double)x - ((long double)s.h + s.l)) > std::ldexp(1.0L, -149)) ++bad;
   }
   report("dsplit_edges", 3, bad);
   // 2. f2d is the exact conversion
@@ -134,5 +135,20 @@ int main() {
     if (std::fabs((long double)p.h + (long double)p.l - want) > std::ldexp(std::fabs(want), -44)) ++bad;
   }
   report("mul", N, bad);
+  // 8. scale2 is ldexp; d2f rounds to the nearest FP32 number
+  bad = 0;
+  for (long i = 0; i < N; ++i) {
+    const double x = rnd(-300, 300);
+    const int sh = int(next() % 601) - 300;
+    if (scale2(x, sh) != std::ldexp(x, sh)) ++bad;
+  }
+  if (scale2(0.0, 5) != 0.0 || scale2(1e-310, 3) != std::ldexp(1e-310, 3)) ++bad;
+  report("scale2", N + 1, bad);
+  bad = 0;
+  for (long i = 0; i < N; ++i) {
+    const double x = rnd(-100, 120);
+    if (d2f(x) != float(x)) ++bad;
+  }
+  report("d2f", N, bad);
   return 0;
 }

@@ -8,7 +8,9 @@ seeded random inputs against long double arithmetic: the FP64 -> pair split
 conversion from the bits, exact small-integer weights, the error-free two-sum,
 a 15-term integer-weighted sum (the mass stencil) within 2^-44 of the sum of
 the terms' magnitudes, the difference of nearby values within 2^-45 of the
-difference itself, and the product with a pair constant within 2^-44.
+difference itself, the product with a pair constant within 2^-44, the power
+of two applied on the exponent field (equal to ldexp) and the rounding of an
+FP64 value to the nearest FP32 number from its bits.
 """
 import os
 import subprocess
@@ -23,6 +25,6 @@ def test_pair_arithmetic(tmp_path):
                     os.path.join(ROOT, "tests", "ff_probe.cpp"), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     rows = {ln.split()[0]: (int(ln.split()[1]), int(ln.split()[2])) for ln in out if ln.strip()}
-    assert set(rows) == {"dsplit", "dsplit_edges", "f2d", "wf", "two_sum", "madd_int", "diff", "mul"}
+    assert set(rows) == {"dsplit", "dsplit_edges", "f2d", "wf", "two_sum", "madd_int", "diff", "mul", "scale2", "d2f"}
     for name, (n, bad) in rows.items():
         assert n > 0 and bad == 0, (name, n, bad)
