@@ -960,9 +960,11 @@ __global__ void __launch_bounds__(512) k_poisson_cg(DevGrid g, const T* __restri
 // stiffness edge counts are the constant 6; elsewhere they come from a table
 // of the 256 incident-cell masks in shared memory.  The arithmetic is that of
 // k_poisson_cg, in the same order.
-// ring depth (stages)
+// ring depth: the apply (3.5 KB per brick from memory) keeps 4 bricks ahead,
+// eight CTAs per SM; the CG form (6.5 KB per brick, twice the stage) 3 ahead,
+// six CTAs per SM
 template <int NV>
-__host__ __device__ constexpr int p7_stages() { return 4; }
+__host__ __device__ constexpr int p7_stages() { return NV == 2 ? 4 : 5; }
 constexpr int P7_THREADS = 128;
 constexpr int P7_CHUNK = 8;    // bricks per chunk at most (the chunk table's)
 template <int NV>   // input vectors: 2 (z and p_old) for the CG form, 1 for the apply

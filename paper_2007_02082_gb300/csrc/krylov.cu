@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(512) k_cg_start(DevGrid g, const T* __restrict
   for (int c = 0; c < NC; ++c) {
     const bool dof = kdof(m, dmask, c), keep = kkeep(m, dmask, c);
     const int64_t i = c * g.nslots + s;
-    T rv = keep ? T(b[i] - y[i]) : T(0);
+    T rv = keep ? (y ? T(b[i] - y[i]) : b[i]) : T(0);
     T zv = rv * dinv[s];
     r[i] = rv;
     z[i] = zv;
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(512) k_cg_start_r(DevGrid g, const T* __restri
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
   const uint16_t m = g.meta[s];
   const bool dof = kdof(m, dmask), keep = kkeep(m, dmask);
-  const T rv = keep ? T(b[s] - y[s]) : T(0);
+  const T rv = keep ? (y ? T(b[s] - y[s]) : b[s]) : T(0);
   r[s] = rv;
   T tv[2] = {dof ? rv * rv : T(0), dof ? b[s] * b[s] : T(0)};
   double* out = partials + (int64_t)gridDim.x * 2;
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(512) k_bcg_start(DevGrid g, const T* __restric
   for (int c = 0; c < NC; ++c) {
     const bool dof = kdof(m, dmask, c), keep = kkeep(m, dmask, c);
     const int64_t i = c * g.nslots + s;
-    T rv = keep ? T(b[i] - y[i]) : T(0);
+    T rv = keep ? (y ? T(b[i] - y[i]) : b[i]) : T(0);
     r[i] = rv;
     rh[i] = rv;
     p[i] = T(0);
@@ -845,7 +845,7 @@ static inline void pend(Prof* p, cudaStream_t s) { if (p && p->on) p->end(s); }
 // one CG solve of A x = b in precision T (x: initial guess in, solution out)
 template <typename T, int NC>
 static cudaError_t cg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b, T* x, T* work, cudaStream_t st,
-                              CaptureCtx* cc, double rtol, const OState* skip_os) {
+                              CaptureCtx* cc, double rtol, const OState* skip_os, bool x_zero) {
   const DevGrid& g = *a.g;
   const int64_t L = int64_t(NC) * g.nslots;
   Work<T> w = carve(work, L);
@@ -857,9 +857,9 @@ static cudaError_t cg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b
     cudaError_t e = cond_handle(st, 0, &cond);
     if (e != cudaSuccess) return e;
   }
-  fe_apply<T>(g, A, NC, x, w.q, st);
-  IBG_LAUNCH((k_cg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, w.q, w.r, w.z, w.pa, A.dinv, A.dmask, a.ks,
-             rb.partials, rb.counter, cond, skip_os);
+  if (!x_zero) fe_apply<T>(g, A, NC, x, w.q, st);
+  IBG_LAUNCH((k_cg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, x_zero ? (const T*)nullptr : (const T*)w.q, w.r,
+             w.z, w.pa, A.dinv, A.dmask, a.ks, rb.partials, rb.counter, cond, skip_os);
   fe_expand2<T>(g, NC, w.z, w.pa, st);
   auto iter = [&](cudaStream_t s, const Cond& c, T* pold, T* pnew) {
     pbegin(a.prof, a.pbase + 0, s);
@@ -886,7 +886,8 @@ static const MGDev<T>* mg_of(const SolveArgs& a) {
 // CG with the multigrid V-cycle as preconditioner (Poisson, one component)
 template <typename T>
 static cudaError_t cg_mg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const MGDev<T>& mg, const T* b, T* x,
-                                 T* work, cudaStream_t st, CaptureCtx* cc, double rtol, const OState* skip_os) {
+                                 T* work, cudaStream_t st, CaptureCtx* cc, double rtol, const OState* skip_os,
+                                 bool x_zero) {
   const DevGrid& g = *a.g;
   const int64_t L = g.nslots;
   Work<T> w = carve(work, L);
@@ -898,9 +899,9 @@ static cudaError_t cg_mg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const M
     cudaError_t e = cond_handle(st, 0, &cond);
     if (e != cudaSuccess) return e;
   }
-  fe_apply<T>(g, A, 1, x, w.q, st);
-  IBG_LAUNCH(k_cg_start_r<T>, g.nbricks, DBV, 0, st, g, b, w.q, w.r, A.dmask, a.ks, rb.partials, rb.counter,
-             skip_os);
+  if (!x_zero) fe_apply<T>(g, A, 1, x, w.q, st);
+  IBG_LAUNCH(k_cg_start_r<T>, g.nbricks, DBV, 0, st, g, b, x_zero ? (const T*)nullptr : (const T*)w.q, w.r, A.dmask,
+             a.ks, rb.partials, rb.counter, skip_os);
   mg_vcycle<T>(g, mg, w.r, w.z, zs, w.q, A.dinv, A.dmask, a.ks, st, a.prof, 9);
   IBG_LAUNCH(k_cg_rz<T>, g.nschunks, DBV, 0, st, g, w.r, w.z, A.dmask, a.ks, rb.partials, rb.counter, cond, 1);
   auto iter = [&](cudaStream_t s, const Cond& c, T* pold, T* pnew) {
@@ -923,7 +924,7 @@ static cudaError_t cg_mg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const M
 
 template <typename T, int NC>
 static cudaError_t bcg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b, T* x, T* work, cudaStream_t st,
-                               CaptureCtx* cc, double rtol, const OState* skip_os) {
+                               CaptureCtx* cc, double rtol, const OState* skip_os, bool x_zero) {
   const DevGrid& g = *a.g;
   const int64_t L = int64_t(NC) * g.nslots;
   Work<T> w = carve(work, L);
@@ -934,10 +935,10 @@ static cudaError_t bcg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* 
     cudaError_t e = cond_handle(st, 0, &cond);
     if (e != cudaSuccess) return e;
   }
-  fe_apply<T>(g, A, NC, x, w.tv, st);
+  if (!x_zero) fe_apply<T>(g, A, NC, x, w.tv, st);
   const int cpl = a.coupled ? 1 : 0;
-  IBG_LAUNCH((k_bcg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, w.tv, w.r, w.rh, w.p, w.v, A.dmask, a.ks,
-             rb.partials, rb.counter, cond, skip_os, cpl);
+  IBG_LAUNCH((k_bcg_start<T, NC>), g.nbricks, DBV, 0, st, g, b, x_zero ? (const T*)nullptr : (const T*)w.tv, w.r,
+             w.rh, w.p, w.v, A.dmask, a.ks, rb.partials, rb.counter, cond, skip_os, cpl);
   // v and t hold the interface-summed operator outputs (the start kernel set v = 0)
   return run_loop(cc, st, cond, a.ks, a.ks_host, g.ninst * NC, a.max_iter, 1, 8, [&](cudaStream_t s, const Cond& c) {
     pbegin(a.prof, a.pbase + 2, s);
@@ -965,17 +966,19 @@ static cudaError_t bcg_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* 
   });
 }
 
+// x_zero: the initial guess is zero (the mixed path's corrections), so its
+// operator product is not formed and the residual starts as b
 template <typename T>
 static cudaError_t inner_enqueue(const SolveArgs& a, const OpDesc<T>& A, const T* b, T* x, T* work, cudaStream_t st,
-                                 CaptureCtx* cc, double rtol, const OState* skip_os) {
-  if (a.bicg) return a.nc == 1 ? bcg_enqueue<T, 1>(a, A, b, x, work, st, cc, rtol, skip_os)
-                               : bcg_enqueue<T, 3>(a, A, b, x, work, st, cc, rtol, skip_os);
+                                 CaptureCtx* cc, double rtol, const OState* skip_os, bool x_zero) {
+  if (a.bicg) return a.nc == 1 ? bcg_enqueue<T, 1>(a, A, b, x, work, st, cc, rtol, skip_os, x_zero)
+                               : bcg_enqueue<T, 3>(a, A, b, x, work, st, cc, rtol, skip_os, x_zero);
   if (a.nc == 1 && a.op == OP_POISSON) {
     const MGDev<T>* mg = mg_of<T>(a);
-    if (mg && mg->any) return cg_mg_enqueue<T>(a, A, *mg, b, x, work, st, cc, rtol, skip_os);
+    if (mg && mg->any) return cg_mg_enqueue<T>(a, A, *mg, b, x, work, st, cc, rtol, skip_os, x_zero);
   }
-  return a.nc == 1 ? cg_enqueue<T, 1>(a, A, b, x, work, st, cc, rtol, skip_os)
-                   : cg_enqueue<T, 3>(a, A, b, x, work, st, cc, rtol, skip_os);
+  return a.nc == 1 ? cg_enqueue<T, 1>(a, A, b, x, work, st, cc, rtol, skip_os, x_zero)
+                   : cg_enqueue<T, 3>(a, A, b, x, work, st, cc, rtol, skip_os, x_zero);
 }
 
 cudaError_t solve_enqueue(const SolveArgs& a, cudaStream_t st, CaptureCtx* cc) {
@@ -983,7 +986,7 @@ cudaError_t solve_enqueue(const SolveArgs& a, cudaStream_t st, CaptureCtx* cc) {
   OpDesc<double> A64{a.op, a.coef64, a.dmask, a.dinv64, a.prof, a.pbase};
   const int ib = (g.ninst + 127) / 128;
   if (!a.mixed) {
-    cudaError_t e = inner_enqueue<double>(a, A64, a.b, a.x, a.w64, st, cc, a.rtol, nullptr);
+    cudaError_t e = inner_enqueue<double>(a, A64, a.b, a.x, a.w64, st, cc, a.rtol, nullptr, false);
     if (e != cudaSuccess) return e;
     IBG_LAUNCH(k_collect, ib, 128, 0, st, a.ks, a.nc, g.ninst, a.rec, (OState*)nullptr);
     return cudaSuccess;
@@ -1002,7 +1005,8 @@ cudaError_t solve_enqueue(const SolveArgs& a, cudaStream_t st, CaptureCtx* cc) {
   };
   auto correction = [&](cudaStream_t s) {
     IBG_LAUNCH(k_scale_residual, g.nbricks, DBV, 0, s, g, (const double*)a.r64, a.r32, a.nc, (const OState*)a.os);
-    cudaError_t e = inner_enqueue<float>(a, A32, a.r32, a.e32, a.w32, s, cc, a.rtol_inner, a.os);
+    // the correction starts from zero (k_residual_outer cleared e32)
+    cudaError_t e = inner_enqueue<float>(a, A32, a.r32, a.e32, a.w32, s, cc, a.rtol_inner, a.os, true);
     IBG_LAUNCH(k_collect, ib, 128, 0, s, a.ks, a.nc, g.ninst, a.rec, a.os);
     IBG_LAUNCH(k_add_f2d_active, g.nbricks, DBV, 0, s, g, a.e32, a.x, a.nc, (const OState*)a.os);
     // the FP32 correction carries hanging values rounded in FP32: restore the

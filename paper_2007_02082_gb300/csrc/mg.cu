@@ -204,15 +204,17 @@ __global__ void __launch_bounds__(512, 3) k_mg_c_prolong(DevGrid g, MGLevelDev<T
   if (skip) return;
   const int nl[3] = {L0.lat_n[3 * inst], L0.lat_n[3 * inst + 1], L0.lat_n[3 * inst + 2]};
   const int lt[3] = {t & 7, (t >> 3) & 7, t >> 6};
+  // every brick's value first, the stores after: no store stands between
+  // two bricks' footprint loads, so all of them are in flight together
+  T out[CH];
 #pragma unroll
   for (int i = 0; i < CH; ++i) {
-    if (i >= nb || !(m[i] & D_VALID)) continue;   // brick padding stays zero
-    const int64_t s = (int64_t)(b0 + i) * DBV + t;
-    if (!keep_slot(m[i], dmask)) { zout[s] = T(0); continue; }
+    out[i] = T(0);
+    if (i >= nb || !keep_slot(m[i], dmask)) continue;
     const T* fp = L0.fp + sfb[i];
     const int l = sl[i];
     if (l == 0) {   // a G0 node itself: weight 1 on its own footprint entry
-      zout[s] = z[i] + T(1) * fp[t];
+      out[i] = z[i] + T(1) * fp[t];
       continue;
     }
     const int sc = 1 << l, nt = (6 + sc) / sc + 1;
@@ -240,8 +242,11 @@ __global__ void __launch_bounds__(512, 3) k_mg_c_prolong(DevGrid g, MGLevelDev<T
       const int e = ((c[2] + ((vb[k] >> 2) & 1)) * nt + (c[1] + ((vb[k] >> 1) & 1))) * nt + (c[0] + (vb[k] & 1));
       v += (T(wn[k]) * inv) * fp[e];   // a Dirichlet G0 node's entry is zero
     }
-    zout[s] = v;
+    out[i] = v;
   }
+#pragma unroll
+  for (int i = 0; i < CH; ++i)   // brick padding stays zero: no store
+    if (i < nb && (m[i] & D_VALID)) zout[(int64_t)(b0 + i) * DBV + t] = out[i];
 }
 
 // b0 = R0 (r - A z), R0 = P0^T over owner slots, in two passes.
