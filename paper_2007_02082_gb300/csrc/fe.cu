@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(512) k_rhs_mass_grad_ff(DevGrid g, const doubl
 }
 
 // out = -(1/dt) (div u, q) (k_rhs_div's operation)
-__global__ void __launch_bounds__(512) k_rhs_div_ff(DevGrid g, const double* __restrict__ u,
+__global__ void __launch_bounds__(512, 3) k_rhs_div_ff(DevGrid g, const double* __restrict__ u,
                                                     double* __restrict__ out) {
   KCOUNT();
   __shared__ ff tile[3 * TILE3];
