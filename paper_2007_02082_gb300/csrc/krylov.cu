@@ -705,14 +705,35 @@ __global__ void __launch_bounds__(512) k_bcgv_xr(DevGrid g, T* __restrict__ x, T
 }
 
 // ---------------------------------------------------------------- FP64 outer loop
-// r = b - y on DOF rows in FP64 (r64), the inner initial guess zeroed (e32);
-// ||r||^2 in FP64, and on the first pass ||b||^2 for the reference norm; per
-// component the power of two that brings ||r|| into [0.5, 1) (sexp), by which
-// k_scale_residual divides r when it rounds it to FP32 as the inner
+// r = b - y on DOF rows, formed exactly from the FP64 values as a pair of FP32
+// numbers (ff_diff; r64 holds the pairs, hi and lo, in place of FP64 values),
+// the inner initial guess zeroed (e32); ||r||^2 and, on the first pass,
+// ||b||^2 for the reference norm, each thread keeping a scaled FP32 sum of
+// squares (scale, sum: no FP64 instruction per element, no underflow for
+// entries above 2^-126) that it hands to the FP64 grid sum as scale^2 sum;
+// per component the power of two that brings ||r|| into [0.5, 1) (sexp), by
+// which k_scale_residual divides r when it rounds it to FP32 as the inner
 // right-hand side, so that the FP32 iterations never see values whose
 // squares leave the FP32 range (a problem in SI units has velocity
 // residuals near 1e-20).  Sets the outer loop condition and the condition of
 // the inner-solve branch.  One CTA per chunk of bricks.
+__device__ __forceinline__ void sumsq_add(float& scale, float& sum, float x) {
+  const float a = fabsf(x);
+  if (a == 0.f) return;
+  if (a > scale) {
+    const float q = scale / a;
+    sum = 1.f + sum * (q * q);
+    scale = a;
+  } else {
+    const float q = a / scale;
+    sum += q * q;
+  }
+}
+__device__ __forceinline__ double sumsq_value(float scale, float sum) {
+  const double s = f2d(scale);
+  return f2d(sum) * (s * s);
+}
+
 template <int NC>
 __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double* __restrict__ b,
                                                         const double* __restrict__ y, double* __restrict__ r64,
@@ -723,36 +744,43 @@ __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double*
   const int b0 = g.scbrick[blockIdx.x], b1 = g.scbrick[blockIdx.x + 1];
   const OState& oi = os[g.binst[b0]];
   const bool first = oi.iter == 0;
-  double w[2 * NC];
+  float rs[NC], rq[NC], bs[NC], bq[NC];
 #pragma unroll
-  for (int c = 0; c < 2 * NC; ++c) w[c] = 0.0;
-  // pairs of slots: 16-byte FP64 loads, 8-byte FP32 stores
+  for (int c = 0; c < NC; ++c) rs[c] = rq[c] = bs[c] = bq[c] = 0.f;
+  // pairs of slots: 16-byte FP64 loads, 16-byte pair and 8-byte FP32 stores
   const int64_t s1 = (int64_t)b1 * DBV;
   if (!oi.done) {
 #pragma unroll 2
     for (int64_t s = (int64_t)b0 * DBV + threadIdx.x * 2; s < s1; s += (int64_t)blockDim.x * 2) {
       const uint32_t mv = *reinterpret_cast<const uint32_t*>(g.meta + s);
       const uint16_t mm[2] = {uint16_t(mv & 0xFFFFu), uint16_t(mv >> 16)};
-      if (!((mm[0] | mm[1]) & D_VALID)) continue;   // brick padding: r32 and e32 stay zero there
+      if (!((mm[0] | mm[1]) & D_VALID)) continue;   // brick padding: r and e32 stay zero there
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int64_t i = c * g.nslots + s;
         const double2 bv = *reinterpret_cast<const double2*>(b + i);
         const double2 yv = *reinterpret_cast<const double2*>(y + i);
         const double be[2] = {bv.x, bv.y}, ye[2] = {yv.x, yv.y};
-        double rv[2];
+        ff rv[2];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          rv[j] = kkeep(mm[j], dmask, c) ? be[j] - ye[j] : 0.0;
+          const ff fb = dsplit(be[j]);
+          rv[j] = kkeep(mm[j], dmask, c) ? ff_diff(fb, dsplit(ye[j])) : ff{0.f, 0.f};
           if (kdof(mm[j], dmask, c)) {
-            w[2 * c] += rv[j] * rv[j];
-            if (first) w[2 * c + 1] += be[j] * be[j];
+            sumsq_add(rs[c], rq[c], rv[j].h);
+            if (first) sumsq_add(bs[c], bq[c], fb.h);
           }
         }
-        *reinterpret_cast<double2*>(r64 + i) = make_double2(rv[0], rv[1]);
+        *reinterpret_cast<float4*>(r64 + i) = make_float4(rv[0].h, rv[0].l, rv[1].h, rv[1].l);
         *reinterpret_cast<float2*>(e32 + i) = make_float2(0.f, 0.f);
       }
     }
+  }
+  double w[2 * NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    w[2 * c] = sumsq_value(rs[c], rq[c]);
+    w[2 * c + 1] = sumsq_value(bs[c], bq[c]);
   }
   double* out = partials + (int64_t)gridDim.x * 2 * NC;
   if (!grid_sum_last<double, 2 * NC>(w, partials, counter, g.scseg, g.ninst, out)) return;
@@ -788,17 +816,26 @@ __global__ void __launch_bounds__(512) k_residual_outer(DevGrid g, const double*
   }
 }
 
-// r32 = r64 * 2^-sexp, rounded to FP32: the scaled inner right-hand side
-// (only instances whose outer loop is still running)
-// (the power of two on the exponent field, the rounding from the bits: no
-// FP64 instruction per element unless a value leaves the normal range)
+// r32 = r * 2^-sexp, rounded to FP32: the scaled inner right-hand side (only
+// instances whose outer loop is still running); r comes as the pair (hi, lo)
+// that k_residual_outer stored in place of an FP64 value
 __global__ void k_scale_residual(DevGrid g, const double* __restrict__ r64, float* __restrict__ r32, int nc,
                                  const OState* os) {
   KCOUNT();
   const OState& o = os[g.binst[blockIdx.x]];
   if (o.done) return;
   const int64_t s = (int64_t)blockIdx.x * DBV + threadIdx.x;
-  for (int c = 0; c < nc; ++c) r32[c * g.nslots + s] = d2f(scale2(r64[c * g.nslots + s], -o.sexp[c]));
+  const float2* rp = reinterpret_cast<const float2*>(r64);
+  for (int c = 0; c < nc; ++c) {
+    const float2 p = rp[c * g.nslots + s];
+    // a power of two applied in at most two exact steps (the scale may leave
+    // the normal FP32 range; the scaled values do not)
+    const int e = -o.sexp[c];
+    const int e1 = e > 126 ? 126 : (e < -126 ? -126 : e);
+    const int e2 = max(-126, min(126, e - e1));
+    const float v = __fadd_rn(p.x, p.y);
+    r32[c * g.nslots + s] = __fmul_rn(__fmul_rn(v, __int_as_float((127 + e1) << 23)), __int_as_float((127 + e2) << 23));
+  }
 }
 
 // x += e * 2^sexp (the inner solution of the scaled right-hand side), only

@@ -32,7 +32,7 @@ struct SolveArgs {
   double* w64 = nullptr;       // FP64 Krylov work (8 * 3 * nslots)
   float* w32 = nullptr;        // FP32 Krylov work (8 * 3 * nslots), mixed only
   double* y64 = nullptr;       // 3 * nslots
-  double* r64 = nullptr;       // 3 * nslots
+  double* r64 = nullptr;       // 3 * nslots: the outer residual, each entry a pair of FP32 numbers (hi, lo)
   float* r32 = nullptr;        // 3 * nslots
   float* e32 = nullptr;        // 3 * nslots
   KState* ks = nullptr;        // 3 device states per instance
