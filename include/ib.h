@@ -119,8 +119,13 @@ typedef struct {
  *   precision           IB_FP64: every solve in FP64.  IB_MIXED: FP32 operators
  *                       and preconditioners inside FP64 defect correction for
  *                       the momentum, Poisson, velocity-correction and force
- *                       (A_F, Eq. 22) solves; FP64 residuals, norms, IB
- *                       interpolation and spreading
+ *                       (A_F, Eq. 22) solves; FP64 IB interpolation and
+ *                       spreading; the field solves' right-hand sides and
+ *                       outer residuals FP64-accurate (FP64 inputs and
+ *                       outputs, stencil sums carried in pairs of FP32
+ *                       numbers to about 2^-44 of the terms' magnitudes,
+ *                       differences formed exactly), their solutions
+ *                       accumulated in FP64
  *   rtol_*              relative residual tolerances of the momentum, Poisson,
  *                       velocity-correction and force solves, relative to
  *                       max(norm of b, norm of the initial residual); 0 selects
