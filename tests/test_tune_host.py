@@ -67,3 +67,36 @@ def test_tune_case_times_each_candidate_once_per_class(monkeypatch, tmp_path):
     choice2, key2, hit2, _ = T.tune_case({"slots": (1 << 20) + 4096, "max_level": 1}, "mixed", cache=cache,
                                          timer=timer)
     assert hit2 and key2 == key and choice2 == choice and len(calls) == len(T.CANDIDATES)
+
+
+def test_every_candidate_is_a_valid_description():
+    """The tuner's defaults and every candidate pass the library's own check of
+    the launch choices: ib_grid_create does not answer IB_EINVAL for them (on a
+    machine without a GPU it stops at the device with IB_ECUDA; with one it
+    returns a handle), while an out-of-range value of each choice is refused."""
+    import ctypes as C
+
+    import workloads as W
+    from paper_2007_02082_gb300 import _abi
+    from paper_2007_02082_gb300.build import build
+    from tests.test_host_setup import _desc
+    lib = _abi.bind(C.CDLL(build()))
+    case = W.cylinder_case(n=(8, 8, 16), M=100)
+
+    def status(choice):
+        d = _desc(case)
+        d.precision = _abi.IB_MIXED
+        for k, v in choice.items():
+            d.tune[_abi.TUNE_INDEX[k]] = v
+        h = C.c_void_p(0)
+        st = lib.ib_grid_create(C.byref(d), C.byref(h))
+        if h.value:
+            lib.ib_grid_destroy(h)
+        return st
+
+    assert set(T.DEFAULTS) == set(_abi.TUNE_INDEX)
+    for over in T.CANDIDATES:
+        assert set(over) <= set(_abi.TUNE_INDEX), over
+        assert status(dict(T.DEFAULTS, **over)) != _abi.IB_EINVAL, over
+    for bad in ({"poisson_kernel": 4}, {"stream_chunk": 5}, {"mg_small": 10}, {"mg_sweeps": 5}, {"mg_persist": 3}):
+        assert status(dict(T.DEFAULTS, **bad)) == _abi.IB_EINVAL, bad
