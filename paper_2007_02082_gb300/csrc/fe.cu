@@ -1483,9 +1483,11 @@ __device__ __forceinline__ void halo15(int t, int& nbk, int& li, int& ti) {
 // coefficient reads of a plain apply).
 // FUSEP: p_new = z + beta p_old while staging the tile (written for the
 // brick's nodes), y = A p_new, and per-component p.y -> alpha (POST_CG_ALPHA).
-// One CTA per chunk, the FP32 mass operator fits 40 registers without spilling
-// when asked for 3 CTAs of 512 threads per SM (57-71 and 2 CTAs otherwise);
-// every other instance keeps the compiler's own choice (a minimum of 0).
+// One CTA per chunk, the FP32 mass operator fits 40 registers (a 16-byte
+// spill) when asked for 3 CTAs of 512 threads per SM (57-71 and 2 CTAs
+// otherwise); every other instance keeps the compiler's own choice (a minimum
+// of 0).  The chunk's neighbour tables sit in shared memory, so a halo load
+// waits on no neighbour-table load.
 template <typename T, int OP, int NC, bool FUSEP, bool PB, bool SYM = false>
 __global__ void __launch_bounds__(512, (sizeof(T) == 4 && OP == OP_MASS && !PB) ? 3 : 0)
     k_apply15(DevGrid g, const T* __restrict__ x, T* __restrict__ y,
