@@ -144,6 +144,9 @@ CASES = {
     "bend_L0": lambda: W.bent_tube_case(R=0.4, Rc=1.0, l_in=0.5, l_out=0.5, h=1.0 / 10, seed=14),
     # pressure inlet on a refined face: port nodes next to hanging nodes
     "pressure_inlet_refined": lambda: W.cylinder_refined_small(n=(16, 16, 8), seed=23, inlet=W.PINLET, a0=0.16),
+    # the reduced copy of the synthetic aorta: arch, taper, three branches,
+    # five ports on two box faces, one refinement level
+    "aorta_40x40x60_L1": lambda: W.aorta_case(n=(40, 40, 60), max_level=1, M=3000, seed=44),
 }
 
 
