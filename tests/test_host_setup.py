@@ -72,6 +72,7 @@ def _desc(case):
     d.max_level, d.refine_band, d.reduce_band = case["max_level"], case["refine_band"], case["reduce_band"]
     d.nu, d.rho, d.dt = case["nu"], case["rho"], case["dt"]
     d.viscous_form = 1 if case.get("viscous", "grad") == "sym" else 0
+    d.port_tangential = _abi.IB_TANGENTIAL_ZERO if case.get("port_tangential") == "zero" else _abi.IB_TANGENTIAL_FREE
     d.n_ports = len(case["ports"])
     for k, p in enumerate(case["ports"]):
         d.ports[k] = _port_struct(p)
@@ -112,7 +113,9 @@ def run_probe(probe, case):
 def oracle_structures(case):
     m = ibfe.build_mesh(case)
     vdir = ibfe.velocity_dirichlet(m)
-    free = ~vdir & ~m.hanging
+    # the force spreads to nodes free in every component (a pressure port's
+    # tangential components are Dirichlet under the zero-tangential option)
+    free = ~ibfe.velocity_dirichlet_components(m).any(axis=1) & ~m.hanging
     ib = ibfe.IB(m, case, free)
     flags = (m.hanging * 1 + vdir * 2 + ibfe.pressure_dirichlet(m) * 4 + ((m.inlet > 0) | (m.pinlet > 0)) * 8
              + m.boundary * 16).astype(np.uint8)
@@ -147,6 +150,10 @@ CASES = {
     # the reduced copy of the synthetic aorta: arch, taper, three branches,
     # five ports on two box faces, one refinement level
     "aorta_40x40x60_L1": lambda: W.aorta_case(n=(40, 40, 60), max_level=1, M=3000, seed=44),
+    # zero tangential velocity on the pressure ports: the force is not spread
+    # onto their nodes
+    "pressure_inlet_tangential_zero": lambda: dict(W.cylinder_refined_small(n=(16, 16, 8), seed=23, inlet=W.PINLET,
+                                                                             a0=0.16), port_tangential="zero"),
 }
 
 
