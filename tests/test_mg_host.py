@@ -137,6 +137,8 @@ CASES = {
                                  W._port(2, 1, (0.0, 0.0, 3.0), 0.499, W.OUTLET)],
                        "X": np.zeros((0, 3)), "dS": np.zeros(0), "UB": np.zeros((0, 3)),
                        "inside": np.ones((24, 8, 8), np.uint8)},
+    # the reduced synthetic aorta: five ports on two faces, branches, one level
+    "aorta_small": W.aorta_case(n=(40, 40, 60), max_level=1, M=3000, seed=44, dt=0.002),
 }
 
 
