@@ -567,7 +567,19 @@ def run_serving(n_req, steps, seed=5):
                       "cells, 0-2 levels, nu 0.01-0.05; mixed path at the 1e-6 accuracy of the parity tests"}
 
 
-def run_batch_gaps(n_req, seed=5):
+def parse_tune(text):
+    """Launch choices given as "key=value,key=value" (keys of the library's
+    tune array); empty text gives None (the library's defaults)."""
+    if not text:
+        return None
+    out = {}
+    for item in text.split(","):
+        k, _, v = item.partition("=")
+        out[k.strip()] = int(v)
+    return out
+
+
+def run_batch_gaps(n_req, seed=5, tune=None):
     """How busy the GPU is inside a batched serving step: a batch of n_req
     serving requests steps through its captured graph (CUDA events, mean of 5
     steps), then steps once eagerly inside the NVTX range 'batch_step_eager'
@@ -580,7 +592,7 @@ def run_batch_gaps(n_req, seed=5):
     stream = W.serving_requests(n_req=n_req, rate=None, seed=seed, steps=40, cells_lo=32 ** 3, cells_hi=96 ** 3)
     out = {}
     for mode in ("graph", "eager"):
-        mem = [IBGrid(c, precision="mixed", deferred=True, profile=(mode == "eager")) for _, c in stream]
+        mem = [IBGrid(c, precision="mixed", deferred=True, profile=(mode == "eager"), tune=tune) for _, c in stream]
         b = IBBatch(mem)
         b.step(2)
         torch.cuda.synchronize()
@@ -607,6 +619,7 @@ def run_batch_gaps(n_req, seed=5):
         for m in mem:
             m.close()
     out["requests"] = n_req
+    out["tune"] = tune
     return out
 
 
@@ -646,12 +659,14 @@ def main():
     ap.add_argument("--batch-gaps", type=int, default=0,
                     help="only time a batch of this many serving requests (graph step, and one eager step in the "
                          "NVTX range 'batch_step_eager' for a launch-list capture) and print the result")
+    ap.add_argument("--batch-tune", default="",
+                    help="launch choices of the --batch-gaps members, e.g. 'mg_persist=2,poisson_kernel=3'")
     args = ap.parse_args()
 
     if args.batch_gaps:
         from paper_2007_02082_gb300 import load_library
         load_library(build_if_missing=True)
-        print(json.dumps({"batch_gaps": run_batch_gaps(args.batch_gaps)}))
+        print(json.dumps({"batch_gaps": run_batch_gaps(args.batch_gaps, tune=parse_tune(args.batch_tune))}))
         return
 
     rank = int(os.environ.get("RANK", "0"))

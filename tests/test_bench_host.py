@@ -30,3 +30,14 @@ def test_timed_class_bandwidth_without_launches():
     import bench
     r = bench.timed_class_bandwidth([0.0] * 12, [0] * 12, 8, False, 1000, 6800.0)
     assert r["gbs"] is None and r["frac"] is None and r["per_class_frac"] == {}
+
+
+def test_parse_tune_reads_launch_choices():
+    """--batch-tune: "key=value" pairs of the library's launch choices, every
+    key one the binding maps; an empty value keeps the library's defaults."""
+    import bench
+    from paper_2007_02082_gb300 import _abi
+    assert bench.parse_tune("") is None
+    t = bench.parse_tune("mg_persist=2, poisson_kernel=3")
+    assert t == {"mg_persist": 2, "poisson_kernel": 3}
+    assert set(t) <= set(_abi.TUNE_INDEX)
